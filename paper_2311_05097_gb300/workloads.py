@@ -1,0 +1,272 @@
+"""Seeded synthetic inputs shared by the CUDA library's tests, the oracle's
+tests and the benchmark.
+
+This module holds geometry and initial conditions only (smooth indicators of
+solids, tanh-profiled drops, parameter draws).  It contains none of the
+time-stepping arithmetic of the method and imports neither the CUDA binding
+nor the oracle.
+
+Every array is float64, x-fastest: 2D shape (ny, nx), 3D shape (nz, ny, nx).
+Cell (i, j[, k]) sits at coordinate (x, y[, z]) = (i, j[, k]).
+
+Shapes follow the paper's experiments: the drop on a cylinder of Sec. 4.2
+(initial fields of Eq. 39), porous media of Sec. 4.1, particles of Secs. 4.3-4.6.
+The micro-CT image of Sec. 4.1 and the literature data of Secs. 4.2-4.3 are not
+available; seeded synthetic stand-ins replace them.
+"""
+import math
+
+import numpy as np
+
+
+def smooth_indicator(zeta, D):
+    """1/2 (1 + tanh(2 zeta / D)) for a signed distance zeta (positive inside)."""
+    return 0.5 * (1.0 + np.tanh(2.0 * zeta / D))
+
+
+def _coords(shape):
+    if len(shape) == 2:
+        ny, nx = shape
+        y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
+                           indexing="ij")
+        return [x, y]
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return [x, y, z]
+
+
+def _periodic_dist(shape, centre):
+    """Minimum-image distance of every cell to ``centre`` on the periodic box."""
+    X = _coords(shape)
+    n = list(reversed(shape))
+    d2 = np.zeros(shape)
+    for a, xa in enumerate(X):
+        d = xa - centre[a]
+        d -= n[a] * np.floor(d / n[a] + 0.5)
+        d2 += d * d
+    return np.sqrt(d2)
+
+
+def disc(shape, centre, R, D):
+    """Smooth indicator of a disc / sphere of radius R (positive inside)."""
+    return smooth_indicator(R - _periodic_dist(shape, centre), D)
+
+
+def slab_walls(shape, thickness, D, axis=1):
+    """Smooth indicator of a wall slab straddling the periodic boundary of ``axis``
+    (x=0, y=1, z=2): cells [0, thickness) and [n - thickness, n) are solid."""
+    X = _coords(shape)
+    n = list(reversed(shape))[axis]
+    y = X[axis]
+    yc = -0.5
+    d = y - yc
+    d -= n * np.floor(d / n + 0.5)
+    return smooth_indicator(thickness - np.abs(d), D)
+
+
+def drop_field(shape, centre, R, D, phi0=None):
+    """phi = (1 - phi0) tanh(2 (R - |x - x_c|) / D): phase 1 inside the drop,
+    phase 2 outside, zero inside solids (the pattern of Eq. 39)."""
+    phi = np.tanh(2.0 * (R - _periodic_dist(shape, centre)) / D)
+    if phi0 is not None:
+        phi = (1.0 - phi0) * phi
+    return phi
+
+
+# ---------------------------------------------------------------------------------------
+# parameter sets (lattice units)
+# ---------------------------------------------------------------------------------------
+
+PAPER_DEFAULTS = dict(d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, D=4.0, solid_eps=1e-3)
+
+
+def params(**kw):
+    d = dict(sigma=0.01, D=4.0, M=0.02, eta=0.0, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
+             d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, theta_deg=90.0,
+             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3)
+    d.update(kw)
+    return d
+
+
+# ---------------------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------------------
+
+def static_drop(n=128, R=25.0, D=4.0):
+    """2D static drop, periodic box, no solid."""
+    shape = (n, n)
+    phi0 = np.zeros(shape)
+    phi = drop_field(shape, ((n - 1) / 2.0, (n - 1) / 2.0), R, D)
+    p = params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=0.1, mu1=0.1, mu2=0.01)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, steps=2000, name="static_drop_2d")
+
+
+def drop_on_cylinder(n=512, Rp=60.0, cyl=(256.0, 160.0), R0=50.0, wall=8, D=4.0,
+                     theta_deg=60.0, rho2=1e-3, mu2=1e-3):
+    """2D drop resting on a fixed cylinder between two wall slabs (Sec. 4.2 layout)."""
+    shape = (n, n)
+    phi0 = slab_walls(shape, wall, D, axis=1) + disc(shape, cyl, Rp, D)
+    centre = (cyl[0], cyl[1] + Rp)
+    phi = drop_field(shape, centre, R0, D, phi0)
+    # sigma and M are those of Secs. 4.1-4.2 (sigma_12 = 0.001, M = 0.1); at
+    # density ratio 1000 the sigma = 0.01, M = 0.02 pair of the static drop is
+    # unstable with this scheme
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=rho2, mu1=0.1, mu2=mu2,
+               theta_deg=theta_deg)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, steps=20000,
+                name="drop_on_cylinder_2d")
+
+
+def rsa_spheres(n, seed=0, rmin=8.0, rmax=16.0, porosity=0.6, reservoir=32, max_tries=200000):
+    """Random sequential addition of non-overlapping spheres in the periodic cube,
+    none in the reservoir x < ``reservoir``, until the solid fraction reaches
+    1 - porosity or the packing jams.  Returns (centres, radii)."""
+    rng = np.random.default_rng(seed)
+    cents, radii = [], []
+    target = (1.0 - porosity) * n ** 3
+    vol = 0.0
+    tries = 0
+    while vol < target and tries < max_tries:
+        tries += 1
+        r = rng.uniform(rmin, rmax)
+        c = np.array([rng.uniform(reservoir + r, n - r), rng.uniform(0, n), rng.uniform(0, n)])
+        ok = True
+        for c2, r2 in zip(cents, radii):
+            d = c - c2
+            d[1:] -= n * np.floor(d[1:] / n + 0.5)
+            if np.dot(d, d) < (r + r2 + 1.0) ** 2:
+                ok = False
+                break
+        if ok:
+            cents.append(c)
+            radii.append(r)
+            vol += 4.0 / 3.0 * math.pi * r ** 3
+    return np.array(cents).reshape(-1, 3), np.array(radii)
+
+
+def porous_drainage_3d(n=256, seed=0, D=4.0, invade=24, porosity=0.6):
+    """3D drainage: random non-overlapping spheres (radius 8-16), phase 1
+    (non-wetting, theta = 120 deg) initially fills x < ``invade``; body force
+    pushes it in +x."""
+    shape = (n, n, n)
+    cents, radii = rsa_spheres(n, seed=seed, porosity=porosity)
+    X = _coords(shape)
+    zeta = np.full(shape, -1e9)
+    for c, r in zip(cents, radii):
+        d2 = np.zeros(shape)
+        for a in range(3):
+            d = X[a] - c[a]
+            d -= n * np.floor(d / n + 0.5)
+            d2 += d * d
+        zeta = np.maximum(zeta, r - np.sqrt(d2))
+    phi0 = smooth_indicator(zeta, D)
+    x = X[0]
+    # phase-1 slab [0, invade) with smooth interfaces on both sides (periodic in x)
+    dx = x - (invade - 1) / 2.0
+    dx -= n * np.floor(dx / n + 0.5)
+    phi = (1.0 - phi0) * np.tanh(2.0 * (invade / 2.0 - np.abs(dx)) / D)
+    p = params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=0.1, mu1=0.1, mu2=0.1, theta_deg=120.0,
+               Fb=(1e-6, 0.0, 0.0))
+    achieved = float((phi0 < 0.5).mean())
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, steps=2000,
+                name="porous_drainage_3d", porosity=achieved)
+
+
+def water_entry(nx=1024, ny=2048, depth=800, wall=8, R=40.0, gap=200.0, D=4.0):
+    """2D water entry of a particle (density 2 rho1, theta 90 deg) dropped at
+    -0.02 towards a liquid pool of depth ``depth`` resting on a wall slab."""
+    shape = (ny, nx)
+    phi0 = slab_walls(shape, wall, D, axis=1)
+    y = _coords(shape)[1]
+    surface = wall + depth
+    particle = dict(x=(nx / 2.0, surface + gap, 0.0), u=(0.0, -0.02, 0.0), w=(0.0, 0.0, 0.0),
+                    R=R, rho_p=2.0)
+    solid = phi0 + disc(shape, particle["x"], R, D)
+    phi = (1.0 - solid) * np.tanh(2.0 * (surface - y) / D)
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1e-3, mu1=0.1, mu2=1e-3,
+               theta_deg=90.0, g=(0.0, -1e-6, 0.0))
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=[particle], steps=50000,
+                name="water_entry_2d")
+
+
+def equal_area_cap_base(theta_deg, area):
+    """Radius and base half-width of a circular cap of given area on a flat wall."""
+    th = math.radians(theta_deg)
+    # area of a cap of radius r and contact angle th: r^2 (th - sin th cos th)
+    r = math.sqrt(area / (th - math.sin(th) * math.cos(th)))
+    return r, r * math.sin(th)
+
+
+def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2=0.01):
+    """A semicircular drop of radius r0 (default 0.3 L, limited so that the
+    equilibrium base stays within 0.7 L) centred on the top face of a bottom
+    wall slab in an L x L periodic box."""
+    shape = (L, L)
+    phi0 = slab_walls(shape, wall, D, axis=1)
+    r0 = 0.3 * L if r0 is None else r0
+    area = 0.5 * math.pi * r0 * r0
+    _, half = equal_area_cap_base(theta_deg, area)
+    clamped = False
+    if 2.0 * half > 0.7 * L:
+        # shrink the drop until the equilibrium base is 0.7 L
+        scale = 0.7 * L / (2.0 * half)
+        r0 *= scale
+        clamped = True
+    centre = ((L - 1) / 2.0, wall - 0.5)
+    phi = drop_field(shape, centre, r0, D, phi0)
+    p = params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=1.0 / rho_ratio, mu1=mu1, mu2=mu2,
+               theta_deg=theta_deg)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, r0=r0, clamped=clamped,
+                wall=wall)
+
+
+def batch_cases(count=256, seed=1, sizes=(64, 128, 256, 512)):
+    """Parameter draws of the batched sweep: box side uniform over ``sizes``,
+    contact angle uniform in [30, 150] deg, density ratio log-uniform in
+    [1, 1000].  Fields are produced lazily by ``flat_wall_drop``."""
+    rng = np.random.default_rng(seed)
+    L = rng.choice(np.array(sizes), size=count)
+    theta = rng.uniform(30.0, 150.0, size=count)
+    ratio = np.exp(rng.uniform(0.0, math.log(1000.0), size=count))
+    return [dict(L=int(L[i]), theta_deg=float(theta[i]), rho_ratio=float(ratio[i]))
+            for i in range(count)]
+
+
+# ---------------------------------------------------------------------------------------
+# small cases for parity tests
+# ---------------------------------------------------------------------------------------
+
+def random_smooth(shape, seed, amp=1.0, modes=4):
+    """Smooth periodic random field made of a few Fourier modes."""
+    rng = np.random.default_rng(seed)
+    X = _coords(shape)
+    n = list(reversed(shape))
+    f = np.zeros(shape)
+    for _ in range(modes):
+        k = [rng.integers(1, 3) for _ in range(len(shape))]
+        ph = rng.uniform(0, 2 * math.pi)
+        arg = sum(2 * math.pi * k[a] * X[a] / n[a] for a in range(len(shape)))
+        f += rng.uniform(-1, 1) * np.sin(arg + ph)
+    return amp * f / max(1.0, np.abs(f).max())
+
+
+def small_case(shape, seed=0, solid=True, theta_deg=60.0, rho_ratio=10.0, mu_ratio=10.0,
+               D=4.0, u_amp=0.0):
+    """A drop (and, with ``solid``, a disc/sphere solid) on a small periodic box
+    with ragged sizes: used by the element-wise parity tests."""
+    rng = np.random.default_rng(seed)
+    dim = len(shape)
+    n = list(reversed(shape))
+    phi0 = np.zeros(shape)
+    if solid:
+        c = [n[a] * rng.uniform(0.25, 0.35) for a in range(dim)]
+        phi0 = disc(shape, c, 0.18 * min(n), D)
+    cd = [n[a] * rng.uniform(0.55, 0.7) for a in range(dim)]
+    phi = drop_field(shape, cd, 0.22 * min(n), D, phi0)
+    u = None
+    if u_amp > 0:
+        u = np.stack([random_smooth(shape, seed + 10 + a, amp=u_amp) for a in range(dim)])
+    p = params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=1.0 / rho_ratio, mu1=0.1,
+               mu2=0.1 / mu_ratio, theta_deg=theta_deg)
+    return dict(shape=shape, phi0=phi0, phi=phi, u=u, params=p)

@@ -1,0 +1,256 @@
+"""Physics pins of the FP64 oracle: invariants, closed forms and textbook
+reductions of the method (see the docstring of each test for the passage it
+follows).  Sizes are chosen so each test runs in seconds on a few CPU cores.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms as CF
+from oracle import oracle as O
+from paper_2311_05097_gb300 import analysis as A
+from paper_2311_05097_gb300 import workloads as W
+
+
+def make(case, **over):
+    prm = dict(case["params"])
+    prm.update(over)
+    s = O.OracleSim(case["shape"], O.make_params(**prm))
+    s.init(case["phi0"], case["phi"], case.get("u"))
+    return s
+
+
+def rel_mass_drift(m1, m0, phi_init):
+    """|sum phi(t) - sum phi(0)| / sum |phi(0)| (normalisation that stays
+    meaningful when sum phi is near zero)."""
+    return abs(m1 - m0) / np.abs(phi_init).sum()
+
+
+# ---- invariants ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("solid", [False, True])
+def test_mass_conserved_2d(solid):
+    """sum phi is conserved: the equilibrium and the source of Eq. (30) have the
+    exact zeroth moments phi and 0, and streaming only moves populations."""
+    c = W.small_case((40, 52), seed=3, solid=solid, theta_deg=60.0, u_amp=0.01)
+    s = make(c)
+    m0 = s.diagnostics()["mass"]
+    s.step(300)
+    assert rel_mass_drift(s.diagnostics()["mass"], m0, c["phi"]) < 1e-13
+
+
+def test_mass_conserved_3d():
+    c = W.small_case((12, 14, 18), seed=4, solid=True, theta_deg=120.0, u_amp=0.01)
+    s = make(c)
+    m0 = s.diagnostics()["mass"]
+    s.step(40)
+    assert rel_mass_drift(s.diagnostics()["mass"], m0, c["phi"]) < 1e-13
+
+
+def test_mass_conserved_with_moving_particle():
+    c = W.small_case((48, 40), seed=5, solid=False)
+    s = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+    s.set_particle(0, O.Particle(x=(15.0, 20.0), u=(0.01, -0.005), w=(0, 0, 0.001), R=6.0,
+                                 rho_p=2.0))
+    # phi vanishes inside solids initially (the pattern of Eq. 39)
+    phi = (1.0 - W.disc(c["shape"], (15.0, 20.0), 6.0, 4.0)) * c["phi"]
+    s.init(c["phi0"], phi)
+    m0 = s.diagnostics()["mass"]
+    s.step(100)
+    assert rel_mass_drift(s.diagnostics()["mass"], m0, phi) < 1e-13
+
+
+def energy_series(s, n_samples, every):
+    E, EK = [], []
+    for _ in range(n_samples):
+        d = s.diagnostics()
+        E.append(d["E_total"])
+        EK.append(d["E_K"])
+        s.step(every)
+    d = s.diagnostics()
+    E.append(d["E_total"])
+    EK.append(d["E_K"])
+    return np.array(E), np.array(EK)
+
+
+@pytest.mark.parametrize("case", ["drop", "wall"])
+def test_total_energy_decays(case):
+    """Theorem 1 (Sec. 2.3): with stationary geometry and no body force the total
+    energy E_F + E_K does not increase.  The lattice scheme is weakly
+    compressible, so energy also sits in pressure waves that E_total does not
+    count; sampled every 50 steps E_total must fall overall, each rise must stay
+    below the kinetic-energy scale, and rises may add up to at most 2 % of the
+    total decrease."""
+    if case == "drop":
+        c = W.static_drop(n=64, R=16.0)
+    else:
+        c = W.flat_wall_drop(64, 60.0, 10.0, r0=16, mu1=0.1, mu2=0.01)
+    s = make(c)
+    E, EK = energy_series(s, 30, 50)
+    dE = np.diff(E)
+    drop = E[0] - E[-1]
+    assert drop > 0
+    assert dE.max() <= EK.max()
+    assert dE[dE > 0].sum() <= 0.02 * drop
+
+
+# ---- closed forms -------------------------------------------------------------------
+
+def test_flat_interface_keeps_tanh_profile():
+    """phi = tanh(2 x/D) is the equilibrium of Eq. (1) (mu of Eq. (9) vanishes in
+    the continuum): a flat interface stays put, the profile changing only by the
+    O(1/D^2) discretisation error."""
+    ny, nx = 64, 4
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    D = 4.0
+    phi = np.tanh(2.0 * (16.0 - np.abs(y - 31.5)) / D)
+    case = dict(shape=(ny, nx), phi0=np.zeros((ny, nx)), phi=phi,
+                params=W.params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=0.1, mu1=0.1, mu2=0.01))
+    s = make(case)
+    s.step(500)
+    m = s.macros()
+    assert np.abs(m["phi"] - phi).max() < 2e-2
+    assert np.abs(m["u"]).max() < 2e-5
+    # the interface does not move: phi = 0 crossings stay within 0.01 cells
+    col = m["phi"][:, 1]
+    j = np.nonzero(col[:-1] * col[1:] < 0)[0]
+    xs = j + col[j] / (col[j] - col[j + 1])
+    np.testing.assert_allclose(xs, [15.5, 47.5], atol=1e-2)
+
+
+def test_laplace_law_2d():
+    """Pressure jump of a static drop: P_in - P_out = sigma/R in 2D (potential
+    form of the surface force in Eq. 16b with sigma from Eq. 1); averaged over
+    the capillary oscillation after 600 steps."""
+    R = 16.0
+    c = W.static_drop(n=64, R=R)
+    s = make(c)
+    s.step(600)
+    dps = []
+    for _ in range(24):
+        s.step(100)
+        dps.append(A.laplace_jump(s.macros()["P"], (31.5, 31.5), R, 4.0))
+    dp = float(np.mean(dps))
+    assert abs(dp / (0.01 / R) - 1.0) < 0.08
+
+
+@pytest.mark.parametrize("d0", [1.0 / 3.0, 0.4])
+def test_taylor_green_decay(d0):
+    """Single-phase reduction (sigma = 0, rho1 = rho2, phi0 = 0): the velocity of
+    a Taylor-Green vortex decays at 2 nu k^2 with nu from Eq. (35)."""
+    n, mu = 32, 0.05
+    k = 2 * math.pi / n
+    y, x = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    U = 1e-3
+    u = np.stack([U * np.sin(k * x) * np.cos(k * y), -U * np.cos(k * x) * np.sin(k * y)])
+    P = -0.25 * U * U * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    s = O.OracleSim((n, n), O.make_params(sigma=0.0, rho1=1.0, rho2=1.0, mu1=mu, mu2=mu, d0=d0))
+    s.init(np.zeros((n, n)), np.ones((n, n)), u, P)
+    s.step(20)
+    a0 = np.abs(s.macros()["u"][0]).max()
+    s.step(400)
+    a1 = np.abs(s.macros()["u"][0]).max()
+    rate = -math.log(a1 / a0) / 400
+    assert abs(rate / CF.taylor_green_rate(mu, k) - 1) < 0.01
+
+
+def poiseuille(D, wall=8, width=32, mu=0.5, Fb=1e-6, steps=12000):
+    ny, nx = width + 2 * wall, 4
+    phi0 = W.slab_walls((ny, nx), wall, D, axis=1)
+    case = dict(shape=(ny, nx), phi0=phi0, phi=1.0 - phi0,
+                params=W.params(sigma=0.0, D=D, rho1=1.0, rho2=1.0, mu1=mu, mu2=mu,
+                                Fb=(Fb, 0.0, 0.0)))
+    s = make(case)
+    s.step(steps)
+    u = s.macros()["u"][0][:, 1]
+    return u, phi0[:, 1]
+
+
+def test_poiseuille_in_indicator_channel():
+    """Channel between smooth-indicator walls driven by F_b (Eq. 16b with the
+    viscosity mu/(1 - phi0)): in the fluid core the profile is the parabola
+    u'' = -F_b/mu; the no-slip line sits inside the diffuse wall layer and moves
+    to the phi0 = 1/2 level as D shrinks."""
+    mu, Fb = 0.5, 1e-6
+    errs = []
+    for D in (4.0, 2.0):
+        u, p0 = poiseuille(D, mu=mu, Fb=Fb)
+        core = p0 < 1e-4
+        y = np.arange(len(u), dtype=float)
+        coef = np.polyfit(y[core], u[core], 2)
+        assert abs(2 * coef[0] / (-Fb / mu) - 1) < 0.01
+        # parabola through the phi0 = 1/2 levels (walls at 7.5 and 7.5 + 32)
+        h = 16.0
+        ua = Fb / (2 * mu) * (h * h - (y - 23.5) ** 2)
+        errs.append(np.linalg.norm((u - ua)[core]) / np.linalg.norm(ua[core]))
+    assert errs[1] < 0.75 * errs[0]
+
+
+def test_particle_force_and_torque_closed_form():
+    """Eq. (27) with f = phi0 (u_s - u*)/dt: a particle translating at u_p and
+    spinning at w in a fluid at rest (phi = 0, theta = 90 deg, so no capillary
+    force) feels F_f = -rho u_p int phi0 dA and T_f = -rho w int phi0 r^2 dA,
+    rho = (rho1 + rho2)/2 by Eq. (17) at phi = 0."""
+    n = 64
+    prm = O.make_params(sigma=0.01, rho1=1.0, rho2=0.5, theta_deg=90.0)
+    s = O.OracleSim((n, n), prm)
+    R, D = 9.0, 4.0
+    up, w = np.array([0.02, -0.01]), 0.003
+    s.set_particle(0, O.Particle(x=(30.3, 33.7), u=tuple(up), w=(0, 0, w), R=R, rho_p=2.0))
+    s.init(np.zeros((n, n)), np.zeros((n, n)))
+    F, T = s.particle_force(0)
+    area, mom2 = CF.tanh_indicator_moments(R, D, dim=2)
+    rho = 0.75
+    np.testing.assert_allclose(F[:2], -rho * up * area, rtol=1e-7)
+    np.testing.assert_allclose(T[2], -rho * w * mom2, rtol=1e-7)
+
+
+def test_particle_update_constant_force():
+    """Eqs. (26a), (28) by first-order explicit Euler with F_in from the last
+    velocity change: for constant F_f the velocity obeys
+    u^{n+1} - u^n = A + beta (u^n - u^{n-1}) with beta = rho/rho_p and
+    A = F_f/M_p + (1 - rho/rho_p) g, whose closed form is checked; the position
+    follows dx/dt = u_p (Eq. 26c)."""
+    prm = O.make_params(rho1=1.0, rho2=0.2, g=(0.0, -1e-5, 0.0))
+    part = O.Particle(x=(10.0, 20.0), u=(0.001, 0.0), R=5.0, rho_p=3.0)
+    Ff = np.array([2e-3, 1e-3, 0.0])
+    Tf = np.array([0.0, 0.0, 5e-3])
+    Vp = math.pi * 25.0
+    Mp = 3.0 * Vp
+    Ip = 0.5 * Mp * 25.0
+    rho = 0.6
+    beta = rho / 3.0
+    A_ = Ff[:2] / Mp + (1 - rho / 3.0) * np.array([0.0, -1e-5])
+    x0, u0 = np.array(part.x[:2]), np.array(part.u[:2])
+    nsteps = 25
+    for _ in range(nsteps):
+        part = O.particle_update(2, prm, part, Ff, Tf)
+    for a in range(2):
+        assert abs(part.u[a] - CF.constant_force_velocity(u0[a], A_[a], beta, nsteps)) < 1e-15
+        assert abs(part.x[a] - CF.constant_force_position(x0[a], u0[a], A_[a], beta, nsteps)) < 1e-12
+    alpha = Tf[2] / Ip
+    assert abs(part.w[2] - CF.constant_force_velocity(0.0, alpha, beta, nsteps)) < 1e-15
+
+
+def test_hmax_solver_geometry():
+    """The equal-area H_max of Eqs. (40)-(41): at the solution the drop circle
+    (radius r, centre k above the cylinder centre) minus the cylinder covers the
+    initial area A0 (checked by counting points on a fine grid), and at
+    theta = 90 deg k^2 = r^2 + Rp^2."""
+    Rp, R0 = 50.0, 50.0
+    A0 = CF.initial_drop_area(R0, Rp)
+    for th in (30.0, 60.0, 90.0, 120.0):
+        H, r, k = CF.hmax_on_cylinder(th, Rp, A0)
+        h = 0.05
+        xs = np.arange(-r - 1, r + 1, h)
+        ys = np.arange(k - r - 1, k + r + 1, h)
+        X, Y = np.meshgrid(xs, ys)
+        inside = ((X ** 2 + (Y - k) ** 2) < r * r) & ((X ** 2 + Y ** 2) >= Rp * Rp)
+        assert abs(inside.sum() * h * h / A0 - 1) < 2e-3
+        assert abs(H - (r + k)) < 1e-12
+        if th == 90.0:
+            assert abs(k * k - (r * r + Rp * Rp)) < 1e-9
+    # a more wetting drop is flatter
+    hs = [CF.hmax_on_cylinder(t, Rp, A0)[0] for t in (30.0, 60.0, 90.0, 120.0)]
+    assert all(a < b for a, b in zip(hs, hs[1:]))
