@@ -1,0 +1,195 @@
+/*
+ * libpf -- GB300 (sm_103a) implementation of the time-stepping hot path of the
+ * consistent and conservative lattice Boltzmann method for the gas-liquid-solid
+ * diffuse-interface model of Zhan, Liu, Chai & Shi, "A thermodynamically
+ * consistent and conservative diffuse-interface model for gas-liquid-solid
+ * multiphase flows" (arXiv 2311.05097).
+ *
+ * One time step advances two lattices in one fused kernel (Sec. 3.3, steps 2-6):
+ *   - the order-parameter lattice of Sec. 3.1 (conservative Cahn-Hilliard
+ *     equation, Eq. 2, with the chemical potential of Eq. 9),
+ *   - the flow lattice of Sec. 3.2 (consistent Navier-Stokes equations, Eq. 16,
+ *     forced by surface tension, the solid penalty rho f and wetting),
+ *   - both collided with the Hermite-moment MRT operator of Eqs. (37)-(38) and
+ *     streamed by pulling.
+ * Free rigid particles add a force/torque reduction (Eq. 27) and an explicit
+ * Newton-Euler update (Eqs. 26, 28) on the device (Sec. 3.3, steps 7-10).
+ *
+ * Lattice units throughout: dx = dt = c = 1, cs^2 = d0.  2D uses D2Q9 for both
+ * lattices; 3D uses D3Q19 (flow) and D3Q7 (order parameter).  Every boundary is
+ * periodic; walls and solids are marked by the smooth indicator phi0 (Sec. 2.1).
+ *
+ * Conventions for every call:
+ *   - Return value: PF_OK (0) or a negative PF_E* code.  The message of the last
+ *     error of the calling thread is available from pf_last_error().
+ *   - Field arrays are double, x-fastest: index (z*ny + y)*nx + x, N = nx*ny*nz.
+ *     Vector fields are component-major: u[a*N + index], a = 0..dim-1.
+ *   - `where` is PF_HOST (caller's host memory) or PF_DEVICE (device memory on
+ *     the handle's GPU).  The caller owns every array it passes; the library
+ *     copies what it needs and keeps no pointer to caller memory.
+ *   - The library owns all device state of a handle and frees it in
+ *     pf_destroy / pf_batch_destroy.
+ *   - Work is issued on the handle's stream (pf_params.stream, or a stream the
+ *     library creates when that is NULL).  pf_step is asynchronous; errors of
+ *     asynchronous work are sticky and are returned by the next call on the
+ *     handle or by pf_sync.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define PF_OK 0
+#define PF_EINVAL (-1)   /* invalid argument or parameter */
+#define PF_ENOMEM (-2)   /* device or host allocation failed */
+#define PF_ECUDA (-3)    /* a CUDA runtime call failed */
+#define PF_ENUMERIC (-4) /* a non-finite value appeared in phi or u */
+#define PF_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define PF_ESTATE (-6)   /* call out of order (e.g. step before init) */
+
+/* ---- precision policies ---- */
+#define PF_P64 0        /* FP64 storage and arithmetic */
+#define PF_P32 1        /* FP32 storage and arithmetic */
+#define PF_PMIX_FP16 2  /* FP16 moving populations (scaled by 2^k), exact
+                           fixed-point rest population of the order-parameter
+                           lattice, FP32 arithmetic and auxiliary fields */
+#define PF_PMIX_BF16 3  /* as PF_PMIX_FP16 with BF16 moving populations */
+
+/* ---- memory location of caller arrays ---- */
+#define PF_HOST 0
+#define PF_DEVICE 1
+
+/* Grid: dim = 2 or 3; nz is ignored (1) in 2D.  periodic[] must be all 1
+ * (walls are expressed through the smooth indicator phi0). */
+typedef struct pf_grid {
+    int dim;
+    int nx, ny, nz;
+    int periodic[3];
+} pf_grid;
+
+/* Model parameters, lattice units (Secs. 2-3). */
+typedef struct pf_params {
+    double sigma;      /* sigma_12, surface tension (Eq. 1); >= 0 */
+    double D;          /* interface width (Eq. 1); > 0 */
+    double M;          /* mobility (Eq. 2); > 0 */
+    double eta;        /* eta of Eq. (30); <= 0 selects 2M/cs^2, i.e. s_1phi = 1 */
+    double rho1, rho2; /* densities of phases 1 and 2 (Eq. 17); > 0 */
+    double mu1, mu2;   /* dynamic viscosities (Eq. 18); > 0 */
+    double d0;         /* cs^2 / c^2 (Sec. 3.2), in (0, 1/2) */
+    double s0, s1, s2, s3, s4; /* relaxation rates of S_H (Eq. 38), in (0, 2);
+                                  s2 is the second-order rate of the
+                                  order-parameter lattice; s_2a, s_2b of the flow
+                                  lattice follow from the viscosity (Eq. 35) */
+    double theta_deg;  /* contact angle of phase 1 on solids (Young's law, Eq. 8) */
+    double Fb[3];      /* body force density on the fluid (Eq. 16b) */
+    double g[3];       /* gravity acting on particles (Eq. 26a) */
+    double solid_eps;  /* lower bound of 1 - phi0 in mu/(1 - phi0) (Eq. 35);
+                          in (0, 1), typically 1e-3 */
+    int precision;     /* PF_P64, PF_P32, PF_PMIX_FP16, PF_PMIX_BF16 */
+    int store_log2_scale[2]; /* PMIX: stored value = population * 2^k for the
+                                order-parameter [0] and flow [1] lattices;
+                                0 selects a default from sigma, D and M */
+    void *stream;      /* cudaStream_t to issue work on, or NULL */
+} pf_params;
+
+/* A free rigid particle (Sec. 2.4), FP64.  Disc (2D, per unit depth) or
+ * sphere (3D) of radius R and density rho_p; its wettability is theta_deg of
+ * the handle.  F and T are the hydrodynamic force and torque of Eq. (27) of
+ * the last step (read only). */
+typedef struct pf_particle {
+    double x[3], u[3], w[3];
+    double R, rho_p;
+    double F[3], T[3];
+} pf_particle;
+
+/* FP64 diagnostics at the current time: mass = sum phi, E_F of Eq. (8),
+ * E_K = sum rho |u|^2 / 2, E_total = E_F + E_K (Sec. 2.3), nan_flag != 0 if
+ * any step produced a non-finite phi or u. */
+typedef struct pf_diag {
+    double mass, E_F, E_K, E_total;
+    int nan_flag;
+} pf_diag;
+
+typedef struct pf_handle pf_handle;
+typedef struct pf_batch pf_batch;
+
+/* Fill *p with the paper's defaults (d0 = 0.4, all s = 1, D = 4, Sec. 4.1),
+ * sigma = 0.01, M = 0.02, rho1 = rho2 = 1, mu1 = mu2 = 0.1, theta = 90 deg,
+ * solid_eps = 1e-3, PF_P64, NULL stream. */
+int pf_params_default(pf_params *p);
+
+/* Create a single-domain simulation.  Validates g and p (PF_EINVAL), allocates
+ * the device state (PF_ENOMEM / PF_ECUDA).  *out is set on success only. */
+int pf_create(const pf_grid *g, const pf_params *p, pf_handle **out);
+
+/* Step 1 of Sec. 3.3: set the fields and initialise both lattices with their
+ * equilibria (Eqs. 30, 32).  phi0 (fixed solids, values in [0, 1]) and phi are
+ * required; u (dim*N) and P (N) may be NULL (zero).  phi should vanish inside
+ * solids and particles (e.g. (1 - phi0) tanh(...) as in Eq. 39).  Particles set
+ * before this call are included in the indicator.  Synchronous. */
+int pf_init_fields(pf_handle *h, const double *phi0, const double *phi, const double *u,
+                   const double *P, int where);
+
+/* Advance n >= 0 time steps (Sec. 3.3 steps 2-10).  Asynchronous; replays a
+ * CUDA graph of the step sequence.  PF_ESTATE before pf_init_fields. */
+int pf_step(pf_handle *h, int64_t n);
+
+/* Macroscopic fields at the current time recomputed from the populations
+ * (Eqs. 31, 17, 36): phi (N), rho (N), u (dim*N), P (N), mu = mu_phi of Eq. (9)
+ * (N).  NULL outputs are skipped.  Synchronous. */
+int pf_get_macros(pf_handle *h, double *phi, double *rho, double *u, double *P, double *mu,
+                  int where);
+
+/* Particles: set = 1 adds (k == count) or overwrites (k < count) particle k
+ * from *inout (its F, T are ignored); set = 0 copies particle k into *inout.
+ * At most PF_MAX_PARTICLES.  Synchronous. */
+#define PF_MAX_PARTICLES 64
+int pf_particle_state(pf_handle *h, int k, pf_particle *inout, int set);
+int pf_num_particles(pf_handle *h);
+
+/* Deterministic FP64 diagnostics (fixed-order reductions).  Synchronous. */
+int pf_diagnostics(pf_handle *h, pf_diag *out);
+
+/* Wait for the handle's stream; PF_ENUMERIC if a non-finite value appeared. */
+int pf_sync(pf_handle *h);
+
+/* Number of time steps taken since pf_init_fields. */
+int64_t pf_time(pf_handle *h);
+
+void pf_destroy(pf_handle *h);
+
+/* Thread-local message of the last error (never NULL). */
+const char *pf_last_error(void);
+
+/* ---- batched independent domains (2D or 3D, one dim per batch) ----
+ * nd domains of uneven size, each with its own grid g[i] and parameters p[i]
+ * (all of one precision; stream taken from p[0]).  pf_batch_step advances all
+ * domains with one persistent launch per step captured in a CUDA graph; the
+ * tile shape and CTAs per SM are chosen by an autotuner on the first step and
+ * cached per (dim, precision, size mix). */
+int pf_batch_create(int nd, const pf_grid *g, const pf_params *p, pf_batch **out);
+int pf_batch_init(pf_batch *b, int i, const double *phi0, const double *phi, const double *u,
+                  const double *P, int where);
+int pf_batch_step(pf_batch *b, int64_t n);
+int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u, double *P,
+                        double *mu, int where);
+int pf_batch_diagnostics(pf_batch *b, int i, pf_diag *out);
+int pf_batch_sync(pf_batch *b);
+/* Total lattice cells of the batch and the chosen launch configuration
+ * (tile_x, tile_y, ctas_per_sm) after the first step; -1 before. */
+int64_t pf_batch_cells(pf_batch *b);
+int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm);
+void pf_batch_destroy(pf_batch *b);
+
+/* Number of kernel launches issued by the library since load (all handles). */
+int64_t pf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

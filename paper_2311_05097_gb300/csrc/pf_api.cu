@@ -1,0 +1,1010 @@
+// C-ABI of libpf (include/pf.h): handles, device memory, CUDA-graph replay of
+// the step sequence, batched domains and the launch-configuration autotuner.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pf.h"
+#include "pf_internal.h"
+
+namespace pf {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(long long n) { g_launches += n; }
+
+bool launch_step2d(int prec, int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
+                   const StepArgs &a)
+{
+    switch (prec) {
+    case PF_P64: return launch_step2d_p64(tx, ty, moving, mode, grid, s, a, nullptr);
+    case PF_P32: return launch_step2d_p32(tx, ty, moving, mode, grid, s, a, nullptr);
+    case PF_PMIX_FP16: return launch_step2d_mixh(tx, ty, moving, mode, grid, s, a, nullptr);
+    default: return launch_step2d_mixb(tx, ty, moving, mode, grid, s, a, nullptr);
+    }
+}
+
+int occupancy_step2d(int prec, int tx, int ty, bool moving, int mode)
+{
+    StepArgs a{};
+    int occ = 0;
+    bool ok;
+    switch (prec) {
+    case PF_P64: ok = launch_step2d_p64(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    case PF_P32: ok = launch_step2d_p32(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    case PF_PMIX_FP16: ok = launch_step2d_mixh(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    default: ok = launch_step2d_mixb(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    }
+    return ok ? occ : 0;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+// ---------------------------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------------------------
+static thread_local std::string t_err = "no error";
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+    } while (0)
+
+extern "C" const char *pf_last_error(void) { return t_err.c_str(); }
+extern "C" int64_t pf_launch_count(void) { return (int64_t)g_launches.load(); }
+
+// ---------------------------------------------------------------------------------------------
+// parameters
+// ---------------------------------------------------------------------------------------------
+extern "C" int pf_params_default(pf_params *p)
+{
+    if (!p) return fail(PF_EINVAL, "pf_params_default: NULL");
+    memset(p, 0, sizeof(*p));
+    p->sigma = 0.01;
+    p->D = 4.0;
+    p->M = 0.02;
+    p->eta = 0.0;
+    p->rho1 = p->rho2 = 1.0;
+    p->mu1 = p->mu2 = 0.1;
+    p->d0 = 0.4;
+    p->s0 = p->s1 = p->s2 = p->s3 = p->s4 = 1.0;
+    p->theta_deg = 90.0;
+    p->solid_eps = 1e-3;
+    p->precision = PF_P64;
+    return PF_OK;
+}
+
+static bool finite_all(const pf_params *p)
+{
+    const double v[] = {p->sigma, p->D, p->M, p->eta, p->rho1, p->rho2, p->mu1, p->mu2, p->d0,
+                        p->s0, p->s1, p->s2, p->s3, p->s4, p->theta_deg, p->Fb[0], p->Fb[1],
+                        p->Fb[2], p->g[0], p->g[1], p->g[2], p->solid_eps};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+static int validate(const pf_grid *g, const pf_params *p)
+{
+    if (!g || !p) return fail(PF_EINVAL, "grid or params is NULL");
+    if (g->dim != 2 && g->dim != 3) return fail(PF_EINVAL, "dim must be 2 or 3 (got %d)", g->dim);
+    if (g->dim == 3) return fail(PF_EINVAL, "3D domains are not built into this library yet");
+    const int nz = g->dim == 2 ? 1 : g->nz;
+    if (g->nx < 4 || g->ny < 4 || (g->dim == 3 && nz < 4))
+        return fail(PF_EINVAL, "grid sizes must be >= 4 (got %d x %d x %d)", g->nx, g->ny, nz);
+    if ((long long)g->nx * g->ny * nz > (1LL << 31))
+        return fail(PF_EINVAL, "grid has more than 2^31 cells");
+    for (int a = 0; a < g->dim; ++a)
+        if (g->periodic[a] != 1)
+            return fail(PF_EINVAL, "only periodic boundaries are supported (walls are phi0 slabs)");
+    if (!finite_all(p)) return fail(PF_EINVAL, "non-finite parameter");
+    if (p->sigma < 0) return fail(PF_EINVAL, "sigma must be >= 0");
+    if (p->D <= 0) return fail(PF_EINVAL, "D must be > 0");
+    if (p->M <= 0) return fail(PF_EINVAL, "M must be > 0");
+    if (p->rho1 <= 0 || p->rho2 <= 0) return fail(PF_EINVAL, "densities must be > 0");
+    if (p->mu1 <= 0 || p->mu2 <= 0) return fail(PF_EINVAL, "viscosities must be > 0");
+    if (!(p->d0 > 0 && p->d0 < 0.5)) return fail(PF_EINVAL, "d0 must lie in (0, 1/2)");
+    const double s[] = {p->s0, p->s1, p->s2, p->s3, p->s4};
+    for (double x : s)
+        if (!(x > 0 && x < 2)) return fail(PF_EINVAL, "relaxation rates must lie in (0, 2)");
+    if (!(p->solid_eps > 0 && p->solid_eps < 1)) return fail(PF_EINVAL, "solid_eps must lie in (0, 1)");
+    if (p->precision < PF_P64 || p->precision > PF_PMIX_BF16)
+        return fail(PF_EINVAL, "unknown precision %d", p->precision);
+    const double cs2 = p->d0;
+    const double eta = p->eta > 0 ? p->eta : 2.0 * p->M / cs2;
+    const double s1phi = 1.0 / (p->M / (eta * cs2) + 0.5);
+    if (!(s1phi > 0 && s1phi < 2)) return fail(PF_EINVAL, "eta gives s_1phi outside (0, 2)");
+    for (int k = 0; k < 2; ++k)
+        if (p->store_log2_scale[k] < 0 || p->store_log2_scale[k] > 24)
+            return fail(PF_EINVAL, "store_log2_scale must lie in [0, 24]");
+    return PF_OK;
+}
+
+static int default_klog2(double mag)
+{
+    // map a typical population magnitude to ~2^-2 in the stored format
+    int k = (int)std::lround(-std::log2(mag)) - 2;
+    if (k < 4) k = 4;
+    if (k > 24) k = 24;
+    return k;
+}
+
+static DevParams derive(int dim, const pf_params *p)
+{
+    DevParams d{};
+    d.sigma = p->sigma;
+    d.D = p->D;
+    d.M = p->M;
+    d.rho1 = p->rho1;
+    d.rho2 = p->rho2;
+    d.mu1 = p->mu1;
+    d.mu2 = p->mu2;
+    d.d0 = p->d0;
+    d.s0 = p->s0;
+    d.s1 = p->s1;
+    d.s2 = p->s2;
+    d.s3 = p->s3;
+    d.s4 = p->s4;
+    d.solid_eps = p->solid_eps;
+    d.dim = dim;
+    for (int a = 0; a < 3; ++a) {
+        d.Fb[a] = a < dim ? p->Fb[a] : 0.0;
+        d.g[a] = a < dim ? p->g[a] : 0.0;
+    }
+    d.cs2 = p->d0;
+    d.cs4 = d.cs2 * d.cs2;
+    d.inv_cs2 = 1.0 / d.cs2;
+    d.eta = p->eta > 0 ? p->eta : 2.0 * p->M / d.cs2;
+    d.s1phi = 1.0 / (p->M / (d.eta * d.cs2) + 0.5);  // M = (1/s_1phi - 1/2) eta cs^2
+    d.cos_t = std::cos(p->theta_deg * 3.14159265358979323846 / 180.0);
+    const double d0 = p->d0;
+    d.w0f = dim == 2 ? 1.0 - 2.0 * d0 + d0 * d0 : 1.0 - 3.0 * d0 + 3.0 * d0 * d0;
+    d.drho = 0.5 * (p->rho1 - p->rho2);
+    d.rhom = 0.5 * (p->rho1 + p->rho2);
+    d.dmu = 0.5 * (p->mu1 - p->mu2);
+    d.mum = 0.5 * (p->mu1 + p->mu2);
+    d.c_dw = 3.0 * p->sigma / p->D;
+    d.c_lap = 3.0 * p->D * p->sigma / 8.0;
+    d.c_pen = 9.0 * p->sigma / p->D;
+    d.c_wet = 3.0 * p->sigma * d.cos_t / p->D;
+    d.c_wlap = 3.0 * p->D * p->sigma * d.cos_t / 8.0;
+    d.Mdrho = p->M * d.drho;
+    if (dim == 2) {
+        d.K = 1.0 - d0;
+        d.Hc0 = (1.0 - d0) / p->s0 + 0.5 * (1.0 - 3.0 * d0);
+        d.Hc1 = 2.0 - 4.0 * d0;
+    } else {
+        d.K = 1.0 - 2.0 * d0;
+        d.Hc0 = (1.0 - d0) / p->s0 + (1.0 - 3.0 * d0);
+        d.Hc1 = 3.0 - 7.0 * d0;
+    }
+    d.Pfac = d.cs2 / (1.0 - d.w0f);
+    d.inv_1mcs2 = 1.0 / (1.0 - d.cs2);
+    d.two_over_1md0 = 2.0 / (1.0 - d0);
+    d.cut = 10.0 * p->D;
+    const bool mix = p->precision >= PF_PMIX_FP16;
+    // typical magnitudes: w_1 eta (3 sigma/D) for the order parameter, w_1 (3 sigma/D)/cs2 for flow
+    const double w1 = dim == 2 ? 0.5 * (d0 - d0 * d0) : 0.5 * d0;
+    const double musc = std::max(3.0 * p->sigma / p->D, 1e-6);
+    int k1 = p->store_log2_scale[0] ? p->store_log2_scale[0] : default_klog2(w1 * d.eta * musc);
+    int k2 = p->store_log2_scale[1] ? p->store_log2_scale[1] : default_klog2(w1 * musc / d.cs2);
+    if (!mix) k1 = k2 = 0;
+    d.klog2[0] = k1;
+    d.klog2[1] = k2;
+    d.scale[0] = std::ldexp(1.0, k1);
+    d.scale[1] = std::ldexp(1.0, k2);
+    d.inv_scale[0] = std::ldexp(1.0, -k1);
+    d.inv_scale[1] = std::ldexp(1.0, -k2);
+    return d;
+}
+
+static size_t store_bytes(int prec)
+{
+    return prec == PF_P64 ? 8 : (prec == PF_P32 ? 4 : 2);
+}
+static size_t aux_bytes(int prec) { return prec == PF_P64 ? 8 : 4; }
+
+// ---------------------------------------------------------------------------------------------
+// one domain's device memory
+// ---------------------------------------------------------------------------------------------
+struct DomainMem {
+    DomainDev d{};
+    void *base = nullptr;  // single allocation for populations, rest, aux, phi0
+    double *macro = nullptr;
+    double *staging = nullptr;  // init inputs (phi0, phi, u, P) and temporaries
+    size_t staging_n = 0;
+};
+
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams &dp, int prec)
+{
+    DomainDev &d = m.d;
+    d.nx = g->nx;
+    d.ny = g->ny;
+    d.nz = dim == 2 ? 1 : g->nz;
+    d.pitch = (int)round_up(d.nx, 32);
+    d.plane = round_up((long long)d.pitch * d.ny * d.nz, 64);
+    d.p = dp;
+    const int Q = dim == 2 ? 18 : 26;
+    const int naux = 2 * dim + 1;
+    const size_t fb = (size_t)Q * d.plane * store_bytes(prec);
+    const size_t rb = prec >= PF_PMIX_FP16 ? (size_t)d.plane * 8 : 0;
+    const size_t ab = (size_t)naux * d.plane * aux_bytes(prec);
+    const size_t pb = (size_t)d.plane * aux_bytes(prec);
+    const size_t total = 2 * fb + 2 * rb + 2 * ab + pb + 256 * 8;
+    CK(cudaMalloc(&m.base, total));
+    CK(cudaMemset(m.base, 0, total));
+    char *c = (char *)m.base;
+    auto take = [&](size_t n) {
+        void *r = c;
+        c += round_up((long long)n, 256);
+        return r;
+    };
+    d.f[0] = take(fb);
+    d.f[1] = take(fb);
+    d.rest[0] = rb ? take(rb) : nullptr;
+    d.rest[1] = rb ? take(rb) : nullptr;
+    d.aux[0] = take(ab);
+    d.aux[1] = take(ab);
+    d.phi0 = take(pb);
+    d.macro = nullptr;
+    return PF_OK;
+}
+
+static int domain_macro(DomainMem &m, int dim)
+{
+    if (m.macro) return PF_OK;
+    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
+    CK(cudaMalloc(&m.macro, sizeof(double) * (size_t)(5 + dim) * N));
+    m.d.macro = m.macro;
+    return PF_OK;
+}
+
+static int domain_staging(DomainMem &m, int dim)
+{
+    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
+    const size_t need = (size_t)(2 + dim + 1 + 2) * N;  // phi0, phi, u, P, phi0tot, mu
+    if (m.staging_n >= need) return PF_OK;
+    if (m.staging) cudaFree(m.staging);
+    m.staging = nullptr;
+    CK(cudaMalloc(&m.staging, sizeof(double) * need));
+    m.staging_n = need;
+    return PF_OK;
+}
+
+static void domain_free(DomainMem &m)
+{
+    if (m.base) cudaFree(m.base);
+    if (m.macro) cudaFree(m.macro);
+    if (m.staging) cudaFree(m.staging);
+    m = DomainMem{};
+}
+
+// copy caller arrays into the staging area and run the init kernels
+static int domain_init(DomainMem &m, int dim, int prec, const double *phi0, const double *phi,
+                       const double *u, const double *P, int where, const ParticleDev *d_parts,
+                       int np, cudaStream_t s)
+{
+    if (!phi0 || !phi) return fail(PF_EINVAL, "phi0 and phi are required");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    int rc = domain_staging(m, dim);
+    if (rc) return rc;
+    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
+    double *sp0 = m.staging, *sphi = sp0 + N, *su = sphi + N, *sP = su + dim * N, *tmp = sP + N;
+    const cudaMemcpyKind kind = where == PF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    CK(cudaMemcpyAsync(sp0, phi0, sizeof(double) * N, kind, s));
+    CK(cudaMemcpyAsync(sphi, phi, sizeof(double) * N, kind, s));
+    if (u) CK(cudaMemcpyAsync(su, u, sizeof(double) * dim * N, kind, s));
+    if (P) CK(cudaMemcpyAsync(sP, P, sizeof(double) * N, kind, s));
+    launch_init(prec, m.d, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, np, s);
+    CK(cudaGetLastError());
+    return PF_OK;
+}
+
+// tile table of a set of domains (2D tiles of tx x ty)
+static void build_tiles(const std::vector<DomainMem *> &doms, int tx, int ty, std::vector<int> &tdom,
+                        std::vector<int2> &txy)
+{
+    tdom.clear();
+    txy.clear();
+    for (size_t k = 0; k < doms.size(); ++k) {
+        DomainDev &d = doms[k]->d;
+        d.tiles_x = (d.nx + tx - 1) / tx;
+        d.tiles_y = (d.ny + ty - 1) / ty;
+        d.tiles_z = 1;
+        d.tile_base = (int)tdom.size();
+        for (int j = 0; j < d.tiles_y; ++j)
+            for (int i = 0; i < d.tiles_x; ++i) {
+                tdom.push_back((int)k);
+                txy.push_back(make_int2(i, j));
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// shared engine of single and batched handles
+// ---------------------------------------------------------------------------------------------
+struct Engine {
+    int dim = 2, prec = PF_P64;
+    std::vector<DomainMem> mem;
+    DomainDev *d_doms = nullptr;
+    int *d_tdom = nullptr;
+    int2 *d_txy = nullptr;
+    int ntiles = 0;
+    int tx = 32, ty = 8, cps = 0, grid = 0;  // tile shape, CTAs per SM, grid size
+    bool tuned = false;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int par = 0;
+    int64_t t = 0;
+    std::vector<bool> inited;
+    int *d_flags = nullptr;
+    double *d_diag = nullptr;  // partials + out
+    // particles (single-domain handles)
+    ParticleDev hp[PF_MAX_PARTICLES];
+    int np = 0;
+    ParticleDev *d_parts = nullptr;
+    double *d_partials = nullptr;
+    size_t partials_cap = 0;
+    // graph of CHUNK steps starting at parity 0
+    static constexpr int CHUNK = 16;
+    cudaGraphExec_t gexec = nullptr;
+    int sticky = PF_OK;
+};
+
+static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
+{
+    E.dim = g[0].dim;
+    E.prec = p[0].precision;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&E.nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (p[0].stream) {
+        E.stream = (cudaStream_t)p[0].stream;
+        E.own_stream = false;
+    } else {
+        CK(cudaStreamCreateWithFlags(&E.stream, cudaStreamNonBlocking));
+        E.own_stream = true;
+    }
+    E.mem.resize(nd);
+    E.inited.assign(nd, false);
+    for (int i = 0; i < nd; ++i) {
+        const DevParams dp = derive(E.dim, &p[i]);
+        int rc = domain_alloc(E.mem[i], E.dim, &g[i], dp, E.prec);
+        if (rc) return rc;
+    }
+    CK(cudaMalloc(&E.d_doms, sizeof(DomainDev) * nd));
+    CK(cudaMalloc(&E.d_flags, sizeof(int) * 4));
+    CK(cudaMemset(E.d_flags, 0, sizeof(int) * 4));
+    CK(cudaMalloc(&E.d_diag, sizeof(double) * (3 * diag_blocks() + 8)));
+    CK(cudaMalloc(&E.d_parts, sizeof(ParticleDev) * PF_MAX_PARTICLES));
+    return PF_OK;
+}
+
+static void engine_free(Engine &E)
+{
+    if (E.gexec) cudaGraphExecDestroy(E.gexec);
+    for (auto &m : E.mem) domain_free(m);
+    if (E.d_doms) cudaFree(E.d_doms);
+    if (E.d_tdom) cudaFree(E.d_tdom);
+    if (E.d_txy) cudaFree(E.d_txy);
+    if (E.d_flags) cudaFree(E.d_flags);
+    if (E.d_diag) cudaFree(E.d_diag);
+    if (E.d_parts) cudaFree(E.d_parts);
+    if (E.d_partials) cudaFree(E.d_partials);
+    if (E.own_stream && E.stream) cudaStreamDestroy(E.stream);
+    E = Engine{};
+}
+
+static void drop_graph(Engine &E)
+{
+    if (E.gexec) cudaGraphExecDestroy(E.gexec);
+    E.gexec = nullptr;
+}
+
+// upload the domain table and the tile table for shape (tx, ty)
+static int engine_tiles(Engine &E, int tx, int ty)
+{
+    std::vector<DomainMem *> ds;
+    for (auto &m : E.mem) ds.push_back(&m);
+    std::vector<int> tdom;
+    std::vector<int2> txy;
+    build_tiles(ds, tx, ty, tdom, txy);
+    if (E.d_tdom) cudaFree(E.d_tdom);
+    if (E.d_txy) cudaFree(E.d_txy);
+    E.d_tdom = nullptr;
+    E.d_txy = nullptr;
+    E.ntiles = (int)tdom.size();
+    CK(cudaMalloc(&E.d_tdom, sizeof(int) * E.ntiles));
+    CK(cudaMalloc(&E.d_txy, sizeof(int2) * E.ntiles));
+    CK(cudaMemcpy(E.d_tdom, tdom.data(), sizeof(int) * E.ntiles, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.d_txy, txy.data(), sizeof(int2) * E.ntiles, cudaMemcpyHostToDevice));
+    std::vector<DomainDev> hd;
+    for (auto &m : E.mem) hd.push_back(m.d);
+    CK(cudaMemcpy(E.d_doms, hd.data(), sizeof(DomainDev) * hd.size(), cudaMemcpyHostToDevice));
+    E.tx = tx;
+    E.ty = ty;
+    const size_t need = (size_t)E.ntiles * std::max(E.np, 1) * 6;
+    if (need > E.partials_cap) {
+        if (E.d_partials) cudaFree(E.d_partials);
+        E.d_partials = nullptr;
+        CK(cudaMalloc(&E.d_partials, sizeof(double) * need));
+        E.partials_cap = need;
+    }
+    drop_graph(E);
+    return PF_OK;
+}
+
+static StepArgs step_args(const Engine &E, int par)
+{
+    StepArgs a{};
+    a.doms = E.d_doms;
+    a.tile_dom = E.d_tdom;
+    a.tile_xy = E.d_txy;
+    a.ntiles = E.ntiles;
+    a.par = par;
+    a.parts = E.d_parts;
+    a.np = E.np;
+    a.partials = E.d_partials;
+    a.flags = E.d_flags;
+    return a;
+}
+
+// issue one time step on E.stream (step kernel, then the particle update)
+static int issue_step(Engine &E, int par)
+{
+    const StepArgs a = step_args(E, par);
+    if (!launch_step2d(E.prec, E.tx, E.ty, E.np > 0, MODE_STEP, E.grid, E.stream, a))
+        return fail(PF_EINVAL, "tile shape %dx%d not built", E.tx, E.ty);
+    if (E.np > 0)
+        launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.stream);
+    CK(cudaGetLastError());
+    return PF_OK;
+}
+
+static int grid_of(Engine &E, int cps)
+{
+    int occ = occupancy_step2d(E.prec, E.tx, E.ty, E.np > 0, MODE_STEP);
+    if (occ < 1) occ = 1;
+    int c = cps > 0 ? std::min(cps, occ) : occ;
+    long long g = (long long)c * E.nsm;
+    if (g > E.ntiles) g = E.ntiles;
+    return (int)std::max(1LL, g);
+}
+
+// Autotuner: time a few steps of each compiled tile shape and CTAs-per-SM
+// choice on the live state (the state advances; steps are counted), keep the
+// fastest; cached per (dim, precision, moving, cell-count bucket, domain count).
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, long long, int>, std::tuple<int, int, int>> g_tune_cache;
+
+static int engine_configure(Engine &E)
+{
+    long long cells = 0;
+    for (auto &m : E.mem) cells += (long long)m.d.nx * m.d.ny * m.d.nz;
+    long long bucket = 1;
+    while (bucket < cells) bucket <<= 1;
+    const auto key = std::make_tuple(E.dim, E.prec, E.np > 0 ? 1 : 0, bucket, (int)E.mem.size());
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            int tx, ty, cps;
+            std::tie(tx, ty, cps) = it->second;
+            int rc = engine_tiles(E, tx, ty);
+            if (rc) return rc;
+            E.cps = cps;
+            E.grid = grid_of(E, cps);
+            E.tuned = true;
+            return PF_OK;
+        }
+    }
+    const int shapes[][2] = {{32, 8}, {64, 4}, {32, 16}};
+    float best = 1e30f;
+    int bx = 32, by = 8, bc = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = cells > (1 << 22) ? 2 : 4;
+    for (auto &sh : shapes) {
+        int rc = engine_tiles(E, sh[0], sh[1]);
+        if (rc) return rc;
+        const int occ = std::max(1, occupancy_step2d(E.prec, sh[0], sh[1], E.np > 0, MODE_STEP));
+        for (int cps = 1; cps <= occ; cps = cps < occ ? std::min(cps * 2, occ) : occ + 1) {
+            E.cps = cps;
+            E.grid = grid_of(E, cps);
+            // warm-up (keeps the parity even so the state stays consistent)
+            for (int r = 0; r < 2; ++r) {
+                rc = issue_step(E, E.par);
+                if (rc) return rc;
+                E.par ^= 1;
+                E.t++;
+            }
+            CK(cudaEventRecord(e0, E.stream));
+            for (int r = 0; r < 2 * reps; ++r) {
+                rc = issue_step(E, E.par);
+                if (rc) return rc;
+                E.par ^= 1;
+                E.t++;
+            }
+            CK(cudaEventRecord(e1, E.stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bx = sh[0];
+                by = sh[1];
+                bc = cps;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = engine_tiles(E, bx, by);
+    if (rc) return rc;
+    E.cps = bc;
+    E.grid = grid_of(E, bc);
+    E.tuned = true;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = std::make_tuple(bx, by, bc);
+    return PF_OK;
+}
+
+static const int64_t TUNE_MIN_STEPS = 256;
+
+static int engine_step(Engine &E, int64_t n, bool autotune)
+{
+    if (E.sticky) return E.sticky;
+    if (n < 0) return fail(PF_EINVAL, "n must be >= 0");
+    for (size_t i = 0; i < E.inited.size(); ++i)
+        if (!E.inited[i]) return fail(PF_ESTATE, "domain %zu stepped before pf_init_fields", i);
+    if (n == 0) return PF_OK;
+    int64_t left = n;
+    if (!E.tuned) {
+        int rc;
+        if (autotune && n >= TUNE_MIN_STEPS) {
+            // the timed candidate steps are real steps of the simulation and
+            // count towards n (every configuration computes the same update)
+            const int64_t t0 = E.t;
+            rc = engine_configure(E);
+            left -= E.t - t0;
+        } else {
+            rc = engine_tiles(E, 32, 8);
+            E.cps = 0;
+            E.grid = grid_of(E, 0);
+            E.tuned = !autotune;
+        }
+        if (rc) return (E.sticky = rc);
+    }
+    while (left > 0 && E.par != 0) {
+        int rc = issue_step(E, E.par);
+        if (rc) return (E.sticky = rc);
+        E.par ^= 1;
+        E.t++;
+        left--;
+    }
+    if (left >= Engine::CHUNK) {
+        if (!E.gexec) {
+            const long long before = g_launches.load();
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal));
+            int rc = PF_OK;
+            for (int k = 0; k < Engine::CHUNK && rc == PF_OK; ++k) rc = issue_step(E, k & 1);
+            cudaError_t ce = cudaStreamEndCapture(E.stream, &graph);
+            if (rc) return (E.sticky = rc);
+            CK(ce);
+            CK(cudaGraphInstantiate(&E.gexec, graph, 0));
+            cudaGraphDestroy(graph);
+            g_launches = before;  // captured launches run (and are counted) at replay
+        }
+        while (left >= Engine::CHUNK) {
+            CK(cudaGraphLaunch(E.gexec, E.stream));
+            count_launches(Engine::CHUNK * (E.np > 0 ? 2 : 1));
+            left -= Engine::CHUNK;
+            E.t += Engine::CHUNK;
+        }
+    }
+    while (left > 0) {
+        int rc = issue_step(E, E.par);
+        if (rc) return (E.sticky = rc);
+        E.par ^= 1;
+        E.t++;
+        left--;
+    }
+    return PF_OK;
+}
+
+static int engine_sync(Engine &E)
+{
+    if (E.sticky) return E.sticky;
+    cudaError_t e = cudaStreamSynchronize(E.stream);
+    if (e != cudaSuccess) {
+        E.sticky = fail(PF_ECUDA, "asynchronous error: %s", cudaGetErrorString(e));
+        return E.sticky;
+    }
+    int flag = 0;
+    CK(cudaMemcpy(&flag, E.d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(PF_ENUMERIC, "a non-finite phi or u appeared");
+    return PF_OK;
+}
+
+// macroscopic pass of domain i into its macro buffer
+static int engine_macros(Engine &E, int i)
+{
+    int rc = domain_macro(E.mem[i], E.dim);
+    if (rc) return rc;
+    // a one-domain tile table for the macro kernel (32 x 8 tiles)
+    std::vector<DomainMem *> ds{&E.mem[i]};
+    std::vector<int> tdom;
+    std::vector<int2> txy;
+    DomainDev saved = E.mem[i].d;
+    build_tiles(ds, 32, 8, tdom, txy);
+    DomainDev dd = E.mem[i].d;
+    E.mem[i].d = saved;
+    E.mem[i].d.macro = E.mem[i].macro;
+    dd.macro = E.mem[i].macro;
+    DomainDev *d_dd = nullptr;
+    int *d_td = nullptr;
+    int2 *d_xy = nullptr;
+    CK(cudaMalloc(&d_dd, sizeof(DomainDev)));
+    CK(cudaMalloc(&d_td, sizeof(int) * tdom.size()));
+    CK(cudaMalloc(&d_xy, sizeof(int2) * txy.size()));
+    CK(cudaMemcpyAsync(d_dd, &dd, sizeof(DomainDev), cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync(d_td, tdom.data(), sizeof(int) * tdom.size(), cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync(d_xy, txy.data(), sizeof(int2) * txy.size(), cudaMemcpyHostToDevice, E.stream));
+    StepArgs a{};
+    a.doms = d_dd;
+    a.tile_dom = d_td;
+    a.tile_xy = d_xy;
+    a.ntiles = (int)tdom.size();
+    a.par = E.par;
+    a.parts = E.d_parts;
+    a.np = E.np;
+    a.partials = nullptr;
+    a.flags = E.d_flags;
+    const int grid = std::min<int>((int)tdom.size(), E.nsm * 4);
+    if (!launch_step2d(E.prec, 32, 8, E.np > 0, MODE_MACROS, grid, E.stream, a))
+        return fail(PF_EINVAL, "macro kernel not built");
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(E.stream));
+    cudaFree(d_dd);
+    cudaFree(d_td);
+    cudaFree(d_xy);
+    return PF_OK;
+}
+
+static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double *u, double *P,
+                             double *mu, int where)
+{
+    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (!E.inited[i]) return fail(PF_ESTATE, "pf_get_macros before pf_init_fields");
+    int rc = engine_sync(E);
+    if (rc && rc != PF_ENUMERIC) return rc;
+    rc = engine_macros(E, i);
+    if (rc) return rc;
+    const DomainMem &m = E.mem[i];
+    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
+    const cudaMemcpyKind kind = where == PF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int d = E.dim;
+    if (phi) CK(cudaMemcpy(phi, m.macro, sizeof(double) * N, kind));
+    if (rho) CK(cudaMemcpy(rho, m.macro + N, sizeof(double) * N, kind));
+    if (u) CK(cudaMemcpy(u, m.macro + 2 * N, sizeof(double) * d * N, kind));
+    if (P) CK(cudaMemcpy(P, m.macro + (2 + d) * N, sizeof(double) * N, kind));
+    if (mu) CK(cudaMemcpy(mu, m.macro + (3 + d) * N, sizeof(double) * N, kind));
+    return PF_OK;
+}
+
+static int engine_diag(Engine &E, int i, pf_diag *out)
+{
+    if (!out) return fail(PF_EINVAL, "out is NULL");
+    if (!E.inited[i]) return fail(PF_ESTATE, "pf_diagnostics before pf_init_fields");
+    int rc = engine_sync(E);
+    const int nan_flag = rc == PF_ENUMERIC ? 1 : 0;
+    if (rc && rc != PF_ENUMERIC) return rc;
+    rc = engine_macros(E, i);
+    if (rc) return rc;
+    DomainDev dd = E.mem[i].d;
+    dd.macro = E.mem[i].macro;
+    double *partial = E.d_diag, *res = E.d_diag + 3 * diag_blocks();
+    launch_diag(dd, partial, res, E.stream);
+    CK(cudaGetLastError());
+    double h[3];
+    CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    out->mass = h[0];
+    out->E_F = h[1];
+    out->E_K = h[2];
+    out->E_total = h[1] + h[2];
+    out->nan_flag = nan_flag;
+    return PF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// single-domain handle
+// ---------------------------------------------------------------------------------------------
+struct pf_handle {
+    Engine E;
+};
+
+extern "C" int pf_create(const pf_grid *g, const pf_params *p, pf_handle **out)
+{
+    if (!out) return fail(PF_EINVAL, "out is NULL");
+    int rc = validate(g, p);
+    if (rc) return rc;
+    pf_handle *h = new (std::nothrow) pf_handle();
+    if (!h) return fail(PF_ENOMEM, "host allocation failed");
+    rc = engine_setup(h->E, 1, g, p);
+    if (rc) {
+        engine_free(h->E);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PF_OK;
+}
+
+extern "C" void pf_destroy(pf_handle *h)
+{
+    if (!h) return;
+    if (h->E.stream) cudaStreamSynchronize(h->E.stream);
+    engine_free(h->E);
+    delete h;
+}
+
+static int upload_particles(Engine &E)
+{
+    CK(cudaMemcpy(E.d_parts, E.hp, sizeof(ParticleDev) * std::max(E.np, 1), cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *phi, const double *u,
+                              const double *P, int where)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    Engine &E = h->E;
+    if (E.sticky) return E.sticky;
+    CK(cudaStreamSynchronize(E.stream));
+    int rc = upload_particles(E);
+    if (rc) return rc;
+    // the fresh state starts at parity 0; reset previous-velocity memory of particles
+    for (int k = 0; k < E.np; ++k)
+        for (int a = 0; a < 3; ++a) {
+            E.hp[k].u_prev[a] = E.hp[k].u[a];
+            E.hp[k].w_prev[a] = E.hp[k].w[a];
+        }
+    rc = upload_particles(E);
+    if (rc) return rc;
+    rc = domain_init(E.mem[0], E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, E.np, E.stream);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(E.d_flags, 0, sizeof(int) * 4, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    E.par = 0;
+    E.t = 0;
+    E.inited[0] = true;
+    return PF_OK;
+}
+
+extern "C" int pf_step(pf_handle *h, int64_t n)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    return engine_step(h->E, n, false);
+}
+
+extern "C" int pf_sync(pf_handle *h)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    return engine_sync(h->E);
+}
+
+extern "C" int64_t pf_time(pf_handle *h) { return h ? h->E.t : -1; }
+
+extern "C" int pf_get_macros(pf_handle *h, double *phi, double *rho, double *u, double *P, double *mu,
+                             int where)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    return engine_get_macros(h->E, 0, phi, rho, u, P, mu, where);
+}
+
+extern "C" int pf_diagnostics(pf_handle *h, pf_diag *out)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    return engine_diag(h->E, 0, out);
+}
+
+extern "C" int pf_num_particles(pf_handle *h) { return h ? h->E.np : -1; }
+
+extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
+{
+    if (!h || !io) return fail(PF_EINVAL, "NULL argument");
+    Engine &E = h->E;
+    if (E.sticky) return E.sticky;
+    CK(cudaStreamSynchronize(E.stream));
+    if (set) {
+        if (k < 0 || k > E.np || k >= PF_MAX_PARTICLES)
+            return fail(PF_EINVAL, "particle index %d out of range (count %d)", k, E.np);
+        if (!(io->R > 0) || !(io->rho_p > 0)) return fail(PF_EINVAL, "particle needs R > 0 and rho_p > 0");
+        if (E.np > 0) CK(cudaMemcpy(E.hp, E.d_parts, sizeof(ParticleDev) * E.np, cudaMemcpyDeviceToHost));
+        ParticleDev &pp = E.hp[k];
+        memset(&pp, 0, sizeof(pp));
+        for (int a = 0; a < 3; ++a) {
+            pp.x[a] = io->x[a];
+            pp.u[a] = io->u[a];
+            pp.w[a] = io->w[a];
+            pp.u_prev[a] = io->u[a];
+            pp.w_prev[a] = io->w[a];
+        }
+        pp.R = io->R;
+        pp.rho_p = io->rho_p;
+        const bool grew = k == E.np;
+        if (grew) E.np++;
+        int rc = upload_particles(E);
+        if (rc) return rc;
+        if (grew) {
+            // partial-sum table grows with the particle count; graphs bake the count in
+            if (E.tuned) {
+                rc = engine_tiles(E, E.tx, E.ty);
+                if (rc) return rc;
+                E.grid = grid_of(E, E.cps);
+            }
+            drop_graph(E);
+        }
+        return PF_OK;
+    }
+    if (k < 0 || k >= E.np) return fail(PF_EINVAL, "particle index %d out of range (count %d)", k, E.np);
+    ParticleDev pp;
+    CK(cudaMemcpy(&pp, E.d_parts + k, sizeof(pp), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < 3; ++a) {
+        io->x[a] = pp.x[a];
+        io->u[a] = pp.u[a];
+        io->w[a] = pp.w[a];
+        io->F[a] = pp.F[a];
+        io->T[a] = pp.T[a];
+    }
+    io->R = pp.R;
+    io->rho_p = pp.rho_p;
+    return PF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// batched domains
+// ---------------------------------------------------------------------------------------------
+struct pf_batch {
+    Engine E;
+};
+
+extern "C" int pf_batch_create(int nd, const pf_grid *g, const pf_params *p, pf_batch **out)
+{
+    if (!out || nd < 1 || !g || !p) return fail(PF_EINVAL, "bad arguments");
+    for (int i = 0; i < nd; ++i) {
+        int rc = validate(&g[i], &p[i]);
+        if (rc) return rc;
+        if (g[i].dim != g[0].dim || p[i].precision != p[0].precision)
+            return fail(PF_EINVAL, "all domains of a batch share dim and precision");
+    }
+    pf_batch *b = new (std::nothrow) pf_batch();
+    if (!b) return fail(PF_ENOMEM, "host allocation failed");
+    int rc = engine_setup(b->E, nd, g, p);
+    if (rc) {
+        engine_free(b->E);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PF_OK;
+}
+
+extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const double *phi, const double *u,
+                             const double *P, int where)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    Engine &E = b->E;
+    if (i < 0 || i >= (int)E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
+    if (E.sticky) return E.sticky;
+    if (E.t != 0) return fail(PF_ESTATE, "all domains are initialised before the first step");
+    int rc = domain_init(E.mem[i], E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, 0, E.stream);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(E.stream));
+    // the staging area is only needed during init
+    cudaFree(E.mem[i].staging);
+    E.mem[i].staging = nullptr;
+    E.mem[i].staging_n = 0;
+    E.inited[i] = true;
+    return PF_OK;
+}
+
+extern "C" int pf_batch_step(pf_batch *b, int64_t n)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    return engine_step(b->E, n, true);
+}
+
+extern "C" int pf_batch_sync(pf_batch *b)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    return engine_sync(b->E);
+}
+
+extern "C" int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u, double *P,
+                                   double *mu, int where)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    if (i < 0 || i >= (int)b->E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
+    int rc = engine_get_macros(b->E, i, phi, rho, u, P, mu, where);
+    // macro buffers of a large batch are released after use
+    if (b->E.mem[i].macro) {
+        cudaFree(b->E.mem[i].macro);
+        b->E.mem[i].macro = nullptr;
+        b->E.mem[i].d.macro = nullptr;
+    }
+    return rc;
+}
+
+extern "C" int pf_batch_diagnostics(pf_batch *b, int i, pf_diag *out)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    if (i < 0 || i >= (int)b->E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
+    int rc = engine_diag(b->E, i, out);
+    if (b->E.mem[i].macro) {
+        cudaFree(b->E.mem[i].macro);
+        b->E.mem[i].macro = nullptr;
+        b->E.mem[i].d.macro = nullptr;
+    }
+    return rc;
+}
+
+extern "C" int64_t pf_batch_cells(pf_batch *b)
+{
+    if (!b) return -1;
+    long long c = 0;
+    for (auto &m : b->E.mem) c += (long long)m.d.nx * m.d.ny * m.d.nz;
+    return c;
+}
+
+extern "C" int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    if (!b->E.tuned) {
+        if (tile_x) *tile_x = -1;
+        if (tile_y) *tile_y = -1;
+        if (ctas_per_sm) *ctas_per_sm = -1;
+        return PF_OK;
+    }
+    if (tile_x) *tile_x = b->E.tx;
+    if (tile_y) *tile_y = b->E.ty;
+    if (ctas_per_sm) *ctas_per_sm = b->E.cps;
+    return PF_OK;
+}
+
+extern "C" void pf_batch_destroy(pf_batch *b)
+{
+    if (!b) return;
+    if (b->E.stream) cudaStreamSynchronize(b->E.stream);
+    engine_free(b->E);
+    delete b;
+}

@@ -1,0 +1,263 @@
+// Device-side building blocks shared by the libpf kernels (sm_103a).
+//
+// Storage layout of one domain (all arrays structure-of-arrays, x fastest):
+//   f[q][plane]     populations of both lattices: q in [0, Q1) order parameter,
+//                   q in [Q1, Q1+Q2) flow; two buffers (pull streaming A -> B).
+//   rest[plane]     PMIX only: rest population of the order-parameter lattice
+//                   as a signed 64-bit fixed-point number (REST_FRAC_BITS).
+//   aux[k][plane]   lagged fields of the previous step: u (dim), S (dim), phi;
+//                   two buffers (neighbours read the old copy).
+//   phi0[plane]     indicator of the fixed solids.
+// plane = pitch * ny * nz rounded up to 64 elements; cell index
+// (z*ny + y)*pitch + x.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace pf {
+
+constexpr int REST_FRAC_BITS = 50;  // rest population = value * 2^-50
+
+enum Mode { MODE_STEP = 0, MODE_MACROS = 1 };
+
+// ---- precision policies ------------------------------------------------------------------
+struct P64 {
+    using real = double;
+    using store = double;
+    using aux = double;
+    static constexpr bool MIX = false;
+    static constexpr int id = 0;
+};
+struct P32 {
+    using real = float;
+    using store = float;
+    using aux = float;
+    static constexpr bool MIX = false;
+    static constexpr int id = 1;
+};
+struct PMixH {
+    using real = float;
+    using store = __half;
+    using aux = float;
+    static constexpr bool MIX = true;
+    static constexpr int id = 2;
+};
+struct PMixB {
+    using real = float;
+    using store = __nv_bfloat16;
+    using aux = float;
+    static constexpr bool MIX = true;
+    static constexpr int id = 3;
+};
+
+// ---- per-domain constants (computed on the host in double) ----------------------------------
+struct DevParams {
+    double sigma, D, M, eta, rho1, rho2, mu1, mu2, d0;
+    double s0, s1, s2, s3, s4, s1phi, cos_t, solid_eps;
+    double Fb[3], g[3];
+    // derived
+    double cs2, cs4, inv_cs2;
+    double w0f;        // rest weight of the flow lattice
+    double drho, rhom; // (rho1 - rho2)/2, (rho1 + rho2)/2
+    double dmu, mum;   // (mu1 - mu2)/2, (mu1 + mu2)/2
+    double c_dw;       // 3 sigma / D           (double well)
+    double c_lap;      // 3 D sigma / 8         (gradient term)
+    double c_pen;      // 9 sigma / D           (solid penalty)
+    double c_wet;      // 3 sigma cos(theta)/D  (wetting)
+    double c_wlap;     // 3 D sigma cos(theta)/8
+    double Mdrho;      // M (rho1 - rho2)/2
+    double K, Hc0, Hc1;  // H = K [Hc0 - Hc1 / s2a]
+    double Pfac;       // cs2 / (1 - w0)
+    double inv_1mcs2;  // 1 / (1 - cs2)
+    double two_over_1md0;  // 2 / (1 - d0)
+    double scale[2], inv_scale[2];  // PMIX population scales 2^k
+    double cut;        // particle indicator is exactly 0 beyond R + cut
+    int klog2[2];      // PMIX scale exponents k of 2^k
+    int dim;
+};
+
+struct ParticleDev {
+    double x[3], u[3], w[3];
+    double R, rho_p;
+    double u_prev[3], w_prev[3];
+    double F[3], T[3];
+};
+
+// One domain of a (possibly batched) launch.
+struct DomainDev {
+    int nx, ny, nz, pitch;
+    long long plane;
+    void *f[2];      // population buffers
+    void *rest[2];   // PMIX rest populations
+    void *aux[2];    // lagged fields
+    void *phi0;      // fixed indicator
+    double *macro;   // MODE_MACROS output: phi, rho, u(dim), P, mu, phi0 (double)
+    int tile_base;   // index of this domain's first tile in the partial-sum table
+    int tiles_x, tiles_y, tiles_z;
+    DevParams p;
+};
+
+// Arguments of the step / macro kernels (2D and 3D).
+struct StepArgs {
+    const DomainDev *doms;
+    const int *tile_dom;   // domain of each tile
+    const int2 *tile_xy;   // tile coordinates (x, y) in tiles
+    int ntiles;
+    int par;               // read buffer parity
+    const ParticleDev *parts;
+    int np;
+    double *partials;      // [tile][particle][6]: F_f and T_f partial sums (Eq. 27)
+    int *flags;            // [0]: non-finite value seen
+};
+
+// ---- helpers -----------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+template <>
+__device__ __forceinline__ __half ldg<__half>(const __half *p)
+{
+    unsigned short v = __ldg(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_half(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 ldg<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    unsigned short v = __ldg(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_bfloat16(v);
+}
+
+// population store <-> compute conversion
+template <class P>
+struct Conv;
+template <>
+struct Conv<P64> {
+    static __device__ __forceinline__ double ld(double v, double) { return v; }
+    static __device__ __forceinline__ double st(double v, double) { return v; }
+};
+template <>
+struct Conv<P32> {
+    static __device__ __forceinline__ float ld(float v, float) { return v; }
+    static __device__ __forceinline__ float st(float v, float) { return v; }
+};
+template <>
+struct Conv<PMixH> {
+    static __device__ __forceinline__ float ld(__half v, float inv_scale)
+    {
+        return __half2float(v) * inv_scale;
+    }
+    static __device__ __forceinline__ __half st(float v, float scale)
+    {
+        return __float2half_rn(v * scale);
+    }
+};
+template <>
+struct Conv<PMixB> {
+    // Values whose fixed-point image would carry bits below 2^-REST_FRAC_BITS
+    // are flushed to zero so every stored value is exact in fixed point.
+    static __device__ __forceinline__ float ld(__nv_bfloat16 v, float inv_scale)
+    {
+        return __bfloat162float(v) * inv_scale;
+    }
+    static __device__ __forceinline__ __nv_bfloat16 st(float v, float scale)
+    {
+        __nv_bfloat16 b = __float2bfloat16_rn(v * scale);
+        return b;
+    }
+};
+
+// Fixed-point image (value * 2^REST_FRAC_BITS) of a stored 16-bit population
+// whose real value is stored * 2^-k.  Exact for every finite input (FP16 with
+// k <= 25; BF16 after the flush in bf16_flush).  Sets *bad for inf/nan.
+__device__ __forceinline__ long long fixed_of_half(__half h, int k, int *bad)
+{
+    unsigned int b = __half_as_ushort(h);
+    int e = (b >> 10) & 0x1f;
+    long long mant = b & 0x3ff;
+    if (e == 31) {
+        *bad = 1;
+        return 0;
+    }
+    if (e) mant |= 0x400;
+    int E = e ? e : 1;
+    // value = mant * 2^(E - 25 - k); fixed = mant * 2^(E - 25 - k + FRAC)
+    int sh = E - 25 - k + REST_FRAC_BITS;
+    if (sh > 62 - 11) {  // |value| >= 2^12: outside the fixed-point range
+        *bad = 1;
+        return 0;
+    }
+    long long v = mant << sh;
+    return (b & 0x8000) ? -v : v;
+}
+
+__device__ __forceinline__ long long fixed_of_bf16(__nv_bfloat16 h, int k, int *bad)
+{
+    unsigned int b = __bfloat16_as_ushort(h);
+    int e = (b >> 7) & 0xff;
+    long long mant = b & 0x7f;
+    if (e == 255) {
+        *bad = 1;
+        return 0;
+    }
+    if (e == 0) return 0;  // subnormals are flushed when stored
+    mant |= 0x80;
+    // value = mant * 2^(e - 134 - k)
+    int sh = e - 134 - k + REST_FRAC_BITS;
+    if (sh < 0) return 0;  // flushed when stored (see bf16_flush)
+    if (sh > 62 - 8) {
+        *bad = 1;
+        return 0;
+    }
+    long long v = mant << sh;
+    return (b & 0x8000) ? -v : v;
+}
+
+// Zero a BF16 whose fixed-point image would need bits below 2^-FRAC.
+__device__ __forceinline__ __nv_bfloat16 bf16_flush(__nv_bfloat16 h, int k)
+{
+    unsigned int b = __bfloat16_as_ushort(h);
+    int e = (b >> 7) & 0xff;
+    if (e == 0 || (e != 255 && e - 134 - k + REST_FRAC_BITS < 0)) return __ushort_as_bfloat16(0);
+    return h;
+}
+
+template <class S>
+__device__ __forceinline__ long long fixed_of(S h, int k, int *bad);
+template <>
+__device__ __forceinline__ long long fixed_of<__half>(__half h, int k, int *bad)
+{
+    return fixed_of_half(h, k, bad);
+}
+template <>
+__device__ __forceinline__ long long fixed_of<__nv_bfloat16>(__nv_bfloat16 h, int k, int *bad)
+{
+    return fixed_of_bf16(h, k, bad);
+}
+
+__device__ __forceinline__ float float_of_fixed(long long v)
+{
+    // split conversion: hi * 2^32 + lo, both exact in float arithmetic up to rounding of the sum
+    int hi = (int)(v >> 32);
+    unsigned int lo = (unsigned int)(v & 0xffffffffull);
+    return __fmaf_rn((float)hi, 4294967296.0f, (float)lo) * (1.0f / 1125899906842624.0f);
+}
+
+__device__ __forceinline__ double double_of_fixed(long long v)
+{
+    return (double)v * (1.0 / 1125899906842624.0);  // 2^-50, exact for |v| < 2^53
+}
+
+__device__ __forceinline__ long long fixed_of_double(double v)
+{
+    return __double2ll_rn(v * 1125899906842624.0);
+}
+
+__device__ __forceinline__ int wrap_idx(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+}  // namespace pf

@@ -1,0 +1,518 @@
+// 2D fused time step of both D2Q9 lattices (Sec. 3.3, steps 2-6 and 7).
+//
+// One CTA updates a TX x TY tile of one domain per iteration of a persistent
+// loop over a tile table (single domain or a batch of uneven domains).  Per
+// tile, in shared memory:
+//   stage A: phi (pulled and summed, Eq. 31) and phi0 on the tile + 2 halo,
+//            w = S_x u_y - u_x S_y of the previous step on the tile + 1 halo;
+//   stage B: mu_phi (Eq. 9) on the tile + 1 halo;
+//   stage C: per cell gradients, S, F (Eq. 33), u*, f, u, P (Eq. 36),
+//            relaxation rates (Eq. 35), Hermite-moment collision of both
+//            lattices (Eqs. 29, 37, 38), store (pull streaming: f_i(x) at
+//            t+1 is read from x - c_i), lagged fields, particle partial sums.
+// Each cell's own populations are read once from DRAM; halo re-reads hit L2.
+#pragma once
+
+#include "pf_common.cuh"
+
+namespace pf {
+
+// D2Q9 velocities in the order of the columns of M_0 (Eq. 38).
+__device__ constexpr int CX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ constexpr int CY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+
+// Hermite-moment MRT collision of one D2Q9 cell (Eqs. 29, 37, 38 with c = 1):
+// h = N_H M_0 f; h* = h - S (h - heq) + (1 - S/2) hF; f* = M_0^-1 N_H^-1 h*.
+template <class R>
+__device__ __forceinline__ void collide9(R f[9], const R heq[9], const R hF[9], const R S[9],
+                                         R cs2)
+{
+    const R cs4 = cs2 * cs2;
+    // raw moments (rows of M_0)
+    R a57 = f[5] + f[7], a68 = f[6] + f[8];
+    R m0 = f[0] + f[1] + f[2] + f[3] + f[4] + a57 + a68;
+    R m1 = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    R m2 = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    R m8 = a57 + a68;
+    R m3 = f[1] + f[3] + m8;
+    R m4 = f[2] + f[4] + m8;
+    R m5 = a57 - a68;
+    R m6 = f[5] - f[6] - f[7] + f[8];
+    R m7 = f[5] + f[6] - f[7] - f[8];
+    // Hermite moments (rows of N_H)
+    R h[9];
+    h[0] = m0;
+    h[1] = m1;
+    h[2] = m2;
+    h[3] = m3 - cs2 * m0;
+    h[4] = m4 - cs2 * m0;
+    h[5] = m5;
+    h[6] = m6 - cs2 * m1;
+    h[7] = m7 - cs2 * m2;
+    h[8] = m8 - cs2 * (m3 + m4) + cs4 * m0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+        h[k] = h[k] - S[k] * (h[k] - heq[k]) + (R(1) - R(0.5) * S[k]) * hF[k];
+    // back to raw moments (N_H^-1)
+    m0 = h[0];
+    m1 = h[1];
+    m2 = h[2];
+    m3 = h[3] + cs2 * h[0];
+    m4 = h[4] + cs2 * h[0];
+    m5 = h[5];
+    m6 = h[6] + cs2 * h[1];
+    m7 = h[7] + cs2 * h[2];
+    m8 = h[8] + cs2 * (h[3] + h[4]) + cs4 * h[0];
+    // populations (M_0^-1)
+    const R q = R(0.25), hh = R(0.5);
+    f[5] = q * (m8 + m5 + m6 + m7);
+    f[6] = q * (m8 - m5 - m6 + m7);
+    f[7] = q * (m8 + m5 - m6 - m7);
+    f[8] = q * (m8 - m5 + m6 - m7);
+    f[1] = hh * (m3 - m8 + m1 - m6);
+    f[3] = hh * (m3 - m8 - m1 + m6);
+    f[2] = hh * (m4 - m8 + m2 - m7);
+    f[4] = hh * (m4 - m8 - m2 + m7);
+    f[0] = m0 - m3 - m4 + m8;
+}
+
+// Isotropic central stencils on a shared-memory array (Sec. 3.2, last
+// paragraph): D2Q9 weights 4/9, 1/9, 1/36 with cs^2 = 1/3.
+template <class R, int W>
+__device__ __forceinline__ void grad9(const R (*a)[W], int x, int y, R &gx, R &gy)
+{
+    const R e = a[y][x + 1], w = a[y][x - 1], n = a[y + 1][x], s = a[y - 1][x];
+    const R ne = a[y + 1][x + 1], nw = a[y + 1][x - 1], sw = a[y - 1][x - 1],
+            se = a[y - 1][x + 1];
+    const R third = R(1) / R(3), twelfth = R(1) / R(12);
+    gx = third * (e - w) + twelfth * ((ne + se) - (nw + sw));
+    gy = third * (n - s) + twelfth * ((ne + nw) - (se + sw));
+}
+
+template <class R, int W>
+__device__ __forceinline__ R lap9(const R (*a)[W], int x, int y)
+{
+    const R c = a[y][x];
+    const R side = a[y][x + 1] + a[y][x - 1] + a[y + 1][x] + a[y - 1][x];
+    const R diag = a[y + 1][x + 1] + a[y + 1][x - 1] + a[y - 1][x - 1] + a[y - 1][x + 1];
+    return R(2) / R(3) * (side - R(4) * c) + R(1) / R(6) * (diag - R(4) * c);
+}
+
+// Smooth indicator of particle k at cell (gx, gy) (minimum image), 0 beyond
+// R + cut where 1/2 (1 + tanh) rounds to 0 in both precisions.
+template <class R>
+__device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy, int nx, int ny,
+                                           double D, double cut, R &rx, R &ry)
+{
+    double dx = (double)gx - pp.x[0], dy = (double)gy - pp.x[1];
+    dx -= nx * rint(dx / nx);
+    dy -= ny * rint(dy / ny);
+    rx = (R)dx;
+    ry = (R)dy;
+    double r2 = dx * dx + dy * dy;
+    double lim = pp.R + cut;
+    if (r2 >= lim * lim) return R(0);
+    R r = sqrt((R)r2);
+    return R(0.5) * (R(1) + tanh(R(2) * ((R)pp.R - r) / (R)D));
+}
+
+template <class P, int TX, int TY, bool MOVING, int MODE>
+__global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
+{
+    using R = typename P::real;
+    using ST = typename P::store;
+    using AX = typename P::aux;
+    constexpr int NT = TX * TY;
+    constexpr int FX = TX + 4, FY = TY + 4;   // tile + 2 frame
+    constexpr int WX = TX + 2, WY = TY + 2;   // tile + 1 frame
+    __shared__ R s_phi[FY][FX];
+    __shared__ R s_p0[FY][FX];
+    __shared__ R s_mu[WY][WX];
+    __shared__ R s_w[WY][WX];
+    __shared__ int s_gx[TX + 6];
+    __shared__ long long s_gy[TY + 6];
+    __shared__ int s_gyi[TY + 6];
+    __shared__ double s_red[NT / 32][6];
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+        const DomainDev &Dm = A.doms[A.tile_dom[t]];
+        const int2 txy = A.tile_xy[t];
+        const int nx = Dm.nx, ny = Dm.ny;
+        const long long plane = Dm.plane;
+        const int x0 = txy.x * TX, y0 = txy.y * TY;
+        const DevParams &p = Dm.p;
+
+        __syncthreads();  // previous tile's shared-memory readers are done
+        for (int k = tid; k < TX + 6; k += NT) s_gx[k] = wrap_idx(x0 - 3 + k, nx);
+        for (int k = tid; k < TY + 6; k += NT) {
+            const int yy = wrap_idx(y0 - 3 + k, ny);
+            s_gyi[k] = yy;
+            s_gy[k] = (long long)yy * Dm.pitch;
+        }
+        __syncthreads();
+
+        const ST *fs = reinterpret_cast<const ST *>(Dm.f[A.par]);
+        ST *fd = reinterpret_cast<ST *>(Dm.f[A.par ^ 1]);
+        const AX *as = reinterpret_cast<const AX *>(Dm.aux[A.par]);
+        AX *ad = reinterpret_cast<AX *>(Dm.aux[A.par ^ 1]);
+        const AX *ph0 = reinterpret_cast<const AX *>(Dm.phi0);
+        const long long *rs = reinterpret_cast<const long long *>(Dm.rest[A.par]);
+        long long *rd = reinterpret_cast<long long *>(Dm.rest[A.par ^ 1]);
+        const R isc1 = (R)p.inv_scale[0], isc2 = (R)p.inv_scale[1];
+
+        // phi at frame cell (hx, hy) of the tile+2 frame: pull and sum (Eq. 31)
+        auto phi_at = [&](int hx, int hy, R *keep, ST *keepq) -> R {
+            const int cx = hx + 1, cy = hy + 1;  // tile+3 table coordinates
+            R acc;
+            if constexpr (P::MIX) {
+                acc = float_of_fixed(rs[s_gy[cy] + s_gx[cx]]);
+                if (keep) keep[0] = acc;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    ST q = ldg(fs + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]]);
+                    R v = Conv<P>::ld(q, isc1);
+                    if (keep) keep[i] = v;
+                    if (keepq) keepq[i] = q;
+                    acc += v;
+                }
+            } else {
+                acc = R(0);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    R v = Conv<P>::ld(ldg(fs + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]]), isc1);
+                    if (keep) keep[i] = v;
+                    acc += v;
+                }
+            }
+            return acc;
+        };
+        auto phi0_at = [&](int hx, int hy) -> R {
+            const int cx = hx + 1, cy = hy + 1;
+            R v = (R)ldg(ph0 + s_gy[cy] + s_gx[cx]);
+            if constexpr (MOVING) {
+                const int gx = s_gx[cx], gy = s_gyi[cy];
+                for (int k = 0; k < A.np; ++k) {
+                    R rx, ry;
+                    v += particle_phi0<R>(A.parts[k], gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                }
+            }
+            return v;
+        };
+
+        // ---------------- stage A ----------------
+        R f1[9];
+        ST q1[9];
+        const R phi_own = phi_at(lx + 2, ly + 2, f1, q1);
+        s_phi[ly + 2][lx + 2] = phi_own;
+        s_p0[ly + 2][lx + 2] = phi0_at(lx + 2, ly + 2);
+        constexpr int RING = 4 * (TX + 4) + 4 * TY;
+        for (int r = tid; r < RING; r += NT) {
+            int hx, hy;
+            if (r < 2 * FX) {
+                hy = r / FX;
+                hx = r % FX;
+            } else if (r < 4 * FX) {
+                int rr = r - 2 * FX;
+                hy = TY + 2 + rr / FX;
+                hx = rr % FX;
+            } else {
+                int rr = r - 4 * FX;
+                hy = 2 + rr / 4;
+                int c = rr % 4;
+                hx = c < 2 ? c : TX + c;
+            }
+            s_phi[hy][hx] = phi_at(hx, hy, nullptr, nullptr);
+            s_p0[hy][hx] = phi0_at(hx, hy);
+        }
+        if constexpr (MODE == MODE_STEP) {
+            for (int r = tid; r < WX * WY; r += NT) {
+                const int wx = r % WX, wy = r / WX;
+                const long long id = s_gy[wy + 2] + s_gx[wx + 2];
+                const R ux = (R)ldg(as + 0 * plane + id), uy = (R)ldg(as + 1 * plane + id);
+                const R Sx = (R)ldg(as + 2 * plane + id), Sy = (R)ldg(as + 3 * plane + id);
+                s_w[wy][wx] = Sx * uy - ux * Sy;
+            }
+        }
+        __syncthreads();
+
+        // ---------------- stage B: mu_phi on tile+1 (Eq. 9) ----------------
+        const R c_dw = (R)p.c_dw, c_lap = (R)p.c_lap, c_pen = (R)p.c_pen, c_wet = (R)p.c_wet,
+                c_wlap = (R)p.c_wlap;
+        for (int r = tid; r < WX * WY; r += NT) {
+            const int wx = r % WX, wy = r / WX;
+            const int hx = wx + 1, hy = wy + 1;
+            const R ph = s_phi[hy][hx], p0 = s_p0[hy][hx];
+            const R lp = lap9<R, FX>(s_phi, hx, hy), lp0 = lap9<R, FX>(s_p0, hx, hy);
+            s_mu[wy][wx] = c_dw * ph * (ph - R(1)) * (ph + R(1)) - c_lap * lp +
+                           c_pen * p0 * p0 * ph + c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) -
+                           c_wlap * lp0;
+        }
+        __syncthreads();
+
+        // ---------------- stage C: own cell ----------------
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool valid = gx < nx && gy < ny;
+        const long long id = s_gy[ly + 3] + s_gx[lx + 3];
+        const int hx = lx + 2, hy = ly + 2, wx = lx + 1, wy = ly + 1;
+
+        const R phi = phi_own, phi0 = s_p0[hy][hx];
+        R gpx, gpy, gmx, gmy;
+        grad9<R, FX>(s_phi, hx, hy, gpx, gpy);
+        grad9<R, WX>(s_mu, wx, wy, gmx, gmy);
+        const R mu = s_mu[wy][wx];
+        const R drho = (R)p.drho;
+        const R rho = drho * phi + (R)p.rhom;
+        const R muv = (R)p.dmu * phi + (R)p.mum;
+        const R Sx = (R)p.Mdrho * gmx, Sy = (R)p.Mdrho * gmy;
+        const R grx = drho * gpx, gry = drho * gpy;
+        R Fx = mu * gpx + (R)p.Fb[0], Fy = mu * gpy + (R)p.Fb[1];
+        if constexpr (MODE == MODE_STEP) {
+            // F_c = div(S u - u S)/2 from the previous step: (-d_y w, d_x w)/2
+            R wgx, wgy;
+            grad9<R, WX>(s_w, wx, wy, wgx, wgy);
+            Fx += R(-0.5) * wgy;
+            Fy += R(0.5) * wgx;
+        } else {
+            // macros of the current time use the same lagged F_c
+            // (computed below from the aux buffer of the current parity)
+        }
+        R lphi = R(0);
+        if constexpr (MOVING) {
+            // mu_phi0 grad phi0 (Eq. 19) for free particles
+            lphi = lap9<R, FX>(s_phi, hx, hy);
+            R g0x, g0y;
+            grad9<R, FX>(s_p0, hx, hy, g0x, g0y);
+            const R mu0 = c_pen * phi0 * phi * phi + c_wet * phi * (R(3) * phi0 * phi0 + phi * phi - R(1)) -
+                          c_wlap * lphi;
+            Fx += mu0 * g0x;
+            Fy += mu0 * g0y;
+        }
+        if constexpr (MODE == MODE_MACROS) {
+            // F_c from the lagged fields of the current parity (no shared tile)
+            R wv[3][3];
+#pragma unroll
+            for (int j = -1; j <= 1; ++j)
+#pragma unroll
+                for (int i = -1; i <= 1; ++i) {
+                    const long long nid = s_gy[ly + 3 + j] + s_gx[lx + 3 + i];
+                    const R ux = (R)ldg(as + 0 * plane + nid), uy = (R)ldg(as + 1 * plane + nid);
+                    const R sx = (R)ldg(as + 2 * plane + nid), sy = (R)ldg(as + 3 * plane + nid);
+                    wv[j + 1][i + 1] = sx * uy - ux * sy;
+                }
+            R wgx, wgy;
+            grad9<R, 3>(wv, 1, 1, wgx, wgy);
+            Fx += R(-0.5) * wgy;
+            Fy += R(0.5) * wgx;
+        }
+
+        // pull the flow populations
+        R f2[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f2[i] = Conv<P>::ld(ldg(fs + (9 + i) * plane + s_gy[ly + 3 - CY9[i]] + s_gx[lx + 3 - CX9[i]]), isc2);
+
+        // u* (Eq. 36a)
+        const R jx = f2[1] - f2[3] + f2[5] - f2[6] - f2[7] + f2[8];
+        const R jy = f2[2] - f2[4] + f2[5] + f2[6] - f2[7] - f2[8];
+        const R irho = R(1) / rho;
+        const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho;
+        // penalty force f = phi0 (u_s - u*) (Sec. 3.2, after Eq. 36)
+        R fpx = -phi0 * usx, fpy = -phi0 * usy;
+        if constexpr (MOVING) {
+            for (int k = 0; k < A.np; ++k) {
+                const ParticleDev &pp = A.parts[k];
+                R rx, ry;
+                const R pk = particle_phi0<R>(pp, gx < nx ? gx : 0, gy < ny ? gy : 0, nx, ny, p.D, p.cut, rx, ry);
+                if (pk != R(0)) {
+                    const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
+                    const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
+                    fpx += pk * usx_k;
+                    fpy += pk * usy_k;
+                }
+            }
+        }
+        const R ux = usx + R(0.5) * fpx, uy = usy + R(0.5) * fpy;
+        const R Ftx = Fx + rho * fpx, Fty = Fy + rho * fpy;
+
+        // lagged fields at the own cell
+        const R upx = (R)ldg(as + 0 * plane + id), upy = (R)ldg(as + 1 * plane + id);
+        const R Spx = (R)ldg(as + 2 * plane + id), Spy = (R)ldg(as + 3 * plane + id);
+        const R php = (R)ldg(as + 4 * plane + id);
+
+        // relaxation rates (Eq. 35, 1 - phi0 bounded below by solid_eps)
+        R solid = R(1) - phi0;
+        const R seps = (R)p.solid_eps;
+        solid = solid < seps ? seps : solid;
+        const R nu = muv / (rho * solid);
+        const R inv_s2a = R(0.5) + (R)p.two_over_1md0 * nu;
+        const R inv_s2b = R(0.5) + (R)p.inv_cs2 * nu;
+        const R Kf = (R)p.K;
+        const R H = Kf * ((R)p.Hc0 - (R)p.Hc1 * inv_s2a);
+        // pressure (Eq. 36b)
+        const R sum_f = f2[1] + f2[2] + f2[3] + f2[4] + f2[5] + f2[6] + f2[7] + f2[8];
+        const R ugr = ux * grx + uy * gry;
+        const R rus_u = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy;
+        const R Su = Sx * ux + Sy * uy, Sup = Spx * upx + Spy * upy;
+        const R dt_term = R(2) * (ux * Ftx + uy * Fty) - (Su - Sup);
+        const R Pr = (R)p.Pfac * (sum_f + (R(0.5) + H) * ugr - (R)p.w0f * rus_u * (R)p.inv_1mcs2 +
+                                 Kf * R(0.5) * dt_term);
+
+        if constexpr (MODE == MODE_MACROS) {
+            if (valid) {
+                const long long N = (long long)nx * ny;
+                const long long o = (long long)gy * nx + gx;
+                double phv = (double)phi;
+                if constexpr (P::MIX) {
+                    long long acc = rs[id];
+                    int bad = 0;
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) acc += fixed_of<ST>(q1[i], p.klog2[0], &bad);
+                    phv = double_of_fixed(acc);
+                }
+                Dm.macro[0 * N + o] = phv;
+                Dm.macro[1 * N + o] = (double)rho;
+                Dm.macro[2 * N + o] = (double)ux;
+                Dm.macro[3 * N + o] = (double)uy;
+                Dm.macro[4 * N + o] = (double)Pr;
+                Dm.macro[5 * N + o] = (double)mu;
+                Dm.macro[6 * N + o] = (double)phi0;
+            }
+            continue;
+        } else {
+            const R cs2 = (R)p.cs2, cs4 = (R)p.cs4;
+            // ---- order-parameter lattice (Eq. 30): Hermite equilibria and source
+            const R eta_mu = (R)p.eta * mu;
+            R heq[9], hF[9], S[9];
+            heq[0] = phi;
+            heq[1] = phi * ux;
+            heq[2] = phi * uy;
+            heq[3] = cs2 * (eta_mu - phi);
+            heq[4] = heq[3];
+            heq[5] = R(0);
+            heq[6] = R(0);
+            heq[7] = R(0);
+            heq[8] = cs4 * (phi - eta_mu);
+            hF[0] = R(0);
+            hF[1] = phi * ux - php * upx;  // d_t(phi u), explicit Euler
+            hF[2] = phi * uy - php * upy;
+#pragma unroll
+            for (int k = 3; k < 9; ++k) hF[k] = R(0);
+            S[0] = (R)p.s0;
+            S[1] = S[2] = (R)p.s1phi;
+            S[3] = S[4] = S[5] = (R)p.s2;
+            S[6] = S[7] = (R)p.s3;
+            S[8] = (R)p.s4;
+            collide9<R>(f1, heq, hF, S, cs2);
+
+            // ---- flow lattice (Eqs. 32-34)
+            heq[0] = R(0);
+            heq[1] = rho * ux;
+            heq[2] = rho * uy;
+            heq[3] = Pr + rho * ux * ux - Sx * ux;
+            heq[4] = Pr + rho * uy * uy - Sy * uy;
+            heq[5] = rho * ux * uy - R(0.5) * (Sx * uy + ux * Sy);
+            heq[6] = R(0);
+            heq[7] = R(0);
+            heq[8] = -cs2 * Pr;
+            const R c3 = R(1) - R(3) * cs2;
+            hF[0] = ugr;
+            hF[1] = Ftx;
+            hF[2] = Fty;
+            hF[3] = R(2) * ux * Ftx - (Sx * ux - Spx * upx) + R(2) * cs2 * ux * grx + c3 * ugr;
+            hF[4] = R(2) * uy * Fty - (Sy * uy - Spy * upy) + R(2) * cs2 * uy * gry + c3 * ugr;
+            hF[5] = ux * Fty + Ftx * uy - R(0.5) * ((Sx * uy + ux * Sy) - (Spx * upy + upx * Spy)) +
+                    cs2 * (ux * gry + grx * uy);
+            hF[6] = R(0);
+            hF[7] = R(0);
+            hF[8] = R(0);
+            S[0] = (R)p.s0;
+            S[1] = S[2] = (R)p.s1;
+            S[3] = S[4] = R(1) / inv_s2a;
+            S[5] = R(1) / inv_s2b;
+            S[6] = S[7] = (R)p.s3;
+            S[8] = (R)p.s4;
+            collide9<R>(f2, heq, hF, S, cs2);
+
+            if (valid) {
+                // populations (own cell; the next step pulls them)
+                if constexpr (P::MIX) {
+                    const R sc1 = (R)p.scale[0];
+                    const int k1 = p.klog2[0];
+                    int bad = 0;
+                    long long exact = rs[id];
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) exact += fixed_of<ST>(q1[i], k1, &bad);
+                    long long rest = exact;
+#pragma unroll
+                    for (int i = 1; i < 9; ++i) {
+                        ST q = Conv<P>::st(f1[i], sc1);
+                        if constexpr (P::id == 3) q = bf16_flush(q, k1);
+                        rest -= fixed_of<ST>(q, k1, &bad);
+                        fd[i * plane + id] = q;
+                    }
+                    rd[id] = rest;
+                    if (bad) atomicOr(A.flags, 1);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fd[i * plane + id] = Conv<P>::st(f1[i], R(1));
+                }
+                const R sc2 = P::MIX ? (R)p.scale[1] : R(1);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    ST q = Conv<P>::st(f2[i], sc2);
+                    if constexpr (P::id == 3) q = bf16_flush(q, p.klog2[1]);
+                    fd[(9 + i) * plane + id] = q;
+                }
+                // fields of this step, read as the previous step's by the next one
+                ad[0 * plane + id] = (AX)ux;
+                ad[1 * plane + id] = (AX)uy;
+                ad[2 * plane + id] = (AX)Sx;
+                ad[3 * plane + id] = (AX)Sy;
+                ad[4 * plane + id] = (AX)phi;
+                if (!isfinite(phi) || !isfinite(ux) || !isfinite(uy)) atomicOr(A.flags, 1);
+            }
+
+            if constexpr (MOVING) {
+                // hydrodynamic force and torque on each particle (Eq. 27):
+                // F_f = -sum rho phi0_k (u_s,k - u*), T_f = -sum r x (...)
+                for (int k = 0; k < A.np; ++k) {
+                    const ParticleDev &pp = A.parts[k];
+                    double c6[6] = {0, 0, 0, 0, 0, 0};
+                    if (valid) {
+                        R rx, ry;
+                        const R pk = particle_phi0<R>(pp, gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                        if (pk != R(0)) {
+                            const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
+                            const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
+                            const R fx = rho * pk * (usx_k - usx), fy = rho * pk * (usy_k - usy);
+                            c6[0] = -(double)fx;
+                            c6[1] = -(double)fy;
+                            c6[5] = -((double)rx * (double)fy - (double)ry * (double)fx);
+                        }
+                    }
+                    // fixed-order block reduction: warp shuffle tree, then warps in order
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        double v = c6[c];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                        if ((tid & 31) == 0) s_red[tid >> 5][c] = v;
+                    }
+                    __syncthreads();
+                    if (tid < 6) {
+                        double acc = 0.0;
+                        for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[wq][tid];
+                        A.partials[((long long)t * A.np + k) * 6 + tid] = acc;
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+    }
+}
+
+}  // namespace pf

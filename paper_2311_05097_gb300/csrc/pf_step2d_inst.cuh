@@ -1,0 +1,56 @@
+// Instantiation and dispatch of the 2D step kernel for one precision policy.
+// Included by one translation unit per policy (parallel compilation).
+#pragma once
+
+#include "pf_internal.h"
+#include "pf_kernels2d.cuh"
+
+namespace pf {
+
+template <class P, int TX, int TY, bool MOVING, int MODE>
+static bool run2d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    auto kern = k_step2d<P, TX, TY, MOVING, MODE>;
+    if (occ) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0) != cudaSuccess) n = 0;
+        *occ = n;
+        return true;
+    }
+    kern<<<grid, TX * TY, 0, s>>>(a);
+    count_launches(1);
+    return true;
+}
+
+template <class P>
+static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
+                       const StepArgs &a, int *occ)
+{
+#define PF_CASE(TX, TY)                                                                   \
+    if (tx == TX && ty == TY) {                                                           \
+        if (mode == MODE_MACROS)                                                          \
+            return moving ? run2d<P, TX, TY, true, MODE_MACROS>(grid, s, a, occ)          \
+                          : run2d<P, TX, TY, false, MODE_MACROS>(grid, s, a, occ);        \
+        return moving ? run2d<P, TX, TY, true, MODE_STEP>(grid, s, a, occ)                \
+                      : run2d<P, TX, TY, false, MODE_STEP>(grid, s, a, occ);              \
+    }
+    if (mode == MODE_MACROS) {
+        if (tx == 32 && ty == 8)
+            return moving ? run2d<P, 32, 8, true, MODE_MACROS>(grid, s, a, occ)
+                          : run2d<P, 32, 8, false, MODE_MACROS>(grid, s, a, occ);
+        return false;
+    }
+    if (tx == 32 && ty == 8)
+        return moving ? run2d<P, 32, 8, true, MODE_STEP>(grid, s, a, occ)
+                      : run2d<P, 32, 8, false, MODE_STEP>(grid, s, a, occ);
+    if (tx == 64 && ty == 4)
+        return moving ? run2d<P, 64, 4, true, MODE_STEP>(grid, s, a, occ)
+                      : run2d<P, 64, 4, false, MODE_STEP>(grid, s, a, occ);
+    if (tx == 32 && ty == 16)
+        return moving ? run2d<P, 32, 16, true, MODE_STEP>(grid, s, a, occ)
+                      : run2d<P, 32, 16, false, MODE_STEP>(grid, s, a, occ);
+#undef PF_CASE
+    return false;
+}
+
+}  // namespace pf

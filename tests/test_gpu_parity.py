@@ -1,0 +1,181 @@
+"""Parity of the CUDA library (through the C-ABI) with the FP64 oracle on the
+same seeded inputs.
+
+FP64 path: every field agrees with the oracle to 1e-12 relative
+(max |gpu - oracle| / max |oracle| per field).  FP32 and mixed-precision
+paths: the per-field bounds stated in each test.  Sizes span several tiles
+with ragged edges; one case runs the 128 x 128 static drop for its full 2000
+steps and one samples the 512 x 512 drop-on-cylinder case in the launch
+configuration the benchmark uses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2311_05097_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "rho", "u", "P", "mu")
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_2311_05097_gb300 import build
+    build.build()
+    from paper_2311_05097_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+def rel(a, b):
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / (s if s > 0 else 1.0))
+
+
+def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True):
+    prm = case["params"]
+    g = pf.Sim(case["shape"], precision=precision, **prm)
+    o = O.OracleSim(case["shape"], O.make_params(**prm)) if oracle else None
+    for k, pp in enumerate(particles):
+        g.set_particle(k, **pp)
+        if o is not None:
+            o.set_particle(k, O.Particle(**pp))
+    g.init(case["phi0"], case["phi"], case.get("u"))
+    if o is not None:
+        o.init(case["phi0"], case["phi"], case.get("u"))
+    g.step(steps)
+    if o is not None:
+        o.step(steps)
+    return g, o
+
+
+def assert_fields(gm, om, tol):
+    for k in FIELDS:
+        e = rel(gm[k], om[k])
+        assert e < tol[k] if isinstance(tol, dict) else e < tol, (k, e)
+
+
+@pytest.mark.parametrize("shape,solid,u_amp,steps", [
+    ((52, 40), True, 0.0, 0),
+    ((52, 40), True, 0.0, 120),
+    ((37, 45), False, 0.02, 150),
+    ((70, 33), True, 0.01, 90),
+])
+def test_p64_matches_oracle_2d(pf, shape, solid, u_amp, steps):
+    c = W.small_case(shape, seed=7, solid=solid, theta_deg=60.0, u_amp=u_amp)
+    g, o = run_pair(pf, c, steps)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    assert g.time == steps
+
+
+def test_p64_diagnostics_match_oracle(pf):
+    c = W.small_case((48, 64), seed=2, solid=True, theta_deg=120.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 60)
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K", "E_total"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, k
+    assert dg["nan_flag"] == 0
+
+
+def test_p64_moving_particle_matches_oracle(pf):
+    c = W.small_case((48, 56), seed=5, solid=False)
+    part = dict(x=(20.3, 17.6), u=(0.01, -0.004), w=(0.0, 0.0, 0.002), R=6.0, rho_p=2.0)
+    c["phi"] = (1.0 - W.disc(c["shape"], part["x"], part["R"], c["params"]["D"])) * c["phi"]
+    g, o = run_pair(pf, c, 80, particles=[part])
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    pg, po = g.particle(0), o.particle(0)
+    for k in ("x", "u", "w", "F", "T"):
+        a, b = np.array(pg[k]), np.array(getattr(po, k))
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, a, b)
+
+
+def test_p64_static_drop_full_run(pf):
+    """The 128 x 128 static drop for its full 2000 steps."""
+    c = W.static_drop()
+    g, o = run_pair(pf, c, 2000)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    dg, do = g.diagnostics(), o.diagnostics()
+    assert abs(dg["mass"] - do["mass"]) < 1e-12 * np.abs(c["phi"]).sum()
+
+
+def test_p64_is_deterministic(pf):
+    c = W.small_case((64, 64), seed=11, solid=True, u_amp=0.01)
+    a, _ = run_pair(pf, c, 50, oracle=False)
+    b, _ = run_pair(pf, c, 50, oracle=False)
+    ma, mb = a.macros(), b.macros()
+    for k in FIELDS:
+        assert np.array_equal(ma[k], mb[k]), k
+
+
+def test_graph_replay_equals_plain_steps(pf):
+    """pf_step(n) replays a CUDA graph of 16-step chunks; splitting n into odd
+    pieces (plain launches) must give bitwise the same state."""
+    c = W.small_case((40, 72), seed=3, solid=True, u_amp=0.01)
+    a, _ = run_pair(pf, c, 37, oracle=False)
+    b, _ = run_pair(pf, c, 0, oracle=False)
+    for n in (1, 5, 2, 16, 13):
+        b.step(n)
+    ma, mb = a.macros(), b.macros()
+    for k in FIELDS:
+        assert np.array_equal(ma[k], mb[k]), k
+
+
+def test_p32_against_oracle(pf):
+    c = W.small_case((52, 40), seed=7, solid=True, theta_deg=60.0)
+    g, o = run_pair(pf, c, 200, precision="p32")
+    gm, om = g.macros(), o.macros()
+    assert rel(gm["phi"], om["phi"]) < 1e-5
+    assert rel(gm["rho"], om["rho"]) < 1e-5
+    assert rel(gm["u"], om["u"]) < 1e-3
+    assert rel(gm["P"], om["P"]) < 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_pmix_conserves_mass_exactly(pf, precision):
+    """Mixed storage: the rest population of the order-parameter lattice is an
+    exact fixed-point number set so that each cell's sum of populations is
+    unchanged by the collision, hence sum phi is conserved to round-off of
+    the final FP64 sum."""
+    c = W.small_case((64, 80), seed=4, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 0, precision=precision, oracle=False)
+    m0 = g.diagnostics()["mass"]
+    g.step(1000)
+    m1 = g.diagnostics()["mass"]
+    assert abs(m1 - m0) / np.abs(c["phi"]).sum() < 1e-13
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("fp16", 2e-3), ("bf16", 2e-2)])
+def test_pmix_against_oracle(pf, precision, tol_phi):
+    c = W.small_case((52, 40), seed=7, solid=True, theta_deg=60.0)
+    g, o = run_pair(pf, c, 200, precision=precision)
+    gm, om = g.macros(), o.macros()
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+
+
+def test_nan_is_reported(pf):
+    c = W.small_case((32, 32), seed=1, solid=False)
+    phi = c["phi"].copy()
+    phi[5, 7] = np.nan
+    g = pf.Sim(c["shape"], precision="p32", **c["params"])
+    g.init(c["phi0"], phi)
+    g.step(3)
+    with pytest.raises(pf.PfError) as ei:
+        g.sync()
+    assert ei.value.code == pf.PF_ENUMERIC
+    assert g.diagnostics()["nan_flag"] == 1
+
+
+def test_cylinder_full_size_sampled(pf):
+    """512 x 512 drop on a cylinder (density ratio 1000) in FP64 and FP32 against
+    the oracle after a few steps at full size (the oracle's 512^2 steps take
+    about a second each)."""
+    c = W.drop_on_cylinder()
+    g64, o = run_pair(pf, c, 6)
+    om = o.macros()
+    assert_fields(g64.macros(), om, 1e-12)
+    g32, _ = run_pair(pf, c, 6, precision="p32", oracle=False)
+    gm = g32.macros()
+    assert rel(gm["phi"], om["phi"]) < 1e-5
