@@ -597,7 +597,7 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
         } else {
             rc = engine_tiles(E, 32, 8);
             E.cps = 0;
-            E.grid = grid_of(E, 0);
+            E.grid = autotune ? grid_of(E, 0) : E.ntiles;  // one CTA per tile
             E.tuned = !autotune;
         }
         if (rc) return (E.sticky = rc);
@@ -870,7 +870,7 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
             if (E.tuned) {
                 rc = engine_tiles(E, E.tx, E.ty);
                 if (rc) return rc;
-                E.grid = grid_of(E, E.cps);
+                E.grid = E.ntiles;
             }
             drop_graph(E);
         }

@@ -52,9 +52,16 @@ def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True):
     return g, o
 
 
-def assert_fields(gm, om, tol):
+def assert_fields(gm, om, tol, mu_scale=None):
+    """Relative max error per field.  mu_phi (Eq. 9) is a small difference of
+    terms of size 3 sigma/D (it vanishes at equilibrium), so its error is
+    measured against max(|mu|, 3 sigma/D): round-off in those terms sets the
+    floor, not |mu| itself."""
     for k in FIELDS:
-        e = rel(gm[k], om[k])
+        if k == "mu" and mu_scale is not None:
+            e = float(np.abs(gm[k] - om[k]).max() / max(np.abs(om[k]).max(), mu_scale))
+        else:
+            e = rel(gm[k], om[k])
         assert e < tol[k] if isinstance(tol, dict) else e < tol, (k, e)
 
 
@@ -96,7 +103,7 @@ def test_p64_static_drop_full_run(pf):
     """The 128 x 128 static drop for its full 2000 steps."""
     c = W.static_drop()
     g, o = run_pair(pf, c, 2000)
-    assert_fields(g.macros(), o.macros(), 1e-12)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
     dg, do = g.diagnostics(), o.diagnostics()
     assert abs(dg["mass"] - do["mass"]) < 1e-12 * np.abs(c["phi"]).sum()
 
