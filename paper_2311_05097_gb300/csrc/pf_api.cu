@@ -45,6 +45,37 @@ int occupancy_step2d(int prec, int tx, int ty, bool moving, int mode)
     return ok ? occ : 0;
 }
 
+void tile_shape3d(int prec, int *tx, int *ty)
+{
+    *tx = prec == PF_P64 ? 16 : 32;
+    *ty = 8;
+}
+
+bool launch_step3d(int prec, int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
+                   const StepArgs &a)
+{
+    switch (prec) {
+    case PF_P64: return launch_step3d_p64(tx, ty, moving, mode, grid, s, a, nullptr);
+    case PF_P32: return launch_step3d_p32(tx, ty, moving, mode, grid, s, a, nullptr);
+    case PF_PMIX_FP16: return launch_step3d_mixh(tx, ty, moving, mode, grid, s, a, nullptr);
+    default: return launch_step3d_mixb(tx, ty, moving, mode, grid, s, a, nullptr);
+    }
+}
+
+int occupancy_step3d(int prec, int tx, int ty, bool moving, int mode)
+{
+    StepArgs a{};
+    int occ = 0;
+    bool ok;
+    switch (prec) {
+    case PF_P64: ok = launch_step3d_p64(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    case PF_P32: ok = launch_step3d_p32(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    case PF_PMIX_FP16: ok = launch_step3d_mixh(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    default: ok = launch_step3d_mixb(tx, ty, moving, mode, 0, 0, a, &occ); break;
+    }
+    return ok ? occ : 0;
+}
+
 }  // namespace pf
 
 using namespace pf;
@@ -111,7 +142,6 @@ static int validate(const pf_grid *g, const pf_params *p)
 {
     if (!g || !p) return fail(PF_EINVAL, "grid or params is NULL");
     if (g->dim != 2 && g->dim != 3) return fail(PF_EINVAL, "dim must be 2 or 3 (got %d)", g->dim);
-    if (g->dim == 3) return fail(PF_EINVAL, "3D domains are not built into this library yet");
     const int nz = g->dim == 2 ? 1 : g->nz;
     if (g->nx < 4 || g->ny < 4 || (g->dim == 3 && nz < 4))
         return fail(PF_EINVAL, "grid sizes must be >= 4 (got %d x %d x %d)", g->nx, g->ny, nz);
@@ -249,6 +279,8 @@ static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams
     d.pitch = (int)round_up(d.nx, 32);
     d.plane = round_up((long long)d.pitch * d.ny * d.nz, 64);
     d.p = dp;
+    d.kf = make_kparams<float>(dp);
+    d.kd = make_kparams<double>(dp);
     const int Q = dim == 2 ? 18 : 26;
     const int naux = 2 * dim + 1;
     const size_t fb = (size_t)Q * d.plane * store_bytes(prec);
@@ -335,13 +367,15 @@ static void build_tiles(const std::vector<DomainMem *> &doms, int tx, int ty, st
         DomainDev &d = doms[k]->d;
         d.tiles_x = (d.nx + tx - 1) / tx;
         d.tiles_y = (d.ny + ty - 1) / ty;
-        d.tiles_z = 1;
+        d.tiles_z = d.p.dim == 3 ? (d.nz + ZCHUNK3D - 1) / ZCHUNK3D : 1;
         d.tile_base = (int)tdom.size();
-        for (int j = 0; j < d.tiles_y; ++j)
-            for (int i = 0; i < d.tiles_x; ++i) {
-                tdom.push_back((int)k);
-                txy.push_back(make_int2(i, j));
-            }
+        // 3D tiles encode (y tile, z chunk) as y + tiles_y * z
+        for (int kz = 0; kz < d.tiles_z; ++kz)
+            for (int j = 0; j < d.tiles_y; ++j)
+                for (int i = 0; i < d.tiles_x; ++i) {
+                    tdom.push_back((int)k);
+                    txy.push_back(make_int2(i, j + d.tiles_y * kz));
+                }
     }
 }
 
@@ -460,6 +494,18 @@ static int engine_tiles(Engine &E, int tx, int ty)
     return PF_OK;
 }
 
+static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
+{
+    if (E.dim == 3) return launch_step3d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
+    return launch_step2d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
+}
+
+static int occupancy_any(const Engine &E, int tx, int ty, int mode)
+{
+    if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode);
+    return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode);
+}
+
 static StepArgs step_args(const Engine &E, int par)
 {
     StepArgs a{};
@@ -479,7 +525,7 @@ static StepArgs step_args(const Engine &E, int par)
 static int issue_step(Engine &E, int par)
 {
     const StepArgs a = step_args(E, par);
-    if (!launch_step2d(E.prec, E.tx, E.ty, E.np > 0, MODE_STEP, E.grid, E.stream, a))
+    if (!launch_any(E, E.tx, E.ty, MODE_STEP, E.grid, a))
         return fail(PF_EINVAL, "tile shape %dx%d not built", E.tx, E.ty);
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.stream);
@@ -489,7 +535,7 @@ static int issue_step(Engine &E, int par)
 
 static int grid_of(Engine &E, int cps)
 {
-    int occ = occupancy_step2d(E.prec, E.tx, E.ty, E.np > 0, MODE_STEP);
+    int occ = occupancy_any(E, E.tx, E.ty, MODE_STEP);
     if (occ < 1) occ = 1;
     int c = cps > 0 ? std::min(cps, occ) : occ;
     long long g = (long long)c * E.nsm;
@@ -524,17 +570,23 @@ static int engine_configure(Engine &E)
             return PF_OK;
         }
     }
-    const int shapes[][2] = {{32, 8}, {64, 4}, {32, 16}};
+    int shapes[3][2] = {{32, 8}, {64, 4}, {32, 16}};
+    int nshapes = 3;
+    if (E.dim == 3) {
+        tile_shape3d(E.prec, &shapes[0][0], &shapes[0][1]);
+        nshapes = 1;
+    }
     float best = 1e30f;
     int bx = 32, by = 8, bc = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int reps = cells > (1 << 22) ? 2 : 4;
-    for (auto &sh : shapes) {
+    for (int si = 0; si < nshapes; ++si) {
+        const int *sh = shapes[si];
         int rc = engine_tiles(E, sh[0], sh[1]);
         if (rc) return rc;
-        const int occ = std::max(1, occupancy_step2d(E.prec, sh[0], sh[1], E.np > 0, MODE_STEP));
+        const int occ = std::max(1, occupancy_any(E, sh[0], sh[1], MODE_STEP));
         for (int cps = 1; cps <= occ; cps = cps < occ ? std::min(cps * 2, occ) : occ + 1) {
             E.cps = cps;
             E.grid = grid_of(E, cps);
@@ -595,7 +647,9 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
             rc = engine_configure(E);
             left -= E.t - t0;
         } else {
-            rc = engine_tiles(E, 32, 8);
+            int tx = 32, ty = 8;
+            if (E.dim == 3) tile_shape3d(E.prec, &tx, &ty);
+            rc = engine_tiles(E, tx, ty);
             E.cps = 0;
             E.grid = autotune ? grid_of(E, 0) : E.ntiles;  // one CTA per tile
             E.tuned = !autotune;
@@ -664,7 +718,9 @@ static int engine_macros(Engine &E, int i)
     std::vector<int> tdom;
     std::vector<int2> txy;
     DomainDev saved = E.mem[i].d;
-    build_tiles(ds, 32, 8, tdom, txy);
+    int mtx = 32, mty = 8;
+    if (E.dim == 3) tile_shape3d(E.prec, &mtx, &mty);
+    build_tiles(ds, mtx, mty, tdom, txy);
     DomainDev dd = E.mem[i].d;
     E.mem[i].d = saved;
     E.mem[i].d.macro = E.mem[i].macro;
@@ -689,7 +745,7 @@ static int engine_macros(Engine &E, int i)
     a.partials = nullptr;
     a.flags = E.d_flags;
     const int grid = std::min<int>((int)tdom.size(), E.nsm * 4);
-    if (!launch_step2d(E.prec, 32, 8, E.np > 0, MODE_MACROS, grid, E.stream, a))
+    if (!launch_any(E, mtx, mty, MODE_MACROS, grid, a))
         return fail(PF_EINVAL, "macro kernel not built");
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(E.stream));

@@ -85,6 +85,58 @@ struct ParticleDev {
     double F[3], T[3];
 };
 
+// The constants the step kernels read, in the kernel's arithmetic type (so a
+// float kernel never converts from double inside the cell loop).
+template <class R>
+struct KParams {
+    R cs2, cs4, inv_cs2, w0f, drho, rhom, dmu, mum;
+    R c_dw, c_lap, c_pen, c_wet, c_wlap, Mdrho;
+    R K, Hc0, Hc1, Pfac, inv_1mcs2, two_over_1md0;
+    R eta, s0, s1, s2, s3, s4, s1phi, solid_eps;
+    R Fb[3];
+    R scale[2], inv_scale[2];
+};
+
+template <class R>
+inline KParams<R> make_kparams(const DevParams &d)
+{
+    KParams<R> k;
+    k.cs2 = (R)d.cs2;
+    k.cs4 = (R)d.cs4;
+    k.inv_cs2 = (R)d.inv_cs2;
+    k.w0f = (R)d.w0f;
+    k.drho = (R)d.drho;
+    k.rhom = (R)d.rhom;
+    k.dmu = (R)d.dmu;
+    k.mum = (R)d.mum;
+    k.c_dw = (R)d.c_dw;
+    k.c_lap = (R)d.c_lap;
+    k.c_pen = (R)d.c_pen;
+    k.c_wet = (R)d.c_wet;
+    k.c_wlap = (R)d.c_wlap;
+    k.Mdrho = (R)d.Mdrho;
+    k.K = (R)d.K;
+    k.Hc0 = (R)d.Hc0;
+    k.Hc1 = (R)d.Hc1;
+    k.Pfac = (R)d.Pfac;
+    k.inv_1mcs2 = (R)d.inv_1mcs2;
+    k.two_over_1md0 = (R)d.two_over_1md0;
+    k.eta = (R)d.eta;
+    k.s0 = (R)d.s0;
+    k.s1 = (R)d.s1;
+    k.s2 = (R)d.s2;
+    k.s3 = (R)d.s3;
+    k.s4 = (R)d.s4;
+    k.s1phi = (R)d.s1phi;
+    k.solid_eps = (R)d.solid_eps;
+    for (int a = 0; a < 3; ++a) k.Fb[a] = (R)d.Fb[a];
+    for (int a = 0; a < 2; ++a) {
+        k.scale[a] = (R)d.scale[a];
+        k.inv_scale[a] = (R)d.inv_scale[a];
+    }
+    return k;
+}
+
 // One domain of a (possibly batched) launch.
 struct DomainDev {
     int nx, ny, nz, pitch;
@@ -97,7 +149,16 @@ struct DomainDev {
     int tile_base;   // index of this domain's first tile in the partial-sum table
     int tiles_x, tiles_y, tiles_z;
     DevParams p;
+    KParams<float> kf;
+    KParams<double> kd;
 };
+
+template <class R>
+__device__ __forceinline__ const KParams<R> &kparams(const DomainDev &d);
+template <>
+__device__ __forceinline__ const KParams<float> &kparams<float>(const DomainDev &d) { return d.kf; }
+template <>
+__device__ __forceinline__ const KParams<double> &kparams<double>(const DomainDev &d) { return d.kd; }
 
 // Arguments of the step / macro kernels (2D and 3D).
 struct StepArgs {

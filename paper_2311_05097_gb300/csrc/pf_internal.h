@@ -26,6 +26,17 @@ bool launch_step2d_p32(int tx, int ty, bool moving, int mode, int grid, cudaStre
 bool launch_step2d_mixh(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
 bool launch_step2d_mixb(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
 
+// 3D: one CTA marches through ZCHUNK3D planes in z
+constexpr int ZCHUNK3D = 32;
+bool launch_step3d(int prec, int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
+                   const StepArgs &a);
+int occupancy_step3d(int prec, int tx, int ty, bool moving, int mode);
+void tile_shape3d(int prec, int *tx, int *ty);
+bool launch_step3d_p64(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
+bool launch_step3d_p32(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
+bool launch_step3d_mixh(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
+bool launch_step3d_mixb(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
+
 void launch_init(int prec, const DomainDev &Dm, const double *phi0, const double *phi, const double *u,
                  const double *Pin, double *tmp, const ParticleDev *parts, int np, cudaStream_t s);
 int diag_blocks();

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
     __shared__ long long s_gy[TY + 6];
     __shared__ int s_gyi[TY + 6];
     __shared__ double s_red[NT / 32][6];
+    __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -145,15 +146,35 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         const long long plane = Dm.plane;
         const int x0 = txy.x * TX, y0 = txy.y * TY;
         const DevParams &p = Dm.p;
+        const KParams<R> &kp = kparams<R>(Dm);
 
         __syncthreads();  // previous tile's shared-memory readers are done
+        if constexpr (MOVING) {
+            if (tid == 0) s_near = 0ull;
+        }
         for (int k = tid; k < TX + 6; k += NT) s_gx[k] = wrap_idx(x0 - 3 + k, nx);
         for (int k = tid; k < TY + 6; k += NT) {
             const int yy = wrap_idx(y0 - 3 + k, ny);
             s_gyi[k] = yy;
             s_gy[k] = (long long)yy * Dm.pitch;
         }
+        if constexpr (MOVING) {
+            // conservative test of the tile + 2 frame against each particle's
+            // reach R + cut (minimum image), one thread per particle
+            __syncthreads();
+            for (int k = tid; k < A.np; k += NT) {
+                const ParticleDev &pp = A.parts[k];
+                double dx = (x0 + 0.5 * (TX - 1)) - pp.x[0], dy = (y0 + 0.5 * (TY - 1)) - pp.x[1];
+                dx -= nx * rint(dx / nx);
+                dy -= ny * rint(dy / ny);
+                const double ex = fmax(fabs(dx) - (0.5 * TX + 2.0), 0.0);
+                const double ey = fmax(fabs(dy) - (0.5 * TY + 2.0), 0.0);
+                const double lim = pp.R + p.cut + 1.0;
+                if (ex * ex + ey * ey < lim * lim) atomicOr(&s_near, 1ull << k);
+            }
+        }
         __syncthreads();
+        [[maybe_unused]] const unsigned long long near = MOVING ? s_near : 0ull;
 
         const ST *fs = reinterpret_cast<const ST *>(Dm.f[A.par]);
         ST *fd = reinterpret_cast<ST *>(Dm.f[A.par ^ 1]);
@@ -162,7 +183,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         const AX *ph0 = reinterpret_cast<const AX *>(Dm.phi0);
         const long long *rs = reinterpret_cast<const long long *>(Dm.rest[A.par]);
         long long *rd = reinterpret_cast<long long *>(Dm.rest[A.par ^ 1]);
-        const R isc1 = (R)p.inv_scale[0], isc2 = (R)p.inv_scale[1];
+        const R isc1 = kp.inv_scale[0], isc2 = kp.inv_scale[1];
 
         // phi at frame cell (hx, hy) of the tile+2 frame: pull and sum (Eq. 31)
         auto phi_at = [&](int hx, int hy, R *keep, ST *keepq) -> R {
@@ -196,6 +217,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
             if constexpr (MOVING) {
                 const int gx = s_gx[cx], gy = s_gyi[cy];
                 for (int k = 0; k < A.np; ++k) {
+                    if (!((near >> k) & 1ull)) continue;
                     R rx, ry;
                     v += particle_phi0<R>(A.parts[k], gx, gy, nx, ny, p.D, p.cut, rx, ry);
                 }
@@ -240,8 +262,8 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         __syncthreads();
 
         // ---------------- stage B: mu_phi on tile+1 (Eq. 9) ----------------
-        const R c_dw = (R)p.c_dw, c_lap = (R)p.c_lap, c_pen = (R)p.c_pen, c_wet = (R)p.c_wet,
-                c_wlap = (R)p.c_wlap;
+        const R c_dw = kp.c_dw, c_lap = kp.c_lap, c_pen = kp.c_pen, c_wet = kp.c_wet,
+                c_wlap = kp.c_wlap;
         for (int r = tid; r < WX * WY; r += NT) {
             const int wx = r % WX, wy = r / WX;
             const int hx = wx + 1, hy = wy + 1;
@@ -264,12 +286,12 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         grad9<R, FX>(s_phi, hx, hy, gpx, gpy);
         grad9<R, WX>(s_mu, wx, wy, gmx, gmy);
         const R mu = s_mu[wy][wx];
-        const R drho = (R)p.drho;
-        const R rho = drho * phi + (R)p.rhom;
-        const R muv = (R)p.dmu * phi + (R)p.mum;
-        const R Sx = (R)p.Mdrho * gmx, Sy = (R)p.Mdrho * gmy;
+        const R drho = kp.drho;
+        const R rho = drho * phi + kp.rhom;
+        const R muv = kp.dmu * phi + kp.mum;
+        const R Sx = kp.Mdrho * gmx, Sy = kp.Mdrho * gmy;
         const R grx = drho * gpx, gry = drho * gpy;
-        R Fx = mu * gpx + (R)p.Fb[0], Fy = mu * gpy + (R)p.Fb[1];
+        R Fx = mu * gpx + kp.Fb[0], Fy = mu * gpy + kp.Fb[1];
         if constexpr (MODE == MODE_STEP) {
             // F_c = div(S u - u S)/2 from the previous step: (-d_y w, d_x w)/2
             R wgx, wgy;
@@ -324,9 +346,10 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         R fpx = -phi0 * usx, fpy = -phi0 * usy;
         if constexpr (MOVING) {
             for (int k = 0; k < A.np; ++k) {
+                if (!((near >> k) & 1ull)) continue;
                 const ParticleDev &pp = A.parts[k];
                 R rx, ry;
-                const R pk = particle_phi0<R>(pp, gx < nx ? gx : 0, gy < ny ? gy : 0, nx, ny, p.D, p.cut, rx, ry);
+                const R pk = particle_phi0<R>(pp, gx, gy, nx, ny, p.D, p.cut, rx, ry);
                 if (pk != R(0)) {
                     const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                     const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
@@ -345,20 +368,20 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
 
         // relaxation rates (Eq. 35, 1 - phi0 bounded below by solid_eps)
         R solid = R(1) - phi0;
-        const R seps = (R)p.solid_eps;
+        const R seps = kp.solid_eps;
         solid = solid < seps ? seps : solid;
         const R nu = muv / (rho * solid);
-        const R inv_s2a = R(0.5) + (R)p.two_over_1md0 * nu;
-        const R inv_s2b = R(0.5) + (R)p.inv_cs2 * nu;
-        const R Kf = (R)p.K;
-        const R H = Kf * ((R)p.Hc0 - (R)p.Hc1 * inv_s2a);
+        const R inv_s2a = R(0.5) + kp.two_over_1md0 * nu;
+        const R inv_s2b = R(0.5) + kp.inv_cs2 * nu;
+        const R Kf = kp.K;
+        const R H = Kf * (kp.Hc0 - kp.Hc1 * inv_s2a);
         // pressure (Eq. 36b)
         const R sum_f = f2[1] + f2[2] + f2[3] + f2[4] + f2[5] + f2[6] + f2[7] + f2[8];
         const R ugr = ux * grx + uy * gry;
         const R rus_u = (rho * ux - Sx) * ux + (rho * uy - Sy) * uy;
         const R Su = Sx * ux + Sy * uy, Sup = Spx * upx + Spy * upy;
         const R dt_term = R(2) * (ux * Ftx + uy * Fty) - (Su - Sup);
-        const R Pr = (R)p.Pfac * (sum_f + (R(0.5) + H) * ugr - (R)p.w0f * rus_u * (R)p.inv_1mcs2 +
+        const R Pr = kp.Pfac * (sum_f + (R(0.5) + H) * ugr - kp.w0f * rus_u * kp.inv_1mcs2 +
                                  Kf * R(0.5) * dt_term);
 
         if constexpr (MODE == MODE_MACROS) {
@@ -383,9 +406,9 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
             }
             continue;
         } else {
-            const R cs2 = (R)p.cs2, cs4 = (R)p.cs4;
+            const R cs2 = kp.cs2, cs4 = kp.cs4;
             // ---- order-parameter lattice (Eq. 30): Hermite equilibria and source
-            const R eta_mu = (R)p.eta * mu;
+            const R eta_mu = kp.eta * mu;
             R heq[9], hF[9], S[9];
             heq[0] = phi;
             heq[1] = phi * ux;
@@ -401,11 +424,11 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
             hF[2] = phi * uy - php * upy;
 #pragma unroll
             for (int k = 3; k < 9; ++k) hF[k] = R(0);
-            S[0] = (R)p.s0;
-            S[1] = S[2] = (R)p.s1phi;
-            S[3] = S[4] = S[5] = (R)p.s2;
-            S[6] = S[7] = (R)p.s3;
-            S[8] = (R)p.s4;
+            S[0] = kp.s0;
+            S[1] = S[2] = kp.s1phi;
+            S[3] = S[4] = S[5] = kp.s2;
+            S[6] = S[7] = kp.s3;
+            S[8] = kp.s4;
             collide9<R>(f1, heq, hF, S, cs2);
 
             // ---- flow lattice (Eqs. 32-34)
@@ -429,18 +452,18 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
             hF[6] = R(0);
             hF[7] = R(0);
             hF[8] = R(0);
-            S[0] = (R)p.s0;
-            S[1] = S[2] = (R)p.s1;
+            S[0] = kp.s0;
+            S[1] = S[2] = kp.s1;
             S[3] = S[4] = R(1) / inv_s2a;
             S[5] = R(1) / inv_s2b;
-            S[6] = S[7] = (R)p.s3;
-            S[8] = (R)p.s4;
+            S[6] = S[7] = kp.s3;
+            S[8] = kp.s4;
             collide9<R>(f2, heq, hF, S, cs2);
 
             if (valid) {
                 // populations (own cell; the next step pulls them)
                 if constexpr (P::MIX) {
-                    const R sc1 = (R)p.scale[0];
+                    const R sc1 = kp.scale[0];
                     const int k1 = p.klog2[0];
                     int bad = 0;
                     long long exact = rs[id];
@@ -460,7 +483,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
 #pragma unroll
                     for (int i = 0; i < 9; ++i) fd[i * plane + id] = Conv<P>::st(f1[i], R(1));
                 }
-                const R sc2 = P::MIX ? (R)p.scale[1] : R(1);
+                const R sc2 = P::MIX ? kp.scale[1] : R(1);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     ST q = Conv<P>::st(f2[i], sc2);
@@ -481,6 +504,11 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
                 // F_f = -sum rho phi0_k (u_s,k - u*), T_f = -sum r x (...)
                 for (int k = 0; k < A.np; ++k) {
                     const ParticleDev &pp = A.parts[k];
+                    if (!((near >> k) & 1ull)) {
+                        // no cell of this tile is reached by particle k
+                        if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;
+                        continue;
+                    }
                     double c6[6] = {0, 0, 0, 0, 0, 0};
                     if (valid) {
                         R rx, ry;

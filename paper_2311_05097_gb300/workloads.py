@@ -118,31 +118,55 @@ def drop_on_cylinder(n=512, Rp=60.0, cyl=(256.0, 160.0), R0=50.0, wall=8, D=4.0,
                 name="drop_on_cylinder_2d")
 
 
-def rsa_spheres(n, seed=0, rmin=8.0, rmax=16.0, porosity=0.6, reservoir=32, max_tries=200000):
+def rsa_spheres(n, seed=0, rmin=8.0, rmax=16.0, porosity=0.6, reservoir=32, max_tries=20000):
     """Random sequential addition of non-overlapping spheres in the periodic cube,
     none in the reservoir x < ``reservoir``, until the solid fraction reaches
-    1 - porosity or the packing jams.  Returns (centres, radii)."""
+    1 - porosity or ``max_tries`` consecutive rejections (the packing jams).
+    Returns (centres, radii)."""
     rng = np.random.default_rng(seed)
-    cents, radii = [], []
+    cents = np.zeros((0, 3))
+    radii = np.zeros(0)
     target = (1.0 - porosity) * n ** 3
     vol = 0.0
-    tries = 0
-    while vol < target and tries < max_tries:
-        tries += 1
+    fails = 0
+    while vol < target and fails < max_tries:
         r = rng.uniform(rmin, rmax)
         c = np.array([rng.uniform(reservoir + r, n - r), rng.uniform(0, n), rng.uniform(0, n)])
-        ok = True
-        for c2, r2 in zip(cents, radii):
-            d = c - c2
-            d[1:] -= n * np.floor(d[1:] / n + 0.5)
-            if np.dot(d, d) < (r + r2 + 1.0) ** 2:
-                ok = False
-                break
-        if ok:
-            cents.append(c)
-            radii.append(r)
-            vol += 4.0 / 3.0 * math.pi * r ** 3
-    return np.array(cents).reshape(-1, 3), np.array(radii)
+        if len(radii):
+            d = cents - c
+            d[:, 1:] -= n * np.floor(d[:, 1:] / n + 0.5)
+            if np.any((d * d).sum(1) < (radii + r + 1.0) ** 2):
+                fails += 1
+                continue
+        fails = 0
+        cents = np.vstack([cents, c])
+        radii = np.append(radii, r)
+        vol += 4.0 / 3.0 * math.pi * r ** 3
+    return cents, radii
+
+
+def spheres_indicator(shape, cents, radii, D):
+    """phi0 of a union of spheres (zeta = max over spheres of R - |x - x_c|),
+    evaluated in each sphere's periodic bounding box."""
+    nz, ny, nx = shape
+    zeta = np.full(shape, -1e9)
+    reach = 10.0 * D
+    for c, r in zip(cents, radii):
+        h = int(math.ceil(r + reach))
+        idx = []
+        for a, n in ((2, nz), (1, ny), (0, nx)):
+            lo = int(math.floor(c[a])) - h
+            idx.append(np.arange(lo, lo + 2 * h + 2) % n)
+        zz, yy, xx = np.meshgrid(*idx, indexing="ij")
+        d2 = np.zeros(zz.shape)
+        for a, g, n in ((0, xx, nx), (1, yy, ny), (2, zz, nz)):
+            d = g - c[a]
+            d -= n * np.floor(d / n + 0.5)
+            d2 += d * d
+        sub = r - np.sqrt(d2)
+        cur = zeta[zz, yy, xx]
+        zeta[zz, yy, xx] = np.maximum(cur, sub)
+    return smooth_indicator(zeta, D)
 
 
 def porous_drainage_3d(n=256, seed=0, D=4.0, invade=24, porosity=0.6):
@@ -151,17 +175,8 @@ def porous_drainage_3d(n=256, seed=0, D=4.0, invade=24, porosity=0.6):
     pushes it in +x."""
     shape = (n, n, n)
     cents, radii = rsa_spheres(n, seed=seed, porosity=porosity)
-    X = _coords(shape)
-    zeta = np.full(shape, -1e9)
-    for c, r in zip(cents, radii):
-        d2 = np.zeros(shape)
-        for a in range(3):
-            d = X[a] - c[a]
-            d -= n * np.floor(d / n + 0.5)
-            d2 += d * d
-        zeta = np.maximum(zeta, r - np.sqrt(d2))
-    phi0 = smooth_indicator(zeta, D)
-    x = X[0]
+    phi0 = spheres_indicator(shape, cents, radii, D)
+    x = np.arange(n, dtype=np.float64)[None, None, :]
     # phase-1 slab [0, invade) with smooth interfaces on both sides (periodic in x)
     dx = x - (invade - 1) / 2.0
     dx -= n * np.floor(dx / n + 0.5)
@@ -170,7 +185,7 @@ def porous_drainage_3d(n=256, seed=0, D=4.0, invade=24, porosity=0.6):
                Fb=(1e-6, 0.0, 0.0))
     achieved = float((phi0 < 0.5).mean())
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, steps=2000,
-                name="porous_drainage_3d", porosity=achieved)
+                name="porous_drainage_3d", porosity=achieved, spheres=len(radii))
 
 
 def water_entry(nx=1024, ny=2048, depth=800, wall=8, R=40.0, gap=200.0, D=4.0):

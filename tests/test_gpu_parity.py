@@ -186,3 +186,44 @@ def test_cylinder_full_size_sampled(pf):
     g32, _ = run_pair(pf, c, 6, precision="p32", oracle=False)
     gm = g32.macros()
     assert rel(gm["phi"], om["phi"]) < 1e-5
+
+
+# ---- 3D: D3Q19 flow + D3Q7 order parameter --------------------------------------------
+
+@pytest.mark.parametrize("shape,solid,u_amp,steps", [
+    ((12, 14, 18), True, 0.0, 0),
+    ((12, 14, 18), True, 0.01, 30),
+    ((37, 10, 20), True, 0.01, 12),   # several z chunks, ragged x/y tiles
+])
+def test_p64_matches_oracle_3d(pf, shape, solid, u_amp, steps):
+    c = W.small_case(shape, seed=9, solid=solid, theta_deg=120.0, u_amp=u_amp)
+    g, o = run_pair(pf, c, steps)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, k
+
+
+def test_p64_moving_sphere_matches_oracle(pf):
+    c = W.small_case((16, 18, 20), seed=6, solid=False)
+    part = dict(x=(9.3, 8.6, 7.9), u=(0.01, -0.004, 0.003), w=(0.001, -0.002, 0.002), R=4.0, rho_p=2.0)
+    c["phi"] = (1.0 - W.disc(c["shape"], part["x"], part["R"], c["params"]["D"])) * c["phi"]
+    g, o = run_pair(pf, c, 15, particles=[part])
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
+    pg, po = g.particle(0), o.particle(0)
+    for k in ("x", "u", "w", "F", "T"):
+        a, b = np.array(pg[k]), np.array(getattr(po, k))
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, a, b)
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 5e-3)])
+def test_3d_reduced_precision_against_oracle(pf, precision, tol_phi):
+    c = W.small_case((20, 24, 28), seed=9, solid=True, theta_deg=120.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 30, precision=precision)
+    gm, om = g.macros(), o.macros()
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    if precision == "fp16":
+        d0 = g.diagnostics()
+        g.step(200)
+        d1 = g.diagnostics()
+        assert abs(d1["mass"] - d0["mass"]) / np.abs(c["phi"]).sum() < 1e-13
