@@ -213,10 +213,12 @@ def equal_area_cap_base(theta_deg, area):
     return r, r * math.sin(th)
 
 
-def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2=0.01):
+def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2=None,
+                   sigma=0.005, M=0.1):
     """A semicircular drop of radius r0 (default 0.3 L, limited so that the
     equilibrium base stays within 0.7 L) centred on the top face of a bottom
-    wall slab in an L x L periodic box."""
+    wall slab in an L x L periodic box.  mu2 defaults to 0.1 r^(-2/3) for
+    density ratio r (kinematic viscosity 0.1 r^(1/3) in phase 2)."""
     shape = (L, L)
     phi0 = slab_walls(shape, wall, D, axis=1)
     r0 = 0.3 * L if r0 is None else r0
@@ -230,7 +232,9 @@ def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2
         clamped = True
     centre = ((L - 1) / 2.0, wall - 0.5)
     phi = drop_field(shape, centre, r0, D, phi0)
-    p = params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=1.0 / rho_ratio, mu1=mu1, mu2=mu2,
+    if mu2 is None:
+        mu2 = mu1 * rho_ratio ** (-2.0 / 3.0)
+    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0 / rho_ratio, mu1=mu1, mu2=mu2,
                theta_deg=theta_deg)
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, r0=r0, clamped=clamped,
                 wall=wall)

@@ -85,7 +85,7 @@ def test_total_energy_decays(case):
     if case == "drop":
         c = W.static_drop(n=64, R=16.0)
     else:
-        c = W.flat_wall_drop(64, 60.0, 10.0, r0=16, mu1=0.1, mu2=0.01)
+        c = W.flat_wall_drop(64, 60.0, 10.0, r0=16, mu1=0.1, mu2=0.01, sigma=0.01, M=0.02)
     s = make(c)
     E, EK = energy_series(s, 30, 50)
     dE = np.diff(E)
