@@ -226,6 +226,18 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         };
 
         // ---------------- stage A ----------------
+        // every load of the own cell is issued here, before the first barrier,
+        // so one DRAM round trip per tile covers them all
+        const long long id = s_gy[ly + 3] + s_gx[lx + 3];
+        ST f2raw[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f2raw[i] = ldg(fs + (9 + i) * plane + s_gy[ly + 3 - CY9[i]] + s_gx[lx + 3 - CX9[i]]);
+        AX lag[5];
+        if constexpr (MODE == MODE_STEP) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) lag[k] = ldg(as + k * plane + id);
+        }
         R f1[9];
         ST q1[9];
         const R phi_own = phi_at(lx + 2, ly + 2, f1, q1);
@@ -278,7 +290,6 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         // ---------------- stage C: own cell ----------------
         const int gx = x0 + lx, gy = y0 + ly;
         const bool valid = gx < nx && gy < ny;
-        const long long id = s_gy[ly + 3] + s_gx[lx + 3];
         const int hx = lx + 2, hy = ly + 2, wx = lx + 1, wy = ly + 1;
 
         const R phi = phi_own, phi0 = s_p0[hy][hx];
@@ -331,11 +342,10 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
             Fy += R(0.5) * wgx;
         }
 
-        // pull the flow populations
+        // the flow populations pulled in stage A
         R f2[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            f2[i] = Conv<P>::ld(ldg(fs + (9 + i) * plane + s_gy[ly + 3 - CY9[i]] + s_gx[lx + 3 - CX9[i]]), isc2);
+        for (int i = 0; i < 9; ++i) f2[i] = Conv<P>::ld(f2raw[i], isc2);
 
         // u* (Eq. 36a)
         const R jx = f2[1] - f2[3] + f2[5] - f2[6] - f2[7] + f2[8];
@@ -361,10 +371,15 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         const R ux = usx + R(0.5) * fpx, uy = usy + R(0.5) * fpy;
         const R Ftx = Fx + rho * fpx, Fty = Fy + rho * fpy;
 
-        // lagged fields at the own cell
-        const R upx = (R)ldg(as + 0 * plane + id), upy = (R)ldg(as + 1 * plane + id);
-        const R Spx = (R)ldg(as + 2 * plane + id), Spy = (R)ldg(as + 3 * plane + id);
-        const R php = (R)ldg(as + 4 * plane + id);
+        // lagged fields at the own cell (loaded in stage A for a step; the
+        // macroscopic pass reads them here)
+        if constexpr (MODE == MODE_MACROS) {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) lag[k] = ldg(as + k * plane + id);
+        }
+        const R upx = (R)lag[0], upy = (R)lag[1];
+        const R Spx = (R)lag[2], Spy = (R)lag[3];
+        const R php = (R)lag[4];
 
         // relaxation rates (Eq. 35, 1 - phi0 bounded below by solid_eps)
         R solid = R(1) - phi0;
