@@ -186,6 +186,36 @@ int64_t pf_batch_cells(pf_batch *b);
 int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm);
 void pf_batch_destroy(pf_batch *b);
 
+/* ---- diagnostics without device allocation ----
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: work recorded by CUDA stream capture (where
+ * cudaMalloc/cudaFree are illegal), real-time or fixed-budget loops, and hosts
+ * whose device memory is owned by another allocator.
+ *
+ * Computes the same FP64 quantities as pf_diagnostics -- out4 = {sum phi,
+ * E_F of Eq. (8), E_K = sum rho |u|^2 / 2, E_F + E_K} -- from caller-owned
+ * device arrays (x-fastest, N = nx*ny*nz; u component-major, dim*N), e.g. the
+ * PF_DEVICE output of pf_get_macros, with phi0 the total solid indicator.
+ * Only g->dim, nx, ny, nz and p->sigma, D, theta_deg are read.  out4 is
+ * host (where = PF_HOST; the call then waits for the result) or device memory
+ * (PF_DEVICE; asynchronous).  Work runs on `stream` (NULL = default stream).
+ *
+ * Nothing is allocated: the reduction's per-block partial sums live in one
+ * fixed array in device global memory, sized for at most
+ * PF_NOALLOC_MAX_CELLS cells (PF_NOALLOC_MAX_BLOCKS blocks of 4096 cells,
+ * about 192 KiB); larger grids return PF_EINVAL.  Every GPU that loads the
+ * library holds that array until the process exits.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the array: each
+ * call overwrites every partial it reads, so nothing carries over, but calls
+ * whose kernels overlap on the GPU (different streams, no ordering) race on
+ * it and must be serialised by the caller. */
+#define PF_NOALLOC_MAX_BLOCKS 8192
+#define PF_NOALLOC_MAX_CELLS (8192LL * 4096LL)
+int pf_diagnostics_noalloc(const pf_grid *g, const pf_params *p, const double *phi,
+                           const double *rho, const double *u, const double *phi0, double *out4,
+                           int where, void *stream);
+
 /* Number of kernel launches issued by the library since load (all handles). */
 int64_t pf_launch_count(void);
 

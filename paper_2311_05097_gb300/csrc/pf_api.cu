@@ -105,6 +105,12 @@ static int fail(int code, const char *fmt, ...)
     } while (0)
 
 extern "C" const char *pf_last_error(void) { return t_err.c_str(); }
+
+int pf::set_error(int code, const char *msg)
+{
+    t_err = msg;
+    return code;
+}
 extern "C" int64_t pf_launch_count(void) { return (int64_t)g_launches.load(); }
 
 // ---------------------------------------------------------------------------------------------

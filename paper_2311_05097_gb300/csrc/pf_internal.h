@@ -7,6 +7,9 @@
 
 namespace pf {
 
+// record the thread-local error message returned by pf_last_error; returns code
+int set_error(int code, const char *msg);
+
 // kernel-launch accounting (pf_launch_count)
 void count_launches(long long n);
 

@@ -98,6 +98,8 @@ def load(build_if_missing=False):
         "pf_batch_config": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "pf_batch_destroy": (None, [vp]),
         "pf_launch_count": (C.c_int64, []),
+        "pf_diagnostics_noalloc": (C.c_int, [C.POINTER(pf_grid), C.POINTER(pf_params), vp, vp, vp, vp,
+                                             C.POINTER(C.c_double), C.c_int, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
