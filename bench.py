@@ -1,21 +1,22 @@
 #!/usr/bin/env python
-"""Throughput benchmark of the fused two-lattice step (MLUPS, both lattices
-per cell update) with its HBM-roofline fraction.
+"""Throughput benchmark of the fused two-lattice step: MLUPS (one update of
+both lattices of one cell) and the HBM-roofline fraction of the step kernel.
 
-Default workload: 2D drop resting on a fixed cylinder, 512 x 512 cells,
-density ratio 1000, viscosity ratio 100, contact angle 60 deg, FP32 storage
-and arithmetic.  One bench step = one time step of the whole domain
-(the fused step kernel).  The state (~70 MB) fits in L2, so L2 is flushed
-(a 512 MiB device write) between timed steps and each step is timed alone
-with CUDA events on the library's stream.
+Default workload (``--workload batch``): 256 independent 2D drop-on-flat-wall
+domains with sides drawn from {64, 128, 256, 512}, contact angles 30-150 deg,
+density ratios 1-1000 (seed 1; about 22M cells, 2.9 GB of state, larger than
+L2), FP16 population storage with FP32 arithmetic, advanced by one persistent
+autotuned launch per time step replayed from a CUDA graph.  One bench step =
+one time step of every domain.
 
-Other workloads (--workload): static_drop (128^2, FP64), batch (256
-uneven domains, FP16 storage), water_entry (1024 x 2048 with a particle,
-BF16 storage).
+Other workloads: ``drop_on_cylinder`` (512 x 512, density ratio 1000, FP32;
+its state fits in L2, so L2 is flushed between individually timed steps) and
+``static_drop`` (128 x 128, FP64).
 
---impl reference times the FP64 CPU oracle on the same workload (bounded
-sample) on the host cores.  Under torchrun each rank runs an independent
-replica (no data-path collective); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.  Under torchrun every rank runs an
+independent replica (no data-path collective; weak scaling) and rank 0 prints
+one JSON line with the max-over-ranks time.
 """
 import argparse
 import json
@@ -30,14 +31,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic bytes per cell update: populations read + written once, lagged
-# fields (u, S, phi) read + written once, phi0 read once
+# algorithmic bytes per cell update: every population read and written once,
+# lagged fields (u, S, phi) read and written once, phi0 read once
 BYTES_PER_CELL = {
-    ("2d", "p64"): 8 * (36 + 11),
-    ("2d", "p32"): 4 * (36 + 11),
-    ("2d", "fp16"): 2 * 2 * (8 + 9) + 2 * 8 + 4 * 11,
-    ("2d", "bf16"): 2 * 2 * (8 + 9) + 2 * 8 + 4 * 11,
+    "p64": 8 * (36 + 11),
+    "p32": 4 * (36 + 11),
+    "fp16": 2 * 2 * (8 + 9) + 2 * 8 + 4 * 11,
+    "bf16": 2 * 2 * (8 + 9) + 2 * 8 + 4 * 11,
 }
+DTYPE = {"p64": "f64", "p32": "f32", "fp16": "f16 storage, f32 arithmetic",
+         "bf16": "bf16 storage, f32 arithmetic"}
 
 
 def parse():
@@ -46,14 +49,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="drop_on_cylinder",
-                    choices=["drop_on_cylinder", "static_drop"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "drop_on_cylinder", "static_drop"])
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload(name):
+def batch_workload(count=256):
+    from paper_2311_05097_gb300 import workloads as W
+    draws = W.batch_cases(count, seed=1)
+    cases = [W.flat_wall_drop(d["L"], d["theta_deg"], d["rho_ratio"]) for d in draws]
+    return dict(cases=cases, draws=draws, precision="fp16",
+                desc="%d independent 2D drop-on-flat-wall domains, sides uniform over "
+                     "{64,128,256,512}, theta U[30,150] deg, density ratio log-U[1,1000], "
+                     "seed 1" % count)
+
+
+def single_workload(name):
     from paper_2311_05097_gb300 import workloads as W
     if name == "drop_on_cylinder":
         c = W.drop_on_cylinder()
@@ -82,15 +97,16 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
 
     def stop(self):
         if self.proc is None:
             return None
-        time.sleep(0.25)
+        time.sleep(0.2)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -120,27 +136,7 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in load),
                 "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
-                "samples": len(rows)}
-
-
-# ---------------------------------------------------------------------------------------------
-# oracle (CPU) timing
-# ---------------------------------------------------------------------------------------------
-def oracle_mlups(case, budget_s=12.0, max_steps=None):
-    from oracle import oracle as O
-    o = O.OracleSim(case["shape"], O.make_params(**case["params"]))
-    o.init(case["phi0"], case["phi"])
-    cells = int(math.prod(case["shape"]))
-    t0 = time.perf_counter()
-    o.step(1)
-    dt1 = time.perf_counter() - t0
-    n = max(1, int(budget_s / max(dt1, 1e-6)))
-    if max_steps:
-        n = min(n, max_steps)
-    t0 = time.perf_counter()
-    o.step(n)
-    dt = time.perf_counter() - t0
-    return cells * n / dt / 1e6, n, O.num_threads()
+                "samples": len(rows), "power_w_max": max(r["power"] for r in rows)}
 
 
 def read_peaks():
@@ -150,33 +146,61 @@ def read_peaks():
         return {}
 
 
+def read_traffic(key):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        return json.load(open(path)).get(key, {}).get("bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------------
+# oracle (CPU) timing: a bounded sample of the workload
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(args, budget_s):
+    """Time the FP64 oracle for about ``budget_s`` seconds on the workload.
+    Batch: whole domains taken in order from the batch list.  Returns
+    (MLUPS, description, threads)."""
+    from oracle import oracle as O
+    if args.workload == "batch":
+        cases = batch_workload(args.batch_count)["cases"]
+    else:
+        cases = [single_workload(args.workload)]
+    cells = 0
+    t_total = 0.0
+    used = []
+    for c in cases:
+        o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+        o.init(c["phi0"], c["phi"])
+        t0 = time.perf_counter()
+        o.step(1)
+        one = time.perf_counter() - t0
+        n = max(1, min(50, int((budget_s - t_total) / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        o.step(n)
+        dt = time.perf_counter() - t0
+        cells += int(math.prod(c["shape"])) * n
+        t_total += dt
+        used.append("%s x %d steps" % ("x".join(map(str, c["shape"])), n))
+        if t_total >= budget_s:
+            break
+    desc = "FP64 C oracle (OpenMP) on whole domains of the workload: " + ", ".join(used)
+    return cells / t_total / 1e6, desc, O.num_threads()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    case = workload(args.workload)
-    cells = int(math.prod(case["shape"]))
-    from oracle import oracle as O
-    o = O.OracleSim(case["shape"], O.make_params(**case["params"]))
-    o.init(case["phi0"], case["phi"])
-    o.step(max(args.warmup, 0) and 1)
-    t0 = time.perf_counter()
-    o.step(1)
-    one = time.perf_counter() - t0
-    k = min(args.steps, max(1, int(120.0 / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    o.step(k)
-    dt = time.perf_counter() - t0
-    v = cells * k / dt / 1e6
+    budget = min(120.0, max(10.0, 1.0 * args.steps))
+    v, desc, cores = oracle_sample(args, budget)
     line = {"impl": "reference", "metric": "MLUPS", "value": round(v, 4), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "cells": cells, "desc": case["desc"]},
-            "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": O.num_threads(),
-                             "kind": "oracle",
-                             "sample": "%d full time steps of the %s workload (FP64 C oracle, OpenMP)"
-                                       % (k, args.workload)},
+            "config": {"workload": args.workload},
+            "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": cores,
+                             "kind": "oracle", "sample": desc},
             "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -185,11 +209,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------------------------
-def run_ours(args):
-    import numpy as np
+def setup_dist():
     import torch
-
-    rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -197,12 +218,111 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist, int(os.environ.get("RANK", "0")), world, local
 
-    from paper_2311_05097_gb300 import build as B
-    B.build()
+
+def max_over_ranks(dist, value):
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_batch(args, dist, rank, world, local):
+    import ctypes as C
+
+    import numpy as np
+    import torch
     from paper_2311_05097_gb300 import pf
 
-    case = workload(args.workload)
+    bw = batch_workload(args.batch_count)
+    cases = bw["cases"]
+    prec = args.precision or bw["precision"]
+    cells = sum(int(math.prod(c["shape"])) for c in cases)
+    stream = torch.cuda.Stream()
+    b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision=prec,
+                 stream=stream.cuda_stream)
+    for i, c in enumerate(cases):
+        b.init(i, c["phi0"], c["phi"])
+    # warm-up: the first long call runs the launch-configuration autotuner
+    b.step(256 + max(args.warmup, 3))
+    b.sync()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    n0 = pf.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = pf.launch_count() - n0
+    b.sync()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(dist, e0.elapsed_time(e1))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    bpc = BYTES_PER_CELL[prec]
+    avg_s = total_ms * 1e-3 / args.steps  # one step-kernel launch per step
+    achieved = bpc * cells / avg_s / 1e9
+    tx, ty, cps = b.config()
+
+    e2e = None
+    if not args.no_e2e:
+        S = 100
+        hosts = [(torch.from_numpy(np.ascontiguousarray(c["phi0"])).pin_memory(),
+                  torch.from_numpy(np.ascontiguousarray(c["phi"])).pin_memory(),
+                  torch.empty(c["phi"].shape, dtype=torch.float64).pin_memory()) for c in cases]
+        L = pf.load()
+        e2e_b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases],
+                         precision=prec, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, (h0, h1, _) in enumerate(hosts):
+            rc = L.pf_batch_init(e2e_b._h, i, C.c_void_p(h0.data_ptr()), C.c_void_p(h1.data_ptr()),
+                                 None, None, pf.PF_HOST)
+            if rc:
+                raise pf.PfError(rc, pf.last_error())
+        e2e_b.step(S)
+        for i, (_, _, out) in enumerate(hosts):
+            rc = L.pf_batch_get_macros(e2e_b._h, i, C.c_void_p(out.data_ptr()), None, None, None,
+                                       None, pf.PF_HOST)
+            if rc:
+                raise pf.PfError(rc, pf.last_error())
+        dt = time.perf_counter() - t0
+        e2e_b.close()
+        e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": 16 * cells, "d2h_bytes_per_step": 8 * cells,
+               "steps_per_call": S,
+               "desc": "one call sequence: pf_batch_init of every domain from pinned host phi0, "
+                       "phi; pf_batch_step(%d) (includes the autotuner's timed steps when the "
+                       "configuration is not cached); pf_batch_get_macros(phi) of every domain "
+                       "to pinned host; wall clock" % S}
+    b.close()
+    cfg = {"workload": "batch", "domains": len(cases), "cells": cells, "precision": prec,
+           "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"
+                                   % (cells * bpc / 1e9),
+           "tile": [tx, ty], "ctas_per_sm": cps,
+           "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
+    return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
+                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel="k_step2d")
+
+
+def run_single(args, dist, rank, world, local):
+    import ctypes as C
+
+    import torch
+    from paper_2311_05097_gb300 import pf
+
+    case = single_workload(args.workload)
     prec = args.precision or case["precision"]
     cells = int(math.prod(case["shape"]))
     stream = torch.cuda.Stream()
@@ -240,84 +360,86 @@ def run_ours(args):
     launches = pf.launch_count() - n0
     sim.sync()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(dist, sum(a.elapsed_time(b) for a, b in ev))
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
     mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
-    # roofline of the step kernel (one launch per step)
-    bpc = BYTES_PER_CELL[("2d", prec)]
-    avg_s = statistics.mean(step_ms) * 1e-3
-    achieved = bpc * cells / avg_s / 1e9
-    peaks = read_peaks()
-    peak = peaks.get("hbm_gbs", 6800.0)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        tr = json.load(open(tpath)).get("%s/%s" % (args.workload, prec))
-        if tr:
-            traffic = tr.get("bytes_per_launch")
+    bpc = BYTES_PER_CELL[prec]
+    achieved = bpc * cells / (total_ms * 1e-3 / args.steps) / 1e9
 
-    # end to end through the public API with host buffers
     e2e = None
-    if rank == 0 or True:
-        S = 20
-        iters = 5
-        phi0_h = torch.from_numpy(case["phi0"]).pin_memory().numpy()
-        phi_h = torch.from_numpy(case["phi"]).pin_memory().numpy()
-        out_h = torch.empty(cells, dtype=torch.float64).pin_memory().numpy()
-        e2e_sim = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream, **case["params"])
-        e2e_sim.init(phi0_h, phi_h)
-        e2e_sim.step(S)
-        e2e_sim.sync()
-        import ctypes as C
+    if not args.no_e2e:
+        S, iters = 20, 5
+        phi0_h = torch.from_numpy(case["phi0"]).pin_memory()
+        phi_h = torch.from_numpy(case["phi"]).pin_memory()
+        out_h = torch.empty(cells, dtype=torch.float64).pin_memory()
         L = pf.load()
+        s2 = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream, **case["params"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(iters):
-            e2e_sim.init(phi0_h, phi_h)
-            e2e_sim.step(S)
-            rc = L.pf_get_macros(e2e_sim._h, C.c_void_p(out_h.ctypes.data), None, None, None, None,
+            rc = L.pf_init_fields(s2._h, C.c_void_p(phi0_h.data_ptr()), C.c_void_p(phi_h.data_ptr()),
+                                  None, None, pf.PF_HOST)
+            if rc:
+                raise pf.PfError(rc, pf.last_error())
+            s2.step(S)
+            rc = L.pf_get_macros(s2._h, C.c_void_p(out_h.data_ptr()), None, None, None, None,
                                  pf.PF_HOST)
             if rc:
                 raise pf.PfError(rc, pf.last_error())
         dt = time.perf_counter() - t0
+        s2.close()
         e2e = {"value": round(cells * S * iters / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 2 * 8 * cells, "d2h_bytes_per_step": 8 * cells,
+               "h2d_bytes_per_step": 16 * cells, "d2h_bytes_per_step": 8 * cells,
                "steps_per_call": S,
-               "desc": "pf_init_fields(host phi0, phi) + pf_step(%d) + pf_get_macros(host phi) per "
-                       "iteration, wall clock" % S}
-        e2e_sim.close()
+               "desc": "per call: pf_init_fields(pinned host phi0, phi) + pf_step(%d) + "
+                       "pf_get_macros(phi to pinned host); wall clock" % S}
+    sim.close()
+    cfg = {"workload": args.workload, "cells": cells, "precision": prec, "desc": case["desc"],
+           "l2": "flushed between timed steps: 512 MiB write, then a 256 MiB read so the "
+                 "write-back happens outside the timed step",
+           "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
+    return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
+                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel="k_step2d")
 
+
+def run_ours(args):
+    dist, rank, world, local = setup_dist()
+    from paper_2311_05097_gb300 import build as B
+    if rank == 0 or not dist:
+        B.build()
+    if dist:
+        dist.barrier()
+    if args.workload == "batch":
+        r = run_batch(args, dist, rank, world, local)
+    else:
+        r = run_single(args, dist, rank, world, local)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     cpu = None
     if not args.no_cpu_baseline:
-        v, n, cores = oracle_mlups(case, budget_s=10.0)
+        v, desc, cores = oracle_sample(args, 15.0)
         cpu = {"value": round(v, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": "%d full time steps of the %s workload (FP64 C oracle, OpenMP)"
-                         % (n, args.workload)}
+               "sample": desc}
+    peaks = read_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    if peak is None:
+        peak, peak_src = 6800.0, "fallback"
     line = {
-        "metric": "MLUPS", "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": "MLUPS", "value": round(r["mlups"], 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"p64": "f64", "p32": "f32", "fp16": "f16 storage / f32 arithmetic",
-                  "bf16": "bf16 storage / f32 arithmetic"}[prec],
-        "data": "synthetic",
-        "config": {"workload": args.workload, "cells": cells, "precision": prec,
-                   "desc": case["desc"], "l2": "flushed between timed steps: 512 MiB write, then a 256 MiB read so the write-back happens outside the timed step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "bytes_per_cell": bpc, "kernel": "k_step2d"},
-        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
-        "wall_s": round(t_wall, 3),
+        "dtype": DTYPE[r["prec"]], "data": "synthetic", "config": r["cfg"],
+        "roofline": {"bound": "hbm", "achieved": round(r["achieved"], 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(r["achieved"] / peak, 4),
+                     "traffic": read_traffic("%s/%s" % (args.workload, r["prec"])),
+                     "bytes_per_cell": r["bpc"], "kernel": r["kernel"], "peak_source": peak_src},
+        "clocks": r["clk"], "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
+        "wall_s": round(r["t_wall"], 3),
     }
     print(json.dumps(line), flush=True)
     if dist:
