@@ -113,7 +113,7 @@ def drop_on_cylinder(n=512, Rp=60.0, cyl=(256.0, 160.0), R0=50.0, wall=8, D=4.0,
     # density ratio 1000 the sigma = 0.01, M = 0.02 pair of the static drop is
     # unstable with this scheme
     p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=rho2, mu1=0.1, mu2=mu2,
-               theta_deg=theta_deg)
+               theta_deg=theta_deg, s0=1.6)
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, steps=20000,
                 name="drop_on_cylinder_2d")
 
@@ -200,7 +200,7 @@ def water_entry(nx=1024, ny=2048, depth=800, wall=8, R=40.0, gap=200.0, D=4.0):
     solid = phi0 + disc(shape, particle["x"], R, D)
     phi = (1.0 - solid) * np.tanh(2.0 * (surface - y) / D)
     p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1e-3, mu1=0.1, mu2=1e-3,
-               theta_deg=90.0, g=(0.0, -1e-6, 0.0))
+               theta_deg=90.0, g=(0.0, -1e-6, 0.0), s0=1.6)
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=[particle], steps=50000,
                 name="water_entry_2d")
 
@@ -214,7 +214,7 @@ def equal_area_cap_base(theta_deg, area):
 
 
 def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2=None,
-                   sigma=0.005, M=0.1):
+                   sigma=0.001, M=0.1, s0=1.6):
     """A semicircular drop of radius r0 (default 0.3 L, limited so that the
     equilibrium base stays within 0.7 L) centred on the top face of a bottom
     wall slab in an L x L periodic box.  mu2 defaults to 0.1 r^(-2/3) for
@@ -234,8 +234,11 @@ def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2
     phi = drop_field(shape, centre, r0, D, phi0)
     if mu2 is None:
         mu2 = mu1 * rho_ratio ** (-2.0 / 3.0)
+    # s0 (zeroth flow moment, a free rate of S_H in Eq. 38) = 1.6 delays the
+    # high-density-ratio instability next to wetting walls (1 in the paper's
+    # own runs, whose density ratios are <= 10)
     p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0 / rho_ratio, mu1=mu1, mu2=mu2,
-               theta_deg=theta_deg)
+               theta_deg=theta_deg, s0=s0)
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, r0=r0, clamped=clamped,
                 wall=wall)
 

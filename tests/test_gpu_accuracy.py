@@ -1,0 +1,153 @@
+"""Accuracy of the FP32 and 16-bit storage paths against the FP64 path on the
+paper-shaped workloads, and of the FP64 path against the physics the paper
+fixes (prescribed contact angle, equal-area drop height on a cylinder).
+
+Each test records its measured numbers in ``gpurun_out/accuracy.jsonl`` (when
+that folder exists) so they can be summarised next to the benchmark.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import closed_forms as CF
+from paper_2311_05097_gb300 import analysis as A
+from paper_2311_05097_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def record(name, **vals):
+    out = os.path.join(ROOT, "gpurun_out")
+    if os.path.isdir(out):
+        with open(os.path.join(out, "accuracy.jsonl"), "a") as f:
+            f.write(json.dumps(dict(test=name, **vals)) + "\n")
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_2311_05097_gb300 import build
+    build.build()
+    from paper_2311_05097_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+def run(pf, case, steps, precision, particles=()):
+    s = pf.Sim(case["shape"], precision=precision, **case["params"])
+    for k, pp in enumerate(particles):
+        s.set_particle(k, **pp)
+    s.init(case["phi0"], case["phi"], case.get("u"))
+    s.step(steps)
+    return s
+
+
+def test_cylinder_fp32_against_fp64(pf):
+    """Drop (R0 = 50) on a cylinder (Rp = 60), 512 x 512, density ratio 1000,
+    theta = 60 deg: FP32 storage and arithmetic stays within 1e-5 of FP64 in
+    phi.  At density ratio 1000 the scheme does not stay stable to the
+    configuration's 20000 steps next to wetting solids (blow-up after a few
+    thousand steps, in the oracle as on the GPU), so the comparison covers the
+    first 3000 steps; the FP64 drop height is compared with the equal-area
+    H_max of Eqs. (40)-(41) only as a trend."""
+    c = W.drop_on_cylinder()
+    steps = 3000
+    s64 = run(pf, c, steps, "p64")
+    s32 = run(pf, c, steps, "p32")
+    m64, m32 = s64.macros(), s32.macros()
+    dphi = float(np.abs(m32["phi"] - m64["phi"]).max())
+    d = s64.diagnostics()
+    # measured height of the drop top above the cylinder centre (x = 256)
+    H = A.drop_top_height(m64["phi"], 256.0, 160.0)
+    A0 = CF.initial_drop_area(50.0, 60.0)
+    Hth, r, k = CF.hmax_on_cylinder(60.0, 60.0, A0)
+    record("cylinder", steps=steps, max_abs_dphi_fp32_vs_fp64=dphi, H_measured=H, H_equal_area=Hth,
+           E_total=d["E_total"], nan=d["nan_flag"])
+    assert d["nan_flag"] == 0
+    assert dphi <= 1e-5
+    # the drop is still relaxing at 20000 steps (sigma = 0.001): it only
+    # moves toward the equilibrium height, from R0 + Rp = 110
+    assert abs(H - Hth) < abs(110.0 - Hth) + 4.0
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_mixed_mass_drift_per_1e4_steps(pf, precision):
+    """Order-parameter mass drift of the 16-bit paths over 10^4 steps
+    (target <= 1e-10 relative)."""
+    c = W.flat_wall_drop(256, 45.0, 20.0, s0=1.0)
+    s = pf.Sim(c["shape"], precision=precision, **c["params"])
+    s.init(c["phi0"], c["phi"])
+    m0 = s.diagnostics()["mass"]
+    s.step(10000)
+    d = s.diagnostics()
+    drift = abs(d["mass"] - m0) / np.abs(c["phi"]).sum()
+    record("mass_drift", precision=precision, steps=10000, drift=drift)
+    assert d["nan_flag"] == 0
+    assert drift <= 1e-10
+
+
+def test_batch_contact_angles(pf):
+    """Flat-wall drops drawn like the batched sweep (theta in [30, 150] deg,
+    density ratio in [1, 1000]): after relaxation the FP16-storage angle is
+    within 1 deg of the FP64 angle; the FP64 angle is compared with the
+    prescribed one."""
+    # density ratios up to 30: higher ratios next to wetting walls do not stay
+    # stable to equilibrium with this scheme (see the design notes)
+    draws = [(64, 35.0, 1.0), (64, 60.0, 30.0), (64, 90.0, 10.0), (64, 120.0, 5.0),
+             (64, 145.0, 20.0), (128, 50.0, 3.0), (128, 100.0, 2.0), (128, 135.0, 30.0)]
+    cases = [W.flat_wall_drop(L, th, r, s0=1.0) for L, th, r in draws]
+    steps = 60000
+    b64 = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="p64")
+    b16 = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="fp16")
+    for i, c in enumerate(cases):
+        b64.init(i, c["phi0"], c["phi"])
+        b16.init(i, c["phi0"], c["phi"])
+    b64.step(steps)
+    b16.step(steps)
+    rows = []
+    for i, ((L, th, r), c) in enumerate(zip(draws, cases)):
+        a64, _ = A.contact_angle_flat(b64.macros(i)["phi"], c["phi0"], 4.0)
+        a16, _ = A.contact_angle_flat(b16.macros(i)["phi"], c["phi0"], 4.0)
+        rows.append(dict(L=L, theta=th, ratio=r, theta_fp64=a64, theta_fp16=a16))
+    record("batch_contact_angles", steps=steps, rows=rows)
+    for row in rows:
+        assert abs(row["theta_fp16"] - row["theta_fp64"]) <= 1.0, row
+        assert abs(row["theta_fp64"] - row["theta"]) <= 8.0, row
+
+
+def test_drainage_3d_saturation(pf):
+    """3D drainage through random spheres (D3Q19 + D3Q7, theta = 120 deg,
+    body force 1e-6, density ratio 10): FP16-storage saturation within 1e-3 of
+    FP64 (128^3 box, 1000 steps)."""
+    c = W.porous_drainage_3d(n=128)
+    steps = 1000
+    s64 = run(pf, c, steps, "p64")
+    s16 = run(pf, c, steps, "fp16")
+    S64 = A.saturation(s64.macros()["phi"], c["phi0"])
+    S16 = A.saturation(s16.macros()["phi"], c["phi0"])
+    S0 = A.saturation(c["phi"], c["phi0"])
+    record("drainage_3d", n=128, steps=steps, porosity=c["porosity"], S_init=S0, S_fp64=S64,
+           S_fp16=S16)
+    assert abs(S16 - S64) <= 1e-3
+
+
+def test_water_entry_bf16_against_fp64(pf):
+    """2D water entry (1024 x 2048, density ratio 1000, particle R = 40,
+    rho_p = 2, theta = 90 deg): BF16-storage particle trajectory against FP64
+    over the first 2000 steps."""
+    c = W.water_entry()
+    part = dict(c["particles"][0])
+    steps = 2000
+    s64 = run(pf, c, steps, "p64", particles=[part])
+    s16 = run(pf, c, steps, "bf16", particles=[part])
+    p64, p16 = s64.particle(0), s16.particle(0)
+    dx = float(np.abs(np.array(p64["x"]) - np.array(p16["x"])).max())
+    du = float(np.abs(np.array(p64["u"]) - np.array(p16["u"])).max())
+    record("water_entry", steps=steps, x_fp64=p64["x"], x_bf16=p16["x"], u_fp64=p64["u"],
+           u_bf16=p16["u"], max_dx=dx, max_du=du)
+    assert s64.diagnostics()["nan_flag"] == 0
+    assert dx < 0.05 and du < 1e-3
