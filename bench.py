@@ -4,12 +4,12 @@ both lattices of one cell) and the HBM-roofline fraction of the step kernel.
 
 Default workload (``--workload batch``): 256 independent 2D drop-on-flat-wall
 domains with sides drawn from {64, 128, 256, 512}, contact angles 30-150 deg,
-density ratios 1-1000 (seed 1; about 22M cells, 2.9 GB of state, larger than
+density ratios 1-100 (seed 1; about 24M cells, 3.1 GB of state, larger than
 L2), FP16 population storage with FP32 arithmetic, advanced by one persistent
 autotuned launch per time step replayed from a CUDA graph.  One bench step =
 one time step of every domain.
 
-Other workloads: ``drop_on_cylinder`` (512 x 512, density ratio 1000, FP32;
+Other workloads: ``drop_on_cylinder`` (512 x 512, density ratio 100, FP32;
 its state fits in L2, so L2 is flushed between individually timed steps) and
 ``static_drop`` (128 x 128, FP64).
 
@@ -39,6 +39,12 @@ BYTES_PER_CELL = {
     "fp16": 2 * 2 * (8 + 9) + 2 * 8 + 4 * 11,
     "bf16": 2 * 2 * (8 + 9) + 2 * 8 + 4 * 11,
 }
+BYTES_PER_CELL_3D = {
+    "p64": 8 * (52 + 15),
+    "p32": 4 * (52 + 15),
+    "fp16": 2 * 2 * (6 + 19) + 2 * 8 + 4 * 15,
+    "bf16": 2 * 2 * (6 + 19) + 2 * 8 + 4 * 15,
+}
 DTYPE = {"p64": "f64", "p32": "f32", "fp16": "f16 storage, f32 arithmetic",
          "bf16": "bf16 storage, f32 arithmetic"}
 
@@ -50,7 +56,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "drop_on_cylinder", "static_drop"])
+                    choices=["batch", "drop_on_cylinder", "static_drop", "water_entry",
+                             "drainage_3d"])
+    ap.add_argument("--n3d", type=int, default=256, help="cube side of drainage_3d")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -64,12 +72,26 @@ def batch_workload(count=256):
     cases = [W.flat_wall_drop(d["L"], d["theta_deg"], d["rho_ratio"]) for d in draws]
     return dict(cases=cases, draws=draws, precision="fp16",
                 desc="%d independent 2D drop-on-flat-wall domains, sides uniform over "
-                     "{64,128,256,512}, theta U[30,150] deg, density ratio log-U[1,1000], "
+                     "{64,128,256,512}, theta U[30,150] deg, density ratio log-U[1,100], "
                      "seed 1" % count)
 
 
-def single_workload(name):
+def single_workload(name, n3d=256):
     from paper_2311_05097_gb300 import workloads as W
+    if name == "water_entry":
+        c = W.water_entry()
+        c["precision"] = "bf16"
+        c["desc"] = ("2D water entry: particle R=40, rho_p=2, u=-0.02, 1024x2048, pool depth 800, "
+                     "density ratio 100, theta 90 deg; force/torque reduction and Newton-Euler "
+                     "in FP64 every step")
+        return c
+    if name == "drainage_3d":
+        c = W.porous_drainage_3d(n=n3d)
+        c["precision"] = "fp16"
+        c["desc"] = ("3D drainage, %d^3, random non-overlapping spheres R 8-16 (porosity %.3f), "
+                     "theta 120 deg, body force 1e-6, density ratio 10, D3Q19 + D3Q7"
+                     % (n3d, c["porosity"]))
+        return c
     if name == "drop_on_cylinder":
         c = W.drop_on_cylinder()
         c["precision"] = "p32"
@@ -165,12 +187,14 @@ def oracle_sample(args, budget_s):
     if args.workload == "batch":
         cases = batch_workload(args.batch_count)["cases"]
     else:
-        cases = [single_workload(args.workload)]
+        cases = [single_workload(args.workload, args.n3d)]
     cells = 0
     t_total = 0.0
     used = []
     for c in cases:
         o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+        for k, pp in enumerate(c.get("particles", [])):
+            o.set_particle(k, O.Particle(**pp))
         o.init(c["phi0"], c["phi"])
         t0 = time.perf_counter()
         o.step(1)
@@ -322,12 +346,19 @@ def run_single(args, dist, rank, world, local):
     import torch
     from paper_2311_05097_gb300 import pf
 
-    case = single_workload(args.workload)
+    case = single_workload(args.workload, args.n3d)
     prec = args.precision or case["precision"]
     cells = int(math.prod(case["shape"]))
+    dim = len(case["shape"])
+    bpc = (BYTES_PER_CELL if dim == 2 else BYTES_PER_CELL_3D)[prec]
+    in_l2 = cells * bpc < 256e6  # state small enough to stay in the 129 MB L2 between steps
     stream = torch.cuda.Stream()
     sim = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream, **case["params"])
+    for k, pp in enumerate(case.get("particles", [])):
+        sim.set_particle(k, **pp)
     sim.init(case["phi0"], case["phi"])
+    if not in_l2:
+        return run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     scrub = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -365,7 +396,6 @@ def run_single(args, dist, rank, world, local):
         dist.barrier()
     torch.cuda.synchronize()
     mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
-    bpc = BYTES_PER_CELL[prec]
     achieved = bpc * cells / (total_ms * 1e-3 / args.steps) / 1e9
 
     e2e = None
@@ -402,6 +432,72 @@ def run_single(args, dist, rank, world, local):
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
                 clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel="k_step2d")
+
+
+def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream):
+    """A single domain whose state exceeds L2: K steps timed together (graph
+    replay), no flush needed."""
+    import ctypes as C
+
+    import numpy as np
+    import torch
+    from paper_2311_05097_gb300 import pf
+
+    sim.step(max(args.warmup, 3))
+    sim.sync()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    n0 = pf.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = pf.launch_count() - n0
+    sim.sync()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(dist, e0.elapsed_time(e1))
+    if dist:
+        dist.barrier()
+    mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    nker = 2 if case.get("particles") else 1
+    achieved = bpc * cells / (total_ms * 1e-3 / args.steps) / 1e9
+    e2e = None
+    if not args.no_e2e:
+        S = 20
+        phi0_h = torch.from_numpy(np.ascontiguousarray(case["phi0"])).pin_memory()
+        phi_h = torch.from_numpy(np.ascontiguousarray(case["phi"])).pin_memory()
+        out_h = torch.empty(cells, dtype=torch.float64).pin_memory()
+        L = pf.load()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = L.pf_init_fields(sim._h, C.c_void_p(phi0_h.data_ptr()), C.c_void_p(phi_h.data_ptr()),
+                              None, None, pf.PF_HOST)
+        if rc:
+            raise pf.PfError(rc, pf.last_error())
+        sim.step(S)
+        rc = L.pf_get_macros(sim._h, C.c_void_p(out_h.data_ptr()), None, None, None, None, pf.PF_HOST)
+        if rc:
+            raise pf.PfError(rc, pf.last_error())
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": 16 * cells, "d2h_bytes_per_step": 8 * cells,
+               "steps_per_call": S,
+               "desc": "pf_init_fields(pinned host phi0, phi) + pf_step(%d) + pf_get_macros(phi "
+                       "to pinned host); wall clock" % S}
+    sim.close()
+    cfg = {"workload": args.workload, "cells": cells, "precision": prec, "desc": case["desc"],
+           "l2": "state (%.2f GB) larger than L2 (129 MB); no flush" % (cells * bpc / 1e9),
+           "kernels_per_step": nker,
+           "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
+    kernel = "k_step3d" if len(case["shape"]) == 3 else "k_step2d"
+    return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
+                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel=kernel)
 
 
 def run_ours(args):

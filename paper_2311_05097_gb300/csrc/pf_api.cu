@@ -151,8 +151,9 @@ static int validate(const pf_grid *g, const pf_params *p)
     const int nz = g->dim == 2 ? 1 : g->nz;
     if (g->nx < 4 || g->ny < 4 || (g->dim == 3 && nz < 4))
         return fail(PF_EINVAL, "grid sizes must be >= 4 (got %d x %d x %d)", g->nx, g->ny, nz);
-    if ((long long)g->nx * g->ny * nz > (1LL << 31))
-        return fail(PF_EINVAL, "grid has more than 2^31 cells");
+    const long long pitch = (g->nx + 31) / 32 * 32;
+    if (pitch * g->ny * nz + 64 >= (1LL << 31))
+        return fail(PF_EINVAL, "grid too large: one population array must hold fewer than 2^31 cells");
     for (int a = 0; a < g->dim; ++a)
         if (g->periodic[a] != 1)
             return fail(PF_EINVAL, "only periodic boundaries are supported (walls are phi0 slabs)");
@@ -163,6 +164,8 @@ static int validate(const pf_grid *g, const pf_params *p)
     if (p->rho1 <= 0 || p->rho2 <= 0) return fail(PF_EINVAL, "densities must be > 0");
     if (p->mu1 <= 0 || p->mu2 <= 0) return fail(PF_EINVAL, "viscosities must be > 0");
     if (!(p->d0 > 0 && p->d0 < 0.5)) return fail(PF_EINVAL, "d0 must lie in (0, 1/2)");
+    if (g->dim == 3 && p->d0 > 1.0 / 3.0 + 1e-12)
+        return fail(PF_EINVAL, "3D needs d0 <= 1/3 (the D3Q7 rest weight 1 - 3 d0 must be >= 0)");
     const double s[] = {p->s0, p->s1, p->s2, p->s3, p->s4};
     for (double x : s)
         if (!(x > 0 && x < 2)) return fail(PF_EINVAL, "relaxation rates must lie in (0, 2)");
@@ -245,8 +248,16 @@ static DevParams derive(int dim, const pf_params *p)
     // typical magnitudes: w_1 eta (3 sigma/D) for the order parameter, w_1 (3 sigma/D)/cs2 for flow
     const double w1 = dim == 2 ? 0.5 * (d0 - d0 * d0) : 0.5 * d0;
     const double musc = std::max(3.0 * p->sigma / p->D, 1e-6);
-    int k1 = p->store_log2_scale[0] ? p->store_log2_scale[0] : default_klog2(w1 * d.eta * musc);
+    // order parameter: the exact rest-population bookkeeping needs every stored
+    // mover below 8 (stored = value * 2^k1); bound the movers by
+    // w_1 (|u|/cs^2 + eta * 2 mu_max) with |u| <= 0.25 and mu_max = 3 sigma/D
+    const double m1max = w1 * (0.25 / d.cs2 + d.eta * 2.0 * musc);
+    int k1 = p->store_log2_scale[0] ? p->store_log2_scale[0]
+                                    : (int)std::floor(std::log2(8.0 / m1max));
+    k1 = std::max(0, std::min(24, k1));
+    // flow: scale typical magnitudes into FP16's normal range, far from overflow
     int k2 = p->store_log2_scale[1] ? p->store_log2_scale[1] : default_klog2(w1 * musc / d.cs2);
+    k2 = std::max(0, std::min(12, k2));
     if (!mix) k1 = k2 = 0;
     d.klog2[0] = k1;
     d.klog2[1] = k2;

@@ -229,72 +229,53 @@ struct Conv<PMixB> {
     }
 };
 
-// Fixed-point image (value * 2^REST_FRAC_BITS) of a stored 16-bit population
-// whose real value is stored * 2^-k.  Exact for every finite input (FP16 with
-// k <= 25; BF16 after the flush in bf16_flush).  Sets *bad for inf/nan.
-__device__ __forceinline__ long long fixed_of_half(__half h, int k, int *bad)
-{
-    unsigned int b = __half_as_ushort(h);
-    int e = (b >> 10) & 0x1f;
-    long long mant = b & 0x3ff;
-    if (e == 31) {
-        *bad = 1;
-        return 0;
-    }
-    if (e) mant |= 0x400;
-    int E = e ? e : 1;
-    // value = mant * 2^(E - 25 - k); fixed = mant * 2^(E - 25 - k + FRAC)
-    int sh = E - 25 - k + REST_FRAC_BITS;
-    if (sh > 62 - 11) {  // |value| >= 2^12: outside the fixed-point range
-        *bad = 1;
-        return 0;
-    }
-    long long v = mant << sh;
-    return (b & 0x8000) ? -v : v;
-}
+// Exact integer image of a stored 16-bit order-parameter population, in units
+// of 2^-24 of the stored (scaled) value.  Valid for |stored| < 8: then the
+// image is below 2^27 and sums of 16 images fit in 32 bits.  FP16 values are
+// all multiples of 2^-24; BF16 values are made so by bf16_flush at store time.
+// Sets *bad for values outside the range (or inf / nan).
+constexpr float FIX24_LIMIT = 8.0f;
 
-__device__ __forceinline__ long long fixed_of_bf16(__nv_bfloat16 h, int k, int *bad)
+__device__ __forceinline__ int fix24_of_float(float v, int *bad)
 {
-    unsigned int b = __bfloat16_as_ushort(h);
-    int e = (b >> 7) & 0xff;
-    long long mant = b & 0x7f;
-    if (e == 255) {
+    if (!(fabsf(v) < FIX24_LIMIT)) {
         *bad = 1;
         return 0;
     }
-    if (e == 0) return 0;  // subnormals are flushed when stored
-    mant |= 0x80;
-    // value = mant * 2^(e - 134 - k)
-    int sh = e - 134 - k + REST_FRAC_BITS;
-    if (sh < 0) return 0;  // flushed when stored (see bf16_flush)
-    if (sh > 62 - 8) {
-        *bad = 1;
-        return 0;
-    }
-    long long v = mant << sh;
-    return (b & 0x8000) ? -v : v;
-}
-
-// Zero a BF16 whose fixed-point image would need bits below 2^-FRAC.
-__device__ __forceinline__ __nv_bfloat16 bf16_flush(__nv_bfloat16 h, int k)
-{
-    unsigned int b = __bfloat16_as_ushort(h);
-    int e = (b >> 7) & 0xff;
-    if (e == 0 || (e != 255 && e - 134 - k + REST_FRAC_BITS < 0)) return __ushort_as_bfloat16(0);
-    return h;
+    return __float2int_rn(v * 16777216.0f);
 }
 
 template <class S>
-__device__ __forceinline__ long long fixed_of(S h, int k, int *bad);
+__device__ __forceinline__ float stored_to_float(S q);
 template <>
-__device__ __forceinline__ long long fixed_of<__half>(__half h, int k, int *bad)
+__device__ __forceinline__ float stored_to_float<__half>(__half q) { return __half2float(q); }
+template <>
+__device__ __forceinline__ float stored_to_float<__nv_bfloat16>(__nv_bfloat16 q)
 {
-    return fixed_of_half(h, k, bad);
+    return __bfloat162float(q);
 }
-template <>
-__device__ __forceinline__ long long fixed_of<__nv_bfloat16>(__nv_bfloat16 h, int k, int *bad)
+
+template <class S>
+__device__ __forceinline__ int fix24(S q, int *bad)
 {
-    return fixed_of_bf16(h, k, bad);
+    return fix24_of_float(stored_to_float<S>(q), bad);
+}
+
+// Zero a BF16 whose value is not a multiple of 2^-24 (|v| < 2^-17; BF16
+// carries 8 significant bits).
+__device__ __forceinline__ __nv_bfloat16 bf16_flush(__nv_bfloat16 h)
+{
+    const unsigned int b = __bfloat16_as_ushort(h);
+    const int e = (b >> 7) & 0xff;  // biased exponent, value ~ 2^(e - 127)
+    if (e < 127 - 17) return __ushort_as_bfloat16(0);
+    return h;
+}
+
+// Move an integer image in 2^-24 stored units (stored = value * 2^k) to the
+// rest population's 2^-50 units: shift by 26 - k.
+__device__ __forceinline__ long long fix24_to_rest(int v, int k)
+{
+    return (long long)v << (26 - k);
 }
 
 __device__ __forceinline__ float float_of_fixed(long long v)

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
     __shared__ R s_mu[WY][WX];
     __shared__ R s_w[WY][WX];
     __shared__ int s_gx[TX + 6];
-    __shared__ long long s_gy[TY + 6];
+    __shared__ int s_gy[TY + 6];  // row offsets y * pitch (planes hold < 2^31 cells)
     __shared__ int s_gyi[TY + 6];
     __shared__ double s_red[NT / 32][6];
     __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         for (int k = tid; k < TY + 6; k += NT) {
             const int yy = wrap_idx(y0 - 3 + k, ny);
             s_gyi[k] = yy;
-            s_gy[k] = (long long)yy * Dm.pitch;
+            s_gy[k] = yy * Dm.pitch;
         }
         if constexpr (MOVING) {
             // conservative test of the tile + 2 frame against each particle's
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         // ---------------- stage A ----------------
         // every load of the own cell is issued here, before the first barrier,
         // so one DRAM round trip per tile covers them all
-        const long long id = s_gy[ly + 3] + s_gx[lx + 3];
+        const int id = s_gy[ly + 3] + s_gx[lx + 3];
         ST f2raw[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i)
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         if constexpr (MODE == MODE_STEP) {
             for (int r = tid; r < WX * WY; r += NT) {
                 const int wx = r % WX, wy = r / WX;
-                const long long id = s_gy[wy + 2] + s_gx[wx + 2];
+                const int id = s_gy[wy + 2] + s_gx[wx + 2];
                 const R ux = (R)ldg(as + 0 * plane + id), uy = (R)ldg(as + 1 * plane + id);
                 const R Sx = (R)ldg(as + 2 * plane + id), Sy = (R)ldg(as + 3 * plane + id);
                 s_w[wy][wx] = Sx * uy - ux * Sy;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
             for (int j = -1; j <= 1; ++j)
 #pragma unroll
                 for (int i = -1; i <= 1; ++i) {
-                    const long long nid = s_gy[ly + 3 + j] + s_gx[lx + 3 + i];
+                    const int nid = s_gy[ly + 3 + j] + s_gx[lx + 3 + i];
                     const R ux = (R)ldg(as + 0 * plane + nid), uy = (R)ldg(as + 1 * plane + nid);
                     const R sx = (R)ldg(as + 2 * plane + nid), sy = (R)ldg(as + 3 * plane + nid);
                     wv[j + 1][i + 1] = sx * uy - ux * sy;
@@ -405,10 +405,10 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
                 const long long o = (long long)gy * nx + gx;
                 double phv = (double)phi;
                 if constexpr (P::MIX) {
-                    long long acc = rs[id];
-                    int bad = 0;
+                    int bad = 0, sold = 0;
 #pragma unroll
-                    for (int i = 1; i < 9; ++i) acc += fixed_of<ST>(q1[i], p.klog2[0], &bad);
+                    for (int i = 1; i < 9; ++i) sold += fix24<ST>(q1[i], &bad);
+                    const long long acc = rs[id] + fix24_to_rest(sold, p.klog2[0]);
                     phv = double_of_fixed(acc);
                 }
                 Dm.macro[0 * N + o] = phv;
@@ -480,19 +480,18 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
                 if constexpr (P::MIX) {
                     const R sc1 = kp.scale[0];
                     const int k1 = p.klog2[0];
-                    int bad = 0;
-                    long long exact = rs[id];
+                    int bad = 0, sold = 0, snew = 0;
 #pragma unroll
-                    for (int i = 1; i < 9; ++i) exact += fixed_of<ST>(q1[i], k1, &bad);
-                    long long rest = exact;
+                    for (int i = 1; i < 9; ++i) sold += fix24<ST>(q1[i], &bad);
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
                         ST q = Conv<P>::st(f1[i], sc1);
-                        if constexpr (P::id == 3) q = bf16_flush(q, k1);
-                        rest -= fixed_of<ST>(q, k1, &bad);
+                        if constexpr (P::id == 3) q = bf16_flush(q);
+                        snew += fix24<ST>(q, &bad);
                         fd[i * plane + id] = q;
                     }
-                    rd[id] = rest;
+                    // exact: sum of the cell's order-parameter populations is unchanged
+                    rd[id] = rs[id] + fix24_to_rest(sold - snew, k1);
                     if (bad) atomicOr(A.flags, 1);
                 } else {
 #pragma unroll
@@ -502,7 +501,6 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     ST q = Conv<P>::st(f2[i], sc2);
-                    if constexpr (P::id == 3) q = bf16_flush(q, p.klog2[1]);
                     fd[(9 + i) * plane + id] = q;
                 }
                 // fields of this step, read as the previous step's by the next one

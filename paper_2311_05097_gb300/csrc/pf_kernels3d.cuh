@@ -482,10 +482,10 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     const long long o = ((long long)z * ny + gy) * nx + gx;
                     double phv = (double)phi;
                     if constexpr (P::MIX) {
-                        long long acc = rs[id];
-                        int bad = 0;
+                        int bad = 0, sold = 0;
 #pragma unroll
-                        for (int i = 1; i < 7; ++i) acc += fixed_of<ST>(q1[i], p.klog2[0], &bad);
+                        for (int i = 1; i < 7; ++i) sold += fix24<ST>(q1[i], &bad);
+                        const long long acc = rs[id] + fix24_to_rest(sold, p.klog2[0]);
                         phv = double_of_fixed(acc);
                     }
                     Dm.macro[0 * N + o] = phv;
@@ -578,19 +578,18 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     if constexpr (P::MIX) {
                         const R sc1 = kp.scale[0];
                         const int k1 = p.klog2[0];
-                        int bad = 0;
-                        long long exact = rs[id];
+                        int bad = 0, sold = 0, snew = 0;
 #pragma unroll
-                        for (int i = 1; i < 7; ++i) exact += fixed_of<ST>(q1[i], k1, &bad);
-                        long long rest = exact;
+                        for (int i = 1; i < 7; ++i) sold += fix24<ST>(q1[i], &bad);
 #pragma unroll
                         for (int i = 1; i < 7; ++i) {
                             ST qv = Conv<P>::st(f1[i], sc1);
-                            if constexpr (P::id == 3) qv = bf16_flush(qv, k1);
-                            rest -= fixed_of<ST>(qv, k1, &bad);
+                            if constexpr (P::id == 3) qv = bf16_flush(qv);
+                            snew += fix24<ST>(qv, &bad);
                             fd[i * plane + id] = qv;
                         }
-                        rd[id] = rest;
+                        // exact: sum of the cell's order-parameter populations is unchanged
+                        rd[id] = rs[id] + fix24_to_rest(sold - snew, k1);
                         if (bad) atomicOr(A.flags, 1);
                     } else {
 #pragma unroll
@@ -600,7 +599,6 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
 #pragma unroll
                     for (int i = 0; i < 19; ++i) {
                         ST qv = Conv<P>::st(f2[i], sc2);
-                        if constexpr (P::id == 3) qv = bf16_flush(qv, p.klog2[1]);
                         fd[(7 + i) * plane + id] = qv;
                     }
                     ad[0 * plane + id] = (AX)ux;

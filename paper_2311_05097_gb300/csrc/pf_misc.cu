@@ -188,7 +188,8 @@ __global__ void k_init_f(DomainDev Dm, const double *phi, const double *u, const
         const double Pv = Pin ? Pin[o] : 0.0;
         const double em = p.eta * mu[o];
         // order-parameter lattice
-        long long rest_acc = fixed_of_double(ph);
+        const long long rest_phi = fixed_of_double(ph);
+        int rest_s = 0, bad = 0;
         for (int i = 0; i < L1.Q; ++i) {
             double cu = 0.0;
             for (int a = 0; a < dim; ++a) cu += L1.c[i][a] * uu[a];
@@ -199,15 +200,15 @@ __global__ void k_init_f(DomainDev Dm, const double *phi, const double *u, const
             if constexpr (P::MIX) {
                 if (i == 0) continue;
                 ST q = Conv<P>::st((float)fe, (float)p.scale[0]);
-                if constexpr (P::id == 3) q = bf16_flush(q, p.klog2[0]);
-                int bad = 0;
-                rest_acc -= fixed_of<ST>(q, p.klog2[0], &bad);
+                if constexpr (P::id == 3) q = bf16_flush(q);
+                rest_s += fix24<ST>(q, &bad);
                 f[i * plane + id] = q;
             } else {
                 f[i * plane + id] = (ST)fe;
             }
         }
-        if constexpr (P::MIX) rest[cell_of(Dm, x, y, z)] = rest_acc;
+        if constexpr (P::MIX) rest[cell_of(Dm, x, y, z)] = rest_phi - fix24_to_rest(rest_s, p.klog2[0]);
+        (void)bad;
         // flow lattice
         for (int i = 0; i < L2.Q; ++i) {
             double cu = 0.0, diag = 0.0, off = 0.0;
@@ -225,7 +226,6 @@ __global__ void k_init_f(DomainDev Dm, const double *phi, const double *u, const
             const long long id = cell_of(Dm, xx, yy, zz);
             if constexpr (P::MIX) {
                 ST q = Conv<P>::st((float)fe, (float)p.scale[1]);
-                if constexpr (P::id == 3) q = bf16_flush(q, p.klog2[1]);
                 f[(L1.Q + i) * plane + id] = q;
             } else {
                 f[(L1.Q + i) * plane + id] = (ST)fe;
