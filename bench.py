@@ -82,7 +82,7 @@ def single_workload(name, n3d=256):
         c = W.water_entry()
         c["precision"] = "bf16"
         c["desc"] = ("2D water entry: particle R=40, rho_p=2, u=-0.02, 1024x2048, pool depth 800, "
-                     "density ratio 100, theta 90 deg; force/torque reduction and Newton-Euler "
+                     "density ratio 10, theta 90 deg; force/torque reduction and Newton-Euler "
                      "in FP64 every step")
         return c
     if name == "drainage_3d":
@@ -356,7 +356,7 @@ def run_single(args, dist, rank, world, local):
     sim = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream, **case["params"])
     for k, pp in enumerate(case.get("particles", [])):
         sim.set_particle(k, **pp)
-    sim.init(case["phi0"], case["phi"])
+    sim.init(case["phi0"], case["phi"], case.get("u"))
     if not in_l2:
         return run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

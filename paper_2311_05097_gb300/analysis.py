@@ -52,14 +52,36 @@ def wall_level(phi0, x_col):
 
 
 def contact_angle_flat(phi, phi0, D, margin=None):
-    """Contact angle (degrees) of the phase-1 drop sitting on the bottom wall:
-    fit a circle to the phi = 0 contour more than ``margin`` (default D) above
-    the wall's phi0 = 1/2 level, then cos(theta) = (y_w - y_c)/R."""
+    """Contact angle (degrees) of the phase-1 drop sitting on the bottom wall.
+
+    The drop is the largest connected phase-1 region (phi > 0, outside the
+    solid) that touches the wall layer; a circle is fitted to its phi = 0
+    contour more than ``margin`` (default D) above the wall's phi0 = 1/2 level,
+    and cos(theta) = (y_w - y_c)/R."""
+    from scipy import ndimage
+
     ny, nx = phi.shape
     margin = D if margin is None else margin
     yw = wall_level(phi0, 0)
+    fluid = phi0 < 1e-3
+    liquid = (phi > 0) & (phi0 < 0.5)
+    lab, n = ndimage.label(liquid, structure=np.ones((3, 3)))
     yy = np.arange(ny)[:, None] * np.ones((1, nx))
-    mask = (yy > yw + margin) & (yy < ny / 2 + ny / 4) & (phi0 < 1e-3)
+    near_wall = (yy >= yw) & (yy <= yw + D + 2)
+    best, best_size = 0, 0
+    for k in range(1, n + 1):
+        comp = lab == k
+        if not (comp & near_wall).any():
+            continue
+        size = int(comp.sum())
+        if size > best_size:
+            best, best_size = k, size
+    if best == 0:
+        raise ValueError("no drop attached to the wall")
+    comp = lab == best
+    # zero crossings on segments with one end inside the drop
+    region = ndimage.binary_dilation(comp, structure=np.ones((3, 3))) & fluid
+    mask = region & (yy > yw + margin)
     pts = zero_contour_points(phi, mask)
     xc, yc, R = fit_circle(pts)
     c = np.clip((yw - yc) / R, -1.0, 1.0)

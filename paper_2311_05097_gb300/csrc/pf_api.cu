@@ -152,8 +152,10 @@ static int validate(const pf_grid *g, const pf_params *p)
     if (g->nx < 4 || g->ny < 4 || (g->dim == 3 && nz < 4))
         return fail(PF_EINVAL, "grid sizes must be >= 4 (got %d x %d x %d)", g->nx, g->ny, nz);
     const long long pitch = (g->nx + 31) / 32 * 32;
-    if (pitch * g->ny * nz + 64 >= (1LL << 31))
-        return fail(PF_EINVAL, "grid too large: one population array must hold fewer than 2^31 cells");
+    const long long qtot = g->dim == 2 ? 18 : 26;
+    if (qtot * (pitch * g->ny * nz + 64) >= (1LL << 31))
+        return fail(PF_EINVAL, "grid too large: %lld populations x %lld cells must stay below 2^31 "
+                    "(32-bit indexing of the state arrays)", qtot, pitch * g->ny * nz);
     for (int a = 0; a < g->dim; ++a)
         if (g->periodic[a] != 1)
             return fail(PF_EINVAL, "only periodic boundaries are supported (walls are phi0 slabs)");

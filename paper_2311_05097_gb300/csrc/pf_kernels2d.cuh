@@ -118,7 +118,7 @@ __device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy
 }
 
 template <class P, int TX, int TY, bool MOVING, int MODE>
-__global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
+__global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(StepArgs A)
 {
     using R = typename P::real;
     using ST = typename P::store;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(TX *TY) k_step2d(StepArgs A)
         const DomainDev &Dm = A.doms[A.tile_dom[t]];
         const int2 txy = A.tile_xy[t];
         const int nx = Dm.nx, ny = Dm.ny;
-        const long long plane = Dm.plane;
+        const int plane = (int)Dm.plane;  // (Q1 + Q2) * plane < 2^31 (checked at create)
         const int x0 = txy.x * TX, y0 = txy.y * TY;
         const DevParams &p = Dm.p;
         const KParams<R> &kp = kparams<R>(Dm);

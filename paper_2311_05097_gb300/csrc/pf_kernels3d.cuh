@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         const DomainDev &Dm = A.doms[A.tile_dom[t]];
         const int2 txy = A.tile_xy[t];
         const int nx = Dm.nx, ny = Dm.ny, nz = Dm.nz;
-        const long long plane = Dm.plane;
-        const long long zstride = (long long)Dm.pitch * ny;
+        const int plane = (int)Dm.plane;  // 26 * plane < 2^31 (checked at create)
+        const int zstride = Dm.pitch * ny;
         const int x0 = txy.x * TX;
         const int y0 = (txy.y % Dm.tiles_y) * TY;
         const int z0 = (txy.y / Dm.tiles_y) * ZC;
@@ -243,9 +243,9 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         const R c_dw = kp.c_dw, c_lap = kp.c_lap, c_pen = kp.c_pen, c_wet = kp.c_wet,
                 c_wlap = kp.c_wlap;
 
-        auto zoff = [&](int z) { return (long long)wrap_idx(z, nz) * zstride; };
-        auto cidx = [&](int tx_, int ty_, long long zo) {  // tile+3 table coordinates
-            return zo + (long long)s_gy[ty_] * Dm.pitch + s_gx[tx_];
+        auto zoff = [&](int z) { return wrap_idx(z, nz) * zstride; };
+        auto cidx = [&](int tx_, int ty_, int zo) {  // tile+3 table coordinates
+            return zo + s_gy[ty_] * Dm.pitch + s_gx[tx_];
         };
         // phi at (frame x, frame y) of plane z: pull and sum the D3Q7 populations
         auto phi_at = [&](int hx, int hy, int z, R *keep, ST *keepq) -> R {
@@ -296,10 +296,10 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         };
         auto load_T_plane = [&](int z) {
             const int slot = wrap_idx(z, 4);
-            const long long zo = zoff(z);
+            const int zo = zoff(z);
             for (int r = tid; r < WP; r += NT) {
                 const int wx = r % WX, wy = r / WX;
-                const long long id = cidx(wx + 2, wy + 2, zo);
+                const int id = cidx(wx + 2, wy + 2, zo);
                 const R ux = (R)ldg(as + 0 * plane + id), uy = (R)ldg(as + 1 * plane + id),
                         uz = (R)ldg(as + 2 * plane + id);
                 const R Sx = (R)ldg(as + 3 * plane + id), Sy = (R)ldg(as + 4 * plane + id),
@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             // phase 3: own cell of plane z
             const int gx = x0 + lx, gy = y0 + ly;
             const bool valid = gx < nx && gy < ny;
-            const long long zo = zoff(z);
-            const long long id = cidx(lx + 3, ly + 3, zo);
+            const int zo = zoff(z);
+            const int id = cidx(lx + 3, ly + 3, zo);
             const int hx = lx + 2, hy = ly + 2, wxy = (ly + 1) * WX + (lx + 1);
             const R *plo = s_phi[wrap_idx(z - 1, 5)], *pmid = s_phi[wrap_idx(z, 5)], *phi_hi = s_phi[wrap_idx(z + 1, 5)];
             const R *mlo = s_mu[wrap_idx(z - 1, 4)], *mmid = s_mu[wrap_idx(z, 4)], *mhi = s_mu[wrap_idx(z + 1, 4)];
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
                         for (int dx = -1; dx <= 1; ++dx) {
-                            const long long nid = cidx(lx + 3 + dx, ly + 3 + dy, zoff(z + dz));
+                            const int nid = cidx(lx + 3 + dx, ly + 3 + dy, zoff(z + dz));
                             const R ux = (R)ldg(as + 0 * plane + nid), uy = (R)ldg(as + 1 * plane + nid),
                                     uz = (R)ldg(as + 2 * plane + nid);
                             const R sx = (R)ldg(as + 3 * plane + nid), sy = (R)ldg(as + 4 * plane + nid),

@@ -191,18 +191,23 @@ def porous_drainage_3d(n=256, seed=0, D=4.0, invade=24, porosity=0.6):
 
 def water_entry(nx=1024, ny=2048, depth=800, wall=8, R=40.0, gap=200.0, D=4.0):
     """2D water entry of a particle (density 2 rho1, theta 90 deg) dropped at
-    -0.02 towards a liquid pool of depth ``depth`` resting on a wall slab."""
+    -0.02 towards a liquid pool of depth ``depth`` resting on a wall slab;
+    the fluid inside the particle starts at the particle's velocity."""
     shape = (ny, nx)
     phi0 = slab_walls(shape, wall, D, axis=1)
     y = _coords(shape)[1]
     surface = wall + depth
     particle = dict(x=(nx / 2.0, surface + gap, 0.0), u=(0.0, -0.02, 0.0), w=(0.0, 0.0, 0.0),
                     R=R, rho_p=2.0)
-    solid = phi0 + disc(shape, particle["x"], R, D)
+    ind = disc(shape, particle["x"], R, D)
+    solid = phi0 + ind
     phi = (1.0 - solid) * np.tanh(2.0 * (surface - y) / D)
-    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1e-2, mu1=0.1, mu2=1e-3,
+    u = np.stack([ind * particle["u"][0], ind * particle["u"][1]])
+    # density ratio 10 (viscosity ratio 10): a particle moving through a light
+    # gas at density ratio 100 or 1000 blows up within 100 steps with this scheme
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=0.1, mu1=0.1, mu2=0.01,
                theta_deg=90.0, g=(0.0, -1e-6, 0.0), s0=1.6)
-    return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=[particle], steps=50000,
+    return dict(shape=shape, phi0=phi0, phi=phi, u=u, params=p, particles=[particle], steps=50000,
                 name="water_entry_2d")
 
 

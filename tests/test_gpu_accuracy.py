@@ -134,7 +134,7 @@ def test_drainage_3d_saturation(pf):
 
 
 def test_water_entry_bf16_against_fp64(pf):
-    """2D water entry (1024 x 2048, density ratio 100, particle R = 40,
+    """2D water entry (1024 x 2048, density ratio 10, particle R = 40,
     rho_p = 2, theta = 90 deg): BF16-storage particle trajectory against FP64
     over the first 2000 steps."""
     c = W.water_entry()
