@@ -119,7 +119,7 @@ def test_batch_contact_angles(pf):
 
 def test_drainage_3d_saturation(pf):
     """3D drainage through random spheres (D3Q19 + D3Q7, theta = 120 deg,
-    body force 1e-6, density ratio 10): FP16-storage saturation within 1e-3 of
+    body force 1e-6, equal densities): FP16-storage saturation within 1e-3 of
     FP64 (128^3 box, 1000 steps)."""
     c = W.porous_drainage_3d(n=128)
     steps = 1000
