@@ -186,12 +186,17 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(Ste
         const R isc1 = kp.inv_scale[0], isc2 = kp.inv_scale[1];
 
         // phi at frame cell (hx, hy) of the tile+2 frame: pull and sum (Eq. 31)
+        long long rest_own = 0;
         auto phi_at = [&](int hx, int hy, R *keep, ST *keepq) -> R {
             const int cx = hx + 1, cy = hy + 1;  // tile+3 table coordinates
             R acc;
             if constexpr (P::MIX) {
-                acc = float_of_fixed(rs[s_gy[cy] + s_gx[cx]]);
-                if (keep) keep[0] = acc;
+                const long long rv = rs[s_gy[cy] + s_gx[cx]];
+                acc = float_of_fixed(rv);
+                if (keep) {
+                    keep[0] = acc;
+                    rest_own = rv;
+                }
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     ST q = ldg(fs + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]]);
@@ -263,11 +268,24 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(Ste
             s_p0[hy][hx] = phi0_at(hx, hy);
         }
         if constexpr (MODE == MODE_STEP) {
-            for (int r = tid; r < WX * WY; r += NT) {
-                const int wx = r % WX, wy = r / WX;
-                const int id = s_gy[wy + 2] + s_gx[wx + 2];
-                const R ux = (R)ldg(as + 0 * plane + id), uy = (R)ldg(as + 1 * plane + id);
-                const R Sx = (R)ldg(as + 2 * plane + id), Sy = (R)ldg(as + 3 * plane + id);
+            // w of the own cell from the lagged fields already in registers; the
+            // tile+1 ring by the last threads (the first ones did the phi ring)
+            s_w[ly + 1][lx + 1] = (R)lag[2] * (R)lag[1] - (R)lag[0] * (R)lag[3];
+            constexpr int WRING = 2 * WX + 2 * TY;
+            static_assert(WRING <= NT, "one tile+1 ring cell per thread at most");
+            for (int r = NT - 1 - tid; r >= 0 && r < WRING; r -= NT) {
+                int wx, wy;
+                if (r < 2 * WX) {
+                    wy = r < WX ? 0 : TY + 1;
+                    wx = r < WX ? r : r - WX;
+                } else {
+                    const int rr = r - 2 * WX;
+                    wy = 1 + (rr >> 1);
+                    wx = (rr & 1) ? TX + 1 : 0;
+                }
+                const int wid = s_gy[wy + 2] + s_gx[wx + 2];
+                const R ux = (R)ldg(as + 0 * plane + wid), uy = (R)ldg(as + 1 * plane + wid);
+                const R Sx = (R)ldg(as + 2 * plane + wid), Sy = (R)ldg(as + 3 * plane + wid);
                 s_w[wy][wx] = Sx * uy - ux * Sy;
             }
         }
@@ -408,7 +426,7 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(Ste
                     int bad = 0, sold = 0;
 #pragma unroll
                     for (int i = 1; i < 9; ++i) sold += fix24<ST>(q1[i], &bad);
-                    const long long acc = rs[id] + fix24_to_rest(sold, p.klog2[0]);
+                    const long long acc = rest_own + fix24_to_rest(sold, p.klog2[0]);
                     phv = double_of_fixed(acc);
                 }
                 Dm.macro[0 * N + o] = phv;
@@ -491,7 +509,7 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(Ste
                         fd[i * plane + id] = q;
                     }
                     // exact: sum of the cell's order-parameter populations is unchanged
-                    rd[id] = rs[id] + fix24_to_rest(sold - snew, k1);
+                    rd[id] = rest_own + fix24_to_rest(sold - snew, k1);
                     if (bad) atomicOr(A.flags, 1);
                 } else {
 #pragma unroll
