@@ -96,7 +96,7 @@ def single_workload(name, n3d=256):
         c = W.drop_on_cylinder()
         c["precision"] = "p32"
         c["desc"] = ("2D drop (R0=50) on a fixed cylinder (Rp=60) between wall slabs, 512x512, "
-                     "density ratio 1000, viscosity ratio 100, theta 60 deg")
+                     "density ratio 100, viscosity ratio 100, theta 60 deg")
     else:
         c = W.static_drop()
         c["precision"] = "p64"

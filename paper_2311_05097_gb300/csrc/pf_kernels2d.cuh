@@ -117,8 +117,17 @@ __device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy
     return R(0.5) * (R(1) + tanh(R(2) * ((R)pp.R - r) / (R)D));
 }
 
+// Resident CTAs per SM requested from the register allocator: FP64 keeps its
+// registers (no cap); the 32 x 8 FP32/16-bit kernels trade a few spills for a
+// fourth CTA, 64 x 4 keeps three; the autotuner picks among the shapes.
+template <class P, int TX, int TY>
+constexpr int step2d_min_blocks()
+{
+    return P::id == 0 ? 1 : (TX * TY > 256 ? 1 : ((TX == 32 && TY == 8) ? 4 : 3));
+}
+
 template <class P, int TX, int TY, bool MOVING, int MODE>
-__global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(StepArgs A)
+__global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_step2d(StepArgs A)
 {
     using R = typename P::real;
     using ST = typename P::store;
@@ -197,14 +206,16 @@ __global__ void __launch_bounds__(TX *TY, (TX * TY <= 256 ? 3 : 1)) k_step2d(Ste
                     keep[0] = acc;
                     rest_own = rv;
                 }
+                R movers = R(0);  // sum in stored units, scaled once
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     ST q = ldg(fs + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]]);
-                    R v = Conv<P>::ld(q, isc1);
-                    if (keep) keep[i] = v;
+                    const R v = stored_to_float<ST>(q);
+                    if (keep) keep[i] = v * isc1;
                     if (keepq) keepq[i] = q;
-                    acc += v;
+                    movers += v;
                 }
+                acc += movers * isc1;
             } else {
                 acc = R(0);
 #pragma unroll
