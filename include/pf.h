@@ -48,7 +48,8 @@ extern "C" {
 #define PF_EINVAL (-1)   /* invalid argument or parameter */
 #define PF_ENOMEM (-2)   /* device or host allocation failed */
 #define PF_ECUDA (-3)    /* a CUDA runtime call failed */
-#define PF_ENUMERIC (-4) /* a non-finite value appeared in phi or u */
+#define PF_ENUMERIC (-4) /* a non-finite phi or u appeared, or a 16-bit order-parameter
+                            population was saturated (see pf_diag.nan_flag) */
 #define PF_ETIMEOUT (-5) /* a bounded device wait gave up */
 #define PF_ESTATE (-6)   /* call out of order (e.g. step before init) */
 
@@ -108,8 +109,12 @@ typedef struct pf_particle {
 } pf_particle;
 
 /* FP64 diagnostics at the current time: mass = sum phi, E_F of Eq. (8),
- * E_K = sum rho |u|^2 / 2, E_total = E_F + E_K (Sec. 2.3), nan_flag != 0 if
- * any step produced a non-finite phi or u. */
+ * E_K = sum rho |u|^2 / 2, E_total = E_F + E_K (Sec. 2.3).  nan_flag is 0 when
+ * every step stayed in range; bit 0 (value 1) is set if a step produced a
+ * non-finite phi or u, bit 1 (value 2) if a 16-bit order-parameter population
+ * reached the storage range (|value| * 2^store_log2_scale[0] >= 8) and was
+ * saturated there: the order parameter stays exactly conserved, but the
+ * populations no longer follow Eq. (21) at that cell. */
 typedef struct pf_diag {
     double mass, E_F, E_K, E_total;
     int nan_flag;
@@ -155,7 +160,8 @@ int pf_num_particles(pf_handle *h);
 /* Deterministic FP64 diagnostics (fixed-order reductions).  Synchronous. */
 int pf_diagnostics(pf_handle *h, pf_diag *out);
 
-/* Wait for the handle's stream; PF_ENUMERIC if a non-finite value appeared. */
+/* Wait for the handle's stream; PF_ENUMERIC if a non-finite value appeared or a
+ * 16-bit population was saturated (pf_diag.nan_flag tells which). */
 int pf_sync(pf_handle *h);
 
 /* Number of time steps taken since pf_init_fields. */

@@ -252,8 +252,8 @@ static DevParams derive(int dim, const pf_params *p)
     const double musc = std::max(3.0 * p->sigma / p->D, 1e-6);
     // order parameter: the exact rest-population bookkeeping needs every stored
     // mover below 8 (stored = value * 2^k1); bound the movers by
-    // w_1 (|u|/cs^2 + eta * 2 mu_max) with |u| <= 0.25 and mu_max = 3 sigma/D
-    const double m1max = w1 * (0.25 / d.cs2 + d.eta * 2.0 * musc);
+    // w_1 (|u|/cs^2 + eta * 2 mu_max) with |u| <= 1 and mu_max = 3 sigma/D
+    const double m1max = w1 * (1.0 / d.cs2 + d.eta * 2.0 * musc);
     int k1 = p->store_log2_scale[0] ? p->store_log2_scale[0]
                                     : (int)std::floor(std::log2(8.0 / m1max));
     k1 = std::max(0, std::min(24, k1));
@@ -282,9 +282,6 @@ static size_t aux_bytes(int prec) { return prec == PF_P64 ? 8 : 4; }
 struct DomainMem {
     DomainDev d{};
     void *base = nullptr;  // single allocation for populations, rest, aux, phi0
-    double *macro = nullptr;
-    double *staging = nullptr;  // init inputs (phi0, phi, u, P) and temporaries
-    size_t staging_n = 0;
 };
 
 static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
@@ -326,52 +323,55 @@ static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams
     return PF_OK;
 }
 
-static int domain_macro(DomainMem &m, int dim)
-{
-    if (m.macro) return PF_OK;
-    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
-    CK(cudaMalloc(&m.macro, sizeof(double) * (size_t)(5 + dim) * N));
-    m.d.macro = m.macro;
-    return PF_OK;
-}
+// device staging area for init inputs (phi0, phi, u, P) and temporaries of
+// one domain; shared by the domains of a batch (their inits are stream-ordered)
+struct Staging {
+    double *p = nullptr;
+    size_t n = 0;
+};
 
-static int domain_staging(DomainMem &m, int dim)
+static int staging_reserve(Staging &st, const DomainMem &m, int dim)
 {
     const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
     const size_t need = (size_t)(2 + dim + 1 + 2) * N;  // phi0, phi, u, P, phi0tot, mu
-    if (m.staging_n >= need) return PF_OK;
-    if (m.staging) cudaFree(m.staging);
-    m.staging = nullptr;
-    CK(cudaMalloc(&m.staging, sizeof(double) * need));
-    m.staging_n = need;
+    if (st.n >= need) return PF_OK;
+    if (st.p) cudaFree(st.p);
+    st.p = nullptr;
+    st.n = 0;
+    CK(cudaMalloc(&st.p, sizeof(double) * need));
+    st.n = need;
     return PF_OK;
+}
+
+static void staging_release(Staging &st)
+{
+    if (st.p) cudaFree(st.p);
+    st = Staging{};
 }
 
 static void domain_free(DomainMem &m)
 {
     if (m.base) cudaFree(m.base);
-    if (m.macro) cudaFree(m.macro);
-    if (m.staging) cudaFree(m.staging);
     m = DomainMem{};
 }
 
 // copy caller arrays into the staging area and run the init kernels
-static int domain_init(DomainMem &m, int dim, int prec, const double *phi0, const double *phi,
+static int domain_init(DomainMem &m, Staging &st, int dim, int prec, const double *phi0, const double *phi,
                        const double *u, const double *P, int where, const ParticleDev *d_parts,
-                       int np, cudaStream_t s)
+                       int np, int *flags, cudaStream_t s)
 {
     if (!phi0 || !phi) return fail(PF_EINVAL, "phi0 and phi are required");
     if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
-    int rc = domain_staging(m, dim);
+    int rc = staging_reserve(st, m, dim);
     if (rc) return rc;
     const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
-    double *sp0 = m.staging, *sphi = sp0 + N, *su = sphi + N, *sP = su + dim * N, *tmp = sP + N;
+    double *sp0 = st.p, *sphi = sp0 + N, *su = sphi + N, *sP = su + dim * N, *tmp = sP + N;
     const cudaMemcpyKind kind = where == PF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     CK(cudaMemcpyAsync(sp0, phi0, sizeof(double) * N, kind, s));
     CK(cudaMemcpyAsync(sphi, phi, sizeof(double) * N, kind, s));
     if (u) CK(cudaMemcpyAsync(su, u, sizeof(double) * dim * N, kind, s));
     if (P) CK(cudaMemcpyAsync(sP, P, sizeof(double) * N, kind, s));
-    launch_init(prec, m.d, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, np, s);
+    launch_init(prec, m.d, flags, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, np, s);
     CK(cudaGetLastError());
     return PF_OK;
 }
@@ -416,6 +416,14 @@ struct Engine {
     int par = 0;
     int64_t t = 0;
     std::vector<bool> inited;
+    Staging staging;
+    // macroscopic pass: one output buffer (largest domain) and per-domain tile
+    // tables of the macro kernel, built on first use
+    double *d_macro = nullptr;
+    DomainDev *d_mdoms = nullptr;
+    int *d_mtdom = nullptr;
+    int2 *d_mtxy = nullptr;
+    std::vector<int> mbase, mcount;
     int *d_flags = nullptr;
     double *d_diag = nullptr;  // partials + out
     // particles (single-domain handles)
@@ -463,6 +471,11 @@ static void engine_free(Engine &E)
 {
     if (E.gexec) cudaGraphExecDestroy(E.gexec);
     for (auto &m : E.mem) domain_free(m);
+    staging_release(E.staging);
+    if (E.d_macro) cudaFree(E.d_macro);
+    if (E.d_mdoms) cudaFree(E.d_mdoms);
+    if (E.d_mtdom) cudaFree(E.d_mtdom);
+    if (E.d_mtxy) cudaFree(E.d_mtxy);
     if (E.d_doms) cudaFree(E.d_doms);
     if (E.d_tdom) cudaFree(E.d_tdom);
     if (E.d_txy) cudaFree(E.d_txy);
@@ -723,54 +736,70 @@ static int engine_sync(Engine &E)
     }
     int flag = 0;
     CK(cudaMemcpy(&flag, E.d_flags, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return fail(PF_ENUMERIC, "a non-finite phi or u appeared");
+    if (flag & 1) return fail(PF_ENUMERIC, "a non-finite phi or u appeared");
+    if (flag & 2)
+        return fail(PF_ENUMERIC, "a 16-bit order-parameter population reached the storage range and was "
+                                 "saturated (raise the flow lattice's resolution or lower store_log2_scale[0])");
     return PF_OK;
 }
 
-// macroscopic pass of domain i into its macro buffer
-static int engine_macros(Engine &E, int i)
+// tile tables and output buffer of the macroscopic pass, built once
+static int engine_macro_tables(Engine &E)
 {
-    int rc = domain_macro(E.mem[i], E.dim);
-    if (rc) return rc;
-    // a one-domain tile table for the macro kernel (32 x 8 tiles)
-    std::vector<DomainMem *> ds{&E.mem[i]};
-    std::vector<int> tdom;
-    std::vector<int2> txy;
-    DomainDev saved = E.mem[i].d;
+    if (E.d_mdoms) return PF_OK;
+    const int nd = (int)E.mem.size();
+    long long nmax = 0;
+    for (auto &m : E.mem) nmax = std::max(nmax, (long long)m.d.nx * m.d.ny * m.d.nz);
+    CK(cudaMalloc(&E.d_macro, sizeof(double) * (size_t)(5 + E.dim) * nmax));
     int mtx = 32, mty = 8;
     if (E.dim == 3) tile_shape3d(E.prec, &mtx, &mty);
+    // build_tiles writes the tiling into the DomainDev it is given: tile copies
+    std::vector<DomainMem> copies(E.mem.begin(), E.mem.end());
+    std::vector<DomainMem *> ds;
+    for (auto &c : copies) ds.push_back(&c);
+    std::vector<int> tdom;
+    std::vector<int2> txy;
     build_tiles(ds, mtx, mty, tdom, txy);
-    DomainDev dd = E.mem[i].d;
-    E.mem[i].d = saved;
-    E.mem[i].d.macro = E.mem[i].macro;
-    dd.macro = E.mem[i].macro;
-    DomainDev *d_dd = nullptr;
-    int *d_td = nullptr;
-    int2 *d_xy = nullptr;
-    CK(cudaMalloc(&d_dd, sizeof(DomainDev)));
-    CK(cudaMalloc(&d_td, sizeof(int) * tdom.size()));
-    CK(cudaMalloc(&d_xy, sizeof(int2) * txy.size()));
-    CK(cudaMemcpyAsync(d_dd, &dd, sizeof(DomainDev), cudaMemcpyHostToDevice, E.stream));
-    CK(cudaMemcpyAsync(d_td, tdom.data(), sizeof(int) * tdom.size(), cudaMemcpyHostToDevice, E.stream));
-    CK(cudaMemcpyAsync(d_xy, txy.data(), sizeof(int2) * txy.size(), cudaMemcpyHostToDevice, E.stream));
+    std::vector<DomainDev> dd(nd);
+    E.mbase.assign(nd, 0);
+    E.mcount.assign(nd, 0);
+    for (int k = 0; k < nd; ++k) {
+        dd[k] = copies[k].d;
+        dd[k].macro = E.d_macro;
+        E.mbase[k] = dd[k].tile_base;
+        E.mcount[k] = dd[k].tiles_x * dd[k].tiles_y * dd[k].tiles_z;
+    }
+    CK(cudaMalloc(&E.d_mdoms, sizeof(DomainDev) * nd));
+    CK(cudaMalloc(&E.d_mtdom, sizeof(int) * tdom.size()));
+    CK(cudaMalloc(&E.d_mtxy, sizeof(int2) * txy.size()));
+    CK(cudaMemcpy(E.d_mdoms, dd.data(), sizeof(DomainDev) * nd, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.d_mtdom, tdom.data(), sizeof(int) * tdom.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(E.d_mtxy, txy.data(), sizeof(int2) * txy.size(), cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+// macroscopic pass of domain i into the engine's macro buffer (E.d_macro,
+// valid until the next macroscopic pass)
+static int engine_macros(Engine &E, int i)
+{
+    int rc = engine_macro_tables(E);
+    if (rc) return rc;
+    int mtx = 32, mty = 8;
+    if (E.dim == 3) tile_shape3d(E.prec, &mtx, &mty);
     StepArgs a{};
-    a.doms = d_dd;
-    a.tile_dom = d_td;
-    a.tile_xy = d_xy;
-    a.ntiles = (int)tdom.size();
+    a.doms = E.d_mdoms;
+    a.tile_dom = E.d_mtdom + E.mbase[i];
+    a.tile_xy = E.d_mtxy + E.mbase[i];
+    a.ntiles = E.mcount[i];
     a.par = E.par;
     a.parts = E.d_parts;
     a.np = E.np;
     a.partials = nullptr;
     a.flags = E.d_flags;
-    const int grid = std::min<int>((int)tdom.size(), E.nsm * 4);
+    const int grid = std::min<int>(E.mcount[i], E.nsm * 4);
     if (!launch_any(E, mtx, mty, MODE_MACROS, grid, a))
         return fail(PF_EINVAL, "macro kernel not built");
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(E.stream));
-    cudaFree(d_dd);
-    cudaFree(d_td);
-    cudaFree(d_xy);
     return PF_OK;
 }
 
@@ -787,11 +816,14 @@ static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double 
     const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
     const cudaMemcpyKind kind = where == PF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     const int d = E.dim;
-    if (phi) CK(cudaMemcpy(phi, m.macro, sizeof(double) * N, kind));
-    if (rho) CK(cudaMemcpy(rho, m.macro + N, sizeof(double) * N, kind));
-    if (u) CK(cudaMemcpy(u, m.macro + 2 * N, sizeof(double) * d * N, kind));
-    if (P) CK(cudaMemcpy(P, m.macro + (2 + d) * N, sizeof(double) * N, kind));
-    if (mu) CK(cudaMemcpy(mu, m.macro + (3 + d) * N, sizeof(double) * N, kind));
+    const double *mac = E.d_macro;
+    // stream-ordered copies after the macroscopic pass, then one wait
+    if (phi) CK(cudaMemcpyAsync(phi, mac, sizeof(double) * N, kind, E.stream));
+    if (rho) CK(cudaMemcpyAsync(rho, mac + N, sizeof(double) * N, kind, E.stream));
+    if (u) CK(cudaMemcpyAsync(u, mac + 2 * N, sizeof(double) * d * N, kind, E.stream));
+    if (P) CK(cudaMemcpyAsync(P, mac + (2 + d) * N, sizeof(double) * N, kind, E.stream));
+    if (mu) CK(cudaMemcpyAsync(mu, mac + (3 + d) * N, sizeof(double) * N, kind, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
     return PF_OK;
 }
 
@@ -800,12 +832,13 @@ static int engine_diag(Engine &E, int i, pf_diag *out)
     if (!out) return fail(PF_EINVAL, "out is NULL");
     if (!E.inited[i]) return fail(PF_ESTATE, "pf_diagnostics before pf_init_fields");
     int rc = engine_sync(E);
-    const int nan_flag = rc == PF_ENUMERIC ? 1 : 0;
+    int nan_flag = 0;
+    if (rc == PF_ENUMERIC) CK(cudaMemcpy(&nan_flag, E.d_flags, sizeof(int), cudaMemcpyDeviceToHost));
     if (rc && rc != PF_ENUMERIC) return rc;
     rc = engine_macros(E, i);
     if (rc) return rc;
     DomainDev dd = E.mem[i].d;
-    dd.macro = E.mem[i].macro;
+    dd.macro = E.d_macro;
     double *partial = E.d_diag, *res = E.d_diag + 3 * diag_blocks();
     launch_diag(dd, partial, res, E.stream);
     CK(cudaGetLastError());
@@ -875,10 +908,12 @@ extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *ph
         }
     rc = upload_particles(E);
     if (rc) return rc;
-    rc = domain_init(E.mem[0], E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, E.np, E.stream);
-    if (rc) return rc;
     CK(cudaMemsetAsync(E.d_flags, 0, sizeof(int) * 4, E.stream));
+    rc = domain_init(E.mem[0], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, E.np, E.d_flags,
+                     E.stream);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(E.stream));
+    staging_release(E.staging);
     E.par = 0;
     E.t = 0;
     E.inited[0] = true;
@@ -1002,13 +1037,10 @@ extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const doubl
     if (i < 0 || i >= (int)E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
     if (E.sticky) return E.sticky;
     if (E.t != 0) return fail(PF_ESTATE, "all domains are initialised before the first step");
-    int rc = domain_init(E.mem[i], E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, 0, E.stream);
+    int rc = domain_init(E.mem[i], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, 0, E.d_flags,
+                         E.stream);
     if (rc) return rc;
     CK(cudaStreamSynchronize(E.stream));
-    // the staging area is only needed during init
-    cudaFree(E.mem[i].staging);
-    E.mem[i].staging = nullptr;
-    E.mem[i].staging_n = 0;
     E.inited[i] = true;
     return PF_OK;
 }
@@ -1030,27 +1062,14 @@ extern "C" int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho,
 {
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (i < 0 || i >= (int)b->E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
-    int rc = engine_get_macros(b->E, i, phi, rho, u, P, mu, where);
-    // macro buffers of a large batch are released after use
-    if (b->E.mem[i].macro) {
-        cudaFree(b->E.mem[i].macro);
-        b->E.mem[i].macro = nullptr;
-        b->E.mem[i].d.macro = nullptr;
-    }
-    return rc;
+    return engine_get_macros(b->E, i, phi, rho, u, P, mu, where);
 }
 
 extern "C" int pf_batch_diagnostics(pf_batch *b, int i, pf_diag *out)
 {
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (i < 0 || i >= (int)b->E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
-    int rc = engine_diag(b->E, i, out);
-    if (b->E.mem[i].macro) {
-        cudaFree(b->E.mem[i].macro);
-        b->E.mem[i].macro = nullptr;
-        b->E.mem[i].d.macro = nullptr;
-    }
-    return rc;
+    return engine_diag(b->E, i, out);
 }
 
 extern "C" int64_t pf_batch_cells(pf_batch *b)

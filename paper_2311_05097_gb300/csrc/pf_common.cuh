@@ -261,6 +261,40 @@ __device__ __forceinline__ int fix24(S q, int *bad)
     return fix24_of_float(stored_to_float<S>(q), bad);
 }
 
+// Image of a value that went through fix24_sat when it was stored.
+template <class S>
+__device__ __forceinline__ int fix24_stored(S q)
+{
+    return __float2int_rn(stored_to_float<S>(q) * 16777216.0f);
+}
+
+// Largest stored magnitude below FIX24_LIMIT.
+template <class S>
+__device__ __forceinline__ S fix24_max_stored();
+template <>
+__device__ __forceinline__ __half fix24_max_stored<__half>() { return __float2half_rz(7.99f); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 fix24_max_stored<__nv_bfloat16>()
+{
+    return __float2bfloat16_rz(7.99f);
+}
+
+// Image of a value about to be stored; a value out of the image's range is
+// saturated in place (so the stored value and its image still agree, and the
+// cell's bookkeeping stays exact) and *sat is set.
+template <class S>
+__device__ __forceinline__ int fix24_sat(S &q, int *sat)
+{
+    float v = stored_to_float<S>(q);
+    if (!(fabsf(v) < FIX24_LIMIT)) {
+        *sat = 1;
+        q = fix24_max_stored<S>();
+        if (v < 0.0f) q = -q;
+        v = stored_to_float<S>(q);
+    }
+    return __float2int_rn(v * 16777216.0f);
+}
+
 // Zero a BF16 whose value is not a multiple of 2^-24 (|v| < 2^-17; BF16
 // carries 8 significant bits).
 __device__ __forceinline__ __nv_bfloat16 bf16_flush(__nv_bfloat16 h)

@@ -40,7 +40,7 @@ bool launch_step3d_p32(int tx, int ty, bool moving, int mode, int grid, cudaStre
 bool launch_step3d_mixh(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
 bool launch_step3d_mixb(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
 
-void launch_init(int prec, const DomainDev &Dm, const double *phi0, const double *phi, const double *u,
+void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, const double *phi, const double *u,
                  const double *Pin, double *tmp, const ParticleDev *parts, int np, cudaStream_t s);
 int diag_blocks();
 void launch_diag(const DomainDev &Dm, double *partial, double *out, cudaStream_t s);

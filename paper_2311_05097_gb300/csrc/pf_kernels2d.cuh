@@ -434,9 +434,9 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const long long o = (long long)gy * nx + gx;
                 double phv = (double)phi;
                 if constexpr (P::MIX) {
-                    int bad = 0, sold = 0;
+                    int sold = 0;
 #pragma unroll
-                    for (int i = 1; i < 9; ++i) sold += fix24<ST>(q1[i], &bad);
+                    for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[i]);
                     const long long acc = rest_own + fix24_to_rest(sold, p.klog2[0]);
                     phv = double_of_fixed(acc);
                 }
@@ -511,17 +511,17 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     const int k1 = p.klog2[0];
                     int bad = 0, sold = 0, snew = 0;
 #pragma unroll
-                    for (int i = 1; i < 9; ++i) sold += fix24<ST>(q1[i], &bad);
+                    for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[i]);
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
                         ST q = Conv<P>::st(f1[i], sc1);
                         if constexpr (P::id == 3) q = bf16_flush(q);
-                        snew += fix24<ST>(q, &bad);
+                        snew += fix24_sat<ST>(q, &bad);
                         fd[i * plane + id] = q;
                     }
                     // exact: sum of the cell's order-parameter populations is unchanged
                     rd[id] = rest_own + fix24_to_rest(sold - snew, k1);
-                    if (bad) atomicOr(A.flags, 1);
+                    if (bad) atomicOr(A.flags, 2);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) fd[i * plane + id] = Conv<P>::st(f1[i], R(1));

@@ -482,9 +482,9 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     const long long o = ((long long)z * ny + gy) * nx + gx;
                     double phv = (double)phi;
                     if constexpr (P::MIX) {
-                        int bad = 0, sold = 0;
+                        int sold = 0;
 #pragma unroll
-                        for (int i = 1; i < 7; ++i) sold += fix24<ST>(q1[i], &bad);
+                        for (int i = 1; i < 7; ++i) sold += fix24_stored<ST>(q1[i]);
                         const long long acc = rs[id] + fix24_to_rest(sold, p.klog2[0]);
                         phv = double_of_fixed(acc);
                     }
@@ -580,17 +580,17 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                         const int k1 = p.klog2[0];
                         int bad = 0, sold = 0, snew = 0;
 #pragma unroll
-                        for (int i = 1; i < 7; ++i) sold += fix24<ST>(q1[i], &bad);
+                        for (int i = 1; i < 7; ++i) sold += fix24_stored<ST>(q1[i]);
 #pragma unroll
                         for (int i = 1; i < 7; ++i) {
                             ST qv = Conv<P>::st(f1[i], sc1);
                             if constexpr (P::id == 3) qv = bf16_flush(qv);
-                            snew += fix24<ST>(qv, &bad);
+                            snew += fix24_sat<ST>(qv, &bad);
                             fd[i * plane + id] = qv;
                         }
                         // exact: sum of the cell's order-parameter populations is unchanged
                         rd[id] = rs[id] + fix24_to_rest(sold - snew, k1);
-                        if (bad) atomicOr(A.flags, 1);
+                        if (bad) atomicOr(A.flags, 2);
                     } else {
 #pragma unroll
                         for (int i = 0; i < 7; ++i) fd[i * plane + id] = Conv<P>::st(f1[i], R(1));

@@ -16,40 +16,6 @@ __device__ const int L19[19][3] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 
                                    {-1, 1, 0},  {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
                                    {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
-struct Lat {
-    int Q;
-    int c[19][3];
-    double w[19];
-};
-
-__device__ void lattice_of(int dim, int which, double d0, Lat &L)
-{
-    if (dim == 2) {
-        L.Q = 9;
-        for (int i = 0; i < 9; ++i) {
-            L.c[i][0] = LX9[i];
-            L.c[i][1] = LY9[i];
-            L.c[i][2] = 0;
-        }
-        L.w[0] = 1.0 - 2.0 * d0 + d0 * d0;
-        for (int i = 1; i <= 4; ++i) L.w[i] = 0.5 * (d0 - d0 * d0);
-        for (int i = 5; i <= 8; ++i) L.w[i] = 0.25 * d0 * d0;
-    } else if (which == 1) {  // D3Q7, order parameter
-        L.Q = 7;
-        for (int i = 0; i < 7; ++i)
-            for (int a = 0; a < 3; ++a) L.c[i][a] = L19[i][a];
-        L.w[0] = 1.0 - 3.0 * d0;
-        for (int i = 1; i < 7; ++i) L.w[i] = 0.5 * d0;
-    } else {  // D3Q19, flow
-        L.Q = 19;
-        for (int i = 0; i < 19; ++i)
-            for (int a = 0; a < 3; ++a) L.c[i][a] = L19[i][a];
-        L.w[0] = 1.0 - 3.0 * d0 + 3.0 * d0 * d0;
-        for (int i = 1; i <= 6; ++i) L.w[i] = 0.5 * (d0 - 2.0 * d0 * d0);
-        for (int i = 7; i < 19; ++i) L.w[i] = 0.25 * d0 * d0;
-    }
-}
-
 __device__ __forceinline__ long long cell_of(const DomainDev &Dm, int x, int y, int z)
 {
     return ((long long)z * Dm.ny + y) * Dm.pitch + x;
@@ -116,6 +82,83 @@ __device__ double particle_indicator_d(const ParticleDev &pp, int x, int y, int 
 }
 
 // ---- initialisation: f = f^eq (Sec. 3.3 step 1) ------------------------------------------------
+//
+// One thread per cell, a grid of (x blocks) x (rows): a row is one (y, z) line
+// of the domain, so cell coordinates need no 64-bit division.  Arithmetic is in
+// the policy's arithmetic type (double for FP64, float otherwise); the
+// fixed-point rest population of the 16-bit policies is formed from the double
+// phi, so the bookkeeping is exact whatever the arithmetic type.
+
+// lattice velocities of the order-parameter (Q1) and flow (Q2) lattices
+template <int DIM>
+struct InitLat;
+template <>
+struct InitLat<2> {
+    static constexpr int Q1 = 9, Q2 = 9;
+    static __device__ __forceinline__ int c1(int i, int a) { return a == 0 ? LX9[i] : (a == 1 ? LY9[i] : 0); }
+    static __device__ __forceinline__ int c2(int i, int a) { return c1(i, a); }
+    template <class R>
+    static __device__ __forceinline__ R w1(int i, R d0)
+    {
+        return i == 0 ? R(1) - R(2) * d0 + d0 * d0 : (i <= 4 ? R(0.5) * (d0 - d0 * d0) : R(0.25) * d0 * d0);
+    }
+    template <class R>
+    static __device__ __forceinline__ R w2(int i, R d0) { return w1<R>(i, d0); }
+};
+template <>
+struct InitLat<3> {
+    static constexpr int Q1 = 7, Q2 = 19;
+    static __device__ __forceinline__ int c1(int i, int a) { return L19[i][a]; }
+    static __device__ __forceinline__ int c2(int i, int a) { return L19[i][a]; }
+    template <class R>
+    static __device__ __forceinline__ R w1(int i, R d0)
+    {
+        return i == 0 ? R(1) - R(3) * d0 : R(0.5) * d0;
+    }
+    template <class R>
+    static __device__ __forceinline__ R w2(int i, R d0)
+    {
+        return i == 0 ? R(1) - R(3) * d0 + R(3) * d0 * d0
+                      : (i <= 6 ? R(0.5) * (d0 - R(2) * d0 * d0) : R(0.25) * d0 * d0);
+    }
+};
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// FD stencil (D2Q9 or D3Q19 with classical weights, cs^2 = 1/3) on a dense
+// x-fastest double array, in arithmetic type R
+template <int DIM, class R>
+__device__ __forceinline__ void fd_grad_lap_r(const DomainDev &Dm, const double *a, int x, int y, int z,
+                                              R g[3], R *lap)
+{
+    constexpr int Q = DIM == 2 ? 9 : 19;
+    const R c0 = (R)a[lin_of(Dm, x, y, z)];
+    R acc = R(0);
+    g[0] = g[1] = g[2] = R(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const int cx = InitLat<DIM>::c2(i, 0), cy = InitLat<DIM>::c2(i, 1), cz = InitLat<DIM>::c2(i, 2);
+        const R w = DIM == 2 ? (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0)) : (i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+        const int xx = wrap1(x + cx, Dm.nx), yy = wrap1(y + cy, Dm.ny), zz = DIM == 2 ? 0 : wrap1(z + cz, Dm.nz);
+        const R v = (R)a[lin_of(Dm, xx, yy, zz)];
+        g[0] += w * R(cx) * v;
+        g[1] += w * R(cy) * v;
+        g[2] += w * R(cz) * v;
+        acc += w * (v - c0);
+    }
+    g[0] *= R(3);
+    g[1] *= R(3);
+    g[2] *= R(3);
+    if (lap) *lap = R(6) * acc;
+}
+
+#define PF_INIT_ROWS_BEGIN                                                                         \
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;                                           \
+    const int rows = Dm.ny * Dm.nz;                                                                \
+    for (int row = blockIdx.y; row < rows; row += gridDim.y) {                                     \
+        const int y = row % Dm.ny, z = row / Dm.ny;                                                \
+        if (x >= Dm.nx) continue;                                                                  \
+        const long long o = (long long)row * Dm.nx + x;
 
 // total indicator (fixed + particles) and the stored fixed indicator
 template <class P>
@@ -123,10 +166,7 @@ __global__ void k_init_phi0(DomainDev Dm, const double *phi0_in, double *phi0tot
                             const ParticleDev *parts, int np)
 {
     using AX = typename P::aux;
-    const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < N;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(o % Dm.nx), y = (int)((o / Dm.nx) % Dm.ny), z = (int)(o / ((long long)Dm.nx * Dm.ny));
+    PF_INIT_ROWS_BEGIN
         double v = phi0_in[o];
         reinterpret_cast<AX *>(Dm.phi0)[cell_of(Dm, x, y, z)] = (AX)v;
         for (int k = 0; k < np; ++k) {
@@ -138,107 +178,111 @@ __global__ void k_init_phi0(DomainDev Dm, const double *phi0_in, double *phi0tot
 }
 
 // chemical potential of Eq. (9) from the initial phi
+template <int DIM, class R>
 __global__ void k_init_mu(DomainDev Dm, const double *phi, const double *phi0tot, double *mu)
 {
     const DevParams &p = Dm.p;
-    const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < N;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(o % Dm.nx), y = (int)((o / Dm.nx) % Dm.ny), z = (int)(o / ((long long)Dm.nx * Dm.ny));
-        double g[3], lp, lp0;
-        fd_grad_lap(Dm, phi, x, y, z, g, &lp);
-        fd_grad_lap(Dm, phi0tot, x, y, z, g, &lp0);
-        const double ph = phi[o], p0 = phi0tot[o];
-        mu[o] = p.c_dw * ph * (ph - 1.0) * (ph + 1.0) - p.c_lap * lp + p.c_pen * p0 * p0 * ph +
-                p.c_wet * p0 * (3.0 * ph * ph + p0 * p0 - 1.0) - p.c_wlap * lp0;
+    PF_INIT_ROWS_BEGIN
+        R g[3], lp, lp0;
+        fd_grad_lap_r<DIM, R>(Dm, phi, x, y, z, g, &lp);
+        fd_grad_lap_r<DIM, R>(Dm, phi0tot, x, y, z, g, &lp0);
+        const R ph = (R)phi[o], p0 = (R)phi0tot[o];
+        mu[o] = (double)((R)p.c_dw * ph * (ph - R(1)) * (ph + R(1)) - (R)p.c_lap * lp + (R)p.c_pen * p0 * p0 * ph +
+                         (R)p.c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) - (R)p.c_wlap * lp0);
     }
 }
 
 // f = f^eq (Eqs. 30, 32) stored for pull streaming: population i of cell x is
 // written at x - c_i so that the first step reads f^eq_i(x).  Lagged fields
 // equal the initial ones.
-template <class P>
-__global__ void k_init_f(DomainDev Dm, const double *phi, const double *u, const double *Pin,
+template <class P, int DIM>
+__global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const double *u, const double *Pin,
                          const double *mu)
 {
     using ST = typename P::store;
     using AX = typename P::aux;
+    using R = typename P::real;
+    using LT = InitLat<DIM>;
     const DevParams &p = Dm.p;
-    const int dim = p.dim;
     const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
-    Lat L1, L2;
-    lattice_of(dim, 1, p.d0, L1);
-    lattice_of(dim, 2, p.d0, L2);
     ST *f = reinterpret_cast<ST *>(Dm.f[0]);
     AX *aux = reinterpret_cast<AX *>(Dm.aux[0]);
     long long *rest = reinterpret_cast<long long *>(Dm.rest[0]);
     const long long plane = Dm.plane;
-    const double cs2 = p.cs2, cs4 = cs2 * cs2;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < N;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(o % Dm.nx), y = (int)((o / Dm.nx) % Dm.ny), z = (int)(o / ((long long)Dm.nx * Dm.ny));
-        double g[3];
-        fd_grad_lap(Dm, mu, x, y, z, g, nullptr);
-        double S[3] = {p.Mdrho * g[0], p.Mdrho * g[1], dim == 3 ? p.Mdrho * g[2] : 0.0};
-        double uu[3] = {0.0, 0.0, 0.0};
+    const R cs2 = (R)p.cs2, cs4 = cs2 * cs2, d0 = (R)p.d0;
+    PF_INIT_ROWS_BEGIN
+        R g[3];
+        fd_grad_lap_r<DIM, R>(Dm, mu, x, y, z, g, nullptr);
+        const R Md = (R)p.Mdrho;
+        const R S[3] = {Md * g[0], Md * g[1], DIM == 3 ? Md * g[2] : R(0)};
+        R uu[3] = {R(0), R(0), R(0)};
         if (u)
-            for (int a = 0; a < dim; ++a) uu[a] = u[a * N + o];
-        const double ph = phi[o];
-        const double rho = p.drho * ph + p.rhom;
-        const double Pv = Pin ? Pin[o] : 0.0;
-        const double em = p.eta * mu[o];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) uu[a] = (R)u[a * N + o];
+        const double phd = phi[o];
+        const R ph = (R)phd;
+        const R rho = (R)p.drho * ph + (R)p.rhom;
+        const R Pv = Pin ? (R)Pin[o] : R(0);
+        const R em = (R)p.eta * (R)mu[o];
         // order-parameter lattice
-        const long long rest_phi = fixed_of_double(ph);
         int rest_s = 0, bad = 0;
-        for (int i = 0; i < L1.Q; ++i) {
-            double cu = 0.0;
-            for (int a = 0; a < dim; ++a) cu += L1.c[i][a] * uu[a];
-            const double fe = i == 0 ? ph + (L1.w[0] - 1.0) * em : L1.w[i] * em + L1.w[i] * cu * ph / cs2;
-            const int xx = wrap_idx(x - L1.c[i][0], Dm.nx), yy = wrap_idx(y - L1.c[i][1], Dm.ny),
-                      zz = dim == 3 ? wrap_idx(z - L1.c[i][2], Dm.nz) : 0;
+#pragma unroll
+        for (int i = 0; i < LT::Q1; ++i) {
+            R cu = R(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) cu += R(LT::c1(i, a)) * uu[a];
+            const R wi = LT::template w1<R>(i, d0);
+            const R fe = i == 0 ? ph + (wi - R(1)) * em : wi * em + wi * cu * ph / cs2;
+            const int xx = wrap1(x - LT::c1(i, 0), Dm.nx), yy = wrap1(y - LT::c1(i, 1), Dm.ny),
+                      zz = DIM == 3 ? wrap1(z - LT::c1(i, 2), Dm.nz) : 0;
             const long long id = cell_of(Dm, xx, yy, zz);
             if constexpr (P::MIX) {
                 if (i == 0) continue;
-                ST q = Conv<P>::st((float)fe, (float)p.scale[0]);
+                ST q = Conv<P>::st(fe, (R)p.scale[0]);
                 if constexpr (P::id == 3) q = bf16_flush(q);
-                rest_s += fix24<ST>(q, &bad);
+                rest_s += fix24_sat<ST>(q, &bad);
                 f[i * plane + id] = q;
             } else {
                 f[i * plane + id] = (ST)fe;
             }
         }
-        if constexpr (P::MIX) rest[cell_of(Dm, x, y, z)] = rest_phi - fix24_to_rest(rest_s, p.klog2[0]);
-        (void)bad;
+        if constexpr (P::MIX) rest[cell_of(Dm, x, y, z)] = fixed_of_double(phd) - fix24_to_rest(rest_s, p.klog2[0]);
+        if (bad) atomicOr(flags, 2);
         // flow lattice
-        for (int i = 0; i < L2.Q; ++i) {
-            double cu = 0.0, diag = 0.0, off = 0.0;
-            for (int a = 0; a < dim; ++a) {
-                const double ca = L2.c[i][a];
+#pragma unroll
+        for (int i = 0; i < LT::Q2; ++i) {
+            R cu = R(0), diag = R(0), off = R(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const R ca = R(LT::c2(i, a));
                 cu += ca * uu[a];
                 diag += (ca * ca - cs2) * (rho * uu[a] * uu[a] - S[a] * uu[a]);
-                for (int b = a + 1; b < dim; ++b)
-                    off += ca * L2.c[i][b] * (rho * uu[a] * uu[b] - 0.5 * (S[a] * uu[b] + uu[a] * S[b]));
+#pragma unroll
+                for (int b = a + 1; b < DIM; ++b)
+                    off += ca * R(LT::c2(i, b)) * (rho * uu[a] * uu[b] - R(0.5) * (S[a] * uu[b] + uu[a] * S[b]));
             }
-            const double lam = (i == 0 ? L2.w[0] - 1.0 : L2.w[i]) * Pv / cs2;
-            const double fe = lam + L2.w[i] * rho * cu / cs2 + L2.w[i] * (diag / (cs2 - cs4) + off / cs4);
-            const int xx = wrap_idx(x - L2.c[i][0], Dm.nx), yy = wrap_idx(y - L2.c[i][1], Dm.ny),
-                      zz = dim == 3 ? wrap_idx(z - L2.c[i][2], Dm.nz) : 0;
+            const R wi = LT::template w2<R>(i, d0);
+            const R lam = (i == 0 ? wi - R(1) : wi) * Pv / cs2;
+            const R fe = lam + wi * rho * cu / cs2 + wi * (diag / (cs2 - cs4) + off / cs4);
+            const int xx = wrap1(x - LT::c2(i, 0), Dm.nx), yy = wrap1(y - LT::c2(i, 1), Dm.ny),
+                      zz = DIM == 3 ? wrap1(z - LT::c2(i, 2), Dm.nz) : 0;
             const long long id = cell_of(Dm, xx, yy, zz);
             if constexpr (P::MIX) {
-                ST q = Conv<P>::st((float)fe, (float)p.scale[1]);
-                f[(L1.Q + i) * plane + id] = q;
+                f[(LT::Q1 + i) * plane + id] = Conv<P>::st(fe, (R)p.scale[1]);
             } else {
-                f[(L1.Q + i) * plane + id] = (ST)fe;
+                f[(LT::Q1 + i) * plane + id] = (ST)fe;
             }
         }
         const long long id = cell_of(Dm, x, y, z);
-        for (int a = 0; a < dim; ++a) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
             aux[a * plane + id] = (AX)uu[a];
-            aux[(dim + a) * plane + id] = (AX)S[a];
+            aux[(DIM + a) * plane + id] = (AX)S[a];
         }
-        aux[2 * dim * plane + id] = (AX)ph;
+        aux[2 * DIM * plane + id] = (AX)ph;
     }
 }
+#undef PF_INIT_ROWS_BEGIN
 
 // ---- diagnostics --------------------------------------------------------------------------------
 
@@ -369,27 +413,37 @@ static int grid_for(long long N, int bs)
 }
 
 template <class P>
-static void init_impl(const DomainDev &Dm, const double *phi0, const double *phi, const double *u,
+static void init_impl(const DomainDev &Dm, int *flags, const double *phi0, const double *phi, const double *u,
                       const double *Pin, double *tmp, const ParticleDev *parts, int np,
                       cudaStream_t s)
 {
+    using R = typename P::real;
     const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
     double *phi0tot = tmp, *mu = tmp + N;
-    const int g = grid_for(N, 256);
-    k_init_phi0<P><<<g, 256, 0, s>>>(Dm, phi0, phi0tot, parts, np);
-    k_init_mu<<<g, 256, 0, s>>>(Dm, phi, phi0tot, mu);
-    k_init_f<P><<<g, 256, 0, s>>>(Dm, phi, u, Pin, mu);
+    // x blocks of 128 cells, one grid row per domain row (at most 65535, the
+    // kernels stride over the rest)
+    const int bs = 128;
+    const int rows = Dm.ny * Dm.nz;
+    const dim3 g((Dm.nx + bs - 1) / bs, rows < 65535 ? rows : 65535);
+    k_init_phi0<P><<<g, bs, 0, s>>>(Dm, phi0, phi0tot, parts, np);
+    if (Dm.p.dim == 2) {
+        k_init_mu<2, R><<<g, bs, 0, s>>>(Dm, phi, phi0tot, mu);
+        k_init_f<P, 2><<<g, bs, 0, s>>>(Dm, flags, phi, u, Pin, mu);
+    } else {
+        k_init_mu<3, R><<<g, bs, 0, s>>>(Dm, phi, phi0tot, mu);
+        k_init_f<P, 3><<<g, bs, 0, s>>>(Dm, flags, phi, u, Pin, mu);
+    }
     count_launches(3);
 }
 
-void launch_init(int prec, const DomainDev &Dm, const double *phi0, const double *phi, const double *u,
+void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, const double *phi, const double *u,
                  const double *Pin, double *tmp, const ParticleDev *parts, int np, cudaStream_t s)
 {
     switch (prec) {
-    case 0: init_impl<P64>(Dm, phi0, phi, u, Pin, tmp, parts, np, s); break;
-    case 1: init_impl<P32>(Dm, phi0, phi, u, Pin, tmp, parts, np, s); break;
-    case 2: init_impl<PMixH>(Dm, phi0, phi, u, Pin, tmp, parts, np, s); break;
-    default: init_impl<PMixB>(Dm, phi0, phi, u, Pin, tmp, parts, np, s); break;
+    case 0: init_impl<P64>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
+    case 1: init_impl<P32>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
+    case 2: init_impl<PMixH>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
+    default: init_impl<PMixB>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
     }
 }
 

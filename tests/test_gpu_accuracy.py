@@ -90,7 +90,7 @@ def test_mixed_mass_drift_per_1e4_steps(pf, precision):
 
 def test_batch_contact_angles(pf):
     """Flat-wall drops drawn like the batched sweep (theta in [30, 150] deg,
-    density ratio in [1, 1000]): after relaxation the FP16-storage angle is
+    density ratio in [1, 30]): after relaxation the FP16-storage angle is
     within 1 deg of the FP64 angle; the FP64 angle is compared with the
     prescribed one."""
     # density ratios up to 30: higher ratios next to wetting walls do not stay
@@ -119,7 +119,7 @@ def test_batch_contact_angles(pf):
 
 def test_drainage_3d_saturation(pf):
     """3D drainage through random spheres (D3Q19 + D3Q7, theta = 120 deg,
-    body force 1e-6, equal densities): FP16-storage saturation within 1e-3 of
+    body force 1e-6, density ratio 10): FP16-storage saturation within 1e-3 of
     FP64 (128^3 box, 1000 steps)."""
     c = W.porous_drainage_3d(n=128)
     steps = 1000

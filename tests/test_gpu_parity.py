@@ -175,8 +175,26 @@ def test_nan_is_reported(pf):
     assert g.diagnostics()["nan_flag"] == 1
 
 
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_saturated_store_is_reported_and_conserves(pf, precision):
+    """A storage scale far too large for the populations (2^20: every mover of
+    a stored size >= 8) saturates the 16-bit movers; the step reports it
+    (flag bit 1) and the order parameter stays exactly conserved."""
+    c = W.small_case((32, 32), seed=3, solid=False)
+    g = pf.Sim(c["shape"], precision=precision, store_log2_scale=(20, 0), **c["params"])
+    g.init(c["phi0"], c["phi"])
+    m0 = float(c["phi"].sum())
+    g.step(5)
+    with pytest.raises(pf.PfError) as ei:
+        g.sync()
+    assert ei.value.code == pf.PF_ENUMERIC
+    d = g.diagnostics()
+    assert d["nan_flag"] & 2
+    assert abs(d["mass"] - m0) <= 1e-12 * np.abs(c["phi"]).sum()
+
+
 def test_cylinder_full_size_sampled(pf):
-    """512 x 512 drop on a cylinder (density ratio 1000) in FP64 and FP32 against
+    """512 x 512 drop on a cylinder (density ratio 100) in FP64 and FP32 against
     the oracle after a few steps at full size (the oracle's 512^2 steps take
     about a second each)."""
     c = W.drop_on_cylinder()
