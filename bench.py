@@ -218,11 +218,22 @@ def run_reference(args):
         return
     budget = min(120.0, max(10.0, 1.0 * args.steps))
     v, desc, cores = oracle_sample(args, budget)
+    if args.workload == "batch":
+        bw = batch_workload(args.batch_count)
+        cells = sum(int(math.prod(c["shape"])) for c in bw["cases"])
+        cfg = {"workload": "batch", "domains": len(bw["cases"]), "cells": cells,
+               "precision": "p64 (oracle)", "desc": bw["desc"]}
+    else:
+        c = single_workload(args.workload, args.n3d)
+        cells = int(math.prod(c["shape"]))
+        cfg = {"workload": args.workload, "cells": cells, "precision": "p64 (oracle)",
+               "desc": c["desc"]}
     line = {"impl": "reference", "metric": "MLUPS", "value": round(v, 4), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": round(cells / (v * 1e6) * 1e3, 3) if v > 0 else None,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload},
+            "config": cfg,
             "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": cores,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -246,12 +257,21 @@ def setup_dist():
 
 
 def max_over_ranks(dist, value):
+    """Maximum of ``value`` over the ranks of the default process group (NCCL
+    on the GPUs; any CPU backend such as gloo reduces a host tensor)."""
     if not dist:
         return value
     import torch
-    t = torch.tensor([value], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_mlups(cells_per_rank, steps, world, slowest_ms):
+    """Whole-job throughput of ``world`` replicas that each advance
+    ``cells_per_rank`` cells by ``steps`` steps, timed by the slowest rank."""
+    return cells_per_rank * steps * world / (slowest_ms * 1e-3) / 1e6
 
 
 def run_batch(args, dist, rank, world, local):
@@ -293,7 +313,7 @@ def run_batch(args, dist, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(cells, args.steps, world, total_ms)
     bpc = BYTES_PER_CELL[prec]
     avg_s = total_ms * 1e-3 / args.steps  # one step-kernel launch per step
     achieved = bpc * cells / avg_s / 1e9
@@ -324,7 +344,8 @@ def run_batch(args, dist, rank, world, local):
         dt = time.perf_counter() - t0
         e2e_b.close()
         e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 16 * cells, "d2h_bytes_per_step": 8 * cells,
+               "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
+               "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
                "desc": "one call sequence: pf_batch_init of every domain from pinned host phi0, "
                        "phi; pf_batch_step(%d) (includes the autotuner's timed steps when the "
@@ -395,7 +416,7 @@ def run_single(args, dist, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(cells, args.steps, world, total_ms)
     achieved = bpc * cells / (total_ms * 1e-3 / args.steps) / 1e9
 
     e2e = None
@@ -421,7 +442,8 @@ def run_single(args, dist, rank, world, local):
         dt = time.perf_counter() - t0
         s2.close()
         e2e = {"value": round(cells * S * iters / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 16 * cells, "d2h_bytes_per_step": 8 * cells,
+               "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
+               "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
                "desc": "per call: pf_init_fields(pinned host phi0, phi) + pf_step(%d) + "
                        "pf_get_macros(phi to pinned host); wall clock" % S}
@@ -464,7 +486,7 @@ def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim
     total_ms = max_over_ranks(dist, e0.elapsed_time(e1))
     if dist:
         dist.barrier()
-    mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(cells, args.steps, world, total_ms)
     nker = 2 if case.get("particles") else 1
     achieved = bpc * cells / (total_ms * 1e-3 / args.steps) / 1e9
     e2e = None
@@ -486,7 +508,8 @@ def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim
             raise pf.PfError(rc, pf.last_error())
         dt = time.perf_counter() - t0
         e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 16 * cells, "d2h_bytes_per_step": 8 * cells,
+               "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
+               "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
                "desc": "pf_init_fields(pinned host phi0, phi) + pf_step(%d) + pf_get_macros(phi "
                        "to pinned host); wall clock" % S}
