@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--n3d", type=int, default=256, help="cube side of drainage_3d")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
+    ap.add_argument("--config", type=int, nargs=4, default=None,
+                    metavar=("TILE_X", "TILE_Y", "CELLS_PER_THREAD", "CTAS_PER_SM"),
+                    help="fix the batch launch configuration instead of autotuning it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -290,6 +293,8 @@ def run_batch(args, dist, rank, world, local):
                  stream=stream.cuda_stream)
     for i, c in enumerate(cases):
         b.init(i, c["phi0"], c["phi"])
+    if args.config:
+        b.set_config(*args.config)
     # warm-up: the first long call runs the launch-configuration autotuner
     b.step(256 + max(args.warmup, 3))
     b.sync()
@@ -317,7 +322,7 @@ def run_batch(args, dist, rank, world, local):
     bpc = BYTES_PER_CELL[prec]
     avg_s = total_ms * 1e-3 / args.steps  # one step-kernel launch per step
     achieved = bpc * cells / avg_s / 1e9
-    tx, ty, cps = b.config()
+    tx, ty, cps, cpt = b.config()
 
     e2e = None
     if not args.no_e2e:
@@ -355,7 +360,7 @@ def run_batch(args, dist, rank, world, local):
     cfg = {"workload": "batch", "domains": len(cases), "cells": cells, "precision": prec,
            "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"
                                    % (cells * bpc / 1e9),
-           "tile": [tx, ty], "ctas_per_sm": cps,
+           "tile": [tx, ty], "ctas_per_sm": cps, "cells_per_thread": cpt,
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
                 clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel="k_step2d")

@@ -409,6 +409,8 @@ struct Engine {
     int2 *d_txy = nullptr;
     int ntiles = 0;
     int tx = 32, ty = 8, cps = 0, grid = 0;  // tile shape, CTAs per SM, grid size
+    int variant = 0;                         // 2D: 0 one cell per thread, 1 two (MODE_STEP_PAIR)
+    bool forced = false;                     // launch configuration set by the caller
     bool tuned = false;
     int nsm = 0;
     cudaStream_t stream = nullptr;
@@ -532,6 +534,8 @@ static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, cons
     return launch_step2d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
 }
 
+static int step_mode(const Engine &E) { return E.variant ? MODE_STEP_PAIR : MODE_STEP; }
+
 static int occupancy_any(const Engine &E, int tx, int ty, int mode)
 {
     if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode);
@@ -557,8 +561,8 @@ static StepArgs step_args(const Engine &E, int par)
 static int issue_step(Engine &E, int par)
 {
     const StepArgs a = step_args(E, par);
-    if (!launch_any(E, E.tx, E.ty, MODE_STEP, E.grid, a))
-        return fail(PF_EINVAL, "tile shape %dx%d not built", E.tx, E.ty);
+    if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a))
+        return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.stream);
     CK(cudaGetLastError());
@@ -567,7 +571,7 @@ static int issue_step(Engine &E, int par)
 
 static int grid_of(Engine &E, int cps)
 {
-    int occ = occupancy_any(E, E.tx, E.ty, MODE_STEP);
+    int occ = occupancy_any(E, E.tx, E.ty, step_mode(E));
     if (occ < 1) occ = 1;
     int c = cps > 0 ? std::min(cps, occ) : occ;
     long long g = (long long)c * E.nsm;
@@ -579,7 +583,7 @@ static int grid_of(Engine &E, int cps)
 // choice on the live state (the state advances; steps are counted), keep the
 // fastest; cached per (dim, precision, moving, cell-count bucket, domain count).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, long long, int>, std::tuple<int, int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, long long, int>, std::tuple<int, int, int, int>> g_tune_cache;
 
 static int engine_configure(Engine &E)
 {
@@ -592,24 +596,28 @@ static int engine_configure(Engine &E)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            int tx, ty, cps;
-            std::tie(tx, ty, cps) = it->second;
+            int tx, ty, var, cps;
+            std::tie(tx, ty, var, cps) = it->second;
             int rc = engine_tiles(E, tx, ty);
             if (rc) return rc;
+            E.variant = var;
             E.cps = cps;
             E.grid = grid_of(E, cps);
             E.tuned = true;
             return PF_OK;
         }
     }
-    int shapes[3][2] = {{32, 8}, {64, 4}, {32, 16}};
-    int nshapes = 3;
+    // (tile x, tile y, variant): one cell per thread, then two (FP32
+    // arithmetic policies without free particles)
+    int shapes[6][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}};
+    int nshapes = (E.prec != PF_P64 && E.np == 0) ? 6 : 3;
     if (E.dim == 3) {
         tile_shape3d(E.prec, &shapes[0][0], &shapes[0][1]);
+        shapes[0][2] = 0;
         nshapes = 1;
     }
     float best = 1e30f;
-    int bx = 32, by = 8, bc = 0;
+    int bx = 32, by = 8, bv = 0, bc = 0;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -618,7 +626,8 @@ static int engine_configure(Engine &E)
         const int *sh = shapes[si];
         int rc = engine_tiles(E, sh[0], sh[1]);
         if (rc) return rc;
-        const int occ = std::max(1, occupancy_any(E, sh[0], sh[1], MODE_STEP));
+        E.variant = sh[2];
+        const int occ = std::max(1, occupancy_any(E, sh[0], sh[1], step_mode(E)));
         for (int cps = 1; cps <= occ; cps = cps < occ ? std::min(cps * 2, occ) : occ + 1) {
             E.cps = cps;
             E.grid = grid_of(E, cps);
@@ -644,6 +653,7 @@ static int engine_configure(Engine &E)
                 best = ms;
                 bx = sh[0];
                 by = sh[1];
+                bv = sh[2];
                 bc = cps;
             }
         }
@@ -652,11 +662,12 @@ static int engine_configure(Engine &E)
     cudaEventDestroy(e1);
     int rc = engine_tiles(E, bx, by);
     if (rc) return rc;
+    E.variant = bv;
     E.cps = bc;
     E.grid = grid_of(E, bc);
     E.tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = std::make_tuple(bx, by, bc);
+    g_tune_cache[key] = std::make_tuple(bx, by, bv, bc);
     return PF_OK;
 }
 
@@ -681,6 +692,7 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
         } else {
             int tx = 32, ty = 8;
             if (E.dim == 3) tile_shape3d(E.prec, &tx, &ty);
+            E.variant = 0;
             rc = engine_tiles(E, tx, ty);
             E.cps = 0;
             E.grid = autotune ? grid_of(E, 0) : E.ntiles;  // one CTA per tile
@@ -853,6 +865,8 @@ static int engine_diag(Engine &E, int i, pf_diag *out)
     return PF_OK;
 }
 
+static int engine_force(Engine &E, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm);
+
 // ---------------------------------------------------------------------------------------------
 // single-domain handle
 // ---------------------------------------------------------------------------------------------
@@ -920,6 +934,14 @@ extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *ph
     return PF_OK;
 }
 
+extern "C" int pf_set_config(pf_handle *h, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    for (size_t i = 0; i < h->E.inited.size(); ++i)
+        if (!h->E.inited[i]) return fail(PF_ESTATE, "pf_set_config before pf_init_fields");
+    return engine_force(h->E, tile_x, tile_y, cells_per_thread, ctas_per_sm);
+}
+
 extern "C" int pf_step(pf_handle *h, int64_t n)
 {
     if (!h) return fail(PF_EINVAL, "handle is NULL");
@@ -978,6 +1000,11 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         if (grew) {
             // partial-sum table grows with the particle count; graphs bake the count in
             if (E.tuned) {
+                if (E.variant) {  // the two-cells-per-thread step has no particle terms
+                    E.variant = 0;
+                    E.tx = 32;
+                    E.ty = 8;
+                }
                 rc = engine_tiles(E, E.tx, E.ty);
                 if (rc) return rc;
                 E.grid = E.ntiles;
@@ -1080,19 +1107,57 @@ extern "C" int64_t pf_batch_cells(pf_batch *b)
     return c;
 }
 
-extern "C" int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm)
+extern "C" int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int *cells_per_thread)
 {
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (!b->E.tuned) {
         if (tile_x) *tile_x = -1;
         if (tile_y) *tile_y = -1;
         if (ctas_per_sm) *ctas_per_sm = -1;
+        if (cells_per_thread) *cells_per_thread = -1;
         return PF_OK;
     }
     if (tile_x) *tile_x = b->E.tx;
     if (tile_y) *tile_y = b->E.ty;
     if (ctas_per_sm) *ctas_per_sm = b->E.cps;
+    if (cells_per_thread) *cells_per_thread = b->E.variant ? 2 : 1;
     return PF_OK;
+}
+
+// fixed launch configuration (skips the autotuner)
+static int engine_force(Engine &E, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm)
+{
+    if (E.sticky) return E.sticky;
+    if (cells_per_thread != 1 && cells_per_thread != 2)
+        return fail(PF_EINVAL, "cells_per_thread must be 1 or 2");
+    if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
+    const int var = cells_per_thread - 1;
+    const int mode = var ? MODE_STEP_PAIR : MODE_STEP;
+    E.variant = var;
+    if (occupancy_any(E, tile_x, tile_y, mode) < 1) {
+        E.variant = 0;
+        return fail(PF_EINVAL, "launch configuration %dx%d with %d cell(s) per thread is not built for "
+                    "this precision / particle setting", tile_x, tile_y, cells_per_thread);
+    }
+    while (E.par != 0) {  // keep graph chunks starting at parity 0
+        int rc = issue_step(E, E.par);
+        if (rc) return (E.sticky = rc);
+        E.par ^= 1;
+        E.t++;
+    }
+    int rc = engine_tiles(E, tile_x, tile_y);
+    if (rc) return (E.sticky = rc);
+    E.cps = ctas_per_sm;
+    E.grid = grid_of(E, ctas_per_sm);
+    E.tuned = true;
+    E.forced = true;
+    return PF_OK;
+}
+
+extern "C" int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm)
+{
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    return engine_force(b->E, tile_x, tile_y, cells_per_thread, ctas_per_sm);
 }
 
 extern "C" void pf_batch_destroy(pf_batch *b)

@@ -20,7 +20,9 @@ namespace pf {
 
 constexpr int REST_FRAC_BITS = 50;  // rest population = value * 2^-50
 
-enum Mode { MODE_STEP = 0, MODE_MACROS = 1 };
+// MODE_STEP_PAIR: the 2D step with two cells per thread (FP32 arithmetic
+// policies, fixed solids)
+enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2 };
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {

@@ -4,6 +4,7 @@
 
 #include "pf_internal.h"
 #include "pf_kernels2d.cuh"
+#include "pf_kernels2d_pair.cuh"
 
 namespace pf {
 
@@ -22,6 +23,37 @@ static bool run2d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
     return true;
 }
 
+template <class P, int TX, int TYP>
+static bool run2d_pair(int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    auto kern = k_step2d_pair<P, TX, TYP>;
+    if (occ) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TYP, 0) != cudaSuccess) n = 0;
+        *occ = n;
+        return true;
+    }
+    kern<<<grid, TX * TYP, 0, s>>>(a);
+    count_launches(1);
+    return true;
+}
+
+// two cells per thread: tiles of tx x ty cells on tx x ty/2 threads
+template <class P>
+static bool dispatch2d_pair(int tx, int ty, bool moving, int grid, cudaStream_t s, const StepArgs &a,
+                            int *occ)
+{
+    if constexpr (P::id == 0) {
+        return false;  // FP64 has no packed arithmetic
+    } else {
+        if (moving) return false;
+        if (tx == 32 && ty == 16) return run2d_pair<P, 32, 8>(grid, s, a, occ);
+        if (tx == 64 && ty == 8) return run2d_pair<P, 64, 4>(grid, s, a, occ);
+        if (tx == 32 && ty == 32) return run2d_pair<P, 32, 16>(grid, s, a, occ);
+        return false;
+    }
+}
+
 template <class P>
 static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
                        const StepArgs &a, int *occ)
@@ -34,6 +66,7 @@ static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStre
         return moving ? run2d<P, TX, TY, true, MODE_STEP>(grid, s, a, occ)                \
                       : run2d<P, TX, TY, false, MODE_STEP>(grid, s, a, occ);              \
     }
+    if (mode == MODE_STEP_PAIR) return dispatch2d_pair<P>(tx, ty, moving, grid, s, a, occ);
     if (mode == MODE_MACROS) {
         if (tx == 32 && ty == 8)
             return moving ? run2d<P, 32, 8, true, MODE_MACROS>(grid, s, a, occ)

@@ -95,7 +95,10 @@ def load(build_if_missing=False):
         "pf_batch_diagnostics": (C.c_int, [vp, C.c_int, C.POINTER(pf_diag)]),
         "pf_batch_sync": (C.c_int, [vp]),
         "pf_batch_cells": (C.c_int64, [vp]),
-        "pf_batch_config": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "pf_batch_config": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
+        "pf_batch_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "pf_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
         "pf_batch_destroy": (None, [vp]),
         "pf_launch_count": (C.c_int64, []),
         "pf_diagnostics_noalloc": (C.c_int, [C.POINTER(pf_grid), C.POINTER(pf_params), vp, vp, vp, vp,
@@ -217,6 +220,11 @@ class Sim:
         keep = [_ptr(a, where) for a in (phi0, phi, u, P)]
         _check(load().pf_init_fields(self._h, *[k[0] for k in keep], where))
 
+    def set_config(self, tile_x, tile_y, cells_per_thread=1, ctas_per_sm=0):
+        """Fix the launch configuration (after init)."""
+        _check(load().pf_set_config(self._h, int(tile_x), int(tile_y), int(cells_per_thread),
+                                    int(ctas_per_sm)))
+
     def step(self, n=1):
         _check(load().pf_step(self._h, int(n)))
 
@@ -291,9 +299,14 @@ class Batch:
         return int(load().pf_batch_cells(self._h))
 
     def config(self):
-        a, b, c = C.c_int(), C.c_int(), C.c_int()
-        _check(load().pf_batch_config(self._h, C.byref(a), C.byref(b), C.byref(c)))
-        return a.value, b.value, c.value
+        """(tile_x, tile_y, ctas_per_sm, cells_per_thread) of the step launches."""
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(load().pf_batch_config(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return a.value, b.value, c.value, d.value
+
+    def set_config(self, tile_x, tile_y, cells_per_thread=1, ctas_per_sm=0):
+        _check(load().pf_batch_set_config(self._h, int(tile_x), int(tile_y), int(cells_per_thread),
+                                          int(ctas_per_sm)))
 
     def macros(self, i):
         sh = self.shapes[i]

@@ -35,7 +35,7 @@ def rel(a, b):
     return float(np.abs(a - b).max() / (s if s > 0 else 1.0))
 
 
-def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True):
+def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True, config=None):
     prm = case["params"]
     g = pf.Sim(case["shape"], precision=precision, **prm)
     o = O.OracleSim(case["shape"], O.make_params(**prm)) if oracle else None
@@ -44,6 +44,8 @@ def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True):
         if o is not None:
             o.set_particle(k, O.Particle(**pp))
     g.init(case["phi0"], case["phi"], case.get("u"))
+    if config is not None:
+        g.set_config(*config)
     if o is not None:
         o.init(case["phi0"], case["phi"], case.get("u"))
     g.step(steps)
@@ -162,6 +164,55 @@ def test_pmix_against_oracle(pf, precision, tol_phi):
     assert rel(gm["phi"], om["phi"]) < tol_phi
 
 
+# ---- two cells per thread (packed FP32 arithmetic) ---------------------------------------
+
+@pytest.mark.parametrize("tile", [(32, 16), (64, 8), (32, 32)])
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_pair_step_against_oracle(pf, precision, tol_phi, tile):
+    """The two-cells-per-thread step on a ragged grid (52 x 37: partial tiles
+    in x and y, and an odd row count so the last pair has one valid cell)."""
+    c = W.small_case((37, 52), seed=7, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 200, precision=precision, config=(tile[0], tile[1], 2))
+    gm, om = g.macros(), o.macros()
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    if precision == "p32":
+        assert rel(gm["rho"], om["rho"]) < 1e-5
+        assert rel(gm["u"], om["u"]) < 1e-3
+        assert rel(gm["P"], om["P"]) < 1e-3
+    assert g.diagnostics()["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_pair_step_conserves_mass_exactly(pf, precision):
+    c = W.small_case((80, 64), seed=4, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, _ = run_pair(pf, c, 0, precision=precision, oracle=False, config=(32, 16, 2))
+    m0 = g.diagnostics()["mass"]
+    g.step(1000)
+    m1 = g.diagnostics()["mass"]
+    assert abs(m1 - m0) / np.abs(c["phi"]).sum() < 1e-13
+
+
+def test_pair_and_single_agree_p32(pf):
+    """Both launch variants compute the same FP32 update (to rounding order)."""
+    c = W.small_case((64, 96), seed=5, solid=True, theta_deg=120.0, rho_ratio=10.0)
+    a, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 8, 1))
+    b, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 16, 2))
+    ma, mb = a.macros(), b.macros()
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(mb[k], ma[k]) < tol, k
+
+
+def test_config_override_rejects_unbuilt(pf):
+    c = W.small_case((32, 32), seed=1, solid=False)
+    g = pf.Sim(c["shape"], precision="p64", **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError) as ei:
+        g.set_config(32, 16, 2)  # no packed arithmetic in FP64
+    assert ei.value.code == pf.PF_EINVAL
+    with pytest.raises(pf.PfError):
+        g.set_config(48, 8, 1)
+
+
 def test_nan_is_reported(pf):
     c = W.small_case((32, 32), seed=1, solid=False)
     phi = c["phi"].copy()
@@ -262,7 +313,7 @@ def test_batch_domains_equal_single_runs(pf):
         b.init(i, c["phi0"], c["phi"], c.get("u"))
     b.step(steps)
     b.sync()
-    tx, ty, cps = b.config()
+    tx, ty, cps, cpt = b.config()
     assert tx > 0 and cps > 0
     for i, c in enumerate(cases):
         g, _ = run_pair(pf, c, steps, oracle=False)
