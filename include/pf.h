@@ -50,7 +50,7 @@ extern "C" {
 #define PF_ECUDA (-3)    /* a CUDA runtime call failed */
 #define PF_ENUMERIC (-4) /* a non-finite phi or u appeared, or a 16-bit order-parameter
                             population was saturated (see pf_diag.nan_flag) */
-#define PF_ETIMEOUT (-5) /* a bounded device wait gave up */
+#define PF_ETIMEOUT (-5) /* a bounded device wait gave up (sticky: the handle's state is lost) */
 #define PF_ESTATE (-6)   /* call out of order (e.g. step before init) */
 
 /* ---- precision policies ---- */
@@ -187,23 +187,28 @@ int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u,
 int pf_batch_diagnostics(pf_batch *b, int i, pf_diag *out);
 int pf_batch_sync(pf_batch *b);
 /* Total lattice cells of the batch and the chosen launch configuration
- * (tile_x, tile_y in cells, ctas_per_sm, cells_per_thread) after the first
- * step; -1 before.  Null out-pointers are skipped. */
+ * (tile_x, tile_y in cells, ctas_per_sm, kernel) after the first step; -1
+ * before.  Null out-pointers are skipped. */
 int64_t pf_batch_cells(pf_batch *b);
-int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int *cells_per_thread);
+int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel);
 
 /* Fix the launch configuration instead of letting the autotuner choose it
  * (for benchmarks and tests of one configuration; no counterpart in the
- * paper).  tile_x x tile_y cells per tile; cells_per_thread 1 or 2 (2: the
- * FP32-arithmetic 2D step on two vertically adjacent cells per thread; P32
- * and PMIX only, fixed solids only -- adding a particle later falls back to
- * one cell per thread); ctas_per_sm 0 = as many as fit, else a cap.  Built
- * 2D tiles: 1 cell/thread 32x8, 64x4, 32x16; 2 cells/thread 32x16, 64x8,
- * 32x32.  3D: the tile of tile_shape3d only.  PF_EINVAL for a configuration
- * that is not built; a pending odd time step is issued first.  Call after
- * init (pf_set_config) or at any time between steps (pf_batch_set_config). */
-int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm);
-int pf_set_config(pf_handle *h, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm);
+ * paper).  tile_x x tile_y cells per tile; ctas_per_sm 0 = as many as fit,
+ * else a cap.  kernel:
+ *   0  one cell per thread (all policies, particles; 2D tiles 32x8, 64x4,
+ *      32x16; 3D the tile of its policy);
+ *   1  2D, two vertically adjacent cells per thread in packed FP32
+ *      arithmetic (P32 and PMIX, fixed solids; tiles 32x16, 64x8, 32x32);
+ *   2  as 1, with each tile's inputs copied into shared memory by
+ *      asynchronous bulk copies one tile ahead (tile 32x16; every nx a
+ *      multiple of 8 for 16-bit storage, of 4 for FP32).
+ * Adding a particle later falls back to kernel 0.  PF_EINVAL for a
+ * configuration that is not built or not allowed; a pending odd time step is
+ * issued first.  Call after init (pf_set_config) or at any time between steps
+ * (pf_batch_set_config). */
+int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int kernel, int ctas_per_sm);
+int pf_set_config(pf_handle *h, int tile_x, int tile_y, int kernel, int ctas_per_sm);
 void pf_batch_destroy(pf_batch *b);
 
 /* ---- diagnostics without device allocation ----

@@ -409,7 +409,7 @@ struct Engine {
     int2 *d_txy = nullptr;
     int ntiles = 0;
     int tx = 32, ty = 8, cps = 0, grid = 0;  // tile shape, CTAs per SM, grid size
-    int variant = 0;                         // 2D: 0 one cell per thread, 1 two (MODE_STEP_PAIR)
+    int variant = 0;                         // 2D: 0 one cell per thread, 1 two, 2 two + staging
     bool forced = false;                     // launch configuration set by the caller
     bool tuned = false;
     int nsm = 0;
@@ -534,7 +534,21 @@ static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, cons
     return launch_step2d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
 }
 
-static int step_mode(const Engine &E) { return E.variant ? MODE_STEP_PAIR : MODE_STEP; }
+static int step_mode(const Engine &E)
+{
+    return E.variant == 2 ? MODE_STEP_STAGE : (E.variant == 1 ? MODE_STEP_PAIR : MODE_STEP);
+}
+
+// the staged 2D step copies 16-byte chunks: every domain's nx must keep its
+// rows' chunks and periodic splits aligned
+static bool stage_ok(const Engine &E)
+{
+    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0) return false;
+    const int q = E.prec == PF_P32 ? 4 : 8;
+    for (auto &m : E.mem)
+        if (m.d.nx % q) return false;
+    return true;
+}
 
 static int occupancy_any(const Engine &E, int tx, int ty, int mode)
 {
@@ -609,6 +623,8 @@ static int engine_configure(Engine &E)
     }
     // (tile x, tile y, variant): one cell per thread, then two (FP32
     // arithmetic policies without free particles)
+    // (kernel 2, the bulk-copy staged variant, is selectable with
+    // pf_set_config but not a candidate: it measured slower than kernel 1)
     int shapes[6][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}};
     int nshapes = (E.prec != PF_P64 && E.np == 0) ? 6 : 3;
     if (E.dim == 3) {
@@ -748,6 +764,10 @@ static int engine_sync(Engine &E)
     }
     int flag = 0;
     CK(cudaMemcpy(&flag, E.d_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 4) {
+        E.sticky = fail(PF_ETIMEOUT, "a step kernel's bounded wait for its staged inputs ran out");
+        return E.sticky;
+    }
     if (flag & 1) return fail(PF_ENUMERIC, "a non-finite phi or u appeared");
     if (flag & 2)
         return fail(PF_ENUMERIC, "a 16-bit order-parameter population reached the storage range and was "
@@ -865,7 +885,7 @@ static int engine_diag(Engine &E, int i, pf_diag *out)
     return PF_OK;
 }
 
-static int engine_force(Engine &E, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm);
+static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_per_sm);
 
 // ---------------------------------------------------------------------------------------------
 // single-domain handle
@@ -934,12 +954,12 @@ extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *ph
     return PF_OK;
 }
 
-extern "C" int pf_set_config(pf_handle *h, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm)
+extern "C" int pf_set_config(pf_handle *h, int tile_x, int tile_y, int kernel, int ctas_per_sm)
 {
     if (!h) return fail(PF_EINVAL, "handle is NULL");
     for (size_t i = 0; i < h->E.inited.size(); ++i)
         if (!h->E.inited[i]) return fail(PF_ESTATE, "pf_set_config before pf_init_fields");
-    return engine_force(h->E, tile_x, tile_y, cells_per_thread, ctas_per_sm);
+    return engine_force(h->E, tile_x, tile_y, kernel, ctas_per_sm);
 }
 
 extern "C" int pf_step(pf_handle *h, int64_t n)
@@ -1107,37 +1127,39 @@ extern "C" int64_t pf_batch_cells(pf_batch *b)
     return c;
 }
 
-extern "C" int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int *cells_per_thread)
+extern "C" int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel)
 {
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (!b->E.tuned) {
         if (tile_x) *tile_x = -1;
         if (tile_y) *tile_y = -1;
         if (ctas_per_sm) *ctas_per_sm = -1;
-        if (cells_per_thread) *cells_per_thread = -1;
+        if (kernel) *kernel = -1;
         return PF_OK;
     }
     if (tile_x) *tile_x = b->E.tx;
     if (tile_y) *tile_y = b->E.ty;
     if (ctas_per_sm) *ctas_per_sm = b->E.cps;
-    if (cells_per_thread) *cells_per_thread = b->E.variant ? 2 : 1;
+    if (kernel) *kernel = b->E.variant;
     return PF_OK;
 }
 
 // fixed launch configuration (skips the autotuner)
-static int engine_force(Engine &E, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm)
+static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_per_sm)
 {
     if (E.sticky) return E.sticky;
-    if (cells_per_thread != 1 && cells_per_thread != 2)
-        return fail(PF_EINVAL, "cells_per_thread must be 1 or 2");
+    const int var = kernel;
+    if (var < 0 || var > 2) return fail(PF_EINVAL, "kernel must be 0, 1 or 2");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
-    const int var = cells_per_thread - 1;
-    const int mode = var ? MODE_STEP_PAIR : MODE_STEP;
+    if (var == 2 && !stage_ok(E))
+        return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
+                               "multiple of %d", E.prec == PF_P32 ? 4 : 8);
+    const int mode = var == 2 ? MODE_STEP_STAGE : (var ? MODE_STEP_PAIR : MODE_STEP);
     E.variant = var;
     if (occupancy_any(E, tile_x, tile_y, mode) < 1) {
         E.variant = 0;
-        return fail(PF_EINVAL, "launch configuration %dx%d with %d cell(s) per thread is not built for "
-                    "this precision / particle setting", tile_x, tile_y, cells_per_thread);
+        return fail(PF_EINVAL, "launch configuration %dx%d of kernel %d is not built for this precision / "
+                    "particle setting", tile_x, tile_y, var);
     }
     while (E.par != 0) {  // keep graph chunks starting at parity 0
         int rc = issue_step(E, E.par);
@@ -1154,10 +1176,10 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int cells_per_thread,
     return PF_OK;
 }
 
-extern "C" int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int cells_per_thread, int ctas_per_sm)
+extern "C" int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int kernel, int ctas_per_sm)
 {
     if (!b) return fail(PF_EINVAL, "batch is NULL");
-    return engine_force(b->E, tile_x, tile_y, cells_per_thread, ctas_per_sm);
+    return engine_force(b->E, tile_x, tile_y, kernel, ctas_per_sm);
 }
 
 extern "C" void pf_batch_destroy(pf_batch *b)

@@ -21,8 +21,9 @@ namespace pf {
 constexpr int REST_FRAC_BITS = 50;  // rest population = value * 2^-50
 
 // MODE_STEP_PAIR: the 2D step with two cells per thread (FP32 arithmetic
-// policies, fixed solids)
-enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2 };
+// policies, fixed solids); MODE_STEP_STAGE: the same with the tile's inputs
+// staged in shared memory by bulk copies
+enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2, MODE_STEP_STAGE = 3 };
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {
@@ -336,6 +337,49 @@ __device__ __forceinline__ int wrap_idx(int v, int n)
 {
     v %= n;
     return v < 0 ? v + n : v;
+}
+
+// ---- asynchronous bulk copies into shared memory (mbarrier completion) ------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier shared-memory accesses before later bulk copies
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Wait for the phase of parity `parity` to complete, at most max_iter polls
+// (with back-off); false if it did not.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, int max_iter)
+{
+    for (int i = 0; i < max_iter; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (i > 16) __nanosleep(64);
+    }
+    return false;
 }
 
 }  // namespace pf

@@ -142,6 +142,204 @@ __device__ __forceinline__ void collide9_pair(F2 f[9], const F2 heq[9], const F2
     f[0] = (m[0] - m[3]) + (m[8] - m[4]);
 }
 
+// Stage B: mu_phi (Eq. 9) on the tile + 1 frame, two rows per work item.
+template <int FX, int WX, int WY, int NT>
+__device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*s_phi)[FX],
+                                        const float (*s_p0)[FX], float (*s_mu)[WX], int tid)
+{
+    {
+        const F2 c_dw = mk2(kp.c_dw), c_lap = mk2(-kp.c_lap), c_pen = mk2(kp.c_pen),
+                 c_wet = mk2(kp.c_wet), c_wlap = mk2(-kp.c_wlap), one = mk2(1.0f), three = mk2(3.0f);
+        constexpr int NPAIR = WX * (WY / 2);
+        for (int r = tid; r < NPAIR; r += NT) {
+            const int wx = r % WX, wy = 2 * (r / WX);
+            const int fx = wx + 1, fy = wy + 1;
+            const F2 ph = mk2(s_phi[fy][fx], s_phi[fy + 1][fx]);
+            const F2 p0 = mk2(s_p0[fy][fx], s_p0[fy + 1][fx]);
+            const F2 lp = lap9_pair<FX>(s_phi, fx, fy), lp0 = lap9_pair<FX>(s_p0, fx, fy);
+            const F2 p02 = p0 * p0;
+            F2 mu = c_dw * ph * ((ph - one) * (ph + one));
+            mu = fma2(c_lap, lp, mu);
+            mu = fma2(c_pen * p02, ph, mu);
+            mu = fma2(c_wet * p0, fma2(three * ph, ph, p02) - one, mu);
+            mu = fma2(c_wlap, lp0, mu);
+            s_mu[wy][wx] = mu.v.x;
+            s_mu[wy + 1][wx] = mu.v.y;
+        }
+    }
+}
+
+// Stage C of the pair step: the update of the thread's two cells (Eqs. 29-38)
+// from the shared tiles (phi, phi0 on tile + 2 at (hx, hy); mu, w on tile + 1
+// at (wx, wy)) and the values gathered in stage A, then their stores.
+template <class P, int FX, int WX>
+__device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p, const KParams<float> &kp,
+                                           const float (*s_phi)[FX], const float (*s_p0)[FX],
+                                           const float (*s_mu)[WX], const float (*s_w)[WX], int hx, int hy,
+                                           int wx, int wy, F2 phi, F2 (&f1)[9],
+                                           const typename P::store (&f2raw)[2][9],
+                                           const typename P::aux (&lag)[2][5],
+                                           const typename P::store (&q1)[2][9], const long long (&rest_own)[2],
+                                           const int (&id)[2], bool valid0, bool valid1, typename P::store *fd,
+                                           long long *rd, typename P::aux *ad, int plane)
+{
+    using ST = typename P::store;
+    using AX = typename P::aux;
+
+    const F2 phi0 = mk2(s_p0[hy][hx], s_p0[hy + 1][hx]);
+    F2 gpx, gpy, gmx, gmy, wgx, wgy;
+    grad9_pair<FX>(s_phi, hx, hy, gpx, gpy);
+    grad9_pair<WX>(s_mu, wx, wy, gmx, gmy);
+    grad9_pair<WX>(s_w, wx, wy, wgx, wgy);
+    const F2 mu = mk2(s_mu[wy][wx], s_mu[wy + 1][wx]);
+    const F2 drho = mk2(kp.drho), half = mk2(0.5f), one = mk2(1.0f), two = mk2(2.0f);
+    const F2 rho = fma2(drho, phi, mk2(kp.rhom));
+    const F2 muv = fma2(mk2(kp.dmu), phi, mk2(kp.mum));
+    const F2 Mdrho = mk2(kp.Mdrho);
+    const F2 Sx = Mdrho * gmx, Sy = Mdrho * gmy;
+    const F2 grx = drho * gpx, gry = drho * gpy;
+    // F = mu grad phi + F_b + F_c, F_c = (-d_y w, d_x w)/2 from the previous step
+    const F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
+    const F2 Fy = fma2(mu, gpy, fma2(half, wgx, mk2(kp.Fb[1])));
+
+    F2 f2[9];
+    const F2 isc2v = mk2(kp.inv_scale[1]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const F2 v = P::MIX ? mk2(stored_to_float<ST>(f2raw[0][i]), stored_to_float<ST>(f2raw[1][i]))
+                            : mk2(Conv<P>::ld(f2raw[0][i], 1.0f), Conv<P>::ld(f2raw[1][i], 1.0f));
+        f2[i] = P::MIX ? v * isc2v : v;
+    }
+    // u* (Eq. 36a)
+    const F2 jx = ((f2[1] - f2[3]) + (f2[5] - f2[6])) + (f2[8] - f2[7]);
+    const F2 jy = ((f2[2] - f2[4]) + (f2[5] + f2[6])) - (f2[7] + f2[8]);
+    const F2 irho = mk2(__frcp_rn(rho.v.x), __frcp_rn(rho.v.y));
+    const F2 usx = fma2(half, Fx, jx) * irho, usy = fma2(half, Fy, jy) * irho;
+    // penalty force f = phi0 (u_s - u*) with u_s = 0 (fixed solids)
+    const F2 nphi0 = mk2(0.0f) - phi0;
+    const F2 fpx = nphi0 * usx, fpy = nphi0 * usy;
+    const F2 ux = fma2(half, fpx, usx), uy = fma2(half, fpy, usy);
+    const F2 Ftx = fma2(rho, fpx, Fx), Fty = fma2(rho, fpy, Fy);
+
+    const F2 upx = mk2((float)lag[0][0], (float)lag[1][0]), upy = mk2((float)lag[0][1], (float)lag[1][1]);
+    const F2 Spx = mk2((float)lag[0][2], (float)lag[1][2]), Spy = mk2((float)lag[0][3], (float)lag[1][3]);
+    const F2 php = mk2((float)lag[0][4], (float)lag[1][4]);
+
+    // relaxation rates (Eq. 35, 1 - phi0 bounded below by solid_eps)
+    const float seps = kp.solid_eps;
+    const F2 solid = one - phi0;
+    const F2 solidc = mk2(fmaxf(solid.v.x, seps), fmaxf(solid.v.y, seps));
+    const F2 nu = muv * irho * mk2(__frcp_rn(solidc.v.x), __frcp_rn(solidc.v.y));
+    const F2 inv_s2a = fma2(mk2(kp.two_over_1md0), nu, half);
+    const F2 inv_s2b = fma2(mk2(kp.inv_cs2), nu, half);
+    const F2 Kf = mk2(kp.K);
+    const F2 H = Kf * (mk2(kp.Hc0) - mk2(kp.Hc1) * inv_s2a);
+    // pressure (Eq. 36b)
+    const F2 sum_f = ((f2[1] + f2[2]) + (f2[3] + f2[4])) + ((f2[5] + f2[6]) + (f2[7] + f2[8]));
+    const F2 ugr = fma2(ux, grx, uy * gry);
+    const F2 rus_u = fma2(fma2(rho, ux, mk2(0.0f) - Sx), ux, fma2(rho, uy, mk2(0.0f) - Sy) * uy);
+    const F2 Su = fma2(Sx, ux, Sy * uy), Sup = fma2(Spx, upx, Spy * upy);
+    const F2 dt_term = fma2(two, fma2(ux, Ftx, uy * Fty), Sup - Su);
+    const F2 Pr = mk2(kp.Pfac) *
+                  fma2(Kf * half, dt_term,
+                       fma2(half + H, ugr, fma2(mk2(-kp.w0f * kp.inv_1mcs2), rus_u, sum_f)));
+
+    const F2 cs2 = mk2(kp.cs2), cs4 = mk2(kp.cs4);
+    F2 heq[9], hF[9], nS[9], cF[9];
+    // ---- order-parameter lattice (Eq. 30): Hermite equilibria and source
+    {
+        const F2 eta_mu = mk2(kp.eta) * mu;
+        heq[0] = phi;
+        heq[1] = phi * ux;
+        heq[2] = phi * uy;
+        heq[3] = cs2 * (eta_mu - phi);
+        heq[4] = heq[3];
+        heq[8] = cs4 * (phi - eta_mu);
+        hF[1] = heq[1] - php * upx;  // d_t(phi u), explicit Euler
+        hF[2] = heq[2] - php * upy;
+        const float s[9] = {kp.s0, kp.s1phi, kp.s1phi, kp.s2, kp.s2, kp.s2, kp.s3, kp.s3, kp.s4};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            nS[k] = mk2(-s[k]);
+            cF[k] = mk2(1.0f - 0.5f * s[k]);
+        }
+        // zero equilibria: moments 5, 6, 7; zero sources: 0 and 3..8
+        collide9_pair<(1u << 5) | (1u << 6) | (1u << 7), 0x1F9u>(f1, heq, hF, nS, cF, cs2, cs4);
+    }
+    // ---- flow lattice (Eqs. 32-34)
+    {
+        const F2 rux = rho * ux, ruy = rho * uy;
+        heq[1] = rux;
+        heq[2] = ruy;
+        heq[3] = Pr + (rux - Sx) * ux;
+        heq[4] = Pr + (ruy - Sy) * uy;
+        heq[5] = rux * uy - half * fma2(Sx, uy, ux * Sy);
+        heq[8] = (mk2(0.0f) - cs2) * Pr;
+        const F2 c3 = one - mk2(3.0f) * cs2;
+        const F2 tcs2 = two * cs2;
+        hF[0] = ugr;
+        hF[1] = Ftx;
+        hF[2] = Fty;
+        hF[3] = fma2(two * ux, Ftx, fma2(tcs2 * ux, grx, fma2(c3, ugr, Spx * upx - Sx * ux)));
+        hF[4] = fma2(two * uy, Fty, fma2(tcs2 * uy, gry, fma2(c3, ugr, Spy * upy - Sy * uy)));
+        hF[5] = fma2(ux, Fty, Ftx * uy) -
+                half * (fma2(Sx, uy, ux * Sy) - fma2(Spx, upy, upx * Spy)) + cs2 * fma2(ux, gry, grx * uy);
+        const F2 s2a = mk2(__frcp_rn(inv_s2a.v.x), __frcp_rn(inv_s2a.v.y));
+        const F2 s2b = mk2(__frcp_rn(inv_s2b.v.x), __frcp_rn(inv_s2b.v.y));
+        nS[0] = mk2(-kp.s0);
+        nS[1] = nS[2] = mk2(-kp.s1);
+        nS[3] = nS[4] = mk2(0.0f) - s2a;
+        nS[5] = mk2(0.0f) - s2b;
+        nS[6] = nS[7] = mk2(-kp.s3);
+        nS[8] = mk2(-kp.s4);
+        cF[0] = mk2(1.0f - 0.5f * kp.s0);
+        cF[1] = cF[2] = mk2(1.0f - 0.5f * kp.s1);
+        cF[3] = cF[4] = fma2(mk2(-0.5f), s2a, one);
+        cF[5] = fma2(mk2(-0.5f), s2b, one);
+        // zero equilibria: moments 0, 6, 7; zero sources: 6, 7, 8
+        collide9_pair<(1u << 0) | (1u << 6) | (1u << 7), (1u << 6) | (1u << 7) | (1u << 8)>(f2, heq, hF, nS,
+                                                                                           cF, cs2, cs4);
+    }
+
+    // ---------------- stores (per cell) ----------------
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        if (!(c == 0 ? valid0 : valid1)) continue;
+        const int idc = id[c];
+        const float phic = c == 0 ? phi.v.x : phi.v.y;
+        const float uxc = c == 0 ? ux.v.x : ux.v.y, uyc = c == 0 ? uy.v.x : uy.v.y;
+        if constexpr (P::MIX) {
+            const float sc1 = kp.scale[0];
+            int bad = 0, sold = 0, snew = 0;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[c][i]);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                ST q = Conv<P>::st(c == 0 ? f1[i].v.x : f1[i].v.y, sc1);
+                if constexpr (P::id == 3) q = bf16_flush(q);
+                snew += fix24_sat<ST>(q, &bad);
+                fd[i * plane + idc] = q;
+            }
+            // exact: sum of the cell's order-parameter populations is unchanged
+            rd[idc] = rest_own[c] + fix24_to_rest(sold - snew, p.klog2[0]);
+            if (bad) atomicOr(A.flags, 2);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fd[i * plane + idc] = Conv<P>::st(c == 0 ? f1[i].v.x : f1[i].v.y, 1.0f);
+        }
+        const float sc2 = P::MIX ? kp.scale[1] : 1.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fd[(9 + i) * plane + idc] = Conv<P>::st(c == 0 ? f2[i].v.x : f2[i].v.y, sc2);
+        // fields of this step, read as the previous step's by the next one
+        ad[0 * plane + idc] = (AX)uxc;
+        ad[1 * plane + idc] = (AX)uyc;
+        ad[2 * plane + idc] = (AX)(c == 0 ? Sx.v.x : Sx.v.y);
+        ad[3 * plane + idc] = (AX)(c == 0 ? Sy.v.x : Sy.v.y);
+        ad[4 * plane + idc] = (AX)phic;
+        if (!isfinite(phic) || !isfinite(uxc) || !isfinite(uyc)) atomicOr(A.flags, 1);
+    }
+}
+
 // 256-thread pair tiles are register heavy: two resident CTAs per SM.
 template <int TX, int TYP>
 constexpr int step2d_pair_min_blocks()
@@ -304,185 +502,15 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
         }
         __syncthreads();
 
-        // ---------------- stage B: mu_phi on tile+1 (Eq. 9), row pairs ----------------
-        {
-            const F2 c_dw = mk2(kp.c_dw), c_lap = mk2(-kp.c_lap), c_pen = mk2(kp.c_pen),
-                     c_wet = mk2(kp.c_wet), c_wlap = mk2(-kp.c_wlap), one = mk2(1.0f), three = mk2(3.0f);
-            constexpr int NPAIR = WX * (WY / 2);
-            for (int r = tid; r < NPAIR; r += NT) {
-                const int wx = r % WX, wy = 2 * (r / WX);
-                const int fx = wx + 1, fy = wy + 1;
-                const F2 ph = mk2(s_phi[fy][fx], s_phi[fy + 1][fx]);
-                const F2 p0 = mk2(s_p0[fy][fx], s_p0[fy + 1][fx]);
-                const F2 lp = lap9_pair<FX>(s_phi, fx, fy), lp0 = lap9_pair<FX>(s_p0, fx, fy);
-                const F2 p02 = p0 * p0;
-                F2 mu = c_dw * ph * ((ph - one) * (ph + one));
-                mu = fma2(c_lap, lp, mu);
-                mu = fma2(c_pen * p02, ph, mu);
-                mu = fma2(c_wet * p0, fma2(three * ph, ph, p02) - one, mu);
-                mu = fma2(c_wlap, lp0, mu);
-                s_mu[wy][wx] = mu.v.x;
-                s_mu[wy + 1][wx] = mu.v.y;
-            }
-        }
+        pair_mu<FX, WX, WY, NT>(kp, s_phi, s_p0, s_mu, tid);
         __syncthreads();
 
         // ---------------- stage C: the thread's two cells ----------------
-        const int gx = x0 + lx, gy0 = y0 + ly0;
-        const bool valid0 = gx < nx && gy0 < ny, valid1 = gx < nx && gy0 + 1 < ny;
-        const int wx = lx + 1, wy = ly0 + 1;
-
-        const F2 phi0 = mk2(s_p0[hy][hx], s_p0[hy + 1][hx]);
-        F2 gpx, gpy, gmx, gmy, wgx, wgy;
-        grad9_pair<FX>(s_phi, hx, hy, gpx, gpy);
-        grad9_pair<WX>(s_mu, wx, wy, gmx, gmy);
-        grad9_pair<WX>(s_w, wx, wy, wgx, wgy);
-        const F2 mu = mk2(s_mu[wy][wx], s_mu[wy + 1][wx]);
-        const F2 drho = mk2(kp.drho), half = mk2(0.5f), one = mk2(1.0f), two = mk2(2.0f);
-        const F2 rho = fma2(drho, phi, mk2(kp.rhom));
-        const F2 muv = fma2(mk2(kp.dmu), phi, mk2(kp.mum));
-        const F2 Mdrho = mk2(kp.Mdrho);
-        const F2 Sx = Mdrho * gmx, Sy = Mdrho * gmy;
-        const F2 grx = drho * gpx, gry = drho * gpy;
-        // F = mu grad phi + F_b + F_c, F_c = (-d_y w, d_x w)/2 from the previous step
-        const F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
-        const F2 Fy = fma2(mu, gpy, fma2(half, wgx, mk2(kp.Fb[1])));
-
-        F2 f2[9];
-        const F2 isc2v = mk2(isc2);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const F2 v = P::MIX ? mk2(stored_to_float<ST>(f2raw[0][i]), stored_to_float<ST>(f2raw[1][i]))
-                                : mk2(Conv<P>::ld(f2raw[0][i], 1.0f), Conv<P>::ld(f2raw[1][i], 1.0f));
-            f2[i] = P::MIX ? v * isc2v : v;
-        }
-        // u* (Eq. 36a)
-        const F2 jx = ((f2[1] - f2[3]) + (f2[5] - f2[6])) + (f2[8] - f2[7]);
-        const F2 jy = ((f2[2] - f2[4]) + (f2[5] + f2[6])) - (f2[7] + f2[8]);
-        const F2 irho = mk2(__frcp_rn(rho.v.x), __frcp_rn(rho.v.y));
-        const F2 usx = fma2(half, Fx, jx) * irho, usy = fma2(half, Fy, jy) * irho;
-        // penalty force f = phi0 (u_s - u*) with u_s = 0 (fixed solids)
-        const F2 nphi0 = mk2(0.0f) - phi0;
-        const F2 fpx = nphi0 * usx, fpy = nphi0 * usy;
-        const F2 ux = fma2(half, fpx, usx), uy = fma2(half, fpy, usy);
-        const F2 Ftx = fma2(rho, fpx, Fx), Fty = fma2(rho, fpy, Fy);
-
-        const F2 upx = mk2((float)lag[0][0], (float)lag[1][0]), upy = mk2((float)lag[0][1], (float)lag[1][1]);
-        const F2 Spx = mk2((float)lag[0][2], (float)lag[1][2]), Spy = mk2((float)lag[0][3], (float)lag[1][3]);
-        const F2 php = mk2((float)lag[0][4], (float)lag[1][4]);
-
-        // relaxation rates (Eq. 35, 1 - phi0 bounded below by solid_eps)
-        const float seps = kp.solid_eps;
-        const F2 solid = one - phi0;
-        const F2 solidc = mk2(fmaxf(solid.v.x, seps), fmaxf(solid.v.y, seps));
-        const F2 nu = muv * irho * mk2(__frcp_rn(solidc.v.x), __frcp_rn(solidc.v.y));
-        const F2 inv_s2a = fma2(mk2(kp.two_over_1md0), nu, half);
-        const F2 inv_s2b = fma2(mk2(kp.inv_cs2), nu, half);
-        const F2 Kf = mk2(kp.K);
-        const F2 H = Kf * (mk2(kp.Hc0) - mk2(kp.Hc1) * inv_s2a);
-        // pressure (Eq. 36b)
-        const F2 sum_f = ((f2[1] + f2[2]) + (f2[3] + f2[4])) + ((f2[5] + f2[6]) + (f2[7] + f2[8]));
-        const F2 ugr = fma2(ux, grx, uy * gry);
-        const F2 rus_u = fma2(fma2(rho, ux, mk2(0.0f) - Sx), ux, fma2(rho, uy, mk2(0.0f) - Sy) * uy);
-        const F2 Su = fma2(Sx, ux, Sy * uy), Sup = fma2(Spx, upx, Spy * upy);
-        const F2 dt_term = fma2(two, fma2(ux, Ftx, uy * Fty), Sup - Su);
-        const F2 Pr = mk2(kp.Pfac) *
-                      fma2(Kf * half, dt_term,
-                           fma2(half + H, ugr, fma2(mk2(-kp.w0f * kp.inv_1mcs2), rus_u, sum_f)));
-
-        const F2 cs2 = mk2(kp.cs2), cs4 = mk2(kp.cs4);
-        F2 heq[9], hF[9], nS[9], cF[9];
-        // ---- order-parameter lattice (Eq. 30): Hermite equilibria and source
         {
-            const F2 eta_mu = mk2(kp.eta) * mu;
-            heq[0] = phi;
-            heq[1] = phi * ux;
-            heq[2] = phi * uy;
-            heq[3] = cs2 * (eta_mu - phi);
-            heq[4] = heq[3];
-            heq[8] = cs4 * (phi - eta_mu);
-            hF[1] = heq[1] - php * upx;  // d_t(phi u), explicit Euler
-            hF[2] = heq[2] - php * upy;
-            const float s[9] = {kp.s0, kp.s1phi, kp.s1phi, kp.s2, kp.s2, kp.s2, kp.s3, kp.s3, kp.s4};
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                nS[k] = mk2(-s[k]);
-                cF[k] = mk2(1.0f - 0.5f * s[k]);
-            }
-            // zero equilibria: moments 5, 6, 7; zero sources: 0 and 3..8
-            collide9_pair<(1u << 5) | (1u << 6) | (1u << 7), 0x1F9u>(f1, heq, hF, nS, cF, cs2, cs4);
-        }
-        // ---- flow lattice (Eqs. 32-34)
-        {
-            const F2 rux = rho * ux, ruy = rho * uy;
-            heq[1] = rux;
-            heq[2] = ruy;
-            heq[3] = Pr + (rux - Sx) * ux;
-            heq[4] = Pr + (ruy - Sy) * uy;
-            heq[5] = rux * uy - half * fma2(Sx, uy, ux * Sy);
-            heq[8] = (mk2(0.0f) - cs2) * Pr;
-            const F2 c3 = one - mk2(3.0f) * cs2;
-            const F2 tcs2 = two * cs2;
-            hF[0] = ugr;
-            hF[1] = Ftx;
-            hF[2] = Fty;
-            hF[3] = fma2(two * ux, Ftx, fma2(tcs2 * ux, grx, fma2(c3, ugr, Spx * upx - Sx * ux)));
-            hF[4] = fma2(two * uy, Fty, fma2(tcs2 * uy, gry, fma2(c3, ugr, Spy * upy - Sy * uy)));
-            hF[5] = fma2(ux, Fty, Ftx * uy) -
-                    half * (fma2(Sx, uy, ux * Sy) - fma2(Spx, upy, upx * Spy)) + cs2 * fma2(ux, gry, grx * uy);
-            const F2 s2a = mk2(__frcp_rn(inv_s2a.v.x), __frcp_rn(inv_s2a.v.y));
-            const F2 s2b = mk2(__frcp_rn(inv_s2b.v.x), __frcp_rn(inv_s2b.v.y));
-            nS[0] = mk2(-kp.s0);
-            nS[1] = nS[2] = mk2(-kp.s1);
-            nS[3] = nS[4] = mk2(0.0f) - s2a;
-            nS[5] = mk2(0.0f) - s2b;
-            nS[6] = nS[7] = mk2(-kp.s3);
-            nS[8] = mk2(-kp.s4);
-            cF[0] = mk2(1.0f - 0.5f * kp.s0);
-            cF[1] = cF[2] = mk2(1.0f - 0.5f * kp.s1);
-            cF[3] = cF[4] = fma2(mk2(-0.5f), s2a, one);
-            cF[5] = fma2(mk2(-0.5f), s2b, one);
-            // zero equilibria: moments 0, 6, 7; zero sources: 6, 7, 8
-            collide9_pair<(1u << 0) | (1u << 6) | (1u << 7), (1u << 6) | (1u << 7) | (1u << 8)>(f2, heq, hF, nS,
-                                                                                               cF, cs2, cs4);
-        }
-
-        // ---------------- stores (per cell) ----------------
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (!(c == 0 ? valid0 : valid1)) continue;
-            const int idc = id[c];
-            const float phic = c == 0 ? phi.v.x : phi.v.y;
-            const float uxc = c == 0 ? ux.v.x : ux.v.y, uyc = c == 0 ? uy.v.x : uy.v.y;
-            if constexpr (P::MIX) {
-                const float sc1 = kp.scale[0];
-                int bad = 0, sold = 0, snew = 0;
-#pragma unroll
-                for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[c][i]);
-#pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    ST q = Conv<P>::st(c == 0 ? f1[i].v.x : f1[i].v.y, sc1);
-                    if constexpr (P::id == 3) q = bf16_flush(q);
-                    snew += fix24_sat<ST>(q, &bad);
-                    fd[i * plane + idc] = q;
-                }
-                // exact: sum of the cell's order-parameter populations is unchanged
-                rd[idc] = rest_own[c] + fix24_to_rest(sold - snew, p.klog2[0]);
-                if (bad) atomicOr(A.flags, 2);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) fd[i * plane + idc] = Conv<P>::st(c == 0 ? f1[i].v.x : f1[i].v.y, 1.0f);
-            }
-            const float sc2 = P::MIX ? kp.scale[1] : 1.0f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) fd[(9 + i) * plane + idc] = Conv<P>::st(c == 0 ? f2[i].v.x : f2[i].v.y, sc2);
-            // fields of this step, read as the previous step's by the next one
-            ad[0 * plane + idc] = (AX)uxc;
-            ad[1 * plane + idc] = (AX)uyc;
-            ad[2 * plane + idc] = (AX)(c == 0 ? Sx.v.x : Sx.v.y);
-            ad[3 * plane + idc] = (AX)(c == 0 ? Sy.v.x : Sy.v.y);
-            ad[4 * plane + idc] = (AX)phic;
-            if (!isfinite(phic) || !isfinite(uxc) || !isfinite(uyc)) atomicOr(A.flags, 1);
+            const int gx = x0 + lx, gy0 = y0 + ly0;
+            const bool valid0 = gx < nx && gy0 < ny, valid1 = gx < nx && gy0 + 1 < ny;
+            pair_cells<P, FX, WX>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, q1,
+                                  rest_own, id, valid0, valid1, fd, rd, ad, plane);
         }
     }
 }

@@ -5,6 +5,7 @@
 #include "pf_internal.h"
 #include "pf_kernels2d.cuh"
 #include "pf_kernels2d_pair.cuh"
+#include "pf_kernels2d_stage.cuh"
 
 namespace pf {
 
@@ -54,6 +55,40 @@ static bool dispatch2d_pair(int tx, int ty, bool moving, int grid, cudaStream_t 
     }
 }
 
+template <class P, int TX, int TYP>
+static bool run2d_stage(int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    auto kern = k_step2d_stage<P, TX, TYP>;
+    const int dyn = StageLayout<P, TX, 2 * TYP>::BYTES;
+    static bool attr = false;  // set once per instantiation (process-wide, any device)
+    if (!attr) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return false;
+        attr = true;
+    }
+    if (occ) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TYP, dyn) != cudaSuccess) n = 0;
+        *occ = n;
+        return true;
+    }
+    kern<<<grid, TX * TYP, dyn, s>>>(a);
+    count_launches(1);
+    return true;
+}
+
+// two cells per thread, inputs staged by bulk copies
+template <class P>
+static bool dispatch2d_stage(int tx, int ty, bool moving, int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    if constexpr (P::id == 0) {
+        return false;
+    } else {
+        if (moving) return false;
+        if (tx == 32 && ty == 16) return run2d_stage<P, 32, 8>(grid, s, a, occ);
+        return false;
+    }
+}
+
 template <class P>
 static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
                        const StepArgs &a, int *occ)
@@ -67,6 +102,7 @@ static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStre
                       : run2d<P, TX, TY, false, MODE_STEP>(grid, s, a, occ);              \
     }
     if (mode == MODE_STEP_PAIR) return dispatch2d_pair<P>(tx, ty, moving, grid, s, a, occ);
+    if (mode == MODE_STEP_STAGE) return dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
     if (mode == MODE_MACROS) {
         if (tx == 32 && ty == 8)
             return moving ? run2d<P, 32, 8, true, MODE_MACROS>(grid, s, a, occ)

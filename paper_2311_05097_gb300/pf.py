@@ -220,10 +220,9 @@ class Sim:
         keep = [_ptr(a, where) for a in (phi0, phi, u, P)]
         _check(load().pf_init_fields(self._h, *[k[0] for k in keep], where))
 
-    def set_config(self, tile_x, tile_y, cells_per_thread=1, ctas_per_sm=0):
-        """Fix the launch configuration (after init)."""
-        _check(load().pf_set_config(self._h, int(tile_x), int(tile_y), int(cells_per_thread),
-                                    int(ctas_per_sm)))
+    def set_config(self, tile_x, tile_y, kernel=0, ctas_per_sm=0):
+        """Fix the launch configuration (after init); kernel 0, 1 or 2 as in pf.h."""
+        _check(load().pf_set_config(self._h, int(tile_x), int(tile_y), int(kernel), int(ctas_per_sm)))
 
     def step(self, n=1):
         _check(load().pf_step(self._h, int(n)))
@@ -299,14 +298,13 @@ class Batch:
         return int(load().pf_batch_cells(self._h))
 
     def config(self):
-        """(tile_x, tile_y, ctas_per_sm, cells_per_thread) of the step launches."""
+        """(tile_x, tile_y, ctas_per_sm, kernel) of the step launches."""
         a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check(load().pf_batch_config(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
         return a.value, b.value, c.value, d.value
 
-    def set_config(self, tile_x, tile_y, cells_per_thread=1, ctas_per_sm=0):
-        _check(load().pf_batch_set_config(self._h, int(tile_x), int(tile_y), int(cells_per_thread),
-                                          int(ctas_per_sm)))
+    def set_config(self, tile_x, tile_y, kernel=0, ctas_per_sm=0):
+        _check(load().pf_batch_set_config(self._h, int(tile_x), int(tile_y), int(kernel), int(ctas_per_sm)))
 
     def macros(self, i):
         sh = self.shapes[i]

@@ -166,13 +166,14 @@ def test_pmix_against_oracle(pf, precision, tol_phi):
 
 # ---- two cells per thread (packed FP32 arithmetic) ---------------------------------------
 
-@pytest.mark.parametrize("tile", [(32, 16), (64, 8), (32, 32)])
+@pytest.mark.parametrize("tile,kernel", [((32, 16), 1), ((64, 8), 1), ((32, 32), 1), ((32, 16), 2)])
 @pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
-def test_pair_step_against_oracle(pf, precision, tol_phi, tile):
-    """The two-cells-per-thread step on a ragged grid (52 x 37: partial tiles
-    in x and y, and an odd row count so the last pair has one valid cell)."""
-    c = W.small_case((37, 52), seed=7, solid=True, theta_deg=60.0, u_amp=0.01)
-    g, o = run_pair(pf, c, 200, precision=precision, config=(tile[0], tile[1], 2))
+def test_pair_step_against_oracle(pf, precision, tol_phi, tile, kernel):
+    """The two-cells-per-thread steps on a ragged grid (56 x 37: partial tiles
+    in x and y, and an odd row count so the last pair has one valid cell;
+    nx a multiple of 8 for the staged kernel)."""
+    c = W.small_case((37, 56), seed=7, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 200, precision=precision, config=(tile[0], tile[1], kernel))
     gm, om = g.macros(), o.macros()
     assert rel(gm["phi"], om["phi"]) < tol_phi
     if precision == "p32":
@@ -182,10 +183,11 @@ def test_pair_step_against_oracle(pf, precision, tol_phi, tile):
     assert g.diagnostics()["nan_flag"] == 0
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
-def test_pair_step_conserves_mass_exactly(pf, precision):
+def test_pair_step_conserves_mass_exactly(pf, precision, kernel):
     c = W.small_case((80, 64), seed=4, solid=True, theta_deg=60.0, u_amp=0.01)
-    g, _ = run_pair(pf, c, 0, precision=precision, oracle=False, config=(32, 16, 2))
+    g, _ = run_pair(pf, c, 0, precision=precision, oracle=False, config=(32, 16, kernel))
     m0 = g.diagnostics()["mass"]
     g.step(1000)
     m1 = g.diagnostics()["mass"]
@@ -193,13 +195,14 @@ def test_pair_step_conserves_mass_exactly(pf, precision):
 
 
 def test_pair_and_single_agree_p32(pf):
-    """Both launch variants compute the same FP32 update (to rounding order)."""
+    """All launch variants compute the same FP32 update (to rounding order)."""
     c = W.small_case((64, 96), seed=5, solid=True, theta_deg=120.0, rho_ratio=10.0)
-    a, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 8, 1))
-    b, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 16, 2))
-    ma, mb = a.macros(), b.macros()
-    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
-        assert rel(mb[k], ma[k]) < tol, k
+    a, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 8, 0))
+    for kernel in (1, 2):
+        b, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 16, kernel))
+        ma, mb = a.macros(), b.macros()
+        for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+            assert rel(mb[k], ma[k]) < tol, (kernel, k)
 
 
 def test_config_override_rejects_unbuilt(pf):
@@ -207,10 +210,15 @@ def test_config_override_rejects_unbuilt(pf):
     g = pf.Sim(c["shape"], precision="p64", **c["params"])
     g.init(c["phi0"], c["phi"])
     with pytest.raises(pf.PfError) as ei:
-        g.set_config(32, 16, 2)  # no packed arithmetic in FP64
+        g.set_config(32, 16, 1)  # no packed arithmetic in FP64
     assert ei.value.code == pf.PF_EINVAL
     with pytest.raises(pf.PfError):
-        g.set_config(48, 8, 1)
+        g.set_config(48, 8, 0)
+    c = W.small_case((32, 52), seed=1, solid=False)  # nx = 52: not a multiple of 8
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(32, 16, 2)
 
 
 def test_nan_is_reported(pf):
