@@ -171,12 +171,18 @@ def read_peaks():
         return {}
 
 
-def read_traffic(key):
+def read_traffic(key, config=None):
+    """DRAM bytes per launch recorded under profiles/ for this workload and
+    precision, or None when there is none or it was taken for another launch
+    configuration than the one timed."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        return json.load(open(path)).get(key, {}).get("bytes_per_launch")
+        ent = json.load(open(path)).get(key, {})
     except Exception:
         return None
+    if config is not None and ent.get("config") is not None and list(ent["config"]) != list(config):
+        return None
+    return ent.get("bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -363,7 +369,8 @@ def run_batch(args, dist, rank, world, local):
            "tile": [tx, ty], "ctas_per_sm": cps, "cells_per_thread": cpt,
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
-                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel="k_step2d")
+                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall,
+                kernel="k_step2d_pair" if cpt else "k_step2d", launch_config=[tx, ty, cpt])
 
 
 def run_single(args, dist, rank, world, local):
@@ -458,7 +465,8 @@ def run_single(args, dist, rank, world, local):
                  "write-back happens outside the timed step",
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
-                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel="k_step2d")
+                clk=clk, launches=launches, e2e=e2e, t_wall=t_wall,
+                kernel="k_step3d" if dim == 3 else "k_step2d")
 
 
 def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream):
@@ -560,7 +568,7 @@ def run_ours(args):
         "dtype": DTYPE[r["prec"]], "data": "synthetic", "config": r["cfg"],
         "roofline": {"bound": "hbm", "achieved": round(r["achieved"], 1), "peak": peak,
                      "unit": "GB/s", "frac": round(r["achieved"] / peak, 4),
-                     "traffic": read_traffic("%s/%s" % (args.workload, r["prec"])),
+                     "traffic": read_traffic("%s/%s" % (args.workload, r["prec"]), r.get("launch_config")),
                      "bytes_per_cell": r["bpc"], "kernel": r["kernel"], "peak_source": peak_src},
         "clocks": r["clk"], "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
         "wall_s": round(r["t_wall"], 3),
