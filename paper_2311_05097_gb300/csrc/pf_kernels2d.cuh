@@ -257,6 +257,14 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         R f1[9];
         ST q1[9];
         const R phi_own = phi_at(lx + 2, ly + 2, f1, q1);
+        // PMIX: the cell's exact fixed-point phi; the pulled movers are dead after this
+        [[maybe_unused]] long long racc = 0;
+        if constexpr (P::MIX) {
+            int sold = 0;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[i]);
+            racc = rest_own + fix24_to_rest(sold, p.klog2[0]);
+        }
         s_phi[ly + 2][lx + 2] = phi_own;
         s_p0[ly + 2][lx + 2] = phi0_at(lx + 2, ly + 2);
         constexpr int RING = 4 * (TX + 4) + 4 * TY;
@@ -433,13 +441,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const long long N = (long long)nx * ny;
                 const long long o = (long long)gy * nx + gx;
                 double phv = (double)phi;
-                if constexpr (P::MIX) {
-                    int sold = 0;
-#pragma unroll
-                    for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[i]);
-                    const long long acc = rest_own + fix24_to_rest(sold, p.klog2[0]);
-                    phv = double_of_fixed(acc);
-                }
+                if constexpr (P::MIX) phv = double_of_fixed(racc);
                 Dm.macro[0 * N + o] = phv;
                 Dm.macro[1 * N + o] = (double)rho;
                 Dm.macro[2 * N + o] = (double)ux;
@@ -509,9 +511,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 if constexpr (P::MIX) {
                     const R sc1 = kp.scale[0];
                     const int k1 = p.klog2[0];
-                    int bad = 0, sold = 0, snew = 0;
-#pragma unroll
-                    for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[i]);
+                    int bad = 0, snew = 0;
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
                         ST q = Conv<P>::st(f1[i], sc1);
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                         fd[i * plane + id] = q;
                     }
                     // exact: sum of the cell's order-parameter populations is unchanged
-                    rd[id] = rest_own + fix24_to_rest(sold - snew, k1);
+                    rd[id] = racc - fix24_to_rest(snew, k1);
                     if (bad) atomicOr(A.flags, 2);
                 } else {
 #pragma unroll

@@ -171,7 +171,8 @@ __device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*
 
 // Stage C of the pair step: the update of the thread's two cells (Eqs. 29-38)
 // from the shared tiles (phi, phi0 on tile + 2 at (hx, hy); mu, w on tile + 1
-// at (wx, wy)) and the values gathered in stage A, then their stores.
+// at (wx, wy)) and the values gathered in stage A, then their stores.  racc:
+// PMIX, each cell's exact fixed-point phi (rest + images of the pulled movers).
 template <class P, int FX, int WX>
 __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p, const KParams<float> &kp,
                                            const float (*s_phi)[FX], const float (*s_p0)[FX],
@@ -179,8 +180,7 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
                                            int wx, int wy, F2 phi, F2 (&f1)[9],
                                            const typename P::store (&f2raw)[2][9],
                                            const typename P::aux (&lag)[2][5],
-                                           const typename P::store (&q1)[2][9], const long long (&rest_own)[2],
-                                           const int (&id)[2], bool valid0, bool valid1, typename P::store *fd,
+                                           const long long (&racc)[2], const int (&id)[2], bool valid0, bool valid1, typename P::store *fd,
                                            long long *rd, typename P::aux *ad, int plane)
 {
     using ST = typename P::store;
@@ -310,9 +310,7 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
         const float uxc = c == 0 ? ux.v.x : ux.v.y, uyc = c == 0 ? uy.v.x : uy.v.y;
         if constexpr (P::MIX) {
             const float sc1 = kp.scale[0];
-            int bad = 0, sold = 0, snew = 0;
-#pragma unroll
-            for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[c][i]);
+            int bad = 0, snew = 0;
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 ST q = Conv<P>::st(c == 0 ? f1[i].v.x : f1[i].v.y, sc1);
@@ -321,7 +319,7 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
                 fd[i * plane + idc] = q;
             }
             // exact: sum of the cell's order-parameter populations is unchanged
-            rd[idc] = rest_own[c] + fix24_to_rest(sold - snew, p.klog2[0]);
+            rd[idc] = racc[c] - fix24_to_rest(snew, p.klog2[0]);
             if (bad) atomicOr(A.flags, 2);
         } else {
 #pragma unroll
@@ -454,6 +452,17 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
                 phi = acc;
             }
         }
+        // PMIX: the cells' exact fixed-point phi; the pulled movers are dead after this
+        long long racc[2] = {0, 0};
+        if constexpr (P::MIX) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                int sold = 0;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[c][i]);
+                racc[c] = rest_own[c] + fix24_to_rest(sold, p.klog2[0]);
+            }
+        }
         const int hx = lx + 2, hy = ly0 + 2;
         s_phi[hy][hx] = phi.v.x;
         s_phi[hy + 1][hx] = phi.v.y;
@@ -509,8 +518,8 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
         {
             const int gx = x0 + lx, gy0 = y0 + ly0;
             const bool valid0 = gx < nx && gy0 < ny, valid1 = gx < nx && gy0 + 1 < ny;
-            pair_cells<P, FX, WX>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, q1,
-                                  rest_own, id, valid0, valid1, fd, rd, ad, plane);
+            pair_cells<P, FX, WX>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, racc,
+                                  id, valid0, valid1, fd, rd, ad, plane);
         }
     }
 }

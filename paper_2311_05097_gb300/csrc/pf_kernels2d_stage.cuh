@@ -272,6 +272,17 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
                 phi = acc;
             }
         }
+        // PMIX: the cells' exact fixed-point phi; the pulled movers are dead after this
+        long long racc[2] = {0, 0};
+        if constexpr (P::MIX) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                int sold = 0;
+#pragma unroll
+                for (int i = 1; i < 9; ++i) sold += fix24_stored<ST>(q1[c][i]);
+                racc[c] = rest_own[c] + fix24_to_rest(sold, p.klog2[0]);
+            }
+        }
         const int hx = lx + 2, hy = ly0 + 2;
         s_phi[hy][hx] = phi.v.x;
         s_phi[hy + 1][hx] = phi.v.y;
@@ -319,8 +330,8 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
         {
             const int gx = x0 + lx, gy0 = y0 + ly0;
             const bool valid0 = gx < nx && gy0 < ny, valid1 = gx < nx && gy0 + 1 < ny;
-            pair_cells<P, FX, WX>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, q1,
-                                  rest_own, id, valid0, valid1, fd, rd, ad, plane);
+            pair_cells<P, FX, WX>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, racc,
+                                  id, valid0, valid1, fd, rd, ad, plane);
         }
     }
 }
