@@ -81,3 +81,28 @@ def constant_force_velocity(u0, A, beta, n):
 def constant_force_position(x0, u0, A, beta, n):
     """x^n = x^0 + sum_{m<n} u^m for the velocities of ``constant_force_velocity``."""
     return x0 + sum(constant_force_velocity(u0, A, beta, m) for m in range(n))
+
+
+def bond_number(rho_p, rho_f, Rp, g, sigma):
+    """Bo = (rho_p - rho_f) R_p^2 |g| / sigma (Sec. 4.4)."""
+    return (rho_p - rho_f) * Rp * Rp * g / sigma
+
+
+def particle_interface_height(L, Rp, theta_deg, Bo):
+    """Equilibrium of one wetting particle (2D disc) trapped at a fluid-fluid
+    interface of equal densities under gravity, in a periodic box of width L
+    (Sec. 4.4, after Mino et al.): the interface slope alpha at the contact
+    point solves L/2 = R_p sin(theta - alpha) + L/(pi Bo) sin(alpha), and the
+    downward distance from the far interface (at the box edge) to the particle
+    centre is h = R_p cos(theta - alpha) + L/(pi Bo) (1 - cos(alpha)).
+    Bo -> 0 gives alpha -> 0 and h -> R_p cos(theta).  Returns (h, alpha)."""
+    th = math.radians(theta_deg)
+    if Bo == 0.0:
+        return Rp * math.cos(th), 0.0
+    c = L / (math.pi * Bo)
+
+    def f(a):
+        return Rp * math.sin(th - a) + c * math.sin(a) - 0.5 * L
+
+    a = optimize.brentq(f, -0.5 * math.pi + 1e-12, 0.5 * math.pi - 1e-12, xtol=1e-15, rtol=1e-15)
+    return Rp * math.cos(th - a) + c * (1.0 - math.cos(a)), a

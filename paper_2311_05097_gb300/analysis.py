@@ -127,3 +127,14 @@ def information_entropy(phi, bins=20, lo=-1.0, hi=1.0):
     p = h / h.sum()
     p = p[p > 0]
     return float(-(p * np.log2(p)).sum())
+
+
+def interface_level(phi, x, y_lo, y_hi):
+    """Height of the phi = 0 crossing (phase 1 below, phase 2 above) in column
+    x between rows y_lo and y_hi, by linear interpolation; NaN if none."""
+    col = np.asarray(phi)[y_lo:y_hi, x]
+    idx = np.where((col[:-1] > 0) & (col[1:] <= 0))[0]
+    if len(idx) == 0:
+        return float("nan")
+    i = idx[0]
+    return float(y_lo + i + col[i] / (col[i] - col[i + 1]))

@@ -215,6 +215,27 @@ def water_entry(nx=1024, ny=2048, depth=800, wall=8, R=40.0, gap=200.0, D=4.0):
                 name="water_entry_2d")
 
 
+def particle_balance(L=256, Rp=32.0, theta_deg=90.0, rho_p=1.1, sigma=0.01, g=2e-5, wall=8, D=4.0, M=0.1):
+    """One free disc (radius Rp, density rho_p) half immersed at the flat
+    interface between two fluids of equal density (rho_f = 1) in a box of
+    width L, periodic in x, with wall slabs of ``wall`` cells below and above
+    (Sec. 4.4 layout; sigma and g scaled together from the paper's 0.001 and
+    2e-6, which keeps the Bond number and shortens the relaxation 10x).
+    Gravity acts on the particle only."""
+    ny = L + 2 * wall
+    shape = (ny, L)
+    phi0 = slab_walls(shape, wall, D, axis=1)
+    y_if = ny / 2.0
+    particle = dict(x=(L / 2.0, y_if, 0.0), u=(0.0, 0.0, 0.0), w=(0.0, 0.0, 0.0), R=Rp, rho_p=rho_p)
+    ind = disc(shape, particle["x"], Rp, D)
+    y = _coords(shape)[1]
+    phi = (1.0 - phi0 - ind) * np.tanh(2.0 * (y_if - y) / D)
+    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, theta_deg=theta_deg,
+               g=(0.0, -g, 0.0))
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=[particle], L=L, Rp=Rp,
+                rho_f=1.0, sigma=sigma, g=g, y_if=y_if, name="particle_balance_2d")
+
+
 def equal_area_cap_base(theta_deg, area):
     """Radius and base half-width of a circular cap of given area on a flat wall."""
     th = math.radians(theta_deg)

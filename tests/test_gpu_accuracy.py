@@ -154,3 +154,25 @@ def test_water_entry_bf16_against_fp64(pf):
            u_bf16=p16["u"], max_dx=dx, max_du=du)
     assert s64.diagnostics()["nan_flag"] == 0
     assert dx < 0.05 and du < 1e-3
+
+
+@pytest.mark.parametrize("theta,rho_p,tol", [(90.0, 1.1, 0.05), (90.0, 1.25, 0.05), (60.0, 1.1, 0.10)])
+def test_particle_balance_at_interface(pf, theta, rho_p, tol):
+    """One free wetting disc at a fluid-fluid interface under gravity (Sec. 4.4:
+    L = 256, R_p = 32, equal fluid densities): after relaxation the downward
+    distance h from the far interface (box edge) to the particle centre
+    matches the closed form of Sec. 4.4 for the Bond number of the run."""
+    c = W.particle_balance(theta_deg=theta, rho_p=rho_p)
+    part = dict(c["particles"][0])
+    s = run(pf, c, 400000, "p32", particles=[part])
+    pp = s.particle(0)
+    m = s.macros()
+    wall = 8
+    y_if = A.interface_level(m["phi"], 0, wall, c["shape"][0] - wall)
+    h = y_if - pp["x"][1]
+    Bo = CF.bond_number(rho_p, c["rho_f"], c["Rp"], c["g"], c["sigma"])
+    h_th, alpha = CF.particle_interface_height(c["L"], c["Rp"], theta, Bo)
+    record("particle_balance", theta=theta, rho_p=rho_p, Bo=Bo, steps=400000, h=h, h_closed_form=h_th,
+           alpha=alpha, x=pp["x"], u=pp["u"])
+    assert s.diagnostics()["nan_flag"] == 0
+    assert abs(h - h_th) <= tol * abs(h_th), (h, h_th)

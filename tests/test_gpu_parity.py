@@ -221,6 +221,26 @@ def test_config_override_rejects_unbuilt(pf):
         g.set_config(32, 16, 2)
 
 
+def test_particle_balance_full_size_against_oracle(pf):
+    """The wetting particle at a fluid interface (256 x 272, gravity on the
+    particle, wall slabs) in FP64 against the oracle: fields and the
+    particle's state after 30 steps at full size."""
+    c = W.particle_balance(theta_deg=60.0, rho_p=1.1)
+    part = dict(c["particles"][0])
+    g, o = run_pair(pf, c, 30, particles=[part])
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["sigma"] / 4.0)
+    pg, po = g.particle(0), o.particle(0)
+    for k in ("x", "u", "F"):
+        a, b = np.array(pg[k]), np.array(getattr(po, k))
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, a, b)
+    # the setup is mirror-symmetric: rotation and torque are round-off noise,
+    # measured against the translational scales (u / R, |F| R)
+    R = c["Rp"]
+    u_s, F_s = np.abs(po.u).max(), np.abs(po.F).max()
+    assert np.abs(np.array(pg["w"]) - np.array(po.w)).max() <= 1e-12 * u_s / R
+    assert np.abs(np.array(pg["T"]) - np.array(po.T)).max() <= 1e-12 * F_s * R
+
+
 def test_nan_is_reported(pf):
     c = W.small_case((32, 32), seed=1, solid=False)
     phi = c["phi"].copy()

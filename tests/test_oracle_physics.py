@@ -254,3 +254,23 @@ def test_hmax_solver_geometry():
     # a more wetting drop is flatter
     hs = [CF.hmax_on_cylinder(t, Rp, A0)[0] for t in (30.0, 60.0, 90.0, 120.0)]
     assert all(a < b for a, b in zip(hs, hs[1:]))
+
+
+def test_particle_interface_height_limits():
+    """Sec. 4.4 closed form: a neutrally buoyant particle (Bo -> 0) sits at
+    h = R_p cos(theta) (its contact line at the flat interface), and the
+    problem is antisymmetric under swapping the phases and the sign of gravity:
+    h(theta, -Bo) = -h(180 - theta, Bo)."""
+    L, Rp = 256, 32.0
+    for th in (45.0, 60.0, 90.0, 120.0):
+        h, a = CF.particle_interface_height(L, Rp, th, 1e-9)
+        assert abs(h - Rp * math.cos(math.radians(th))) < 1e-5 and abs(a) < 1e-6
+        for Bo in (0.1, 0.3, 0.5):
+            hp, ap = CF.particle_interface_height(L, Rp, th, Bo)
+            hm, am = CF.particle_interface_height(L, Rp, 180.0 - th, -Bo)
+            assert abs(hp + hm) < 1e-9 and abs(ap + am) < 1e-12
+    # heavier particles sit lower; more wetting (smaller theta) pulls them into phase 1
+    hs = [CF.particle_interface_height(L, Rp, 90.0, Bo)[0] for Bo in (0.1, 0.2, 0.4)]
+    assert hs[0] < hs[1] < hs[2]
+    hs = [CF.particle_interface_height(L, Rp, th, 0.2)[0] for th in (120.0, 90.0, 60.0)]
+    assert hs[0] < hs[1] < hs[2]
