@@ -20,6 +20,7 @@ class OrcParams(C.Structure):
         ("d0", C.c_double), ("s0", C.c_double), ("s1", C.c_double), ("s2", C.c_double),
         ("s3", C.c_double), ("s4", C.c_double), ("theta_deg", C.c_double),
         ("Fb", C.c_double * 3), ("g", C.c_double * 3), ("solid_eps", C.c_double),
+        ("rep_xi", C.c_double), ("rep_eps", C.c_double),
     ]
 
 
@@ -29,6 +30,7 @@ class OrcParticle(C.Structure):
         ("R", C.c_double), ("rho_p", C.c_double),
         ("u_prev", C.c_double * 3), ("w_prev", C.c_double * 3),
         ("F", C.c_double * 3), ("T", C.c_double * 3),
+        ("theta_deg", C.c_double),
     ]
 
 
@@ -76,6 +78,8 @@ def lib():
         L.orc_particle_update.argtypes = [C.c_int, C.POINTER(OrcParams), C.POINTER(OrcParticle),
                                           _DP, _DP]
         L.orc_particle_force.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
+        L.orc_repulsion.argtypes = [C.c_int, C.POINTER(OrcParams), _IP, C.c_int,
+                                    C.POINTER(OrcParticle), _DP]
         _lib = L
     return _lib
 
@@ -99,7 +103,7 @@ def make_params(**kw):
     """Oracle parameters from keyword arguments (paper defaults for the rest)."""
     d = dict(sigma=0.01, D=4.0, M=0.02, eta=0.0, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
              d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, theta_deg=90.0,
-             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3)
+             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0)
     d.update(kw)
     p = OrcParams()
     for k, v in d.items():
@@ -114,7 +118,8 @@ def make_params(**kw):
 class Particle:
     """Plain particle record (FP64) mirroring the oracle's struct."""
 
-    def __init__(self, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0):
+    def __init__(self, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0, theta_deg=None):
+        self.theta_deg = float("nan") if theta_deg is None else float(theta_deg)
         self.x = list(x) + [0.0] * (3 - len(x))
         self.u = list(u) + [0.0] * (3 - len(u))
         self.w = list(w) + [0.0] * (3 - len(w))
@@ -130,11 +135,13 @@ class Particle:
         for k in ("x", "u", "w", "u_prev", "w_prev", "F", "T"):
             setattr(c, k, (C.c_double * 3)(*getattr(self, k)))
         c.R, c.rho_p = self.R, self.rho_p
+        c.theta_deg = self.theta_deg
         return c
 
     @classmethod
     def from_c(cls, c):
         p = cls(list(c.x), list(c.u), list(c.w), c.R, c.rho_p)
+        p.theta_deg = c.theta_deg
         p.u_prev, p.w_prev = list(c.u_prev), list(c.w_prev)
         p.F, p.T = list(c.F), list(c.T)
         return p
@@ -303,6 +310,15 @@ def particle_update(dim, params, part, Ff, Tf):
     c = part.to_c()
     lib().orc_particle_update(dim, C.byref(params), C.byref(c), _p(_arr(Ff, 3)), _p(_arr(Tf, 3)))
     return Particle.from_c(c)
+
+
+def repulsion(dim, params, n, parts):
+    """Repulsion force on each particle (np x 3), reading R19."""
+    arr = (OrcParticle * max(len(parts), 1))(*[q.to_c() for q in parts])
+    nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    out = np.zeros(3 * max(len(parts), 1))
+    lib().orc_repulsion(dim, C.byref(params), nn, len(parts), arr, _p(out))
+    return out[:3 * len(parts)].reshape(len(parts), 3)
 
 
 def num_threads():

@@ -40,6 +40,21 @@
  *       (a != b); M_H rows are tensor Hermite polynomials of the velocities; the
  *       viscosity relation of Eq. (35) and the 3D K, H of Sec. 3.2 are used as
  *       printed.
+ *   R18 particles with their own contact angle theta_k (Sec. 4.5): the wetting
+ *       terms of Eqs. (8), (9), (19) are summed over solids, each with its own
+ *       angle; every solid without an own angle (the fixed field and such
+ *       particles) forms one solid with the simulation's theta.  The penalty
+ *       term keeps the total phi0.  Writing W = sum_s cos(theta_s) phi0_s and
+ *       V = sum_s cos(theta_s) phi0_s^3, the wetting part of mu_phi is
+ *       3 sigma/D (3 phi^2 W + V - W) - 3 D sigma/8 lap W, and the particle force
+ *       sum_s mu_phi0,s grad phi0_s is 9 sigma/D phi0 phi^2 grad phi0 +
+ *       3 sigma/D [phi (phi^2 - 1) grad W + phi grad V] - 3 D sigma/8 lap(phi) grad W
+ *       (the phi0_s^2 grad phi0_s terms discretised as grad V / 3).
+ *   R19 particle-particle repulsion of Sec. 4.5 as printed: (x_k - x_j)/eps times
+ *       (R_k + R_j + xi - d)^2 for R_k + R_j <= d <= R_k + R_j + xi, times
+ *       (R_k + R_j - d) for d <= R_k + R_j, zero beyond (minimum image), added to
+ *       the force of Eq. (26a) from the positions before the update.  The
+ *       particle-wall form needs a wall geometry and is not built.
  */
 #include "pf_oracle.h"
 
@@ -76,6 +91,8 @@ struct orc_sim {
     double *phi, *rho, *muv, *lap_phi, *lap_phi0, *mu, *mu0;
     double *gphi, *gphi0, *gmu, *S, *grho, *Fc, *F, *ustar, *fpen, *u, *Ftot;
     double *s2a, *s2b, *P, *tmp, *tmp3;
+    /* R18: angle-weighted indicators and their stencils */
+    double *wfld, *vfld, *lap_w, *gw, *gv;
 };
 
 int orc_num_threads(void)
@@ -520,6 +537,32 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp, const d
     }
 }
 
+/* Reading R19: particle-particle repulsion of Sec. 4.5 on each particle. */
+void orc_repulsion(int dim, const orc_params *p, const int *n, int np, const orc_particle *parts,
+                   double *out)
+{
+    for (int k = 0; k < np; ++k) {
+        for (int a = 0; a < 3; ++a) out[3 * k + a] = 0.0;
+        if (!(p->rep_eps > 0.0)) continue;
+        for (int j = 0; j < np; ++j) {
+            if (j == k) continue;
+            double dx[3], d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double v = a < dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
+                if (a < dim) v -= n[a] * floor(v / n[a] + 0.5);
+                dx[a] = v;
+                d2 += v * v;
+            }
+            const double dist = sqrt(d2), rr = parts[k].R + parts[j].R;
+            double f;
+            if (dist > rr + p->rep_xi) f = 0.0;
+            else if (dist >= rr) f = (rr + p->rep_xi - dist) * (rr + p->rep_xi - dist) / p->rep_eps;
+            else f = (rr - dist) / p->rep_eps;
+            for (int a = 0; a < 3; ++a) out[3 * k + a] += f * dx[a];
+        }
+    }
+}
+
 /* minimum-image offset x - x_p on the periodic box */
 static void rel_pos(const orc_sim *s, long x, long y, long z, const double *xp, double *r)
 {
@@ -606,6 +649,11 @@ orc_sim *orc_create(int dim, int nx, int ny, int nz, const orc_params *p)
     s->P = zalloc(N);
     s->tmp = zalloc(N);
     s->tmp3 = zalloc(3 * N);
+    s->wfld = zalloc(N);
+    s->vfld = zalloc(N);
+    s->lap_w = zalloc(N);
+    s->gw = zalloc(3 * N);
+    s->gv = zalloc(3 * N);
     return s;
 }
 
@@ -615,26 +663,52 @@ void orc_destroy(orc_sim *s)
     double *bufs[] = {s->f1,  s->g1,   s->f2,   s->g2,   s->phi0_fixed, s->phi0, s->u_prev,
                       s->phi_prev, s->S_prev, s->phi, s->rho, s->muv, s->lap_phi, s->lap_phi0,
                       s->mu,  s->mu0,  s->gphi, s->gphi0, s->gmu, s->S, s->grho, s->Fc, s->F,
-                      s->ustar, s->fpen, s->u, s->Ftot, s->s2a, s->s2b, s->P, s->tmp, s->tmp3};
+                      s->ustar, s->fpen, s->u, s->Ftot, s->s2a, s->s2b, s->P, s->tmp, s->tmp3,
+                      s->wfld, s->vfld, s->lap_w, s->gw, s->gv};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) free(bufs[i]);
     free(s);
 }
 
-/* Step 9 of Sec. 3.3: total indicator = fixed solids + particles (reading R1). */
+static int own_angle(const orc_particle *pp) { return isfinite(pp->theta_deg) != 0; }
+
+/* R18: does any particle carry its own contact angle */
+static int any_own_angle(const orc_sim *s)
+{
+    for (int k = 0; k < s->np; ++k)
+        if (own_angle(&s->parts[k])) return 1;
+    return 0;
+}
+
+/* Step 9 of Sec. 3.3: total indicator = fixed solids + particles (reading R1);
+ * with own particle angles also W and V of reading R18. */
 static void update_phi0(orc_sim *s)
 {
+    const int own = any_own_angle(s);
 #pragma omp parallel for collapse(2) schedule(static)
     for (long z = 0; z < s->nz; ++z)
         for (long y = 0; y < s->ny; ++y)
             for (long x = 0; x < s->nx; ++x) {
                 long id = (z * s->ny + y) * s->nx + x;
                 double v = s->phi0_fixed[id];
+                double dflt = s->phi0_fixed[id], w = 0.0, vv = 0.0;
                 for (int k = 0; k < s->np; ++k) {
                     double r[3];
                     rel_pos(s, x, y, z, s->parts[k].x, r);
-                    v += particle_indicator(s, &s->parts[k], r);
+                    double pk = particle_indicator(s, &s->parts[k], r);
+                    v += pk;
+                    if (own_angle(&s->parts[k])) {
+                        double ck = cos(s->parts[k].theta_deg * M_PI / 180.0);
+                        w += ck * pk;
+                        vv += ck * pk * pk * pk;
+                    } else {
+                        dflt += pk;
+                    }
                 }
                 s->phi0[id] = v;
+                if (own) {
+                    s->wfld[id] = s->cos_t * dflt + w;
+                    s->vfld[id] = s->cos_t * dflt * dflt * dflt + vv;
+                }
             }
 }
 
@@ -664,9 +738,25 @@ static void compute_macros(orc_sim *s)
     orc_grad(d, s->nx, s->ny, s->nz, s->phi0, s->gphi0);
 
     /* chemical potentials, Eqs. (9), (19) */
-    for (long id = 0; id < N; ++id) {
-        s->mu[id] = orc_mu_phi(p, s->phi[id], s->phi0[id], s->lap_phi[id], s->lap_phi0[id]);
-        s->mu0[id] = s->np > 0 ? orc_mu_phi0(p, s->phi[id], s->phi0[id], s->lap_phi[id]) : 0.0;
+    const int own = any_own_angle(s);
+    if (!own) {
+        for (long id = 0; id < N; ++id) {
+            s->mu[id] = orc_mu_phi(p, s->phi[id], s->phi0[id], s->lap_phi[id], s->lap_phi0[id]);
+            s->mu0[id] = s->np > 0 ? orc_mu_phi0(p, s->phi[id], s->phi0[id], s->lap_phi[id]) : 0.0;
+        }
+    } else {
+        /* reading R18: wetting terms per solid through W and V */
+        const double sg = p->sigma, D = p->D;
+        orc_lap(d, s->nx, s->ny, s->nz, s->wfld, s->lap_w);
+        orc_grad(d, s->nx, s->ny, s->nz, s->wfld, s->gw);
+        orc_grad(d, s->nx, s->ny, s->nz, s->vfld, s->gv);
+        for (long id = 0; id < N; ++id) {
+            const double ph = s->phi[id], p0 = s->phi0[id], W = s->wfld[id], V = s->vfld[id];
+            s->mu[id] = 3.0 * sg / D * ph * (ph - 1.0) * (ph + 1.0) - 3.0 * D * sg / 8.0 * s->lap_phi[id] +
+                        9.0 * sg / D * p0 * p0 * ph + 3.0 * sg / D * (3.0 * ph * ph * W + V - W) -
+                        3.0 * D * sg / 8.0 * s->lap_w[id];
+            s->mu0[id] = 0.0;
+        }
     }
 
     /* S = M grad(mu) (rho1 - rho2)/2 (Sec. 2.2); grad rho from Eq. (17) */
@@ -697,6 +787,18 @@ static void compute_macros(orc_sim *s)
                                   s->Fc[k]
                             : 0.0;
         }
+    if (own) {
+        /* reading R18: sum over solids of mu_phi0,s grad phi0_s */
+        const double sg = p->sigma, D = p->D;
+        for (int a = 0; a < d; ++a)
+            for (long id = 0; id < N; ++id) {
+                long k = a * N + id;
+                const double ph = s->phi[id], p0 = s->phi0[id];
+                s->F[k] += 9.0 * sg / D * p0 * ph * ph * s->gphi0[k] +
+                           3.0 * sg / D * (ph * (ph * ph - 1.0) * s->gw[k] + ph * s->gv[k]) -
+                           3.0 * D * sg / 8.0 * s->lap_phi[id] * s->gw[k];
+            }
+    }
 
     /* steps 5-6: u* (Eq. 36a), f, u (Eq. 36b) */
 #pragma omp parallel for collapse(2) schedule(static)
@@ -934,8 +1036,18 @@ static void one_step(orc_sim *s)
     memcpy(s->S_prev, s->S, sizeof(double) * 3 * N);
     memcpy(s->phi_prev, s->phi, sizeof(double) * N);
 
-    /* steps 8-10: particle update; the indicator follows at the next pass */
-    for (int k = 0; k < s->np; ++k) orc_particle_update(d, p, &s->parts[k], Ff[k], Tf[k]);
+    /* steps 8-10: particle update (hydrodynamic force plus the repulsion of
+     * reading R19 from the positions before the update); the indicator follows
+     * at the next pass */
+    double Frep[ORC_MAXP * 3];
+    const int nn[3] = {s->nx, s->ny, s->nz};
+    orc_repulsion(d, p, nn, s->np, s->parts, Frep);
+    for (int k = 0; k < s->np; ++k) {
+        double Fk[3];
+        for (int a = 0; a < 3; ++a) Fk[a] = Ff[k][a] + Frep[3 * k + a];
+        orc_particle_update(d, p, &s->parts[k], Fk, Tf[k]);
+        for (int a = 0; a < 3; ++a) s->parts[k].F[a] = Ff[k][a];
+    }
 }
 
 void orc_step(orc_sim *s, long n)
@@ -975,19 +1087,24 @@ void orc_diagnostics(orc_sim *s, double *out4)
     const orc_params *p = &s->p;
     compute_macros(s);
     double sg = p->sigma, D = p->D, ct = s->cos_t;
+    const int own = any_own_angle(s);
     double mass = 0.0, EF = 0.0, EK = 0.0;
     for (long id = 0; id < N; ++id) {
         double ph = s->phi[id], p0 = s->phi0[id];
-        double g2 = 0.0, g0g = 0.0, u2 = 0.0;
+        double g2 = 0.0, g0g = 0.0, gwg = 0.0, u2 = 0.0;
         for (int a = 0; a < d; ++a) {
             g2 += s->gphi[a * N + id] * s->gphi[a * N + id];
             g0g += s->gphi0[a * N + id] * s->gphi[a * N + id];
+            if (own) gwg += s->gw[a * N + id] * s->gphi[a * N + id];
             u2 += s->u[a * N + id] * s->u[a * N + id];
         }
         double e = 3.0 * sg / (4.0 * D) * (1.0 - ph) * (1.0 - ph) * (1.0 + ph) * (1.0 + ph) +
-                   3.0 * D * sg / 16.0 * g2 + 9.0 * sg / (2.0 * D) * p0 * p0 * ph * ph +
-                   3.0 * sg * ct / D * p0 * ph * (ph * ph + p0 * p0 - 1.0) +
-                   3.0 * D * sg * ct / 8.0 * g0g;
+                   3.0 * D * sg / 16.0 * g2 + 9.0 * sg / (2.0 * D) * p0 * p0 * ph * ph;
+        if (!own)
+            e += 3.0 * sg * ct / D * p0 * ph * (ph * ph + p0 * p0 - 1.0) + 3.0 * D * sg * ct / 8.0 * g0g;
+        else  /* reading R18: sum over solids with their own angles */
+            e += 3.0 * sg / D * (ph * (ph * ph - 1.0) * s->wfld[id] + ph * s->vfld[id]) +
+                 3.0 * D * sg / 8.0 * gwg;
         mass += ph;
         EF += e;
         EK += 0.5 * s->rho[id] * u2;

@@ -34,6 +34,8 @@ typedef struct orc_params {
     double Fb[3];      /* body force on the fluid (Eq. 16b) */
     double g[3];       /* gravity acting on particles (Eq. 26a) */
     double solid_eps;  /* lower bound on 1 - phi0 in the viscosity (reading of Eq. 35) */
+    double rep_xi;     /* particle-particle repulsion range xi (Sec. 4.5) */
+    double rep_eps;    /* its stiffness epsilon; <= 0 switches the repulsion off */
 } orc_params;
 
 typedef struct orc_particle {
@@ -41,6 +43,7 @@ typedef struct orc_particle {
     double R, rho_p;              /* radius, density */
     double u_prev[3], w_prev[3];  /* previous-step velocities (Eq. 28) */
     double F[3], T[3];            /* last hydrodynamic force / torque (Eq. 27) */
+    double theta_deg;             /* own contact angle (Sec. 4.5), NaN = the simulation's */
 } orc_particle;
 
 typedef struct orc_sim orc_sim;
@@ -104,6 +107,10 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp,
                          const double *Ff, const double *Tf);
 /* Hydrodynamic force and torque on particle k (Eq. 27) at the current time. */
 void orc_particle_force(orc_sim *s, int k, double *F3, double *T3);
+/* Short-range particle-particle repulsion of Sec. 4.5 on each of np
+ * particles (minimum image on the periodic box n[3]); out is np x 3. */
+void orc_repulsion(int dim, const orc_params *p, const int *n, int np, const orc_particle *parts,
+                   double *out);
 
 #ifdef __cplusplus
 }

@@ -274,3 +274,73 @@ def test_particle_interface_height_limits():
     assert hs[0] < hs[1] < hs[2]
     hs = [CF.particle_interface_height(L, Rp, th, 0.2)[0] for th in (120.0, 90.0, 60.0)]
     assert hs[0] < hs[1] < hs[2]
+
+
+def test_repulsion_invariants():
+    """Particle-particle repulsion (Sec. 4.5, reading R19): Newton's third law
+    (forces sum to zero), central and repulsive, zero beyond R_k + R_j + xi and
+    continuous there, periodic minimum image, off when eps = 0."""
+    rng = np.random.default_rng(3)
+    n = (64, 48)
+    p = O.make_params(rep_xi=3.0, rep_eps=0.5)
+    parts = [O.Particle((rng.uniform(0, n[0]), rng.uniform(0, n[1])), R=rng.uniform(3, 6)) for _ in range(12)]
+    F = O.repulsion(2, p, n, parts)
+    assert np.abs(F.sum(axis=0)).max() < 1e-12 * max(np.abs(F).max(), 1.0)
+    # a pair: radial, repulsive, range, continuity at the edge of the range
+    for dist, expect in ((8.0, True), (10.5, True), (13.0 - 1e-7, True), (13.0 + 1e-9, False), (20.0, False)):
+        a, b = O.Particle((20.0, 20.0), R=5.0), O.Particle((20.0 + dist * 0.6, 20.0 + dist * 0.8), R=5.0)
+        Fa, Fb = O.repulsion(2, p, n, [a, b])
+        assert np.allclose(Fa, -Fb, rtol=0, atol=1e-15)
+        dx = np.array(a.x) - np.array(b.x)
+        if expect:
+            assert Fa @ dx > 0 and abs(Fa[0] * dx[1] - Fa[1] * dx[0]) < 1e-12 * np.abs(Fa).max() * dist
+        else:
+            assert np.abs(Fa).max() == 0.0
+        if dist > 13.0 - 1e-3 and expect:
+            assert np.abs(Fa).max() < 1e-12
+    # across the periodic edge in x
+    a, b = O.Particle((1.0, 10.0), R=4.0), O.Particle((n[0] - 6.0, 10.0), R=4.0)
+    Fa, Fb = O.repulsion(2, p, n, [a, b])
+    assert Fa[0] > 0 and Fb[0] < 0
+    assert np.abs(O.repulsion(2, O.make_params(rep_xi=3.0, rep_eps=0.0), n, [a, b])).max() == 0.0
+
+
+def test_own_contact_angle_superposes_eq9():
+    """A particle with its own contact angle (reading R18): the oracle's mu_phi
+    equals Eq. 9 with the total phi0 and no wetting, plus the wetting part of
+    Eq. 9 of each solid with its own angle (the fixed disc at the simulation's
+    60 deg, the particle at 130 deg) -- the superposition the reading defines,
+    evaluated with the pinned pointwise Eq. 9."""
+    c = W.small_case((40, 48), seed=2, solid=True, theta_deg=60.0)
+    prm = dict(c["params"])
+    part = O.Particle((34.0, 12.0), R=6.0, rho_p=2.0, theta_deg=130.0)
+    phi = (1.0 - W.disc(c["shape"], part.x, part.R, prm["D"])) * c["phi"]
+    o = O.OracleSim(c["shape"], O.make_params(**prm))
+    o.set_particle(0, part)
+    o.init(c["phi0"], phi)
+    m = o.macros()
+    ph, mu = m["phi"], m["mu"]
+    p0_tot = o.phi0()
+    p0_fix = c["phi0"]
+    p0_par = p0_tot - p0_fix
+    lphi = O.lap(ph)
+    P = {th: O.make_params(**dict(prm, theta_deg=th)) for th in (90.0, 60.0, 130.0)}
+
+    def eq9(params, p0, i):
+        return O.mu_phi(params, ph.flat[i], p0.flat[i], lphi.flat[i], O_lap[id(p0)].flat[i])
+
+    O_lap = {id(p0_tot): O.lap(p0_tot), id(p0_fix): O.lap(p0_fix), id(p0_par): O.lap(p0_par)}
+    err = 0.0
+    for i in range(ph.size):
+        expect = eq9(P[90.0], p0_tot, i)
+        expect += eq9(P[60.0], p0_fix, i) - eq9(P[90.0], p0_fix, i)
+        expect += eq9(P[130.0], p0_par, i) - eq9(P[90.0], p0_par, i)
+        err = max(err, abs(mu.flat[i] - expect))
+    assert err < 1e-14, err
+    # the same particle without its own angle reproduces the single-angle path
+    o2 = O.OracleSim(c["shape"], O.make_params(**prm))
+    o2.set_particle(0, O.Particle((34.0, 12.0), R=6.0, rho_p=2.0))
+    o2.init(c["phi0"], phi)
+    mu2 = o2.macros()["mu"]
+    ref = np.array([eq9(P[60.0], p0_tot, i) for i in range(ph.size)]).reshape(ph.shape)
+    assert np.abs(mu2 - ref).max() < 1e-14
