@@ -91,6 +91,12 @@ typedef struct pf_params {
     double g[3];       /* gravity acting on particles (Eq. 26a) */
     double solid_eps;  /* lower bound of 1 - phi0 in mu/(1 - phi0) (Eq. 35);
                           in (0, 1), typically 1e-3 */
+    double rep_xi;     /* particle-particle repulsion (Sec. 4.5): range xi >= 0 */
+    double rep_eps;    /* and stiffness eps; 0 switches it off.  Force on k from j:
+                          (x_k - x_j)/eps (R_k + R_j + xi - d)^2 for
+                          R_k + R_j <= d <= R_k + R_j + xi, (x_k - x_j)/eps
+                          (R_k + R_j - d) for d < R_k + R_j (as printed), zero
+                          beyond; added to Eq. 26a, not to pf_particle.F */
     int precision;     /* PF_P64, PF_P32, PF_PMIX_FP16, PF_PMIX_BF16 */
     int store_log2_scale[2]; /* PMIX: stored value = population * 2^k for the
                                 order-parameter [0] and flow [1] lattices;
@@ -99,12 +105,16 @@ typedef struct pf_params {
 } pf_params;
 
 /* A free rigid particle (Sec. 2.4), FP64.  Disc (2D, per unit depth) or
- * sphere (3D) of radius R and density rho_p; its wettability is theta_deg of
- * the handle.  F and T are the hydrodynamic force and torque of Eq. (27) of
- * the last step (read only). */
+ * sphere (3D) of radius R and density rho_p; its wettability is its own
+ * theta_deg, or the handle's when that is NaN.  F and T are the hydrodynamic
+ * force and torque of Eq. (27) of the last step (read only). */
 typedef struct pf_particle {
     double x[3], u[3], w[3];
     double R, rho_p;
+    double theta_deg;  /* own contact angle (Sec. 4.5; 2D only), or NaN for the
+                          handle's theta_deg.  The wetting terms of Eqs. 8, 9, 19
+                          are then summed per solid, each with its own angle;
+                          all solids without an own angle form one solid. */
     double F[3], T[3];
 } pf_particle;
 
@@ -125,7 +135,7 @@ typedef struct pf_batch pf_batch;
 
 /* Fill *p with the paper's defaults (d0 = 0.4, all s = 1, D = 4, Sec. 4.1),
  * sigma = 0.01, M = 0.02, rho1 = rho2 = 1, mu1 = mu2 = 0.1, theta = 90 deg,
- * solid_eps = 1e-3, PF_P64, NULL stream. */
+ * solid_eps = 1e-3, no particle repulsion, PF_P64, NULL stream. */
 int pf_params_default(pf_params *p);
 
 /* Create a single-domain simulation.  Validates g and p (PF_EINVAL), allocates

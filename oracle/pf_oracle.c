@@ -921,8 +921,20 @@ void orc_init(orc_sim *s, const double *phi0, const double *phi, const double *u
     }
     orc_lap(d, s->nx, s->ny, s->nz, s->phi, s->lap_phi);
     orc_lap(d, s->nx, s->ny, s->nz, s->phi0, s->lap_phi0);
-    for (long id = 0; id < N; ++id)
-        s->mu[id] = orc_mu_phi(p, s->phi[id], s->phi0[id], s->lap_phi[id], s->lap_phi0[id]);
+    if (!any_own_angle(s)) {
+        for (long id = 0; id < N; ++id)
+            s->mu[id] = orc_mu_phi(p, s->phi[id], s->phi0[id], s->lap_phi[id], s->lap_phi0[id]);
+    } else {
+        /* reading R18, as in the steps */
+        const double sg = p->sigma, D = p->D;
+        orc_lap(d, s->nx, s->ny, s->nz, s->wfld, s->lap_w);
+        for (long id = 0; id < N; ++id) {
+            const double ph = s->phi[id], p0 = s->phi0[id], W = s->wfld[id], V = s->vfld[id];
+            s->mu[id] = 3.0 * sg / D * ph * (ph - 1.0) * (ph + 1.0) - 3.0 * D * sg / 8.0 * s->lap_phi[id] +
+                        9.0 * sg / D * p0 * p0 * ph + 3.0 * sg / D * (3.0 * ph * ph * W + V - W) -
+                        3.0 * D * sg / 8.0 * s->lap_w[id];
+        }
+    }
     orc_grad(d, s->nx, s->ny, s->nz, s->mu, s->gmu);
     for (long k = 0; k < 3 * N; ++k) s->S[k] = p->M * s->gmu[k] * drho;
     /* step 1 of Sec. 3.3: f = f^eq */

@@ -138,7 +138,7 @@ static bool finite_all(const pf_params *p)
 {
     const double v[] = {p->sigma, p->D, p->M, p->eta, p->rho1, p->rho2, p->mu1, p->mu2, p->d0,
                         p->s0, p->s1, p->s2, p->s3, p->s4, p->theta_deg, p->Fb[0], p->Fb[1],
-                        p->Fb[2], p->g[0], p->g[1], p->g[2], p->solid_eps};
+                        p->Fb[2], p->g[0], p->g[1], p->g[2], p->solid_eps, p->rep_xi, p->rep_eps};
     for (double x : v)
         if (!std::isfinite(x)) return false;
     return true;
@@ -172,6 +172,7 @@ static int validate(const pf_grid *g, const pf_params *p)
     for (double x : s)
         if (!(x > 0 && x < 2)) return fail(PF_EINVAL, "relaxation rates must lie in (0, 2)");
     if (!(p->solid_eps > 0 && p->solid_eps < 1)) return fail(PF_EINVAL, "solid_eps must lie in (0, 1)");
+    if (p->rep_xi < 0 || p->rep_eps < 0) return fail(PF_EINVAL, "rep_xi and rep_eps must be >= 0");
     if (p->precision < PF_P64 || p->precision > PF_PMIX_BF16)
         return fail(PF_EINVAL, "unknown precision %d", p->precision);
     const double cs2 = p->d0;
@@ -210,6 +211,8 @@ static DevParams derive(int dim, const pf_params *p)
     d.s3 = p->s3;
     d.s4 = p->s4;
     d.solid_eps = p->solid_eps;
+    d.rep_xi = p->rep_xi;
+    d.rep_eps = p->rep_eps;
     d.dim = dim;
     for (int a = 0; a < 3; ++a) {
         d.Fb[a] = a < dim ? p->Fb[a] : 0.0;
@@ -333,7 +336,7 @@ struct Staging {
 static int staging_reserve(Staging &st, const DomainMem &m, int dim)
 {
     const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
-    const size_t need = (size_t)(2 + dim + 1 + 2) * N;  // phi0, phi, u, P, phi0tot, mu
+    const size_t need = (size_t)(2 + dim + 1 + 4) * N;  // phi0, phi, u, P, phi0tot, mu, W, V
     if (st.n >= need) return PF_OK;
     if (st.p) cudaFree(st.p);
     st.p = nullptr;
@@ -358,7 +361,7 @@ static void domain_free(DomainMem &m)
 // copy caller arrays into the staging area and run the init kernels
 static int domain_init(DomainMem &m, Staging &st, int dim, int prec, const double *phi0, const double *phi,
                        const double *u, const double *P, int where, const ParticleDev *d_parts,
-                       int np, int *flags, cudaStream_t s)
+                       const ParticleDev *hparts, int np, int *flags, cudaStream_t s)
 {
     if (!phi0 || !phi) return fail(PF_EINVAL, "phi0 and phi are required");
     if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
@@ -371,7 +374,9 @@ static int domain_init(DomainMem &m, Staging &st, int dim, int prec, const doubl
     CK(cudaMemcpyAsync(sphi, phi, sizeof(double) * N, kind, s));
     if (u) CK(cudaMemcpyAsync(su, u, sizeof(double) * dim * N, kind, s));
     if (P) CK(cudaMemcpyAsync(sP, P, sizeof(double) * N, kind, s));
-    launch_init(prec, m.d, flags, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, np, s);
+    int wv = 0;
+    for (int k = 0; k < np; ++k) wv |= hparts ? hparts[k].own : 0;
+    launch_init(prec, m.d, flags, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, np, wv, s);
     CK(cudaGetLastError());
     return PF_OK;
 }
@@ -431,7 +436,9 @@ struct Engine {
     // particles (single-domain handles)
     ParticleDev hp[PF_MAX_PARTICLES];
     int np = 0;
+    int wv = 0;                 // some particle has its own contact angle
     ParticleDev *d_parts = nullptr;
+    double *d_frep = nullptr;   // repulsion force per particle (3 doubles each)
     double *d_partials = nullptr;
     size_t partials_cap = 0;
     // graph of CHUNK steps starting at parity 0
@@ -466,6 +473,7 @@ static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
     CK(cudaMemset(E.d_flags, 0, sizeof(int) * 4));
     CK(cudaMalloc(&E.d_diag, sizeof(double) * (3 * diag_blocks() + 8)));
     CK(cudaMalloc(&E.d_parts, sizeof(ParticleDev) * PF_MAX_PARTICLES));
+    CK(cudaMalloc(&E.d_frep, sizeof(double) * 3 * PF_MAX_PARTICLES));
     return PF_OK;
 }
 
@@ -484,6 +492,7 @@ static void engine_free(Engine &E)
     if (E.d_flags) cudaFree(E.d_flags);
     if (E.d_diag) cudaFree(E.d_diag);
     if (E.d_parts) cudaFree(E.d_parts);
+    if (E.d_frep) cudaFree(E.d_frep);
     if (E.d_partials) cudaFree(E.d_partials);
     if (E.own_stream && E.stream) cudaStreamDestroy(E.stream);
     E = Engine{};
@@ -568,6 +577,7 @@ static StepArgs step_args(const Engine &E, int par)
     a.np = E.np;
     a.partials = E.d_partials;
     a.flags = E.d_flags;
+    a.wv = E.wv;
     return a;
 }
 
@@ -578,7 +588,8 @@ static int issue_step(Engine &E, int par)
     if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a))
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
     if (E.np > 0)
-        launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.stream);
+        launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.d_frep, E.mem[0].d.nx,
+                               E.mem[0].d.ny, E.mem[0].d.nz, E.stream);
     CK(cudaGetLastError());
     return PF_OK;
 }
@@ -782,7 +793,7 @@ static int engine_macro_tables(Engine &E)
     const int nd = (int)E.mem.size();
     long long nmax = 0;
     for (auto &m : E.mem) nmax = std::max(nmax, (long long)m.d.nx * m.d.ny * m.d.nz);
-    CK(cudaMalloc(&E.d_macro, sizeof(double) * (size_t)(5 + E.dim) * nmax));
+    CK(cudaMalloc(&E.d_macro, sizeof(double) * (size_t)(7 + E.dim) * nmax));
     int mtx = 32, mty = 8;
     if (E.dim == 3) tile_shape3d(E.prec, &mtx, &mty);
     // build_tiles writes the tiling into the DomainDev it is given: tile copies
@@ -828,6 +839,7 @@ static int engine_macros(Engine &E, int i)
     a.np = E.np;
     a.partials = nullptr;
     a.flags = E.d_flags;
+    a.wv = E.wv;
     const int grid = std::min<int>(E.mcount[i], E.nsm * 4);
     if (!launch_any(E, mtx, mty, MODE_MACROS, grid, a))
         return fail(PF_EINVAL, "macro kernel not built");
@@ -872,7 +884,7 @@ static int engine_diag(Engine &E, int i, pf_diag *out)
     DomainDev dd = E.mem[i].d;
     dd.macro = E.d_macro;
     double *partial = E.d_diag, *res = E.d_diag + 3 * diag_blocks();
-    launch_diag(dd, partial, res, E.stream);
+    launch_diag(dd, partial, res, E.wv, E.stream);
     CK(cudaGetLastError());
     double h[3];
     CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, E.stream));
@@ -943,7 +955,7 @@ extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *ph
     rc = upload_particles(E);
     if (rc) return rc;
     CK(cudaMemsetAsync(E.d_flags, 0, sizeof(int) * 4, E.stream));
-    rc = domain_init(E.mem[0], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, E.np, E.d_flags,
+    rc = domain_init(E.mem[0], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, E.hp, E.np, E.d_flags,
                      E.stream);
     if (rc) return rc;
     CK(cudaStreamSynchronize(E.stream));
@@ -1001,6 +1013,10 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         if (k < 0 || k > E.np || k >= PF_MAX_PARTICLES)
             return fail(PF_EINVAL, "particle index %d out of range (count %d)", k, E.np);
         if (!(io->R > 0) || !(io->rho_p > 0)) return fail(PF_EINVAL, "particle needs R > 0 and rho_p > 0");
+        const bool own = !std::isnan(io->theta_deg);
+        if (own && !(io->theta_deg > 0 && io->theta_deg < 180))
+            return fail(PF_EINVAL, "particle theta_deg must be NaN or lie in (0, 180)");
+        if (own && E.dim == 3) return fail(PF_EINVAL, "own particle contact angles are built for 2D");
         if (E.np > 0) CK(cudaMemcpy(E.hp, E.d_parts, sizeof(ParticleDev) * E.np, cudaMemcpyDeviceToHost));
         ParticleDev &pp = E.hp[k];
         memset(&pp, 0, sizeof(pp));
@@ -1013,8 +1029,15 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         }
         pp.R = io->R;
         pp.rho_p = io->rho_p;
+        pp.theta_deg = own ? io->theta_deg : NAN;
+        pp.own = own ? 1 : 0;
+        pp.ct = own ? std::cos(io->theta_deg * 3.14159265358979323846 / 180.0) : 0.0;
         const bool grew = k == E.np;
         if (grew) E.np++;
+        int wv = 0;
+        for (int j = 0; j < E.np; ++j) wv |= E.hp[j].own;
+        if (wv != E.wv) drop_graph(E);  // the step arguments change
+        E.wv = wv;
         int rc = upload_particles(E);
         if (rc) return rc;
         if (grew) {
@@ -1045,6 +1068,7 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
     }
     io->R = pp.R;
     io->rho_p = pp.rho_p;
+    io->theta_deg = pp.theta_deg;
     return PF_OK;
 }
 
@@ -1084,7 +1108,7 @@ extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const doubl
     if (i < 0 || i >= (int)E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
     if (E.sticky) return E.sticky;
     if (E.t != 0) return fail(PF_ESTATE, "all domains are initialised before the first step");
-    int rc = domain_init(E.mem[i], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, 0, E.d_flags,
+    int rc = domain_init(E.mem[i], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, nullptr, 0, E.d_flags,
                          E.stream);
     if (rc) return rc;
     CK(cudaStreamSynchronize(E.stream));

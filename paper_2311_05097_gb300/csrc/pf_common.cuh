@@ -60,6 +60,7 @@ struct DevParams {
     double sigma, D, M, eta, rho1, rho2, mu1, mu2, d0;
     double s0, s1, s2, s3, s4, s1phi, cos_t, solid_eps;
     double Fb[3], g[3];
+    double rep_xi, rep_eps;  // particle-particle repulsion (Sec. 4.5); eps <= 0: off
     // derived
     double cs2, cs4, inv_cs2;
     double w0f;        // rest weight of the flow lattice
@@ -86,6 +87,9 @@ struct ParticleDev {
     double R, rho_p;
     double u_prev[3], w_prev[3];
     double F[3], T[3];
+    double theta_deg;  // own contact angle, NaN for the handle's
+    double ct;         // cos(theta_deg) when own
+    int own;           // 1 if the particle has its own contact angle
 };
 
 // The constants the step kernels read, in the kernel's arithmetic type (so a
@@ -174,6 +178,7 @@ struct StepArgs {
     int np;
     double *partials;      // [tile][particle][6]: F_f and T_f partial sums (Eq. 27)
     int *flags;            // [0]: non-finite value seen
+    int wv;                // some particle has its own contact angle (W, V fields)
 };
 
 // ---- helpers -----------------------------------------------------------------------------------

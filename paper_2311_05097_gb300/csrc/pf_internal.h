@@ -41,10 +41,10 @@ bool launch_step3d_mixh(int tx, int ty, bool moving, int mode, int grid, cudaStr
 bool launch_step3d_mixb(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ);
 
 void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, const double *phi, const double *u,
-                 const double *Pin, double *tmp, const ParticleDev *parts, int np, cudaStream_t s);
+                 const double *Pin, double *tmp, const ParticleDev *parts, int np, int wv, cudaStream_t s);
 int diag_blocks();
-void launch_diag(const DomainDev &Dm, double *partial, double *out, cudaStream_t s);
+void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cudaStream_t s);
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                            const DevParams &p, cudaStream_t s);
+                            const DevParams &p, double *frep, int nx, int ny, int nz, cudaStream_t s);
 
 }  // namespace pf

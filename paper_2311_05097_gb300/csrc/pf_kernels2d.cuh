@@ -137,6 +137,11 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     constexpr int WX = TX + 2, WY = TY + 2;   // tile + 1 frame
     __shared__ R s_phi[FY][FX];
     __shared__ R s_p0[FY][FX];
+    // free particles with their own contact angle: W = sum_s cos(theta_s) phi0_s,
+    // V = sum_s cos(theta_s) phi0_s^3 on the tile + 2 frame
+    constexpr int WVY = MOVING ? FY : 1, WVX = MOVING ? FX : 1;
+    __shared__ R s_W[WVY][WVX];
+    __shared__ R s_V[WVY][WVX];
     __shared__ R s_mu[WY][WX];
     __shared__ R s_w[WY][WX];
     __shared__ int s_gx[TX + 6];
@@ -232,10 +237,24 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             R v = (R)ldg(ph0 + s_gy[cy] + s_gx[cx]);
             if constexpr (MOVING) {
                 const int gx = s_gx[cx], gy = s_gyi[cy];
+                R dflt = v, w = R(0), vv = R(0);
                 for (int k = 0; k < A.np; ++k) {
                     if (!((near >> k) & 1ull)) continue;
                     R rx, ry;
-                    v += particle_phi0<R>(A.parts[k], gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                    const R pk = particle_phi0<R>(A.parts[k], gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                    v += pk;
+                    if (A.parts[k].own) {
+                        const R ck = (R)A.parts[k].ct;
+                        w += ck * pk;
+                        vv += ck * pk * pk * pk;
+                    } else {
+                        dflt += pk;
+                    }
+                }
+                if (A.wv) {
+                    const R ct = (R)p.cos_t;
+                    s_W[hy][hx] = ct * dflt + w;
+                    s_V[hy][hx] = ct * dflt * dflt * dflt + vv;
                 }
             }
             return v;
@@ -317,10 +336,22 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             const int wx = r % WX, wy = r / WX;
             const int hx = wx + 1, hy = wy + 1;
             const R ph = s_phi[hy][hx], p0 = s_p0[hy][hx];
-            const R lp = lap9<R, FX>(s_phi, hx, hy), lp0 = lap9<R, FX>(s_p0, hx, hy);
-            s_mu[wy][wx] = c_dw * ph * (ph - R(1)) * (ph + R(1)) - c_lap * lp +
-                           c_pen * p0 * p0 * ph + c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) -
-                           c_wlap * lp0;
+            const R lp = lap9<R, FX>(s_phi, hx, hy);
+            const R base = c_dw * ph * (ph - R(1)) * (ph + R(1)) - c_lap * lp + c_pen * p0 * p0 * ph;
+            bool own_wet = false;
+            if constexpr (MOVING) {
+                if (A.wv) {
+                    // wetting summed per solid (own particle angles), through W and V
+                    const R Wv = s_W[hy][hx], Vv = s_V[hy][hx];
+                    s_mu[wy][wx] =
+                        base + c_dw * (R(3) * ph * ph * Wv + Vv - Wv) - c_lap * lap9<R, WVX>(s_W, hx, hy);
+                    own_wet = true;
+                }
+            }
+            if (!own_wet) {
+                const R lp0 = lap9<R, FX>(s_p0, hx, hy);
+                s_mu[wy][wx] = base + c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) - c_wlap * lp0;
+            }
         }
         __syncthreads();
 
@@ -356,10 +387,21 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             lphi = lap9<R, FX>(s_phi, hx, hy);
             R g0x, g0y;
             grad9<R, FX>(s_p0, hx, hy, g0x, g0y);
-            const R mu0 = c_pen * phi0 * phi * phi + c_wet * phi * (R(3) * phi0 * phi0 + phi * phi - R(1)) -
-                          c_wlap * lphi;
-            Fx += mu0 * g0x;
-            Fy += mu0 * g0y;
+            if (A.wv) {
+                // sum over solids of mu_phi0,s grad phi0_s with their own angles
+                R gWx, gWy, gVx, gVy;
+                grad9<R, WVX>(s_W, hx, hy, gWx, gWy);
+                grad9<R, WVX>(s_V, hx, hy, gVx, gVy);
+                const R pen = c_pen * phi0 * phi * phi;
+                const R aW = c_dw * phi * (phi * phi - R(1)) - c_lap * lphi, aV = c_dw * phi;
+                Fx += pen * g0x + aW * gWx + aV * gVx;
+                Fy += pen * g0y + aW * gWy + aV * gVy;
+            } else {
+                const R mu0 = c_pen * phi0 * phi * phi + c_wet * phi * (R(3) * phi0 * phi0 + phi * phi - R(1)) -
+                              c_wlap * lphi;
+                Fx += mu0 * g0x;
+                Fy += mu0 * g0y;
+            }
         }
         if constexpr (MODE == MODE_MACROS) {
             // F_c from the lagged fields of the current parity (no shared tile)
@@ -449,6 +491,12 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 Dm.macro[4 * N + o] = (double)Pr;
                 Dm.macro[5 * N + o] = (double)mu;
                 Dm.macro[6 * N + o] = (double)phi0;
+                if constexpr (MOVING) {
+                    if (A.wv) {
+                        Dm.macro[7 * N + o] = (double)s_W[hy][hx];
+                        Dm.macro[8 * N + o] = (double)s_V[hy][hx];
+                    }
+                }
             }
             continue;
         } else {

@@ -160,35 +160,58 @@ __device__ __forceinline__ void fd_grad_lap_r(const DomainDev &Dm, const double 
         if (x >= Dm.nx) continue;                                                                  \
         const long long o = (long long)row * Dm.nx + x;
 
-// total indicator (fixed + particles) and the stored fixed indicator
+// total indicator (fixed + particles) and the stored fixed indicator; with
+// particles of their own contact angle also W = sum_s cos(theta_s) phi0_s and
+// V = sum_s cos(theta_s) phi0_s^3 (all solids without an own angle as one)
 template <class P>
 __global__ void k_init_phi0(DomainDev Dm, const double *phi0_in, double *phi0tot,
-                            const ParticleDev *parts, int np)
+                            const ParticleDev *parts, int np, double *Wf, double *Vf, int wv)
 {
     using AX = typename P::aux;
     PF_INIT_ROWS_BEGIN
         double v = phi0_in[o];
         reinterpret_cast<AX *>(Dm.phi0)[cell_of(Dm, x, y, z)] = (AX)v;
+        double dflt = v, w = 0.0, vv = 0.0;
         for (int k = 0; k < np; ++k) {
             double r[3];
-            v += particle_indicator_d(parts[k], x, y, z, Dm, r);
+            const double pk = particle_indicator_d(parts[k], x, y, z, Dm, r);
+            v += pk;
+            if (parts[k].own) {
+                w += parts[k].ct * pk;
+                vv += parts[k].ct * pk * pk * pk;
+            } else {
+                dflt += pk;
+            }
         }
         phi0tot[o] = v;
+        if (wv) {
+            Wf[o] = Dm.p.cos_t * dflt + w;
+            Vf[o] = Dm.p.cos_t * dflt * dflt * dflt + vv;
+        }
     }
 }
 
-// chemical potential of Eq. (9) from the initial phi
+// chemical potential of Eq. (9) from the initial phi (with own particle
+// angles: the wetting terms summed per solid through W and V)
 template <int DIM, class R>
-__global__ void k_init_mu(DomainDev Dm, const double *phi, const double *phi0tot, double *mu)
+__global__ void k_init_mu(DomainDev Dm, const double *phi, const double *phi0tot, double *mu, const double *Wf,
+                          const double *Vf, int wv)
 {
     const DevParams &p = Dm.p;
     PF_INIT_ROWS_BEGIN
         R g[3], lp, lp0;
         fd_grad_lap_r<DIM, R>(Dm, phi, x, y, z, g, &lp);
-        fd_grad_lap_r<DIM, R>(Dm, phi0tot, x, y, z, g, &lp0);
         const R ph = (R)phi[o], p0 = (R)phi0tot[o];
-        mu[o] = (double)((R)p.c_dw * ph * (ph - R(1)) * (ph + R(1)) - (R)p.c_lap * lp + (R)p.c_pen * p0 * p0 * ph +
-                         (R)p.c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) - (R)p.c_wlap * lp0);
+        const R base = (R)p.c_dw * ph * (ph - R(1)) * (ph + R(1)) - (R)p.c_lap * lp + (R)p.c_pen * p0 * p0 * ph;
+        if (!wv) {
+            fd_grad_lap_r<DIM, R>(Dm, phi0tot, x, y, z, g, &lp0);
+            mu[o] = (double)(base + (R)p.c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) - (R)p.c_wlap * lp0);
+        } else {
+            R lw;
+            fd_grad_lap_r<DIM, R>(Dm, Wf, x, y, z, g, &lw);
+            const R W = (R)Wf[o], V = (R)Vf[o];
+            mu[o] = (double)(base + (R)p.c_dw * (R(3) * ph * ph * W + V - W) - (R)p.c_lap * lw);
+        }
     }
 }
 
@@ -287,13 +310,14 @@ __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const doub
 // ---- diagnostics --------------------------------------------------------------------------------
 
 // macro = [phi, rho, u (dim), P, mu, phi0] (double, x-fastest)
-__global__ void k_diag_partial(DomainDev Dm, double *partial)
+__global__ void k_diag_partial(DomainDev Dm, double *partial, int wv)
 {
     const DevParams &p = Dm.p;
     const int dim = p.dim;
     const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
     const double *phi = Dm.macro, *rho = Dm.macro + N, *u = Dm.macro + 2 * N;
     const double *phi0 = Dm.macro + (2 + dim + 2) * N;
+    const double *Wf = phi0 + N, *Vf = phi0 + 2 * N;  // own particle angles only
     double acc[3] = {0.0, 0.0, 0.0};
     // each thread walks a fixed contiguous range: deterministic order
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -303,7 +327,7 @@ __global__ void k_diag_partial(DomainDev Dm, double *partial)
         const int x = (int)(o % Dm.nx), y = (int)((o / Dm.nx) % Dm.ny), z = (int)(o / ((long long)Dm.nx * Dm.ny));
         double g[3], g0[3];
         fd_grad_lap(Dm, phi, x, y, z, g, nullptr);
-        fd_grad_lap(Dm, phi0, x, y, z, g0, nullptr);
+        fd_grad_lap(Dm, wv ? Wf : phi0, x, y, z, g0, nullptr);
         const double ph = phi[o], p0 = phi0[o];
         double g2 = 0.0, g0g = 0.0, u2 = 0.0;
         for (int a = 0; a < dim; ++a) {
@@ -312,10 +336,12 @@ __global__ void k_diag_partial(DomainDev Dm, double *partial)
             u2 += u[a * N + o] * u[a * N + o];
         }
         const double s = p.sigma, D = p.D, ct = p.cos_t;
-        const double e = 3.0 * s / (4.0 * D) * (1.0 - ph) * (1.0 - ph) * (1.0 + ph) * (1.0 + ph) +
-                         3.0 * D * s / 16.0 * g2 + 9.0 * s / (2.0 * D) * p0 * p0 * ph * ph +
-                         3.0 * s * ct / D * p0 * ph * (ph * ph + p0 * p0 - 1.0) +
-                         3.0 * D * s * ct / 8.0 * g0g;
+        double e = 3.0 * s / (4.0 * D) * (1.0 - ph) * (1.0 - ph) * (1.0 + ph) * (1.0 + ph) +
+                   3.0 * D * s / 16.0 * g2 + 9.0 * s / (2.0 * D) * p0 * p0 * ph * ph;
+        if (!wv)
+            e += 3.0 * s * ct / D * p0 * ph * (ph * ph + p0 * p0 - 1.0) + 3.0 * D * s * ct / 8.0 * g0g;
+        else  // wetting energy summed per solid with its own angle (g0 = grad W)
+            e += 3.0 * s / D * (ph * (ph * ph - 1.0) * Wf[o] + ph * Vf[o]) + 3.0 * D * s / 8.0 * g0g;
         acc[0] += ph;
         acc[1] += e;
         acc[2] += 0.5 * rho[o] * u2;
@@ -349,9 +375,41 @@ __global__ void k_diag_final(const double *partial, int nblocks, double *out)
         for (int c = 0; c < 3; ++c) out[c] = red[0][c];
 }
 
-// ---- particles: reduce per-tile partial sums, Newton-Euler (Eqs. 26, 28) ----------------------
+// ---- particles: repulsion (Sec. 4.5), per-tile partial sums, Newton-Euler (Eqs. 26, 28) --------
+// Force on particle k from the others (as printed: (x_k - x_j)/eps times
+// (R_k + R_j + xi - d)^2 within xi of contact, (R_k + R_j - d) overlapping),
+// minimum image; from the positions before this step's update.
+__global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams p, int nx, int ny, int nz,
+                                     double *frep)
+{
+    const int k = threadIdx.x;
+    if (k >= np) return;
+    const int n[3] = {nx, ny, nz};
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (p.rep_eps > 0.0) {
+        for (int j = 0; j < np; ++j) {
+            if (j == k) continue;
+            double dx[3], d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                double v = a < p.dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
+                if (a < p.dim) v -= n[a] * floor(v / n[a] + 0.5);
+                dx[a] = v;
+                d2 += v * v;
+            }
+            const double dist = sqrt(d2), rr = parts[k].R + parts[j].R;
+            double f = 0.0;
+            if (dist <= rr + p.rep_xi) {
+                if (dist >= rr) f = (rr + p.rep_xi - dist) * (rr + p.rep_xi - dist) / p.rep_eps;
+                else f = (rr - dist) / p.rep_eps;
+            }
+            for (int a = 0; a < 3; ++a) acc[a] += f * dx[a];
+        }
+    }
+    for (int a = 0; a < 3; ++a) frep[3 * k + a] = acc[a];
+}
+
 __global__ void k_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                                  DevParams p)
+                                  DevParams p, const double *frep)
 {
     const int k = blockIdx.x;
     if (k >= np) return;
@@ -385,7 +443,7 @@ __global__ void k_particle_update(ParticleDev *parts, int np, const double *part
     for (int c = 0; c < 3; ++c) {
         const double Fin = rho_bar * Vp * (pp.u[c] - pp.u_prev[c]);
         const double Tin = If * (pp.w[c] - pp.w_prev[c]);
-        a[c] = (red[0][c] + Fin + (1.0 - rho_bar / pp.rho_p) * Mp * p.g[c]) / Mp;
+        a[c] = (red[0][c] + frep[3 * k + c] + Fin + (1.0 - rho_bar / pp.rho_p) * Mp * p.g[c]) / Mp;
         al[c] = (red[0][3 + c] + Tin) / Ip;
     }
     if (p.dim == 2) {
@@ -414,53 +472,54 @@ static int grid_for(long long N, int bs)
 
 template <class P>
 static void init_impl(const DomainDev &Dm, int *flags, const double *phi0, const double *phi, const double *u,
-                      const double *Pin, double *tmp, const ParticleDev *parts, int np,
+                      const double *Pin, double *tmp, const ParticleDev *parts, int np, int wv,
                       cudaStream_t s)
 {
     using R = typename P::real;
     const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
-    double *phi0tot = tmp, *mu = tmp + N;
+    double *phi0tot = tmp, *mu = tmp + N, *Wf = tmp + 2 * N, *Vf = tmp + 3 * N;
     // x blocks of 128 cells, one grid row per domain row (at most 65535, the
     // kernels stride over the rest)
     const int bs = 128;
     const int rows = Dm.ny * Dm.nz;
     const dim3 g((Dm.nx + bs - 1) / bs, rows < 65535 ? rows : 65535);
-    k_init_phi0<P><<<g, bs, 0, s>>>(Dm, phi0, phi0tot, parts, np);
+    k_init_phi0<P><<<g, bs, 0, s>>>(Dm, phi0, phi0tot, parts, np, Wf, Vf, wv);
     if (Dm.p.dim == 2) {
-        k_init_mu<2, R><<<g, bs, 0, s>>>(Dm, phi, phi0tot, mu);
+        k_init_mu<2, R><<<g, bs, 0, s>>>(Dm, phi, phi0tot, mu, Wf, Vf, wv);
         k_init_f<P, 2><<<g, bs, 0, s>>>(Dm, flags, phi, u, Pin, mu);
     } else {
-        k_init_mu<3, R><<<g, bs, 0, s>>>(Dm, phi, phi0tot, mu);
+        k_init_mu<3, R><<<g, bs, 0, s>>>(Dm, phi, phi0tot, mu, Wf, Vf, wv);
         k_init_f<P, 3><<<g, bs, 0, s>>>(Dm, flags, phi, u, Pin, mu);
     }
     count_launches(3);
 }
 
 void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, const double *phi, const double *u,
-                 const double *Pin, double *tmp, const ParticleDev *parts, int np, cudaStream_t s)
+                 const double *Pin, double *tmp, const ParticleDev *parts, int np, int wv, cudaStream_t s)
 {
     switch (prec) {
-    case 0: init_impl<P64>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
-    case 1: init_impl<P32>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
-    case 2: init_impl<PMixH>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
-    default: init_impl<PMixB>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, s); break;
+    case 0: init_impl<P64>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, wv, s); break;
+    case 1: init_impl<P32>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, wv, s); break;
+    case 2: init_impl<PMixH>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, wv, s); break;
+    default: init_impl<PMixB>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, wv, s); break;
     }
 }
 
 int diag_blocks() { return 120; }
 
-void launch_diag(const DomainDev &Dm, double *partial, double *out, cudaStream_t s)
+void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cudaStream_t s)
 {
-    k_diag_partial<<<diag_blocks(), 256, 0, s>>>(Dm, partial);
+    k_diag_partial<<<diag_blocks(), 256, 0, s>>>(Dm, partial, wv);
     k_diag_final<<<1, 256, 0, s>>>(partial, diag_blocks(), out);
     count_launches(2);
 }
 
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                            const DevParams &p, cudaStream_t s)
+                            const DevParams &p, double *frep, int nx, int ny, int nz, cudaStream_t s)
 {
-    k_particle_update<<<np, 256, 0, s>>>(parts, np, partials, ntiles, p);
-    count_launches(1);
+    k_particle_repulsion<<<1, 64, 0, s>>>(parts, np, p, nx, ny, nz, frep);
+    k_particle_update<<<np, 256, 0, s>>>(parts, np, partials, ntiles, p, frep);
+    count_launches(2);
 }
 
 }  // namespace pf

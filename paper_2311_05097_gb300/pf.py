@@ -38,14 +38,15 @@ class pf_params(C.Structure):
         ("d0", C.c_double), ("s0", C.c_double), ("s1", C.c_double), ("s2", C.c_double),
         ("s3", C.c_double), ("s4", C.c_double), ("theta_deg", C.c_double),
         ("Fb", C.c_double * 3), ("g", C.c_double * 3), ("solid_eps", C.c_double),
+        ("rep_xi", C.c_double), ("rep_eps", C.c_double),
         ("precision", C.c_int), ("store_log2_scale", C.c_int * 2), ("stream", C.c_void_p),
     ]
 
 
 class pf_particle(C.Structure):
     _fields_ = [("x", C.c_double * 3), ("u", C.c_double * 3), ("w", C.c_double * 3),
-                ("R", C.c_double), ("rho_p", C.c_double), ("F", C.c_double * 3),
-                ("T", C.c_double * 3)]
+                ("R", C.c_double), ("rho_p", C.c_double), ("theta_deg", C.c_double),
+                ("F", C.c_double * 3), ("T", C.c_double * 3)]
 
 
 class pf_diag(C.Structure):
@@ -201,19 +202,21 @@ class Sim:
         except Exception:
             pass
 
-    def set_particle(self, k, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0):
+    def set_particle(self, k, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0, theta_deg=None):
+        """Add or overwrite particle k; theta_deg None keeps the handle's angle."""
         pp = pf_particle()
         pp.x = (C.c_double * 3)(*(tuple(x) + (0.0,) * (3 - len(x))))
         pp.u = (C.c_double * 3)(*(tuple(u) + (0.0,) * (3 - len(u))))
         pp.w = (C.c_double * 3)(*(tuple(w) + (0.0,) * (3 - len(w))))
         pp.R, pp.rho_p = float(R), float(rho_p)
+        pp.theta_deg = float("nan") if theta_deg is None else float(theta_deg)
         _check(load().pf_particle_state(self._h, int(k), C.byref(pp), 1))
 
     def particle(self, k):
         pp = pf_particle()
         _check(load().pf_particle_state(self._h, int(k), C.byref(pp), 0))
         return dict(x=list(pp.x), u=list(pp.u), w=list(pp.w), R=pp.R, rho_p=pp.rho_p,
-                    F=list(pp.F), T=list(pp.T))
+                    theta_deg=pp.theta_deg, F=list(pp.F), T=list(pp.T))
 
     def init(self, phi0, phi, u=None, P=None):
         where = PF_DEVICE if _is_device(phi) else PF_HOST

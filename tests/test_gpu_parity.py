@@ -101,6 +101,37 @@ def test_p64_moving_particle_matches_oracle(pf):
         assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, a, b)
 
 
+def test_p64_own_angles_and_repulsion_match_oracle(pf):
+    """Three free particles, two with their own contact angle (45, 135 deg;
+    the third and the fixed disc at the handle's 60 deg) and two within the
+    repulsion range (Sec. 4.5), FP64 against the oracle: fields, the FP64
+    diagnostics and every particle's state after 80 steps."""
+    c = W.small_case((72, 64), seed=6, solid=True, theta_deg=60.0)
+    c["params"] = dict(c["params"], rep_xi=2.0, rep_eps=1e4)
+    parts = [dict(x=(20.0, 46.0), u=(0.004, 0.0), R=6.0, rho_p=2.0, theta_deg=45.0),
+             dict(x=(33.0, 46.0), u=(-0.004, 0.0), R=6.0, rho_p=2.0, theta_deg=135.0),
+             dict(x=(50.0, 18.0), u=(0.0, 0.003), R=5.0, rho_p=1.5)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], c["params"]["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 80, particles=parts)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * 0.01 / 4.0)
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-12), (k, dg[k], do[k])
+    for k in range(3):
+        pg, po = g.particle(k), o.particle(k)
+        for f in ("x", "u", "w", "F", "T"):
+            a, b = np.array(pg[f]), np.array(getattr(po, f))
+            assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, f, a, b)
+    # the repulsion pushed the close pair apart relative to no repulsion
+    c2 = dict(c, params=dict(c["params"], rep_eps=0.0))
+    g2, _ = run_pair(pf, c2, 80, particles=parts, oracle=False)
+    assert g.particle(0)["u"][0] < g2.particle(0)["u"][0]
+    assert g.particle(1)["u"][0] > g2.particle(1)["u"][0]
+
+
 def test_p64_static_drop_full_run(pf):
     """The 128 x 128 static drop for its full 2000 steps."""
     c = W.static_drop()
