@@ -116,6 +116,9 @@ typedef struct pf_particle {
                           are then summed per solid, each with its own angle;
                           all solids without an own angle form one solid. */
     double F[3], T[3];
+    int prescribed;    /* 1: the particle keeps the u and w it was given (prescribed
+                          motion, e.g. a rotating cylinder): x advances by u, F and
+                          T are still reported; 0: Newton-Euler (Eqs. 26, 28) */
 } pf_particle;
 
 /* FP64 diagnostics at the current time: mass = sum phi, E_F of Eq. (8),

@@ -30,7 +30,7 @@ class OrcParticle(C.Structure):
         ("R", C.c_double), ("rho_p", C.c_double),
         ("u_prev", C.c_double * 3), ("w_prev", C.c_double * 3),
         ("F", C.c_double * 3), ("T", C.c_double * 3),
-        ("theta_deg", C.c_double),
+        ("theta_deg", C.c_double), ("prescribed", C.c_int),
     ]
 
 
@@ -118,8 +118,9 @@ def make_params(**kw):
 class Particle:
     """Plain particle record (FP64) mirroring the oracle's struct."""
 
-    def __init__(self, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0, theta_deg=None):
+    def __init__(self, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0, theta_deg=None, prescribed=False):
         self.theta_deg = float("nan") if theta_deg is None else float(theta_deg)
+        self.prescribed = bool(prescribed)
         self.x = list(x) + [0.0] * (3 - len(x))
         self.u = list(u) + [0.0] * (3 - len(u))
         self.w = list(w) + [0.0] * (3 - len(w))
@@ -136,12 +137,14 @@ class Particle:
             setattr(c, k, (C.c_double * 3)(*getattr(self, k)))
         c.R, c.rho_p = self.R, self.rho_p
         c.theta_deg = self.theta_deg
+        c.prescribed = 1 if self.prescribed else 0
         return c
 
     @classmethod
     def from_c(cls, c):
         p = cls(list(c.x), list(c.u), list(c.w), c.R, c.rho_p)
         p.theta_deg = c.theta_deg
+        p.prescribed = bool(c.prescribed)
         p.u_prev, p.w_prev = list(c.u_prev), list(c.w_prev)
         p.F, p.T = list(c.F), list(c.T)
         return p

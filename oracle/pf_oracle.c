@@ -531,9 +531,11 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp, const d
         pp->T[k] = Tf[k];
         pp->x[k] += pp->u[k];
         pp->u_prev[k] = pp->u[k];
-        pp->u[k] += a[k];
         pp->w_prev[k] = pp->w[k];
-        pp->w[k] += al[k];
+        if (!pp->prescribed) {
+            pp->u[k] += a[k];
+            pp->w[k] += al[k];
+        }
     }
 }
 

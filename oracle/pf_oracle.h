@@ -44,6 +44,7 @@ typedef struct orc_particle {
     double u_prev[3], w_prev[3];  /* previous-step velocities (Eq. 28) */
     double F[3], T[3];            /* last hydrodynamic force / torque (Eq. 27) */
     double theta_deg;             /* own contact angle (Sec. 4.5), NaN = the simulation's */
+    int prescribed;               /* 1: u and w kept (prescribed motion), x advances by u */
 } orc_particle;
 
 typedef struct orc_sim orc_sim;

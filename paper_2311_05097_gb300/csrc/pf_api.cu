@@ -1030,6 +1030,7 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         pp.R = io->R;
         pp.rho_p = io->rho_p;
         pp.theta_deg = own ? io->theta_deg : NAN;
+        pp.prescribed = io->prescribed ? 1 : 0;
         pp.own = own ? 1 : 0;
         pp.ct = own ? std::cos(io->theta_deg * 3.14159265358979323846 / 180.0) : 0.0;
         const bool grew = k == E.np;
@@ -1069,6 +1070,7 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
     io->R = pp.R;
     io->rho_p = pp.rho_p;
     io->theta_deg = pp.theta_deg;
+    io->prescribed = pp.prescribed;
     return PF_OK;
 }
 

@@ -90,6 +90,7 @@ struct ParticleDev {
     double theta_deg;  // own contact angle, NaN for the handle's
     double ct;         // cos(theta_deg) when own
     int own;           // 1 if the particle has its own contact angle
+    int prescribed;    // 1: u and w are kept (prescribed motion)
 };
 
 // The constants the step kernels read, in the kernel's arithmetic type (so a

@@ -455,9 +455,11 @@ __global__ void k_particle_update(ParticleDev *parts, int np, const double *part
         pp.T[c] = red[0][3 + c];
         pp.x[c] += pp.u[c];
         pp.u_prev[c] = pp.u[c];
-        pp.u[c] += a[c];
         pp.w_prev[c] = pp.w[c];
-        pp.w[c] += al[c];
+        if (!pp.prescribed) {
+            pp.u[c] += a[c];
+            pp.w[c] += al[c];
+        }
     }
 }
 

@@ -236,6 +236,45 @@ def particle_balance(L=256, Rp=32.0, theta_deg=90.0, rho_p=1.1, sigma=0.01, g=2e
                 rho_f=1.0, sigma=sigma, g=g, y_if=y_if, name="particle_balance_2d")
 
 
+def annulus_mixing(n=512, count=15, seed=4, D=5.0, omega=1e-4, g=1e-6, rep_xi=2.5, rep_eps=1e4):
+    """Two fluid layers and ``count`` free wetting particles in the annulus
+    between a fixed outer wall (radius n/2) and an inner cylinder (radius
+    n/8) rotating at ``omega`` rad/step (Sec. 4.5 layout in lattice units,
+    dx = 0.01 of the paper: R_p in [20, 30], rho_p in [0.95, 1.05], theta_k in
+    [45, 135] deg, neutral walls, sigma = 0.001, equal fluid densities and
+    viscosities, gravity on the particles, short-range repulsion).  The inner
+    cylinder is particle 0 with prescribed rotation."""
+    rng = np.random.default_rng(seed)
+    shape = (n, n)
+    c = (n - 1) / 2.0
+    r_out, r_in = n / 2.0, n / 8.0
+    X, Y = _coords(shape)
+    r = np.hypot(X - c, Y - c)
+    phi0 = smooth_indicator(r - r_out, D)  # outer wall: solid outside r_out
+    parts = [dict(x=(c, c, 0.0), u=(0.0, 0.0, 0.0), w=(0.0, 0.0, omega), R=r_in, rho_p=1.0,
+                  prescribed=True)]
+    placed = []
+    tries = 0
+    while len(placed) < count and tries < 100000:
+        tries += 1
+        R = rng.uniform(20.0, 30.0)
+        rad = rng.uniform(r_in + R + 6.0, r_out - R - 6.0)
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        x, y = c + rad * math.cos(ang), c + rad * math.sin(ang)
+        if all(math.hypot(x - q[0], y - q[1]) > R + q[2] + 6.0 for q in placed):
+            placed.append((x, y, R))
+    for x, y, R in placed:
+        parts.append(dict(x=(x, y, 0.0), u=(0.0, 0.0, 0.0), w=(0.0, 0.0, 0.0), R=R,
+                          rho_p=rng.uniform(0.95, 1.05), theta_deg=rng.uniform(45.0, 135.0)))
+    solid = phi0.copy()
+    for q in parts:
+        solid = solid + disc(shape, q["x"], q["R"], D)
+    phi = (1.0 - solid) * np.tanh(-2.0 * (Y - c) / D)
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, theta_deg=90.0,
+               g=(0.0, -g, 0.0), rep_xi=rep_xi, rep_eps=rep_eps)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, name="annulus_mixing_2d")
+
+
 def equal_area_cap_base(theta_deg, area):
     """Radius and base half-width of a circular cap of given area on a flat wall."""
     th = math.radians(theta_deg)

@@ -132,6 +132,26 @@ def test_p64_own_angles_and_repulsion_match_oracle(pf):
     assert g.particle(1)["u"][0] > g2.particle(1)["u"][0]
 
 
+def test_annulus_mixing_full_size_against_oracle(pf):
+    """Sec. 4.5 layout at full size (512 x 512, outer wall, inner cylinder of
+    prescribed rotation, 15 wetting particles with their own angles,
+    repulsion): FP64 fields and particle states against the oracle after 3
+    steps."""
+    c = W.annulus_mixing()
+    g, o = run_pair(pf, c, 3, particles=c["particles"])
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * 0.001 / 5.0)
+    for k in range(len(c["particles"])):
+        pg, po = g.particle(k), o.particle(k)
+        for f in ("x", "u", "w"):
+            a, b = np.array(pg[f]), np.array(getattr(po, f))
+            assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, f, a, b)
+        # F is a sum over the particle's cells of terms that largely cancel:
+        # measured against the momentum-exchange scale rho pi R^2 |u_s|
+        R = po.R
+        us = np.abs(po.u).max() + abs(po.w[2]) * R + 1e-4
+        assert np.abs(np.array(pg["F"]) - np.array(po.F)).max() <= 1e-12 * math.pi * R * R * us, k
+
+
 def test_p64_static_drop_full_run(pf):
     """The 128 x 128 static drop for its full 2000 steps."""
     c = W.static_drop()
