@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "drop_on_cylinder", "static_drop", "water_entry",
-                             "drainage_3d"])
+                             "drainage_3d", "annulus"])
     ap.add_argument("--n3d", type=int, default=256, help="cube side of drainage_3d")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
@@ -87,6 +87,14 @@ def single_workload(name, n3d=256):
         c["desc"] = ("2D water entry: particle R=40, rho_p=2, u=-0.02, 1024x2048, pool depth 800, "
                      "density ratio 10, theta 90 deg; force/torque reduction and Newton-Euler "
                      "in FP64 every step")
+        return c
+    if name == "annulus":
+        c = W.annulus_mixing()
+        c["precision"] = "p32"
+        c["desc"] = ("2D annulus mixing (Sec. 4.5 layout): 512x512, outer wall, inner cylinder R=64 "
+                     "rotating at 1e-4 rad/step, 15 free wetting particles (R 20-30, own contact angles "
+                     "45-135 deg), repulsion, gravity on particles; force/torque reduction and "
+                     "Newton-Euler in FP64 every step")
         return c
     if name == "drainage_3d":
         c = W.porous_drainage_3d(n=n3d)
