@@ -345,6 +345,12 @@ __device__ __forceinline__ int wrap_idx(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// periodic index for v in [-n, 2n): no division
+__device__ __forceinline__ int wrap_near(int v, int n)
+{
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
 // ---- asynchronous bulk copies into shared memory (mbarrier completion) ------------------------
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {

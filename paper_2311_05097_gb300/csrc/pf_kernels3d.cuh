@@ -243,7 +243,9 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         const R c_dw = kp.c_dw, c_lap = kp.c_lap, c_pen = kp.c_pen, c_wet = kp.c_wet,
                 c_wlap = kp.c_wlap;
 
-        auto zoff = [&](int z) { return wrap_idx(z, nz) * zstride; };
+        // the planes touched lie in [z0 - 3, min(z0 + ZC, nz) + 2], inside
+        // [-nz, 2 nz) since nz >= 4
+        auto zoff = [&](int z) { return wrap_near(z, nz) * zstride; };
         auto cidx = [&](int tx_, int ty_, int zo) {  // tile+3 table coordinates
             return zo + s_gy[ty_] * Dm.pitch + s_gx[tx_];
         };
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             const int cx = hx + 1, cy = hy + 1;
             R v = (R)ldg(ph0 + cidx(cx, cy, zoff(z)));
             if constexpr (MOVING) {
-                const int gx = s_gx[cx], gy = s_gy[cy], gz = wrap_idx(z, nz);
+                const int gx = s_gx[cx], gy = s_gy[cy], gz = wrap_near(z, nz);
                 for (int k = 0; k < A.np; ++k) {
                     R rx, ry, rz;
                     v += particle_phi0_3d<R>(A.parts[k], gx, gy, gz, nx, ny, nz, p.D, p.cut, rx, ry, rz);
