@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
     __shared__ R s_mu[4][WP];
     __shared__ R s_T[4][3][WP];
     __shared__ int s_gx[TX + 6];
-    __shared__ int s_gy[TY + 6];
+    __shared__ int s_gy[TY + 6];   // wrapped row offsets y * pitch
+    __shared__ int s_gyi[TY + 6];  // wrapped rows
     __shared__ double s_red[NT / 32][6];
 
     const int tid = threadIdx.x;
@@ -229,7 +230,11 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
 
         __syncthreads();
         for (int k = tid; k < TX + 6; k += NT) s_gx[k] = wrap_idx(x0 - 3 + k, nx);
-        for (int k = tid; k < TY + 6; k += NT) s_gy[k] = wrap_idx(y0 - 3 + k, ny);
+        for (int k = tid; k < TY + 6; k += NT) {
+            const int yy = wrap_idx(y0 - 3 + k, ny);
+            s_gyi[k] = yy;
+            s_gy[k] = yy * Dm.pitch;
+        }
         __syncthreads();
 
         const ST *fs = reinterpret_cast<const ST *>(Dm.f[A.par]);
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         // [-nz, 2 nz) since nz >= 4
         auto zoff = [&](int z) { return wrap_near(z, nz) * zstride; };
         auto cidx = [&](int tx_, int ty_, int zo) {  // tile+3 table coordinates
-            return zo + s_gy[ty_] * Dm.pitch + s_gx[tx_];
+            return zo + s_gy[ty_] + s_gx[tx_];
         };
         // phi at (frame x, frame y) of plane z: pull and sum the D3Q7 populations
         auto phi_at = [&](int hx, int hy, int z, R *keep, ST *keepq) -> R {
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             const int cx = hx + 1, cy = hy + 1;
             R v = (R)ldg(ph0 + cidx(cx, cy, zoff(z)));
             if constexpr (MOVING) {
-                const int gx = s_gx[cx], gy = s_gy[cy], gz = wrap_near(z, nz);
+                const int gx = s_gx[cx], gy = s_gyi[cy], gz = wrap_near(z, nz);
                 for (int k = 0; k < A.np; ++k) {
                     R rx, ry, rz;
                     v += particle_phi0_3d<R>(A.parts[k], gx, gy, gz, nx, ny, nz, p.D, p.cut, rx, ry, rz);
