@@ -78,6 +78,8 @@ def lib():
         L.orc_particle_update.argtypes = [C.c_int, C.POINTER(OrcParams), C.POINTER(OrcParticle),
                                           _DP, _DP]
         L.orc_particle_force.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
+        L.orc_set_walls.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_walls.restype = C.c_int
         L.orc_repulsion.argtypes = [C.c_int, C.POINTER(OrcParams), _IP, C.c_int,
                                     C.POINTER(OrcParticle), _DP]
         _lib = L
@@ -209,6 +211,11 @@ class OracleSim:
         a = np.empty(self.N)
         lib().orc_get_phi0(self._h, _p(a))
         return a.reshape(self.shape)
+
+    def set_walls(self, wall_y=True):
+        """Walls at the ends of y (reading R21); call before init."""
+        if lib().orc_set_walls(self._h, 1 if wall_y else 0) != 0:
+            raise ValueError("walls are 2D only")
 
     def set_particle(self, k, part):
         c = part.to_c()

@@ -55,6 +55,11 @@
  *       (R_k + R_j - d) for d <= R_k + R_j, zero beyond (minimum image), added to
  *       the force of Eq. (26a) from the positions before the update.  The
  *       particle-wall form needs a wall geometry and is not built.
+ *   R21 box walls (2D, y = -1/2 and y = ny - 1/2; the paper's no-flux boxes):
+ *       halfway bounce-back of both lattices at resting walls; the stencils read
+ *       rows beyond a wall as the mirror image of the rows inside (zero normal
+ *       gradient of phi, mu and phi0: no flux), except the products
+ *       S_a u_b - u_a S_b of F_c, which change sign under the mirror.
  */
 #include "pf_oracle.h"
 
@@ -93,6 +98,7 @@ struct orc_sim {
     double *s2a, *s2b, *P, *tmp, *tmp3;
     /* R18: angle-weighted indicators and their stencils */
     double *wfld, *vfld, *lap_w, *gw, *gv;
+    int wall_y;  /* R21: walls at the ends of y instead of periodicity */
 };
 
 int orc_num_threads(void)
@@ -426,6 +432,72 @@ static long nb_index(int nx, int ny, int nz, long x, long y, long z, const int *
     return (zz * ny + yy) * nx + xx;
 }
 
+/* neighbour of (x, y, z) along c with the walls of reading R21: a row beyond a
+ * wall is the mirror image of the row inside; *mirrored tells which */
+static long nb_index_bc(const orc_sim *s, long x, long y, long z, const int *c, int *mirrored)
+{
+    long yy = y + c[1];
+    *mirrored = 0;
+    if (s->wall_y) {
+        if (yy < 0) {
+            yy = -1 - yy;
+            *mirrored = 1;
+        } else if (yy >= s->ny) {
+            yy = 2L * s->ny - 1 - yy;
+            *mirrored = 1;
+        }
+    } else {
+        yy = wrap(yy, s->ny);
+    }
+    long xx = wrap(x + c[0], s->nx), zz = wrap(z + c[2], s->nz);
+    return (zz * s->ny + yy) * s->nx + xx;
+}
+
+/* stencils of the simulation's box; parity -1: the field changes sign under
+ * the wall mirror */
+static void sim_grad(const orc_sim *s, const double *psi, int parity, double *grad)
+{
+    int Q, c[19][3];
+    double w[19];
+    fd_stencil(s->dim, &Q, c, w);
+    const long N = s->N;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (long z = 0; z < s->nz; ++z)
+        for (long y = 0; y < s->ny; ++y)
+            for (long x = 0; x < s->nx; ++x) {
+                long id = (z * s->ny + y) * s->nx + x;
+                double g[3] = {0.0, 0.0, 0.0};
+                for (int i = 1; i < Q; ++i) {
+                    int m;
+                    double v = psi[nb_index_bc(s, x, y, z, c[i], &m)];
+                    if (m && parity < 0) v = -v;
+                    for (int a = 0; a < s->dim; ++a) g[a] += w[i] * c[i][a] * v;
+                }
+                for (int a = 0; a < s->dim; ++a) grad[a * N + id] = 3.0 * g[a];
+            }
+}
+
+static void sim_lap(const orc_sim *s, const double *psi, int parity, double *lap)
+{
+    int Q, c[19][3];
+    double w[19];
+    fd_stencil(s->dim, &Q, c, w);
+#pragma omp parallel for collapse(2) schedule(static)
+    for (long z = 0; z < s->nz; ++z)
+        for (long y = 0; y < s->ny; ++y)
+            for (long x = 0; x < s->nx; ++x) {
+                long id = (z * s->ny + y) * s->nx + x;
+                double acc = 0.0;
+                for (int i = 1; i < Q; ++i) {
+                    int m;
+                    double v = psi[nb_index_bc(s, x, y, z, c[i], &m)];
+                    if (m && parity < 0) v = -v;
+                    acc += w[i] * (v - psi[id]);
+                }
+                lap[id] = 6.0 * acc;
+            }
+}
+
 void orc_grad(int dim, int nx, int ny, int nz, const double *psi, double *grad)
 {
     int Q, c[19][3];
@@ -551,7 +623,7 @@ void orc_repulsion(int dim, const orc_params *p, const int *n, int np, const orc
             double dx[3], d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double v = a < dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
-                if (a < dim) v -= n[a] * floor(v / n[a] + 0.5);
+                if (a < dim && n[a] > 0) v -= n[a] * floor(v / n[a] + 0.5);
                 dx[a] = v;
                 d2 += v * v;
             }
@@ -572,8 +644,8 @@ static void rel_pos(const orc_sim *s, long x, long y, long z, const double *xp, 
     int n[3] = {s->nx, s->ny, s->nz};
     for (int a = 0; a < 3; ++a) {
         double d = X[a] - xp[a];
-        if (a < s->dim) d -= n[a] * floor(d / n[a] + 0.5);
-        else d = 0.0;
+        if (a < s->dim && !(a == 1 && s->wall_y)) d -= n[a] * floor(d / n[a] + 0.5);
+        else if (a >= s->dim) d = 0.0;
         r[a] = d;
     }
 }
@@ -734,10 +806,10 @@ static void compute_macros(orc_sim *s)
     }
 
     /* stencils */
-    orc_lap(d, s->nx, s->ny, s->nz, s->phi, s->lap_phi);
-    orc_lap(d, s->nx, s->ny, s->nz, s->phi0, s->lap_phi0);
-    orc_grad(d, s->nx, s->ny, s->nz, s->phi, s->gphi);
-    orc_grad(d, s->nx, s->ny, s->nz, s->phi0, s->gphi0);
+    sim_lap(s, s->phi, 1, s->lap_phi);
+    sim_lap(s, s->phi0, 1, s->lap_phi0);
+    sim_grad(s, s->phi, 1, s->gphi);
+    sim_grad(s, s->phi0, 1, s->gphi0);
 
     /* chemical potentials, Eqs. (9), (19) */
     const int own = any_own_angle(s);
@@ -749,9 +821,9 @@ static void compute_macros(orc_sim *s)
     } else {
         /* reading R18: wetting terms per solid through W and V */
         const double sg = p->sigma, D = p->D;
-        orc_lap(d, s->nx, s->ny, s->nz, s->wfld, s->lap_w);
-        orc_grad(d, s->nx, s->ny, s->nz, s->wfld, s->gw);
-        orc_grad(d, s->nx, s->ny, s->nz, s->vfld, s->gv);
+        sim_lap(s, s->wfld, 1, s->lap_w);
+        sim_grad(s, s->wfld, 1, s->gw);
+        sim_grad(s, s->vfld, 1, s->gv);
         for (long id = 0; id < N; ++id) {
             const double ph = s->phi[id], p0 = s->phi0[id], W = s->wfld[id], V = s->vfld[id];
             s->mu[id] = 3.0 * sg / D * ph * (ph - 1.0) * (ph + 1.0) - 3.0 * D * sg / 8.0 * s->lap_phi[id] +
@@ -762,7 +834,7 @@ static void compute_macros(orc_sim *s)
     }
 
     /* S = M grad(mu) (rho1 - rho2)/2 (Sec. 2.2); grad rho from Eq. (17) */
-    orc_grad(d, s->nx, s->ny, s->nz, s->mu, s->gmu);
+    sim_grad(s, s->mu, 1, s->gmu);
     for (long k = 0; k < 3 * N; ++k) {
         s->S[k] = p->M * s->gmu[k] * drho;
         s->grho[k] = drho * s->gphi[k];
@@ -777,7 +849,8 @@ static void compute_macros(orc_sim *s)
             for (long id = 0; id < N; ++id)
                 s->tmp[id] = s->S_prev[a * N + id] * s->u_prev[b * N + id] -
                              s->u_prev[a * N + id] * s->S_prev[b * N + id];
-            orc_grad(d, s->nx, s->ny, s->nz, s->tmp, s->tmp3);
+            /* S_a u_b - u_a S_b changes sign under the wall mirror when a or b is y */
+            sim_grad(s, s->tmp, (a == 1 || b == 1) ? -1 : 1, s->tmp3);
             for (long id = 0; id < N; ++id) s->Fc[b * N + id] += 0.5 * s->tmp3[a * N + id];
         }
 
@@ -921,15 +994,15 @@ void orc_init(orc_sim *s, const double *phi0, const double *phi, const double *u
         s->P[id] = P ? P[id] : 0.0;
         s->rho[id] = drho * phi[id] + 0.5 * (p->rho1 + p->rho2);
     }
-    orc_lap(d, s->nx, s->ny, s->nz, s->phi, s->lap_phi);
-    orc_lap(d, s->nx, s->ny, s->nz, s->phi0, s->lap_phi0);
+    sim_lap(s, s->phi, 1, s->lap_phi);
+    sim_lap(s, s->phi0, 1, s->lap_phi0);
     if (!any_own_angle(s)) {
         for (long id = 0; id < N; ++id)
             s->mu[id] = orc_mu_phi(p, s->phi[id], s->phi0[id], s->lap_phi[id], s->lap_phi0[id]);
     } else {
         /* reading R18, as in the steps */
         const double sg = p->sigma, D = p->D;
-        orc_lap(d, s->nx, s->ny, s->nz, s->wfld, s->lap_w);
+        sim_lap(s, s->wfld, 1, s->lap_w);
         for (long id = 0; id < N; ++id) {
             const double ph = s->phi[id], p0 = s->phi0[id], W = s->wfld[id], V = s->vfld[id];
             s->mu[id] = 3.0 * sg / D * ph * (ph - 1.0) * (ph + 1.0) - 3.0 * D * sg / 8.0 * s->lap_phi[id] +
@@ -937,7 +1010,7 @@ void orc_init(orc_sim *s, const double *phi0, const double *phi, const double *u
                         3.0 * D * sg / 8.0 * s->lap_w[id];
         }
     }
-    orc_grad(d, s->nx, s->ny, s->nz, s->mu, s->gmu);
+    sim_grad(s, s->mu, 1, s->gmu);
     for (long k = 0; k < 3 * N; ++k) s->S[k] = p->M * s->gmu[k] * drho;
     /* step 1 of Sec. 3.3: f = f^eq */
     for (long id = 0; id < N; ++id) {
@@ -1024,19 +1097,29 @@ static void one_step(orc_sim *s)
         for (int i = 0; i < Q2; ++i) s->f2[i * N + id] = f[i] - Lv[i] + Fs[i] - 0.5 * LF[i];
     }
 
-    /* streaming, left-hand side of Eq. (29), periodic box */
+    /* streaming, left-hand side of Eq. (29): periodic box, or (reading R21)
+     * halfway bounce-back where a population would cross a wall */
     for (int lat = 0; lat < 2; ++lat) {
         const orc_lat *L = lat == 0 ? &s->L1 : &s->L2;
         double *src = lat == 0 ? s->f1 : s->f2;
         double *dst = lat == 0 ? s->g1 : s->g2;
+        int opp[ORC_QMAX];
+        for (int i = 0; i < L->Q; ++i)
+            for (int j = 0; j < L->Q; ++j)
+                if (L->c[j][0] == -L->c[i][0] && L->c[j][1] == -L->c[i][1] && L->c[j][2] == -L->c[i][2])
+                    opp[i] = j;
 #pragma omp parallel for collapse(2) schedule(static)
         for (long z = 0; z < s->nz; ++z)
             for (long y = 0; y < s->ny; ++y)
                 for (long x = 0; x < s->nx; ++x) {
                     long id = (z * s->ny + y) * s->nx + x;
-                    for (int i = 0; i < L->Q; ++i)
-                        dst[i * N + nb_index(s->nx, s->ny, s->nz, x, y, z, L->c[i])] =
-                            src[i * N + id];
+                    for (int i = 0; i < L->Q; ++i) {
+                        const long yd = y + L->c[i][1];
+                        if (s->wall_y && (yd < 0 || yd >= s->ny))
+                            dst[opp[i] * N + id] = src[i * N + id];
+                        else
+                            dst[i * N + nb_index(s->nx, s->ny, s->nz, x, y, z, L->c[i])] = src[i * N + id];
+                    }
                 }
     }
     double *t1 = s->f1, *t2 = s->f2;
@@ -1054,7 +1137,7 @@ static void one_step(orc_sim *s)
      * reading R19 from the positions before the update); the indicator follows
      * at the next pass */
     double Frep[ORC_MAXP * 3];
-    const int nn[3] = {s->nx, s->ny, s->nz};
+    const int nn[3] = {s->nx, s->wall_y ? 0 : s->ny, s->nz};
     orc_repulsion(d, p, nn, s->np, s->parts, Frep);
     for (int k = 0; k < s->np; ++k) {
         double Fk[3];
@@ -1149,3 +1232,10 @@ int orc_get_particle(orc_sim *s, int k, orc_particle *pp)
 }
 
 int orc_num_particles(orc_sim *s) { return s->np; }
+
+int orc_set_walls(orc_sim *s, int wall_y)
+{
+    if (wall_y && s->dim != 2) return -1;
+    s->wall_y = wall_y ? 1 : 0;
+    return 0;
+}

@@ -74,6 +74,8 @@ void orc_get_f(orc_sim *s, double *f1, double *f2);
 int orc_set_particle(orc_sim *s, int k, const orc_particle *pp);
 int orc_get_particle(orc_sim *s, int k, orc_particle *pp);
 int orc_num_particles(orc_sim *s);
+/* Reading R21: walls at y = -1/2 and y = ny - 1/2 (2D; before init). */
+int orc_set_walls(orc_sim *s, int wall_y);
 /* The total solid indicator phi0 at the current time. */
 void orc_get_phi0(orc_sim *s, double *phi0);
 
@@ -109,7 +111,7 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp,
 /* Hydrodynamic force and torque on particle k (Eq. 27) at the current time. */
 void orc_particle_force(orc_sim *s, int k, double *F3, double *T3);
 /* Short-range particle-particle repulsion of Sec. 4.5 on each of np
- * particles (minimum image on the periodic box n[3]); out is np x 3. */
+ * particles (minimum image along the axes with n[a] > 0); out is np x 3. */
 void orc_repulsion(int dim, const orc_params *p, const int *n, int np, const orc_particle *parts,
                    double *out);
 

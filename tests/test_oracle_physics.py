@@ -344,3 +344,34 @@ def test_own_contact_angle_superposes_eq9():
     mu2 = o2.macros()["mu"]
     ref = np.array([eq9(P[60.0], p0_tot, i) for i in range(ph.size)]).reshape(ph.shape)
     assert np.abs(mu2 - ref).max() < 1e-14
+
+
+def test_walls_poiseuille_converges_second_order():
+    """Box walls (reading R21, halfway bounce-back): a body-force-driven channel
+    of ny rows between walls at y = -1/2 and ny - 1/2 approaches
+    u(y) = F_b (y + 1/2)(ny - 1/2 - y) / (2 mu) with a second-order error."""
+    errs = []
+    for ny, steps in ((16, 20000), (32, 60000)):
+        nx = 4
+        prm = O.make_params(sigma=0.0, mu1=0.1, mu2=0.1, Fb=(1e-6, 0, 0))
+        s = O.OracleSim((ny, nx), prm)
+        s.set_walls(True)
+        s.init(np.zeros((ny, nx)), np.zeros((ny, nx)))
+        s.step(steps)
+        u = s.macros()["u"][0][:, 0]
+        y = np.arange(ny)
+        ua = 1e-6 / (2 * 0.1) * (y + 0.5) * (ny - 0.5 - y)
+        errs.append(np.abs(u - ua).max() / ua.max())
+    assert errs[1] < 1e-3 and errs[0] / errs[1] > 3.5, errs
+
+
+def test_walls_conserve_mass():
+    """Bounce-back returns every population that would leave: sum phi is kept
+    to round-off with walls (a drop next to them, random initial flow)."""
+    c = W.small_case((40, 36), seed=3, solid=False, u_amp=0.01)
+    s = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+    s.set_walls(True)
+    s.init(c["phi0"], c["phi"], c["u"])
+    m0 = s.diagnostics()["mass"]
+    s.step(400)
+    assert abs(s.diagnostics()["mass"] - m0) <= 1e-13 * np.abs(c["phi"]).sum()
