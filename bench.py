@@ -10,8 +10,10 @@ autotuned launch per time step replayed from a CUDA graph.  One bench step =
 one time step of every domain.
 
 Other workloads: ``drop_on_cylinder`` (512 x 512, density ratio 100, FP32;
-its state fits in L2, so L2 is flushed between individually timed steps) and
-``static_drop`` (128 x 128, FP64).
+its state fits in L2, so L2 is flushed between individually timed steps),
+``static_drop`` (128 x 128, FP64), ``water_entry``, ``annulus`` (moving
+particles), ``porous_2d`` (phase separation in random discs between
+bounce-back walls) and ``drainage_3d``.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload on the host cores.  Under torchrun every rank runs an
@@ -57,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "drop_on_cylinder", "static_drop", "water_entry",
-                             "drainage_3d", "annulus"])
+                             "drainage_3d", "annulus", "porous_2d"])
     ap.add_argument("--n3d", type=int, default=256, help="cube side of drainage_3d")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
@@ -95,6 +97,13 @@ def single_workload(name, n3d=256):
                      "rotating at 1e-4 rad/step, 15 free wetting particles (R 20-30, own contact angles "
                      "45-135 deg), repulsion, gravity on particles; force/torque reduction and "
                      "Newton-Euler in FP64 every step")
+        return c
+    if name == "porous_2d":
+        c = W.porous_phase_separation_2d(n=1024, theta_deg=45.0)
+        c["precision"] = "p32"
+        c["desc"] = ("2D phase separation in a porous medium (Sec. 4.1 setting), 1024x1024, random discs "
+                     "R 6-12 (porosity %.3f), phi = (1 - phi0) U(-1,1), theta 45 deg, sigma 1e-3, M 0.1, "
+                     "equal densities; no-flux bounce-back walls at both ends of y" % c["porosity"])
         return c
     if name == "drainage_3d":
         c = W.porous_drainage_3d(n=n3d)
@@ -210,6 +219,8 @@ def oracle_sample(args, budget_s):
     used = []
     for c in cases:
         o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+        if c.get("walls_y"):
+            o.set_walls(True)
         for k, pp in enumerate(c.get("particles", [])):
             o.set_particle(k, O.Particle(**pp))
         o.init(c["phi0"], c["phi"])
@@ -394,7 +405,8 @@ def run_single(args, dist, rank, world, local):
     bpc = (BYTES_PER_CELL if dim == 2 else BYTES_PER_CELL_3D)[prec]
     in_l2 = cells * bpc < 256e6  # state small enough to stay in the 129 MB L2 between steps
     stream = torch.cuda.Stream()
-    sim = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream, **case["params"])
+    sim = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream,
+                 walls_y=case.get("walls_y", False), **case["params"])
     for k, pp in enumerate(case.get("particles", [])):
         sim.set_particle(k, **pp)
     sim.init(case["phi0"], case["phi"], case.get("u"))
@@ -446,7 +458,8 @@ def run_single(args, dist, rank, world, local):
         phi_h = torch.from_numpy(case["phi"]).pin_memory()
         out_h = torch.empty(cells, dtype=torch.float64).pin_memory()
         L = pf.load()
-        s2 = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream, **case["params"])
+        s2 = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream,
+                 walls_y=case.get("walls_y", False), **case["params"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(iters):

@@ -156,9 +156,12 @@ static int validate(const pf_grid *g, const pf_params *p)
     if (qtot * (pitch * g->ny * nz + 64) >= (1LL << 31))
         return fail(PF_EINVAL, "grid too large: %lld populations x %lld cells must stay below 2^31 "
                     "(32-bit indexing of the state arrays)", qtot, pitch * g->ny * nz);
-    for (int a = 0; a < g->dim; ++a)
-        if (g->periodic[a] != 1)
-            return fail(PF_EINVAL, "only periodic boundaries are supported (walls are phi0 slabs)");
+    for (int a = 0; a < g->dim; ++a) {
+        const bool wall_ok = g->dim == 2 && a == 1 && g->periodic[a] == 0;
+        if (g->periodic[a] != 1 && !wall_ok)
+            return fail(PF_EINVAL, "boundaries must be periodic, except walls at the ends of y in 2D "
+                                   "(periodic[1] = 0)");
+    }
     if (!finite_all(p)) return fail(PF_EINVAL, "non-finite parameter");
     if (p->sigma < 0) return fail(PF_EINVAL, "sigma must be >= 0");
     if (p->D <= 0) return fail(PF_EINVAL, "D must be > 0");
@@ -295,6 +298,7 @@ static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams
     d.nx = g->nx;
     d.ny = g->ny;
     d.nz = dim == 2 ? 1 : g->nz;
+    d.wall_y = dim == 2 && g->periodic[1] == 0 ? 1 : 0;
     d.pitch = (int)round_up(d.nx, 32);
     d.plane = round_up((long long)d.pitch * d.ny * d.nz, 64);
     d.p = dp;
@@ -550,9 +554,16 @@ static int step_mode(const Engine &E)
 
 // the staged 2D step copies 16-byte chunks: every domain's nx must keep its
 // rows' chunks and periodic splits aligned
+static bool any_walls(const Engine &E)
+{
+    for (auto &m : E.mem)
+        if (m.d.wall_y) return true;
+    return false;
+}
+
 static bool stage_ok(const Engine &E)
 {
-    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0) return false;
+    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0 || any_walls(E)) return false;
     const int q = E.prec == PF_P32 ? 4 : 8;
     for (auto &m : E.mem)
         if (m.d.nx % q) return false;
@@ -589,7 +600,7 @@ static int issue_step(Engine &E, int par)
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.d_frep, E.mem[0].d.nx,
-                               E.mem[0].d.ny, E.mem[0].d.nz, E.stream);
+                               E.mem[0].d.wall_y ? 0 : E.mem[0].d.ny, E.mem[0].d.nz, E.stream);
     CK(cudaGetLastError());
     return PF_OK;
 }
@@ -637,7 +648,7 @@ static int engine_configure(Engine &E)
     // (kernel 2, the bulk-copy staged variant, is selectable with
     // pf_set_config but not a candidate: it measured slower than kernel 1)
     int shapes[6][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}};
-    int nshapes = (E.prec != PF_P64 && E.np == 0) ? 6 : 3;
+    int nshapes = (E.prec != PF_P64 && E.np == 0 && !any_walls(E)) ? 6 : 3;
     if (E.dim == 3) {
         tile_shape3d(E.prec, &shapes[0][0], &shapes[0][1]);
         shapes[0][2] = 0;
@@ -1177,6 +1188,8 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
     const int var = kernel;
     if (var < 0 || var > 2) return fail(PF_EINVAL, "kernel must be 0, 1 or 2");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
+    if (var != 0 && any_walls(E))
+        return fail(PF_EINVAL, "domains with walls run kernel 0 only");
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);

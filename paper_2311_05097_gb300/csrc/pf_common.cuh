@@ -148,6 +148,7 @@ inline KParams<R> make_kparams(const DevParams &d)
 // One domain of a (possibly batched) launch.
 struct DomainDev {
     int nx, ny, nz, pitch;
+    int wall_y;      // 2D: walls at y = -1/2 and ny - 1/2 (halfway bounce-back), else periodic
     long long plane;
     void *f[2];      // population buffers
     void *rest[2];   // PMIX rest populations

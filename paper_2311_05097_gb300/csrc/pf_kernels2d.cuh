@@ -17,9 +17,11 @@
 
 namespace pf {
 
-// D2Q9 velocities in the order of the columns of M_0 (Eq. 38).
+// D2Q9 velocities in the order of the columns of M_0 (Eq. 38), and the
+// opposite direction of each.
 __device__ constexpr int CX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int CY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__device__ constexpr int OPP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
 
 // Hermite-moment MRT collision of one D2Q9 cell (Eqs. 29, 37, 38 with c = 1):
@@ -107,7 +109,7 @@ __device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy
 {
     double dx = (double)gx - pp.x[0], dy = (double)gy - pp.x[1];
     dx -= nx * rint(dx / nx);
-    dy -= ny * rint(dy / ny);
+    if (ny > 0) dy -= ny * rint(dy / ny);  // ny <= 0: walls in y, no minimum image
     rx = (R)dx;
     ry = (R)dy;
     double r2 = dx * dx + dy * dy;
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     __shared__ int s_gx[TX + 6];
     __shared__ int s_gy[TY + 6];  // row offsets y * pitch (planes hold < 2^31 cells)
     __shared__ int s_gyi[TY + 6];
+    __shared__ int s_out[TY + 6];  // walls: the row lies beyond a wall (mirror image)
     __shared__ double s_red[NT / 32][6];
     __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
 
@@ -166,12 +169,27 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         if constexpr (MOVING) {
             if (tid == 0) s_near = 0ull;
         }
+        const int wall = Dm.wall_y;
+        const int nyw = wall ? 0 : ny;  // minimum image in y only without walls
         for (int k = tid; k < TX + 6; k += NT) s_gx[k] = wrap_idx(x0 - 3 + k, nx);
         for (int k = tid; k < TY + 6; k += NT) {
-            const int yy = wrap_idx(y0 - 3 + k, ny);
+            const int y = y0 - 3 + k;
+            int yy, out = 0;
+            if (wall) {
+                // rows beyond a wall read their mirror image (clamped: the rows
+                // that far out only feed cells beyond the domain)
+                yy = y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
+                out = y < 0 || y >= ny;
+                yy = min(max(yy, 0), ny - 1);
+            } else {
+                yy = wrap_idx(y, ny);
+            }
             s_gyi[k] = yy;
             s_gy[k] = yy * Dm.pitch;
+            s_out[k] = out;
         }
+        // a tile whose frames reach beyond a wall
+        const bool wall_tile = wall && (y0 - 3 < 0 || y0 + TY + 3 > ny);
         if constexpr (MOVING) {
             // conservative test of the tile + 2 frame against each particle's
             // reach R + cut (minimum image), one thread per particle
@@ -180,7 +198,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const ParticleDev &pp = A.parts[k];
                 double dx = (x0 + 0.5 * (TX - 1)) - pp.x[0], dy = (y0 + 0.5 * (TY - 1)) - pp.x[1];
                 dx -= nx * rint(dx / nx);
-                dy -= ny * rint(dy / ny);
+                if (!wall) dy -= ny * rint(dy / ny);
                 const double ex = fmax(fabs(dx) - (0.5 * TX + 2.0), 0.0);
                 const double ey = fmax(fabs(dy) - (0.5 * TY + 2.0), 0.0);
                 const double lim = pp.R + p.cut + 1.0;
@@ -199,6 +217,16 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         long long *rd = reinterpret_cast<long long *>(Dm.rest[A.par ^ 1]);
         const R isc1 = kp.inv_scale[0], isc2 = kp.inv_scale[1];
 
+        // offset of the population that table cell (cx, cy) pulls as direction
+        // i of the lattice starting at plane `base`: from cell - c_i, or, where
+        // that lies beyond a wall, its own opposite population (halfway
+        // bounce-back)
+        auto pull = [&](int base, int i, int cx, int cy) -> int {
+            if (wall_tile && s_out[cy - CY9[i]] && !s_out[cy])
+                return (base + OPP9[i]) * plane + s_gy[cy] + s_gx[cx];
+            return (base + i) * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]];
+        };
+
         // phi at frame cell (hx, hy) of the tile+2 frame: pull and sum (Eq. 31)
         long long rest_own = 0;
         auto phi_at = [&](int hx, int hy, R *keep, ST *keepq) -> R {
@@ -214,7 +242,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 R movers = R(0);  // sum in stored units, scaled once
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
-                    ST q = ldg(fs + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]]);
+                    ST q = ldg(fs + pull(0, i, cx, cy));
                     const R v = stored_to_float<ST>(q);
                     if (keep) keep[i] = v * isc1;
                     if (keepq) keepq[i] = q;
@@ -225,7 +253,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 acc = R(0);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    R v = Conv<P>::ld(ldg(fs + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]]), isc1);
+                    R v = Conv<P>::ld(ldg(fs + pull(0, i, cx, cy)), isc1);
                     if (keep) keep[i] = v;
                     acc += v;
                 }
@@ -241,7 +269,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 for (int k = 0; k < A.np; ++k) {
                     if (!((near >> k) & 1ull)) continue;
                     R rx, ry;
-                    const R pk = particle_phi0<R>(A.parts[k], gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                    const R pk = particle_phi0<R>(A.parts[k], gx, gy, nx, nyw, p.D, p.cut, rx, ry);
                     v += pk;
                     if (A.parts[k].own) {
                         const R ck = (R)A.parts[k].ct;
@@ -266,8 +294,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         const int id = s_gy[ly + 3] + s_gx[lx + 3];
         ST f2raw[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            f2raw[i] = ldg(fs + (9 + i) * plane + s_gy[ly + 3 - CY9[i]] + s_gx[lx + 3 - CX9[i]]);
+        for (int i = 0; i < 9; ++i) f2raw[i] = ldg(fs + pull(9, i, lx + 3, ly + 3));
         AX lag[5];
         if constexpr (MODE == MODE_STEP) {
 #pragma unroll
@@ -308,7 +335,8 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         if constexpr (MODE == MODE_STEP) {
             // w of the own cell from the lagged fields already in registers; the
             // tile+1 ring by the last threads (the first ones did the phi ring)
-            s_w[ly + 1][lx + 1] = (R)lag[2] * (R)lag[1] - (R)lag[0] * (R)lag[3];
+            // (odd under a wall mirror: rows beyond a wall take the sign change)
+            s_w[ly + 1][lx + 1] = (s_out[ly + 3] ? R(-1) : R(1)) * ((R)lag[2] * (R)lag[1] - (R)lag[0] * (R)lag[3]);
             constexpr int WRING = 2 * WX + 2 * TY;
             static_assert(WRING <= NT, "one tile+1 ring cell per thread at most");
             for (int r = NT - 1 - tid; r >= 0 && r < WRING; r -= NT) {
@@ -324,7 +352,18 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const int wid = s_gy[wy + 2] + s_gx[wx + 2];
                 const R ux = (R)ldg(as + 0 * plane + wid), uy = (R)ldg(as + 1 * plane + wid);
                 const R Sx = (R)ldg(as + 2 * plane + wid), Sy = (R)ldg(as + 3 * plane + wid);
-                s_w[wy][wx] = Sx * uy - ux * Sy;
+                s_w[wy][wx] = (s_out[wy + 2] ? R(-1) : R(1)) * (Sx * uy - ux * Sy);
+            }
+        }
+        if (wall_tile) {
+            // phi beyond a wall is the mirror image of phi inside (no flux)
+            __syncthreads();
+            for (int r = tid; r < FX * FY; r += NT) {
+                const int hx = r % FX, hy = r / FX;
+                if (!s_out[hy + 1]) continue;
+                const int y = y0 - 2 + hy;
+                const int hym = (y < 0 ? -1 - y : 2 * ny - 1 - y) - (y0 - 2);
+                if (hym >= 0 && hym < FY && !s_out[hym + 1]) s_phi[hy][hx] = s_phi[hym][hx];
             }
         }
         __syncthreads();
@@ -413,7 +452,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     const int nid = s_gy[ly + 3 + j] + s_gx[lx + 3 + i];
                     const R ux = (R)ldg(as + 0 * plane + nid), uy = (R)ldg(as + 1 * plane + nid);
                     const R sx = (R)ldg(as + 2 * plane + nid), sy = (R)ldg(as + 3 * plane + nid);
-                    wv[j + 1][i + 1] = sx * uy - ux * sy;
+                    wv[j + 1][i + 1] = (s_out[ly + 3 + j] ? R(-1) : R(1)) * (sx * uy - ux * sy);
                 }
             R wgx, wgy;
             grad9<R, 3>(wv, 1, 1, wgx, wgy);
@@ -438,7 +477,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 if (!((near >> k) & 1ull)) continue;
                 const ParticleDev &pp = A.parts[k];
                 R rx, ry;
-                const R pk = particle_phi0<R>(pp, gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                const R pk = particle_phi0<R>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
                 if (pk != R(0)) {
                     const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                     const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
@@ -602,7 +641,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     double c6[6] = {0, 0, 0, 0, 0, 0};
                     if (valid) {
                         R rx, ry;
-                        const R pk = particle_phi0<R>(pp, gx, gy, nx, ny, p.D, p.cut, rx, ry);
+                        const R pk = particle_phi0<R>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
                         if (pk != R(0)) {
                             const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                             const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;

@@ -26,6 +26,14 @@ __device__ __forceinline__ long long lin_of(const DomainDev &Dm, int x, int y, i
     return ((long long)z * Dm.ny + y) * Dm.nx + x;
 }
 
+// row of a neighbour at y: periodic, or, with walls at the ends of y, the
+// mirror image of the row inside (zero normal gradient)
+__device__ __forceinline__ int row_bc(const DomainDev &Dm, int y)
+{
+    if (Dm.wall_y) return y < 0 ? -1 - y : (y >= Dm.ny ? 2 * Dm.ny - 1 - y : y);
+    return wrap_idx(y, Dm.ny);
+}
+
 // FD stencil (D2Q9 or D3Q19 with classical weights, cs^2 = 1/3) on a dense
 // x-fastest double array.
 __device__ void fd_grad_lap(const DomainDev &Dm, const double *a, int x, int y, int z, double g[3],
@@ -50,7 +58,7 @@ __device__ void fd_grad_lap(const DomainDev &Dm, const double *a, int x, int y, 
             cz = L19[i][2];
             w = i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0;
         }
-        const int xx = wrap_idx(x + cx, Dm.nx), yy = wrap_idx(y + cy, Dm.ny),
+        const int xx = wrap_idx(x + cx, Dm.nx), yy = row_bc(Dm, y + cy),
                   zz = dim == 2 ? 0 : wrap_idx(z + cz, Dm.nz);
         const double v = a[lin_of(Dm, xx, yy, zz)];
         g[0] += w * cx * v;
@@ -72,7 +80,7 @@ __device__ double particle_indicator_d(const ParticleDev &pp, int x, int y, int 
     const int n[3] = {Dm.nx, Dm.ny, Dm.nz};
     double r2 = 0.0;
     for (int a = 0; a < 3; ++a) {
-        if (a < dim) d[a] -= n[a] * rint(d[a] / n[a]);
+        if (a < dim && !(a == 1 && Dm.wall_y)) d[a] -= n[a] * rint(d[a] / n[a]);
         r[a] = d[a];
         r2 += d[a] * d[a];
     }
@@ -104,6 +112,8 @@ struct InitLat<2> {
     }
     template <class R>
     static __device__ __forceinline__ R w2(int i, R d0) { return w1<R>(i, d0); }
+    static __device__ __forceinline__ int opp(int i) { return i == 0 ? 0 : (i <= 4 ? 1 + (i + 1) % 4 : 5 + (i - 3) % 4); }
+    static __device__ __forceinline__ int opp2(int i) { return opp(i); }
 };
 template <>
 struct InitLat<3> {
@@ -121,6 +131,9 @@ struct InitLat<3> {
         return i == 0 ? R(1) - R(3) * d0 + R(3) * d0 * d0
                       : (i <= 6 ? R(0.5) * (d0 - R(2) * d0 * d0) : R(0.25) * d0 * d0);
     }
+    // walls are 2D only: the 3D lattices never bounce back
+    static __device__ __forceinline__ int opp(int i) { return i; }
+    static __device__ __forceinline__ int opp2(int i) { return i; }
 };
 
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -139,7 +152,7 @@ __device__ __forceinline__ void fd_grad_lap_r(const DomainDev &Dm, const double 
     for (int i = 1; i < Q; ++i) {
         const int cx = InitLat<DIM>::c2(i, 0), cy = InitLat<DIM>::c2(i, 1), cz = InitLat<DIM>::c2(i, 2);
         const R w = DIM == 2 ? (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0)) : (i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0));
-        const int xx = wrap1(x + cx, Dm.nx), yy = wrap1(y + cy, Dm.ny), zz = DIM == 2 ? 0 : wrap1(z + cz, Dm.nz);
+        const int xx = wrap1(x + cx, Dm.nx), yy = row_bc(Dm, y + cy), zz = DIM == 2 ? 0 : wrap1(z + cz, Dm.nz);
         const R v = (R)a[lin_of(Dm, xx, yy, zz)];
         g[0] += w * R(cx) * v;
         g[1] += w * R(cy) * v;
@@ -216,8 +229,9 @@ __global__ void k_init_mu(DomainDev Dm, const double *phi, const double *phi0tot
 }
 
 // f = f^eq (Eqs. 30, 32) stored for pull streaming: population i of cell x is
-// written at x - c_i so that the first step reads f^eq_i(x).  Lagged fields
-// equal the initial ones.
+// written at x - c_i so that the first step reads f^eq_i(x); where x - c_i
+// lies beyond a wall the first step bounces back, reading population opp(i)
+// of x itself, so it is written there.  Lagged fields equal the initial ones.
 template <class P, int DIM>
 __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const double *u, const double *Pin,
                          const double *mu)
@@ -256,17 +270,20 @@ __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const doub
             for (int a = 0; a < DIM; ++a) cu += R(LT::c1(i, a)) * uu[a];
             const R wi = LT::template w1<R>(i, d0);
             const R fe = i == 0 ? ph + (wi - R(1)) * em : wi * em + wi * cu * ph / cs2;
-            const int xx = wrap1(x - LT::c1(i, 0), Dm.nx), yy = wrap1(y - LT::c1(i, 1), Dm.ny),
+            const int ys = y - LT::c1(i, 1);
+            const bool bb = Dm.wall_y && (ys < 0 || ys >= Dm.ny);
+            const int xx = bb ? x : wrap1(x - LT::c1(i, 0), Dm.nx), yy = bb ? y : wrap1(ys, Dm.ny),
                       zz = DIM == 3 ? wrap1(z - LT::c1(i, 2), Dm.nz) : 0;
             const long long id = cell_of(Dm, xx, yy, zz);
+            const int slot = bb ? LT::opp(i) : i;
             if constexpr (P::MIX) {
                 if (i == 0) continue;
                 ST q = Conv<P>::st(fe, (R)p.scale[0]);
                 if constexpr (P::id == 3) q = bf16_flush(q);
                 rest_s += fix24_sat<ST>(q, &bad);
-                f[i * plane + id] = q;
+                f[slot * plane + id] = q;
             } else {
-                f[i * plane + id] = (ST)fe;
+                f[slot * plane + id] = (ST)fe;
             }
         }
         if constexpr (P::MIX) rest[cell_of(Dm, x, y, z)] = fixed_of_double(phd) - fix24_to_rest(rest_s, p.klog2[0]);
@@ -287,13 +304,16 @@ __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const doub
             const R wi = LT::template w2<R>(i, d0);
             const R lam = (i == 0 ? wi - R(1) : wi) * Pv / cs2;
             const R fe = lam + wi * rho * cu / cs2 + wi * (diag / (cs2 - cs4) + off / cs4);
-            const int xx = wrap1(x - LT::c2(i, 0), Dm.nx), yy = wrap1(y - LT::c2(i, 1), Dm.ny),
+            const int ys = y - LT::c2(i, 1);
+            const bool bb = Dm.wall_y && (ys < 0 || ys >= Dm.ny);
+            const int xx = bb ? x : wrap1(x - LT::c2(i, 0), Dm.nx), yy = bb ? y : wrap1(ys, Dm.ny),
                       zz = DIM == 3 ? wrap1(z - LT::c2(i, 2), Dm.nz) : 0;
             const long long id = cell_of(Dm, xx, yy, zz);
+            const int slot = LT::Q1 + (bb ? LT::opp2(i) : i);
             if constexpr (P::MIX) {
-                f[(LT::Q1 + i) * plane + id] = Conv<P>::st(fe, (R)p.scale[1]);
+                f[slot * plane + id] = Conv<P>::st(fe, (R)p.scale[1]);
             } else {
-                f[(LT::Q1 + i) * plane + id] = (ST)fe;
+                f[slot * plane + id] = (ST)fe;
             }
         }
         const long long id = cell_of(Dm, x, y, z);
@@ -392,7 +412,7 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
             double dx[3], d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double v = a < p.dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
-                if (a < p.dim) v -= n[a] * floor(v / n[a] + 0.5);
+                if (a < p.dim && n[a] > 0) v -= n[a] * floor(v / n[a] + 0.5);  // n <= 0: walls
                 dx[a] = v;
                 d2 += v * v;
             }

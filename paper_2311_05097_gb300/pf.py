@@ -146,13 +146,15 @@ def make_params(precision=PF_P64, stream=None, **kw):
     return p
 
 
-def make_grid(shape):
+def make_grid(shape, walls_y=False):
+    """Grid of a (ny, nx) or (nz, ny, nx) box; walls_y (2D): no-flux walls at
+    both ends of y instead of periodicity."""
     g = pf_grid()
     if len(shape) == 2:
         g.dim, g.ny, g.nx, g.nz = 2, shape[0], shape[1], 1
     else:
         g.dim, g.nz, g.ny, g.nx = 3, shape[0], shape[1], shape[2]
-    g.periodic = (C.c_int * 3)(1, 1, 1)
+    g.periodic = (C.c_int * 3)(1, 0 if walls_y else 1, 1)
     return g
 
 
@@ -178,14 +180,15 @@ def _is_device(a):
 
 
 class Sim:
-    """A single periodic domain advanced by libpf (pf_create ... pf_destroy)."""
+    """One domain advanced by libpf (pf_create ... pf_destroy): periodic, or in
+    2D with walls_y=True bounded by no-flux walls at both ends of y."""
 
-    def __init__(self, shape, precision=PF_P64, stream=None, **params):
+    def __init__(self, shape, precision=PF_P64, stream=None, walls_y=False, **params):
         L = load()
         self.shape = tuple(shape)
         self.dim = len(shape)
         self.N = int(np.prod(shape))
-        self._g = make_grid(shape)
+        self._g = make_grid(shape, walls_y)
         self._p = make_params(precision=precision, stream=stream, **params)
         h = C.c_void_p()
         _check(L.pf_create(C.byref(self._g), C.byref(self._p), C.byref(h)))
@@ -263,14 +266,16 @@ class Sim:
 
 
 class Batch:
-    """Many independent domains of uneven size advanced together (pf_batch_*)."""
+    """Many independent domains of uneven size advanced together (pf_batch_*);
+    walls_y: one flag for all domains or one per domain (2D)."""
 
-    def __init__(self, shapes, params_list, precision=PF_PMIX_FP16, stream=None):
+    def __init__(self, shapes, params_list, precision=PF_PMIX_FP16, stream=None, walls_y=False):
         L = load()
         n = len(shapes)
         self.shapes = [tuple(s) for s in shapes]
         self.dim = len(shapes[0])
-        G = (pf_grid * n)(*[make_grid(s) for s in shapes])
+        wl = list(walls_y) if isinstance(walls_y, (list, tuple)) else [walls_y] * n
+        G = (pf_grid * n)(*[make_grid(s, w) for s, w in zip(shapes, wl)])
         P = (pf_params * n)(*[make_params(precision=precision, stream=stream, **pp)
                                for pp in params_list])
         h = C.c_void_p()

@@ -193,6 +193,55 @@ def porous_drainage_3d(n=256, seed=0, D=4.0, invade=24, porosity=0.6):
                 name="porous_drainage_3d", porosity=achieved, spheres=len(radii))
 
 
+def rsa_discs(shape, seed=0, rmin=6.0, rmax=12.0, porosity=0.7, clear=2.0, max_tries=20000):
+    """Random sequential addition of non-overlapping discs in a box periodic in
+    x and bounded in y (each disc at least ``clear`` from the ends of y),
+    until the solid fraction reaches 1 - porosity or ``max_tries`` consecutive
+    rejections.  Returns (centres (x, y), radii)."""
+    rng = np.random.default_rng(seed)
+    ny, nx = shape
+    cents = np.zeros((0, 2))
+    radii = np.zeros(0)
+    target = (1.0 - porosity) * nx * ny
+    area = 0.0
+    fails = 0
+    while area < target and fails < max_tries:
+        r = rng.uniform(rmin, rmax)
+        c = np.array([rng.uniform(0, nx), rng.uniform(r + clear, ny - r - clear)])
+        if len(radii):
+            d = cents - c
+            d[:, 0] -= nx * np.floor(d[:, 0] / nx + 0.5)
+            if np.any((d * d).sum(1) < (radii + r + 1.0) ** 2):
+                fails += 1
+                continue
+        fails = 0
+        cents = np.vstack([cents, c])
+        radii = np.append(radii, r)
+        area += math.pi * r * r
+    return cents, radii
+
+
+def porous_phase_separation_2d(n=256, theta_deg=90.0, seed=0, porosity=0.7, D=4.0):
+    """Phase separation inside a 2D porous medium (the setting of Sec. 4.1,
+    with random discs standing in for the micro-CT image): no-flux walls at
+    both ends of y (periodic in x), phi = (1 - phi0) * U(-1, 1) per cell,
+    equal densities and viscosities, sigma = 0.001, M = 0.1, D = 4."""
+    shape = (n, n)
+    cents, radii = rsa_discs(shape, seed=seed, porosity=porosity)
+    x, y = _coords(shape)
+    zeta = np.full(shape, -1e9)
+    for c, r in zip(cents, radii):
+        dx = x - c[0]
+        dx -= n * np.floor(dx / n + 0.5)
+        zeta = np.maximum(zeta, r - np.sqrt(dx * dx + (y - c[1]) ** 2))
+    phi0 = smooth_indicator(zeta, D)
+    rng = np.random.default_rng(seed + 1000)
+    phi = (1.0 - phi0) * rng.uniform(-1.0, 1.0, shape)
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, theta_deg=theta_deg, d0=0.4)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, walls_y=True,
+                name="porous_phase_separation_2d", porosity=float((phi0 < 0.5).mean()), discs=len(radii))
+
+
 def water_entry(nx=1024, ny=2048, depth=800, wall=8, R=40.0, gap=200.0, D=4.0):
     """2D water entry of a particle (density 2 rho1, theta 90 deg) dropped at
     -0.02 towards a liquid pool of depth ``depth`` resting on a wall slab;
@@ -342,6 +391,31 @@ def random_smooth(shape, seed, amp=1.0, modes=4):
         arg = sum(2 * math.pi * k[a] * X[a] / n[a] for a in range(len(shape)))
         f += rng.uniform(-1, 1) * np.sin(arg + ph)
     return amp * f / max(1.0, np.abs(f).max())
+
+
+def wall_case(shape, seed=0, solid=True, theta_deg=60.0, u_amp=0.01, D=4.0):
+    """2D box with no-flux walls at both ends of y: a drop cut by the top wall
+    (a 90 degree contact line there), a solid disc close to the bottom wall and
+    a smooth random initial flow.  Used by the wall parity tests."""
+    rng = np.random.default_rng(seed)
+    ny, nx = shape
+    x, y = _coords(shape)
+
+    def dist(cx, cy):  # periodic in x only: no image across a wall
+        dx = x - cx
+        dx -= nx * np.floor(dx / nx + 0.5)
+        return np.sqrt(dx * dx + (y - cy) ** 2)
+
+    phi0 = np.zeros(shape)
+    if solid:
+        phi0 = smooth_indicator(0.15 * min(nx, ny) - dist(nx * rng.uniform(0.2, 0.3), 0.22 * ny), D)
+    phi = (1.0 - phi0) * np.tanh(2.0 * (0.25 * min(nx, ny) - dist(nx * rng.uniform(0.55, 0.65), 0.88 * ny)) / D)
+    u = None
+    if u_amp > 0:
+        u = np.stack([random_smooth(shape, seed + 10 + a, amp=u_amp) for a in range(2)])
+    p = params(sigma=0.01, D=D, M=0.02, rho1=1.0, rho2=0.1, mu1=0.1, mu2=0.01,
+               theta_deg=theta_deg, d0=0.4)
+    return dict(shape=shape, phi0=phi0, phi=phi, u=u, params=p)
 
 
 def small_case(shape, seed=0, solid=True, theta_deg=60.0, rho_ratio=10.0, mu_ratio=10.0,

@@ -35,10 +35,12 @@ def rel(a, b):
     return float(np.abs(a - b).max() / (s if s > 0 else 1.0))
 
 
-def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True, config=None):
+def run_pair(pf, case, steps, precision="p64", particles=(), oracle=True, config=None, walls=False):
     prm = case["params"]
-    g = pf.Sim(case["shape"], precision=precision, **prm)
+    g = pf.Sim(case["shape"], precision=precision, walls_y=walls, **prm)
     o = O.OracleSim(case["shape"], O.make_params(**prm)) if oracle else None
+    if o is not None and walls:
+        o.set_walls(True)
     for k, pp in enumerate(particles):
         g.set_particle(k, **pp)
         if o is not None:
@@ -419,3 +421,95 @@ def test_batch_fp16_mass_and_diagnostics(pf):
         d = b.diagnostics(i)
         assert d["nan_flag"] == 0
         assert abs(d["mass"] - m0[i]) / np.abs(c["phi"]).sum() < 1e-13
+
+
+# ---- box walls at the ends of y (2D; halfway bounce-back, mirrored stencils) ------------
+
+@pytest.mark.parametrize("shape,steps,config", [
+    ((37, 52), 0, None),
+    ((37, 52), 150, None),
+    ((44, 33), 120, (64, 4, 0)),
+    ((29, 70), 120, (32, 16, 0)),
+])
+def test_walls_p64_matches_oracle(pf, shape, steps, config):
+    """A drop cut by the top wall, a disc near the bottom one, random initial
+    flow; ragged row counts so that the wall rows fall inside partial tiles."""
+    c = W.wall_case(shape, seed=3)
+    g, o = run_pair(pf, c, steps, config=config, walls=True)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K", "E_total"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, k
+
+
+def test_walls_moving_particle_matches_oracle(pf):
+    """A free particle close to the bottom wall: its indicator and force sums
+    take no periodic image across the wall."""
+    c = W.wall_case((48, 56), seed=5, solid=False)
+    part = dict(x=(20.3, 8.6), u=(0.01, -0.004), w=(0.0, 0.0, 0.002), R=6.0, rho_p=2.0)
+    c["phi"] = (1.0 - W.disc(c["shape"], part["x"], part["R"], c["params"]["D"])) * c["phi"]
+    g, o = run_pair(pf, c, 80, particles=[part], walls=True)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    pg, po = g.particle(0), o.particle(0)
+    for k in ("x", "u", "w", "F", "T"):
+        a, b = np.array(pg[k]), np.array(getattr(po, k))
+        assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, a, b)
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_walls_reduced_precision_against_oracle(pf, precision, tol_phi):
+    c = W.wall_case((37, 52), seed=3)
+    g, o = run_pair(pf, c, 200, precision=precision, walls=True)
+    gm, om = g.macros(), o.macros()
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    if precision == "p32":
+        assert rel(gm["rho"], om["rho"]) < 1e-5
+        assert rel(gm["u"], om["u"]) < 1e-3
+        assert rel(gm["P"], om["P"]) < 1e-3
+    assert g.diagnostics()["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_walls_conserve_mass_exactly(pf, precision):
+    """Bounce-back hands every stored population to exactly one puller, so the
+    fixed-point bookkeeping keeps sum phi exact with walls too."""
+    c = W.wall_case((64, 80), seed=4)
+    g, _ = run_pair(pf, c, 0, precision=precision, oracle=False, walls=True)
+    m0 = g.diagnostics()["mass"]
+    g.step(1000)
+    m1 = g.diagnostics()["mass"]
+    assert abs(m1 - m0) / np.abs(c["phi"]).sum() < 1e-13
+
+
+def test_walls_reject_pair_kernels(pf):
+    c = W.wall_case((32, 64), seed=1, solid=False)
+    g = pf.Sim(c["shape"], precision="fp16", walls_y=True, **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError) as ei:
+        g.set_config(32, 16, 1)
+    assert ei.value.code == pf.PF_EINVAL
+    g.set_config(32, 8, 0)
+    g.step(4)
+
+
+def test_batch_mixes_wall_and_periodic_domains(pf):
+    """One batch holding a walled domain and a periodic one (per-domain
+    boundary flag in the tile table): each evolves as when run alone."""
+    cases = [W.wall_case((37, 52), seed=3), W.small_case((52, 40), seed=3, solid=False, u_amp=0.01)]
+    steps = 300
+    b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="p64",
+                 walls_y=[True, False])
+    for i, c in enumerate(cases):
+        b.init(i, c["phi0"], c["phi"], c.get("u"))
+    b.step(steps)
+    b.sync()
+    for i, c in enumerate(cases):
+        g, _ = run_pair(pf, c, steps, oracle=False, walls=(i == 0))
+        mb, mg = b.macros(i), g.macros()
+        for k in FIELDS:
+            assert np.array_equal(mb[k], mg[k]), (i, k)
+    o = O.OracleSim(cases[0]["shape"], O.make_params(**cases[0]["params"]))
+    o.set_walls(True)
+    o.init(cases[0]["phi0"], cases[0]["phi"], cases[0]["u"])
+    o.step(steps)
+    assert_fields(b.macros(0), o.macros(), 1e-12)
