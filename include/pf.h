@@ -101,7 +101,15 @@ typedef struct pf_params {
                           (x_k - x_j)/eps (R_k + R_j + xi - d)^2 for
                           R_k + R_j <= d <= R_k + R_j + xi, (x_k - x_j)/eps
                           (R_k + R_j - d) for d < R_k + R_j (as printed), zero
-                          beyond; added to Eq. 26a, not to pf_particle.F */
+                          beyond; added to Eq. 26a, not to pf_particle.F.
+                          With eps > 0 each particle is also pushed off the
+                          nearest wall: the same form with 2 R_k for R_k + R_j,
+                          eps/2 for eps and the mirror image of the particle
+                          across that wall for x_j (the box walls of pf_grid,
+                          and the circle wall_circle) */
+    double wall_circle[3]; /* 2D: a circular wall (centre x, y; radius) seen only
+                              by the particle-wall repulsion (the fluid sees
+                              walls through phi0); radius 0: none */
     int precision;     /* PF_P64, PF_P32, PF_PMIX_FP16, PF_PMIX_BF16 */
     int store_log2_scale[2]; /* PMIX: stored value = population * 2^k for the
                                 order-parameter [0] and flow [1] lattices;

@@ -20,7 +20,7 @@ class OrcParams(C.Structure):
         ("d0", C.c_double), ("s0", C.c_double), ("s1", C.c_double), ("s2", C.c_double),
         ("s3", C.c_double), ("s4", C.c_double), ("theta_deg", C.c_double),
         ("Fb", C.c_double * 3), ("g", C.c_double * 3), ("solid_eps", C.c_double),
-        ("rep_xi", C.c_double), ("rep_eps", C.c_double),
+        ("rep_xi", C.c_double), ("rep_eps", C.c_double), ("wall_circle", C.c_double * 3),
     ]
 
 
@@ -80,7 +80,7 @@ def lib():
         L.orc_particle_force.argtypes = [C.c_void_p, C.c_int, _DP, _DP]
         L.orc_set_walls.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_walls.restype = C.c_int
-        L.orc_repulsion.argtypes = [C.c_int, C.POINTER(OrcParams), _IP, C.c_int,
+        L.orc_repulsion.argtypes = [C.c_int, C.POINTER(OrcParams), _IP, C.c_int, C.c_int,
                                     C.POINTER(OrcParticle), _DP]
         _lib = L
     return _lib
@@ -105,11 +105,12 @@ def make_params(**kw):
     """Oracle parameters from keyword arguments (paper defaults for the rest)."""
     d = dict(sigma=0.01, D=4.0, M=0.02, eta=0.0, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
              d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, theta_deg=90.0,
-             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0)
+             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0,
+             wall_circle=(0.0, 0.0, 0.0))
     d.update(kw)
     p = OrcParams()
     for k, v in d.items():
-        if k in ("Fb", "g"):
+        if k in ("Fb", "g", "wall_circle"):
             v = tuple(v) + (0.0,) * (3 - len(v))
             setattr(p, k, (C.c_double * 3)(*v))
         else:
@@ -322,12 +323,13 @@ def particle_update(dim, params, part, Ff, Tf):
     return Particle.from_c(c)
 
 
-def repulsion(dim, params, n, parts):
-    """Repulsion force on each particle (np x 3), reading R19."""
+def repulsion(dim, params, n, parts, walls_y=False):
+    """Repulsion force on each particle (np x 3), readings R19 and R22; n is
+    (nx, ny[, nz]); walls_y: box walls at the ends of y."""
     arr = (OrcParticle * max(len(parts), 1))(*[q.to_c() for q in parts])
     nn = (C.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
     out = np.zeros(3 * max(len(parts), 1))
-    lib().orc_repulsion(dim, C.byref(params), nn, len(parts), arr, _p(out))
+    lib().orc_repulsion(dim, C.byref(params), nn, 1 if walls_y else 0, len(parts), arr, _p(out))
     return out[:3 * len(parts)].reshape(len(parts), 3)
 
 

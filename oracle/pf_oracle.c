@@ -53,13 +53,17 @@
  *   R19 particle-particle repulsion of Sec. 4.5 as printed: (x_k - x_j)/eps times
  *       (R_k + R_j + xi - d)^2 for R_k + R_j <= d <= R_k + R_j + xi, times
  *       (R_k + R_j - d) for d <= R_k + R_j, zero beyond (minimum image), added to
- *       the force of Eq. (26a) from the positions before the update.  The
- *       particle-wall form needs a wall geometry and is not built.
+ *       the force of Eq. (26a) from the positions before the update.
  *   R21 box walls (2D, y = -1/2 and y = ny - 1/2; the paper's no-flux boxes):
  *       halfway bounce-back of both lattices at resting walls; the stencils read
  *       rows beyond a wall as the mirror image of the rows inside (zero normal
  *       gradient of phi, mu and phi0: no flux), except the products
  *       S_a u_b - u_a S_b of F_c, which change sign under the mirror.
+ *   R22 particle-wall repulsion of Sec. 4.5: the imaginary particle is the
+ *       mirror image of particle k across the nearest wall (a box wall of R21,
+ *       or a circular wall given by centre and radius, mirrored along the
+ *       radius), d' its distance; the printed form with 2 R_k for R_k + R_j and
+ *       eps/2 for eps; the nearest wall only; added like R19.
  */
 #include "pf_oracle.h"
 
@@ -611,19 +615,59 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp, const d
     }
 }
 
-/* Reading R19: particle-particle repulsion of Sec. 4.5 on each particle. */
-void orc_repulsion(int dim, const orc_params *p, const int *n, int np, const orc_particle *parts,
-                   double *out)
+/* Readings R19 and R22: particle-particle and particle-wall repulsion of
+ * Sec. 4.5 on each particle. */
+void orc_repulsion(int dim, const orc_params *p, const int *n, int wall_y, int np,
+                   const orc_particle *parts, double *out)
 {
     for (int k = 0; k < np; ++k) {
         for (int a = 0; a < 3; ++a) out[3 * k + a] = 0.0;
         if (!(p->rep_eps > 0.0)) continue;
+        /* the wall: x_k - x'_k towards the nearest imaginary particle, the
+         * mirror image of particle k across the nearest wall */
+        double best = INFINITY, dw[3] = {0.0, 0.0, 0.0};
+        if (wall_y && dim == 2) {
+            const double y = parts[k].x[1];
+            const double d_lo = 2.0 * (y + 0.5), d_hi = 2.0 * (n[1] - 0.5 - y);
+            if (d_lo < best) {
+                best = d_lo;
+                dw[0] = 0.0;
+                dw[1] = d_lo;
+            }
+            if (d_hi < best) {
+                best = d_hi;
+                dw[0] = 0.0;
+                dw[1] = -d_hi;
+            }
+        }
+        if (dim == 2 && p->wall_circle[2] > 0.0) {
+            const double ex = parts[k].x[0] - p->wall_circle[0], ey = parts[k].x[1] - p->wall_circle[1];
+            const double r = sqrt(ex * ex + ey * ey);
+            if (r > 0.0) {
+                /* image at radius 2 R_w - r on the same ray */
+                const double dd = 2.0 * fabs(p->wall_circle[2] - r);
+                if (dd < best) {
+                    const double s = (r - (2.0 * p->wall_circle[2] - r)) / r;
+                    best = dd;
+                    dw[0] = s * ex;
+                    dw[1] = s * ey;
+                }
+            }
+        }
+        if (best < INFINITY) {
+            const double rr = 2.0 * parts[k].R;
+            double f;
+            if (best > rr + p->rep_xi) f = 0.0;
+            else if (best >= rr) f = (rr + p->rep_xi - best) * (rr + p->rep_xi - best) / (0.5 * p->rep_eps);
+            else f = (rr - best) / (0.5 * p->rep_eps);
+            for (int a = 0; a < 3; ++a) out[3 * k + a] += f * dw[a];
+        }
         for (int j = 0; j < np; ++j) {
             if (j == k) continue;
             double dx[3], d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double v = a < dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
-                if (a < dim && n[a] > 0) v -= n[a] * floor(v / n[a] + 0.5);
+                if (a < dim && !(a == 1 && wall_y)) v -= n[a] * floor(v / n[a] + 0.5);
                 dx[a] = v;
                 d2 += v * v;
             }
@@ -1137,8 +1181,8 @@ static void one_step(orc_sim *s)
      * reading R19 from the positions before the update); the indicator follows
      * at the next pass */
     double Frep[ORC_MAXP * 3];
-    const int nn[3] = {s->nx, s->wall_y ? 0 : s->ny, s->nz};
-    orc_repulsion(d, p, nn, s->np, s->parts, Frep);
+    const int nn[3] = {s->nx, s->ny, s->nz};
+    orc_repulsion(d, p, nn, s->wall_y, s->np, s->parts, Frep);
     for (int k = 0; k < s->np; ++k) {
         double Fk[3];
         for (int a = 0; a < 3; ++a) Fk[a] = Ff[k][a] + Frep[3 * k + a];

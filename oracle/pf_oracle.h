@@ -36,6 +36,9 @@ typedef struct orc_params {
     double solid_eps;  /* lower bound on 1 - phi0 in the viscosity (reading of Eq. 35) */
     double rep_xi;     /* particle-particle repulsion range xi (Sec. 4.5) */
     double rep_eps;    /* its stiffness epsilon; <= 0 switches the repulsion off */
+    double wall_circle[3]; /* circular wall (centre x, y; radius) seen by the
+                              particle-wall repulsion (reading R22); radius <= 0:
+                              none */
 } orc_params;
 
 typedef struct orc_particle {
@@ -110,10 +113,13 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp,
                          const double *Ff, const double *Tf);
 /* Hydrodynamic force and torque on particle k (Eq. 27) at the current time. */
 void orc_particle_force(orc_sim *s, int k, double *F3, double *T3);
-/* Short-range particle-particle repulsion of Sec. 4.5 on each of np
- * particles (minimum image along the axes with n[a] > 0); out is np x 3. */
-void orc_repulsion(int dim, const orc_params *p, const int *n, int np, const orc_particle *parts,
-                   double *out);
+/* Short-range repulsion of Sec. 4.5 on each of np particles: from the other
+ * particles (minimum image along periodic axes; wall_y: y is bounded by walls
+ * at -1/2 and n[1] - 1/2) plus, from the nearest wall (the box walls when
+ * wall_y, the circle p->wall_circle), the particle-wall term (reading R22);
+ * out is np x 3. */
+void orc_repulsion(int dim, const orc_params *p, const int *n, int wall_y, int np,
+                   const orc_particle *parts, double *out);
 
 #ifdef __cplusplus
 }

@@ -138,7 +138,8 @@ static bool finite_all(const pf_params *p)
 {
     const double v[] = {p->sigma, p->D, p->M, p->eta, p->rho1, p->rho2, p->mu1, p->mu2, p->d0,
                         p->s0, p->s1, p->s2, p->s3, p->s4, p->theta_deg, p->Fb[0], p->Fb[1],
-                        p->Fb[2], p->g[0], p->g[1], p->g[2], p->solid_eps, p->rep_xi, p->rep_eps};
+                        p->Fb[2], p->g[0], p->g[1], p->g[2], p->solid_eps, p->rep_xi, p->rep_eps,
+                        p->wall_circle[0], p->wall_circle[1], p->wall_circle[2]};
     for (double x : v)
         if (!std::isfinite(x)) return false;
     return true;
@@ -176,6 +177,8 @@ static int validate(const pf_grid *g, const pf_params *p)
         if (!(x > 0 && x < 2)) return fail(PF_EINVAL, "relaxation rates must lie in (0, 2)");
     if (!(p->solid_eps > 0 && p->solid_eps < 1)) return fail(PF_EINVAL, "solid_eps must lie in (0, 1)");
     if (p->rep_xi < 0 || p->rep_eps < 0) return fail(PF_EINVAL, "rep_xi and rep_eps must be >= 0");
+    if (p->wall_circle[2] < 0 || (g->dim == 3 && p->wall_circle[2] > 0))
+        return fail(PF_EINVAL, "wall_circle: radius >= 0, 2D only");
     if (p->precision < PF_P64 || p->precision > PF_PMIX_BF16)
         return fail(PF_EINVAL, "unknown precision %d", p->precision);
     const double cs2 = p->d0;
@@ -216,6 +219,7 @@ static DevParams derive(int dim, const pf_params *p)
     d.solid_eps = p->solid_eps;
     d.rep_xi = p->rep_xi;
     d.rep_eps = p->rep_eps;
+    for (int a = 0; a < 3; ++a) d.wall_circle[a] = p->wall_circle[a];
     d.dim = dim;
     for (int a = 0; a < 3; ++a) {
         d.Fb[a] = a < dim ? p->Fb[a] : 0.0;
@@ -600,7 +604,7 @@ static int issue_step(Engine &E, int par)
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.d_frep, E.mem[0].d.nx,
-                               E.mem[0].d.wall_y ? 0 : E.mem[0].d.ny, E.mem[0].d.nz, E.stream);
+                               E.mem[0].d.ny, E.mem[0].d.nz, E.mem[0].d.wall_y, E.stream);
     CK(cudaGetLastError());
     return PF_OK;
 }

@@ -61,6 +61,7 @@ struct DevParams {
     double s0, s1, s2, s3, s4, s1phi, cos_t, solid_eps;
     double Fb[3], g[3];
     double rep_xi, rep_eps;  // particle-particle repulsion (Sec. 4.5); eps <= 0: off
+    double wall_circle[3];   // circular wall of the particle-wall repulsion; radius <= 0: none
     // derived
     double cs2, cs4, inv_cs2;
     double w0f;        // rest weight of the flow lattice

@@ -45,6 +45,7 @@ void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, 
 int diag_blocks();
 void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cudaStream_t s);
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                            const DevParams &p, double *frep, int nx, int ny, int nz, cudaStream_t s);
+                            const DevParams &p, double *frep, int nx, int ny, int nz, int wall_y,
+                            cudaStream_t s);
 
 }  // namespace pf

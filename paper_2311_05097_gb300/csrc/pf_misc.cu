@@ -398,21 +398,62 @@ __global__ void k_diag_final(const double *partial, int nblocks, double *out)
 // ---- particles: repulsion (Sec. 4.5), per-tile partial sums, Newton-Euler (Eqs. 26, 28) --------
 // Force on particle k from the others (as printed: (x_k - x_j)/eps times
 // (R_k + R_j + xi - d)^2 within xi of contact, (R_k + R_j - d) overlapping),
-// minimum image; from the positions before this step's update.
+// minimum image, and from the nearest wall (the same form with 2 R_k and
+// eps/2, x_j the mirror image of particle k across that wall: a box wall at
+// y = -1/2 or ny - 1/2, or the circle p.wall_circle along its radius); from
+// the positions before this step's update.
 __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams p, int nx, int ny, int nz,
-                                     double *frep)
+                                     int wall_y, double *frep)
 {
     const int k = threadIdx.x;
     if (k >= np) return;
     const int n[3] = {nx, ny, nz};
     double acc[3] = {0.0, 0.0, 0.0};
     if (p.rep_eps > 0.0) {
+        double best = INFINITY, dw0 = 0.0, dw1 = 0.0;  // x_k - x'_k
+        if (wall_y && p.dim == 2) {
+            const double y = parts[k].x[1];
+            const double lo = 2.0 * (y + 0.5), hi = 2.0 * (ny - 0.5 - y);
+            if (lo < best) {
+                best = lo;
+                dw0 = 0.0;
+                dw1 = lo;
+            }
+            if (hi < best) {
+                best = hi;
+                dw0 = 0.0;
+                dw1 = -hi;
+            }
+        }
+        if (p.dim == 2 && p.wall_circle[2] > 0.0) {
+            const double ex = parts[k].x[0] - p.wall_circle[0], ey = parts[k].x[1] - p.wall_circle[1];
+            const double r = sqrt(ex * ex + ey * ey);
+            if (r > 0.0) {
+                const double dd = 2.0 * fabs(p.wall_circle[2] - r);
+                if (dd < best) {
+                    const double s = (r - (2.0 * p.wall_circle[2] - r)) / r;
+                    best = dd;
+                    dw0 = s * ex;
+                    dw1 = s * ey;
+                }
+            }
+        }
+        if (best < INFINITY) {
+            const double rr = 2.0 * parts[k].R;
+            double f = 0.0;
+            if (best <= rr + p.rep_xi) {
+                if (best >= rr) f = (rr + p.rep_xi - best) * (rr + p.rep_xi - best) / (0.5 * p.rep_eps);
+                else f = (rr - best) / (0.5 * p.rep_eps);
+            }
+            acc[0] += f * dw0;
+            acc[1] += f * dw1;
+        }
         for (int j = 0; j < np; ++j) {
             if (j == k) continue;
             double dx[3], d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double v = a < p.dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
-                if (a < p.dim && n[a] > 0) v -= n[a] * floor(v / n[a] + 0.5);  // n <= 0: walls
+                if (a < p.dim && !(a == 1 && wall_y)) v -= n[a] * floor(v / n[a] + 0.5);
                 dx[a] = v;
                 d2 += v * v;
             }
@@ -537,9 +578,9 @@ void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cuda
 }
 
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                            const DevParams &p, double *frep, int nx, int ny, int nz, cudaStream_t s)
+                            const DevParams &p, double *frep, int nx, int ny, int nz, int wall_y, cudaStream_t s)
 {
-    k_particle_repulsion<<<1, 64, 0, s>>>(parts, np, p, nx, ny, nz, frep);
+    k_particle_repulsion<<<1, 64, 0, s>>>(parts, np, p, nx, ny, nz, wall_y, frep);
     k_particle_update<<<np, 256, 0, s>>>(parts, np, partials, ntiles, p, frep);
     count_launches(2);
 }

@@ -38,7 +38,7 @@ class pf_params(C.Structure):
         ("d0", C.c_double), ("s0", C.c_double), ("s1", C.c_double), ("s2", C.c_double),
         ("s3", C.c_double), ("s4", C.c_double), ("theta_deg", C.c_double),
         ("Fb", C.c_double * 3), ("g", C.c_double * 3), ("solid_eps", C.c_double),
-        ("rep_xi", C.c_double), ("rep_eps", C.c_double),
+        ("rep_xi", C.c_double), ("rep_eps", C.c_double), ("wall_circle", C.c_double * 3),
         ("precision", C.c_int), ("store_log2_scale", C.c_int * 2), ("stream", C.c_void_p),
     ]
 
@@ -132,7 +132,7 @@ def make_params(precision=PF_P64, stream=None, **kw):
     p = pf_params()
     _check(load().pf_params_default(C.byref(p)))
     for k, v in kw.items():
-        if k in ("Fb", "g"):
+        if k in ("Fb", "g", "wall_circle"):
             v = tuple(v) + (0.0,) * (3 - len(v))
             setattr(p, k, (C.c_double * 3)(*v))
         elif k == "store_log2_scale":

@@ -84,7 +84,8 @@ PAPER_DEFAULTS = dict(d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, D=4.0, sol
 def params(**kw):
     d = dict(sigma=0.01, D=4.0, M=0.02, eta=0.0, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
              d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, theta_deg=90.0,
-             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0)
+             Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0,
+             wall_circle=(0.0, 0.0, 0.0))
     d.update(kw)
     return d
 
@@ -291,8 +292,9 @@ def annulus_mixing(n=512, count=15, seed=4, D=5.0, omega=1e-4, g=1e-6, rep_xi=2.
     n/8) rotating at ``omega`` rad/step (Sec. 4.5 layout in lattice units,
     dx = 0.01 of the paper: R_p in [20, 30], rho_p in [0.95, 1.05], theta_k in
     [45, 135] deg, neutral walls, sigma = 0.001, equal fluid densities and
-    viscosities, gravity on the particles, short-range repulsion).  The inner
-    cylinder is particle 0 with prescribed rotation."""
+    viscosities, gravity on the particles, short-range particle-particle and
+    particle-wall repulsion).  The inner cylinder is particle 0 with prescribed
+    rotation."""
     rng = np.random.default_rng(seed)
     shape = (n, n)
     c = (n - 1) / 2.0
@@ -319,8 +321,9 @@ def annulus_mixing(n=512, count=15, seed=4, D=5.0, omega=1e-4, g=1e-6, rep_xi=2.
     for q in parts:
         solid = solid + disc(shape, q["x"], q["R"], D)
     phi = (1.0 - solid) * np.tanh(-2.0 * (Y - c) / D)
+    # the outer wall also repels the particles (its phi0 = 1/2 circle)
     p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, theta_deg=90.0,
-               g=(0.0, -g, 0.0), rep_xi=rep_xi, rep_eps=rep_eps)
+               g=(0.0, -g, 0.0), rep_xi=rep_xi, rep_eps=rep_eps, wall_circle=(c, c, r_out))
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, name="annulus_mixing_2d")
 
 

@@ -209,3 +209,36 @@ def test_annulus_mixing_runs_and_mixes(pf):
     assert ps[0]["w"][2] == parts[0]["w"][2] and ps[0]["x"][:2] == list(parts[0]["x"][:2])
     assert gap > -2.0
     assert H1 > H0
+
+
+def test_porous_phase_separation_2d(pf):
+    """Phase separation from phi = (1 - phi0) U(-1, 1) inside random discs
+    between bounce-back walls (the setting of Sec. 4.1 on a synthetic 256 x 256
+    medium), FP64, theta = 45, 90, 135 deg, 20000 steps: the total free energy
+    E_F + E_K decays, sum phi is conserved (drift as in R14 below 1e-10), and
+    the phase that wets the solid (phase 1 below 90 deg) gathers on the solid
+    surface: the mean of phi over the surface layer 0.05 < phi0 < 0.5 is
+    ordered by the contact angle."""
+    layer_mean, drops = {}, {}
+    for th in (45.0, 90.0, 135.0):
+        c = W.porous_phase_separation_2d(n=256, theta_deg=th, seed=0)
+        s = pf.Sim(c["shape"], precision="p64", walls_y=True, **c["params"])
+        s.init(c["phi0"], c["phi"])
+        d0 = s.diagnostics()
+        E = [d0["E_total"]]
+        for _ in range(10):
+            s.step(2000)
+            E.append(s.diagnostics()["E_total"])
+        d1 = s.diagnostics()
+        assert d1["nan_flag"] == 0
+        drift = abs(d1["mass"] - d0["mass"]) / np.abs(c["phi"]).sum()
+        assert drift < 1e-10, (th, drift)
+        for a, b in zip(E, E[1:]):
+            assert b <= a * (1.0 + 1e-9), (th, E)
+        phi0 = c["phi0"]
+        layer = (phi0 > 0.05) & (phi0 < 0.5)
+        layer_mean[th] = float(s.macros()["phi"][layer].mean())
+        drops[th] = E[-1] / E[0]
+        record("porous_phase_separation_2d", theta=th, porosity=c["porosity"], discs=c["discs"],
+               E_ratio=drops[th], E=E, mass_drift=drift, surface_layer_mean_phi=layer_mean[th])
+    assert layer_mean[45.0] > layer_mean[90.0] > layer_mean[135.0], layer_mean

@@ -513,3 +513,35 @@ def test_batch_mixes_wall_and_periodic_domains(pf):
     o.init(cases[0]["phi0"], cases[0]["phi"], cases[0]["u"])
     o.step(steps)
     assert_fields(b.macros(0), o.macros(), 1e-12)
+
+
+def test_p64_particle_wall_repulsion_matches_oracle(pf):
+    """Particles next to the box walls and to a circular wall (Sec. 4.5
+    particle-wall repulsion against the mirror image across the nearest
+    wall), FP64 against the oracle after 60 steps; the walls push the
+    particles away compared with no repulsion."""
+    c = W.wall_case((64, 72), seed=8, solid=False, u_amp=0.0)
+    prm = dict(c["params"], rep_xi=3.0, rep_eps=1e4, wall_circle=(36.0, 32.0, 40.0))
+    c["params"] = prm
+    # nearest walls: bottom (d' = 11), top (d' = 12), circle (d' = 12); range 2R + xi = 13
+    parts = [dict(x=(20.0, 5.0), u=(0.0, -0.003), R=5.0, rho_p=2.0),
+             dict(x=(52.0, 57.5), u=(0.0, 0.003), R=5.0, rho_p=2.0),
+             dict(x=(36.0 + 34.0, 32.0), u=(0.003, 0.0), R=5.0, rho_p=2.0)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], prm["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 60, particles=parts, walls=True)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    for k in range(3):
+        pg, po = g.particle(k), o.particle(k)
+        R = po.R
+        us = np.abs(po.u).max() + abs(po.w[2]) * R + 1e-4
+        assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() <= 1e-12 * np.abs(po.x).max(), k
+        assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() <= 1e-12 * us, k
+        assert np.abs(np.array(pg["w"]) - np.array(po.w)).max() <= 1e-12 * us / R, k
+    c2 = dict(c, params=dict(prm, rep_eps=0.0))
+    g2, _ = run_pair(pf, c2, 60, particles=parts, oracle=False, walls=True)
+    assert g.particle(0)["u"][1] > g2.particle(0)["u"][1]   # bottom wall pushes up
+    assert g.particle(1)["u"][1] < g2.particle(1)["u"][1]   # top wall pushes down
+    assert g.particle(2)["u"][0] < g2.particle(2)["u"][0]   # the circle pushes inwards

@@ -375,3 +375,74 @@ def test_walls_conserve_mass():
     m0 = s.diagnostics()["mass"]
     s.step(400)
     assert abs(s.diagnostics()["mass"] - m0) <= 1e-13 * np.abs(c["phi"]).sum()
+
+
+def test_walls_give_a_right_contact_angle():
+    """The mirrored stencil rows at a box wall (reading R21) mean zero normal
+    gradient of phi there, i.e. a 90 degree contact angle: a half-ellipse of
+    phase 1 resting on the bottom wall relaxes to a half-circle centred on the
+    wall line y = -1/2 (a periodic image or a wrong mirror would pull the
+    contact line away from 90 degrees)."""
+    ny, nx = 24, 48
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    a, b = 14.0, 7.0
+    r = np.sqrt(((x - 24.0) / a) ** 2 + ((y + 0.5) / b) ** 2)
+    phi = np.tanh(2.0 * (1.0 - r) * math.sqrt(a * b) / 4.0)
+    prm = O.make_params(sigma=0.03, D=4.0, M=0.1, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1)
+    s = O.OracleSim((ny, nx), prm)
+    s.set_walls(True)
+    s.init(np.zeros((ny, nx)), phi)
+    s.step(4000)
+    ph = s.macros()["phi"]
+    pts = A.zero_contour_points(ph)
+    pts = pts[pts[:, 1] > 4.0]  # away from the wall layer
+    xc, yc, R = A.fit_circle(pts)
+    theta = math.degrees(math.acos(max(-1.0, min(1.0, (-0.5 - yc) / R))))
+    assert abs(theta - 90.0) < 0.5, (theta, xc, yc, R)
+    assert abs(R - math.sqrt(a * b)) < 0.5, R
+    # height above the wall line equals the half-width along the wall row
+    col, row = ph[:, 24], ph[0, 24:]
+    j = int(np.nonzero(col < 0)[0][0])
+    height = j - 1 + col[j - 1] / (col[j - 1] - col[j]) + 0.5
+    i = int(np.nonzero(row < 0)[0][0])
+    half = i - 1 + row[i - 1] / (row[i - 1] - row[i])
+    assert abs(height - half) < 0.2, (height, half)
+
+
+def test_particle_wall_repulsion():
+    """Particle-wall repulsion (Sec. 4.5, reading R22): the printed form with
+    2 R_k, eps/2 and the mirror image across the nearest wall; a box wall and
+    a circular wall through the same point with the same normal give the same
+    force; zero beyond 2 R_k + xi; only the nearest wall acts."""
+    n = (64, 48)
+    R, xi, eps = 5.0, 3.0, 0.5
+    p = O.make_params(rep_xi=xi, rep_eps=eps)
+    # d' = 2 (y + 1/2): overlapping (d' < 2R), within xi, at the edge, beyond
+    for y, expect in ((4.0, None), (5.2, None), (5.9, None), (6.0 + 1e-9, 0.0), (20.0, 0.0)):
+        a = O.Particle((30.0, y), R=R)
+        F = O.repulsion(2, p, n, [a], walls_y=True)[0]
+        d = 2.0 * (y + 0.5)
+        if expect is None:
+            g = (2 * R + xi - d) ** 2 if d >= 2 * R else (2 * R - d)
+            assert F[0] == 0.0 and abs(F[1] - d * g / (eps / 2)) <= 1e-13 * abs(F[1]) and F[1] > 0
+        else:
+            assert np.abs(F).max() == 0.0
+        # the same wall as a huge circle centred above, tangent to y = -1/2 at x = 30
+        Rw = 1e6
+        pc = O.make_params(rep_xi=xi, rep_eps=eps, wall_circle=(30.0, Rw - 0.5, Rw))
+        Fc = O.repulsion(2, pc, n, [a])[0]
+        assert np.allclose(Fc, F, rtol=1e-8, atol=1e-12), (y, F, Fc)
+    # top wall pushes down; only the nearest wall counts; off without walls
+    a = O.Particle((30.0, n[1] - 6.0), R=R)
+    assert O.repulsion(2, p, n, [a], walls_y=True)[0][1] < 0
+    assert np.abs(O.repulsion(2, p, n, [a])[0]).max() == 0.0
+    small = O.Particle((30.0, 4.0), R=2.0)  # both walls within range only when ny is tiny
+    F1 = O.repulsion(2, p, (64, 12), [small], walls_y=True)[0]
+    F2 = O.repulsion(2, p, (64, 1000), [small], walls_y=True)[0]
+    assert np.array_equal(F1, F2)
+    # circle: points to the centre, radial
+    pc = O.make_params(rep_xi=xi, rep_eps=eps, wall_circle=(32.0, 24.0, 20.0))
+    b = O.Particle((32.0 + 14.0 * 0.6, 24.0 + 14.0 * 0.8), R=R)
+    Fb = O.repulsion(2, pc, n, [b])[0]
+    r = np.array([0.6, 0.8])
+    assert Fb[:2] @ r < 0 and abs(Fb[0] * r[1] - Fb[1] * r[0]) < 1e-12 * np.abs(Fb).max()
