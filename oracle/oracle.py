@@ -21,6 +21,7 @@ class OrcParams(C.Structure):
         ("s3", C.c_double), ("s4", C.c_double), ("theta_deg", C.c_double),
         ("Fb", C.c_double * 3), ("g", C.c_double * 3), ("solid_eps", C.c_double),
         ("rep_xi", C.c_double), ("rep_eps", C.c_double), ("wall_circle", C.c_double * 3),
+        ("phase_model", C.c_int),
     ]
 
 
@@ -106,13 +107,15 @@ def make_params(**kw):
     d = dict(sigma=0.01, D=4.0, M=0.02, eta=0.0, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
              d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, theta_deg=90.0,
              Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0,
-             wall_circle=(0.0, 0.0, 0.0))
+             wall_circle=(0.0, 0.0, 0.0), phase_model=0)
     d.update(kw)
     p = OrcParams()
     for k, v in d.items():
         if k in ("Fb", "g", "wall_circle"):
             v = tuple(v) + (0.0,) * (3 - len(v))
             setattr(p, k, (C.c_double * 3)(*v))
+        elif k == "phase_model":
+            p.phase_model = int(v)
         else:
             setattr(p, k, float(v))
     return p

@@ -64,6 +64,15 @@
  *       or a circular wall given by centre and radius, mirrored along the
  *       radius), d' its distance; the printed form with 2 R_k for R_k + R_j and
  *       eps/2 for eps; the nearest wall only; added like R19.
+ *   R23 conservative Allen-Cahn order parameter (the paper prints none; an
+ *       option next to Eq. 2): d_t phi + div(phi u) = div(M (grad phi - theta n))
+ *       with theta = (2/D)(1 - phi^2), n = grad phi / |grad phi| (0 where
+ *       |grad phi|^2 <= 1e-24), whose flat profile tanh(2 zeta/D) has zero flux.
+ *       On the lattice of Eq. (30): eta mu -> phi in the equilibrium (second
+ *       Hermite moment zero), s_1phi = 1/(M/cs^2 + 1/2), and cs^2 theta n added
+ *       to the source G; the mass flux of the momentum equation becomes
+ *       S = M (rho1 - rho2)/2 (grad phi - theta n); mu_phi of Eq. (9) still
+ *       gives the surface force, and solids and particles enter it as before.
  */
 #include "pf_oracle.h"
 
@@ -102,6 +111,7 @@ struct orc_sim {
     double *s2a, *s2b, *P, *tmp, *tmp3;
     /* R18: angle-weighted indicators and their stencils */
     double *wfld, *vfld, *lap_w, *gw, *gv;
+    double *tn;  /* R23: theta n of the Allen-Cahn flux */
     int wall_y;  /* R21: walls at the ends of y instead of periodicity */
 };
 
@@ -729,8 +739,8 @@ orc_sim *orc_create(int dim, int nx, int ny, int nz, const orc_params *p)
     s->p = *p;
     s->cs2 = p->d0;
     s->eta = p->eta > 0.0 ? p->eta : 2.0 * p->M / s->cs2;
-    /* M = (1/s_1phi - 1/2) eta cs^2 dt  (Sec. 3.1) */
-    s->s1phi = 1.0 / (p->M / (s->eta * s->cs2) + 0.5);
+    /* M = (1/s_1phi - 1/2) eta cs^2 dt  (Sec. 3.1); R23: eta = 1 */
+    s->s1phi = p->phase_model == 1 ? 1.0 / (p->M / s->cs2 + 0.5) : 1.0 / (p->M / (s->eta * s->cs2) + 0.5);
     s->cos_t = cos(p->theta_deg * M_PI / 180.0);
     lattice_setup(&s->L1, dim == 2 ? ORC_D2Q9 : ORC_D3Q7, p->d0);
     lattice_setup(&s->L2, dim == 2 ? ORC_D2Q9 : ORC_D3Q19, p->d0);
@@ -767,6 +777,7 @@ orc_sim *orc_create(int dim, int nx, int ny, int nz, const orc_params *p)
     s->P = zalloc(N);
     s->tmp = zalloc(N);
     s->tmp3 = zalloc(3 * N);
+    s->tn = zalloc(3 * N);
     s->wfld = zalloc(N);
     s->vfld = zalloc(N);
     s->lap_w = zalloc(N);
@@ -782,7 +793,7 @@ void orc_destroy(orc_sim *s)
                       s->phi_prev, s->S_prev, s->phi, s->rho, s->muv, s->lap_phi, s->lap_phi0,
                       s->mu,  s->mu0,  s->gphi, s->gphi0, s->gmu, s->S, s->grho, s->Fc, s->F,
                       s->ustar, s->fpen, s->u, s->Ftot, s->s2a, s->s2b, s->P, s->tmp, s->tmp3,
-                      s->wfld, s->vfld, s->lap_w, s->gw, s->gv};
+                      s->wfld, s->vfld, s->lap_w, s->gw, s->gv, s->tn};
     for (size_t i = 0; i < sizeof(bufs) / sizeof(bufs[0]); ++i) free(bufs[i]);
     free(s);
 }
@@ -831,6 +842,20 @@ static void update_phi0(orc_sim *s)
 }
 
 /* Sec. 3.3 steps 3-6 (and the pieces of Eqs. 33-36 the collision needs). */
+/* R23: theta n = (2/D)(1 - phi^2) grad phi / |grad phi| per cell */
+static void cac_theta_n(orc_sim *s)
+{
+    const long N = s->N;
+    for (long id = 0; id < N; ++id) {
+        double g2 = 0.0;
+        for (int a = 0; a < s->dim; ++a) g2 += s->gphi[a * N + id] * s->gphi[a * N + id];
+        const double ph = s->phi[id];
+        const double th = 2.0 / s->p.D * (1.0 - ph * ph);
+        const double inv = g2 > 1e-24 ? 1.0 / sqrt(g2) : 0.0;
+        for (int a = 0; a < 3; ++a) s->tn[a * N + id] = a < s->dim ? th * s->gphi[a * N + id] * inv : 0.0;
+    }
+}
+
 static void compute_macros(orc_sim *s)
 {
     const orc_params *p = &s->p;
@@ -877,10 +902,12 @@ static void compute_macros(orc_sim *s)
         }
     }
 
-    /* S = M grad(mu) (rho1 - rho2)/2 (Sec. 2.2); grad rho from Eq. (17) */
+    /* S = M grad(mu) (rho1 - rho2)/2 (Sec. 2.2), or with R23
+     * M (grad phi - theta n)(rho1 - rho2)/2; grad rho from Eq. (17) */
     sim_grad(s, s->mu, 1, s->gmu);
+    if (p->phase_model == 1) cac_theta_n(s);
     for (long k = 0; k < 3 * N; ++k) {
-        s->S[k] = p->M * s->gmu[k] * drho;
+        s->S[k] = p->phase_model == 1 ? p->M * (s->gphi[k] - s->tn[k]) * drho : p->M * s->gmu[k] * drho;
         s->grho[k] = drho * s->gphi[k];
     }
 
@@ -1055,7 +1082,12 @@ void orc_init(orc_sim *s, const double *phi0, const double *phi, const double *u
         }
     }
     sim_grad(s, s->mu, 1, s->gmu);
-    for (long k = 0; k < 3 * N; ++k) s->S[k] = p->M * s->gmu[k] * drho;
+    if (p->phase_model == 1) {
+        sim_grad(s, s->phi, 1, s->gphi);
+        cac_theta_n(s);
+    }
+    for (long k = 0; k < 3 * N; ++k)
+        s->S[k] = p->phase_model == 1 ? p->M * (s->gphi[k] - s->tn[k]) * drho : p->M * s->gmu[k] * drho;
     /* step 1 of Sec. 3.3: f = f^eq */
     for (long id = 0; id < N; ++id) {
         double uu[3], SS[3], fe[ORC_QMAX];
@@ -1063,7 +1095,10 @@ void orc_init(orc_sim *s, const double *phi0, const double *phi, const double *u
             uu[a] = s->u[a * N + id];
             SS[a] = s->S[a * N + id];
         }
-        feq1_lat(&s->L1, s->cs2, s->phi[id], uu, s->mu[id], s->eta, fe);
+        if (p->phase_model == 1)
+            feq1_lat(&s->L1, s->cs2, s->phi[id], uu, s->phi[id], 1.0, fe);
+        else
+            feq1_lat(&s->L1, s->cs2, s->phi[id], uu, s->mu[id], s->eta, fe);
         for (int i = 0; i < s->L1.Q; ++i) s->f1[i * N + id] = fe[i];
         feq2_lat(&s->L2, s->cs2, s->rho[id], uu, SS, s->P[id], fe);
         for (int i = 0; i < s->L2.Q; ++i) s->f2[i * N + id] = fe[i];
@@ -1108,8 +1143,11 @@ static void one_step(orc_sim *s)
             LF[ORC_QMAX], S1[ORC_QMAX], G[3];
         int Q1 = s->L1.Q;
         for (int i = 0; i < Q1; ++i) f[i] = s->f1[i * N + id];
-        feq1_lat(&s->L1, cs2, phi, uu, s->mu[id], s->eta, fe);
-        for (int a = 0; a < 3; ++a) G[a] = phi * uu[a] - s->phi_prev[id] * up[a];
+        const int cac = p->phase_model == 1;
+        /* R23: eta mu -> phi, and the sharpening flux cs^2 theta n in G */
+        feq1_lat(&s->L1, cs2, phi, uu, cac ? phi : s->mu[id], cac ? 1.0 : s->eta, fe);
+        for (int a = 0; a < 3; ++a)
+            G[a] = phi * uu[a] - s->phi_prev[id] * up[a] + (cac ? cs2 * s->tn[a * N + id] : 0.0);
         src1_lat(&s->L1, cs2, G, Fs);
         orc_rates(s->L1.kind, 1, p->s0, s->s1phi, p->s2, p->s2, p->s3, p->s4, S1);
         for (int i = 0; i < Q1; ++i) v[i] = f[i] - fe[i];

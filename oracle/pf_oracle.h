@@ -39,6 +39,8 @@ typedef struct orc_params {
     double wall_circle[3]; /* circular wall (centre x, y; radius) seen by the
                               particle-wall repulsion (reading R22); radius <= 0:
                               none */
+    int phase_model;   /* 0: Cahn-Hilliard order parameter (Eq. 2, Sec. 3.1);
+                          1: conservative Allen-Cahn (reading R23) */
 } orc_params;
 
 typedef struct orc_particle {

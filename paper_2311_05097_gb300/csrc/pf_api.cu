@@ -545,10 +545,18 @@ static int engine_tiles(Engine &E, int tx, int ty)
     return PF_OK;
 }
 
+// domains only the single-cell kernel handles: walls at the ends of y
+static bool any_walls(const Engine &E)
+{
+    for (auto &m : E.mem)
+        if (m.d.wall_y) return true;
+    return false;
+}
+
 static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
 {
     if (E.dim == 3) return launch_step3d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
-    return launch_step2d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
+    return launch_step2d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0), grid, E.stream, a);
 }
 
 static int step_mode(const Engine &E)
@@ -558,13 +566,6 @@ static int step_mode(const Engine &E)
 
 // the staged 2D step copies 16-byte chunks: every domain's nx must keep its
 // rows' chunks and periodic splits aligned
-static bool any_walls(const Engine &E)
-{
-    for (auto &m : E.mem)
-        if (m.d.wall_y) return true;
-    return false;
-}
-
 static bool stage_ok(const Engine &E)
 {
     if (E.dim != 2 || E.prec == PF_P64 || E.np > 0 || any_walls(E)) return false;
@@ -577,7 +578,7 @@ static bool stage_ok(const Engine &E)
 static int occupancy_any(const Engine &E, int tx, int ty, int mode)
 {
     if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode);
-    return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode);
+    return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0));
 }
 
 static StepArgs step_args(const Engine &E, int par)

@@ -24,6 +24,9 @@ constexpr int REST_FRAC_BITS = 50;  // rest population = value * 2^-50
 // policies, fixed solids); MODE_STEP_STAGE: the same with the tile's inputs
 // staged in shared memory by bulk copies
 enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2, MODE_STEP_STAGE = 3 };
+// or'ed into a 2D mode: the launch holds a domain with walls (the single-cell
+// kernel's wall-handling instantiation)
+constexpr int MODE_EXT = 16;
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {

@@ -103,13 +103,13 @@ __device__ __forceinline__ R lap9(const R (*a)[W], int x, int y)
 
 // Smooth indicator of particle k at cell (gx, gy) (minimum image), 0 beyond
 // R + cut where 1/2 (1 + tanh) rounds to 0 in both precisions.
-template <class R>
+template <class R, bool EXT>
 __device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy, int nx, int ny,
                                            double D, double cut, R &rx, R &ry)
 {
     double dx = (double)gx - pp.x[0], dy = (double)gy - pp.x[1];
     dx -= nx * rint(dx / nx);
-    if (ny > 0) dy -= ny * rint(dy / ny);  // ny <= 0: walls in y, no minimum image
+    if (!EXT || ny > 0) dy -= ny * rint(dy / ny);  // ny <= 0: walls in y, no minimum image
     rx = (R)dx;
     ry = (R)dy;
     double r2 = dx * dx + dy * dy;
@@ -128,7 +128,9 @@ constexpr int step2d_min_blocks()
     return P::id == 0 ? 1 : (TX * TY > 256 ? 1 : ((TX == 32 && TY == 8) ? 4 : 3));
 }
 
-template <class P, int TX, int TY, bool MOVING, int MODE>
+// EXT: the instantiation also handles domains with walls at the ends of y;
+// without it the wall code is compiled out (it costs registers)
+template <class P, int TX, int TY, bool MOVING, int MODE, bool EXT>
 __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_step2d(StepArgs A)
 {
     using R = typename P::real;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     __shared__ int s_gx[TX + 6];
     __shared__ int s_gy[TY + 6];  // row offsets y * pitch (planes hold < 2^31 cells)
     __shared__ int s_gyi[TY + 6];
-    __shared__ int s_out[TY + 6];  // walls: the row lies beyond a wall (mirror image)
+    __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
     __shared__ double s_red[NT / 32][6];
     __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
 
@@ -169,27 +171,38 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         if constexpr (MOVING) {
             if (tid == 0) s_near = 0ull;
         }
-        const int wall = Dm.wall_y;
+        const int wall = EXT ? Dm.wall_y : 0;
         const int nyw = wall ? 0 : ny;  // minimum image in y only without walls
         for (int k = tid; k < TX + 6; k += NT) s_gx[k] = wrap_idx(x0 - 3 + k, nx);
         for (int k = tid; k < TY + 6; k += NT) {
-            const int y = y0 - 3 + k;
-            int yy, out = 0;
-            if (wall) {
-                // rows beyond a wall read their mirror image (clamped: the rows
-                // that far out only feed cells beyond the domain)
-                yy = y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
-                out = y < 0 || y >= ny;
-                yy = min(max(yy, 0), ny - 1);
+            if constexpr (EXT) {
+                const int y = y0 - 3 + k;
+                int yy, out = 0;
+                if (wall) {
+                    // rows beyond a wall read their mirror image (clamped: the
+                    // rows that far out only feed cells beyond the domain)
+                    yy = y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
+                    out = y < 0 || y >= ny;
+                    yy = min(max(yy, 0), ny - 1);
+                } else {
+                    yy = wrap_idx(y, ny);
+                }
+                s_gyi[k] = yy;
+                s_gy[k] = yy * Dm.pitch;
+                s_out[k] = out;
             } else {
-                yy = wrap_idx(y, ny);
+                const int yy = wrap_idx(y0 - 3 + k, ny);
+                s_gyi[k] = yy;
+                s_gy[k] = yy * Dm.pitch;
             }
-            s_gyi[k] = yy;
-            s_gy[k] = yy * Dm.pitch;
-            s_out[k] = out;
         }
         // a tile whose frames reach beyond a wall
-        const bool wall_tile = wall && (y0 - 3 < 0 || y0 + TY + 3 > ny);
+        const bool wall_tile = EXT && wall && (y0 - 3 < 0 || y0 + TY + 3 > ny);
+        // sign of w = S_x u_y - u_x S_y at table row r: odd under a wall mirror
+        auto wsign = [&](int r) -> R {
+            if constexpr (EXT) return s_out[r] ? R(-1) : R(1);
+            return R(1);
+        };
         if constexpr (MOVING) {
             // conservative test of the tile + 2 frame against each particle's
             // reach R + cut (minimum image), one thread per particle
@@ -198,7 +211,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const ParticleDev &pp = A.parts[k];
                 double dx = (x0 + 0.5 * (TX - 1)) - pp.x[0], dy = (y0 + 0.5 * (TY - 1)) - pp.x[1];
                 dx -= nx * rint(dx / nx);
-                if (!wall) dy -= ny * rint(dy / ny);
+                if (!EXT || !wall) dy -= ny * rint(dy / ny);
                 const double ex = fmax(fabs(dx) - (0.5 * TX + 2.0), 0.0);
                 const double ey = fmax(fabs(dy) - (0.5 * TY + 2.0), 0.0);
                 const double lim = pp.R + p.cut + 1.0;
@@ -222,9 +235,11 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         // that lies beyond a wall, its own opposite population (halfway
         // bounce-back)
         auto pull = [&](int base, int i, int cx, int cy) -> int {
-            if (wall_tile && s_out[cy - CY9[i]] && !s_out[cy])
-                return (base + OPP9[i]) * plane + s_gy[cy] + s_gx[cx];
-            return (base + i) * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]];
+            if constexpr (EXT) {
+                if (wall_tile && s_out[cy - CY9[i]] && !s_out[cy])
+                    return (base + OPP9[i]) * plane + s_gy[cy] + s_gx[cx];
+            }
+            return base * plane + i * plane + s_gy[cy - CY9[i]] + s_gx[cx - CX9[i]];
         };
 
         // phi at frame cell (hx, hy) of the tile+2 frame: pull and sum (Eq. 31)
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 for (int k = 0; k < A.np; ++k) {
                     if (!((near >> k) & 1ull)) continue;
                     R rx, ry;
-                    const R pk = particle_phi0<R>(A.parts[k], gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+                    const R pk = particle_phi0<R, EXT>(A.parts[k], gx, gy, nx, nyw, p.D, p.cut, rx, ry);
                     v += pk;
                     if (A.parts[k].own) {
                         const R ck = (R)A.parts[k].ct;
@@ -336,7 +351,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             // w of the own cell from the lagged fields already in registers; the
             // tile+1 ring by the last threads (the first ones did the phi ring)
             // (odd under a wall mirror: rows beyond a wall take the sign change)
-            s_w[ly + 1][lx + 1] = (s_out[ly + 3] ? R(-1) : R(1)) * ((R)lag[2] * (R)lag[1] - (R)lag[0] * (R)lag[3]);
+            s_w[ly + 1][lx + 1] = wsign(ly + 3) * ((R)lag[2] * (R)lag[1] - (R)lag[0] * (R)lag[3]);
             constexpr int WRING = 2 * WX + 2 * TY;
             static_assert(WRING <= NT, "one tile+1 ring cell per thread at most");
             for (int r = NT - 1 - tid; r >= 0 && r < WRING; r -= NT) {
@@ -352,18 +367,20 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const int wid = s_gy[wy + 2] + s_gx[wx + 2];
                 const R ux = (R)ldg(as + 0 * plane + wid), uy = (R)ldg(as + 1 * plane + wid);
                 const R Sx = (R)ldg(as + 2 * plane + wid), Sy = (R)ldg(as + 3 * plane + wid);
-                s_w[wy][wx] = (s_out[wy + 2] ? R(-1) : R(1)) * (Sx * uy - ux * Sy);
+                s_w[wy][wx] = wsign(wy + 2) * (Sx * uy - ux * Sy);
             }
         }
-        if (wall_tile) {
-            // phi beyond a wall is the mirror image of phi inside (no flux)
-            __syncthreads();
-            for (int r = tid; r < FX * FY; r += NT) {
-                const int hx = r % FX, hy = r / FX;
-                if (!s_out[hy + 1]) continue;
-                const int y = y0 - 2 + hy;
-                const int hym = (y < 0 ? -1 - y : 2 * ny - 1 - y) - (y0 - 2);
-                if (hym >= 0 && hym < FY && !s_out[hym + 1]) s_phi[hy][hx] = s_phi[hym][hx];
+        if constexpr (EXT) {
+            if (wall_tile) {
+                // phi beyond a wall is the mirror image of phi inside (no flux)
+                __syncthreads();
+                for (int r = tid; r < FX * FY; r += NT) {
+                    const int hx = r % FX, hy = r / FX;
+                    if (!s_out[hy + 1]) continue;
+                    const int y = y0 - 2 + hy;
+                    const int hym = (y < 0 ? -1 - y : 2 * ny - 1 - y) - (y0 - 2);
+                    if (hym >= 0 && hym < FY && !s_out[hym + 1]) s_phi[hy][hx] = s_phi[hym][hx];
+                }
             }
         }
         __syncthreads();
@@ -452,7 +469,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     const int nid = s_gy[ly + 3 + j] + s_gx[lx + 3 + i];
                     const R ux = (R)ldg(as + 0 * plane + nid), uy = (R)ldg(as + 1 * plane + nid);
                     const R sx = (R)ldg(as + 2 * plane + nid), sy = (R)ldg(as + 3 * plane + nid);
-                    wv[j + 1][i + 1] = (s_out[ly + 3 + j] ? R(-1) : R(1)) * (sx * uy - ux * sy);
+                    wv[j + 1][i + 1] = wsign(ly + 3 + j) * (sx * uy - ux * sy);
                 }
             R wgx, wgy;
             grad9<R, 3>(wv, 1, 1, wgx, wgy);
@@ -477,7 +494,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 if (!((near >> k) & 1ull)) continue;
                 const ParticleDev &pp = A.parts[k];
                 R rx, ry;
-                const R pk = particle_phi0<R>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+                const R pk = particle_phi0<R, EXT>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
                 if (pk != R(0)) {
                     const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                     const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
@@ -641,7 +658,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     double c6[6] = {0, 0, 0, 0, 0, 0};
                     if (valid) {
                         R rx, ry;
-                        const R pk = particle_phi0<R>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+                        const R pk = particle_phi0<R, EXT>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
                         if (pk != R(0)) {
                             const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                             const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;

@@ -9,10 +9,10 @@
 
 namespace pf {
 
-template <class P, int TX, int TY, bool MOVING, int MODE>
+template <class P, int TX, int TY, bool MOVING, int MODE, bool EXT>
 static bool run2d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
-    auto kern = k_step2d<P, TX, TY, MOVING, MODE>;
+    auto kern = k_step2d<P, TX, TY, MOVING, MODE, EXT>;
     if (occ) {
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0) != cudaSuccess) n = 0;
@@ -89,37 +89,38 @@ static bool dispatch2d_stage(int tx, int ty, bool moving, int grid, cudaStream_t
     }
 }
 
+template <class P, bool EXT>
+static bool dispatch2d_single(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
+                              const StepArgs &a, int *occ)
+{
+    if (mode == MODE_MACROS) {
+        if (tx == 32 && ty == 8)
+            return moving ? run2d<P, 32, 8, true, MODE_MACROS, EXT>(grid, s, a, occ)
+                          : run2d<P, 32, 8, false, MODE_MACROS, EXT>(grid, s, a, occ);
+        return false;
+    }
+    if (tx == 32 && ty == 8)
+        return moving ? run2d<P, 32, 8, true, MODE_STEP, EXT>(grid, s, a, occ)
+                      : run2d<P, 32, 8, false, MODE_STEP, EXT>(grid, s, a, occ);
+    if (tx == 64 && ty == 4)
+        return moving ? run2d<P, 64, 4, true, MODE_STEP, EXT>(grid, s, a, occ)
+                      : run2d<P, 64, 4, false, MODE_STEP, EXT>(grid, s, a, occ);
+    if (tx == 32 && ty == 16)
+        return moving ? run2d<P, 32, 16, true, MODE_STEP, EXT>(grid, s, a, occ)
+                      : run2d<P, 32, 16, false, MODE_STEP, EXT>(grid, s, a, occ);
+    return false;
+}
+
 template <class P>
 static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
                        const StepArgs &a, int *occ)
 {
-#define PF_CASE(TX, TY)                                                                   \
-    if (tx == TX && ty == TY) {                                                           \
-        if (mode == MODE_MACROS)                                                          \
-            return moving ? run2d<P, TX, TY, true, MODE_MACROS>(grid, s, a, occ)          \
-                          : run2d<P, TX, TY, false, MODE_MACROS>(grid, s, a, occ);        \
-        return moving ? run2d<P, TX, TY, true, MODE_STEP>(grid, s, a, occ)                \
-                      : run2d<P, TX, TY, false, MODE_STEP>(grid, s, a, occ);              \
-    }
-    if (mode == MODE_STEP_PAIR) return dispatch2d_pair<P>(tx, ty, moving, grid, s, a, occ);
-    if (mode == MODE_STEP_STAGE) return dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
-    if (mode == MODE_MACROS) {
-        if (tx == 32 && ty == 8)
-            return moving ? run2d<P, 32, 8, true, MODE_MACROS>(grid, s, a, occ)
-                          : run2d<P, 32, 8, false, MODE_MACROS>(grid, s, a, occ);
-        return false;
-    }
-    if (tx == 32 && ty == 8)
-        return moving ? run2d<P, 32, 8, true, MODE_STEP>(grid, s, a, occ)
-                      : run2d<P, 32, 8, false, MODE_STEP>(grid, s, a, occ);
-    if (tx == 64 && ty == 4)
-        return moving ? run2d<P, 64, 4, true, MODE_STEP>(grid, s, a, occ)
-                      : run2d<P, 64, 4, false, MODE_STEP>(grid, s, a, occ);
-    if (tx == 32 && ty == 16)
-        return moving ? run2d<P, 32, 16, true, MODE_STEP>(grid, s, a, occ)
-                      : run2d<P, 32, 16, false, MODE_STEP>(grid, s, a, occ);
-#undef PF_CASE
-    return false;
+    const bool ext = (mode & MODE_EXT) != 0;
+    mode &= ~MODE_EXT;
+    if (mode == MODE_STEP_PAIR) return !ext && dispatch2d_pair<P>(tx, ty, moving, grid, s, a, occ);
+    if (mode == MODE_STEP_STAGE) return !ext && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
+    return ext ? dispatch2d_single<P, true>(tx, ty, moving, mode, grid, s, a, occ)
+               : dispatch2d_single<P, false>(tx, ty, moving, mode, grid, s, a, occ);
 }
 
 }  // namespace pf

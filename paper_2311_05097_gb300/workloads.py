@@ -85,7 +85,7 @@ def params(**kw):
     d = dict(sigma=0.01, D=4.0, M=0.02, eta=0.0, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
              d0=0.4, s0=1.0, s1=1.0, s2=1.0, s3=1.0, s4=1.0, theta_deg=90.0,
              Fb=(0.0, 0.0, 0.0), g=(0.0, 0.0, 0.0), solid_eps=1e-3, rep_xi=0.0, rep_eps=0.0,
-             wall_circle=(0.0, 0.0, 0.0))
+             wall_circle=(0.0, 0.0, 0.0), phase_model=0)
     d.update(kw)
     return d
 
