@@ -110,6 +110,17 @@ typedef struct pf_params {
     double wall_circle[3]; /* 2D: a circular wall (centre x, y; radius) seen only
                               by the particle-wall repulsion (the fluid sees
                               walls through phi0); radius 0: none */
+    int phase_model;   /* 0 (default): the Cahn-Hilliard order parameter of
+                          Eq. 2 on the lattice of Eq. 30.  1 (2D, single-cell
+                          kernel only): a conservative Allen-Cahn order
+                          parameter, d_t phi + div(phi u) =
+                          div(M (grad phi - theta n)), theta = (2/D)(1 - phi^2),
+                          n = grad phi/|grad phi|, on the same lattice
+                          (equilibrium with eta mu replaced by phi, s_1phi =
+                          1/(M/cs^2 + 1/2), cs^2 theta n in the source) and the
+                          mass flux S = M (rho1 - rho2)/2 (grad phi - theta n);
+                          eta is unused; mu_phi of Eq. 9 still drives the
+                          surface force.  The paper prints no such scheme */
     int precision;     /* PF_P64, PF_P32, PF_PMIX_FP16, PF_PMIX_BF16 */
     int store_log2_scale[2]; /* PMIX: stored value = population * 2^k for the
                                 order-parameter [0] and flow [1] lattices;

@@ -182,7 +182,9 @@ static int validate(const pf_grid *g, const pf_params *p)
     if (p->precision < PF_P64 || p->precision > PF_PMIX_BF16)
         return fail(PF_EINVAL, "unknown precision %d", p->precision);
     const double cs2 = p->d0;
-    const double eta = p->eta > 0 ? p->eta : 2.0 * p->M / cs2;
+    if (p->phase_model != 0 && p->phase_model != 1) return fail(PF_EINVAL, "phase_model must be 0 or 1");
+    if (p->phase_model == 1 && g->dim != 2) return fail(PF_EINVAL, "phase_model 1 (Allen-Cahn) is 2D only");
+    const double eta = p->phase_model == 1 ? 1.0 : (p->eta > 0 ? p->eta : 2.0 * p->M / cs2);
     const double s1phi = 1.0 / (p->M / (eta * cs2) + 0.5);
     if (!(s1phi > 0 && s1phi < 2)) return fail(PF_EINVAL, "eta gives s_1phi outside (0, 2)");
     for (int k = 0; k < 2; ++k)
@@ -228,7 +230,9 @@ static DevParams derive(int dim, const pf_params *p)
     d.cs2 = p->d0;
     d.cs4 = d.cs2 * d.cs2;
     d.inv_cs2 = 1.0 / d.cs2;
-    d.eta = p->eta > 0 ? p->eta : 2.0 * p->M / d.cs2;
+    d.phase_model = p->phase_model;
+    // Allen-Cahn: eta mu -> phi in the equilibrium, so eta = 1 sets s_1phi
+    d.eta = p->phase_model == 1 ? 1.0 : (p->eta > 0 ? p->eta : 2.0 * p->M / d.cs2);
     d.s1phi = 1.0 / (p->M / (d.eta * d.cs2) + 0.5);  // M = (1/s_1phi - 1/2) eta cs^2
     d.cos_t = std::cos(p->theta_deg * 3.14159265358979323846 / 180.0);
     const double d0 = p->d0;
@@ -263,7 +267,9 @@ static DevParams derive(int dim, const pf_params *p)
     // order parameter: the exact rest-population bookkeeping needs every stored
     // mover below 8 (stored = value * 2^k1); bound the movers by
     // w_1 (|u|/cs^2 + eta * 2 mu_max) with |u| <= 1 and mu_max = 3 sigma/D
-    const double m1max = w1 * (1.0 / d.cs2 + d.eta * 2.0 * musc);
+    // (Allen-Cahn: w_1 |phi| (1 + |u|/cs^2) with |phi| <= 3/2)
+    const double m1max = p->phase_model == 1 ? 1.5 * w1 * (1.0 + 1.0 / d.cs2)
+                                             : w1 * (1.0 / d.cs2 + d.eta * 2.0 * musc);
     int k1 = p->store_log2_scale[0] ? p->store_log2_scale[0]
                                     : (int)std::floor(std::log2(8.0 / m1max));
     k1 = std::max(0, std::min(24, k1));
@@ -545,11 +551,12 @@ static int engine_tiles(Engine &E, int tx, int ty)
     return PF_OK;
 }
 
-// domains only the single-cell kernel handles: walls at the ends of y
+// domains only the single-cell kernel handles: walls at the ends of y, or the
+// Allen-Cahn order parameter
 static bool any_walls(const Engine &E)
 {
     for (auto &m : E.mem)
-        if (m.d.wall_y) return true;
+        if (m.d.wall_y || m.d.p.phase_model == 1) return true;
     return false;
 }
 
@@ -1194,7 +1201,7 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
     if (var < 0 || var > 2) return fail(PF_EINVAL, "kernel must be 0, 1 or 2");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
     if (var != 0 && any_walls(E))
-        return fail(PF_EINVAL, "domains with walls run kernel 0 only");
+        return fail(PF_EINVAL, "domains with walls or the Allen-Cahn order parameter run kernel 0 only");
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);

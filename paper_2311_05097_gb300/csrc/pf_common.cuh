@@ -24,8 +24,8 @@ constexpr int REST_FRAC_BITS = 50;  // rest population = value * 2^-50
 // policies, fixed solids); MODE_STEP_STAGE: the same with the tile's inputs
 // staged in shared memory by bulk copies
 enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2, MODE_STEP_STAGE = 3 };
-// or'ed into a 2D mode: the launch holds a domain with walls (the single-cell
-// kernel's wall-handling instantiation)
+// or'ed into a 2D mode: the launch holds a domain with walls or the Allen-Cahn
+// order parameter (the single-cell kernel's instantiation that handles them)
 constexpr int MODE_EXT = 16;
 
 // ---- precision policies ------------------------------------------------------------------
@@ -84,6 +84,7 @@ struct DevParams {
     double cut;        // particle indicator is exactly 0 beyond R + cut
     int klog2[2];      // PMIX scale exponents k of 2^k
     int dim;
+    int phase_model;   // 0: Cahn-Hilliard (Eq. 2); 1: conservative Allen-Cahn
 };
 
 struct ParticleDev {
@@ -105,6 +106,7 @@ struct KParams {
     R c_dw, c_lap, c_pen, c_wet, c_wlap, Mdrho;
     R K, Hc0, Hc1, Pfac, inv_1mcs2, two_over_1md0;
     R eta, s0, s1, s2, s3, s4, s1phi, solid_eps;
+    R two_over_D;  // conservative Allen-Cahn: theta = (2/D)(1 - phi^2)
     R Fb[3];
     R scale[2], inv_scale[2];
 };
@@ -141,6 +143,7 @@ inline KParams<R> make_kparams(const DevParams &d)
     k.s4 = (R)d.s4;
     k.s1phi = (R)d.s1phi;
     k.solid_eps = (R)d.solid_eps;
+    k.two_over_D = (R)(2.0 / d.D);
     for (int a = 0; a < 3; ++a) k.Fb[a] = (R)d.Fb[a];
     for (int a = 0; a < 2; ++a) {
         k.scale[a] = (R)d.scale[a];

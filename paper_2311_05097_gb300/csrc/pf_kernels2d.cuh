@@ -424,7 +424,19 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         const R drho = kp.drho;
         const R rho = drho * phi + kp.rhom;
         const R muv = kp.dmu * phi + kp.mum;
-        const R Sx = kp.Mdrho * gmx, Sy = kp.Mdrho * gmy;
+        // conservative Allen-Cahn option: theta n = (2/D)(1 - phi^2) grad phi/|grad phi|
+        const bool cac = EXT && p.phase_model == 1;
+        R tnx = R(0), tny = R(0);
+        if (cac) {
+            const R g2 = gpx * gpx + gpy * gpy;
+            const R th = kp.two_over_D * (R(1) - phi * phi);
+            const R inv = g2 > R(1e-24) ? R(1) / sqrt(g2) : R(0);
+            tnx = th * gpx * inv;
+            tny = th * gpy * inv;
+        }
+        // mass flux: S = M (rho1 - rho2)/2 grad mu, or (grad phi - theta n) for Allen-Cahn
+        const R Sx = cac ? kp.Mdrho * (gpx - tnx) : kp.Mdrho * gmx;
+        const R Sy = cac ? kp.Mdrho * (gpy - tny) : kp.Mdrho * gmy;
         const R grx = drho * gpx, gry = drho * gpy;
         R Fx = mu * gpx + kp.Fb[0], Fy = mu * gpy + kp.Fb[1];
         if constexpr (MODE == MODE_STEP) {
@@ -558,7 +570,8 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         } else {
             const R cs2 = kp.cs2, cs4 = kp.cs4;
             // ---- order-parameter lattice (Eq. 30): Hermite equilibria and source
-            const R eta_mu = kp.eta * mu;
+            // (Allen-Cahn: eta mu -> phi, and cs^2 theta n joins the source)
+            const R eta_mu = cac ? phi : kp.eta * mu;
             R heq[9], hF[9], S[9];
             heq[0] = phi;
             heq[1] = phi * ux;
@@ -572,6 +585,10 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             hF[0] = R(0);
             hF[1] = phi * ux - php * upx;  // d_t(phi u), explicit Euler
             hF[2] = phi * uy - php * upy;
+            if (cac) {
+                hF[1] += cs2 * tnx;
+                hF[2] += cs2 * tny;
+            }
 #pragma unroll
             for (int k = 3; k < 9; ++k) hF[k] = R(0);
             S[0] = kp.s0;

@@ -39,6 +39,7 @@ class pf_params(C.Structure):
         ("s3", C.c_double), ("s4", C.c_double), ("theta_deg", C.c_double),
         ("Fb", C.c_double * 3), ("g", C.c_double * 3), ("solid_eps", C.c_double),
         ("rep_xi", C.c_double), ("rep_eps", C.c_double), ("wall_circle", C.c_double * 3),
+        ("phase_model", C.c_int),
         ("precision", C.c_int), ("store_log2_scale", C.c_int * 2), ("stream", C.c_void_p),
     ]
 
@@ -139,6 +140,8 @@ def make_params(precision=PF_P64, stream=None, **kw):
             setattr(p, k, (C.c_int * 2)(*v))
         elif k == "eta":
             p.eta = float(v)
+        elif k == "phase_model":
+            p.phase_model = int(v)
         else:
             setattr(p, k, float(v))
     p.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision

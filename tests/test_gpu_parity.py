@@ -494,7 +494,8 @@ def test_walls_reject_pair_kernels(pf):
 
 def test_batch_mixes_wall_and_periodic_domains(pf):
     """One batch holding a walled domain and a periodic one (per-domain
-    boundary flag in the tile table): each evolves as when run alone."""
+    boundary flag in the tile table): each evolves as when run alone (the
+    walled one bit for bit)."""
     cases = [W.wall_case((37, 52), seed=3), W.small_case((52, 40), seed=3, solid=False, u_amp=0.01)]
     steps = 300
     b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="p64",
@@ -507,7 +508,12 @@ def test_batch_mixes_wall_and_periodic_domains(pf):
         g, _ = run_pair(pf, c, steps, oracle=False, walls=(i == 0))
         mb, mg = b.macros(i), g.macros()
         for k in FIELDS:
-            assert np.array_equal(mb[k], mg[k]), (i, k)
+            if i == 0:
+                assert np.array_equal(mb[k], mg[k]), (i, k)
+            else:
+                # the batch runs the periodic domain through the wall-handling
+                # instantiation: the same arithmetic, compiled apart (rounding)
+                assert rel(mb[k], mg[k]) < 1e-12, (i, k, rel(mb[k], mg[k]))
     o = O.OracleSim(cases[0]["shape"], O.make_params(**cases[0]["params"]))
     o.set_walls(True)
     o.init(cases[0]["phi0"], cases[0]["phi"], cases[0]["u"])
@@ -545,3 +551,54 @@ def test_p64_particle_wall_repulsion_matches_oracle(pf):
     assert g.particle(0)["u"][1] > g2.particle(0)["u"][1]   # bottom wall pushes up
     assert g.particle(1)["u"][1] < g2.particle(1)["u"][1]   # top wall pushes down
     assert g.particle(2)["u"][0] < g2.particle(2)["u"][0]   # the circle pushes inwards
+
+
+# ---- conservative Allen-Cahn order parameter (2D option) --------------------------------
+
+@pytest.mark.parametrize("shape,solid,walls,steps", [
+    ((52, 40), True, False, 120),
+    ((37, 45), False, False, 150),
+    ((37, 52), True, True, 120),
+])
+def test_allen_cahn_p64_matches_oracle(pf, shape, solid, walls, steps):
+    """phase_model 1 (flux M (grad phi - theta n) on the lattice of Eq. 30),
+    FP64 against the oracle: with a fixed solid, with random flow, and inside
+    box walls."""
+    if walls:
+        c = W.wall_case(shape, seed=3)
+    else:
+        c = W.small_case(shape, seed=7, solid=solid, theta_deg=60.0, u_amp=0.01)
+    c["params"] = dict(c["params"], phase_model=1)
+    g, o = run_pair(pf, c, steps, walls=walls)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, k
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_allen_cahn_reduced_precision(pf, precision, tol_phi):
+    """The Allen-Cahn option in FP32 and with 16-bit storage against the FP64
+    oracle; mixed storage keeps sum phi exact."""
+    c = W.small_case((52, 40), seed=7, solid=False, u_amp=0.01)
+    c["params"] = dict(c["params"], phase_model=1)
+    g, o = run_pair(pf, c, 200, precision=precision)
+    gm, om = g.macros(), o.macros()
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    assert g.diagnostics()["nan_flag"] == 0
+    if precision != "p32":
+        m0 = float(np.sum(c["phi"]))
+        g.step(1000)
+        assert abs(g.diagnostics()["mass"] - m0) / np.abs(c["phi"]).sum() < 1e-13
+
+
+def test_allen_cahn_rejections(pf):
+    c = W.small_case((32, 32), seed=1, solid=False)
+    g = pf.Sim(c["shape"], precision="fp16", **dict(c["params"], phase_model=1))
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(32, 16, 1)  # the two-cells-per-thread kernels have no Allen-Cahn path
+    with pytest.raises(pf.PfError):
+        pf.Sim((16, 16, 16), precision="p32", **dict(c["params"], d0=0.3, phase_model=1))
+    with pytest.raises(pf.PfError):
+        pf.Sim((32, 32), precision="p32", **dict(c["params"], phase_model=2))
