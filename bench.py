@@ -393,6 +393,7 @@ def run_batch(args, dist, rank, world, local):
 
 
 def run_single(args, dist, rank, world, local):
+    import numpy as np
     import ctypes as C
 
     import torch
@@ -456,15 +457,22 @@ def run_single(args, dist, rank, world, local):
         S, iters = 20, 5
         phi0_h = torch.from_numpy(case["phi0"]).pin_memory()
         phi_h = torch.from_numpy(case["phi"]).pin_memory()
+        u0 = case.get("u")
+        u_h = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory() if u0 is not None else None
         out_h = torch.empty(cells, dtype=torch.float64).pin_memory()
         L = pf.load()
         s2 = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream,
                  walls_y=case.get("walls_y", False), **case["params"])
+        parts = case.get("particles", [])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(iters):
+            # the same workload as the timed run: particles reset, initial flow
+            for k, pp in enumerate(parts):
+                s2.set_particle(k, **pp)
             rc = L.pf_init_fields(s2._h, C.c_void_p(phi0_h.data_ptr()), C.c_void_p(phi_h.data_ptr()),
-                                  None, None, pf.PF_HOST)
+                                  C.c_void_p(u_h.data_ptr()) if u_h is not None else None, None,
+                                  pf.PF_HOST)
             if rc:
                 raise pf.PfError(rc, pf.last_error())
             s2.step(S)
@@ -474,12 +482,14 @@ def run_single(args, dist, rank, world, local):
                 raise pf.PfError(rc, pf.last_error())
         dt = time.perf_counter() - t0
         s2.close()
+        h2d = (16 + (8 * dim if u_h is not None else 0)) * cells + C.sizeof(pf.pf_particle) * len(parts)
         e2e = {"value": round(cells * S * iters / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
-               "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
+               "h2d_bytes_per_step": h2d // S, "d2h_bytes_per_step": 8 * cells // S,
+               "h2d_bytes_per_call": h2d, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
-               "desc": "per call: pf_init_fields(pinned host phi0, phi) + pf_step(%d) + "
-                       "pf_get_macros(phi to pinned host); wall clock" % S}
+               "desc": "per call: pf_particle_state(set) of every particle + pf_init_fields(pinned host "
+                       "phi0, phi%s) + pf_step(%d) + pf_get_macros(phi to pinned host); wall clock"
+                       % (", u" if u_h is not None else "", S)}
     sim.close()
     cfg = {"workload": args.workload, "cells": cells, "precision": prec, "desc": case["desc"],
            "l2": "flushed between timed steps: 512 MiB write, then a 256 MiB read so the "
@@ -528,12 +538,18 @@ def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim
         S = 20
         phi0_h = torch.from_numpy(np.ascontiguousarray(case["phi0"])).pin_memory()
         phi_h = torch.from_numpy(np.ascontiguousarray(case["phi"])).pin_memory()
+        u0 = case.get("u")
+        u_h = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory() if u0 is not None else None
         out_h = torch.empty(cells, dtype=torch.float64).pin_memory()
+        parts = case.get("particles", [])
         L = pf.load()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        # the same workload as the timed run: particles reset, initial flow
+        for k, pp in enumerate(parts):
+            sim.set_particle(k, **pp)
         rc = L.pf_init_fields(sim._h, C.c_void_p(phi0_h.data_ptr()), C.c_void_p(phi_h.data_ptr()),
-                              None, None, pf.PF_HOST)
+                              C.c_void_p(u_h.data_ptr()) if u_h is not None else None, None, pf.PF_HOST)
         if rc:
             raise pf.PfError(rc, pf.last_error())
         sim.step(S)
@@ -541,12 +557,15 @@ def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim
         if rc:
             raise pf.PfError(rc, pf.last_error())
         dt = time.perf_counter() - t0
+        dim = len(case["shape"])
+        h2d = (16 + (8 * dim if u_h is not None else 0)) * cells + C.sizeof(pf.pf_particle) * len(parts)
         e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
-               "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
-               "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
+               "h2d_bytes_per_step": h2d // S, "d2h_bytes_per_step": 8 * cells // S,
+               "h2d_bytes_per_call": h2d, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
-               "desc": "pf_init_fields(pinned host phi0, phi) + pf_step(%d) + pf_get_macros(phi "
-                       "to pinned host); wall clock" % S}
+               "desc": "pf_particle_state(set) of every particle + pf_init_fields(pinned host phi0, "
+                       "phi%s) + pf_step(%d) + pf_get_macros(phi to pinned host); wall clock"
+                       % (", u" if u_h is not None else "", S)}
     sim.close()
     cfg = {"workload": args.workload, "cells": cells, "precision": prec, "desc": case["desc"],
            "l2": "state (%.2f GB) larger than L2 (129 MB); no flush" % (cells * bpc / 1e9),

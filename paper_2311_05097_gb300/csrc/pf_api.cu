@@ -183,7 +183,6 @@ static int validate(const pf_grid *g, const pf_params *p)
         return fail(PF_EINVAL, "unknown precision %d", p->precision);
     const double cs2 = p->d0;
     if (p->phase_model != 0 && p->phase_model != 1) return fail(PF_EINVAL, "phase_model must be 0 or 1");
-    if (p->phase_model == 1 && g->dim != 2) return fail(PF_EINVAL, "phase_model 1 (Allen-Cahn) is 2D only");
     const double eta = p->phase_model == 1 ? 1.0 : (p->eta > 0 ? p->eta : 2.0 * p->M / cs2);
     const double s1phi = 1.0 / (p->M / (eta * cs2) + 0.5);
     if (!(s1phi > 0 && s1phi < 2)) return fail(PF_EINVAL, "eta gives s_1phi outside (0, 2)");

@@ -370,7 +370,21 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             const R drho = kp.drho;
             const R rho = drho * phi + kp.rhom;
             const R muv = kp.dmu * phi + kp.mum;
-            const R Sx = kp.Mdrho * gmx, Sy = kp.Mdrho * gmy, Sz = kp.Mdrho * gmz;
+            // conservative Allen-Cahn option: theta n = (2/D)(1 - phi^2) grad phi/|grad phi|
+            // and the mass flux M (rho1 - rho2)/2 (grad phi - theta n)
+            const bool cac = Dm.p.phase_model == 1;
+            R tnx = R(0), tny = R(0), tnz = R(0);
+            if (cac) {
+                const R g2 = gpx * gpx + gpy * gpy + gpz * gpz;
+                const R th = kp.two_over_D * (R(1) - phi * phi);
+                const R inv = g2 > R(1e-24) ? R(1) / sqrt(g2) : R(0);
+                tnx = th * gpx * inv;
+                tny = th * gpy * inv;
+                tnz = th * gpz * inv;
+            }
+            const R Sx = cac ? kp.Mdrho * (gpx - tnx) : kp.Mdrho * gmx;
+            const R Sy = cac ? kp.Mdrho * (gpy - tny) : kp.Mdrho * gmy;
+            const R Sz = cac ? kp.Mdrho * (gpz - tnz) : kp.Mdrho * gmz;
             const R grx = drho * gpx, gry = drho * gpy, grz = drho * gpz;
             R Fx = mu * gpx + kp.Fb[0], Fy = mu * gpy + kp.Fb[1], Fz = mu * gpz + kp.Fb[2];
             if constexpr (MODE == MODE_STEP) {
@@ -508,7 +522,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             } else {
                 const R cs2 = kp.cs2, cs4 = kp.cs4;
                 // order-parameter lattice (D3Q7)
-                const R em = kp.eta * mu;
+                const R em = cac ? phi : kp.eta * mu;  // Allen-Cahn: eta mu -> phi
                 {
                     R heq[7], hF[7], S[7];
                     heq[0] = phi;
@@ -520,6 +534,11 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     hF[1] = phi * ux - php * upx;
                     hF[2] = phi * uy - php * upy;
                     hF[3] = phi * uz - php * upz;
+                    if (cac) {
+                        hF[1] += cs2 * tnx;
+                        hF[2] += cs2 * tny;
+                        hF[3] += cs2 * tnz;
+                    }
                     hF[4] = hF[5] = hF[6] = R(0);
                     S[0] = kp.s0;
                     S[1] = S[2] = S[3] = kp.s1phi;

@@ -249,17 +249,18 @@ __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const doub
     const R cs2 = (R)p.cs2, cs4 = cs2 * cs2, d0 = (R)p.d0;
     PF_INIT_ROWS_BEGIN
         R g[3];
-        const bool cac = p.phase_model == 1;  // conservative Allen-Cahn option (2D)
+        const bool cac = p.phase_model == 1;  // conservative Allen-Cahn option
         fd_grad_lap_r<DIM, R>(Dm, cac ? phi : mu, x, y, z, g, nullptr);
         if (cac) {
             // S from grad phi - theta n, theta = (2/D)(1 - phi^2), n = grad phi/|grad phi|
             const R pc = (R)phi[o];
-            const R g2 = g[0] * g[0] + g[1] * g[1];
+            R g2 = R(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) g2 += g[a] * g[a];
             const R th = R(2.0 / p.D) * (R(1) - pc * pc);
             const R inv = g2 > R(1e-24) ? R(1) / sqrt(g2) : R(0);
-            const R gx = g[0], gy = g[1];
-            g[0] = gx - th * gx * inv;
-            g[1] = gy - th * gy * inv;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) g[a] = g[a] - th * g[a] * inv;
         }
         const R Md = (R)p.Mdrho;
         const R S[3] = {Md * g[0], Md * g[1], DIM == 3 ? Md * g[2] : R(0)};
