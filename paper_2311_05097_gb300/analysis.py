@@ -129,6 +129,20 @@ def information_entropy(phi, bins=20, lo=-1.0, hi=1.0):
     return float(-(p * np.log2(p)).sum())
 
 
+def displacement_efficiency(phi, phi0, x_lo, x_hi):
+    """De of Sec. 4.6: the share of fluid 1 (volume fraction (1 + phi)/2 of
+    the fluid part 1 - phi0, phi0 the total solid indicator: walls and
+    particles) found outside the cavity x_lo <= x <= x_hi."""
+    fluid = np.clip(1.0 - phi0, 0.0, 1.0)
+    # phase of the fluid part (phi is scaled by 1 - phi0 near solids)
+    c = np.clip(phi / np.maximum(fluid, 1e-3), -1.0, 1.0)
+    f1 = 0.5 * (1.0 + c) * fluid * (fluid > 0.01)
+    x = np.arange(phi.shape[1])[None, :]
+    out = (x < x_lo) | (x > x_hi)
+    tot = f1.sum()
+    return float((f1 * out).sum() / tot) if tot > 0 else 0.0
+
+
 def interface_level(phi, x, y_lo, y_hi):
     """Height of the phi = 0 crossing (phase 1 below, phase 2 above) in column
     x between rows y_lo and y_hi, by linear interpolation; NaN if none."""

@@ -327,6 +327,68 @@ def annulus_mixing(n=512, count=15, seed=4, D=5.0, omega=1e-4, g=1e-6, rep_xi=2.
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, name="annulus_mixing_2d")
 
 
+def channel_displacement(L=256, count=16, seed=5, D=5.0, Fb=4e-8, rep_xi=2.5, rep_eps=1e4,
+                         particles=True, fluid1=True):
+    """Displacement of a drop of fluid 1 out of a cavity by fluid 2 and free
+    particles in a channel of height L and length 5L (Sec. 4.6 layout in
+    lattice units, dx = 0.01 of the paper): periodic in x, no-flux box walls at
+    both ends of y, a bottom wall of height L/4 with a large cavity (the circle
+    of radius L centred at (L, L)) and a small one (radius L/4 centred at
+    (9L/4, L/4); see the reading of its centre) holding the drop; ``count``
+    particles R in [0.0625 L, 0.078 L], rho_p in [0.95, 1.05], theta_k in
+    [80, 100] deg, most of them above the large cavity; fluid 2 drives with a
+    body force Fb in x; equal densities, mu1 = 0.1, mu2 = 0.01, sigma = 0.001,
+    neutral walls.  ``particles`` / ``fluid1`` switch off the particles (the
+    paper's case B) or the drop (case A)."""
+    rng = np.random.default_rng(seed)
+    shape = (L, 5 * L)
+    X, Y = _coords(shape)
+    xc_small = 9.0 * L / 4.0
+
+    def ind(zeta):
+        return smooth_indicator(zeta, D)
+
+    # bottom wall below y = L/4, minus the two cavities (product of indicators)
+    phi0 = (ind(L / 4.0 - Y) * ind(np.hypot(X - L, Y - L) - L)
+            * ind(np.hypot(X - xc_small, Y - L / 4.0) - L / 4.0))
+    parts = []
+    if particles:
+        placed = []
+        tries = 0
+        while len(placed) < count and tries < 200000:
+            tries += 1
+            R = rng.uniform(0.0625 * L, 0.078 * L)
+            # three quarters above the large cavity, the rest upstream of the drop
+            x = rng.uniform(0.35 * L, 1.65 * L) if len(placed) < 0.75 * count else rng.uniform(1.7 * L, 4.8 * L)
+            y = rng.uniform(0.0, L - R - 4.0)
+            xi, yi = int(round(x)) % shape[1], int(round(y))
+            if yi < 0 or yi >= L:
+                continue
+            # clear of the solid (phi0 < 1e-3 on a ring just outside the particle)
+            ang = np.linspace(0.0, 2 * math.pi, 32, endpoint=False)
+            rx = (np.round(x + (R + 4.0) * np.cos(ang)).astype(int)) % shape[1]
+            ry = np.round(y + (R + 4.0) * np.sin(ang)).astype(int)
+            if np.any(ry < 0) or np.any(ry >= L) or np.any(phi0[ry, rx] > 1e-3) or phi0[yi, xi] > 1e-3:
+                continue
+            if any(math.hypot(x - q[0], y - q[1]) < R + q[2] + 6.0 for q in placed):
+                continue
+            placed.append((x, y, R))
+        for x, y, R in placed:
+            parts.append(dict(x=(x, y, 0.0), u=(0.0, 0.0, 0.0), w=(0.0, 0.0, 0.0), R=R,
+                              rho_p=rng.uniform(0.95, 1.05), theta_deg=rng.uniform(80.0, 100.0)))
+    solid = phi0.copy()
+    for q in parts:
+        solid = solid + disc(shape, q["x"], q["R"], D)
+    if fluid1:
+        phi = (1.0 - solid) * np.tanh(2.0 * (L / 4.0 - np.hypot(X - xc_small, Y - L / 4.0)) / D)
+    else:
+        phi = -(1.0 - solid)
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.01, theta_deg=90.0,
+               Fb=(Fb, 0.0, 0.0), rep_xi=rep_xi, rep_eps=rep_eps)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, walls_y=True,
+                cavity=(2.0 * L, 2.5 * L), name="channel_displacement_2d")
+
+
 def equal_area_cap_base(theta_deg, area):
     """Radius and base half-width of a circular cap of given area on a flat wall."""
     th = math.radians(theta_deg)
