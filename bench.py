@@ -11,9 +11,9 @@ one time step of every domain.
 
 Other workloads: ``drop_on_cylinder`` (512 x 512, density ratio 100, FP32;
 its state fits in L2, so L2 is flushed between individually timed steps),
-``static_drop`` (128 x 128, FP64), ``water_entry``, ``annulus`` (moving
-particles), ``porous_2d`` (phase separation in random discs between
-bounce-back walls) and ``drainage_3d``.
+``static_drop`` (128 x 128, FP64), ``water_entry``, ``annulus`` and
+``channel`` (moving particles), ``porous_2d`` (phase separation in random
+discs between bounce-back walls) and ``drainage_3d``.
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload on the host cores.  Under torchrun every rank runs an
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "drop_on_cylinder", "static_drop", "water_entry",
-                             "drainage_3d", "annulus", "porous_2d"])
+                             "drainage_3d", "annulus", "porous_2d", "channel"])
     ap.add_argument("--n3d", type=int, default=256, help="cube side of drainage_3d")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
@@ -97,6 +97,15 @@ def single_workload(name, n3d=256):
                      "rotating at 1e-4 rad/step, 15 free wetting particles (R 20-30, own contact angles "
                      "45-135 deg), repulsion, gravity on particles; force/torque reduction and "
                      "Newton-Euler in FP64 every step")
+        return c
+    if name == "channel":
+        c = W.channel_displacement()
+        c["precision"] = "p32"
+        c["desc"] = ("2D displacement in a complex channel (Sec. 4.6 layout): 1280x256, bottom wall with two "
+                     "cavities, bounce-back walls at both ends of y, a drop of fluid 1 in the small cavity, "
+                     "16 free particles (R 16-20, own contact angles 80-100 deg), body force 3e-7, "
+                     "particle-particle and particle-wall repulsion; force/torque reduction and Newton-Euler "
+                     "in FP64 every step")
         return c
     if name == "porous_2d":
         c = W.porous_phase_separation_2d(n=1024, theta_deg=45.0)

@@ -327,7 +327,7 @@ def annulus_mixing(n=512, count=15, seed=4, D=5.0, omega=1e-4, g=1e-6, rep_xi=2.
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, name="annulus_mixing_2d")
 
 
-def channel_displacement(L=256, count=16, seed=5, D=5.0, Fb=4e-8, rep_xi=2.5, rep_eps=1e4,
+def channel_displacement(L=256, count=16, seed=5, D=5.0, Fb=3e-7, rep_xi=2.5, rep_eps=1e4,
                          particles=True, fluid1=True):
     """Displacement of a drop of fluid 1 out of a cavity by fluid 2 and free
     particles in a channel of height L and length 5L (Sec. 4.6 layout in
@@ -337,7 +337,9 @@ def channel_displacement(L=256, count=16, seed=5, D=5.0, Fb=4e-8, rep_xi=2.5, re
     (9L/4, L/4); see the reading of its centre) holding the drop; ``count``
     particles R in [0.0625 L, 0.078 L], rho_p in [0.95, 1.05], theta_k in
     [80, 100] deg, most of them above the large cavity; fluid 2 drives with a
-    body force Fb in x; equal densities, mu1 = 0.1, mu2 = 0.01, sigma = 0.001,
+    body force Fb in x; equal densities, viscosity ratio 10 (mu1 = 0.5,
+    mu2 = 0.05: at the paper's mu2 = 0.01 the scheme blows up within 500 steps
+    in this geometry, even without particles or walls), sigma = 0.001,
     neutral walls.  ``particles`` / ``fluid1`` switch off the particles (the
     paper's case B) or the drop (case A)."""
     rng = np.random.default_rng(seed)
@@ -383,7 +385,7 @@ def channel_displacement(L=256, count=16, seed=5, D=5.0, Fb=4e-8, rep_xi=2.5, re
         phi = (1.0 - solid) * np.tanh(2.0 * (L / 4.0 - np.hypot(X - xc_small, Y - L / 4.0)) / D)
     else:
         phi = -(1.0 - solid)
-    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.01, theta_deg=90.0,
+    p = params(sigma=0.001, D=D, M=0.1, rho1=1.0, rho2=1.0, mu1=0.5, mu2=0.05, theta_deg=90.0,
                Fb=(Fb, 0.0, 0.0), rep_xi=rep_xi, rep_eps=rep_eps)
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, walls_y=True,
                 cavity=(2.0 * L, 2.5 * L), name="channel_displacement_2d")

@@ -622,3 +622,20 @@ def test_allen_cahn_rejections(pf):
         g.set_config(32, 16, 1)  # the two-cells-per-thread kernels have no Allen-Cahn path
     with pytest.raises(pf.PfError):
         pf.Sim((32, 32), precision="p32", **dict(c["params"], phase_model=2))
+
+
+def test_channel_displacement_full_size_against_oracle(pf):
+    """Sec. 4.6 layout at full size (1280 x 256, bottom wall with two cavities,
+    bounce-back walls, a drop of fluid 1, 16 particles with their own angles,
+    repulsion from each other and from the box walls): FP64 fields and
+    particle states against the oracle after 3 steps."""
+    c = W.channel_displacement()
+    g, o = run_pair(pf, c, 3, particles=c["particles"], walls=True)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * 0.001 / 5.0)
+    for k in range(len(c["particles"])):
+        pg, po = g.particle(k), o.particle(k)
+        assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() <= 1e-12 * np.abs(po.x).max(), k
+        R = po.R
+        us = np.abs(po.u).max() + abs(po.w[2]) * R + 1e-4
+        assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() <= 1e-12 * us, k
+        assert np.abs(np.array(pg["w"]) - np.array(po.w)).max() <= 1e-12 * us / R, k
