@@ -140,9 +140,13 @@ typedef struct pf_particle {
                           are then summed per solid, each with its own angle;
                           all solids without an own angle form one solid. */
     double F[3], T[3];
-    int prescribed;    /* 1: the particle keeps the u and w it was given (prescribed
-                          motion, e.g. a rotating cylinder): x advances by u, F and
-                          T are still reported; 0: Newton-Euler (Eqs. 26, 28) */
+    int prescribed;    /* held motion, bit flags (0: Newton-Euler, Eqs. 26, 28):
+                          1 keeps all of the u and w it was given (prescribed
+                          motion, e.g. a rotating cylinder); 2, 4, 8 keep the
+                          translation along x, y, z; 16 keeps the rotation (the
+                          two-particle balance of Sec. 4.4 holds 2 | 16).  x
+                          advances by u; F and T are still reported.  Values
+                          outside 0..31: PF_EINVAL */
 } pf_particle;
 
 /* FP64 diagnostics at the current time: mass = sum phi, E_F of Eq. (8),

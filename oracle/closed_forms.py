@@ -106,3 +106,34 @@ def particle_interface_height(L, Rp, theta_deg, Bo):
 
     a = optimize.brentq(f, -0.5 * math.pi + 1e-12, 0.5 * math.pi - 1e-12, xtol=1e-15, rtol=1e-15)
     return Rp * math.cos(th - a) + c * (1.0 - math.cos(a)), a
+
+
+
+def particle_pair_balance(L, Rp, theta_deg, Bo, delta):
+    """Equilibrium of two equal wetting particles (2D discs) at a fluid-fluid
+    interface of equal densities under gravity, centres 2 delta apart in a
+    periodic box of width L, allowed to move only vertically (Sec. 4.4, after
+    Mino et al.).  The fluid carries both weights through one pressure jump,
+    dp L = 2 pi sigma Bo, so every interface piece is an arc of radius
+    R_c = sigma/dp = L/(2 pi Bo).  The slope angles alpha (wide gap, L - 2 delta)
+    and beta (narrow gap, 2 delta) at the contact points follow from the arcs
+    closing the gaps: L/2 - delta = R_p sin(theta - alpha) + R_c sin(alpha),
+    delta = R_p sin(theta - beta) + R_c sin(beta).  The printed balances then
+    give the lateral force F_lat = sigma (cos alpha - cos beta)
+    + R_p (cos(theta - beta) - cos(theta - alpha)) dp (> 0: repulsive) and
+    satisfy the vertical one identically.  h is the downward distance from the
+    interface at the middle of the wide gap to the centres.
+    Returns dict(h, F_lat_over_sigma, alpha, beta, Rc)."""
+    th = math.radians(theta_deg)
+    Rc = L / (2.0 * math.pi * Bo)
+
+    def slope(gap_half):
+        def f(a):
+            return Rp * math.sin(th - a) + Rc * math.sin(a) - gap_half
+        return optimize.brentq(f, -0.5 * math.pi + 1e-12, 0.5 * math.pi - 1e-12, xtol=1e-15, rtol=1e-15)
+
+    a = slope(0.5 * L - delta)
+    b = slope(delta)
+    h = Rp * math.cos(th - a) + Rc * (1.0 - math.cos(a))
+    f_lat = (math.cos(a) - math.cos(b)) + Rp / Rc * (math.cos(th - b) - math.cos(th - a))
+    return dict(h=h, F_lat_over_sigma=f_lat, alpha=a, beta=b, Rc=Rc)

@@ -125,8 +125,10 @@ class Particle:
     """Plain particle record (FP64) mirroring the oracle's struct."""
 
     def __init__(self, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0, theta_deg=None, prescribed=False):
+        # prescribed: False/True (all of u and w held) or the bit flags of the
+        # held components (2, 4, 8: x, y, z translation; 16: rotation)
         self.theta_deg = float("nan") if theta_deg is None else float(theta_deg)
-        self.prescribed = bool(prescribed)
+        self.prescribed = int(prescribed)
         self.x = list(x) + [0.0] * (3 - len(x))
         self.u = list(u) + [0.0] * (3 - len(u))
         self.w = list(w) + [0.0] * (3 - len(w))
@@ -143,14 +145,14 @@ class Particle:
             setattr(c, k, (C.c_double * 3)(*getattr(self, k)))
         c.R, c.rho_p = self.R, self.rho_p
         c.theta_deg = self.theta_deg
-        c.prescribed = 1 if self.prescribed else 0
+        c.prescribed = int(self.prescribed)
         return c
 
     @classmethod
     def from_c(cls, c):
         p = cls(list(c.x), list(c.u), list(c.w), c.R, c.rho_p)
         p.theta_deg = c.theta_deg
-        p.prescribed = bool(c.prescribed)
+        p.prescribed = int(c.prescribed)
         p.u_prev, p.w_prev = list(c.u_prev), list(c.w_prev)
         p.F, p.T = list(c.F), list(c.T)
         return p

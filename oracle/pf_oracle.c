@@ -73,6 +73,10 @@
  *       to the source G; the mass flux of the momentum equation becomes
  *       S = M (rho1 - rho2)/2 (grad phi - theta n); mu_phi of Eq. (9) still
  *       gives the surface force, and solids and particles enter it as before.
+  *   R25 the two-particle balance of Sec. 4.4 lets the particles move only
+ *       vertically: a particle may hold single components of its motion
+ *       (translation along an axis, the rotation), which keep their given
+ *       value while the hydrodynamic force and torque are still reported.
  */
 #include "pf_oracle.h"
 
@@ -618,10 +622,10 @@ void orc_particle_update(int dim, const orc_params *p, orc_particle *pp, const d
         pp->x[k] += pp->u[k];
         pp->u_prev[k] = pp->u[k];
         pp->w_prev[k] = pp->w[k];
-        if (!pp->prescribed) {
-            pp->u[k] += a[k];
-            pp->w[k] += al[k];
-        }
+        /* R25: held components keep their value (bit 0: all; bits 1-3:
+         * translation along x, y, z; bit 4: rotation) */
+        if (!(pp->prescribed & 1) && !(pp->prescribed & (2 << k))) pp->u[k] += a[k];
+        if (!(pp->prescribed & 1) && !(pp->prescribed & 16)) pp->w[k] += al[k];
     }
 }
 

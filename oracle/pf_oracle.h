@@ -49,7 +49,9 @@ typedef struct orc_particle {
     double u_prev[3], w_prev[3];  /* previous-step velocities (Eq. 28) */
     double F[3], T[3];            /* last hydrodynamic force / torque (Eq. 27) */
     double theta_deg;             /* own contact angle (Sec. 4.5), NaN = the simulation's */
-    int prescribed;               /* 1: u and w kept (prescribed motion), x advances by u */
+    int prescribed;               /* bit flags of held motion (reading R25): 1 all of u and
+                                     w kept (prescribed motion); 2, 4, 8 the x, y, z
+                                     translation; 16 the rotation; x advances by u */
 } orc_particle;
 
 typedef struct orc_sim orc_sim;

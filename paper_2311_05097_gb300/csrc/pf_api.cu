@@ -1039,6 +1039,8 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         if (own && !(io->theta_deg > 0 && io->theta_deg < 180))
             return fail(PF_EINVAL, "particle theta_deg must be NaN or lie in (0, 180)");
         if (own && E.dim == 3) return fail(PF_EINVAL, "own particle contact angles are built for 2D");
+        if (io->prescribed < 0 || io->prescribed > 31)
+            return fail(PF_EINVAL, "particle prescribed flags must lie in 0..31");
         if (E.np > 0) CK(cudaMemcpy(E.hp, E.d_parts, sizeof(ParticleDev) * E.np, cudaMemcpyDeviceToHost));
         ParticleDev &pp = E.hp[k];
         memset(&pp, 0, sizeof(pp));
@@ -1052,7 +1054,7 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         pp.R = io->R;
         pp.rho_p = io->rho_p;
         pp.theta_deg = own ? io->theta_deg : NAN;
-        pp.prescribed = io->prescribed ? 1 : 0;
+        pp.prescribed = io->prescribed;
         pp.own = own ? 1 : 0;
         pp.ct = own ? std::cos(io->theta_deg * 3.14159265358979323846 / 180.0) : 0.0;
         const bool grew = k == E.np;

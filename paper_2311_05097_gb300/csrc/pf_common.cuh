@@ -95,7 +95,7 @@ struct ParticleDev {
     double theta_deg;  // own contact angle, NaN for the handle's
     double ct;         // cos(theta_deg) when own
     int own;           // 1 if the particle has its own contact angle
-    int prescribed;    // 1: u and w are kept (prescribed motion)
+    int prescribed;    // held motion: 1 all of u and w; 2, 4, 8 x, y, z translation; 16 rotation
 };
 
 // The constants the step kernels read, in the kernel's arithmetic type (so a

@@ -119,6 +119,19 @@ __device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy
     return R(0.5) * (R(1) + tanh(R(2) * ((R)pp.R - r) / (R)D));
 }
 
+// The same indicator from the offset (dx, dy) of the cell to the particle's
+// centre, given in the arithmetic type (no minimum-image arithmetic).
+template <class R>
+__device__ __forceinline__ R particle_phi0_rel(R dx, R dy, R Rp, R lim, R D, R &rx, R &ry)
+{
+    rx = dx;
+    ry = dy;
+    const R r2 = dx * dx + dy * dy;
+    if (r2 >= lim * lim) return R(0);
+    const R r = sqrt(r2);
+    return R(0.5) * (R(1) + tanh(R(2) * (Rp - r) / D));
+}
+
 // Resident CTAs per SM requested from the register allocator: FP64 keeps its
 // registers (no cap); the 32 x 8 FP32/16-bit kernels trade a few spills for a
 // fourth CTA, 64 x 4 keeps three; the autotuner picks among the shapes.
@@ -154,6 +167,12 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
     __shared__ double s_red[NT / 32][6];
     __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
+    // particles whose image nearest to the tile is the minimum image of every
+    // cell of its frames, and that image's centre in table coordinates (the
+    // cells then skip the FP64 minimum-image arithmetic)
+    constexpr int PMAX = 64;
+    __shared__ unsigned long long s_fast;
+    __shared__ R s_pcx[MOVING ? PMAX : 1], s_pcy[MOVING ? PMAX : 1];
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -169,7 +188,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
 
         __syncthreads();  // previous tile's shared-memory readers are done
         if constexpr (MOVING) {
-            if (tid == 0) s_near = 0ull;
+            if (tid == 0) s_near = s_fast = 0ull;
         }
         const int wall = EXT ? Dm.wall_y : 0;
         const int nyw = wall ? 0 : ny;  // minimum image in y only without walls
@@ -215,11 +234,32 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const double ex = fmax(fabs(dx) - (0.5 * TX + 2.0), 0.0);
                 const double ey = fmax(fabs(dy) - (0.5 * TY + 2.0), 0.0);
                 const double lim = pp.R + p.cut + 1.0;
-                if (ex * ex + ey * ey < lim * lim) atomicOr(&s_near, 1ull << k);
+                if (ex * ex + ey * ey < lim * lim) {
+                    atomicOr(&s_near, 1ull << k);
+                    // a cell of the frames farther than nx/2 from this image is at
+                    // least R + cut + 1 from every image when the box is this wide
+                    const double span = 2.0 * (pp.R + p.cut) + 8.0;
+                    const bool fx = nx >= span + TX;
+                    const bool fy = (EXT && wall) ? !wall_tile : ny >= span + TY;
+                    if (fx && fy) {
+                        s_pcx[k] = (R)((x0 + 0.5 * (TX - 1)) - dx - (x0 - 3));
+                        s_pcy[k] = (R)((y0 + 0.5 * (TY - 1)) - dy - (y0 - 3));
+                        atomicOr(&s_fast, 1ull << k);
+                    }
+                }
             }
         }
         __syncthreads();
         [[maybe_unused]] const unsigned long long near = MOVING ? s_near : 0ull;
+        [[maybe_unused]] const unsigned long long fast = MOVING ? s_fast : 0ull;
+        // indicator of particle k at table cell (cx, cy), global cell (gx, gy)
+        [[maybe_unused]] auto pphi0 = [&](int k, int cx, int cy, int gx, int gy, R &rx, R &ry) -> R {
+            const ParticleDev &pp = A.parts[k];
+            if ((fast >> k) & 1ull)
+                return particle_phi0_rel<R>(R(cx) - s_pcx[k], R(cy) - s_pcy[k], (R)pp.R, (R)pp.R + (R)p.cut,
+                                            (R)p.D, rx, ry);
+            return particle_phi0<R, EXT>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+        };
 
         const ST *fs = reinterpret_cast<const ST *>(Dm.f[A.par]);
         ST *fd = reinterpret_cast<ST *>(Dm.f[A.par ^ 1]);
@@ -284,7 +324,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 for (int k = 0; k < A.np; ++k) {
                     if (!((near >> k) & 1ull)) continue;
                     R rx, ry;
-                    const R pk = particle_phi0<R, EXT>(A.parts[k], gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+                    const R pk = pphi0(k, cx, cy, gx, gy, rx, ry);
                     v += pk;
                     if (A.parts[k].own) {
                         const R ck = (R)A.parts[k].ct;
@@ -506,7 +546,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 if (!((near >> k) & 1ull)) continue;
                 const ParticleDev &pp = A.parts[k];
                 R rx, ry;
-                const R pk = particle_phi0<R, EXT>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+                const R pk = pphi0(k, lx + 3, ly + 3, gx, gy, rx, ry);
                 if (pk != R(0)) {
                     const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                     const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
@@ -672,31 +712,46 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                         if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;
                         continue;
                     }
-                    double c6[6] = {0, 0, 0, 0, 0, 0};
+                    // 2D: F_x, F_y and T_z (components 0, 1, 5); the others stay 0
+                    double c6[3] = {0, 0, 0};
+                    bool hit = false;
                     if (valid) {
                         R rx, ry;
-                        const R pk = particle_phi0<R, EXT>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
+                        const R pk = pphi0(k, lx + 3, ly + 3, gx, gy, rx, ry);
                         if (pk != R(0)) {
+                            hit = true;
                             const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
                             const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
                             const R fx = rho * pk * (usx_k - usx), fy = rho * pk * (usy_k - usy);
                             c6[0] = -(double)fx;
                             c6[1] = -(double)fy;
-                            c6[5] = -((double)rx * (double)fy - (double)ry * (double)fx);
+                            c6[2] = -((double)rx * (double)fy - (double)ry * (double)fx);
                         }
                     }
-                    // fixed-order block reduction: warp shuffle tree, then warps in order
+                    if (!__syncthreads_or(hit)) {
+                        // the indicator is 0 on every cell of the tile (it rounds to
+                        // 0 well inside the reach used for the tile test)
+                        if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;
+                        continue;
+                    }
+                    // fixed-order block reduction: warp shuffle tree (skipped by
+                    // warps whose terms are all 0), then warps in order
+                    const bool wany = __any_sync(0xffffffffu, hit);
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) {
+                    for (int c = 0; c < 3; ++c) {
                         double v = c6[c];
+                        if (wany) {
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                        }
                         if ((tid & 31) == 0) s_red[tid >> 5][c] = v;
                     }
                     __syncthreads();
                     if (tid < 6) {
                         double acc = 0.0;
-                        for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[wq][tid];
+                        const int c = tid == 5 ? 2 : tid;
+                        if (tid < 2 || tid == 5)
+                            for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[wq][c];
                         A.partials[((long long)t * A.np + k) * 6 + tid] = acc;
                     }
                     __syncthreads();

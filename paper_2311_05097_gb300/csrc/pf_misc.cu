@@ -529,10 +529,10 @@ __global__ void k_particle_update(ParticleDev *parts, int np, const double *part
         pp.x[c] += pp.u[c];
         pp.u_prev[c] = pp.u[c];
         pp.w_prev[c] = pp.w[c];
-        if (!pp.prescribed) {
-            pp.u[c] += a[c];
-            pp.w[c] += al[c];
-        }
+        // held components keep their value (bit 0: all; bits 1-3: translation
+        // along x, y, z; bit 4: rotation)
+        if (!(pp.prescribed & 1) && !(pp.prescribed & (2 << c))) pp.u[c] += a[c];
+        if (!(pp.prescribed & 1) && !(pp.prescribed & 16)) pp.w[c] += al[c];
     }
 }
 

@@ -211,21 +211,23 @@ class Sim:
     def set_particle(self, k, x, u=(0, 0, 0), w=(0, 0, 0), R=10.0, rho_p=1.0, theta_deg=None,
                      prescribed=False):
         """Add or overwrite particle k; theta_deg None keeps the handle's angle;
-        prescribed keeps the given u, w (e.g. a rotating cylinder)."""
+        prescribed: True keeps the given u, w (e.g. a rotating cylinder), or
+        the bit flags of held components (2, 4, 8: x, y, z translation;
+        16: rotation)."""
         pp = pf_particle()
         pp.x = (C.c_double * 3)(*(tuple(x) + (0.0,) * (3 - len(x))))
         pp.u = (C.c_double * 3)(*(tuple(u) + (0.0,) * (3 - len(u))))
         pp.w = (C.c_double * 3)(*(tuple(w) + (0.0,) * (3 - len(w))))
         pp.R, pp.rho_p = float(R), float(rho_p)
         pp.theta_deg = float("nan") if theta_deg is None else float(theta_deg)
-        pp.prescribed = 1 if prescribed else 0
+        pp.prescribed = int(prescribed)
         _check(load().pf_particle_state(self._h, int(k), C.byref(pp), 1))
 
     def particle(self, k):
         pp = pf_particle()
         _check(load().pf_particle_state(self._h, int(k), C.byref(pp), 0))
         return dict(x=list(pp.x), u=list(pp.u), w=list(pp.w), R=pp.R, rho_p=pp.rho_p,
-                    theta_deg=pp.theta_deg, prescribed=bool(pp.prescribed), F=list(pp.F), T=list(pp.T))
+                    theta_deg=pp.theta_deg, prescribed=int(pp.prescribed), F=list(pp.F), T=list(pp.T))
 
     def init(self, phi0, phi, u=None, P=None):
         where = PF_DEVICE if _is_device(phi) else PF_HOST

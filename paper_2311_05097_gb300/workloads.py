@@ -286,6 +286,28 @@ def particle_balance(L=256, Rp=32.0, theta_deg=90.0, rho_p=1.1, sigma=0.01, g=2e
                 rho_f=1.0, sigma=sigma, g=g, y_if=y_if, name="particle_balance_2d")
 
 
+def particle_pair_balance(L=256, Rp=16.0, delta=24.0, theta_deg=90.0, rho_p=1.25, sigma=0.01, g=2e-5,
+                          wall=8, D=3.0, M=0.1):
+    """Two equal discs half immersed at the flat interface of two fluids of
+    equal density, centres at L/2 -+ delta, in the box of ``particle_balance``
+    (Sec. 4.4 two-particle case: R_p = 16, D = 3; sigma and g scaled together
+    as there).  Each particle holds its horizontal translation and its
+    rotation (moves only vertically); gravity acts on the particles only."""
+    ny = L + 2 * wall
+    shape = (ny, L)
+    phi0 = slab_walls(shape, wall, D, axis=1)
+    y_if = ny / 2.0
+    parts = [dict(x=(L / 2.0 + s * delta, y_if, 0.0), u=(0.0, 0.0, 0.0), w=(0.0, 0.0, 0.0), R=Rp,
+                  rho_p=rho_p, prescribed=2 | 16) for s in (-1.0, 1.0)]
+    solid = phi0 + sum(disc(shape, q["x"], Rp, D) for q in parts)
+    y = _coords(shape)[1]
+    phi = (1.0 - solid) * np.tanh(2.0 * (y_if - y) / D)
+    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1, theta_deg=theta_deg,
+               g=(0.0, -g, 0.0))
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, particles=parts, L=L, Rp=Rp, delta=delta,
+                rho_f=1.0, sigma=sigma, g=g, y_if=y_if, wall=wall, name="particle_pair_balance_2d")
+
+
 def annulus_mixing(n=512, count=15, seed=4, D=5.0, omega=1e-4, g=1e-6, rep_xi=2.5, rep_eps=1e4):
     """Two fluid layers and ``count`` free wetting particles in the annulus
     between a fixed outer wall (radius n/2) and an inner cylinder (radius

@@ -285,3 +285,30 @@ def test_channel_displacement_runs(pf):
         assert De[0] < 0.05 and De[-1] > 0.3 and all(b > a for a, b in zip(De, De[1:])), (case, De)
         if parts:
             assert adv > 100.0 and gap > 0.0, (adv, gap)
+
+
+@pytest.mark.parametrize("delta", [24.0, 48.0])
+def test_particle_pair_balance(pf, delta):
+    """Two equal wetting discs at the interface, allowed to move only
+    vertically (Sec. 4.4 two-particle case, R_p = 16, Bo = 0.128): after
+    relaxation the depth h below the interface at the middle of the wide gap
+    and the horizontal force on the right particle (F_lat, the force that
+    holds it) match the closed form built from the printed balances."""
+    c = W.particle_pair_balance(delta=delta)
+    s = run(pf, c, 400000, "p32", particles=c["particles"])
+    parts = [s.particle(k) for k in range(2)]
+    m = s.macros()
+    L = c["L"]
+    # the middle of the wide gap is the periodic edge x = 0
+    y_if = A.interface_level(m["phi"], 0, c["wall"], c["shape"][0] - c["wall"])
+    h = y_if - 0.5 * (parts[0]["x"][1] + parts[1]["x"][1])
+    f_lat = 0.5 * (parts[1]["F"][0] - parts[0]["F"][0])  # outward force on each particle
+    Bo = CF.bond_number(c["particles"][0]["rho_p"], c["rho_f"], c["Rp"], c["g"], c["sigma"])
+    th = CF.particle_pair_balance(L, c["Rp"], 90.0, Bo, delta)
+    record("particle_pair_balance", delta=delta, Bo=Bo, h=h, h_closed_form=th["h"], F_lat=f_lat,
+           F_lat_closed_form=th["F_lat_over_sigma"] * c["sigma"], alpha=th["alpha"], beta=th["beta"],
+           x=[p["x"] for p in parts], u=[p["u"] for p in parts], F=[p["F"] for p in parts])
+    assert s.diagnostics()["nan_flag"] == 0
+    assert abs(parts[0]["x"][0] - (L / 2 - delta)) < 1e-9 and abs(parts[1]["x"][0] - (L / 2 + delta)) < 1e-9
+    assert abs(h - th["h"]) <= 0.15 * abs(th["h"]), (h, th["h"])
+    assert f_lat * th["F_lat_over_sigma"] > 0, (f_lat, th)

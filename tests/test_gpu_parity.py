@@ -639,3 +639,27 @@ def test_channel_displacement_full_size_against_oracle(pf):
         us = np.abs(po.u).max() + abs(po.w[2]) * R + 1e-4
         assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() <= 1e-12 * us, k
         assert np.abs(np.array(pg["w"]) - np.array(po.w)).max() <= 1e-12 * us / R, k
+
+
+def test_p64_held_components_match_oracle(pf):
+    """Particles that hold their horizontal translation and rotation (the
+    two-particle balance of Sec. 4.4) and one that holds only its vertical
+    translation, FP64 against the oracle after 60 steps."""
+    c = W.small_case((56, 64), seed=12, solid=False)
+    c["params"] = dict(c["params"], g=(0.0, -2e-5, 0.0))
+    parts = [dict(x=(18.0, 30.0), u=(0.002, 0.0), w=(0.0, 0.0, 0.001), R=6.0, rho_p=1.5, prescribed=2 | 16),
+             dict(x=(44.0, 28.0), u=(0.0, -0.001), R=6.0, rho_p=1.5, prescribed=4)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], c["params"]["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 60, particles=parts)
+    assert_fields(g.macros(), o.macros(), 1e-12)
+    for k in range(2):
+        pg, po = g.particle(k), o.particle(k)
+        for f in ("x", "u", "w", "F", "T"):
+            a, b = np.array(pg[f]), np.array(getattr(po, f))
+            assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, f, a, b)
+    p0, p1 = g.particle(0), g.particle(1)
+    assert p0["u"][0] == 0.002 and p0["w"][2] == 0.001 and p0["u"][1] != 0.0
+    assert p1["u"][1] == -0.001 and p1["u"][0] != 0.0

@@ -446,3 +446,45 @@ def test_particle_wall_repulsion():
     Fb = O.repulsion(2, pc, n, [b])[0]
     r = np.array([0.6, 0.8])
     assert Fb[:2] @ r < 0 and abs(Fb[0] * r[1] - Fb[1] * r[0]) < 1e-12 * np.abs(Fb).max()
+
+
+def test_particle_pair_balance_closed_form():
+    """Two particles at an interface (Sec. 4.4, two-particle case): the closed
+    form reduces to the single particle in a box of width L/2 when the gaps are
+    equal (and F_lat = 0 there), swapping the gaps flips F_lat, the printed
+    vertical balance sigma (sin a + sin b) + R_p dp (sin(theta - a) +
+    sin(theta - b)) = pi sigma Bo holds, and Bo -> 0 leaves a flat interface."""
+    L, R = 256.0, 16.0
+    for theta in (60.0, 90.0, 120.0):
+        for Bo in (0.05, 0.128, 0.3):
+            half = CF.particle_pair_balance(L, R, theta, Bo, L / 4)
+            h1, a1 = CF.particle_interface_height(L / 2, R, theta, Bo)
+            assert abs(half["h"] - h1) < 1e-9 and abs(half["alpha"] - a1) < 1e-12
+            assert abs(half["F_lat_over_sigma"]) < 1e-14
+            for d in (24.0, 40.0, 52.0):
+                r = CF.particle_pair_balance(L, R, theta, Bo, d)
+                s = CF.particle_pair_balance(L, R, theta, Bo, L / 2 - d)
+                assert abs(r["F_lat_over_sigma"] + s["F_lat_over_sigma"]) < 1e-12
+                th = math.radians(theta)
+                vert = (math.sin(r["alpha"]) + math.sin(r["beta"])
+                        + R / r["Rc"] * (math.sin(th - r["alpha"]) + math.sin(th - r["beta"])))
+                assert abs(vert - math.pi * Bo) < 1e-12 * max(1.0, math.pi * Bo)
+            # the narrow gap attracts (capillary attraction of like particles)
+            assert CF.particle_pair_balance(L, R, theta, Bo, 24.0)["F_lat_over_sigma"] < 0
+    r = CF.particle_pair_balance(L, R, 70.0, 1e-9, 30.0)
+    assert abs(r["h"] - R * math.cos(math.radians(70.0))) < 1e-5 and abs(r["F_lat_over_sigma"]) < 1e-8
+
+
+def test_held_particle_components():
+    """Reading R25: held components of a particle's motion keep their value
+    under a force and torque, the free ones follow Newton-Euler."""
+    p = O.make_params(g=(0.0, -1e-5, 0.0))
+    base = O.Particle((10.0, 10.0), u=(0.01, 0.0, 0.0), w=(0.0, 0.0, 0.002), R=5.0, rho_p=2.0)
+    free = O.particle_update(2, p, base, (1e-3, 2e-3, 0.0), (0.0, 0.0, 1e-3))
+    held = O.particle_update(2, p, O.Particle((10.0, 10.0), u=(0.01, 0.0, 0.0), w=(0.0, 0.0, 0.002), R=5.0,
+                                              rho_p=2.0, prescribed=2 | 16),
+                             (1e-3, 2e-3, 0.0), (0.0, 0.0, 1e-3))
+    assert held.u[0] == 0.01 and held.w[2] == 0.002
+    assert held.u[1] == free.u[1] != 0.0
+    assert free.u[0] != 0.01 and free.w[2] != 0.002
+    assert held.x[0] == free.x[0] == 10.01
