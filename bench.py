@@ -59,29 +59,63 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "drop_on_cylinder", "static_drop", "water_entry",
-                             "drainage_3d", "annulus", "porous_2d", "channel"])
+                             "drainage_3d", "annulus", "porous_2d", "channel", "drops"])
     ap.add_argument("--n3d", type=int, default=256, help="cube side of drainage_3d")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--config", type=int, nargs=4, default=None,
                     metavar=("TILE_X", "TILE_Y", "CELLS_PER_THREAD", "CTAS_PER_SM"),
                     help="fix the batch launch configuration instead of autotuning it")
+    ap.add_argument("--phase-model", type=int, default=0, choices=[0, 1],
+                    help="order parameter: 0 Cahn-Hilliard (the paper's), 1 conservative Allen-Cahn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def batch_workload(count=256):
+def with_phase_model(c, phase_model):
+    """The workload with the order-parameter lattice chosen (0: Cahn-Hilliard,
+    1: conservative Allen-Cahn)."""
+    if phase_model:
+        c["params"] = dict(c["params"], phase_model=phase_model)
+        if "desc" in c:
+            c["desc"] += "; conservative Allen-Cahn order parameter"
+    return c
+
+
+def batch_workload(count=256, phase_model=0):
     from paper_2311_05097_gb300 import workloads as W
     draws = W.batch_cases(count, seed=1)
-    cases = [W.flat_wall_drop(d["L"], d["theta_deg"], d["rho_ratio"]) for d in draws]
+    cases = [with_phase_model(W.flat_wall_drop(d["L"], d["theta_deg"], d["rho_ratio"]), phase_model)
+             for d in draws]
     return dict(cases=cases, draws=draws, precision="fp16",
                 desc="%d independent 2D drop-on-flat-wall domains, sides uniform over "
                      "{64,128,256,512}, theta U[30,150] deg, density ratio log-U[1,100], "
-                     "seed 1" % count)
+                     "seed 1%s" % (count, "; conservative Allen-Cahn order parameter" if phase_model else ""))
 
 
-def single_workload(name, n3d=256):
+def batch_like(args):
+    """The batched workload named by --workload (batch or drops)."""
+    if args.workload == "drops":
+        return drops_workload(args.batch_count, args.phase_model)
+    return batch_workload(args.batch_count, args.phase_model)
+
+
+def drops_workload(count=256, phase_model=0):
+    from paper_2311_05097_gb300 import workloads as W
+    draws = W.batch_cases(count, seed=1)
+    cases = [with_phase_model(W.periodic_drop(d["L"], d["rho_ratio"]), phase_model) for d in draws]
+    return dict(cases=cases, draws=draws, precision="fp16",
+                desc="%d independent 2D periodic drop domains (radius L/4, no solid), sides uniform over "
+                     "{64,128,256,512}, density ratio log-U[1,100], seed 1%s"
+                     % (count, "; conservative Allen-Cahn order parameter" if phase_model else ""))
+
+
+def single_workload(name, n3d=256, phase_model=0):
+    return with_phase_model(_single_workload(name, n3d), phase_model)
+
+
+def _single_workload(name, n3d=256):
     from paper_2311_05097_gb300 import workloads as W
     if name == "water_entry":
         c = W.water_entry()
@@ -203,12 +237,13 @@ def read_traffic(key, config=None):
     configuration than the one timed."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        ent = json.load(open(path)).get(key, {})
+        ents = json.load(open(path)).get(key, [])
     except Exception:
         return None
-    if config is not None and ent.get("config") is not None and list(ent["config"]) != list(config):
-        return None
-    return ent.get("bytes_per_launch")
+    for ent in ents if isinstance(ents, list) else [ents]:
+        if config is None or ent.get("config") is None or list(ent["config"]) == list(config):
+            return ent.get("bytes_per_launch")
+    return None
 
 
 # ---------------------------------------------------------------------------------------------
@@ -219,10 +254,10 @@ def oracle_sample(args, budget_s):
     Batch: whole domains taken in order from the batch list.  Returns
     (MLUPS, description, threads)."""
     from oracle import oracle as O
-    if args.workload == "batch":
-        cases = batch_workload(args.batch_count)["cases"]
+    if args.workload in ("batch", "drops"):
+        cases = batch_like(args)["cases"]
     else:
-        cases = [single_workload(args.workload, args.n3d)]
+        cases = [single_workload(args.workload, args.n3d, args.phase_model)]
     cells = 0
     t_total = 0.0
     used = []
@@ -255,13 +290,13 @@ def run_reference(args):
         return
     budget = min(120.0, max(10.0, 1.0 * args.steps))
     v, desc, cores = oracle_sample(args, budget)
-    if args.workload == "batch":
-        bw = batch_workload(args.batch_count)
+    if args.workload in ("batch", "drops"):
+        bw = batch_like(args)
         cells = sum(int(math.prod(c["shape"])) for c in bw["cases"])
-        cfg = {"workload": "batch", "domains": len(bw["cases"]), "cells": cells,
+        cfg = {"workload": args.workload, "domains": len(bw["cases"]), "cells": cells,
                "precision": "p64 (oracle)", "desc": bw["desc"]}
     else:
-        c = single_workload(args.workload, args.n3d)
+        c = single_workload(args.workload, args.n3d, args.phase_model)
         cells = int(math.prod(c["shape"]))
         cfg = {"workload": args.workload, "cells": cells, "precision": "p64 (oracle)",
                "desc": c["desc"]}
@@ -270,7 +305,7 @@ def run_reference(args):
             "ms_per_step": round(cells / (v * 1e6) * 1e3, 3) if v > 0 else None,
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": cfg,
+            "config": dict(cfg, order_parameter="allen-cahn" if args.phase_model else "cahn-hilliard"),
             "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS", "cores": cores,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -318,7 +353,7 @@ def run_batch(args, dist, rank, world, local):
     import torch
     from paper_2311_05097_gb300 import pf
 
-    bw = batch_workload(args.batch_count)
+    bw = batch_like(args)
     cases = bw["cases"]
     prec = args.precision or bw["precision"]
     cells = sum(int(math.prod(c["shape"])) for c in cases)
@@ -391,7 +426,7 @@ def run_batch(args, dist, rank, world, local):
                        "configuration is not cached); pf_batch_get_macros(phi) of every domain "
                        "to pinned host; wall clock" % S}
     b.close()
-    cfg = {"workload": "batch", "domains": len(cases), "cells": cells, "precision": prec,
+    cfg = {"workload": args.workload, "domains": len(cases), "cells": cells, "precision": prec,
            "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"
                                    % (cells * bpc / 1e9),
            "tile": [tx, ty], "ctas_per_sm": cps, "cells_per_thread": cpt,
@@ -408,7 +443,7 @@ def run_single(args, dist, rank, world, local):
     import torch
     from paper_2311_05097_gb300 import pf
 
-    case = single_workload(args.workload, args.n3d)
+    case = single_workload(args.workload, args.n3d, args.phase_model)
     prec = args.precision or case["precision"]
     cells = int(math.prod(case["shape"]))
     dim = len(case["shape"])
@@ -608,7 +643,8 @@ def roofline_entry(args, r, peak, peak_src):
                 "hbm_frac": round(r["achieved"] / peak, 4)}
     return {"bound": "hbm", "achieved": round(r["achieved"], 1), "peak": peak,
             "unit": "GB/s", "frac": round(r["achieved"] / peak, 4),
-            "traffic": read_traffic("%s/%s" % (args.workload, r["prec"]), r.get("launch_config")),
+            "traffic": read_traffic("%s/%s%s" % (args.workload, r["prec"], "/allen-cahn" if args.phase_model else ""),
+                                    r.get("launch_config")),
             "bytes_per_cell": r["bpc"], "kernel": r["kernel"], "peak_source": peak_src}
 
 
@@ -619,7 +655,7 @@ def run_ours(args):
         B.build()
     if dist:
         dist.barrier()
-    if args.workload == "batch":
+    if args.workload in ("batch", "drops"):
         r = run_batch(args, dist, rank, world, local)
     else:
         r = run_single(args, dist, rank, world, local)
@@ -641,7 +677,8 @@ def run_ours(args):
         "metric": "MLUPS", "value": round(r["mlups"], 2), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": DTYPE[r["prec"]], "data": "synthetic", "config": r["cfg"],
+        "dtype": DTYPE[r["prec"]], "data": "synthetic",
+        "config": dict(r["cfg"], order_parameter="allen-cahn" if args.phase_model else "cahn-hilliard"),
         "roofline": roofline_entry(args, r, peak, peak_src),
         "clocks": r["clk"], "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
         "wall_s": round(r["t_wall"], 3),

@@ -111,8 +111,8 @@ typedef struct pf_params {
                               by the particle-wall repulsion (the fluid sees
                               walls through phi0); radius 0: none */
     int phase_model;   /* 0 (default): the Cahn-Hilliard order parameter of
-                          Eq. 2 on the lattice of Eq. 30.  1 (in 2D on the
-                          single-cell kernel only): a conservative Allen-Cahn order
+                          Eq. 2 on the lattice of Eq. 30.  1 (2D kernels 0 and 1,
+                          and 3D): a conservative Allen-Cahn order
                           parameter, d_t phi + div(phi u) =
                           div(M (grad phi - theta n)), theta = (2/D)(1 - phi^2),
                           n = grad phi/|grad phi|, on the same lattice

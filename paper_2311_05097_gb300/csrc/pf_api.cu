@@ -550,19 +550,33 @@ static int engine_tiles(Engine &E, int tx, int ty)
     return PF_OK;
 }
 
-// domains only the single-cell kernel handles: walls at the ends of y, or the
-// Allen-Cahn order parameter
+// domains only the single-cell kernel handles: walls at the ends of y
 static bool any_walls(const Engine &E)
 {
     for (auto &m : E.mem)
-        if (m.d.wall_y || m.d.p.phase_model == 1) return true;
+        if (m.d.wall_y) return true;
     return false;
+}
+
+// domains with the Allen-Cahn order parameter
+static bool any_cac(const Engine &E)
+{
+    for (auto &m : E.mem)
+        if (m.d.p.phase_model == 1) return true;
+    return false;
+}
+
+// the instantiation flags of a 2D launch
+static int mode_flags(const Engine &E)
+{
+    const bool w = any_walls(E), c = any_cac(E);
+    return (w || c ? MODE_EXT : 0) | (c ? MODE_CAC : 0);
 }
 
 static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
 {
     if (E.dim == 3) return launch_step3d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
-    return launch_step2d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0), grid, E.stream, a);
+    return launch_step2d(E.prec, tx, ty, E.np > 0, mode | mode_flags(E), grid, E.stream, a);
 }
 
 static int step_mode(const Engine &E)
@@ -574,7 +588,7 @@ static int step_mode(const Engine &E)
 // rows' chunks and periodic splits aligned
 static bool stage_ok(const Engine &E)
 {
-    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0 || any_walls(E)) return false;
+    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0 || any_walls(E) || any_cac(E)) return false;
     const int q = E.prec == PF_P32 ? 4 : 8;
     for (auto &m : E.mem)
         if (m.d.nx % q) return false;
@@ -584,7 +598,7 @@ static bool stage_ok(const Engine &E)
 static int occupancy_any(const Engine &E, int tx, int ty, int mode)
 {
     if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode);
-    return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0));
+    return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode | mode_flags(E));
 }
 
 static StepArgs step_args(const Engine &E, int par)
@@ -1202,7 +1216,7 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
     if (var < 0 || var > 2) return fail(PF_EINVAL, "kernel must be 0, 1 or 2");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
     if (var != 0 && any_walls(E))
-        return fail(PF_EINVAL, "domains with walls or the Allen-Cahn order parameter run kernel 0 only");
+        return fail(PF_EINVAL, "domains with walls run kernel 0 only");
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);

@@ -27,6 +27,9 @@ enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2, MODE_STEP_STAGE 
 // or'ed into a 2D mode: the launch holds a domain with walls or the Allen-Cahn
 // order parameter (the single-cell kernel's instantiation that handles them)
 constexpr int MODE_EXT = 16;
+// or'ed into a 2D mode: the launch holds an Allen-Cahn domain (the
+// two-cells-per-thread kernels' instantiation that handles it)
+constexpr int MODE_CAC = 32;
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {

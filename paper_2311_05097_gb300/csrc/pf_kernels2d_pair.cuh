@@ -173,7 +173,9 @@ __device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*
 // from the shared tiles (phi, phi0 on tile + 2 at (hx, hy); mu, w on tile + 1
 // at (wx, wy)) and the values gathered in stage A, then their stores.  racc:
 // PMIX, each cell's exact fixed-point phi (rest + images of the pulled movers).
-template <class P, int FX, int WX>
+// CAC: the instantiation also serves domains with the conservative Allen-Cahn
+// order parameter (checked per domain)
+template <class P, int FX, int WX, bool CAC = false>
 __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p, const KParams<float> &kp,
                                            const float (*s_phi)[FX], const float (*s_p0)[FX],
                                            const float (*s_mu)[WX], const float (*s_w)[WX], int hx, int hy,
@@ -196,7 +198,20 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     const F2 rho = fma2(drho, phi, mk2(kp.rhom));
     const F2 muv = fma2(mk2(kp.dmu), phi, mk2(kp.mum));
     const F2 Mdrho = mk2(kp.Mdrho);
-    const F2 Sx = Mdrho * gmx, Sy = Mdrho * gmy;
+    // conservative Allen-Cahn option: theta n = (2/D)(1 - phi^2) grad phi/|grad phi|
+    // and the mass flux M (rho1 - rho2)/2 (grad phi - theta n)
+    const bool cac = CAC && p.phase_model == 1;
+    F2 tnx = mk2(0.0f), tny = mk2(0.0f);
+    if (cac) {
+        const F2 g2 = fma2(gpx, gpx, gpy * gpy);
+        const F2 th = mk2(kp.two_over_D) * (one - phi * phi);
+        const F2 inv = mk2(g2.v.x > 1e-24f ? 1.0f / sqrtf(g2.v.x) : 0.0f,
+                           g2.v.y > 1e-24f ? 1.0f / sqrtf(g2.v.y) : 0.0f);
+        tnx = th * gpx * inv;
+        tny = th * gpy * inv;
+    }
+    const F2 Sx = cac ? Mdrho * (gpx - tnx) : Mdrho * gmx;
+    const F2 Sy = cac ? Mdrho * (gpy - tny) : Mdrho * gmy;
     const F2 grx = drho * gpx, gry = drho * gpy;
     // F = mu grad phi + F_b + F_c, F_c = (-d_y w, d_x w)/2 from the previous step
     const F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
@@ -248,7 +263,7 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     F2 heq[9], hF[9], nS[9], cF[9];
     // ---- order-parameter lattice (Eq. 30): Hermite equilibria and source
     {
-        const F2 eta_mu = mk2(kp.eta) * mu;
+        const F2 eta_mu = cac ? phi : mk2(kp.eta) * mu;  // Allen-Cahn: eta mu -> phi
         heq[0] = phi;
         heq[1] = phi * ux;
         heq[2] = phi * uy;
@@ -257,6 +272,10 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
         heq[8] = cs4 * (phi - eta_mu);
         hF[1] = heq[1] - php * upx;  // d_t(phi u), explicit Euler
         hF[2] = heq[2] - php * upy;
+        if (cac) {
+            hF[1] = fma2(cs2, tnx, hF[1]);
+            hF[2] = fma2(cs2, tny, hF[2]);
+        }
         const float s[9] = {kp.s0, kp.s1phi, kp.s1phi, kp.s2, kp.s2, kp.s2, kp.s3, kp.s3, kp.s4};
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -345,7 +364,7 @@ constexpr int step2d_pair_min_blocks()
     return TX * TYP > 256 ? 1 : 2;
 }
 
-template <class P, int TX, int TYP>
+template <class P, int TX, int TYP, bool CAC>
 __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) k_step2d_pair(StepArgs A)
 {
     using ST = typename P::store;
@@ -518,7 +537,7 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
         {
             const int gx = x0 + lx, gy0 = y0 + ly0;
             const bool valid0 = gx < nx && gy0 < ny, valid1 = gx < nx && gy0 + 1 < ny;
-            pair_cells<P, FX, WX>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, racc,
+            pair_cells<P, FX, WX, CAC>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, racc,
                                   id, valid0, valid1, fd, rd, ad, plane);
         }
     }

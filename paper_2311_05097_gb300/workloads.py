@@ -451,6 +451,17 @@ def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2
                 wall=wall)
 
 
+def periodic_drop(L, rho_ratio, D=4.0, sigma=0.01, M=0.1, mu1=0.1, s0=1.6):
+    """A drop of radius L/4 at the centre of an L x L periodic box without
+    solids (mu2 as in ``flat_wall_drop``): a batch domain for either
+    order-parameter lattice."""
+    shape = (L, L)
+    phi = drop_field(shape, ((L - 1) / 2.0, (L - 1) / 2.0), 0.25 * L, D)
+    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0 / rho_ratio, mu1=mu1,
+               mu2=mu1 * rho_ratio ** (-2.0 / 3.0), s0=s0)
+    return dict(shape=shape, phi0=np.zeros(shape), phi=phi, params=p)
+
+
 def batch_cases(count=256, seed=1, sizes=(64, 128, 256, 512), max_ratio=100.0):
     """Parameter draws of the batched sweep: box side uniform over ``sizes``,
     contact angle uniform in [30, 150] deg, density ratio log-uniform in
