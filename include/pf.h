@@ -66,12 +66,12 @@ extern "C" {
 #define PF_DEVICE 1
 
 /* Grid: dim = 2 or 3; nz is ignored (1) in 2D.  periodic[a] = 1: periodic
- * along axis a.  2D only: periodic[1] = 0 puts no-flux walls at y = -1/2 and
- * y = ny - 1/2 (the paper's box walls): halfway bounce-back of both lattices
- * at resting walls, and the finite-difference stencils see mirror images of
- * the rows inside (zero normal gradient of phi, mu and phi0).  Walls run the
- * one-cell-per-thread step (kernel 0).  Solid walls of any shape can also be
- * given through the smooth indicator phi0. */
+ * along axis a.  periodic[1] = 0 (2D or 3D) puts no-flux walls at y = -1/2
+ * and y = ny - 1/2 (the paper's box walls): halfway bounce-back of both
+ * lattices at resting walls, and the finite-difference stencils see mirror
+ * images of the rows inside (zero normal gradient of phi, mu and phi0).  In
+ * 2D walls run the one-cell-per-thread step (kernel 0).  Solid walls of any
+ * shape can also be given through the smooth indicator phi0. */
 typedef struct pf_grid {
     int dim;
     int nx, ny, nz;

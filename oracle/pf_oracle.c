@@ -54,7 +54,7 @@
  *       (R_k + R_j + xi - d)^2 for R_k + R_j <= d <= R_k + R_j + xi, times
  *       (R_k + R_j - d) for d <= R_k + R_j, zero beyond (minimum image), added to
  *       the force of Eq. (26a) from the positions before the update.
- *   R21 box walls (2D, y = -1/2 and y = ny - 1/2; the paper's no-flux boxes):
+ *   R21 box walls (y = -1/2 and y = ny - 1/2, 2D and 3D; the paper's no-flux boxes):
  *       halfway bounce-back of both lattices at resting walls; the stencils read
  *       rows beyond a wall as the mirror image of the rows inside (zero normal
  *       gradient of phi, mu and phi0: no flux), except the products
@@ -640,7 +640,7 @@ void orc_repulsion(int dim, const orc_params *p, const int *n, int wall_y, int n
         /* the wall: x_k - x'_k towards the nearest imaginary particle, the
          * mirror image of particle k across the nearest wall */
         double best = INFINITY, dw[3] = {0.0, 0.0, 0.0};
-        if (wall_y && dim == 2) {
+        if (wall_y) {
             const double y = parts[k].x[1];
             const double d_lo = 2.0 * (y + 0.5), d_hi = 2.0 * (n[1] - 0.5 - y);
             if (d_lo < best) {
@@ -1321,7 +1321,6 @@ int orc_num_particles(orc_sim *s) { return s->np; }
 
 int orc_set_walls(orc_sim *s, int wall_y)
 {
-    if (wall_y && s->dim != 2) return -1;
     s->wall_y = wall_y ? 1 : 0;
     return 0;
 }

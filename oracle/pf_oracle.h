@@ -81,7 +81,7 @@ void orc_get_f(orc_sim *s, double *f1, double *f2);
 int orc_set_particle(orc_sim *s, int k, const orc_particle *pp);
 int orc_get_particle(orc_sim *s, int k, orc_particle *pp);
 int orc_num_particles(orc_sim *s);
-/* Reading R21: walls at y = -1/2 and y = ny - 1/2 (2D; before init). */
+/* Reading R21: walls at y = -1/2 and y = ny - 1/2 (2D and 3D; before init). */
 int orc_set_walls(orc_sim *s, int wall_y);
 /* The total solid indicator phi0 at the current time. */
 void orc_get_phi0(orc_sim *s, double *phi0);

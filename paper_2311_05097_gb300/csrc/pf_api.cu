@@ -158,9 +158,9 @@ static int validate(const pf_grid *g, const pf_params *p)
         return fail(PF_EINVAL, "grid too large: %lld populations x %lld cells must stay below 2^31 "
                     "(32-bit indexing of the state arrays)", qtot, pitch * g->ny * nz);
     for (int a = 0; a < g->dim; ++a) {
-        const bool wall_ok = g->dim == 2 && a == 1 && g->periodic[a] == 0;
+        const bool wall_ok = a == 1 && g->periodic[a] == 0;
         if (g->periodic[a] != 1 && !wall_ok)
-            return fail(PF_EINVAL, "boundaries must be periodic, except walls at the ends of y in 2D "
+            return fail(PF_EINVAL, "boundaries must be periodic, except walls at the ends of y "
                                    "(periodic[1] = 0)");
     }
     if (!finite_all(p)) return fail(PF_EINVAL, "non-finite parameter");
@@ -307,7 +307,7 @@ static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams
     d.nx = g->nx;
     d.ny = g->ny;
     d.nz = dim == 2 ? 1 : g->nz;
-    d.wall_y = dim == 2 && g->periodic[1] == 0 ? 1 : 0;
+    d.wall_y = g->periodic[1] == 0 ? 1 : 0;
     d.pitch = (int)round_up(d.nx, 32);
     d.plane = round_up((long long)d.pitch * d.ny * d.nz, 64);
     d.p = dp;
@@ -575,7 +575,8 @@ static int mode_flags(const Engine &E)
 
 static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
 {
-    if (E.dim == 3) return launch_step3d(E.prec, tx, ty, E.np > 0, mode, grid, E.stream, a);
+    if (E.dim == 3)
+        return launch_step3d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0), grid, E.stream, a);
     return launch_step2d(E.prec, tx, ty, E.np > 0, mode | mode_flags(E), grid, E.stream, a);
 }
 
@@ -597,7 +598,7 @@ static bool stage_ok(const Engine &E)
 
 static int occupancy_any(const Engine &E, int tx, int ty, int mode)
 {
-    if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode);
+    if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0));
     return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode | mode_flags(E));
 }
 

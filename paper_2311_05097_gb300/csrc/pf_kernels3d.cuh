@@ -20,6 +20,8 @@ namespace pf {
 __device__ constexpr int C19X[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __device__ constexpr int C19Y[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __device__ constexpr int C19Z[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+// opposite direction (pairs 1-2, 3-4, ..., 17-18)
+__device__ __forceinline__ int opp19(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
 // Hermite-moment MRT collision of one D3Q19 cell.  Raw moments m = M0 f with
 // rows 1, c_a, c_a^2, c_x c_y, c_x c_z, c_y c_z, c_x c_y^2, c_x c_z^2,
@@ -183,7 +185,7 @@ __device__ __forceinline__ R particle_phi0_3d(const ParticleDev &pp, int gx, int
 {
     double dx = (double)gx - pp.x[0], dy = (double)gy - pp.x[1], dz = (double)gz - pp.x[2];
     dx -= nx * rint(dx / nx);
-    dy -= ny * rint(dy / ny);
+    if (ny > 0) dy -= ny * rint(dy / ny);  // ny <= 0: walls in y, no minimum image
     dz -= nz * rint(dz / nz);
     rx = (R)dx;
     ry = (R)dy;
@@ -195,7 +197,8 @@ __device__ __forceinline__ R particle_phi0_3d(const ParticleDev &pp, int gx, int
     return R(0.5) * (R(1) + tanh(R(2) * ((R)pp.R - r) / (R)D));
 }
 
-template <class P, int TX, int TY, int ZC, bool MOVING, int MODE>
+// EXT: the instantiation also handles domains with walls at the ends of y
+template <class P, int TX, int TY, int ZC, bool MOVING, int MODE, bool EXT>
 __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
 {
     using R = typename P::real;
@@ -211,6 +214,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
     __shared__ int s_gx[TX + 6];
     __shared__ int s_gy[TY + 6];   // wrapped row offsets y * pitch
     __shared__ int s_gyi[TY + 6];  // wrapped rows
+    __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
     __shared__ double s_red[NT / 32][6];
 
     const int tid = threadIdx.x;
@@ -229,13 +233,39 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         const KParams<R> &kp = kparams<R>(Dm);
 
         __syncthreads();
+        const int wall = EXT ? Dm.wall_y : 0;
+        const int nyw = wall ? 0 : ny;  // minimum image in y only without walls
         for (int k = tid; k < TX + 6; k += NT) s_gx[k] = wrap_idx(x0 - 3 + k, nx);
         for (int k = tid; k < TY + 6; k += NT) {
-            const int yy = wrap_idx(y0 - 3 + k, ny);
-            s_gyi[k] = yy;
-            s_gy[k] = yy * Dm.pitch;
+            if constexpr (EXT) {
+                const int y = y0 - 3 + k;
+                int yy, out = 0;
+                if (wall) {
+                    // rows beyond a wall read their mirror image (clamped: the
+                    // rows that far out only feed cells beyond the domain)
+                    yy = y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y);
+                    out = y < 0 || y >= ny;
+                    yy = min(max(yy, 0), ny - 1);
+                } else {
+                    yy = wrap_idx(y, ny);
+                }
+                s_gyi[k] = yy;
+                s_gy[k] = yy * Dm.pitch;
+                s_out[k] = out;
+            } else {
+                const int yy = wrap_idx(y0 - 3 + k, ny);
+                s_gyi[k] = yy;
+                s_gy[k] = yy * Dm.pitch;
+            }
         }
         __syncthreads();
+        // a tile whose frames reach beyond a wall
+        const bool wall_tile = EXT && wall && (y0 - 3 < 0 || y0 + TY + 3 > ny);
+        // sign of the y-odd products T_xy, T_yz at table row r under a wall mirror
+        auto wsign = [&](int r) -> R {
+            if constexpr (EXT) return s_out[r] ? R(-1) : R(1);
+            return R(1);
+        };
 
         const ST *fs = reinterpret_cast<const ST *>(Dm.f[A.par]);
         ST *fd = reinterpret_cast<ST *>(Dm.f[A.par ^ 1]);
@@ -254,6 +284,17 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
         auto cidx = [&](int tx_, int ty_, int zo) {  // tile+3 table coordinates
             return zo + s_gy[ty_] + s_gx[tx_];
         };
+        // offset of the population that table cell (cx, cy) of plane z pulls as
+        // direction i of the lattice starting at plane `base`: from cell - c_i,
+        // or, where that lies beyond a wall, its own opposite population
+        // (halfway bounce-back)
+        auto pull = [&](int base, int i, int cx, int cy, int z) -> int {
+            if constexpr (EXT) {
+                if (wall_tile && s_out[cy - C19Y[i]] && !s_out[cy])
+                    return (base + opp19(i)) * plane + cidx(cx, cy, zoff(z));
+            }
+            return base * plane + i * plane + cidx(cx - C19X[i], cy - C19Y[i], zoff(z - C19Z[i]));
+        };
         // phi at (frame x, frame y) of plane z: pull and sum the D3Q7 populations
         auto phi_at = [&](int hx, int hy, int z, R *keep, ST *keepq) -> R {
             const int cx = hx + 1, cy = hy + 1;
@@ -263,7 +304,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                 if (keep) keep[0] = acc;
 #pragma unroll
                 for (int i = 1; i < 7; ++i) {
-                    const ST qv = ldg(fs + i * plane + cidx(cx - C19X[i], cy - C19Y[i], zoff(z - C19Z[i])));
+                    const ST qv = ldg(fs + pull(0, i, cx, cy, z));
                     const R v = Conv<P>::ld(qv, isc1);
                     if (keep) keep[i] = v;
                     if (keepq) keepq[i] = qv;
@@ -273,8 +314,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                 acc = R(0);
 #pragma unroll
                 for (int i = 0; i < 7; ++i) {
-                    const R v = Conv<P>::ld(
-                        ldg(fs + i * plane + cidx(cx - C19X[i], cy - C19Y[i], zoff(z - C19Z[i]))), isc1);
+                    const R v = Conv<P>::ld(ldg(fs + pull(0, i, cx, cy, z)), isc1);
                     if (keep) keep[i] = v;
                     acc += v;
                 }
@@ -288,7 +328,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                 const int gx = s_gx[cx], gy = s_gyi[cy], gz = wrap_near(z, nz);
                 for (int k = 0; k < A.np; ++k) {
                     R rx, ry, rz;
-                    v += particle_phi0_3d<R>(A.parts[k], gx, gy, gz, nx, ny, nz, p.D, p.cut, rx, ry, rz);
+                    v += particle_phi0_3d<R>(A.parts[k], gx, gy, gz, nx, nyw, nz, p.D, p.cut, rx, ry, rz);
                 }
             }
             return v;
@@ -311,9 +351,10 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                         uz = (R)ldg(as + 2 * plane + id);
                 const R Sx = (R)ldg(as + 3 * plane + id), Sy = (R)ldg(as + 4 * plane + id),
                         Sz = (R)ldg(as + 5 * plane + id);
-                s_T[slot][0][r] = Sx * uy - ux * Sy;
+                const R sg = wsign(wy + 2);  // T_xy and T_yz are odd under the wall mirror
+                s_T[slot][0][r] = sg * (Sx * uy - ux * Sy);
                 s_T[slot][1][r] = Sx * uz - ux * Sz;
-                s_T[slot][2][r] = Sy * uz - uy * Sz;
+                s_T[slot][2][r] = sg * (Sy * uz - uy * Sz);
             }
         };
         auto mu_plane = [&](int z) {
@@ -329,6 +370,21 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             }
         };
 
+        // walls: phi beyond a wall is the mirror image of phi inside (no flux);
+        // refills the rows of plane z's slot beyond the wall (after a barrier)
+        auto mirror_phi_plane = [&](int z) {
+            if constexpr (EXT) {
+                const int slot = wrap_idx(z, 5);
+                for (int r = tid; r < FP; r += NT) {
+                    const int hx = r % FX, hy = r / FX;
+                    if (!s_out[hy + 1]) continue;
+                    const int y = y0 - 2 + hy;
+                    const int hym = (y < 0 ? -1 - y : 2 * ny - 1 - y) - (y0 - 2);
+                    if (hym >= 0 && hym < FY && !s_out[hym + 1]) s_phi[slot][r] = s_phi[slot][hym * FX + hx];
+                }
+            }
+        };
+
         // prologue: phi planes z0-2 .. z0+1, T planes z0-1, z0, mu planes z0-1, z0
         for (int z = z0 - 2; z <= z0 + 1; ++z) load_phi_plane(z);
         if constexpr (MODE == MODE_STEP) {
@@ -336,6 +392,10 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             load_T_plane(z0);
         }
         __syncthreads();
+        if (wall_tile) {
+            for (int z = z0 - 2; z <= z0 + 1; ++z) mirror_phi_plane(z);
+            __syncthreads();
+        }
         mu_plane(z0 - 1);
         mu_plane(z0);
         __syncthreads();
@@ -346,6 +406,10 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             load_phi_plane(z + 2);
             if constexpr (MODE == MODE_STEP) load_T_plane(z + 1);
             __syncthreads();
+            if (wall_tile) {
+                mirror_phi_plane(z + 2);
+                __syncthreads();
+            }
             // phase 2: mu plane z+1
             mu_plane(z + 1);
             __syncthreads();
@@ -421,9 +485,10 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                                     uz = (R)ldg(as + 2 * plane + nid);
                             const R sx = (R)ldg(as + 3 * plane + nid), sy = (R)ldg(as + 4 * plane + nid),
                                     sz = (R)ldg(as + 5 * plane + nid);
-                            T[0][dz + 1][dy + 1][dx + 1] = sx * uy - ux * sy;
+                            const R sg = wsign(ly + 3 + dy);
+                            T[0][dz + 1][dy + 1][dx + 1] = sg * (sx * uy - ux * sy);
                             T[1][dz + 1][dy + 1][dx + 1] = sx * uz - ux * sz;
-                            T[2][dz + 1][dy + 1][dx + 1] = sy * uz - uy * sz;
+                            T[2][dz + 1][dy + 1][dx + 1] = sg * (sy * uz - uy * sz);
                         }
                 R g[3][3];
 #pragma unroll
@@ -448,8 +513,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             R f2[19];
 #pragma unroll
             for (int i = 0; i < 19; ++i)
-                f2[i] = Conv<P>::ld(
-                    ldg(fs + (7 + i) * plane + cidx(lx + 3 - C19X[i], ly + 3 - C19Y[i], zoff(z - C19Z[i]))), isc2);
+                f2[i] = Conv<P>::ld(ldg(fs + pull(7, i, lx + 3, ly + 3, z)), isc2);
             R jx = R(0), jy = R(0), jz = R(0), sum_f = R(0);
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
@@ -466,7 +530,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                 for (int k = 0; k < A.np; ++k) {
                     const ParticleDev &pp = A.parts[k];
                     R rx, ry, rz;
-                    const R pk = particle_phi0_3d<R>(pp, gx, gy, z, nx, ny, nz, p.D, p.cut, rx, ry, rz);
+                    const R pk = particle_phi0_3d<R>(pp, gx, gy, z, nx, nyw, nz, p.D, p.cut, rx, ry, rz);
                     if (pk != R(0)) {
                         fpx += pk * ((R)pp.u[0] + (R)pp.w[1] * rz - (R)pp.w[2] * ry);
                         fpy += pk * ((R)pp.u[1] + (R)pp.w[2] * rx - (R)pp.w[0] * rz);
@@ -642,7 +706,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                         double c6[6] = {0, 0, 0, 0, 0, 0};
                         if (valid) {
                             R rx, ry, rz;
-                            const R pk = particle_phi0_3d<R>(pp, gx, gy, z, nx, ny, nz, p.D, p.cut, rx, ry, rz);
+                            const R pk = particle_phi0_3d<R>(pp, gx, gy, z, nx, nyw, nz, p.D, p.cut, rx, ry, rz);
                             if (pk != R(0)) {
                                 const R vx = (R)pp.u[0] + (R)pp.w[1] * rz - (R)pp.w[2] * ry;
                                 const R vy = (R)pp.u[1] + (R)pp.w[2] * rx - (R)pp.w[0] * rz;

@@ -131,9 +131,9 @@ struct InitLat<3> {
         return i == 0 ? R(1) - R(3) * d0 + R(3) * d0 * d0
                       : (i <= 6 ? R(0.5) * (d0 - R(2) * d0 * d0) : R(0.25) * d0 * d0);
     }
-    // walls are 2D only: the 3D lattices never bounce back
-    static __device__ __forceinline__ int opp(int i) { return i; }
-    static __device__ __forceinline__ int opp2(int i) { return i; }
+    // opposite directions: pairs 1-2, 3-4, ..., 17-18 (D3Q7 is the first 7)
+    static __device__ __forceinline__ int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    static __device__ __forceinline__ int opp2(int i) { return opp(i); }
 };
 
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -285,7 +285,7 @@ __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const doub
             const int ys = y - LT::c1(i, 1);
             const bool bb = Dm.wall_y && (ys < 0 || ys >= Dm.ny);
             const int xx = bb ? x : wrap1(x - LT::c1(i, 0), Dm.nx), yy = bb ? y : wrap1(ys, Dm.ny),
-                      zz = DIM == 3 ? wrap1(z - LT::c1(i, 2), Dm.nz) : 0;
+                      zz = DIM == 3 ? (bb ? z : wrap1(z - LT::c1(i, 2), Dm.nz)) : 0;
             const long long id = cell_of(Dm, xx, yy, zz);
             const int slot = bb ? LT::opp(i) : i;
             if constexpr (P::MIX) {
@@ -319,7 +319,7 @@ __global__ void k_init_f(DomainDev Dm, int *flags, const double *phi, const doub
             const int ys = y - LT::c2(i, 1);
             const bool bb = Dm.wall_y && (ys < 0 || ys >= Dm.ny);
             const int xx = bb ? x : wrap1(x - LT::c2(i, 0), Dm.nx), yy = bb ? y : wrap1(ys, Dm.ny),
-                      zz = DIM == 3 ? wrap1(z - LT::c2(i, 2), Dm.nz) : 0;
+                      zz = DIM == 3 ? (bb ? z : wrap1(z - LT::c2(i, 2), Dm.nz)) : 0;
             const long long id = cell_of(Dm, xx, yy, zz);
             const int slot = LT::Q1 + (bb ? LT::opp2(i) : i);
             if constexpr (P::MIX) {
@@ -423,7 +423,7 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
     double acc[3] = {0.0, 0.0, 0.0};
     if (p.rep_eps > 0.0) {
         double best = INFINITY, dw0 = 0.0, dw1 = 0.0;  // x_k - x'_k
-        if (wall_y && p.dim == 2) {
+        if (wall_y) {
             const double y = parts[k].x[1];
             const double lo = 2.0 * (y + 0.5), hi = 2.0 * (ny - 0.5 - y);
             if (lo < best) {

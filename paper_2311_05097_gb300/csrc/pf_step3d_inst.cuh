@@ -6,10 +6,10 @@
 
 namespace pf {
 
-template <class P, int TX, int TY, bool MOVING, int MODE>
+template <class P, int TX, int TY, bool MOVING, int MODE, bool EXT>
 static bool run3d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
-    auto kern = k_step3d<P, TX, TY, ZCHUNK3D, MOVING, MODE>;
+    auto kern = k_step3d<P, TX, TY, ZCHUNK3D, MOVING, MODE, EXT>;
     if (occ) {
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0) != cudaSuccess) n = 0;
@@ -21,16 +21,26 @@ static bool run3d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
     return true;
 }
 
+template <class P, int TX, int TY, bool EXT>
+static bool dispatch3d_ext(bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    if (mode == MODE_MACROS)
+        return moving ? run3d<P, TX, TY, true, MODE_MACROS, EXT>(grid, s, a, occ)
+                      : run3d<P, TX, TY, false, MODE_MACROS, EXT>(grid, s, a, occ);
+    return moving ? run3d<P, TX, TY, true, MODE_STEP, EXT>(grid, s, a, occ)
+                  : run3d<P, TX, TY, false, MODE_STEP, EXT>(grid, s, a, occ);
+}
+
+// mode may carry MODE_EXT: a domain of the launch has walls
 template <class P, int TX, int TY>
 static bool dispatch3d(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
                        const StepArgs &a, int *occ)
 {
     if (tx != TX || ty != TY) return false;
-    if (mode == MODE_MACROS)
-        return moving ? run3d<P, TX, TY, true, MODE_MACROS>(grid, s, a, occ)
-                      : run3d<P, TX, TY, false, MODE_MACROS>(grid, s, a, occ);
-    return moving ? run3d<P, TX, TY, true, MODE_STEP>(grid, s, a, occ)
-                  : run3d<P, TX, TY, false, MODE_STEP>(grid, s, a, occ);
+    const bool ext = (mode & MODE_EXT) != 0;
+    mode &= ~(MODE_EXT | MODE_CAC);
+    return ext ? dispatch3d_ext<P, TX, TY, true>(moving, mode, grid, s, a, occ)
+               : dispatch3d_ext<P, TX, TY, false>(moving, mode, grid, s, a, occ);
 }
 
 }  // namespace pf

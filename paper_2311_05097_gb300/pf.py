@@ -150,8 +150,8 @@ def make_params(precision=PF_P64, stream=None, **kw):
 
 
 def make_grid(shape, walls_y=False):
-    """Grid of a (ny, nx) or (nz, ny, nx) box; walls_y (2D): no-flux walls at
-    both ends of y instead of periodicity."""
+    """Grid of a (ny, nx) or (nz, ny, nx) box; walls_y: no-flux walls at both
+    ends of y instead of periodicity."""
     g = pf_grid()
     if len(shape) == 2:
         g.dim, g.ny, g.nx, g.nz = 2, shape[0], shape[1], 1
@@ -183,8 +183,8 @@ def _is_device(a):
 
 
 class Sim:
-    """One domain advanced by libpf (pf_create ... pf_destroy): periodic, or in
-    2D with walls_y=True bounded by no-flux walls at both ends of y."""
+    """One domain advanced by libpf (pf_create ... pf_destroy): periodic, or
+    with walls_y=True bounded by no-flux walls at both ends of y."""
 
     def __init__(self, shape, precision=PF_P64, stream=None, walls_y=False, **params):
         L = load()
@@ -272,7 +272,7 @@ class Sim:
 
 class Batch:
     """Many independent domains of uneven size advanced together (pf_batch_*);
-    walls_y: one flag for all domains or one per domain (2D)."""
+    walls_y: one flag for all domains or one per domain."""
 
     def __init__(self, shapes, params_list, precision=PF_PMIX_FP16, stream=None, walls_y=False):
         L = load()

@@ -56,12 +56,13 @@ def test_params_default_and_validation(lib):
     g2 = lib.make_grid((2, 16))
     p = lib.make_params()
     assert L.pf_create(C.byref(g2), C.byref(p), C.byref(h)) == lib.PF_EINVAL
-    # walls only at the ends of y, and only in 2D
+    # walls only at the ends of y
     g3 = lib.make_grid((16, 16))
     g3.periodic[0] = 0
     assert L.pf_create(C.byref(g3), C.byref(p), C.byref(h)) == lib.PF_EINVAL
     assert "periodic" in lib.last_error()
     g3 = lib.make_grid((8, 16, 16), walls_y=True)
+    g3.periodic[2] = 0
     assert L.pf_create(C.byref(g3), C.byref(p), C.byref(h)) == lib.PF_EINVAL
 
 

@@ -2,8 +2,9 @@
 paper-shaped workloads, and of the FP64 path against the physics the paper
 fixes (prescribed contact angle, equal-area drop height on a cylinder).
 
-Each test records its measured numbers in ``gpurun_out/accuracy.jsonl`` (when
-that folder exists) so they can be summarised next to the benchmark.
+Each test appends its measured numbers as one JSON line to the file named by
+the environment variable PF_ACCURACY_LOG (when it is set), so they can be
+summarised next to the benchmark.
 """
 import json
 import math
@@ -18,13 +19,10 @@ from paper_2311_05097_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-
-
 def record(name, **vals):
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
-        with open(os.path.join(out, "accuracy.jsonl"), "a") as f:
+    path = os.environ.get("PF_ACCURACY_LOG")
+    if path:
+        with open(path, "a") as f:
             f.write(json.dumps(dict(test=name, **vals)) + "\n")
 
 

@@ -709,10 +709,11 @@ def test_p64_held_components_match_oracle(pf):
     assert_fields(dict(gm, u=om["u"]), om, 1e-12)
     for k in range(2):
         pg, po = g.particle(k), o.particle(k)
-        # particle quantities against their physical scales (velocity scale
-        # |u| + |w| R, force rho pi R^2 |u_s|), as for the annulus
+        # particle quantities against the velocity scale of the flow that drives
+        # them (the same us as for u above), the force scale rho pi R^2 us and
+        # the torque scale pi R^3 us
         R = po.R
-        vs = np.abs(po.u).max() + abs(po.w[2]) * R + 1e-4
+        vs = us
         scale = dict(x=np.abs(po.x).max(), u=vs, w=vs / R, F=math.pi * R * R * vs, T=math.pi * R ** 3 * vs)
         for f in ("x", "u", "w", "F", "T"):
             a, b = np.array(pg[f]), np.array(getattr(po, f))
@@ -720,3 +721,41 @@ def test_p64_held_components_match_oracle(pf):
     p0, p1 = g.particle(0), g.particle(1)
     assert p0["u"][0] == 0.002 and p0["w"][2] == 0.001 and p0["u"][1] != 0.0
     assert p1["u"][1] == -0.001 and p1["u"][0] != 0.0
+
+
+@pytest.mark.parametrize("shape,steps", [((12, 14, 18), 30), ((37, 10, 20), 12), ((9, 21, 33), 20)])
+def test_walls_3d_p64_matches_oracle(pf, shape, steps):
+    """Box walls in 3D (halfway bounce-back of D3Q19/D3Q7, mirrored stencil
+    rows, y-odd T_xy and T_yz): FP64 against the oracle with a sphere solid
+    and random flow; ragged tiles, several z chunks, walls inside partial
+    tiles."""
+    c = W.small_case(shape, seed=9, solid=True, theta_deg=120.0, u_amp=0.01)
+    g, o = run_pair(pf, c, steps, walls=True)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, k
+
+
+def test_walls_3d_moving_sphere_matches_oracle(pf):
+    c = W.small_case((16, 18, 20), seed=6, solid=False)
+    part = dict(x=(9.3, 5.2, 8.1), u=(0.004, -0.006, 0.002), w=(0.001, 0.0, -0.002), R=4.0, rho_p=2.0)
+    c["phi"] = (1.0 - W.disc(c["shape"], part["x"], part["R"], c["params"]["D"])) * c["phi"]
+    g, o = run_pair(pf, c, 15, particles=[part], walls=True)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
+    pg, po = g.particle(0), o.particle(0)
+    vs = np.abs(po.u).max() + np.abs(po.w).max() * po.R + 1e-4
+    assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() <= 1e-12 * np.abs(po.x).max()
+    assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() <= 1e-12 * vs
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 5e-3)])
+def test_walls_3d_reduced_precision(pf, precision, tol_phi):
+    c = W.small_case((24, 20, 36), seed=2, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 100, precision=precision, walls=True)
+    assert rel(g.macros()["phi"], o.macros()["phi"]) < tol_phi
+    if precision == "fp16":
+        m0 = float(np.sum(c["phi"]))
+        g.step(1000)
+        assert abs(g.diagnostics()["mass"] - m0) / np.abs(c["phi"]).sum() < 1e-13
+    assert g.diagnostics()["nan_flag"] == 0

@@ -488,3 +488,29 @@ def test_held_particle_components():
     assert held.u[1] == free.u[1] != 0.0
     assert free.u[0] != 0.01 and free.w[2] != 0.002
     assert held.x[0] == free.x[0] == 10.01
+
+
+def test_walls_3d_poiseuille_and_mass():
+    """Box walls in 3D (reading R21 with D3Q19/D3Q7): a body-force channel
+    between walls at y = -1/2 and ny - 1/2, periodic in x and z, approaches
+    u(y) = F_b (y + 1/2)(ny - 1/2 - y)/(2 mu), uniform in x and z; a drop next
+    to the walls with random flow keeps sum phi to round-off."""
+    ny = 16
+    prm = O.make_params(sigma=0.0, mu1=0.1, mu2=0.1, Fb=(1e-6, 0, 0), d0=0.3)
+    s = O.OracleSim((4, ny, 4), prm)
+    s.set_walls(True)
+    s.init(np.zeros((4, ny, 4)), np.zeros((4, ny, 4)))
+    s.step(20000)
+    u = s.macros()["u"][0]
+    y = np.arange(ny)
+    ua = 1e-6 / (2 * 0.1) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.abs(u - u[0:1, :, 0:1]).max() < 1e-15
+    assert np.abs(u[0, :, 0] - ua).max() < 0.01 * ua.max()
+    c = W.small_case((10, 14, 12), seed=3, solid=False, u_amp=0.01)
+    c["params"] = dict(c["params"], d0=0.3)
+    s = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+    s.set_walls(True)
+    s.init(c["phi0"], c["phi"], c["u"])
+    m0 = s.diagnostics()["mass"]
+    s.step(200)
+    assert abs(s.diagnostics()["mass"] - m0) <= 1e-13 * np.abs(c["phi"]).sum()
