@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     constexpr int PMAX = 64;
     __shared__ unsigned long long s_fast;
     __shared__ R s_pcx[MOVING ? PMAX : 1], s_pcy[MOVING ? PMAX : 1];
+    // per near particle, in the arithmetic type: radius, reach R + cut, u_x, u_y,
+    // w_z, cos(own angle) (0 without one)
+    __shared__ R s_pv[MOVING ? PMAX : 1][6];
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -236,6 +239,12 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 const double lim = pp.R + p.cut + 1.0;
                 if (ex * ex + ey * ey < lim * lim) {
                     atomicOr(&s_near, 1ull << k);
+                    s_pv[k][0] = (R)pp.R;
+                    s_pv[k][1] = (R)pp.R + (R)p.cut;
+                    s_pv[k][2] = (R)pp.u[0];
+                    s_pv[k][3] = (R)pp.u[1];
+                    s_pv[k][4] = (R)pp.w[2];
+                    s_pv[k][5] = pp.own ? (R)pp.ct : R(0);
                     // a cell of the frames farther than nx/2 from this image is at
                     // least R + cut + 1 from every image when the box is this wide
                     const double span = 2.0 * (pp.R + p.cut) + 8.0;
@@ -252,12 +261,14 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         __syncthreads();
         [[maybe_unused]] const unsigned long long near = MOVING ? s_near : 0ull;
         [[maybe_unused]] const unsigned long long fast = MOVING ? s_fast : 0ull;
+        [[maybe_unused]] const R Dr = (R)p.D;
+        [[maybe_unused]] const R kp_cos_t = (R)p.cos_t;
         // indicator of particle k at table cell (cx, cy), global cell (gx, gy)
         [[maybe_unused]] auto pphi0 = [&](int k, int cx, int cy, int gx, int gy, R &rx, R &ry) -> R {
             const ParticleDev &pp = A.parts[k];
             if ((fast >> k) & 1ull)
-                return particle_phi0_rel<R>(R(cx) - s_pcx[k], R(cy) - s_pcy[k], (R)pp.R, (R)pp.R + (R)p.cut,
-                                            (R)p.D, rx, ry);
+                return particle_phi0_rel<R>(R(cx) - s_pcx[k], R(cy) - s_pcy[k], s_pv[k][0], s_pv[k][1], Dr,
+                                            rx, ry);
             return particle_phi0<R, EXT>(pp, gx, gy, nx, nyw, p.D, p.cut, rx, ry);
         };
 
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     const R pk = pphi0(k, cx, cy, gx, gy, rx, ry);
                     v += pk;
                     if (A.parts[k].own) {
-                        const R ck = (R)A.parts[k].ct;
+                        const R ck = s_pv[k][5];
                         w += ck * pk;
                         vv += ck * pk * pk * pk;
                     } else {
@@ -335,7 +346,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     }
                 }
                 if (A.wv) {
-                    const R ct = (R)p.cos_t;
+                    const R ct = kp_cos_t;
                     s_W[hy][hx] = ct * dflt + w;
                     s_V[hy][hx] = ct * dflt * dflt * dflt + vv;
                 }
@@ -548,8 +559,8 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 R rx, ry;
                 const R pk = pphi0(k, lx + 3, ly + 3, gx, gy, rx, ry);
                 if (pk != R(0)) {
-                    const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
-                    const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
+                    const R usx_k = s_pv[k][2] - s_pv[k][4] * ry;
+                    const R usy_k = s_pv[k][3] + s_pv[k][4] * rx;
                     fpx += pk * usx_k;
                     fpy += pk * usy_k;
                 }
@@ -712,20 +723,23 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                         if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;
                         continue;
                     }
-                    // 2D: F_x, F_y and T_z (components 0, 1, 5); the others stay 0
-                    double c6[3] = {0, 0, 0};
+                    // 2D: F_x, F_y and T_z (components 0, 1, 5); the others stay 0.
+                    // The cell terms and the warp's shuffle tree are in the
+                    // arithmetic type (the terms are computed in it); the warps'
+                    // sums, the tiles' partials and the update are FP64.
+                    R c6[3] = {R(0), R(0), R(0)};
                     bool hit = false;
                     if (valid) {
                         R rx, ry;
                         const R pk = pphi0(k, lx + 3, ly + 3, gx, gy, rx, ry);
                         if (pk != R(0)) {
                             hit = true;
-                            const R usx_k = (R)pp.u[0] - (R)pp.w[2] * ry;
-                            const R usy_k = (R)pp.u[1] + (R)pp.w[2] * rx;
+                            const R usx_k = s_pv[k][2] - s_pv[k][4] * ry;
+                            const R usy_k = s_pv[k][3] + s_pv[k][4] * rx;
                             const R fx = rho * pk * (usx_k - usx), fy = rho * pk * (usy_k - usy);
-                            c6[0] = -(double)fx;
-                            c6[1] = -(double)fy;
-                            c6[2] = -((double)rx * (double)fy - (double)ry * (double)fx);
+                            c6[0] = -fx;
+                            c6[1] = -fy;
+                            c6[2] = -(rx * fy - ry * fx);
                         }
                     }
                     if (!__syncthreads_or(hit)) {
@@ -739,12 +753,12 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                     const bool wany = __any_sync(0xffffffffu, hit);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
-                        double v = c6[c];
+                        R v = c6[c];
                         if (wany) {
 #pragma unroll
                             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                         }
-                        if ((tid & 31) == 0) s_red[tid >> 5][c] = v;
+                        if ((tid & 31) == 0) s_red[tid >> 5][c] = (double)v;
                     }
                     __syncthreads();
                     if (tid < 6) {
