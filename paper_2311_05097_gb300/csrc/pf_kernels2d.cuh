@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     __shared__ int s_gy[TY + 6];  // row offsets y * pitch (planes hold < 2^31 cells)
     __shared__ int s_gyi[TY + 6];
     __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
-    __shared__ double s_red[NT / 32][6];
+    __shared__ double s_red[2][NT / 32][3];  // warps' sums, double-buffered over particles
     __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
     // particles whose image nearest to the tile is the minimum image of every
     // cell of its frames, and that image's centre in table coordinates (the
@@ -716,6 +716,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             if constexpr (MOVING) {
                 // hydrodynamic force and torque on each particle (Eq. 27):
                 // F_f = -sum rho phi0_k (u_s,k - u*), T_f = -sum r x (...)
+                int nred = 0;  // reductions so far in this tile: picks the s_red buffer
                 for (int k = 0; k < A.np; ++k) {
                     const ParticleDev &pp = A.parts[k];
                     if (!((near >> k) & 1ull)) {
@@ -742,15 +743,14 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                             c6[2] = -(rx * fy - ry * fx);
                         }
                     }
-                    if (!__syncthreads_or(hit)) {
-                        // the indicator is 0 on every cell of the tile (it rounds to
-                        // 0 well inside the reach used for the tile test)
-                        if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;
-                        continue;
-                    }
                     // fixed-order block reduction: warp shuffle tree (skipped by
-                    // warps whose terms are all 0), then warps in order
+                    // warps whose terms are all 0: the indicator rounds to 0 well
+                    // inside the reach used for the tile test), then warps in
+                    // order; one barrier per particle (the buffer written here is
+                    // next written two particles later, after another barrier)
                     const bool wany = __any_sync(0xffffffffu, hit);
+                    double(*red)[3] = s_red[nred & 1];
+                    ++nred;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         R v = c6[c];
@@ -758,17 +758,16 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
 #pragma unroll
                             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                         }
-                        if ((tid & 31) == 0) s_red[tid >> 5][c] = (double)v;
+                        if ((tid & 31) == 0) red[tid >> 5][c] = (double)v;
                     }
                     __syncthreads();
                     if (tid < 6) {
                         double acc = 0.0;
                         const int c = tid == 5 ? 2 : tid;
                         if (tid < 2 || tid == 5)
-                            for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[wq][c];
+                            for (int wq = 0; wq < NT / 32; ++wq) acc += red[wq][c];
                         A.partials[((long long)t * A.np + k) * 6 + tid] = acc;
                     }
-                    __syncthreads();
                 }
             }
         }
