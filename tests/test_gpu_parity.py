@@ -759,3 +759,30 @@ def test_walls_3d_reduced_precision(pf, precision, tol_phi):
         g.step(1000)
         assert abs(g.diagnostics()["mass"] - m0) / np.abs(c["phi"]).sum() < 1e-13
     assert g.diagnostics()["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("shape,walls", [((4, 4), False), ((4, 6), True), ((5, 4), True), ((4, 4, 4), False),
+                                         ((4, 5, 4), True)])
+def test_smallest_grids_match_oracle(pf, shape, walls):
+    """The smallest grids the library accepts (4 cells per axis; one tile
+    holds both walls and wraps several times), FP64 against the oracle."""
+    c = W.small_case(shape, seed=13, solid=False, u_amp=0.01, D=2.0)
+    g, o = run_pair(pf, c, 25, walls=walls)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
+
+
+def test_zero_steps_and_split_steps(pf):
+    """pf_step(0) changes nothing; n steps in pieces equal n steps at once."""
+    c = W.small_case((37, 45), seed=2, solid=True, u_amp=0.01)
+    a, _ = run_pair(pf, c, 0, oracle=False)
+    m0 = a.macros()
+    a.step(0)
+    assert a.time == 0
+    for k in FIELDS:
+        assert np.array_equal(a.macros()[k], m0[k]), k
+    a.step(7)
+    a.step(0)
+    a.step(13)
+    b, _ = run_pair(pf, c, 20, oracle=False)
+    for k in FIELDS:
+        assert np.array_equal(a.macros()[k], b.macros()[k]), k
