@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--precision", default=None)
     ap.add_argument("--config", type=int, nargs=4, default=None,
-                    metavar=("TILE_X", "TILE_Y", "CELLS_PER_THREAD", "CTAS_PER_SM"),
+                    metavar=("TILE_X", "TILE_Y", "KERNEL", "CTAS_PER_SM"),
                     help="fix the batch launch configuration instead of autotuning it")
     ap.add_argument("--phase-model", type=int, default=0, choices=[0, 1],
                     help="order parameter: 0 Cahn-Hilliard (the paper's), 1 conservative Allen-Cahn")
@@ -429,7 +429,7 @@ def run_batch(args, dist, rank, world, local):
     cfg = {"workload": args.workload, "domains": len(cases), "cells": cells, "precision": prec,
            "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"
                                    % (cells * bpc / 1e9),
-           "tile": [tx, ty], "ctas_per_sm": cps, "cells_per_thread": cpt,
+           "tile": [tx, ty], "ctas_per_sm": cps, "kernel": cpt, "cells_per_thread": 2 if cpt else 1,
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
                 clk=clk, launches=launches, e2e=e2e, t_wall=t_wall,
