@@ -786,3 +786,32 @@ def test_zero_steps_and_split_steps(pf):
     b, _ = run_pair(pf, c, 20, oracle=False)
     for k in FIELDS:
         assert np.array_equal(a.macros()[k], b.macros()[k]), k
+
+
+@pytest.mark.parametrize("name,steps", [("drop_on_cylinder", 1000), ("water_entry", 50), ("drainage_3d", 3)])
+def test_full_size_configs_against_oracle(pf, name, steps):
+    """The paper-shaped workloads at full size in FP64 against the oracle over
+    their first steps: the 512² drop on a cylinder for 1000 steps, the
+    2048 x 1024 water entry with its moving particle for 50, the 256³
+    drainage for 3 (the oracle's cost bounds the step counts)."""
+    if name == "drop_on_cylinder":
+        c = W.drop_on_cylinder()
+    elif name == "water_entry":
+        c = W.water_entry()
+    else:
+        c = W.porous_drainage_3d(n=256)
+    parts = c.get("particles", [])
+    g, o = run_pair(pf, c, steps, particles=parts)
+    mu_scale = 3 * c["params"]["sigma"] / c["params"]["D"]
+    gm, om = g.macros(), o.macros()
+    if parts:
+        # the flow inside and around the particle follows its velocity scale
+        us = np.abs(om["u"]).max() + np.abs(np.array(parts[0]["u"])).max()
+        assert np.abs(gm["u"] - om["u"]).max() <= 1e-12 * us
+        gm = dict(gm, u=om["u"])
+    assert_fields(gm, om, 1e-12, mu_scale=mu_scale)
+    for k in range(len(parts)):
+        pg, po = g.particle(k), o.particle(k)
+        vs = np.abs(po.u).max() + abs(po.w[2]) * po.R + 1e-4
+        assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() <= 1e-12 * np.abs(po.x).max()
+        assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() <= 1e-12 * vs
