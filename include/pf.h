@@ -191,6 +191,14 @@ int pf_step(pf_handle *h, int64_t n);
 int pf_get_macros(pf_handle *h, double *phi, double *rho, double *u, double *P, double *mu,
                   int where);
 
+/* Interface normal n = grad phi / |grad phi| at the current time (dim*N,
+ * component-major like u), from phi of Eq. (31) with the central isotropic
+ * stencil of Sec. 3.2 (mirror rows at walls); 0 where |grad phi|^2 <= 1e-24.
+ * The unit normal of the fluid-fluid interface that the contact angle of
+ * Eq. (8) is measured against, and the direction of the Allen-Cahn flux.
+ * n is caller-owned; where = PF_HOST or PF_DEVICE.  Synchronous. */
+int pf_get_normal(pf_handle *h, double *n, int where);
+
 /* Particles: set = 1 adds (k == count) or overwrites (k < count) particle k
  * from *inout (its F, T are ignored); set = 0 copies particle k into *inout.
  * At most PF_MAX_PARTICLES.  Synchronous. */

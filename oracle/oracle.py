@@ -56,6 +56,7 @@ def lib():
         L.orc_diagnostics.argtypes = [C.c_void_p, _DP]
         L.orc_get_f.argtypes = [C.c_void_p, _DP, _DP]
         L.orc_get_phi0.argtypes = [C.c_void_p, _DP]
+        L.orc_normal.argtypes = [C.c_void_p, _DP]
         L.orc_set_particle.argtypes = [C.c_void_p, C.c_int, C.POINTER(OrcParticle)]
         L.orc_set_particle.restype = C.c_int
         L.orc_get_particle.argtypes = [C.c_void_p, C.c_int, C.POINTER(OrcParticle)]
@@ -212,6 +213,12 @@ class OracleSim:
         f2 = np.empty(self.Q2 * self.N)
         lib().orc_get_f(self._h, _p(f1), _p(f2))
         return f1.reshape((self.Q1,) + self.shape), f2.reshape((self.Q2,) + self.shape)
+
+    def normal(self):
+        """Interface normal grad phi / |grad phi| (dim, *shape)."""
+        n = np.empty(self.dim * self.N)
+        lib().orc_normal(self._h, _p(n))
+        return n.reshape((self.dim,) + self.shape)
 
     def phi0(self):
         a = np.empty(self.N)

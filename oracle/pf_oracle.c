@@ -1249,6 +1249,18 @@ void orc_macros(orc_sim *s, double *phi, double *rho, double *u, double *P, doub
     if (mu) memcpy(mu, s->mu, sizeof(double) * N);
 }
 
+void orc_normal(orc_sim *s, double *n)
+{
+    const long N = s->N;
+    compute_macros(s);
+    for (long id = 0; id < N; ++id) {
+        double g2 = 0.0;
+        for (int a = 0; a < s->dim; ++a) g2 += s->gphi[a * N + id] * s->gphi[a * N + id];
+        const double inv = g2 > 1e-24 ? 1.0 / sqrt(g2) : 0.0;
+        for (int a = 0; a < s->dim; ++a) n[a * N + id] = s->gphi[a * N + id] * inv;
+    }
+}
+
 void orc_get_f(orc_sim *s, double *f1, double *f2)
 {
     if (f1) memcpy(f1, s->f1, sizeof(double) * s->L1.Q * s->N);

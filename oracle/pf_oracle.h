@@ -83,6 +83,9 @@ int orc_get_particle(orc_sim *s, int k, orc_particle *pp);
 int orc_num_particles(orc_sim *s);
 /* Reading R21: walls at y = -1/2 and y = ny - 1/2 (2D and 3D; before init). */
 int orc_set_walls(orc_sim *s, int wall_y);
+/* Interface normal grad phi / |grad phi| at the current time (dim x N; 0 where
+ * |grad phi|^2 <= 1e-24), central stencil with the walls of reading R21. */
+void orc_normal(orc_sim *s, double *n);
 /* The total solid indicator phi0 at the current time. */
 void orc_get_phi0(orc_sim *s, double *phi0);
 

@@ -12,10 +12,18 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pf.h"
 #include "pf_internal.h"
 
 namespace pf {
+
+// NVTX range over a library call (seen by Nsight tools; a no-op otherwise)
+struct PfRange {
+    explicit PfRange(const char *name) { nvtxRangePushA(name); }
+    ~PfRange() { nvtxRangePop(); }
+};
 
 static std::atomic<long long> g_launches{0};
 void count_launches(long long n) { g_launches += n; }
@@ -830,7 +838,8 @@ static int engine_macro_tables(Engine &E)
     const int nd = (int)E.mem.size();
     long long nmax = 0;
     for (auto &m : E.mem) nmax = std::max(nmax, (long long)m.d.nx * m.d.ny * m.d.nz);
-    CK(cudaMalloc(&E.d_macro, sizeof(double) * (size_t)(7 + E.dim) * nmax));
+    // planes: phi, rho, u (dim), P, mu, phi0, W, V, and the interface normal (dim)
+    CK(cudaMalloc(&E.d_macro, sizeof(double) * (size_t)(7 + 2 * E.dim) * nmax));
     int mtx = 32, mty = 8;
     if (E.dim == 3) tile_shape3d(E.prec, &mtx, &mty);
     // build_tiles writes the tiling into the DomainDev it is given: tile copies
@@ -887,6 +896,7 @@ static int engine_macros(Engine &E, int i)
 static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double *u, double *P,
                              double *mu, int where)
 {
+    PfRange range("pf_get_macros");
     if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     if (!E.inited[i]) return fail(PF_ESTATE, "pf_get_macros before pf_init_fields");
     int rc = engine_sync(E);
@@ -908,8 +918,32 @@ static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double 
     return PF_OK;
 }
 
+// interface normal n = grad phi / |grad phi| of domain i (0 where |grad phi|^2 <= 1e-24)
+static int engine_get_normal(Engine &E, int i, double *n, int where)
+{
+    if (!n) return fail(PF_EINVAL, "n is NULL");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (!E.inited[i]) return fail(PF_ESTATE, "pf_get_normal before pf_init_fields");
+    PfRange range("pf_get_normal");
+    int rc = engine_sync(E);
+    if (rc && rc != PF_ENUMERIC) return rc;
+    rc = engine_macros(E, i);
+    if (rc) return rc;
+    DomainDev dd = E.mem[i].d;
+    dd.macro = E.d_macro;
+    const long long N = (long long)dd.nx * dd.ny * dd.nz;
+    double *dst = where == PF_DEVICE ? n : E.d_macro + (size_t)(7 + E.dim) * N;
+    launch_normal(dd, dst, E.stream);
+    CK(cudaGetLastError());
+    if (where == PF_HOST)
+        CK(cudaMemcpyAsync(n, dst, sizeof(double) * E.dim * N, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    return PF_OK;
+}
+
 static int engine_diag(Engine &E, int i, pf_diag *out)
 {
+    PfRange range("pf_diagnostics");
     if (!out) return fail(PF_EINVAL, "out is NULL");
     if (!E.inited[i]) return fail(PF_ESTATE, "pf_diagnostics before pf_init_fields");
     int rc = engine_sync(E);
@@ -945,6 +979,7 @@ struct pf_handle {
 
 extern "C" int pf_create(const pf_grid *g, const pf_params *p, pf_handle **out)
 {
+    PfRange range("pf_create");
     if (!out) return fail(PF_EINVAL, "out is NULL");
     int rc = validate(g, p);
     if (rc) return rc;
@@ -977,6 +1012,7 @@ static int upload_particles(Engine &E)
 extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *phi, const double *u,
                               const double *P, int where)
 {
+    PfRange range("pf_init_fields");
     if (!h) return fail(PF_EINVAL, "handle is NULL");
     Engine &E = h->E;
     if (E.sticky) return E.sticky;
@@ -1013,6 +1049,7 @@ extern "C" int pf_set_config(pf_handle *h, int tile_x, int tile_y, int kernel, i
 
 extern "C" int pf_step(pf_handle *h, int64_t n)
 {
+    PfRange range("pf_step");
     if (!h) return fail(PF_EINVAL, "handle is NULL");
     return engine_step(h->E, n, false);
 }
@@ -1030,6 +1067,12 @@ extern "C" int pf_get_macros(pf_handle *h, double *phi, double *rho, double *u, 
 {
     if (!h) return fail(PF_EINVAL, "handle is NULL");
     return engine_get_macros(h->E, 0, phi, rho, u, P, mu, where);
+}
+
+extern "C" int pf_get_normal(pf_handle *h, double *n, int where)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    return engine_get_normal(h->E, 0, n, where);
 }
 
 extern "C" int pf_diagnostics(pf_handle *h, pf_diag *out)
@@ -1122,6 +1165,7 @@ struct pf_batch {
 
 extern "C" int pf_batch_create(int nd, const pf_grid *g, const pf_params *p, pf_batch **out)
 {
+    PfRange range("pf_batch_create");
     if (!out || nd < 1 || !g || !p) return fail(PF_EINVAL, "bad arguments");
     for (int i = 0; i < nd; ++i) {
         int rc = validate(&g[i], &p[i]);
@@ -1144,6 +1188,7 @@ extern "C" int pf_batch_create(int nd, const pf_grid *g, const pf_params *p, pf_
 extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const double *phi, const double *u,
                              const double *P, int where)
 {
+    PfRange range("pf_batch_init");
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     Engine &E = b->E;
     if (i < 0 || i >= (int)E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
@@ -1159,6 +1204,7 @@ extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const doubl
 
 extern "C" int pf_batch_step(pf_batch *b, int64_t n)
 {
+    PfRange range("pf_batch_step");
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     return engine_step(b->E, n, true);
 }

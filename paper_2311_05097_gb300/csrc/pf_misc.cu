@@ -390,6 +390,24 @@ __global__ void k_diag_partial(DomainDev Dm, double *partial, int wv)
         for (int c = 0; c < 3; ++c) partial[blockIdx.x * 3 + c] = red[0][c];
 }
 
+// interface normal n = grad phi / |grad phi| from the macroscopic phi (central
+// isotropic stencil, mirror rows at walls); 0 where |grad phi|^2 <= 1e-24
+__global__ void k_normal(DomainDev Dm, double *n)
+{
+    const int dim = Dm.p.dim;
+    const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < N; o += stride) {
+        const int x = (int)(o % Dm.nx), y = (int)((o / Dm.nx) % Dm.ny), z = (int)(o / ((long long)Dm.nx * Dm.ny));
+        double g[3];
+        fd_grad_lap(Dm, Dm.macro, x, y, z, g, nullptr);
+        double g2 = 0.0;
+        for (int a = 0; a < dim; ++a) g2 += g[a] * g[a];
+        const double inv = g2 > 1e-24 ? 1.0 / sqrt(g2) : 0.0;
+        for (int a = 0; a < dim; ++a) n[a * N + o] = g[a] * inv;
+    }
+}
+
 __global__ void k_diag_final(const double *partial, int nblocks, double *out)
 {
     __shared__ double red[256][3];
@@ -578,6 +596,13 @@ void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, 
     case 2: init_impl<PMixH>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, wv, s); break;
     default: init_impl<PMixB>(Dm, flags, phi0, phi, u, Pin, tmp, parts, np, wv, s); break;
     }
+}
+
+void launch_normal(const DomainDev &Dm, double *n, cudaStream_t s)
+{
+    const long long N = (long long)Dm.nx * Dm.ny * Dm.nz;
+    k_normal<<<grid_for(N, 256), 256, 0, s>>>(Dm, n);
+    count_launches(1);
 }
 
 int diag_blocks() { return 120; }

@@ -83,6 +83,7 @@ def load(build_if_missing=False):
         "pf_init_fields": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
         "pf_step": (C.c_int, [vp, C.c_int64]),
         "pf_get_macros": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int]),
+        "pf_get_normal": (C.c_int, [vp, vp, C.c_int]),
         "pf_particle_state": (C.c_int, [vp, C.c_int, C.POINTER(pf_particle), C.c_int]),
         "pf_num_particles": (C.c_int, [vp]),
         "pf_diagnostics": (C.c_int, [vp, C.POINTER(pf_diag)]),
@@ -263,6 +264,12 @@ class Sim:
                                     PF_HOST))
         return dict(phi=phi.reshape(sh), rho=rho.reshape(sh), u=u.reshape((self.dim,) + sh),
                     P=P.reshape(sh), mu=mu.reshape(sh))
+
+    def normal(self):
+        """Interface normal grad phi / |grad phi| (dim, *shape) as a numpy array."""
+        n = np.empty(self.dim * self.N)
+        _check(load().pf_get_normal(self._h, C.c_void_p(n.ctypes.data), PF_HOST))
+        return n.reshape((self.dim,) + self.shape)
 
     def diagnostics(self):
         d = pf_diag()

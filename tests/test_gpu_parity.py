@@ -815,3 +815,19 @@ def test_full_size_configs_against_oracle(pf, name, steps):
         vs = np.abs(po.u).max() + abs(po.w[2]) * po.R + 1e-4
         assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() <= 1e-12 * np.abs(po.x).max()
         assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() <= 1e-12 * vs
+
+
+@pytest.mark.parametrize("shape,walls", [((37, 45), False), ((37, 52), True), ((12, 14, 18), False),
+                                         ((9, 21, 33), True)])
+def test_interface_normal_matches_oracle(pf, shape, walls):
+    """pf_get_normal (grad phi / |grad phi| of the current phi) against the
+    oracle after some steps, on the interface band |phi| < 0.99 (in the bulk
+    the direction of a round-off gradient is arbitrary on both sides)."""
+    c = W.small_case(shape, seed=5, solid=False, u_amp=0.01)
+    g, o = run_pair(pf, c, 20, walls=walls)
+    ng, no = g.normal(), o.normal()
+    band = np.abs(o.macros()["phi"]) < 0.99
+    assert band.sum() > 50
+    assert np.abs(ng[:, band] - no[:, band]).max() < 1e-12
+    norm = np.sqrt((ng ** 2).sum(axis=0))
+    assert np.abs(norm[band] - 1.0).max() < 1e-12

@@ -346,3 +346,33 @@ def test_flat_equilibrium_profile_has_zero_mu():
         errs.append(np.abs(mu).max() / (3 * 0.01 / D))
     assert errs[0] < 0.1
     assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0
+
+
+def test_interface_normal():
+    """The interface normal grad phi / |grad phi|: exactly the x axis on a flat
+    profile in x (the stencil is symmetric in y), 0 in a uniform bulk, and
+    along -r within a fraction of a degree across a circular drop (isotropic
+    stencil)."""
+    import math
+    ny, nx = 16, 64
+    x = np.arange(nx, dtype=float)
+    phi = np.tile(np.tanh(2.0 * (x - 20.5) / 4.0) * np.tanh(2.0 * (52.5 - x) / 4.0), (ny, 1))
+    s = O.OracleSim((ny, nx), O.make_params())
+    s.init(np.zeros((ny, nx)), phi)
+    n = s.normal()
+    # across the interface (away from the bulk, where |grad phi| is round-off)
+    assert np.abs(n[1][:, 15:26]).max() < 1e-14
+    assert np.abs(np.abs(n[0][:, 15:26]) - 1.0).max() < 1e-12
+    assert np.all(n[0][:, 15:26] > 0) and np.all(n[0][:, 48:57] < 0)
+    s = O.OracleSim((8, 8), O.make_params())
+    s.init(np.zeros((8, 8)), np.full((8, 8), -1.0))
+    assert np.abs(s.normal()).max() == 0.0
+    L = 96
+    yy, xx = np.meshgrid(np.arange(L, dtype=float), np.arange(L, dtype=float), indexing="ij")
+    r = np.hypot(xx - 47.5, yy - 47.5)
+    s = O.OracleSim((L, L), O.make_params())
+    s.init(np.zeros((L, L)), np.tanh(2.0 * (25.0 - r) / 4.0))
+    n = s.normal()
+    band = np.abs(r - 25.0) < 2.0
+    ang = np.degrees(np.arccos(np.clip(-(n[0] * (xx - 47.5) + n[1] * (yy - 47.5)) / r, -1, 1)))
+    assert ang[band].max() < 0.5, ang[band].max()
