@@ -199,6 +199,20 @@ int pf_get_macros(pf_handle *h, double *phi, double *rho, double *u, double *P, 
  * n is caller-owned; where = PF_HOST or PF_DEVICE.  Synchronous. */
 int pf_get_normal(pf_handle *h, double *n, int where);
 
+/* Checkpoint and resume (the paper has no counterpart; the step has no
+ * randomness, so a resumed run is bit-identical to an uninterrupted one).
+ * pf_state_size: bytes of the state of h (current populations, PMIX rest
+ * populations, lagged fields, fixed indicator, particles, time).
+ * pf_save_state: writes it into the caller's host buffer buf of `bytes`
+ * (>= pf_state_size); synchronous; PF_ESTATE before pf_init_fields.
+ * pf_load_state: replaces the state of h by one saved from a handle with the
+ * same grid, walls, precision and particle count (set the particles first;
+ * their saved positions and velocities replace them); the parameters are the
+ * handle's own.  PF_EINVAL on a mismatch or a short buffer. */
+int pf_state_size(pf_handle *h, int64_t *bytes);
+int pf_save_state(pf_handle *h, void *buf, int64_t bytes);
+int pf_load_state(pf_handle *h, const void *buf, int64_t bytes);
+
 /* Particles: set = 1 adds (k == count) or overwrites (k < count) particle k
  * from *inout (its F, T are ignored); set = 0 copies particle k into *inout.
  * At most PF_MAX_PARTICLES.  Synchronous. */

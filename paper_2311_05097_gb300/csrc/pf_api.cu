@@ -1081,6 +1081,130 @@ extern "C" int pf_diagnostics(pf_handle *h, pf_diag *out)
     return engine_diag(h->E, 0, out);
 }
 
+// ---- checkpoint / resume ----------------------------------------------------------------------
+// The state that the next step reads: the current populations, the PMIX rest
+// populations, the lagged fields, the fixed indicator, the particles and the
+// time.  Loading it into a handle created with the same grid, parameters and
+// particle count continues the run bit for bit (the step has no randomness).
+struct PfStateHeader {
+    char magic[8];
+    int version, dim, prec, nx, ny, nz, np, wall_y;
+    long long t, fb, rb, ab, pb;
+};
+
+static void state_sizes(const Engine &E, size_t &fb, size_t &rb, size_t &ab, size_t &pb)
+{
+    const DomainDev &d = E.mem[0].d;
+    const int Q = E.dim == 2 ? 18 : 26, naux = 2 * E.dim + 1;
+    fb = (size_t)Q * d.plane * store_bytes(E.prec);
+    rb = E.prec >= PF_PMIX_FP16 ? (size_t)d.plane * 8 : 0;
+    ab = (size_t)naux * d.plane * aux_bytes(E.prec);
+    pb = (size_t)d.plane * aux_bytes(E.prec);
+}
+
+static size_t state_bytes(const Engine &E)
+{
+    size_t fb, rb, ab, pb;
+    state_sizes(E, fb, rb, ab, pb);
+    return sizeof(PfStateHeader) + fb + rb + ab + pb + sizeof(ParticleDev) * (size_t)E.np;
+}
+
+extern "C" int pf_state_size(pf_handle *h, int64_t *bytes)
+{
+    if (!h || !bytes) return fail(PF_EINVAL, "NULL argument");
+    *bytes = (int64_t)state_bytes(h->E);
+    return PF_OK;
+}
+
+extern "C" int pf_save_state(pf_handle *h, void *buf, int64_t bytes)
+{
+    if (!h || !buf) return fail(PF_EINVAL, "NULL argument");
+    Engine &E = h->E;
+    if (!E.inited[0]) return fail(PF_ESTATE, "pf_save_state before pf_init_fields");
+    if (bytes < (int64_t)state_bytes(E)) return fail(PF_EINVAL, "buffer of %lld bytes is smaller than the state (%lld)",
+                                                    (long long)bytes, (long long)state_bytes(E));
+    PfRange range("pf_save_state");
+    int rc = engine_sync(E);
+    if (rc) return rc;
+    const DomainDev &d = E.mem[0].d;
+    PfStateHeader hd{};
+    memcpy(hd.magic, "PFSTATE", 8);
+    hd.version = 1;
+    hd.dim = E.dim;
+    hd.prec = E.prec;
+    hd.nx = d.nx;
+    hd.ny = d.ny;
+    hd.nz = d.nz;
+    hd.np = E.np;
+    hd.wall_y = d.wall_y;
+    hd.t = E.t;
+    size_t fb, rb, ab, pb;
+    state_sizes(E, fb, rb, ab, pb);
+    hd.fb = (long long)fb;
+    hd.rb = (long long)rb;
+    hd.ab = (long long)ab;
+    hd.pb = (long long)pb;
+    char *o = static_cast<char *>(buf);
+    memcpy(o, &hd, sizeof(hd));
+    o += sizeof(hd);
+    CK(cudaMemcpy(o, d.f[E.par], fb, cudaMemcpyDeviceToHost));
+    o += fb;
+    if (rb) CK(cudaMemcpy(o, d.rest[E.par], rb, cudaMemcpyDeviceToHost));
+    o += rb;
+    CK(cudaMemcpy(o, d.aux[E.par], ab, cudaMemcpyDeviceToHost));
+    o += ab;
+    CK(cudaMemcpy(o, d.phi0, pb, cudaMemcpyDeviceToHost));
+    o += pb;
+    if (E.np) CK(cudaMemcpy(o, E.d_parts, sizeof(ParticleDev) * E.np, cudaMemcpyDeviceToHost));
+    return PF_OK;
+}
+
+extern "C" int pf_load_state(pf_handle *h, const void *buf, int64_t bytes)
+{
+    if (!h || !buf) return fail(PF_EINVAL, "NULL argument");
+    Engine &E = h->E;
+    if (bytes < (int64_t)sizeof(PfStateHeader)) return fail(PF_EINVAL, "buffer too small for a state header");
+    PfStateHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    const DomainDev &d = E.mem[0].d;
+    size_t fb, rb, ab, pb;
+    state_sizes(E, fb, rb, ab, pb);
+    if (memcmp(hd.magic, "PFSTATE", 8) != 0 || hd.version != 1) return fail(PF_EINVAL, "not a libpf state");
+    if (hd.dim != E.dim || hd.prec != E.prec || hd.nx != d.nx || hd.ny != d.ny || hd.nz != d.nz ||
+        hd.wall_y != d.wall_y || hd.fb != (long long)fb || hd.rb != (long long)rb || hd.ab != (long long)ab ||
+        hd.pb != (long long)pb)
+        return fail(PF_EINVAL, "the state was saved from another grid or precision");
+    if (hd.np != E.np)
+        return fail(PF_EINVAL, "the state holds %d particles, the handle %d: set as many before loading", hd.np,
+                    E.np);
+    if (bytes < (int64_t)state_bytes(E)) return fail(PF_EINVAL, "buffer shorter than the state it announces");
+    if (E.sticky) return E.sticky;
+    PfRange range("pf_load_state");
+    CK(cudaStreamSynchronize(E.stream));
+    const char *in = static_cast<const char *>(buf) + sizeof(hd);
+    CK(cudaMemcpy(d.f[E.par], in, fb, cudaMemcpyHostToDevice));
+    in += fb;
+    if (rb) CK(cudaMemcpy(d.rest[E.par], in, rb, cudaMemcpyHostToDevice));
+    in += rb;
+    CK(cudaMemcpy(d.aux[E.par], in, ab, cudaMemcpyHostToDevice));
+    in += ab;
+    CK(cudaMemcpy(d.phi0, in, pb, cudaMemcpyHostToDevice));
+    in += pb;
+    if (E.np) {
+        memcpy(E.hp, in, sizeof(ParticleDev) * E.np);
+        int wv = 0;
+        for (int j = 0; j < E.np; ++j) wv |= E.hp[j].own;
+        if (wv != E.wv) drop_graph(E);
+        E.wv = wv;
+        int rc = upload_particles(E);
+        if (rc) return rc;
+    }
+    CK(cudaMemset(E.d_flags, 0, sizeof(int) * 4));
+    E.t = hd.t;
+    E.inited[0] = true;
+    return PF_OK;
+}
+
 extern "C" int pf_num_particles(pf_handle *h) { return h ? h->E.np : -1; }
 
 extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)

@@ -84,6 +84,9 @@ def load(build_if_missing=False):
         "pf_step": (C.c_int, [vp, C.c_int64]),
         "pf_get_macros": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int]),
         "pf_get_normal": (C.c_int, [vp, vp, C.c_int]),
+        "pf_state_size": (C.c_int, [vp, C.POINTER(C.c_int64)]),
+        "pf_save_state": (C.c_int, [vp, vp, C.c_int64]),
+        "pf_load_state": (C.c_int, [vp, vp, C.c_int64]),
         "pf_particle_state": (C.c_int, [vp, C.c_int, C.POINTER(pf_particle), C.c_int]),
         "pf_num_particles": (C.c_int, [vp]),
         "pf_diagnostics": (C.c_int, [vp, C.POINTER(pf_diag)]),
@@ -264,6 +267,20 @@ class Sim:
                                     PF_HOST))
         return dict(phi=phi.reshape(sh), rho=rho.reshape(sh), u=u.reshape((self.dim,) + sh),
                     P=P.reshape(sh), mu=mu.reshape(sh))
+
+    def save_state(self):
+        """The run's state as bytes (pf_save_state)."""
+        n = C.c_int64()
+        _check(load().pf_state_size(self._h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(load().pf_save_state(self._h, buf, n.value))
+        return buf.raw
+
+    def load_state(self, state):
+        """Continue from bytes written by save_state (same grid, precision and
+        particle count)."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(load().pf_load_state(self._h, buf, len(state)))
 
     def normal(self):
         """Interface normal grad phi / |grad phi| (dim, *shape) as a numpy array."""

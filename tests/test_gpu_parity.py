@@ -831,3 +831,38 @@ def test_interface_normal_matches_oracle(pf, shape, walls):
     assert np.abs(ng[:, band] - no[:, band]).max() < 1e-12
     norm = np.sqrt((ng ** 2).sum(axis=0))
     assert np.abs(norm[band] - 1.0).max() < 1e-12
+
+
+@pytest.mark.parametrize("precision,walls,with_particle", [("p64", False, False), ("fp16", True, False),
+                                                           ("p32", False, True)])
+def test_checkpoint_resume_is_bit_identical(pf, precision, walls, with_particle):
+    """pf_save_state after 37 steps, pf_load_state into a fresh handle, 40
+    more steps: every field, the particle and the time equal those of the
+    uninterrupted run bit for bit."""
+    c = W.wall_case((37, 52), seed=3) if walls else W.small_case((40, 56), seed=8, solid=True, u_amp=0.01)
+    parts = []
+    if with_particle:
+        parts = [dict(x=(20.3, 17.6), u=(0.01, -0.004), w=(0.0, 0.0, 0.002), R=6.0, rho_p=2.0)]
+        c["phi"] = (1.0 - W.disc(c["shape"], parts[0]["x"], 6.0, c["params"]["D"])) * c["phi"]
+    a, _ = run_pair(pf, c, 37, precision=precision, particles=parts, oracle=False, walls=walls)
+    state = a.save_state()
+    a.step(40)
+    b = pf.Sim(c["shape"], precision=precision, walls_y=walls, **c["params"])
+    for k, pp in enumerate(parts):
+        b.set_particle(k, **pp)
+    b.load_state(state)
+    assert b.time == 37
+    b.step(40)
+    assert b.time == a.time == 77
+    ma, mb = a.macros(), b.macros()
+    for k in FIELDS:
+        assert np.array_equal(ma[k], mb[k]), k
+    for k in range(len(parts)):
+        pa, pb = a.particle(k), b.particle(k)
+        for f in ("x", "u", "w", "F", "T"):
+            assert pa[f] == pb[f], f
+    # a state from another grid is refused
+    d = W.small_case((40, 48), seed=8)
+    e = pf.Sim(d["shape"], precision=precision, **d["params"])
+    with pytest.raises(pf.PfError):
+        e.load_state(state)
