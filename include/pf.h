@@ -50,7 +50,10 @@ extern "C" {
 #define PF_ECUDA (-3)    /* a CUDA runtime call failed */
 #define PF_ENUMERIC (-4) /* a non-finite phi or u appeared, or a 16-bit order-parameter
                             population was saturated (see pf_diag.nan_flag) */
-#define PF_ETIMEOUT (-5) /* a bounded device wait gave up (sticky: the handle's state is lost) */
+#define PF_ETIMEOUT (-5) /* a bounded device wait gave up (sticky: the handle's state is lost);
+                           the environment variable PF_WAIT_POLLS, read at create, sets the
+                           polls of one wait (fault injection: a tiny value makes the staged
+                           kernel 2 give up at once) */
 #define PF_ESTATE (-6)   /* call out of order (e.g. step before init) */
 
 /* ---- precision policies ---- */

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -466,12 +467,17 @@ struct Engine {
     static constexpr int CHUNK = 16;
     cudaGraphExec_t gexec = nullptr;
     int sticky = PF_OK;
+    // polls of one bounded device wait; 0: the kernels' default.  Read from the
+    // environment variable PF_WAIT_POLLS at create (fault injection: a tiny
+    // value makes the staged kernel's first wait give up -> PF_ETIMEOUT)
+    int wait_polls = 0;
 };
 
 static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
 {
     E.dim = g[0].dim;
     E.prec = p[0].precision;
+    if (const char *w = std::getenv("PF_WAIT_POLLS")) E.wait_polls = std::max(0, std::atoi(w));
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&E.nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -623,6 +629,7 @@ static StepArgs step_args(const Engine &E, int par)
     a.partials = E.d_partials;
     a.flags = E.d_flags;
     a.wv = E.wv;
+    a.wait_polls = E.wait_polls;
     return a;
 }
 

@@ -189,9 +189,10 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
     __syncthreads();
     if ((int)blockIdx.x < A.ntiles) stage_issue<P, TX, TY, NT>(A, blockIdx.x, s_rows, sbase, bar, tid);
     unsigned phase = 0;
+    const int polls = A.wait_polls > 0 ? A.wait_polls : STAGE_WAIT_POLLS;
 
     for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
-        const bool ok = mbar_wait_bounded(bar, phase, STAGE_WAIT_POLLS);
+        const bool ok = mbar_wait_bounded(bar, phase, polls);
         phase ^= 1u;
         // all threads agree; the barrier also ends the previous tile's
         // shared-memory reads before stage A rewrites the tiles

@@ -866,3 +866,25 @@ def test_checkpoint_resume_is_bit_identical(pf, precision, walls, with_particle)
     e = pf.Sim(d["shape"], precision=precision, **d["params"])
     with pytest.raises(pf.PfError):
         e.load_state(state)
+
+
+def test_bounded_wait_timeout_is_reported(pf, monkeypatch):
+    """A bounded device wait that runs out ends its kernel with PF_ETIMEOUT
+    instead of hanging: with PF_WAIT_POLLS=1 the staged kernel's first wait
+    on its bulk copies gives up (it still lets the copies in flight land), the
+    handle reports the sticky error, and a new handle works normally."""
+    c = W.small_case((32, 64), seed=1, solid=False)
+    monkeypatch.setenv("PF_WAIT_POLLS", "1")
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    monkeypatch.delenv("PF_WAIT_POLLS")
+    g.init(c["phi0"], c["phi"])
+    g.set_config(32, 16, 2)
+    g.step(1)
+    with pytest.raises(pf.PfError) as ei:
+        g.sync()
+    assert ei.value.code == pf.PF_ETIMEOUT
+    with pytest.raises(pf.PfError):
+        g.step(1)  # sticky
+    h, _ = run_pair(pf, c, 20, precision="fp16", oracle=False, config=(32, 16, 2))
+    h.sync()
+    assert h.diagnostics()["nan_flag"] == 0
