@@ -268,6 +268,25 @@ class Sim:
         return dict(phi=phi.reshape(sh), rho=rho.reshape(sh), u=u.reshape((self.dim,) + sh),
                     P=P.reshape(sh), mu=mu.reshape(sh))
 
+    def run_logged(self, n, every, path=None):
+        """Advance n steps, taking the FP64 diagnostics every ``every`` steps;
+        returns the records (dicts with t, mass, E_F, E_K, E_total, nan_flag)
+        and, with ``path``, appends each as one JSON line to that file."""
+        import json
+        recs = []
+        done = 0
+        while done < n:
+            k = min(every, n - done)
+            self.step(k)
+            done += k
+            d = self.diagnostics()
+            rec = dict(t=int(self.time), **{key: (float(v) if key != "nan_flag" else int(v)) for key, v in d.items()})
+            recs.append(rec)
+            if path:
+                with open(path, "a") as f:
+                    f.write(json.dumps(rec) + "\n")
+        return recs
+
     def save_state(self):
         """The run's state as bytes (pf_save_state)."""
         n = C.c_int64()

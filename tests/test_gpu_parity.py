@@ -888,3 +888,21 @@ def test_bounded_wait_timeout_is_reported(pf, monkeypatch):
     h, _ = run_pair(pf, c, 20, precision="fp16", oracle=False, config=(32, 16, 2))
     h.sync()
     assert h.diagnostics()["nan_flag"] == 0
+
+
+def test_run_logged_records_diagnostics(pf, tmp_path):
+    """The diagnostics log of a run: one JSON line per interval with the time
+    and the FP64 mass and energies, equal to the oracle's at those times."""
+    import json
+    c = W.small_case((40, 48), seed=4, solid=True, u_amp=0.01)
+    g, o = run_pair(pf, c, 0)
+    path = tmp_path / "diag.jsonl"
+    recs = g.run_logged(60, 20, str(path))
+    lines = [json.loads(x) for x in open(path)]
+    assert [r["t"] for r in lines] == [20, 40, 60] and lines == recs
+    for r in recs:
+        o.step(20)
+        do = o.diagnostics()
+        for k in ("mass", "E_F", "E_K", "E_total"):
+            assert abs(r[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, (r["t"], k)
+        assert r["nan_flag"] == 0
