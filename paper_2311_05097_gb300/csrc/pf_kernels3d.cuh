@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
     __shared__ int s_gy[TY + 6];   // wrapped row offsets y * pitch
     __shared__ int s_gyi[TY + 6];  // wrapped rows
     __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
-    __shared__ double s_red[NT / 32][6];
+    __shared__ double s_red[2][NT / 32][6];  // warps' sums, double-buffered over particles
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -704,10 +704,12 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     for (int k = 0; k < A.np; ++k) {
                         const ParticleDev &pp = A.parts[k];
                         double c6[6] = {0, 0, 0, 0, 0, 0};
+                        bool hit = false;
                         if (valid) {
                             R rx, ry, rz;
                             const R pk = particle_phi0_3d<R>(pp, gx, gy, z, nx, nyw, nz, p.D, p.cut, rx, ry, rz);
                             if (pk != R(0)) {
+                                hit = true;
                                 const R vx = (R)pp.u[0] + (R)pp.w[1] * rz - (R)pp.w[2] * ry;
                                 const R vy = (R)pp.u[1] + (R)pp.w[2] * rx - (R)pp.w[0] * rz;
                                 const R vz = (R)pp.u[2] + (R)pp.w[0] * ry - (R)pp.w[1] * rx;
@@ -721,22 +723,28 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                                 c6[5] = -((double)rx * fy - (double)ry * fx);
                             }
                         }
+                        // warp shuffle tree (skipped by warps whose terms are all 0),
+                        // warps in order; one barrier per particle and plane (the
+                        // buffer written here is next written after another barrier)
+                        const bool wany = __any_sync(0xffffffffu, hit);
+                        double(*red)[6] = s_red[k & 1];
 #pragma unroll
                         for (int c = 0; c < 6; ++c) {
                             double v = c6[c];
+                            if (wany) {
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                            if ((tid & 31) == 0) s_red[tid >> 5][c] = v;
+                                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                            }
+                            if ((tid & 31) == 0) red[tid >> 5][c] = v;
                         }
                         __syncthreads();
                         if (tid < 6) {
                             // per tile and plane: partial sums accumulate over the z loop in order
                             double acc = 0.0;
-                            for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[wq][tid];
+                            for (int wq = 0; wq < NT / 32; ++wq) acc += red[wq][tid];
                             double *dst = A.partials + ((long long)t * A.np + k) * 6 + tid;
                             *dst = (z == z0 ? 0.0 : *dst) + acc;
                         }
-                        __syncthreads();
                     }
                 }
             }
