@@ -262,13 +262,16 @@ int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int
  * (for benchmarks and tests of one configuration; no counterpart in the
  * paper).  tile_x x tile_y cells per tile; ctas_per_sm 0 = as many as fit,
  * else a cap.  kernel:
- *   0  one cell per thread (all policies, particles; 2D tiles 32x8, 64x4,
- *      32x16; 3D the tile of its policy);
+ *   0  one cell per thread (all policies, particles, walls, either
+ *      order-parameter lattice; 2D tiles 32x8, 64x4, 32x16; 3D the tile
+ *      of its policy);
  *   1  2D, two vertically adjacent cells per thread in packed FP32
- *      arithmetic (P32 and PMIX, fixed solids; tiles 32x16, 64x8, 32x32);
+ *      arithmetic (P32 and PMIX, fixed solids, no walls, either lattice;
+ *      tiles 32x16, 64x8, 32x32);
  *   2  as 1, with each tile's inputs copied into shared memory by
  *      asynchronous bulk copies one tile ahead (tile 32x16; every nx a
- *      multiple of 8 for 16-bit storage, of 4 for FP32).
+ *      multiple of 8 for 16-bit storage, of 4 for FP32; the Cahn-Hilliard
+ *      lattice only).
  * Adding a particle later falls back to kernel 0.  PF_EINVAL for a
  * configuration that is not built or not allowed; a pending odd time step is
  * issued first.  Call after init (pf_set_config) or at any time between steps
