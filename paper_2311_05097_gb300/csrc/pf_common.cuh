@@ -271,6 +271,8 @@ __device__ __forceinline__ float stored_to_float(S q);
 template <>
 __device__ __forceinline__ float stored_to_float<__half>(__half q) { return __half2float(q); }
 template <>
+__device__ __forceinline__ float stored_to_float<float>(float q) { return q; }
+template <>
 __device__ __forceinline__ float stored_to_float<__nv_bfloat16>(__nv_bfloat16 q)
 {
     return __bfloat162float(q);

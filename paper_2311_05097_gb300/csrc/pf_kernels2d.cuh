@@ -555,7 +555,6 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
         if constexpr (MOVING) {
             for (int k = 0; k < A.np; ++k) {
                 if (!((near >> k) & 1ull)) continue;
-                const ParticleDev &pp = A.parts[k];
                 R rx, ry;
                 const R pk = pphi0(k, lx + 3, ly + 3, gx, gy, rx, ry);
                 if (pk != R(0)) {
@@ -718,7 +717,6 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 // F_f = -sum rho phi0_k (u_s,k - u*), T_f = -sum r x (...)
                 int nred = 0;  // reductions so far in this tile: picks the s_red buffer
                 for (int k = 0; k < A.np; ++k) {
-                    const ParticleDev &pp = A.parts[k];
                     if (!((near >> k) & 1ull)) {
                         // no cell of this tile is reached by particle k
                         if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
         const AX *ph0 = reinterpret_cast<const AX *>(Dm.phi0);
         const long long *rs = reinterpret_cast<const long long *>(Dm.rest[A.par]);
         long long *rd = reinterpret_cast<long long *>(Dm.rest[A.par ^ 1]);
-        const float isc1 = kp.inv_scale[0], isc2 = kp.inv_scale[1];
+        const float isc1 = kp.inv_scale[0];
 
         // phi at frame cell (hx, hy) of the tile+2 frame: pull and sum (Eq. 31)
         auto phi_ring = [&](int hx, int hy) -> float {
