@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--config", type=int, nargs=4, default=None,
                     metavar=("TILE_X", "TILE_Y", "KERNEL", "CTAS_PER_SM"),
-                    help="fix the batch launch configuration instead of autotuning it")
+                    help="fix the launch configuration instead of autotuning it")
     ap.add_argument("--phase-model", type=int, default=0, choices=[0, 1],
                     help="order parameter: 0 Cahn-Hilliard (the paper's), 1 conservative Allen-Cahn")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -436,6 +436,13 @@ def run_batch(args, dist, rank, world, local):
                 kernel="k_step2d_pair" if cpt else "k_step2d", launch_config=[tx, ty, cpt])
 
 
+def step_kernel_name(dim, variant):
+    """The step kernel(s) of a launch variant (the roofline's dominant kernel)."""
+    if dim == 3:
+        return "k_step3d"
+    return ["k_step2d", "k_step2d_pair", "k_step2d_stage", "k_step2d_pair+k_step2d"][variant]
+
+
 def run_single(args, dist, rank, world, local):
     import numpy as np
     import ctypes as C
@@ -455,8 +462,16 @@ def run_single(args, dist, rank, world, local):
     for k, pp in enumerate(case.get("particles", [])):
         sim.set_particle(k, **pp)
     sim.init(case["phi0"], case["phi"], case.get("u"))
+    if args.config:
+        sim.set_config(*args.config)
+    else:
+        sim.step(256)  # untimed: the first call of >= 256 steps runs the launch-configuration autotuner
+    tx, ty, cps, kern = sim.config()
+    launch = {"tile": [tx, ty], "ctas_per_sm": cps, "kernel": kern,
+              "kernel_desc": ["one cell per thread", "two cells per thread", "two cells per thread, staged",
+                              "near tiles one cell, far tiles two cells per thread"][kern]}
     if not in_l2:
-        return run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream)
+        return run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream, launch)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     scrub = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -537,14 +552,14 @@ def run_single(args, dist, rank, world, local):
     sim.close()
     cfg = {"workload": args.workload, "cells": cells, "precision": prec, "desc": case["desc"],
            "l2": "flushed between timed steps: 512 MiB write, then a 256 MiB read so the "
-                 "write-back happens outside the timed step",
+                 "write-back happens outside the timed step", **launch,
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
                 clk=clk, launches=launches, e2e=e2e, t_wall=t_wall,
-                kernel="k_step3d" if dim == 3 else "k_step2d")
+                kernel=step_kernel_name(dim, launch["kernel"]))
 
 
-def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream):
+def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream, launch):
     """A single domain whose state exceeds L2: K steps timed together (graph
     replay), no flush needed."""
     import ctypes as C
@@ -575,7 +590,7 @@ def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim
     if dist:
         dist.barrier()
     mlups = whole_job_mlups(cells, args.steps, world, total_ms)
-    nker = 2 if case.get("particles") else 1
+    nker = round(launches / args.steps)
     achieved = bpc * cells / (total_ms * 1e-3 / args.steps) / 1e9
     e2e = None
     if not args.no_e2e:
@@ -612,10 +627,10 @@ def run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim
                        % (", u" if u_h is not None else "", S)}
     sim.close()
     cfg = {"workload": args.workload, "cells": cells, "precision": prec, "desc": case["desc"],
-           "l2": "state (%.2f GB) larger than L2 (129 MB); no flush" % (cells * bpc / 1e9),
+           "l2": "state (%.2f GB) larger than L2 (129 MB); no flush" % (cells * bpc / 1e9), **launch,
            "kernels_per_step": nker,
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
-    kernel = "k_step3d" if len(case["shape"]) == 3 else "k_step2d"
+    kernel = step_kernel_name(len(case["shape"]), launch["kernel"])
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
                 clk=clk, launches=launches, e2e=e2e, t_wall=t_wall, kernel=kernel)
 

@@ -271,13 +271,23 @@ int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int
  *   2  as 1, with each tile's inputs copied into shared memory by
  *      asynchronous bulk copies one tile ahead (tile 32x16; every nx a
  *      multiple of 8 for 16-bit storage, of 4 for FP32; the Cahn-Hilliard
- *      lattice only).
+ *      lattice only);
+ *   3  2D with free particles: the tiles out of every particle's reach run
+ *      kernel 1 (with the fixed solids' mu_phi0 grad phi0 of Eq. 19), the
+ *      others kernel 0, chosen on the device each step (one domain, P32 or
+ *      PMIX, tile 32x16, no walls, the Cahn-Hilliard lattice, no particle
+ *      with its own contact angle; giving one its own angle later falls back
+ *      to kernel 0).
  * Adding a particle later falls back to kernel 0.  PF_EINVAL for a
  * configuration that is not built or not allowed; a pending odd time step is
  * issued first.  Call after init (pf_set_config) or at any time between steps
  * (pf_batch_set_config). */
 int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int kernel, int ctas_per_sm);
 int pf_set_config(pf_handle *h, int tile_x, int tile_y, int kernel, int ctas_per_sm);
+/* The launch configuration of a single simulation, as pf_batch_config: -1
+ * until a step call of at least 256 steps has run the autotuner or
+ * pf_set_config has fixed it. */
+int pf_get_config(pf_handle *h, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel);
 void pf_batch_destroy(pf_batch *b);
 
 /* ---- diagnostics without device allocation ----

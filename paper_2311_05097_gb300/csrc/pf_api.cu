@@ -436,7 +436,12 @@ struct Engine {
     int2 *d_txy = nullptr;
     int ntiles = 0;
     int tx = 32, ty = 8, cps = 0, grid = 0;  // tile shape, CTAs per SM, grid size
-    int variant = 0;                         // 2D: 0 one cell per thread, 1 two, 2 two + staging
+    int variant = 0;                         // 2D: 0 one cell per thread, 1 two, 2 two + staging,
+                                             // 3 particle domain split: near tiles 0, far tiles 1
+    int *d_lists = nullptr;                  // variant 3: near / far tile lists (2 x ntiles) ...
+    int *d_counts = nullptr;                 // ... and their lengths
+    int lists_cap = 0;
+    int grid_far = 0;                        // variant 3: grid of the far-tile launch
     bool forced = false;                     // launch configuration set by the caller
     bool tuned = false;
     int nsm = 0;
@@ -521,6 +526,8 @@ static void engine_free(Engine &E)
     if (E.d_parts) cudaFree(E.d_parts);
     if (E.d_frep) cudaFree(E.d_frep);
     if (E.d_partials) cudaFree(E.d_partials);
+    if (E.d_lists) cudaFree(E.d_lists);
+    if (E.d_counts) cudaFree(E.d_counts);
     if (E.own_stream && E.stream) cudaStreamDestroy(E.stream);
     E = Engine{};
 }
@@ -596,7 +603,17 @@ static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, cons
 
 static int step_mode(const Engine &E)
 {
+    // (variant 3: the single-cell launch of the near tiles; the far tiles are
+    // launched beside it in issue_step)
     return E.variant == 2 ? MODE_STEP_STAGE : (E.variant == 1 ? MODE_STEP_PAIR : MODE_STEP);
+}
+
+// a particle domain whose far tiles the two-cells-per-thread step can run:
+// one 2D domain, FP32 or 16-bit storage, no walls, the Cahn-Hilliard lattice,
+// no particle with its own contact angle
+static bool split_ok(const Engine &E)
+{
+    return E.dim == 2 && E.np > 0 && !E.wv && E.prec != PF_P64 && E.mem.size() == 1 && !any_walls(E) && !any_cac(E);
 }
 
 // the staged 2D step copies 16-byte chunks: every domain's nx must keep its
@@ -637,8 +654,22 @@ static StepArgs step_args(const Engine &E, int par)
 static int issue_step(Engine &E, int par)
 {
     const StepArgs a = step_args(E, par);
-    if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a))
+    if (E.variant == 3) {
+        // tiles out of every particle's reach run the two-cells-per-thread
+        // step (with the fixed solids' mu_phi0 grad phi0), the others the
+        // single-cell step with the particle terms
+        launch_split_tiles(a, E.tx, E.ty, E.d_lists, E.d_counts, E.stream);
+        StepArgs af = a, an = a;
+        af.tile_list = E.d_lists + E.ntiles;
+        af.tile_count = E.d_counts + 1;
+        an.tile_list = E.d_lists;
+        an.tile_count = E.d_counts;
+        if (!launch_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0, E.grid_far, af) ||
+            !launch_any(E, E.tx, E.ty, MODE_STEP, E.grid, an))
+            return fail(PF_EINVAL, "split step of tile shape %dx%d not built", E.tx, E.ty);
+    } else if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a)) {
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
+    }
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.d_frep, E.mem[0].d.nx,
                                E.mem[0].d.ny, E.mem[0].d.nz, E.mem[0].d.wall_y, E.stream);
@@ -654,6 +685,21 @@ static int grid_of(Engine &E, int cps)
     long long g = (long long)c * E.nsm;
     if (g > E.ntiles) g = E.ntiles;
     return (int)std::max(1LL, g);
+}
+
+// variant 3: tile lists and the far-tile grid (before any graph capture)
+static int split_setup(Engine &E)
+{
+    if (E.lists_cap < 2 * E.ntiles) {
+        if (E.d_lists) cudaFree(E.d_lists);
+        E.d_lists = nullptr;
+        CK(cudaMalloc(&E.d_lists, sizeof(int) * 2 * (size_t)E.ntiles));
+        E.lists_cap = 2 * E.ntiles;
+    }
+    if (!E.d_counts) CK(cudaMalloc(&E.d_counts, sizeof(int) * 2));
+    const int occ = std::max(1, occupancy_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0));
+    E.grid_far = (int)std::max(1LL, std::min((long long)occ * E.nsm, (long long)E.ntiles));
+    return PF_OK;
 }
 
 // Autotuner: time a few steps of each compiled tile shape and CTAs-per-SM
@@ -675,11 +721,16 @@ static int engine_configure(Engine &E)
         if (it != g_tune_cache.end()) {
             int tx, ty, var, cps;
             std::tie(tx, ty, var, cps) = it->second;
+            if (var == 3 && !split_ok(E)) var = 0;
             int rc = engine_tiles(E, tx, ty);
             if (rc) return rc;
             E.variant = var;
             E.cps = cps;
             E.grid = grid_of(E, cps);
+            if (var == 3) {
+                rc = split_setup(E);
+                if (rc) return rc;
+            }
             E.tuned = true;
             return PF_OK;
         }
@@ -690,6 +741,14 @@ static int engine_configure(Engine &E)
     // pf_set_config but not a candidate: it measured slower than kernel 1)
     int shapes[6][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}};
     int nshapes = (E.prec != PF_P64 && E.np == 0 && !any_walls(E)) ? 6 : 3;
+    if (split_ok(E)) {
+        // particle domain: also the split of near (single-cell) and far
+        // (two-cells-per-thread) tiles
+        shapes[3][0] = 32;
+        shapes[3][1] = 16;
+        shapes[3][2] = 3;
+        nshapes = 4;
+    }
     if (E.dim == 3) {
         tile_shape3d(E.prec, &shapes[0][0], &shapes[0][1]);
         shapes[0][2] = 0;
@@ -706,6 +765,10 @@ static int engine_configure(Engine &E)
         int rc = engine_tiles(E, sh[0], sh[1]);
         if (rc) return rc;
         E.variant = sh[2];
+        if (E.variant == 3) {
+            rc = split_setup(E);
+            if (rc) return rc;
+        }
         const int occ = std::max(1, occupancy_any(E, sh[0], sh[1], step_mode(E)));
         for (int cps = 1; cps <= occ; cps = cps < occ ? std::min(cps * 2, occ) : occ + 1) {
             E.cps = cps;
@@ -744,6 +807,10 @@ static int engine_configure(Engine &E)
     E.variant = bv;
     E.cps = bc;
     E.grid = grid_of(E, bc);
+    if (bv == 3) {
+        rc = split_setup(E);
+        if (rc) return rc;
+    }
     E.tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = std::make_tuple(bx, by, bv, bc);
@@ -1252,6 +1319,13 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         for (int j = 0; j < E.np; ++j) wv |= E.hp[j].own;
         if (wv != E.wv) drop_graph(E);  // the step arguments change
         E.wv = wv;
+        if (E.variant == 3 && !split_ok(E)) {  // own angles: the far tiles need W and V
+            E.variant = 0;
+            int rc0 = engine_tiles(E, E.tx, E.ty);
+            if (rc0) return rc0;
+            E.grid = grid_of(E, E.cps);
+            drop_graph(E);
+        }
         int rc = upload_particles(E);
         if (rc) return rc;
         if (grew) {
@@ -1369,21 +1443,26 @@ extern "C" int64_t pf_batch_cells(pf_batch *b)
     return c;
 }
 
+static int engine_config(const Engine &E, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel)
+{
+    const bool t = E.tuned;
+    if (tile_x) *tile_x = t ? E.tx : -1;
+    if (tile_y) *tile_y = t ? E.ty : -1;
+    if (ctas_per_sm) *ctas_per_sm = t ? E.cps : -1;
+    if (kernel) *kernel = t ? E.variant : -1;
+    return PF_OK;
+}
+
 extern "C" int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel)
 {
     if (!b) return fail(PF_EINVAL, "batch is NULL");
-    if (!b->E.tuned) {
-        if (tile_x) *tile_x = -1;
-        if (tile_y) *tile_y = -1;
-        if (ctas_per_sm) *ctas_per_sm = -1;
-        if (kernel) *kernel = -1;
-        return PF_OK;
-    }
-    if (tile_x) *tile_x = b->E.tx;
-    if (tile_y) *tile_y = b->E.ty;
-    if (ctas_per_sm) *ctas_per_sm = b->E.cps;
-    if (kernel) *kernel = b->E.variant;
-    return PF_OK;
+    return engine_config(b->E, tile_x, tile_y, ctas_per_sm, kernel);
+}
+
+extern "C" int pf_get_config(pf_handle *h, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel)
+{
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    return engine_config(h->E, tile_x, tile_y, ctas_per_sm, kernel);
 }
 
 // fixed launch configuration (skips the autotuner)
@@ -1391,17 +1470,20 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
 {
     if (E.sticky) return E.sticky;
     const int var = kernel;
-    if (var < 0 || var > 2) return fail(PF_EINVAL, "kernel must be 0, 1 or 2");
+    if (var < 0 || var > 3) return fail(PF_EINVAL, "kernel must be 0, 1, 2 or 3");
+    if (var == 3 && (!split_ok(E) || tile_x != 32 || tile_y != 16))
+        return fail(PF_EINVAL, "kernel 3 (near tiles single-cell, far tiles two-cells) needs one 2D particle "
+                               "domain in FP32 or 16-bit storage without walls, own angles or the Allen-Cahn "
+                               "lattice, and 32x16 tiles");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
     if (var != 0 && any_walls(E))
         return fail(PF_EINVAL, "domains with walls run kernel 0 only");
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);
-    const int mode = var == 2 ? MODE_STEP_STAGE : (var ? MODE_STEP_PAIR : MODE_STEP);
-    E.variant = var;
-    if (occupancy_any(E, tile_x, tile_y, mode) < 1) {
-        E.variant = 0;
+    const int mode = var == 2 ? MODE_STEP_STAGE : (var == 1 ? MODE_STEP_PAIR : MODE_STEP);
+    if (occupancy_any(E, tile_x, tile_y, mode) < 1 ||
+        (var == 3 && occupancy_any(E, tile_x, tile_y, MODE_STEP_PAIR | MODE_MU0) < 1)) {
         return fail(PF_EINVAL, "launch configuration %dx%d of kernel %d is not built for this precision / "
                     "particle setting", tile_x, tile_y, var);
     }
@@ -1411,10 +1493,15 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
         E.par ^= 1;
         E.t++;
     }
+    E.variant = var;
     int rc = engine_tiles(E, tile_x, tile_y);
     if (rc) return (E.sticky = rc);
     E.cps = ctas_per_sm;
     E.grid = grid_of(E, ctas_per_sm);
+    if (var == 3) {
+        rc = split_setup(E);
+        if (rc) return (E.sticky = rc);
+    }
     E.tuned = true;
     E.forced = true;
     return PF_OK;

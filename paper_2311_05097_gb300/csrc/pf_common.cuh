@@ -30,6 +30,9 @@ constexpr int MODE_EXT = 16;
 // or'ed into a 2D mode: the launch holds an Allen-Cahn domain (the
 // two-cells-per-thread kernels' instantiation that handles it)
 constexpr int MODE_CAC = 32;
+// or'ed into MODE_STEP_PAIR: the launch runs the far tiles of a particle domain
+// (the fixed solids' mu_phi0 grad phi0 term is on)
+constexpr int MODE_MU0 = 64;
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {
@@ -192,6 +195,8 @@ struct StepArgs {
     int *flags;            // [0]: non-finite value seen
     int wv;                // some particle has its own contact angle (W, V fields)
     int wait_polls;        // polls of one bounded device wait (staged kernel); 0: default
+    const int *tile_list;  // optional: the tiles to run (indices into the tile table) ...
+    const int *tile_count; // ... and their number, both in device memory (else all ntiles)
 };
 
 // ---- helpers -----------------------------------------------------------------------------------

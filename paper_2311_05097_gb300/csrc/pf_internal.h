@@ -44,6 +44,8 @@ void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, 
                  const double *Pin, double *tmp, const ParticleDev *parts, int np, int wv, cudaStream_t s);
 int diag_blocks();
 void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cudaStream_t s);
+// near / far tile lists of a particle domain (single-cell / two-cells step)
+void launch_split_tiles(const StepArgs &a, int tx, int ty, int *lists, int *counts, cudaStream_t s);
 // interface normal (dim planes of N) from Dm.macro's phi plane
 void launch_normal(const DomainDev &Dm, double *n, cudaStream_t s);
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,

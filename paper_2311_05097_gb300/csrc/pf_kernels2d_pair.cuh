@@ -174,8 +174,10 @@ __device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*
 // at (wx, wy)) and the values gathered in stage A, then their stores.  racc:
 // PMIX, each cell's exact fixed-point phi (rest + images of the pulled movers).
 // CAC: the instantiation also serves domains with the conservative Allen-Cahn
-// order parameter (checked per domain)
-template <class P, int FX, int WX, bool CAC = false>
+// order parameter (checked per domain).  MU0: the simulation holds free
+// particles, so the force carries mu_phi0 grad phi0 (Eq. 19) of the fixed
+// solids too (the tiles this kernel gets are out of every particle's reach).
+template <class P, int FX, int WX, bool CAC = false, bool MU0 = false>
 __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p, const KParams<float> &kp,
                                            const float (*s_phi)[FX], const float (*s_p0)[FX],
                                            const float (*s_mu)[WX], const float (*s_w)[WX], int hx, int hy,
@@ -214,8 +216,18 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     const F2 Sy = cac ? Mdrho * (gpy - tny) : Mdrho * gmy;
     const F2 grx = drho * gpx, gry = drho * gpy;
     // F = mu grad phi + F_b + F_c, F_c = (-d_y w, d_x w)/2 from the previous step
-    const F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
-    const F2 Fy = fma2(mu, gpy, fma2(half, wgx, mk2(kp.Fb[1])));
+    F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
+    F2 Fy = fma2(mu, gpy, fma2(half, wgx, mk2(kp.Fb[1])));
+    if constexpr (MU0) {
+        const F2 lphi = lap9_pair<FX>(s_phi, hx, hy);
+        F2 g0x, g0y;
+        grad9_pair<FX>(s_p0, hx, hy, g0x, g0y);
+        const F2 mu0 = fma2(mk2(kp.c_pen) * phi0, phi * phi,
+                            fma2(mk2(kp.c_wet) * phi, fma2(mk2(3.0f) * phi0, phi0, phi * phi - one),
+                                 mk2(-kp.c_wlap) * lphi));
+        Fx = fma2(mu0, g0x, Fx);
+        Fy = fma2(mu0, g0y, Fy);
+    }
 
     F2 f2[9];
     const F2 isc2v = mk2(kp.inv_scale[1]);
@@ -364,7 +376,7 @@ constexpr int step2d_pair_min_blocks()
     return TX * TYP > 256 ? 1 : 2;
 }
 
-template <class P, int TX, int TYP, bool CAC>
+template <class P, int TX, int TYP, bool CAC, bool MU0 = false>
 __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) k_step2d_pair(StepArgs A)
 {
     using ST = typename P::store;
@@ -384,7 +396,9 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly0 = 2 * (tid / TX);  // first of the thread's two rows
 
-    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int nlist = A.tile_list ? *A.tile_count : A.ntiles;
+    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
+        const int t = A.tile_list ? A.tile_list[it] : it;
         const DomainDev &Dm = A.doms[A.tile_dom[t]];
         const int2 txy = A.tile_xy[t];
         const int nx = Dm.nx, ny = Dm.ny;
@@ -537,7 +551,7 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
         {
             const int gx = x0 + lx, gy0 = y0 + ly0;
             const bool valid0 = gx < nx && gy0 < ny, valid1 = gx < nx && gy0 + 1 < ny;
-            pair_cells<P, FX, WX, CAC>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, racc,
+            pair_cells<P, FX, WX, CAC, MU0>(A, p, kp, s_phi, s_p0, s_mu, s_w, hx, hy, lx + 1, ly0 + 1, phi, f1, f2raw, lag, racc,
                                   id, valid0, valid1, fd, rd, ad, plane);
         }
     }

@@ -408,6 +408,53 @@ __global__ void k_normal(DomainDev Dm, double *n)
     }
 }
 
+// Split of a particle domain's tiles (tx x ty cells) into those some
+// particle's indicator may reach (the same conservative test as the
+// single-cell step: its tile + 2 frame against R + cut + 1, minimum image)
+// and the rest: near tiles at lists[0 ..), far ones at lists[ntiles ..),
+// their numbers in counts[0], counts[1].  The far tiles' force partials are
+// zeroed here (the step that runs them computes none).  One block.
+__global__ void k_split_tiles(StepArgs A, int tx, int ty, int *lists, int *counts)
+{
+    __shared__ int cnear, cfar;
+    if (threadIdx.x == 0) cnear = cfar = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < A.ntiles; t += blockDim.x) {
+        const DomainDev &Dm = A.doms[A.tile_dom[t]];
+        const int2 txy = A.tile_xy[t];
+        const int nx = Dm.nx, ny = Dm.ny;
+        const int x0 = txy.x * tx, y0 = txy.y * ty;
+        bool near = false;
+        for (int k = 0; k < A.np && !near; ++k) {
+            const ParticleDev &pp = A.parts[k];
+            double dx = (x0 + 0.5 * (tx - 1)) - pp.x[0], dy = (y0 + 0.5 * (ty - 1)) - pp.x[1];
+            dx -= nx * rint(dx / nx);
+            dy -= ny * rint(dy / ny);
+            const double ex = fmax(fabs(dx) - (0.5 * tx + 2.0), 0.0);
+            const double ey = fmax(fabs(dy) - (0.5 * ty + 2.0), 0.0);
+            const double lim = pp.R + Dm.p.cut + 1.0;
+            near = ex * ex + ey * ey < lim * lim;
+        }
+        if (near) {
+            lists[atomicAdd(&cnear, 1)] = t;
+        } else {
+            lists[A.ntiles + atomicAdd(&cfar, 1)] = t;
+            for (int c = 0; c < 6 * A.np; ++c) A.partials[(long long)t * A.np * 6 + c] = 0.0;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        counts[0] = cnear;
+        counts[1] = cfar;
+    }
+}
+
+void launch_split_tiles(const StepArgs &a, int tx, int ty, int *lists, int *counts, cudaStream_t s)
+{
+    k_split_tiles<<<1, 1024, 0, s>>>(a, tx, ty, lists, counts);
+    count_launches(1);
+}
+
 __global__ void k_diag_final(const double *partial, int nblocks, double *out)
 {
     __shared__ double red[256][3];

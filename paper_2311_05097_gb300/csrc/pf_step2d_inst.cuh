@@ -24,10 +24,10 @@ static bool run2d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
     return true;
 }
 
-template <class P, int TX, int TYP, bool CAC>
+template <class P, int TX, int TYP, bool CAC, bool MU0 = false>
 static bool run2d_pair(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
-    auto kern = k_step2d_pair<P, TX, TYP, CAC>;
+    auto kern = k_step2d_pair<P, TX, TYP, CAC, MU0>;
     if (occ) {
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TYP, 0) != cudaSuccess) n = 0;
@@ -41,12 +41,14 @@ static bool run2d_pair(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 
 // two cells per thread: tiles of tx x ty cells on tx x ty/2 threads
 template <class P>
-static bool dispatch2d_pair(int tx, int ty, bool moving, bool cac, int grid, cudaStream_t s, const StepArgs &a,
-                            int *occ)
+static bool dispatch2d_pair(int tx, int ty, bool moving, bool cac, bool mu0, int grid, cudaStream_t s,
+                            const StepArgs &a, int *occ)
 {
     if constexpr (P::id == 0) {
         return false;  // FP64 has no packed arithmetic
     } else {
+        // far tiles of a particle domain: 32 x 16, Cahn-Hilliard
+        if (mu0) return tx == 32 && ty == 16 && !cac && run2d_pair<P, 32, 8, false, true>(grid, s, a, occ);
         if (moving) return false;
         if (tx == 32 && ty == 16)
             return cac ? run2d_pair<P, 32, 8, true>(grid, s, a, occ) : run2d_pair<P, 32, 8, false>(grid, s, a, occ);
@@ -118,10 +120,10 @@ template <class P>
 static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
                        const StepArgs &a, int *occ)
 {
-    const bool ext = (mode & MODE_EXT) != 0, cac = (mode & MODE_CAC) != 0;
-    mode &= ~(MODE_EXT | MODE_CAC);
+    const bool ext = (mode & MODE_EXT) != 0, cac = (mode & MODE_CAC) != 0, mu0 = (mode & MODE_MU0) != 0;
+    mode &= ~(MODE_EXT | MODE_CAC | MODE_MU0);
     // (the library never asks the two-cells-per-thread kernels for walls)
-    if (mode == MODE_STEP_PAIR) return dispatch2d_pair<P>(tx, ty, moving, cac, grid, s, a, occ);
+    if (mode == MODE_STEP_PAIR) return dispatch2d_pair<P>(tx, ty, moving, cac, mu0, grid, s, a, occ);
     if (mode == MODE_STEP_STAGE) return !ext && !cac && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
     return ext ? dispatch2d_single<P, true>(tx, ty, moving, mode, grid, s, a, occ)
                : dispatch2d_single<P, false>(tx, ty, moving, mode, grid, s, a, occ);

@@ -101,6 +101,8 @@ def load(build_if_missing=False):
         "pf_batch_diagnostics": (C.c_int, [vp, C.c_int, C.POINTER(pf_diag)]),
         "pf_batch_sync": (C.c_int, [vp]),
         "pf_batch_cells": (C.c_int64, [vp]),
+        "pf_get_config": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int)]),
         "pf_batch_config": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
         "pf_batch_set_config": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int]),
@@ -239,8 +241,14 @@ class Sim:
         _check(load().pf_init_fields(self._h, *[k[0] for k in keep], where))
 
     def set_config(self, tile_x, tile_y, kernel=0, ctas_per_sm=0):
-        """Fix the launch configuration (after init); kernel 0, 1 or 2 as in pf.h."""
+        """Fix the launch configuration (after init); kernel 0, 1, 2 or 3 as in pf.h."""
         _check(load().pf_set_config(self._h, int(tile_x), int(tile_y), int(kernel), int(ctas_per_sm)))
+
+    def config(self):
+        """(tile_x, tile_y, ctas_per_sm, kernel) of the step launches; -1 before tuning."""
+        a, b, c, d = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(load().pf_get_config(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return a.value, b.value, c.value, d.value
 
     def step(self, n=1):
         _check(load().pf_step(self._h, int(n)))

@@ -906,3 +906,59 @@ def test_run_logged_records_diagnostics(pf, tmp_path):
         for k in ("mass", "E_F", "E_K", "E_total"):
             assert abs(r[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-300) + 1e-15, (r["t"], k)
         assert r["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3)])
+def test_split_particle_step_against_oracle(pf, precision, tol_phi):
+    """Launch variant 3 on a particle domain: the tiles out of every particle's
+    reach run the two-cells-per-thread step with the fixed solids'
+    mu_phi0 grad phi0 (Eq. 19), the others the single-cell step with the
+    particle terms.  Against the FP64 oracle and against variant 0 at the same
+    precision: fields and the particles' states after 200 steps."""
+    c = W.small_case((128, 96), seed=11, solid=True, theta_deg=60.0, u_amp=0.005)
+    parts = [dict(x=(40.3, 30.6), u=(0.01, -0.004), w=(0.0, 0.0, 0.002), R=6.0, rho_p=2.0),
+             dict(x=(95.0, 70.0), u=(-0.006, 0.003), R=5.0, rho_p=1.5)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], c["params"]["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 200, precision=precision, particles=parts, config=(32, 16, 3))
+    s, _ = run_pair(pf, c, 200, precision=precision, particles=parts, oracle=False, config=(32, 16, 0))
+    gm, om, sm = g.macros(), o.macros(), s.macros()
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    assert rel(gm["rho"], om["rho"]) < tol_phi
+    for k in ("u", "P"):
+        assert rel(gm[k], om[k]) < 100 * tol_phi, k
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(gm[k], sm[k]) < (tol if precision == "p32" else 10 * tol_phi), k
+    us = max(np.abs(om["u"]).max(), 1e-3)
+    for k in range(len(parts)):
+        pg, po, ps = g.particle(k), o.particle(k), s.particle(k)
+        assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() < 1e-3
+        assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() < 100 * tol_phi * us
+        assert np.abs(np.array(pg["u"]) - np.array(ps["u"])).max() < 100 * tol_phi * us
+    assert g.diagnostics()["nan_flag"] == 0
+
+
+def test_split_particle_step_rejected_where_not_built(pf):
+    c = W.small_case((64, 64), seed=1, solid=False)
+    part = dict(x=(20.0, 20.0), R=5.0, rho_p=2.0)
+    g = pf.Sim(c["shape"], precision="p64", **c["params"])
+    g.set_particle(0, **part)
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(32, 16, 3)  # FP64: no packed arithmetic
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(32, 16, 3)  # no particle
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    g.set_particle(0, **part)
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(32, 8, 3)  # 32 x 16 tiles only
+    g.set_config(32, 16, 3)
+    g.step(5)
+    g.set_particle(0, **dict(part, theta_deg=45.0))  # own angle: back to the single-cell step
+    g.step(5)
+    assert g.diagnostics()["nan_flag"] == 0
