@@ -438,10 +438,11 @@ struct Engine {
     int tx = 32, ty = 8, cps = 0, grid = 0;  // tile shape, CTAs per SM, grid size
     int variant = 0;                         // 2D: 0 one cell per thread, 1 two, 2 two + staging,
                                              // 3 particle domain split: near tiles 0, far tiles 1
-    int *d_lists = nullptr;                  // variant 3: near / far tile lists (2 x ntiles) ...
-    int *d_counts = nullptr;                 // ... and their lengths
-    int lists_cap = 0;
+    unsigned char *d_sel = nullptr;          // variant 3: per tile 1 near a particle, 0 far
+    int sel_cap = 0;
     int grid_far = 0;                        // variant 3: grid of the far-tile launch
+    cudaStream_t side = nullptr;             // variant 3: the near tiles run on this stream beside
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // the far ones (fork / join)
     bool forced = false;                     // launch configuration set by the caller
     bool tuned = false;
     int nsm = 0;
@@ -526,8 +527,10 @@ static void engine_free(Engine &E)
     if (E.d_parts) cudaFree(E.d_parts);
     if (E.d_frep) cudaFree(E.d_frep);
     if (E.d_partials) cudaFree(E.d_partials);
-    if (E.d_lists) cudaFree(E.d_lists);
-    if (E.d_counts) cudaFree(E.d_counts);
+    if (E.d_sel) cudaFree(E.d_sel);
+    if (E.ev_fork) cudaEventDestroy(E.ev_fork);
+    if (E.ev_join) cudaEventDestroy(E.ev_join);
+    if (E.side) cudaStreamDestroy(E.side);
     if (E.own_stream && E.stream) cudaStreamDestroy(E.stream);
     E = Engine{};
 }
@@ -658,21 +661,31 @@ static int issue_step(Engine &E, int par)
         // tiles out of every particle's reach run the two-cells-per-thread
         // step (with the fixed solids' mu_phi0 grad phi0), the others the
         // single-cell step with the particle terms
-        launch_split_tiles(a, E.tx, E.ty, E.d_lists, E.d_counts, E.stream);
+        launch_split_tiles(a, E.tx, E.ty, E.d_sel, E.stream);
         StepArgs af = a, an = a;
-        af.tile_list = E.d_lists + E.ntiles;
-        af.tile_count = E.d_counts + 1;
-        an.tile_list = E.d_lists;
-        an.tile_count = E.d_counts;
-        if (!launch_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0, E.grid_far, af) ||
-            !launch_any(E, E.tx, E.ty, MODE_STEP, E.grid, an))
-            return fail(PF_EINVAL, "split step of tile shape %dx%d not built", E.tx, E.ty);
+        af.tile_sel = an.tile_sel = E.d_sel;
+        af.sel = 0;
+        an.sel = 1;
+        // the two launches write disjoint tiles and read only the previous
+        // parity: the (short, latency-bound) near launch runs on a side
+        // stream beside the far one, joined before the particle update
+        CK(cudaEventRecord(E.ev_fork, E.stream));
+        CK(cudaStreamWaitEvent(E.side, E.ev_fork, 0));
+        cudaStream_t main = E.stream;
+        E.stream = E.side;
+        const bool ok_near = launch_any(E, E.tx, E.ty, MODE_STEP, E.grid, an);
+        E.stream = main;
+        CK(cudaEventRecord(E.ev_join, E.side));
+        const bool ok_far = launch_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0, E.grid_far, af);
+        CK(cudaStreamWaitEvent(E.stream, E.ev_join, 0));
+        if (!ok_near || !ok_far) return fail(PF_EINVAL, "split step of tile shape %dx%d not built", E.tx, E.ty);
     } else if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a)) {
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
     }
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.d_frep, E.mem[0].d.nx,
-                               E.mem[0].d.ny, E.mem[0].d.nz, E.mem[0].d.wall_y, E.stream);
+                               E.mem[0].d.ny, E.mem[0].d.nz, E.mem[0].d.wall_y,
+                               E.variant == 3 ? E.d_sel : nullptr, E.stream);
     CK(cudaGetLastError());
     return PF_OK;
 }
@@ -690,13 +703,15 @@ static int grid_of(Engine &E, int cps)
 // variant 3: tile lists and the far-tile grid (before any graph capture)
 static int split_setup(Engine &E)
 {
-    if (E.lists_cap < 2 * E.ntiles) {
-        if (E.d_lists) cudaFree(E.d_lists);
-        E.d_lists = nullptr;
-        CK(cudaMalloc(&E.d_lists, sizeof(int) * 2 * (size_t)E.ntiles));
-        E.lists_cap = 2 * E.ntiles;
+    if (E.sel_cap < E.ntiles) {
+        if (E.d_sel) cudaFree(E.d_sel);
+        E.d_sel = nullptr;
+        CK(cudaMalloc(&E.d_sel, (size_t)E.ntiles));
+        E.sel_cap = E.ntiles;
     }
-    if (!E.d_counts) CK(cudaMalloc(&E.d_counts, sizeof(int) * 2));
+    if (!E.side) CK(cudaStreamCreateWithFlags(&E.side, cudaStreamNonBlocking));
+    if (!E.ev_fork) CK(cudaEventCreateWithFlags(&E.ev_fork, cudaEventDisableTiming));
+    if (!E.ev_join) CK(cudaEventCreateWithFlags(&E.ev_join, cudaEventDisableTiming));
     const int occ = std::max(1, occupancy_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0));
     E.grid_far = (int)std::max(1LL, std::min((long long)occ * E.nsm, (long long)E.ntiles));
     return PF_OK;

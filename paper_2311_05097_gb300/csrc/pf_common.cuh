@@ -195,8 +195,8 @@ struct StepArgs {
     int *flags;            // [0]: non-finite value seen
     int wv;                // some particle has its own contact angle (W, V fields)
     int wait_polls;        // polls of one bounded device wait (staged kernel); 0: default
-    const int *tile_list;  // optional: the tiles to run (indices into the tile table) ...
-    const int *tile_count; // ... and their number, both in device memory (else all ntiles)
+    const unsigned char *tile_sel;  // optional, per tile in device memory: run only the tiles ...
+    int sel;                        // ... whose byte equals sel (else every tile)
 };
 
 // ---- helpers -----------------------------------------------------------------------------------

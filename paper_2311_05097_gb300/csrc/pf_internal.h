@@ -45,11 +45,11 @@ void launch_init(int prec, const DomainDev &Dm, int *flags, const double *phi0, 
 int diag_blocks();
 void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cudaStream_t s);
 // near / far tile lists of a particle domain (single-cell / two-cells step)
-void launch_split_tiles(const StepArgs &a, int tx, int ty, int *lists, int *counts, cudaStream_t s);
+void launch_split_tiles(const StepArgs &a, int tx, int ty, unsigned char *sel, cudaStream_t s);
 // interface normal (dim planes of N) from Dm.macro's phi plane
 void launch_normal(const DomainDev &Dm, double *n, cudaStream_t s);
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
                             const DevParams &p, double *frep, int nx, int ny, int nz, int wall_y,
-                            cudaStream_t s);
+                            const unsigned char *sel, cudaStream_t s);
 
 }  // namespace pf

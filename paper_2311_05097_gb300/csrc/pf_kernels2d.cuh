@@ -180,9 +180,8 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
 
-    const int nlist = A.tile_list ? *A.tile_count : A.ntiles;
-    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
-        const int t = A.tile_list ? A.tile_list[it] : it;
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+        if (A.tile_sel && A.tile_sel[t] != A.sel) continue;  // (uniform in the block)
         const DomainDev &Dm = A.doms[A.tile_dom[t]];
         const int2 txy = A.tile_xy[t];
         const int nx = Dm.nx, ny = Dm.ny;

@@ -396,9 +396,8 @@ __global__ void __launch_bounds__(TX *TYP, (step2d_pair_min_blocks<TX, TYP>())) 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly0 = 2 * (tid / TX);  // first of the thread's two rows
 
-    const int nlist = A.tile_list ? *A.tile_count : A.ntiles;
-    for (int it = blockIdx.x; it < nlist; it += gridDim.x) {
-        const int t = A.tile_list ? A.tile_list[it] : it;
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+        if (A.tile_sel && A.tile_sel[t] != A.sel) continue;  // (uniform in the block)
         const DomainDev &Dm = A.doms[A.tile_dom[t]];
         const int2 txy = A.tile_xy[t];
         const int nx = Dm.nx, ny = Dm.ny;

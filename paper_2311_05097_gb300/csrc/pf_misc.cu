@@ -410,48 +410,36 @@ __global__ void k_normal(DomainDev Dm, double *n)
 
 // Split of a particle domain's tiles (tx x ty cells) into those some
 // particle's indicator may reach (the same conservative test as the
-// single-cell step: its tile + 2 frame against R + cut + 1, minimum image)
-// and the rest: near tiles at lists[0 ..), far ones at lists[ntiles ..),
-// their numbers in counts[0], counts[1].  The far tiles' force partials are
-// zeroed here (the step that runs them computes none).  One block.
-__global__ void k_split_tiles(StepArgs A, int tx, int ty, int *lists, int *counts)
+// single-cell step: its tile + 2 frame against R + cut + 1, minimum image),
+// sel[t] = 1, and the rest, sel[t] = 0, whose force partials are zeroed here
+// (the step that runs them computes none).  One thread per tile.
+__global__ void k_split_tiles(StepArgs A, int tx, int ty, unsigned char *sel)
 {
-    __shared__ int cnear, cfar;
-    if (threadIdx.x == 0) cnear = cfar = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < A.ntiles; t += blockDim.x) {
-        const DomainDev &Dm = A.doms[A.tile_dom[t]];
-        const int2 txy = A.tile_xy[t];
-        const int nx = Dm.nx, ny = Dm.ny;
-        const int x0 = txy.x * tx, y0 = txy.y * ty;
-        bool near = false;
-        for (int k = 0; k < A.np && !near; ++k) {
-            const ParticleDev &pp = A.parts[k];
-            double dx = (x0 + 0.5 * (tx - 1)) - pp.x[0], dy = (y0 + 0.5 * (ty - 1)) - pp.x[1];
-            dx -= nx * rint(dx / nx);
-            dy -= ny * rint(dy / ny);
-            const double ex = fmax(fabs(dx) - (0.5 * tx + 2.0), 0.0);
-            const double ey = fmax(fabs(dy) - (0.5 * ty + 2.0), 0.0);
-            const double lim = pp.R + Dm.p.cut + 1.0;
-            near = ex * ex + ey * ey < lim * lim;
-        }
-        if (near) {
-            lists[atomicAdd(&cnear, 1)] = t;
-        } else {
-            lists[A.ntiles + atomicAdd(&cfar, 1)] = t;
-            for (int c = 0; c < 6 * A.np; ++c) A.partials[(long long)t * A.np * 6 + c] = 0.0;
-        }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.ntiles) return;
+    const DomainDev &Dm = A.doms[A.tile_dom[t]];
+    const int2 txy = A.tile_xy[t];
+    const int nx = Dm.nx, ny = Dm.ny;
+    const int x0 = txy.x * tx, y0 = txy.y * ty;
+    bool near = false;
+    for (int k = 0; k < A.np && !near; ++k) {
+        const ParticleDev &pp = A.parts[k];
+        double dx = (x0 + 0.5 * (tx - 1)) - pp.x[0], dy = (y0 + 0.5 * (ty - 1)) - pp.x[1];
+        dx -= nx * rint(dx / nx);
+        dy -= ny * rint(dy / ny);
+        const double ex = fmax(fabs(dx) - (0.5 * tx + 2.0), 0.0);
+        const double ey = fmax(fabs(dy) - (0.5 * ty + 2.0), 0.0);
+        const double lim = pp.R + Dm.p.cut + 1.0;
+        near = ex * ex + ey * ey < lim * lim;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        counts[0] = cnear;
-        counts[1] = cfar;
-    }
+    sel[t] = near ? 1 : 0;
+    if (!near)
+        for (int c = 0; c < 6 * A.np; ++c) A.partials[(long long)t * A.np * 6 + c] = 0.0;
 }
 
-void launch_split_tiles(const StepArgs &a, int tx, int ty, int *lists, int *counts, cudaStream_t s)
+void launch_split_tiles(const StepArgs &a, int tx, int ty, unsigned char *sel, cudaStream_t s)
 {
-    k_split_tiles<<<1, 1024, 0, s>>>(a, tx, ty, lists, counts);
+    k_split_tiles<<<(a.ntiles + 255) / 256, 256, 0, s>>>(a, tx, ty, sel);
     count_launches(1);
 }
 
@@ -546,15 +534,19 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
     for (int a = 0; a < 3; ++a) frep[3 * k + a] = acc[a];
 }
 
+// sel: optional per-tile flags; tiles with sel[t] == 0 hold zero partials
+// and are skipped (adding them would not change the sums)
 __global__ void k_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                                  DevParams p, const double *frep)
+                                  DevParams p, const double *frep, const unsigned char *sel)
 {
     const int k = blockIdx.x;
     if (k >= np) return;
     __shared__ double red[256][6];
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+        if (sel && !sel[t]) continue;
         for (int c = 0; c < 6; ++c) acc[c] += partials[((long long)t * np + k) * 6 + c];
+    }
     for (int c = 0; c < 6; ++c) red[threadIdx.x][c] = acc[c];
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -662,10 +654,11 @@ void launch_diag(const DomainDev &Dm, double *partial, double *out, int wv, cuda
 }
 
 void launch_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
-                            const DevParams &p, double *frep, int nx, int ny, int nz, int wall_y, cudaStream_t s)
+                            const DevParams &p, double *frep, int nx, int ny, int nz, int wall_y,
+                            const unsigned char *sel, cudaStream_t s)
 {
     k_particle_repulsion<<<1, 64, 0, s>>>(parts, np, p, nx, ny, nz, wall_y, frep);
-    k_particle_update<<<np, 256, 0, s>>>(parts, np, partials, ntiles, p, frep);
+    k_particle_update<<<np, 256, 0, s>>>(parts, np, partials, ntiles, p, frep, sel);
     count_launches(2);
 }
 
