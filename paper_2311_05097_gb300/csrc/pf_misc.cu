@@ -534,6 +534,9 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
     for (int a = 0; a < 3; ++a) frep[3 * k + a] = acc[a];
 }
 
+// One block per particle; each thread sums a fixed strided set of tiles, then
+// a fixed tree (the order depends only on the tile count).
+constexpr int UPDATE_THREADS = 512;
 // sel: optional per-tile flags; tiles with sel[t] == 0 hold zero partials
 // and are skipped (adding them would not change the sums)
 __global__ void k_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
@@ -541,7 +544,7 @@ __global__ void k_particle_update(ParticleDev *parts, int np, const double *part
 {
     const int k = blockIdx.x;
     if (k >= np) return;
-    __shared__ double red[256][6];
+    __shared__ double red[UPDATE_THREADS][6];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         if (sel && !sel[t]) continue;
@@ -658,7 +661,7 @@ void launch_particle_update(ParticleDev *parts, int np, const double *partials, 
                             const unsigned char *sel, cudaStream_t s)
 {
     k_particle_repulsion<<<1, 64, 0, s>>>(parts, np, p, nx, ny, nz, wall_y, frep);
-    k_particle_update<<<np, 256, 0, s>>>(parts, np, partials, ntiles, p, frep, sel);
+    k_particle_update<<<np, UPDATE_THREADS, 0, s>>>(parts, np, partials, ntiles, p, frep, sel);
     count_launches(2);
 }
 
