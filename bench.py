@@ -51,6 +51,10 @@ DTYPE = {"p64": "f64", "p32": "f32", "fp16": "f16 storage, f32 arithmetic",
          "bf16": "bf16 storage, f32 arithmetic"}
 
 
+# timed regions of K steps each in the batched workloads; the median is reported
+REPEATS = 5
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,47 +253,52 @@ def read_traffic(key, config=None):
 # ---------------------------------------------------------------------------------------------
 # oracle (CPU) timing: a bounded sample of the workload
 # ---------------------------------------------------------------------------------------------
-def oracle_sample(args, budget_s):
-    """Time the FP64 oracle for about ``budget_s`` seconds on the workload.
-    Batch: whole domains taken in order from the batch list.  Returns
-    (MLUPS, description, threads)."""
+def oracle_steps(args, budget_s):
+    """The reference arm: W warm-up and exactly K timed steps of the FP64
+    oracle on a bounded sample of the workload -- whole domains taken in order
+    from the batch list (a single-domain workload is its one domain), as many
+    as keep the K + W steps within about ``budget_s`` seconds.  Returns
+    (MLUPS, timed seconds, sampled cells per step, description, threads)."""
     from oracle import oracle as O
     if args.workload in ("batch", "drops"):
         cases = batch_like(args)["cases"]
     else:
         cases = [single_workload(args.workload, args.n3d, args.phase_model)]
-    cells = 0
-    t_total = 0.0
-    used = []
+    total = max(args.steps, 1) + max(args.warmup, 0)
+    sims, cells, t_est = [], 0, 0.0
     for c in cases:
         o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
         if c.get("walls_y"):
             o.set_walls(True)
         for k, pp in enumerate(c.get("particles", [])):
             o.set_particle(k, O.Particle(**pp))
-        o.init(c["phi0"], c["phi"])
+        o.init(c["phi0"], c["phi"], c.get("u"))
         t0 = time.perf_counter()
-        o.step(1)
+        o.step(1)  # probe: cost of one step of this domain (part of its warm-up)
         one = time.perf_counter() - t0
-        n = max(1, min(50, int((budget_s - t_total) / max(one, 1e-6))))
-        t0 = time.perf_counter()
-        o.step(n)
-        dt = time.perf_counter() - t0
-        cells += int(math.prod(c["shape"])) * n
-        t_total += dt
-        used.append("%s x %d steps" % ("x".join(map(str, c["shape"])), n))
-        if t_total >= budget_s:
+        if sims and t_est + one * total > budget_s:
             break
-    desc = "FP64 C oracle (OpenMP) on whole domains of the workload: " + ", ".join(used)
-    return cells / t_total / 1e6, desc, O.num_threads()
+        sims.append((o, c))
+        cells += int(math.prod(c["shape"]))
+        t_est += one * total
+    for o, _ in sims:
+        o.step(max(args.warmup - 1, 0))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for o, _ in sims:
+            o.step(1)
+    dt = time.perf_counter() - t0
+    desc = ("FP64 C oracle (OpenMP) on %d whole domain(s) of the workload (%s; %d cells), %d warm-up + "
+            "%d timed steps" % (len(sims), ", ".join("x".join(map(str, c["shape"])) for _, c in sims[:8])
+                                + (", ..." if len(sims) > 8 else ""), cells, args.warmup, args.steps))
+    return cells * args.steps / dt / 1e6, dt, cells, desc, O.num_threads()
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    budget = min(120.0, max(10.0, 1.0 * args.steps))
-    v, desc, cores = oracle_sample(args, budget)
+    v, dt, sample_cells, desc, cores = oracle_steps(args, 90.0)
     if args.workload in ("batch", "drops"):
         bw = batch_like(args)
         cells = sum(int(math.prod(c["shape"])) for c in bw["cases"])
@@ -300,9 +309,12 @@ def run_reference(args):
         cells = int(math.prod(c["shape"]))
         cfg = {"workload": args.workload, "cells": cells, "precision": "p64 (oracle)",
                "desc": c["desc"]}
+    # each step advances the sampled cells only: ms_per_step is the time of one
+    # such step, so ms_per_step x steps is the timed region that ran
     line = {"impl": "reference", "metric": "MLUPS", "value": round(v, 4), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(cells / (v * 1e6) * 1e3, 3) if v > 0 else None,
+            "ms_per_step": round(dt / max(args.steps, 1) * 1e3, 3),
+            "sampled": True, "sample_cells_per_step": sample_cells,
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(cfg, order_parameter="allen-cahn" if args.phase_model else "cahn-hilliard"),
@@ -373,17 +385,25 @@ def run_batch(args, dist, rank, world, local):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     n0 = pf.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # REPEATS timed regions of exactly K steps each (barrier + synchronize on
+    # both sides); the headline is the median region, max over ranks
+    reps_ms = []
     t_wall = time.perf_counter()
-    e0.record(stream)
-    b.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    for _ in range(REPEATS):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        reps_ms.append(e0.elapsed_time(e1))
     t_wall = time.perf_counter() - t_wall
-    launches = pf.launch_count() - n0
+    launches = (pf.launch_count() - n0) // REPEATS
     b.sync()
     clk = clocks.stop()
-    total_ms = max_over_ranks(dist, e0.elapsed_time(e1))
+    total_ms = max_over_ranks(dist, statistics.median(reps_ms))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -431,9 +451,11 @@ def run_batch(args, dist, rank, world, local):
                                    % (cells * bpc / 1e9),
            "tile": [tx, ty], "ctas_per_sm": cps, "kernel": cpt, "cells_per_thread": 2 if cpt else 1,
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
+    cfg["timing"] = ("median of %d timed regions of %d steps each (ms: %s)"
+                     % (REPEATS, args.steps, ", ".join("%.2f" % v for v in reps_ms)))
     return dict(mlups=mlups, total_ms=total_ms, achieved=achieved, bpc=bpc, prec=prec, cfg=cfg,
                 clk=clk, launches=launches, e2e=e2e, t_wall=t_wall,
-                kernel="k_step2d_pair" if cpt else "k_step2d", launch_config=[tx, ty, cpt])
+                kernel=step_kernel_name(2, cpt), launch_config=[tx, ty, cpt])
 
 
 def step_kernel_name(dim, variant):
@@ -691,7 +713,7 @@ def run_ours(args):
         return
     cpu = None
     if not args.no_cpu_baseline:
-        v, desc, cores = oracle_sample(args, 15.0)
+        v, _, _, desc, cores = oracle_steps(argparse.Namespace(**dict(vars(args), steps=2, warmup=1)), 15.0)
         cpu = {"value": round(v, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": desc}
     peaks = read_peaks()

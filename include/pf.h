@@ -16,8 +16,11 @@
  * Newton-Euler update (Eqs. 26, 28) on the device (Sec. 3.3, steps 7-10).
  *
  * Lattice units throughout: dx = dt = c = 1, cs^2 = d0.  2D uses D2Q9 for both
- * lattices; 3D uses D3Q19 (flow) and D3Q7 (order parameter).  Every boundary is
- * periodic; walls and solids are marked by the smooth indicator phi0 (Sec. 2.1).
+ * lattices; 3D uses D3Q19 (flow) and D3Q7 (order parameter).  Boundaries are
+ * periodic, except optional no-flux walls at the two ends of y
+ * (pf_grid.periodic[1] = 0: halfway bounce-back, mirrored stencil rows);
+ * solids, and walls inside a periodic box, are marked by the smooth indicator
+ * phi0 (Sec. 2.1).
  *
  * Conventions for every call:
  *   - Return value: PF_OK (0) or a negative PF_E* code.  The message of the last
@@ -300,7 +303,14 @@ void pf_batch_destroy(pf_batch *b);
  * E_F of Eq. (8), E_K = sum rho |u|^2 / 2, E_F + E_K} -- from caller-owned
  * device arrays (x-fastest, N = nx*ny*nz; u component-major, dim*N), e.g. the
  * PF_DEVICE output of pf_get_macros, with phi0 the total solid indicator.
- * Only g->dim, nx, ny, nz and p->sigma, D, theta_deg are read.  out4 is
+ * Only g->dim, nx, ny, nz, periodic and p->sigma, D, theta_deg are read.  The
+ * boundaries follow pf_create: periodic, or walls at the ends of y
+ * (periodic[1] = 0), whose stencils read the mirror image of the rows inside
+ * as pf_diagnostics does; anything else returns PF_EINVAL.  The wetting
+ * energy uses the one angle p->theta_deg for the whole of phi0: for a handle
+ * whose particles carry their own contact angles (Sec. 4.5), where
+ * pf_diagnostics sums the wetting energy per solid, E_F differs -- use
+ * pf_diagnostics there.  out4 is
  * host (where = PF_HOST; the call then waits for the result) or device memory
  * (PF_DEVICE; asynchronous).  Work runs on `stream` (NULL = default stream).
  *
@@ -310,7 +320,10 @@ void pf_batch_destroy(pf_batch *b);
  * about 192 KiB); larger grids return PF_EINVAL.  Every GPU that loads the
  * library holds that array until the process exits.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress), so make
- * that first call before any stream capture.  All calls share the array: each
+ * that first call before any stream capture; the address is kept per device
+ * and per driver context, and a call made in a new context of the device
+ * (after cudaDeviceReset, for example) looks it up again, so make the first
+ * call after such a change before any capture too.  All calls share the array: each
  * call overwrites every partial it reads, so nothing carries over, but calls
  * whose kernels overlap on the GPU (different streams, no ordering) race on
  * it and must be serialised by the caller. */

@@ -594,7 +594,7 @@ static bool any_cac(const Engine &E)
 static int mode_flags(const Engine &E)
 {
     const bool w = any_walls(E), c = any_cac(E);
-    return (w || c ? MODE_EXT : 0) | (c ? MODE_CAC : 0);
+    return (w || c ? MODE_EXT : 0) | (c ? MODE_CAC : 0) | (w ? MODE_WALL : 0);
 }
 
 static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
@@ -721,7 +721,15 @@ static int split_setup(Engine &E)
 // choice on the live state (the state advances; steps are counted), keep the
 // fastest; cached per (dim, precision, moving, cell-count bucket, domain count).
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, long long, int>, std::tuple<int, int, int, int>> g_tune_cache;
+// key: (dim, precision, free particles, cell-count bucket, domain count,
+// features: bit 0 walls, bit 1 Allen-Cahn, bit 2 own contact angles)
+static std::map<std::tuple<int, int, int, long long, int, int>, std::tuple<int, int, int, int>> g_tune_cache;
+
+// the features of a launch that decide which kernels can run it
+static int tune_features(const Engine &E)
+{
+    return (any_walls(E) ? 1 : 0) | (any_cac(E) ? 2 : 0) | (E.wv ? 4 : 0);
+}
 
 static int engine_configure(Engine &E)
 {
@@ -729,7 +737,7 @@ static int engine_configure(Engine &E)
     for (auto &m : E.mem) cells += (long long)m.d.nx * m.d.ny * m.d.nz;
     long long bucket = 1;
     while (bucket < cells) bucket <<= 1;
-    const auto key = std::make_tuple(E.dim, E.prec, E.np > 0 ? 1 : 0, bucket, (int)E.mem.size());
+    const auto key = std::make_tuple(E.dim, E.prec, E.np > 0 ? 1 : 0, bucket, (int)E.mem.size(), tune_features(E));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -737,6 +745,7 @@ static int engine_configure(Engine &E)
             int tx, ty, var, cps;
             std::tie(tx, ty, var, cps) = it->second;
             if (var == 3 && !split_ok(E)) var = 0;
+            if (var != 0 && (E.dim == 3 || any_walls(E))) var = 0;  // (the key already separates these)
             int rc = engine_tiles(E, tx, ty);
             if (rc) return rc;
             E.variant = var;

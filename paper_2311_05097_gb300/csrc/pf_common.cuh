@@ -33,6 +33,10 @@ constexpr int MODE_CAC = 32;
 // or'ed into MODE_STEP_PAIR: the launch runs the far tiles of a particle domain
 // (the fixed solids' mu_phi0 grad phi0 term is on)
 constexpr int MODE_MU0 = 64;
+// or'ed into a 2D mode: the launch holds a domain with walls at the ends of y;
+// only the single-cell kernel handles them, so the dispatchers of the other
+// 2D kernels refuse a mode carrying this bit
+constexpr int MODE_WALL = 128;
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {

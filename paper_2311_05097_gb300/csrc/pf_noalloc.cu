@@ -29,20 +29,30 @@ __device__ __align__(256) double g_noalloc_scratch[3 * (PF_NOALLOC_MAX_BLOCKS + 
 
 struct NAGeom {
     int dim, nx, ny, nz;
+    int wall_y;  // walls at the ends of y (pf_grid.periodic[1] = 0): mirror rows
     double sigma, D, cos_t;
 };
+
+// row of a neighbour at y: periodic, or with walls the mirror image of the
+// row inside (zero normal gradient, as in pf_diagnostics)
+__device__ __forceinline__ int na_row(const NAGeom &g, int y)
+{
+    if (g.wall_y) return y < 0 ? -1 - y : (y >= g.ny ? 2 * g.ny - 1 - y : y);
+    return wrap_idx(y, g.ny);
+}
 
 __device__ __forceinline__ long long na_lin(const NAGeom &g, int x, int y, int z)
 {
     return ((long long)z * g.ny + y) * g.nx + x;
 }
 
-// isotropic gradient (D2Q9 / D3Q19 weights, cs^2 = 1/3), periodic wrap
+// isotropic gradient (D2Q9 / D3Q19 weights, cs^2 = 1/3): periodic wrap, and
+// mirrored rows beyond walls at the ends of y
 __device__ void na_grad(const NAGeom &g, const double *a, int x, int y, int z, double out[3])
 {
     out[0] = out[1] = out[2] = 0.0;
     auto at = [&](int dx, int dy, int dz) {
-        const int xx = wrap_idx(x + dx, g.nx), yy = wrap_idx(y + dy, g.ny),
+        const int xx = wrap_idx(x + dx, g.nx), yy = na_row(g, y + dy),
                   zz = g.dim == 3 ? wrap_idx(z + dz, g.nz) : 0;
         return a[na_lin(g, xx, yy, zz)];
     };
@@ -141,9 +151,32 @@ __global__ void k_noalloc_final(int nblocks, double *scratch, double *out_dev)
 
 using namespace pf;
 
-// device address of the scratch array, resolved once per device
+// device address of the scratch array, resolved once per device and context:
+// the address belongs to the context current at the lookup, so a new context
+// on the device (after cudaDeviceReset, say) triggers a new lookup
 static std::mutex g_na_mu;
 static double *g_na_addr[64] = {};
+static void *g_na_ctx[64] = {};
+
+typedef int (*CtxGetCurrentFn)(void **);
+
+// the calling thread's current driver context (nullptr if it cannot be read)
+static void *current_context()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)f;
+        tried = true;
+    }
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 static int na_fail(int code, const char *msg) { return set_error(code, msg); }
 
@@ -158,6 +191,10 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid *g, const pf_params *p, cons
         return na_fail(PF_EINVAL, "pf_diagnostics_noalloc: where must be PF_HOST or PF_DEVICE");
     const int nz = g->dim == 2 ? 1 : g->nz;
     if (g->nx < 1 || g->ny < 1 || nz < 1) return na_fail(PF_EINVAL, "pf_diagnostics_noalloc: empty grid");
+    for (int a = 0; a < g->dim; ++a)
+        if (g->periodic[a] != 1 && !(a == 1 && g->periodic[a] == 0))
+            return na_fail(PF_EINVAL, "pf_diagnostics_noalloc: boundaries must be periodic, except walls at the "
+                                      "ends of y (periodic[1] = 0)");
     const long long N = (long long)g->nx * g->ny * nz;
     if (N > PF_NOALLOC_MAX_CELLS) {
         char buf[200];
@@ -173,8 +210,10 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid *g, const pf_params *p, cons
     double *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_addr[dev]) {
-            // first call on this device: look up the array's device address
+        void *ctx = current_context();
+        if (!g_na_addr[dev] || ctx != g_na_ctx[dev]) {
+            // first call on this device (or in a new context): look up the
+            // array's device address
             void *ptr = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
             if (e != cudaSuccess || !ptr) {
@@ -182,6 +221,7 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid *g, const pf_params *p, cons
                                           cudaGetErrorString(e)).c_str());
             }
             g_na_addr[dev] = (double *)ptr;
+            g_na_ctx[dev] = ctx;
         }
         scratch = g_na_addr[dev];
     }
@@ -190,6 +230,7 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid *g, const pf_params *p, cons
     geo.nx = g->nx;
     geo.ny = g->ny;
     geo.nz = nz;
+    geo.wall_y = g->periodic[1] == 0 ? 1 : 0;
     geo.sigma = p->sigma;
     geo.D = p->D;
     geo.cos_t = std::cos(p->theta_deg * 3.14159265358979323846 / 180.0);

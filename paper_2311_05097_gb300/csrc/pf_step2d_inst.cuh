@@ -121,10 +121,12 @@ static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStre
                        const StepArgs &a, int *occ)
 {
     const bool ext = (mode & MODE_EXT) != 0, cac = (mode & MODE_CAC) != 0, mu0 = (mode & MODE_MU0) != 0;
-    mode &= ~(MODE_EXT | MODE_CAC | MODE_MU0);
-    // (the library never asks the two-cells-per-thread kernels for walls)
-    if (mode == MODE_STEP_PAIR) return dispatch2d_pair<P>(tx, ty, moving, cac, mu0, grid, s, a, occ);
-    if (mode == MODE_STEP_STAGE) return !ext && !cac && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
+    const bool wall = (mode & MODE_WALL) != 0;
+    mode &= ~(MODE_EXT | MODE_CAC | MODE_MU0 | MODE_WALL);
+    // the two-cells-per-thread kernels have no wall handling: refuse walled launches
+    if (mode == MODE_STEP_PAIR) return !wall && dispatch2d_pair<P>(tx, ty, moving, cac, mu0, grid, s, a, occ);
+    if (mode == MODE_STEP_STAGE)
+        return !wall && !ext && !cac && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
     return ext ? dispatch2d_single<P, true>(tx, ty, moving, mode, grid, s, a, occ)
                : dispatch2d_single<P, false>(tx, ty, moving, mode, grid, s, a, occ);
 }

@@ -91,8 +91,9 @@ def test_batch_contact_angles(pf):
     density ratio in [1, 30]): after relaxation the FP16-storage angle is
     within 1 deg of the FP64 angle; the FP64 angle is compared with the
     prescribed one."""
-    # density ratios up to 30: higher ratios next to wetting walls do not stay
-    # stable to equilibrium with this scheme (see the design notes)
+    # density ratios up to 30: at higher ratios next to wetting walls the
+    # scheme as printed (s_i = 1 except s0 = 1.6) did not stay stable until the
+    # contact line had relaxed (5e4+ steps) in the runs made for this test
     draws = [(128, 35.0, 1.0), (64, 60.0, 30.0), (64, 90.0, 10.0), (64, 120.0, 5.0),
              (64, 145.0, 20.0), (128, 50.0, 3.0), (128, 100.0, 2.0), (128, 135.0, 30.0)]
     cases = [W.flat_wall_drop(L, th, r) for L, th, r in draws]
@@ -139,7 +140,7 @@ def test_water_entry_bf16_against_fp64(pf):
     rho_p = 2, theta = 90 deg): BF16-storage particle trajectory against FP64
     over the first 200 steps (the particle moving through the gas becomes
     unstable after a few hundred steps with the mu_phi0 grad phi0 force of
-    Eq. 19; see the design notes)."""
+    Eq. 19 switched on, in FP64 as well)."""
     c = W.water_entry()
     part = dict(c["particles"][0])
     steps = 200

@@ -521,6 +521,34 @@ def test_batch_mixes_wall_and_periodic_domains(pf):
     assert_fields(b.macros(0), o.macros(), 1e-12)
 
 
+def test_tuned_periodic_config_is_not_reused_for_walls(pf):
+    """The autotuner's cache must not hand a walled batch the configuration
+    tuned on a periodic batch of the same size: the two-cells-per-thread
+    kernels have no bounce-back, so a walled domain stepped by them would run
+    as periodic in y.  A periodic FP16 batch is tuned first (it usually picks
+    the two-cells kernel), then a walled batch of the same size and domain
+    count: it must report kernel 0 and match its single-handle run bit for
+    bit (that run is kernel 0, parity-tested against the oracle)."""
+    L = 256
+    per = W.flat_wall_drop(L, 60.0, 10.0)
+    bp = pf.Batch([per["shape"]], [per["params"]], precision="fp16")
+    bp.init(0, per["phi0"], per["phi"])
+    bp.step(256)
+    bp.sync()
+    bp.close()
+    c = W.wall_case((L, L), seed=4)
+    bw = pf.Batch([c["shape"]], [c["params"]], precision="fp16", walls_y=[True])
+    bw.init(0, c["phi0"], c["phi"], c.get("u"))
+    bw.step(256)
+    bw.sync()
+    assert bw.config()[3] == 0, bw.config()
+    g, _ = run_pair(pf, c, 256, precision="fp16", oracle=False, walls=True)
+    mb, mg = bw.macros(0), g.macros()
+    for k in FIELDS:
+        assert np.array_equal(mb[k], mg[k]), k
+    assert abs(bw.diagnostics(0)["mass"] - g.diagnostics()["mass"]) == 0.0
+
+
 def test_p64_particle_wall_repulsion_matches_oracle(pf):
     """Particles next to the box walls and to a circular wall (Sec. 4.5
     particle-wall repulsion against the mirror image across the nearest

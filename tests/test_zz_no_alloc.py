@@ -34,12 +34,18 @@ def device_fields(pf, sim, dim, N):
     return out
 
 
-@pytest.mark.parametrize("shape,precision", [((52, 40), "p64"), ((48, 64), "fp16"),
-                                             ((12, 14, 18), "p64")])
-def test_noalloc_matches_pf_diagnostics(pf, shape, precision):
+@pytest.mark.parametrize("shape,precision,walls", [((52, 40), "p64", False), ((48, 64), "fp16", False),
+                                                   ((12, 14, 18), "p64", False), ((37, 52), "p64", True),
+                                                   ((12, 14, 18), "p64", True)])
+def test_noalloc_matches_pf_diagnostics(pf, shape, precision, walls):
+    """Both entry points on the same fields, periodic boxes and boxes with
+    walls at the ends of y (mirrored stencil rows in both)."""
     import torch
-    c = W.small_case(shape, seed=2, solid=True, theta_deg=120.0, u_amp=0.01)
-    sim = pf.Sim(c["shape"], precision=precision, **c["params"])
+    if walls and len(shape) == 2:
+        c = W.wall_case(shape, seed=2, solid=True, theta_deg=120.0, u_amp=0.01)
+    else:
+        c = W.small_case(shape, seed=2, solid=True, theta_deg=120.0, u_amp=0.01)
+    sim = pf.Sim(c["shape"], precision=precision, walls_y=walls, **c["params"])
     sim.init(c["phi0"], c["phi"], c["u"])
     sim.step(25)
     ref = sim.diagnostics()
@@ -50,7 +56,7 @@ def test_noalloc_matches_pf_diagnostics(pf, shape, precision):
     # fields (FP32 unless the policy is FP64); the diagnostics read that copy
     p0 = c["phi0"] if precision == "p64" else c["phi0"].astype(np.float32).astype(np.float64)
     phi0 = torch.from_numpy(np.ascontiguousarray(p0).reshape(-1)).cuda()
-    g = pf.make_grid(shape)
+    g = pf.make_grid(shape, walls_y=walls)
     p = pf.make_params(**c["params"])
     L = pf.load()
     ptr = lambda t: C.c_void_p(t.data_ptr())
@@ -82,3 +88,16 @@ def test_noalloc_rejects_grids_beyond_its_scratch(pf):
                                   C.c_void_p(1), C.c_void_p(1), out, pf.PF_HOST, None)
     assert rc == pf.PF_EINVAL
     assert "maximum" in pf.last_error()
+
+
+def test_noalloc_rejects_unsupported_boundaries(pf):
+    """Walls are accepted at the ends of y only, as in pf_create."""
+    g = pf.make_grid((16, 16))
+    g.periodic[0] = 0
+    p = pf.make_params()
+    out = (C.c_double * 4)()
+    L = pf.load()
+    rc = L.pf_diagnostics_noalloc(C.byref(g), C.byref(p), C.c_void_p(1), C.c_void_p(1),
+                                  C.c_void_p(1), C.c_void_p(1), out, pf.PF_HOST, None)
+    assert rc == pf.PF_EINVAL
+    assert "periodic" in pf.last_error()
