@@ -51,6 +51,12 @@ DTYPE = {"p64": "f64", "p32": "f32", "fp16": "f16 storage, f32 arithmetic",
          "bf16": "bf16 storage, f32 arithmetic"}
 
 
+KERNEL_DESC = ["one cell per thread (tiles)", "two cells per thread (tiles)",
+               "two cells per thread (tiles), bulk-copy staging",
+               "near tiles one cell, far tiles two cells per thread",
+               "two cells per thread on strips marched in y (tile = strip width x segment rows), "
+               "tensor-copy staging"]
+
 # timed regions of K steps each in the batched workloads; the median is reported
 REPEATS = 5
 
@@ -450,6 +456,7 @@ def run_batch(args, dist, rank, world, local):
            "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"
                                    % (cells * bpc / 1e9),
            "tile": [tx, ty], "ctas_per_sm": cps, "kernel": cpt, "cells_per_thread": 2 if cpt else 1,
+           "kernel_desc": KERNEL_DESC[cpt],
            "parallelism": "independent replicas per GPU" if world > 1 else "single GPU"}
     cfg["timing"] = ("median of %d timed regions of %d steps each (ms: %s)"
                      % (REPEATS, args.steps, ", ".join("%.2f" % v for v in reps_ms)))
@@ -462,7 +469,7 @@ def step_kernel_name(dim, variant):
     """The step kernel(s) of a launch variant (the roofline's dominant kernel)."""
     if dim == 3:
         return "k_step3d"
-    return ["k_step2d", "k_step2d_pair", "k_step2d_stage", "k_step2d_pair+k_step2d"][variant]
+    return ["k_step2d", "k_step2d_pair", "k_step2d_stage", "k_step2d_pair+k_step2d", "k_step2d_strip"][variant]
 
 
 def run_single(args, dist, rank, world, local):
@@ -502,7 +509,8 @@ def run_single(args, dist, rank, world, local):
     tx, ty, cps, kern = sim.config()
     launch = {"tile": [tx, ty], "ctas_per_sm": cps, "kernel": kern,
               "kernel_desc": ["one cell per thread", "two cells per thread", "two cells per thread, staged",
-                              "near tiles one cell, far tiles two cells per thread"][kern]}
+                              "near tiles one cell, far tiles two cells per thread",
+                              "two cells per thread on strips marched in y, tensor-copy staging"][kern]}
     if not in_l2:
         return run_single_large(args, dist, rank, world, local, case, prec, cells, bpc, sim, stream, launch)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

@@ -1,5 +1,6 @@
 // C-ABI of libpf (include/pf.h): handles, device memory, CUDA-graph replay of
 // the step sequence, batched domains and the launch-configuration autotuner.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -13,6 +14,7 @@
 #include <tuple>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/pf.h"
@@ -161,7 +163,7 @@ static int validate(const pf_grid *g, const pf_params *p)
     const int nz = g->dim == 2 ? 1 : g->nz;
     if (g->nx < 4 || g->ny < 4 || (g->dim == 3 && nz < 4))
         return fail(PF_EINVAL, "grid sizes must be >= 4 (got %d x %d x %d)", g->nx, g->ny, nz);
-    const long long pitch = (g->nx + 31) / 32 * 32;
+    const long long pitch = (g->nx + (g->dim == 2 ? 2 * STRIP_GHOST : 0) + 31) / 32 * 32;
     const long long qtot = g->dim == 2 ? 18 : 26;
     if (qtot * (pitch * g->ny * nz + 64) >= (1LL << 31))
         return fail(PF_EINVAL, "grid too large: %lld populations x %lld cells must stay below 2^31 "
@@ -317,7 +319,10 @@ static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams
     d.ny = g->ny;
     d.nz = dim == 2 ? 1 : g->nz;
     d.wall_y = g->periodic[1] == 0 ? 1 : 0;
-    d.pitch = (int)round_up(d.nx, 32);
+    // 2D rows carry STRIP_GHOST ghost columns after the row's end and, in the
+    // padding of the previous row, before its start (the strip step's periodic
+    // images in x)
+    d.pitch = (int)round_up(d.nx + (dim == 2 ? 2 * STRIP_GHOST : 0), 32);
     d.plane = round_up((long long)d.pitch * d.ny * d.nz, 64);
     d.p = dp;
     d.kf = make_kparams<float>(dp);
@@ -328,11 +333,12 @@ static int domain_alloc(DomainMem &m, int dim, const pf_grid *g, const DevParams
     const size_t rb = prec >= PF_PMIX_FP16 ? (size_t)d.plane * 8 : 0;
     const size_t ab = (size_t)naux * d.plane * aux_bytes(prec);
     const size_t pb = (size_t)d.plane * aux_bytes(prec);
-    const size_t total = 2 * fb + 2 * rb + 2 * ab + pb + 256 * 8;
+    const size_t total = 2 * fb + 2 * rb + 2 * ab + pb + 256 * 8 + 256 * 8;
     CK(cudaMalloc(&m.base, total));
     CK(cudaMemset(m.base, 0, total));
     char *c = (char *)m.base;
     auto take = [&](size_t n) {
+        c += 256;  // front pad: the ghost columns left of row 0 of the first plane
         void *r = c;
         c += round_up((long long)n, 256);
         return r;
@@ -441,6 +447,12 @@ struct Engine {
     unsigned char *d_sel = nullptr;          // variant 3: per tile 1 near a particle, 0 far
     int sel_cap = 0;
     int grid_far = 0;                        // variant 3: grid of the far-tile launch
+    // variant 4 (strips marched in y): work items, tensor maps, ghost columns
+    int4 *d_items = nullptr;
+    int nitems = 0;
+    void *d_maps = nullptr;                  // STRIP_MAPS tensor maps per domain
+    bool maps_ok = false;
+    bool ghosts_ok = false;                  // the buffer the next step reads has valid ghost columns
     cudaStream_t side = nullptr;             // variant 3: the near tiles run on this stream beside
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // the far ones (fork / join)
     bool forced = false;                     // launch configuration set by the caller
@@ -528,6 +540,8 @@ static void engine_free(Engine &E)
     if (E.d_frep) cudaFree(E.d_frep);
     if (E.d_partials) cudaFree(E.d_partials);
     if (E.d_sel) cudaFree(E.d_sel);
+    if (E.d_items) cudaFree(E.d_items);
+    if (E.d_maps) cudaFree(E.d_maps);
     if (E.ev_fork) cudaEventDestroy(E.ev_fork);
     if (E.ev_join) cudaEventDestroy(E.ev_join);
     if (E.side) cudaStreamDestroy(E.side);
@@ -608,6 +622,7 @@ static int step_mode(const Engine &E)
 {
     // (variant 3: the single-cell launch of the near tiles; the far tiles are
     // launched beside it in issue_step)
+    if (E.variant == 4) return MODE_STEP_STRIP;
     return E.variant == 2 ? MODE_STEP_STAGE : (E.variant == 1 ? MODE_STEP_PAIR : MODE_STEP);
 }
 
@@ -627,6 +642,16 @@ static bool stage_ok(const Engine &E)
     const int q = E.prec == PF_P32 ? 4 : 8;
     for (auto &m : E.mem)
         if (m.d.nx % q) return false;
+    return true;
+}
+
+// the strip step (variant 4): 2D, FP32 or 16-bit storage, no free particles,
+// no walls at the ends of y, every nx even and >= the ghost width
+static bool strip_ok(const Engine &E)
+{
+    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0 || any_walls(E)) return false;
+    for (auto &m : E.mem)
+        if (m.d.nx % 2 || m.d.nx < STRIP_GHOST || m.d.pitch < m.d.nx + 2 * STRIP_GHOST) return false;
     return true;
 }
 
@@ -650,6 +675,9 @@ static StepArgs step_args(const Engine &E, int par)
     a.flags = E.d_flags;
     a.wv = E.wv;
     a.wait_polls = E.wait_polls;
+    a.items = E.d_items;
+    a.nitems = E.nitems;
+    a.strip_maps = E.d_maps;
     return a;
 }
 
@@ -679,9 +707,16 @@ static int issue_step(Engine &E, int par)
         const bool ok_far = launch_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0, E.grid_far, af);
         CK(cudaStreamWaitEvent(E.stream, E.ev_join, 0));
         if (!ok_near || !ok_far) return fail(PF_EINVAL, "split step of tile shape %dx%d not built", E.tx, E.ty);
+    } else if (E.variant == 4) {
+        if (!E.ghosts_ok && !launch_any(E, STRIP_SW, 0, MODE_FILL_GHOSTS, (int)E.mem.size(), a))
+            return fail(PF_EINVAL, "ghost pass not built");
+        if (!launch_any(E, E.tx, E.ty, MODE_STEP_STRIP, E.grid, a))
+            return fail(PF_EINVAL, "strip step of width %d not built", E.tx);
     } else if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a)) {
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
     }
+    // the strip step writes the ghost columns of what it stores; the others do not
+    E.ghosts_ok = E.variant == 4;
     if (E.np > 0)
         launch_particle_update(E.d_parts, E.np, E.d_partials, E.ntiles, E.mem[0].d.p, E.d_frep, E.mem[0].d.nx,
                                E.mem[0].d.ny, E.mem[0].d.nz, E.mem[0].d.wall_y,
@@ -696,7 +731,8 @@ static int grid_of(Engine &E, int cps)
     if (occ < 1) occ = 1;
     int c = cps > 0 ? std::min(cps, occ) : occ;
     long long g = (long long)c * E.nsm;
-    if (g > E.ntiles) g = E.ntiles;
+    const long long units = E.variant == 4 ? E.nitems : E.ntiles;
+    if (g > units) g = units;
     return (int)std::max(1LL, g);
 }
 
@@ -717,18 +753,146 @@ static int split_setup(Engine &E)
     return PF_OK;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, fetched through the runtime (no libcuda link)
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    });
+    return fn;
+}
+
+// One tiled tensor map over a row-major array whose rows carry STRIP_GHOST
+// ghost columns on each side: x' = x + STRIP_GHOST in [0, pitch), y in
+// [0, ny), then `planes` planes; box = (bx, 1 row, planes).
+static int encode_map(CUtensorMap *m, CUtensorMapDataType type, int es, const void *cell0, int pitch, int ny,
+                      int planes, long long plane, int bx)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return fail(PF_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const char *base = static_cast<const char *>(cell0) - (size_t)STRIP_GHOST * es;
+    const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)ny, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, 1u, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const cuuint32_t rank = planes > 1 ? 3u : 2u;
+    CUresult r = fn(m, type, rank, const_cast<char *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PF_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PF_OK;
+}
+
+// variant 4: the tensor maps of every domain (both read parities) and the
+// work items of segments of `seg` rows (strips of STRIP_SW columns), ordered
+// largest first, then by domain, segment and strip (neighbouring strips of a
+// segment run side by side and share their halo columns in L2)
+static int strip_setup(Engine &E, int seg)
+{
+    if (!E.maps_ok) {
+        const int nd = (int)E.mem.size();
+        std::vector<CUtensorMap> maps((size_t)nd * STRIP_MAPS);
+        memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+        const bool mix = E.prec >= PF_PMIX_FP16;
+        const int es = (int)store_bytes(E.prec);
+        const CUtensorMapDataType ft = E.prec == PF_P32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                       : E.prec == PF_PMIX_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        const int hs = 16 / es, w1 = STRIP_SW + 2 * hs;
+        for (int i = 0; i < nd; ++i) {
+            const DomainDev &d = E.mem[i].d;
+            CUtensorMap *m = &maps[(size_t)i * STRIP_MAPS];
+            int rc = PF_OK;
+            for (int par = 0; par < 2 && rc == PF_OK; ++par) {
+                CUtensorMap *q = m + par * STRIP_MAPS_PER_PAR;
+                const char *f = static_cast<const char *>(d.f[par]);
+                const char *aux = static_cast<const char *>(d.aux[par]);
+                const int i1 = mix ? 1 : 0, q1 = mix ? 8 : 9;
+                rc = encode_map(q + SM_F1, ft, es, f + (size_t)i1 * d.plane * es, d.pitch, d.ny, q1, d.plane, w1);
+                if (!rc)
+                    rc = encode_map(q + SM_F2, ft, es, f + (size_t)9 * d.plane * es, d.pitch, d.ny, 9, d.plane, w1);
+                if (!rc && mix)
+                    rc = encode_map(q + SM_REST, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, d.rest[par], d.pitch, d.ny, 1,
+                                    d.plane, STRIP_SW + 4);
+                if (!rc)
+                    rc = encode_map(q + SM_US, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, aux, d.pitch, d.ny, 4, d.plane,
+                                    STRIP_SW + 8);
+                if (!rc)
+                    rc = encode_map(q + SM_PHIL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, aux + (size_t)4 * d.plane * 4,
+                                    d.pitch, d.ny, 1, d.plane, STRIP_SW);
+            }
+            if (!rc)
+                rc = encode_map(m + SM_PHI0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.phi0, d.pitch, d.ny, 1, d.plane,
+                                STRIP_SW + 8);
+            if (rc) return rc;
+        }
+        if (E.d_maps) cudaFree(E.d_maps);
+        E.d_maps = nullptr;
+        CK(cudaMalloc(&E.d_maps, sizeof(CUtensorMap) * maps.size()));
+        CK(cudaMemcpy(E.d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+        E.maps_ok = true;
+    }
+    struct It {
+        int4 v;
+        long long cells;
+    };
+    std::vector<It> its;
+    for (int i = 0; i < (int)E.mem.size(); ++i) {
+        const DomainDev &d = E.mem[i].d;
+        for (int ya = 0; ya < d.ny; ya += seg)
+            for (int x0 = 0; x0 < d.nx; x0 += STRIP_SW) {
+                const int yb = std::min(ya + seg, d.ny);
+                its.push_back({make_int4(i, x0, ya, yb), (long long)(yb - ya) * std::min(STRIP_SW, d.nx - x0)});
+            }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const It &a, const It &b) { return a.cells > b.cells; });
+    std::vector<int4> items;
+    for (auto &t : its) items.push_back(t.v);
+    if (E.d_items) cudaFree(E.d_items);
+    E.d_items = nullptr;
+    E.nitems = (int)items.size();
+    CK(cudaMalloc(&E.d_items, sizeof(int4) * items.size()));
+    CK(cudaMemcpy(E.d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+// fill the ghost columns of the buffers the next step reads, unless valid
+// (before a graph capture or replay: the captured steps then never need it)
+static int ensure_ghosts(Engine &E)
+{
+    if (E.variant != 4 || E.ghosts_ok) return PF_OK;
+    const StepArgs a = step_args(E, E.par);
+    if (!launch_any(E, STRIP_SW, 0, MODE_FILL_GHOSTS, (int)E.mem.size(), a))
+        return fail(PF_EINVAL, "ghost pass not built");
+    CK(cudaGetLastError());
+    E.ghosts_ok = true;
+    return PF_OK;
+}
+
 // Autotuner: time a few steps of each compiled tile shape and CTAs-per-SM
 // choice on the live state (the state advances; steps are counted), keep the
 // fastest; cached per (dim, precision, moving, cell-count bucket, domain count).
 static std::mutex g_tune_mu;
 // key: (dim, precision, free particles, cell-count bucket, domain count,
-// features: bit 0 walls, bit 1 Allen-Cahn, bit 2 own contact angles)
+// features: bit 0 walls, bit 1 Allen-Cahn, bit 2 own contact angles, bit 3
+// the strip step can run it)
 static std::map<std::tuple<int, int, int, long long, int, int>, std::tuple<int, int, int, int>> g_tune_cache;
 
 // the features of a launch that decide which kernels can run it
 static int tune_features(const Engine &E)
 {
-    return (any_walls(E) ? 1 : 0) | (any_cac(E) ? 2 : 0) | (E.wv ? 4 : 0);
+    return (any_walls(E) ? 1 : 0) | (any_cac(E) ? 2 : 0) | (E.wv ? 4 : 0) | (strip_ok(E) ? 8 : 0);
 }
 
 static int engine_configure(Engine &E)
@@ -744,17 +908,25 @@ static int engine_configure(Engine &E)
         if (it != g_tune_cache.end()) {
             int tx, ty, var, cps;
             std::tie(tx, ty, var, cps) = it->second;
-            if (var == 3 && !split_ok(E)) var = 0;
-            if (var != 0 && (E.dim == 3 || any_walls(E))) var = 0;  // (the key already separates these)
+            if ((var == 3 && !split_ok(E)) || (var == 4 && !strip_ok(E)) ||
+                (var != 0 && (E.dim == 3 || any_walls(E)))) {  // (the key already separates these)
+                var = 0;
+                tx = 32;
+                ty = 8;
+            }
             int rc = engine_tiles(E, tx, ty);
             if (rc) return rc;
             E.variant = var;
             E.cps = cps;
-            E.grid = grid_of(E, cps);
             if (var == 3) {
                 rc = split_setup(E);
                 if (rc) return rc;
             }
+            if (var == 4) {
+                rc = strip_setup(E, ty);
+                if (rc) return rc;
+            }
+            E.grid = grid_of(E, cps);
             E.tuned = true;
             return PF_OK;
         }
@@ -763,8 +935,11 @@ static int engine_configure(Engine &E)
     // arithmetic policies without free particles)
     // (kernel 2, the bulk-copy staged variant, is selectable with
     // pf_set_config but not a candidate: it measured slower than kernel 1)
-    int shapes[6][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}};
+    // (kernel 4: tile = strip width x segment rows)
+    int shapes[8][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 128, 4},
+                        {64, 256, 4}};
     int nshapes = (E.prec != PF_P64 && E.np == 0 && !any_walls(E)) ? 6 : 3;
+    if (nshapes == 6 && strip_ok(E)) nshapes = 8;
     if (split_ok(E)) {
         // particle domain: also the split of near (single-cell) and far
         // (two-cells-per-thread) tiles
@@ -791,6 +966,10 @@ static int engine_configure(Engine &E)
         E.variant = sh[2];
         if (E.variant == 3) {
             rc = split_setup(E);
+            if (rc) return rc;
+        }
+        if (E.variant == 4) {
+            rc = strip_setup(E, sh[1]);
             if (rc) return rc;
         }
         const int occ = std::max(1, occupancy_any(E, sh[0], sh[1], step_mode(E)));
@@ -830,11 +1009,15 @@ static int engine_configure(Engine &E)
     if (rc) return rc;
     E.variant = bv;
     E.cps = bc;
-    E.grid = grid_of(E, bc);
     if (bv == 3) {
         rc = split_setup(E);
         if (rc) return rc;
     }
+    if (bv == 4) {
+        rc = strip_setup(E, by);
+        if (rc) return rc;
+    }
+    E.grid = grid_of(E, bc);
     E.tuned = true;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = std::make_tuple(bx, by, bv, bc);
@@ -878,6 +1061,8 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
         left--;
     }
     if (left >= Engine::CHUNK) {
+        int grc = ensure_ghosts(E);
+        if (grc) return (E.sticky = grc);
         if (!E.gexec) {
             const long long before = g_launches.load();
             cudaGraph_t graph;
@@ -1126,6 +1311,7 @@ extern "C" int pf_init_fields(pf_handle *h, const double *phi0, const double *ph
     rc = upload_particles(E);
     if (rc) return rc;
     CK(cudaMemsetAsync(E.d_flags, 0, sizeof(int) * 4, E.stream));
+    E.ghosts_ok = false;
     rc = domain_init(E.mem[0], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, E.hp, E.np, E.d_flags,
                      E.stream);
     if (rc) return rc;
@@ -1297,6 +1483,7 @@ extern "C" int pf_load_state(pf_handle *h, const void *buf, int64_t bytes)
         int rc = upload_particles(E);
         if (rc) return rc;
     }
+    E.ghosts_ok = false;
     CK(cudaMemset(E.d_flags, 0, sizeof(int) * 4));
     E.t = hd.t;
     E.inited[0] = true;
@@ -1423,6 +1610,7 @@ extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const doubl
     if (i < 0 || i >= (int)E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
     if (E.sticky) return E.sticky;
     if (E.t != 0) return fail(PF_ESTATE, "all domains are initialised before the first step");
+    E.ghosts_ok = false;
     int rc = domain_init(E.mem[i], E.staging, E.dim, E.prec, phi0, phi, u, P, where, E.d_parts, nullptr, 0, E.d_flags,
                          E.stream);
     if (rc) return rc;
@@ -1494,7 +1682,11 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
 {
     if (E.sticky) return E.sticky;
     const int var = kernel;
-    if (var < 0 || var > 3) return fail(PF_EINVAL, "kernel must be 0, 1, 2 or 3");
+    if (var < 0 || var > 4) return fail(PF_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
+    if (var == 4 && (!strip_ok(E) || tile_x != STRIP_SW || tile_y < 1))
+        return fail(PF_EINVAL, "kernel 4 (strips marched in y) needs 2D domains in FP32 or 16-bit storage without "
+                               "particles or walls at the ends of y, every nx even and >= %d, tile_x = %d (the "
+                               "strip width) and tile_y >= 1 (the segment rows)", STRIP_GHOST, STRIP_SW);
     if (var == 3 && (!split_ok(E) || tile_x != 32 || tile_y != 16))
         return fail(PF_EINVAL, "kernel 3 (near tiles single-cell, far tiles two-cells) needs one 2D particle "
                                "domain in FP32 or 16-bit storage without walls, own angles or the Allen-Cahn "
@@ -1505,7 +1697,7 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);
-    const int mode = var == 2 ? MODE_STEP_STAGE : (var == 1 ? MODE_STEP_PAIR : MODE_STEP);
+    const int mode = var == 4 ? MODE_STEP_STRIP : var == 2 ? MODE_STEP_STAGE : (var == 1 ? MODE_STEP_PAIR : MODE_STEP);
     if (occupancy_any(E, tile_x, tile_y, mode) < 1 ||
         (var == 3 && occupancy_any(E, tile_x, tile_y, MODE_STEP_PAIR | MODE_MU0) < 1)) {
         return fail(PF_EINVAL, "launch configuration %dx%d of kernel %d is not built for this precision / "
@@ -1518,14 +1710,20 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
         E.t++;
     }
     E.variant = var;
-    int rc = engine_tiles(E, tile_x, tile_y);
+    int rc = engine_tiles(E, var == 4 ? 32 : tile_x, var == 4 ? 8 : tile_y);
     if (rc) return (E.sticky = rc);
+    E.tx = tile_x;
+    E.ty = tile_y;
     E.cps = ctas_per_sm;
-    E.grid = grid_of(E, ctas_per_sm);
     if (var == 3) {
         rc = split_setup(E);
         if (rc) return (E.sticky = rc);
     }
+    if (var == 4) {
+        rc = strip_setup(E, tile_y);
+        if (rc) return (E.sticky = rc);
+    }
+    E.grid = grid_of(E, ctas_per_sm);
     E.tuned = true;
     E.forced = true;
     return PF_OK;

@@ -23,7 +23,17 @@ constexpr int REST_FRAC_BITS = 50;  // rest population = value * 2^-50
 // MODE_STEP_PAIR: the 2D step with two cells per thread (FP32 arithmetic
 // policies, fixed solids); MODE_STEP_STAGE: the same with the tile's inputs
 // staged in shared memory by bulk copies
-enum Mode { MODE_STEP = 0, MODE_MACROS = 1, MODE_STEP_PAIR = 2, MODE_STEP_STAGE = 3 };
+// MODE_STEP_STRIP: two cells per thread on strips marched in y, inputs staged
+// by tensor copies; MODE_FILL_GHOSTS: the pass that refreshes the ghost columns
+// the strip step reads
+enum Mode {
+    MODE_STEP = 0,
+    MODE_MACROS = 1,
+    MODE_STEP_PAIR = 2,
+    MODE_STEP_STAGE = 3,
+    MODE_STEP_STRIP = 4,
+    MODE_FILL_GHOSTS = 5
+};
 // or'ed into a 2D mode: the launch holds a domain with walls or the Allen-Cahn
 // order parameter (the single-cell kernel's instantiation that handles them)
 constexpr int MODE_EXT = 16;
@@ -37,6 +47,17 @@ constexpr int MODE_MU0 = 64;
 // only the single-cell kernel handles them, so the dispatchers of the other
 // 2D kernels refuse a mode carrying this bit
 constexpr int MODE_WALL = 128;
+
+// Strip step (MODE_STEP_STRIP): strips of STRIP_SW columns; 2D rows carry
+// STRIP_GHOST ghost columns (periodic images) on each side.  Tensor maps of
+// one domain: per read parity the order-parameter box, the flow box, the rest
+// population, the lagged u and S (4 planes), the lagged phi; then phi0.
+constexpr int STRIP_SW = 64;
+constexpr int STRIP_GHOST = 8;
+constexpr int STRIP_MAPS_PER_PAR = 5;
+constexpr int STRIP_MAPS = 2 * STRIP_MAPS_PER_PAR + 1;
+enum StripMap { SM_F1 = 0, SM_F2 = 1, SM_REST = 2, SM_US = 3, SM_PHIL = 4 };
+constexpr int SM_PHI0 = 2 * STRIP_MAPS_PER_PAR;
 
 // ---- precision policies ------------------------------------------------------------------
 struct P64 {
@@ -201,6 +222,9 @@ struct StepArgs {
     int wait_polls;        // polls of one bounded device wait (staged kernel); 0: default
     const unsigned char *tile_sel;  // optional, per tile in device memory: run only the tiles ...
     int sel;                        // ... whose byte equals sel (else every tile)
+    const int4 *items;              // strip kernel: work items (domain, x0, first row, end row)
+    int nitems;
+    const void *strip_maps;         // strip kernel: the tensor maps of every domain (128 bytes each)
 };
 
 // ---- helpers -----------------------------------------------------------------------------------

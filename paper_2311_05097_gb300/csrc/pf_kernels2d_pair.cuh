@@ -169,33 +169,22 @@ __device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*
     }
 }
 
-// Stage C of the pair step: the update of the thread's two cells (Eqs. 29-38)
-// from the shared tiles (phi, phi0 on tile + 2 at (hx, hy); mu, w on tile + 1
-// at (wx, wy)) and the values gathered in stage A, then their stores.  racc:
-// PMIX, each cell's exact fixed-point phi (rest + images of the pulled movers).
-// CAC: the instantiation also serves domains with the conservative Allen-Cahn
-// order parameter (checked per domain).  MU0: the simulation holds free
-// particles, so the force carries mu_phi0 grad phi0 (Eq. 19) of the fixed
-// solids too (the tiles this kernel gets are out of every particle's reach).
-template <class P, int FX, int WX, bool CAC = false, bool MU0 = false>
-__device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p, const KParams<float> &kp,
-                                           const float (*s_phi)[FX], const float (*s_p0)[FX],
-                                           const float (*s_mu)[WX], const float (*s_w)[WX], int hx, int hy,
-                                           int wx, int wy, F2 phi, F2 (&f1)[9],
-                                           const typename P::store (&f2raw)[2][9],
-                                           const typename P::aux (&lag)[2][5],
-                                           const long long (&racc)[2], const int (&id)[2], bool valid0, bool valid1, typename P::store *fd,
-                                           long long *rd, typename P::aux *ad, int plane)
+// The update of two cells (Eqs. 29-38) from their stencil values, shared by
+// every two-cells-per-thread kernel: phi, phi0 and mu_phi of the cells, the
+// gradients of phi, mu_phi and w = S_x u_y - u_x S_y (previous step), the
+// previous step's u, S, phi (upx .. php), and both lattices' pulled
+// populations in the arithmetic scale (f1, f2; replaced by the
+// post-collision populations).  Returns u and S of this step.  CAC: the
+// instantiation also serves domains with the conservative Allen-Cahn order
+// parameter (checked per domain).  MU0: the force carries mu_phi0 grad phi0
+// (Eq. 19) of the fixed solids, from lphi (Laplacian of phi) and g0 (grad
+// phi0).
+template <bool CAC, bool MU0>
+__device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<float> &kp, F2 phi, F2 phi0,
+                                             F2 mu, F2 gpx, F2 gpy, F2 gmx, F2 gmy, F2 wgx, F2 wgy, F2 lphi,
+                                             F2 g0x, F2 g0y, F2 upx, F2 upy, F2 Spx, F2 Spy, F2 php,
+                                             F2 (&f1)[9], F2 (&f2)[9], F2 &ux, F2 &uy, F2 &Sx, F2 &Sy)
 {
-    using ST = typename P::store;
-    using AX = typename P::aux;
-
-    const F2 phi0 = mk2(s_p0[hy][hx], s_p0[hy + 1][hx]);
-    F2 gpx, gpy, gmx, gmy, wgx, wgy;
-    grad9_pair<FX>(s_phi, hx, hy, gpx, gpy);
-    grad9_pair<WX>(s_mu, wx, wy, gmx, gmy);
-    grad9_pair<WX>(s_w, wx, wy, wgx, wgy);
-    const F2 mu = mk2(s_mu[wy][wx], s_mu[wy + 1][wx]);
     const F2 drho = mk2(kp.drho), half = mk2(0.5f), one = mk2(1.0f), two = mk2(2.0f);
     const F2 rho = fma2(drho, phi, mk2(kp.rhom));
     const F2 muv = fma2(mk2(kp.dmu), phi, mk2(kp.mum));
@@ -212,16 +201,13 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
         tnx = th * gpx * inv;
         tny = th * gpy * inv;
     }
-    const F2 Sx = cac ? Mdrho * (gpx - tnx) : Mdrho * gmx;
-    const F2 Sy = cac ? Mdrho * (gpy - tny) : Mdrho * gmy;
+    Sx = cac ? Mdrho * (gpx - tnx) : Mdrho * gmx;
+    Sy = cac ? Mdrho * (gpy - tny) : Mdrho * gmy;
     const F2 grx = drho * gpx, gry = drho * gpy;
     // F = mu grad phi + F_b + F_c, F_c = (-d_y w, d_x w)/2 from the previous step
     F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
     F2 Fy = fma2(mu, gpy, fma2(half, wgx, mk2(kp.Fb[1])));
     if constexpr (MU0) {
-        const F2 lphi = lap9_pair<FX>(s_phi, hx, hy);
-        F2 g0x, g0y;
-        grad9_pair<FX>(s_p0, hx, hy, g0x, g0y);
         const F2 mu0 = fma2(mk2(kp.c_pen) * phi0, phi * phi,
                             fma2(mk2(kp.c_wet) * phi, fma2(mk2(3.0f) * phi0, phi0, phi * phi - one),
                                  mk2(-kp.c_wlap) * lphi));
@@ -229,14 +215,6 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
         Fy = fma2(mu0, g0y, Fy);
     }
 
-    F2 f2[9];
-    const F2 isc2v = mk2(kp.inv_scale[1]);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const F2 v = P::MIX ? mk2(stored_to_float<ST>(f2raw[0][i]), stored_to_float<ST>(f2raw[1][i]))
-                            : mk2(Conv<P>::ld(f2raw[0][i], 1.0f), Conv<P>::ld(f2raw[1][i], 1.0f));
-        f2[i] = P::MIX ? v * isc2v : v;
-    }
     // u* (Eq. 36a)
     const F2 jx = ((f2[1] - f2[3]) + (f2[5] - f2[6])) + (f2[8] - f2[7]);
     const F2 jy = ((f2[2] - f2[4]) + (f2[5] + f2[6])) - (f2[7] + f2[8]);
@@ -245,12 +223,9 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     // penalty force f = phi0 (u_s - u*) with u_s = 0 (fixed solids)
     const F2 nphi0 = mk2(0.0f) - phi0;
     const F2 fpx = nphi0 * usx, fpy = nphi0 * usy;
-    const F2 ux = fma2(half, fpx, usx), uy = fma2(half, fpy, usy);
+    ux = fma2(half, fpx, usx);
+    uy = fma2(half, fpy, usy);
     const F2 Ftx = fma2(rho, fpx, Fx), Fty = fma2(rho, fpy, Fy);
-
-    const F2 upx = mk2((float)lag[0][0], (float)lag[1][0]), upy = mk2((float)lag[0][1], (float)lag[1][1]);
-    const F2 Spx = mk2((float)lag[0][2], (float)lag[1][2]), Spy = mk2((float)lag[0][3], (float)lag[1][3]);
-    const F2 php = mk2((float)lag[0][4], (float)lag[1][4]);
 
     // relaxation rates (Eq. 35, 1 - phi0 bounded below by solid_eps)
     const float seps = kp.solid_eps;
@@ -331,6 +306,54 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
         collide9_pair<(1u << 0) | (1u << 6) | (1u << 7), (1u << 6) | (1u << 7) | (1u << 8)>(f2, heq, hF, nS,
                                                                                            cF, cs2, cs4);
     }
+}
+
+// Stage C of the pair step: the update of the thread's two cells (Eqs. 29-38)
+// from the shared tiles (phi, phi0 on tile + 2 at (hx, hy); mu, w on tile + 1
+// at (wx, wy)) and the values gathered in stage A, then their stores.  racc:
+// PMIX, each cell's exact fixed-point phi (rest + images of the pulled movers).
+// CAC: the instantiation also serves domains with the conservative Allen-Cahn
+// order parameter (checked per domain).  MU0: the simulation holds free
+// particles, so the force carries mu_phi0 grad phi0 (Eq. 19) of the fixed
+// solids too (the tiles this kernel gets are out of every particle's reach).
+template <class P, int FX, int WX, bool CAC = false, bool MU0 = false>
+__device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p, const KParams<float> &kp,
+                                           const float (*s_phi)[FX], const float (*s_p0)[FX],
+                                           const float (*s_mu)[WX], const float (*s_w)[WX], int hx, int hy,
+                                           int wx, int wy, F2 phi, F2 (&f1)[9],
+                                           const typename P::store (&f2raw)[2][9],
+                                           const typename P::aux (&lag)[2][5],
+                                           const long long (&racc)[2], const int (&id)[2], bool valid0, bool valid1, typename P::store *fd,
+                                           long long *rd, typename P::aux *ad, int plane)
+{
+    using ST = typename P::store;
+    using AX = typename P::aux;
+
+    const F2 phi0 = mk2(s_p0[hy][hx], s_p0[hy + 1][hx]);
+    F2 gpx, gpy, gmx, gmy, wgx, wgy;
+    grad9_pair<FX>(s_phi, hx, hy, gpx, gpy);
+    grad9_pair<WX>(s_mu, wx, wy, gmx, gmy);
+    grad9_pair<WX>(s_w, wx, wy, wgx, wgy);
+    const F2 mu = mk2(s_mu[wy][wx], s_mu[wy + 1][wx]);
+    F2 lphi = mk2(0.0f), g0x = mk2(0.0f), g0y = mk2(0.0f);
+    if constexpr (MU0) {
+        lphi = lap9_pair<FX>(s_phi, hx, hy);
+        grad9_pair<FX>(s_p0, hx, hy, g0x, g0y);
+    }
+    F2 f2[9];
+    const F2 isc2v = mk2(kp.inv_scale[1]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const F2 v = P::MIX ? mk2(stored_to_float<ST>(f2raw[0][i]), stored_to_float<ST>(f2raw[1][i]))
+                            : mk2(Conv<P>::ld(f2raw[0][i], 1.0f), Conv<P>::ld(f2raw[1][i], 1.0f));
+        f2[i] = P::MIX ? v * isc2v : v;
+    }
+    const F2 upx = mk2((float)lag[0][0], (float)lag[1][0]), upy = mk2((float)lag[0][1], (float)lag[1][1]);
+    const F2 Spx = mk2((float)lag[0][2], (float)lag[1][2]), Spy = mk2((float)lag[0][3], (float)lag[1][3]);
+    const F2 php = mk2((float)lag[0][4], (float)lag[1][4]);
+    F2 ux, uy, Sx, Sy;
+    pair_physics<CAC, MU0>(p, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, lphi, g0x, g0y, upx, upy, Spx,
+                           Spy, php, f1, f2, ux, uy, Sx, Sy);
 
     // ---------------- stores (per cell) ----------------
 #pragma unroll

@@ -6,6 +6,7 @@
 #include "pf_kernels2d.cuh"
 #include "pf_kernels2d_pair.cuh"
 #include "pf_kernels2d_stage.cuh"
+#include "pf_kernels2d_strip.cuh"
 
 namespace pf {
 
@@ -94,6 +95,51 @@ static bool dispatch2d_stage(int tx, int ty, bool moving, int grid, cudaStream_t
     }
 }
 
+template <class P, int B, bool CAC>
+static bool run2d_strip(int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    auto kern = k_step2d_strip<P, B, CAC>;
+    const int dyn = StripLayout<P, B>::BYTES;
+    static bool attr = false;  // set once per instantiation (process-wide, any device)
+    if (!attr) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess) return false;
+        attr = true;
+    }
+    if (occ) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 32 * B, dyn) != cudaSuccess) n = 0;
+        *occ = n;
+        return true;
+    }
+    kern<<<grid, 32 * B, dyn, s>>>(a);
+    count_launches(1);
+    return true;
+}
+
+// strips marched in y (tile_x = strip width, tile_y = segment rows: any), and
+// the ghost-column pass it needs (grid = number of domains)
+template <class P>
+static bool dispatch2d_strip(int tx, bool moving, bool cac, bool fill, int grid, cudaStream_t s, const StepArgs &a,
+                             int *occ)
+{
+    if constexpr (P::id == 0) {
+        return false;
+    } else {
+        if (fill) {
+            if (occ) {
+                *occ = 1;
+                return true;
+            }
+            k_fill_ghosts<P><<<dim3(64, grid), 256, 0, s>>>(a.doms, a.par);
+            count_launches(1);
+            return true;
+        }
+        if (moving || tx != STRIP_SW) return false;
+        constexpr int B = strip_band<P>();
+        return cac ? run2d_strip<P, B, true>(grid, s, a, occ) : run2d_strip<P, B, false>(grid, s, a, occ);
+    }
+}
+
 template <class P, bool EXT>
 static bool dispatch2d_single(int tx, int ty, bool moving, int mode, int grid, cudaStream_t s,
                               const StepArgs &a, int *occ)
@@ -127,6 +173,8 @@ static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStre
     if (mode == MODE_STEP_PAIR) return !wall && dispatch2d_pair<P>(tx, ty, moving, cac, mu0, grid, s, a, occ);
     if (mode == MODE_STEP_STAGE)
         return !wall && !ext && !cac && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
+    if (mode == MODE_STEP_STRIP || mode == MODE_FILL_GHOSTS)
+        return !wall && dispatch2d_strip<P>(tx, moving, cac, mode == MODE_FILL_GHOSTS, grid, s, a, occ);
     return ext ? dispatch2d_single<P, true>(tx, ty, moving, mode, grid, s, a, occ)
                : dispatch2d_single<P, false>(tx, ty, moving, mode, grid, s, a, occ);
 }

@@ -1,0 +1,194 @@
+"""The strip step (kernel 4): two cells per thread on strips of 64 columns
+marched in y, every input staged in shared memory by tensor copies, periodic
+wrap in x through ghost columns.  Parity with the FP64 oracle on ragged
+grids (partial strips, partial bands, partial segments, a domain narrower
+than two ghost widths), exact mass with 16-bit storage, independence of the
+segment length, agreement with the other two-cells kernel, ghost refill
+after other kernels and after a checkpoint load, batches of uneven domains,
+and a bounded wait that runs out."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2311_05097_gb300 import workloads as W
+
+from test_gpu_parity import FIELDS, rel, run_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    from paper_2311_05097_gb300 import build
+    build.build()
+    from paper_2311_05097_gb300 import pf as _pf
+    _pf.load()
+    return _pf
+
+
+# per-field bounds (max |gpu - oracle| / max |oracle|) after 200 steps, as for
+# the other two-cells kernel: FP32 storage, and 16-bit storage of the
+# populations (FP16: 11 significant bits, BF16: 8) with FP32 arithmetic
+TOL = {
+    "p32": dict(phi=1e-5, rho=1e-5, u=1e-3, P=1e-3, mu=1e-3),
+    "fp16": dict(phi=2e-3, rho=2e-3, u=5e-2, P=5e-2, mu=5e-2),
+    "bf16": dict(phi=2e-2, rho=2e-2, u=5e-1, P=5e-1, mu=5e-1),
+}
+
+
+def field_errors(gm, om, mu_scale):
+    e = {k: rel(gm[k], om[k]) for k in ("phi", "rho", "u", "P")}
+    e["mu"] = float(np.abs(gm["mu"] - om["mu"]).max() / max(np.abs(om["mu"]).max(), mu_scale))
+    return e
+
+
+@pytest.mark.parametrize("shape,seg", [((37, 136), 16), ((70, 96), 128), ((64, 64), 8), ((24, 10), 8)])
+@pytest.mark.parametrize("precision", ["p32", "fp16", "bf16"])
+def test_strip_step_against_oracle(pf, precision, shape, seg):
+    """Ragged grids: 136 columns (two full strips and one of 8), 37 rows in
+    segments of 16 (the last one partial, its last band partial); 96 x 70 in
+    one segment (a partial strip and a partial band); 64 x 64 in eight
+    one-band segments; 10 x 24 (every cell is copied into a ghost column on
+    both sides)."""
+    c = W.small_case(shape, seed=7, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, o = run_pair(pf, c, 200, precision=precision, config=(64, seg, 4))
+    assert g.config()[3] == 4
+    e = field_errors(g.macros(), o.macros(), 3 * c["params"]["sigma"] / c["params"]["D"])
+    print("strip", precision, shape, seg, e)
+    for k, v in e.items():
+        assert v < TOL[precision][k], (k, v)
+    assert g.diagnostics()["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_strip_conserves_mass_exactly(pf, precision):
+    c = W.small_case((80, 128), seed=4, solid=True, theta_deg=60.0, u_amp=0.01)
+    g, _ = run_pair(pf, c, 0, precision=precision, oracle=False, config=(64, 32, 4))
+    m0 = g.diagnostics()["mass"]
+    g.step(1000)
+    d = g.diagnostics()
+    assert d["nan_flag"] == 0
+    assert abs(d["mass"] - m0) / np.abs(c["phi"]).sum() < 1e-13
+
+
+def test_strip_segments_are_bit_identical(pf):
+    """Every cell computes phi, mu and w from the same inputs whether its row
+    starts a segment or not: the segment length does not change the result."""
+    c = W.small_case((70, 96), seed=3, solid=True, theta_deg=120.0, u_amp=0.01)
+    a, _ = run_pair(pf, c, 150, precision="fp16", oracle=False, config=(64, 8, 4))
+    b, _ = run_pair(pf, c, 150, precision="fp16", oracle=False, config=(64, 256, 4))
+    ma, mb = a.macros(), b.macros()
+    for k in FIELDS:
+        assert np.array_equal(ma[k], mb[k]), k
+
+
+def test_strip_and_pair_agree_p32(pf):
+    """The strip step and the tiled two-cells step compute the same FP32
+    update (to rounding order of the stencil sums)."""
+    c = W.small_case((64, 96), seed=5, solid=True, theta_deg=120.0, rho_ratio=10.0)
+    a, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 16, 1))
+    b, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(64, 128, 4))
+    ma, mb = a.macros(), b.macros()
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(mb[k], ma[k]) < tol, k
+
+
+def test_strip_refills_ghosts_after_other_kernels(pf):
+    """Steps of another kernel leave the ghost columns stale; switching to the
+    strip step refills them first (a stale ghost would corrupt the columns
+    next to x = 0 and x = nx - 1)."""
+    c = W.small_case((64, 96), seed=6, solid=True, theta_deg=60.0, u_amp=0.01)
+    a, _ = run_pair(pf, c, 100, precision="p32", oracle=False, config=(32, 16, 1))
+    a.step(100)
+    b, _ = run_pair(pf, c, 100, precision="p32", oracle=False, config=(32, 16, 1))
+    b.set_config(64, 128, 4)
+    b.step(100)
+    ma, mb = a.macros(), b.macros()
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(mb[k], ma[k]) < tol, k
+
+
+def test_strip_resume_after_load_is_bit_identical(pf):
+    """A checkpoint holds no ghost columns: the loaded handle refills them
+    before its first strip step, and continues bit for bit."""
+    c = W.small_case((70, 96), seed=8, solid=True, theta_deg=60.0, u_amp=0.01)
+    a, _ = run_pair(pf, c, 120, precision="fp16", oracle=False, config=(64, 128, 4))
+    b, _ = run_pair(pf, c, 60, precision="fp16", oracle=False, config=(64, 128, 4))
+    st = b.save_state()
+    h = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    h.init(c["phi0"], c["phi"])
+    h.set_config(64, 128, 4)
+    h.load_state(st)
+    h.step(60)
+    ma, mh = a.macros(), h.macros()
+    for k in FIELDS:
+        assert np.array_equal(ma[k], mh[k]), k
+
+
+def test_batch_strip_equals_single_runs(pf):
+    """A batch of uneven domains in one strip launch: each domain evolves
+    exactly as when run alone with the same kernel; one against the oracle."""
+    cases = [W.flat_wall_drop(64, 40.0, 30.0), W.flat_wall_drop(128, 140.0, 3.0),
+             W.small_case((70, 96), seed=3, solid=True, theta_deg=120.0, u_amp=0.01)]
+    steps = 200
+    b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="fp16")
+    for i, c in enumerate(cases):
+        b.init(i, c["phi0"], c["phi"], c.get("u"))
+    b.set_config(64, 32, 4)
+    b.step(steps)
+    b.sync()
+    for i, c in enumerate(cases):
+        g, _ = run_pair(pf, c, steps, precision="fp16", oracle=False, config=(64, 32, 4))
+        mb, mg = b.macros(i), g.macros()
+        for k in FIELDS:
+            assert np.array_equal(mb[k], mg[k]), (i, k)
+    c = cases[2]
+    o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+    o.init(c["phi0"], c["phi"], c["u"])
+    o.step(steps)
+    e = field_errors(b.macros(2), o.macros(), 3 * c["params"]["sigma"] / c["params"]["D"])
+    for k, v in e.items():
+        assert v < TOL["fp16"][k], (k, v)
+
+
+def test_strip_rejected_where_not_built(pf):
+    c = W.small_case((32, 64), seed=1, solid=False)
+    g = pf.Sim(c["shape"], precision="p64", **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(64, 128, 4)  # FP64: no packed arithmetic
+    c = W.small_case((32, 65), seed=1, solid=False)
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(64, 128, 4)  # odd nx
+    c = W.wall_case((32, 64), seed=1)
+    g = pf.Sim(c["shape"], precision="fp16", walls_y=True, **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(64, 128, 4)  # walls at the ends of y
+    c = W.small_case((32, 64), seed=1, solid=False)
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    g.init(c["phi0"], c["phi"])
+    with pytest.raises(pf.PfError):
+        g.set_config(32, 128, 4)  # tile_x is the strip width, 64
+
+
+def test_strip_bounded_wait_timeout_is_reported(pf, monkeypatch):
+    """With PF_WAIT_POLLS=1 the strip step's first wait on its tensor copies
+    gives up: the copies in flight still land (a second wait with the default
+    bound), the kernel ends, the handle reports PF_ETIMEOUT, and a new handle
+    works normally."""
+    c = W.small_case((32, 64), seed=1, solid=False)
+    monkeypatch.setenv("PF_WAIT_POLLS", "1")
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    monkeypatch.delenv("PF_WAIT_POLLS")
+    g.init(c["phi0"], c["phi"])
+    g.set_config(64, 128, 4)
+    g.step(1)
+    with pytest.raises(pf.PfError) as ei:
+        g.sync()
+    assert ei.value.code == pf.PF_ETIMEOUT
+    h, _ = run_pair(pf, c, 20, precision="fp16", oracle=False, config=(64, 128, 4))
+    h.sync()
+    assert h.diagnostics()["nan_flag"] == 0
