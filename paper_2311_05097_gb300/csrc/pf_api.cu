@@ -818,19 +818,15 @@ static int strip_setup(Engine &E, int seg)
                 CUtensorMap *q = m + par * STRIP_MAPS_PER_PAR;
                 const char *f = static_cast<const char *>(d.f[par]);
                 const char *aux = static_cast<const char *>(d.aux[par]);
-                const int i1 = mix ? 1 : 0, q1 = mix ? 8 : 9;
-                rc = encode_map(q + SM_F1, ft, es, f + (size_t)i1 * d.plane * es, d.pitch, d.ny, q1, d.plane, w1);
-                if (!rc)
-                    rc = encode_map(q + SM_F2, ft, es, f + (size_t)9 * d.plane * es, d.pitch, d.ny, 9, d.plane, w1);
+                const int i1 = mix ? 1 : 0;  // (the PMIX rest population is held apart)
+                rc = encode_map(q + SM_F, ft, es, f + (size_t)i1 * d.plane * es, d.pitch, d.ny, 18 - i1, d.plane, w1);
                 if (!rc && mix)
                     rc = encode_map(q + SM_REST, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, d.rest[par], d.pitch, d.ny, 1,
                                     d.plane, STRIP_SW + 4);
                 if (!rc)
                     rc = encode_map(q + SM_US, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, aux, d.pitch, d.ny, 4, d.plane,
                                     STRIP_SW + 8);
-                if (!rc)
-                    rc = encode_map(q + SM_PHIL, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, aux + (size_t)4 * d.plane * 4,
-                                    d.pitch, d.ny, 1, d.plane, STRIP_SW);
+
             }
             if (!rc)
                 rc = encode_map(m + SM_PHI0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.phi0, d.pitch, d.ny, 1, d.plane,

@@ -50,13 +50,14 @@ constexpr int MODE_WALL = 128;
 
 // Strip step (MODE_STEP_STRIP): strips of STRIP_SW columns; 2D rows carry
 // STRIP_GHOST ghost columns (periodic images) on each side.  Tensor maps of
-// one domain: per read parity the order-parameter box, the flow box, the rest
-// population, the lagged u and S (4 planes), the lagged phi; then phi0.
+// one domain: per read parity the populations (the order parameter's staged
+// planes, then the flow's), the rest population, the lagged u and S (4
+// planes); then phi0.
 constexpr int STRIP_SW = 64;
 constexpr int STRIP_GHOST = 8;
-constexpr int STRIP_MAPS_PER_PAR = 5;
+constexpr int STRIP_MAPS_PER_PAR = 3;
 constexpr int STRIP_MAPS = 2 * STRIP_MAPS_PER_PAR + 1;
-enum StripMap { SM_F1 = 0, SM_F2 = 1, SM_REST = 2, SM_US = 3, SM_PHIL = 4 };
+enum StripMap { SM_F = 0, SM_REST = 1, SM_US = 2 };
 constexpr int SM_PHI0 = 2 * STRIP_MAPS_PER_PAR;
 
 // ---- precision policies ------------------------------------------------------------------

@@ -32,6 +32,17 @@ __device__ __forceinline__ F2 operator-(F2 a, F2 b)
 // a * b + c
 __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
 
+// 1 / a per lane with the hardware's approximate reciprocal (one instruction,
+// within 1 ulp; subnormals flushed): the arguments here are a density, a
+// bounded 1 - phi0 and inverse relaxation rates >= 1/2, all normal numbers
+__device__ __forceinline__ float rcp_fast(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ F2 rcp2(F2 a) { return mk2(rcp_fast(a.v.x), rcp_fast(a.v.y)); }
+
 // Column values a[y - 1 .. y + 2][x] of a shared array, as the pairs of the
 // stencils of rows (y, y + 1).
 template <int W>
@@ -178,12 +189,20 @@ __device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*
 // instantiation also serves domains with the conservative Allen-Cahn order
 // parameter (checked per domain).  MU0: the force carries mu_phi0 grad phi0
 // (Eq. 19) of the fixed solids, from lphi (Laplacian of phi) and g0 (grad
-// phi0).
-template <bool CAC, bool MU0>
-__device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<float> &kp, F2 phi, F2 phi0,
+// phi0).  done1(f1) runs as soon as the order-parameter lattice has collided
+// (a caller can store it and free its registers before the flow lattice
+// collides); done2(f2, u_x, u_y, S_x, S_y) at the end.
+struct NoEmit {
+    template <class... T>
+    __device__ __forceinline__ void operator()(T &&...) const {}
+};
+
+template <bool CAC, bool MU0, class E1 = NoEmit, class E2 = NoEmit>
+__device__ __forceinline__ void pair_physics(int phase_model, const KParams<float> &kp, F2 phi, F2 phi0,
                                              F2 mu, F2 gpx, F2 gpy, F2 gmx, F2 gmy, F2 wgx, F2 wgy, F2 lphi,
                                              F2 g0x, F2 g0y, F2 upx, F2 upy, F2 Spx, F2 Spy, F2 php,
-                                             F2 (&f1)[9], F2 (&f2)[9], F2 &ux, F2 &uy, F2 &Sx, F2 &Sy)
+                                             F2 (&f1)[9], F2 (&f2)[9], F2 &ux, F2 &uy, F2 &Sx, F2 &Sy,
+                                             E1 done1 = E1(), E2 done2 = E2())
 {
     const F2 drho = mk2(kp.drho), half = mk2(0.5f), one = mk2(1.0f), two = mk2(2.0f);
     const F2 rho = fma2(drho, phi, mk2(kp.rhom));
@@ -191,7 +210,7 @@ __device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<f
     const F2 Mdrho = mk2(kp.Mdrho);
     // conservative Allen-Cahn option: theta n = (2/D)(1 - phi^2) grad phi/|grad phi|
     // and the mass flux M (rho1 - rho2)/2 (grad phi - theta n)
-    const bool cac = CAC && p.phase_model == 1;
+    const bool cac = CAC && phase_model == 1;
     F2 tnx = mk2(0.0f), tny = mk2(0.0f);
     if (cac) {
         const F2 g2 = fma2(gpx, gpx, gpy * gpy);
@@ -218,7 +237,7 @@ __device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<f
     // u* (Eq. 36a)
     const F2 jx = ((f2[1] - f2[3]) + (f2[5] - f2[6])) + (f2[8] - f2[7]);
     const F2 jy = ((f2[2] - f2[4]) + (f2[5] + f2[6])) - (f2[7] + f2[8]);
-    const F2 irho = mk2(__frcp_rn(rho.v.x), __frcp_rn(rho.v.y));
+    const F2 irho = rcp2(rho);
     const F2 usx = fma2(half, Fx, jx) * irho, usy = fma2(half, Fy, jy) * irho;
     // penalty force f = phi0 (u_s - u*) with u_s = 0 (fixed solids)
     const F2 nphi0 = mk2(0.0f) - phi0;
@@ -231,7 +250,7 @@ __device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<f
     const float seps = kp.solid_eps;
     const F2 solid = one - phi0;
     const F2 solidc = mk2(fmaxf(solid.v.x, seps), fmaxf(solid.v.y, seps));
-    const F2 nu = muv * irho * mk2(__frcp_rn(solidc.v.x), __frcp_rn(solidc.v.y));
+    const F2 nu = muv * irho * rcp2(solidc);
     const F2 inv_s2a = fma2(mk2(kp.two_over_1md0), nu, half);
     const F2 inv_s2b = fma2(mk2(kp.inv_cs2), nu, half);
     const F2 Kf = mk2(kp.K);
@@ -271,6 +290,7 @@ __device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<f
         }
         // zero equilibria: moments 5, 6, 7; zero sources: 0 and 3..8
         collide9_pair<(1u << 5) | (1u << 6) | (1u << 7), 0x1F9u>(f1, heq, hF, nS, cF, cs2, cs4);
+        done1(f1);
     }
     // ---- flow lattice (Eqs. 32-34)
     {
@@ -290,8 +310,8 @@ __device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<f
         hF[4] = fma2(two * uy, Fty, fma2(tcs2 * uy, gry, fma2(c3, ugr, Spy * upy - Sy * uy)));
         hF[5] = fma2(ux, Fty, Ftx * uy) -
                 half * (fma2(Sx, uy, ux * Sy) - fma2(Spx, upy, upx * Spy)) + cs2 * fma2(ux, gry, grx * uy);
-        const F2 s2a = mk2(__frcp_rn(inv_s2a.v.x), __frcp_rn(inv_s2a.v.y));
-        const F2 s2b = mk2(__frcp_rn(inv_s2b.v.x), __frcp_rn(inv_s2b.v.y));
+        const F2 s2a = rcp2(inv_s2a);
+        const F2 s2b = rcp2(inv_s2b);
         nS[0] = mk2(-kp.s0);
         nS[1] = nS[2] = mk2(-kp.s1);
         nS[3] = nS[4] = mk2(0.0f) - s2a;
@@ -306,6 +326,7 @@ __device__ __forceinline__ void pair_physics(const DevParams &p, const KParams<f
         collide9_pair<(1u << 0) | (1u << 6) | (1u << 7), (1u << 6) | (1u << 7) | (1u << 8)>(f2, heq, hF, nS,
                                                                                            cF, cs2, cs4);
     }
+    done2(f2, ux, uy, Sx, Sy);
 }
 
 // Stage C of the pair step: the update of the thread's two cells (Eqs. 29-38)
@@ -352,8 +373,8 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     const F2 Spx = mk2((float)lag[0][2], (float)lag[1][2]), Spy = mk2((float)lag[0][3], (float)lag[1][3]);
     const F2 php = mk2((float)lag[0][4], (float)lag[1][4]);
     F2 ux, uy, Sx, Sy;
-    pair_physics<CAC, MU0>(p, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, lphi, g0x, g0y, upx, upy, Spx,
-                           Spy, php, f1, f2, ux, uy, Sx, Sy);
+    pair_physics<CAC, MU0>(p.phase_model, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, lphi, g0x, g0y, upx, upy,
+                           Spx, Spy, php, f1, f2, ux, uy, Sx, Sy);
 
     // ---------------- stores (per cell) ----------------
 #pragma unroll

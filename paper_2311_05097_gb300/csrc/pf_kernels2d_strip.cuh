@@ -10,15 +10,15 @@
 //     of the CTA owns row Y + w of the band, lane l the horizontally adjacent
 //     cells x0 + 2l, x0 + 2l + 1.
 //   - Every staged array row (both lattices' populations, the PMIX rest
-//     population, the lagged u, S and phi, phi0) is copied into a ring of
+//     population, the lagged u and S, phi0) is copied into a ring of
 //     R = 2B + 4 shared-memory rows by one 3D / 2D tensor copy per array and row
 //     (cp.async.bulk.tensor, completing on an mbarrier).  The copies of band
-//     k + 1 are issued when band k starts, so DRAM latency hides behind a whole
-//     band of work; nothing is read from global memory by the threads.
-//   - phi (Eq. 31) is computed once per row and kept in a ring of B + 4 rows,
-//     mu_phi (Eq. 9) and w = S_x u_y - u_x S_y once per row in rings of B + 4
-//     rows: the halo in y costs nothing but the few rows that start a segment;
-//     the halo in x is 2 columns on each side of the strip.
+//     k + 1 are issued early in band k, so DRAM latency hides behind most of a
+//     band of work; the threads read only the lagged phi of their own cells
+//     from global memory.
+//   - phi (Eq. 31), mu_phi (Eq. 9) and w = S_x u_y - u_x S_y are computed once
+//     per row and kept in rings of rows: the halo in y costs nothing but the
+//     few rows that start a segment; the halo in x is 2 columns on each side.
 //   - Periodic wrap in y is the row index taken modulo ny.  Periodic wrap in x
 //     comes from ghost columns: every row of every array is followed by 8
 //     columns holding copies of its first 8 cells and preceded (in the padding
@@ -53,22 +53,27 @@ struct StripLayout {
     static constexpr int W1 = SW + 2 * HS;         // population box: x0 - HS .. x0 + SW + HS
     static constexpr int WR = SW + 4;              // rest: x0 - 2 .. x0 + SW + 2
     static constexpr int WA = SW + 8;              // u, S and phi0: x0 - 4 .. x0 + SW + 4
-    static constexpr int WL = SW;                  // lagged phi: the strip
     static constexpr int B1 = Q1 * W1 * ES, B2 = 9 * W1 * ES, BR = P::MIX ? WR * 8 : 0, BA = 4 * WA * 4,
-                         BL = WL * 4, B0 = WA * 4;
-    static constexpr int O1 = 0, O2 = up128_c(O1 + B1), OR = up128_c(O2 + B2), OA = up128_c(OR + BR),
-                         OL = up128_c(OA + BA), O0 = up128_c(OL + BL);
+                         B0 = WA * 4;
+    // both lattices' staged planes arrive in one box: order parameter, then flow
+    static constexpr int O1 = 0, O2 = O1 + B1, OR = up128_c(O2 + B2), OA = up128_c(OR + BR),
+                         O0 = up128_c(OA + BA);
     static constexpr int ROW = up128_c(O0 + B0);   // bytes of one ring row
-    static constexpr int ROW_TX = B1 + B2 + BR + BA + BL + B0;  // bytes the copies of one row deliver
-    static constexpr int NBOX = P::MIX ? 6 : 5;    // tensor copies per row
+    static constexpr int ROW_TX = B1 + B2 + BR + BA + B0;  // bytes the copies of one row deliver
+    static constexpr int NBOX = P::MIX ? 4 : 3;    // tensor copies per row
     static constexpr int R = 2 * B + 4;            // staged ring rows
-    static constexpr int RW = B + 4;               // working ring rows (phi, mu, w)
-    static constexpr int FP = SW + 4;              // phi ring: x0 - 2 .. x0 + SW + 2
-    static constexpr int FM = SW + 2;              // mu and w rings: x0 - 1 .. x0 + SW + 1
-    static constexpr int OPHI = R * ROW, OMU = OPHI + RW * FP * 4, OW = OMU + RW * FM * 4;
-    static constexpr int OBAR = up128_c(OW + RW * FM * 4);
+    // working rings: phi (x0 - 2 .. x0 + SW + 2) and w (x0 - 1 .. x0 + SW + 1)
+    // are written for the next band while the last warps still read them for
+    // the current one (2B + 4 and 2B + 2 rows keep the two apart); mu
+    // (x0 - 1 .. x0 + SW + 1) is written behind a barrier (B + 4 rows)
+    static constexpr int RP = 2 * B + 4, RWW = 2 * B + 2, RM = B + 4;
+    static constexpr int FP = SW + 4, FM = SW + 2;
+    static constexpr int OPHI = R * ROW, OW = OPHI + RP * FP * 4, OMU = OW + RWW * FM * 4;
+    static constexpr int OKP = up128_c(OMU + RM * FM * 4);  // the domain's constants
+    static constexpr int OIT = up128_c(OKP + (int)sizeof(KParams<float>));  // the item's pointers and scalars
+    static constexpr int OBAR = up128_c(OIT + 64);
     static constexpr int BYTES = OBAR + 16;
-    static_assert((W1 * ES) % 16 == 0 && (WR * 8) % 16 == 0 && (WA * 4) % 16 == 0 && (WL * 4) % 16 == 0,
+    static_assert((W1 * ES) % 16 == 0 && (WR * 8) % 16 == 0 && (WA * 4) % 16 == 0,
                   "tensor boxes must be whole 16-byte chunks");
     static_assert(HS >= 3, "the order-parameter pulls of the phi frame reach 3 columns beyond the strip");
 };
@@ -139,41 +144,54 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const void *map, int x
         : "memory");
 }
 
-// Issue the copies of the nrows staged rows r0 .. r0 + nrows - 1 (segment rows,
-// wrapped to the domain) into their ring rows, completing on bar.  Warp 0 only.
-// Tensor coordinates: x' = x + STRIP_GHOST (the maps start at the left ghost
-// of row 0), y the wrapped row, plane 0 (each map starts at its first plane).
+// Issue the copies of staged row r (segment coordinates, wrapped to the
+// domain) into its ring row, completing on bar: box `box` of the row (lanes
+// 0 .. NBOX - 1 of a warp each issue one).  The expected bytes were
+// registered on bar before.  Tensor coordinates: x' = x + STRIP_GHOST (the
+// maps start at the left ghost of row 0), y the wrapped row, plane 0 (each
+// map starts at its first plane).
 template <class P, int B>
-__device__ __forceinline__ void strip_issue(const char *maps, int par, int x0, int ya, int ny, int r0, int nrows,
-                                            unsigned sbase, unsigned bar, int lane)
+__device__ __forceinline__ void strip_copy(const char *maps, int par, int x0, int ya, int ny, int r, int box,
+                                           unsigned sbase, unsigned bar)
 {
     using L = StripLayout<P, B>;
-    if (lane == 0) mbar_arrive_expect_tx(bar, (unsigned)(nrows * L::ROW_TX));
-    __syncwarp();
     const char *pm = maps + (size_t)par * STRIP_MAPS_PER_PAR * 128;
-    for (int j = lane; j < nrows * L::NBOX; j += 32) {
-        const int rr = j / L::NBOX, box = j - rr * L::NBOX;
-        const int r = r0 + rr;
-        int y = r % ny;
-        if (y < 0) y += ny;
-        const unsigned row = sbase + (unsigned)(((r - ya + 3) % L::R) * L::ROW);
-        const int g = STRIP_GHOST;
-        if (box == 0)
-            tma_load_3d(row + L::O1, pm + SM_F1 * 128, x0 - L::HS + g, y, 0, bar);
-        else if (box == 1)
-            tma_load_3d(row + L::O2, pm + SM_F2 * 128, x0 - L::HS + g, y, 0, bar);
-        else if (box == 2)
-            tma_load_3d(row + L::OA, pm + SM_US * 128, x0 - 4 + g, y, 0, bar);
-        else if (box == 3)
-            tma_load_2d(row + L::OL, pm + SM_PHIL * 128, x0 + g, y, bar);
-        else if (box == 4)
-            tma_load_2d(row + L::O0, maps + SM_PHI0 * 128, x0 - 4 + g, y, bar);
-        else
-            tma_load_2d(row + L::OR, pm + SM_REST * 128, x0 - 2 + g, y, bar);
-    }
+    int y = r % ny;
+    if (y < 0) y += ny;
+    const unsigned row = sbase + (unsigned)(((r - ya + 3) % L::R) * L::ROW);
+    const int g = STRIP_GHOST;
+    if (box == 0)
+        tma_load_3d(row + L::O1, pm + SM_F * 128, x0 - L::HS + g, y, 0, bar);
+    else if (box == 1)
+        tma_load_3d(row + L::OA, pm + SM_US * 128, x0 - 4 + g, y, 0, bar);
+    else if (box == 2)
+        tma_load_2d(row + L::O0, maps + SM_PHI0 * 128, x0 - 4 + g, y, bar);
+    else
+        tma_load_2d(row + L::OR, pm + SM_REST * 128, x0 - 2 + g, y, bar);
 }
 
+// what the update of a work item needs besides the constants (kept in shared
+// memory: the band loop holds no registers for it)
+struct StripItem {
+    void *fd;            // populations written this step
+    void *ad;            // lagged fields written this step
+    void *rd;            // rest populations written this step
+    const void *as;      // lagged fields read this step
+    int klog1;           // PMIX scale exponent of the order-parameter lattice
+    int phase_model;
+};
+
 // ---- the kernel ---------------------------------------------------------------------------------
+// Per band k (rows Y .. Y + B - 1 of the segment) the CTA runs
+//   A: phi of rows Y + 2 .. Y + B + 1 and w of rows Y + 1 .. Y + B (every warp)
+//   -- barrier 1 (also: every wait on band k's copies succeeded) --
+//      every warp issues the copies of one row of band k + 1 (into the ring
+//      rows band k - 1 used; all their readers are past barrier 1)
+//   B: mu_phi of rows Y + 1 .. Y + B
+//   -- barrier 2 --
+//   C: the update of row Y + warp
+// Phase A of band k + 1 overlaps the last warps' phase C of band k (the phi
+// and w rings are long enough to keep the rows apart).
 template <class P, int B, bool CAC>
 __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 {
@@ -182,21 +200,22 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
     using L = StripLayout<P, B>;
     static_assert(sizeof(typename P::real) == 4, "strip kernel: FP32 arithmetic policies only");
     static_assert(sizeof(AX) == 4, "strip kernel: FP32 auxiliary fields");
-    constexpr int NT = 32 * B, R = L::R, RW = L::RW, HS = L::HS;
+    constexpr int NT = 32 * B, R = L::R, HS = L::HS;
     constexpr int FP = L::FP, FM = L::FM;
     extern __shared__ __align__(128) unsigned char smem[];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned sbase = smem_u32(smem);
     const unsigned bar[2] = {sbase + L::OBAR, sbase + L::OBAR + 8};
-    float *s_phi = reinterpret_cast<float *>(smem + L::OPHI);  // [RW][FP]
-    float *s_mu = reinterpret_cast<float *>(smem + L::OMU);    // [RW][FM]
-    float *s_w = reinterpret_cast<float *>(smem + L::OW);      // [RW][FM]
+    float *s_phi = reinterpret_cast<float *>(smem + L::OPHI);  // [RP][FP]
+    float *s_w = reinterpret_cast<float *>(smem + L::OW);      // [RWW][FM]
+    float *s_mu = reinterpret_cast<float *>(smem + L::OMU);    // [RM][FM]
+    KParams<float> *s_kp = reinterpret_cast<KParams<float> *>(smem + L::OKP);
+    StripItem *s_it = reinterpret_cast<StripItem *>(smem + L::OIT);
     if (tid == 0) {
         mbar_init(bar[0], 1);
         mbar_init(bar[1], 1);
     }
-    __syncthreads();
     unsigned phase[2] = {0u, 0u};
     const int polls = A.wait_polls > 0 ? A.wait_polls : STAGE_WAIT_POLLS;
     const char *maps_all = reinterpret_cast<const char *>(A.strip_maps);
@@ -207,93 +226,105 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         const int x0 = item.y, ya = item.z, yb = item.w;
         const int nx = Dm.nx, ny = Dm.ny, pitch = Dm.pitch;
         const int plane = (int)Dm.plane;
-        const KParams<float> &kp = Dm.kf;
-        const DevParams &p = Dm.p;
-        const char *maps = maps_all + (size_t)item.x * STRIP_MAPS * 128;
         const int K = (yb - ya + B - 1) / B;
-        const float isc1 = kp.inv_scale[0];
+        auto maps = [&]() { return maps_all + (size_t)item.x * STRIP_MAPS * 128; };
 
-        // shared-memory views of staged row r (segment coordinates)
-        auto srow = [&](int r) -> const unsigned char * { return smem + ((r - ya + 3) % R) * L::ROW; };
-        auto f1s = [&](int r, int q, int c) -> ST {
-            return reinterpret_cast<const ST *>(srow(r) + L::O1)[q * L::W1 + c];
-        };
-        auto f2s = [&](int r, int q, int c) -> ST {
-            return reinterpret_cast<const ST *>(srow(r) + L::O2)[q * L::W1 + c];
-        };
-        auto phir = [&](int r) -> float * { return s_phi + ((r - ya + 2 + RW) % RW) * FP; };
-        auto mur = [&](int r) -> float * { return s_mu + ((r - ya + 1 + RW) % RW) * FM; };
-        auto wr = [&](int r) -> float * { return s_w + ((r - ya + 1 + RW) % RW) * FM; };
+        // the previous item's readers of every ring are done; its copies landed
+        fence_proxy_async_smem();
+        __syncthreads();
+        for (int j = tid; j < (int)(sizeof(KParams<float>) / 4); j += NT)
+            reinterpret_cast<float *>(s_kp)[j] = reinterpret_cast<const float *>(&Dm.kf)[j];
+        if (tid == NT - 1) {
+            s_it->fd = Dm.f[A.par ^ 1];
+            s_it->ad = Dm.aux[A.par ^ 1];
+            s_it->rd = Dm.rest[A.par ^ 1];
+            s_it->as = Dm.aux[A.par];
+            s_it->klog1 = Dm.p.klog2[0];
+            s_it->phase_model = Dm.p.phase_model;
+        }
+        if (tid == 0) mbar_arrive_expect_tx(bar[0], (unsigned)((B + 6) * L::ROW_TX));
+        __syncthreads();  // the constants and the item block are visible; the bytes are registered
+        // band group 0: rows ya - 3 .. ya + B + 2, one box per lane, rows over the warps
+        if (lane < L::NBOX)
+            for (int rr = warp; rr < B + 6; rr += B)
+                strip_copy<P, B>(maps(), A.par, x0, ya, ny, ya - 3 + rr, lane, sbase, bar[0]);
 
-        // one bounded wait on band group j (its phase advances only on success);
-        // every thread learns whether any thread's wait ran out
+        // ring rows of segment row r (byte offsets into shared memory)
+        auto srow_o = [&](int r) -> int { return ((r - ya + 3) % R) * L::ROW; };
+        auto srow = [&](int r) -> const unsigned char * { return smem + srow_o(r); };
+        auto phir = [&](int r) -> float * { return s_phi + ((r - ya + 2) % L::RP) * FP; };
+        auto wr = [&](int r) -> float * { return s_w + ((r - ya + 1) % L::RWW) * FM; };
+        auto mur = [&](int r) -> float * { return s_mu + ((r - ya + 1) % L::RM) * FM; };
+
+        // one bounded wait on band group j (its phase advances on success)
         auto wait_group = [&](int j) -> bool {
             const int b = j & 1;
             const bool ok = mbar_wait_bounded(bar[b], phase[b], polls);
-            const bool all = !__syncthreads_or(!ok);
-            if (all) phase[b] ^= 1u;
-            return all;
+            if (ok) phase[b] ^= 1u;
+            return ok;
         };
-        // a wait ran out: report, give the copies still in flight (groups
-        // [pending_from, pending_to)) a second bounded wait to land, end the CTA
-        auto give_up = [&](int pending_from, int pending_to) {
+        // a wait ran out (known to every thread at a barrier): report; a thread
+        // whose own wait failed gives band group j's copies a second bounded
+        // wait to land; end the CTA
+        auto give_up = [&](int j, bool my_ok) {
             if (tid == 0) atomicOr(A.flags, 4);
-            for (int j = pending_from; j < pending_to; ++j) {
-                const int b = j & 1;
-                mbar_wait_bounded(bar[b], phase[b], STAGE_WAIT_POLLS);  // (the default bound, not the injected one)
-                phase[b] ^= 1u;
-            }
+            if (!my_ok) mbar_wait_bounded(bar[j & 1], phase[j & 1], STAGE_WAIT_POLLS);
         };
 
-        // phi (Eq. 31) of rows [rs, rs + nr), columns x0 - 2 .. x0 + SW + 2 (pairs)
-        auto phase_phi = [&](int rs, int nr) {
-            constexpr int NP = FP / 2;
-            for (int j = tid; j < nr * NP; j += NT) {
-                const int rr = j / NP, m = j - rr * NP;
-                const int r = rs + rr;
-                const int c = 2 * m + HS - 2;  // staged column of the left cell
-                F2 phv;
-                if constexpr (P::MIX) {
-                    const longlong2 rv = *reinterpret_cast<const longlong2 *>(srow(r) + L::OR + 16 * m);
-                    F2 movers = mk2(0.0f);
+        // phase A: phi (Eq. 31) of rows [rp, rp + np_) on columns x0 - 2 .. x0 + SW + 2
+        // and w = S_x u_y - u_x S_y of the previous step on rows [rw, rw + nw),
+        // columns x0 - 1 .. x0 + SW + 1; one list of pair items
+        auto phase_a = [&](int rp, int np_, int rw, int nw) {
+            constexpr int NPP = FP / 2, NPW = FM / 2;
+            const int nphi = np_ * NPP, ntot = nphi + nw * NPW;
+            for (int j = tid; j < ntot; j += NT) {
+                if (j < nphi) {
+                    const int rr = j / NPP, m = j - rr * NPP;
+                    const int r = rp + rr;
+                    const int c = 2 * m + HS - 2;  // staged column of the left cell
+                    // rows r - 1, r, r + 1 (byte offsets of the left cell in the order-parameter box)
+                    const int ro[3] = {srow_o(r - 1) + L::O1 + c * L::ES, srow_o(r) + L::O1 + c * L::ES,
+                                       srow_o(r + 1) + L::O1 + c * L::ES};
+                    F2 phv;
+                    if constexpr (P::MIX) {
+                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(r) + L::OR + 16 * m);
+                        F2 movers = mk2(0.0f);
 #pragma unroll
-                    for (int i = 1; i < 9; ++i)
-                        movers = movers + mk2(stored_to_float<ST>(f1s(r - CY9[i], i - 1, c - CX9[i])),
-                                              stored_to_float<ST>(f1s(r - CY9[i], i - 1, c + 1 - CX9[i])));
-                    phv = fma2(movers, mk2(isc1), mk2(float_of_fixed(rv.x), float_of_fixed(rv.y)));
+                        for (int i = 1; i < 9; ++i) {
+                            const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + (i - 1) * L::W1 -
+                                          CX9[i];
+                            movers = movers + mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1]));
+                        }
+                        phv = fma2(movers, mk2(s_kp->inv_scale[0]), mk2(float_of_fixed(rv.x), float_of_fixed(rv.y)));
+                    } else {
+                        F2 acc = mk2(0.0f);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + i * L::W1 - CX9[i];
+                            acc = acc + mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
+                        }
+                        phv = acc;
+                    }
+                    *reinterpret_cast<float2 *>(phir(r) + 2 * m) = phv.v;
                 } else {
-                    F2 acc = mk2(0.0f);
+                    const int jj = j - nphi, rr = jj / NPW, m = jj - rr * NPW;
+                    const int r = rw + rr;
+                    const float *us = reinterpret_cast<const float *>(srow(r) + L::OA) + 2 * m + 3;  // left cell
+                    float wv[2];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        acc = acc + mk2(Conv<P>::ld(f1s(r - CY9[i], i, c - CX9[i]), 1.0f),
-                                        Conv<P>::ld(f1s(r - CY9[i], i, c + 1 - CX9[i]), 1.0f));
-                    phv = acc;
+                    for (int e = 0; e < 2; ++e) {
+                        const float ux = us[e], uy = us[L::WA + e];
+                        const float Sx = us[2 * L::WA + e], Sy = us[3 * L::WA + e];
+                        wv[e] = Sx * uy - ux * Sy;
+                    }
+                    *reinterpret_cast<float2 *>(wr(r) + 2 * m) = make_float2(wv[0], wv[1]);
                 }
-                *reinterpret_cast<float2 *>(phir(r) + 2 * m) = phv.v;
             }
         };
-        // w = S_x u_y - u_x S_y of the previous step, rows [rs, rs + nr),
-        // columns x0 - 1 .. x0 + SW + 1
-        auto phase_w = [&](int rs, int nr) {
+        // phase B: mu_phi (Eq. 9), rows [rs, rs + nr), columns x0 - 1 .. x0 + SW + 1
+        auto phase_b = [&](int rs, int nr) {
             constexpr int NP = FM / 2;
-            for (int j = tid; j < nr * NP; j += NT) {
-                const int rr = j / NP, m = j - rr * NP;
-                const int r = rs + rr;
-                const float *us = reinterpret_cast<const float *>(srow(r) + L::OA);
-                const int c = 2 * m + 3;  // u, S column of the left cell (x - x0 + 4)
-                float wv[2];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const float ux = us[0 * L::WA + c + e], uy = us[1 * L::WA + c + e];
-                    const float Sx = us[2 * L::WA + c + e], Sy = us[3 * L::WA + c + e];
-                    wv[e] = Sx * uy - ux * Sy;
-                }
-                *reinterpret_cast<float2 *>(wr(r) + 2 * m) = make_float2(wv[0], wv[1]);
-            }
-        };
-        // mu_phi (Eq. 9), rows [rs, rs + nr), columns x0 - 1 .. x0 + SW + 1
-        auto phase_mu = [&](int rs, int nr) {
-            constexpr int NP = FM / 2;
+            const KParams<float> &kp = *s_kp;
             const F2 c_dw = mk2(kp.c_dw), c_lap = mk2(-kp.c_lap), c_pen = mk2(kp.c_pen), c_wet = mk2(kp.c_wet),
                      c_wlap = mk2(-kp.c_wlap), one = mk2(1.0f), three = mk2(3.0f);
             for (int j = tid; j < nr * NP; j += NT) {
@@ -326,35 +357,36 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 
         // ---- prologue: rows ya - 3 .. ya + B + 2 staged; phi of ya - 2 .. ya + 1,
         // w and mu of ya - 1 .. ya
-        if (warp == 0) strip_issue<P, B>(maps, A.par, x0, ya, ny, ya - 3, B + 6, sbase, bar[0], lane);
-        if (!wait_group(0)) {
-            give_up(0, 1);
-            return;
+        {
+            const bool ok = wait_group(0);
+            if (ok) phase_a(ya - 2, 4, ya - 1, 2);
+            if (__syncthreads_or(!ok)) {
+                give_up(0, ok);
+                return;
+            }
+            phase_b(ya - 1, 2);
         }
-        phase_phi(ya - 2, 4);
-        phase_w(ya - 1, 2);
-        __syncthreads();
-        phase_mu(ya - 1, 2);
-        fence_proxy_async_smem();  // this thread's reads of the ring precede the next copies
-        __syncthreads();
 
         for (int k = 0; k < K; ++k) {
             const int Y = ya + k * B;
-            if (k + 1 < K && warp == 0)
-                strip_issue<P, B>(maps, A.par, x0, ya, ny, Y + B + 3, B, sbase, bar[(k + 1) & 1], lane);
-            if (k >= 1 && !wait_group(k)) {
-                give_up(k, k + 1 < K ? k + 2 : k + 1);
+            const bool ok = k == 0 || wait_group(k);
+            if (ok) phase_a(Y + 2, B, Y + 1, B);
+            fence_proxy_async_smem();  // this thread's reads of the ring precede the next copies
+            if (tid == 0 && k + 1 < K) mbar_arrive_expect_tx(bar[(k + 1) & 1], (unsigned)(B * L::ROW_TX));
+            if (__syncthreads_or(!ok)) {  // barrier 1
+                give_up(k, ok);  // (group k + 1 has its bytes registered but no copy issued)
                 return;
             }
-            phase_phi(Y + 2, B);
-            phase_w(Y + 1, B);
-            __syncthreads();
-            phase_mu(Y + 1, B);
-            __syncthreads();
+            // band group k + 1: rows Y + B + 3 .. Y + 2B + 2, row Y + B + 3 + warp, one box per lane
+            if (k + 1 < K && lane < L::NBOX)
+                strip_copy<P, B>(maps(), A.par, x0, ya, ny, Y + B + 3 + warp, lane, sbase, bar[(k + 1) & 1]);
+            phase_b(Y + 1, B);
+            __syncthreads();  // barrier 2
 
-            // ---- the thread's two cells: row Y + warp, columns x0 + 2 lane, + 1
+            // ---- phase C: the thread's two cells, row Y + warp, columns x0 + 2 lane, + 1
             const int r = Y + warp, x = x0 + 2 * lane;
             if (r < yb && x < nx) {
+                const KParams<float> &kp = *s_kp;
                 // phi, mu, w: 4-wide windows of rows r - 1 .. r + 1
                 float4 wph[3], wmu[3], ww[3];
 #pragma unroll
@@ -373,6 +405,9 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                     const float2 wb = *reinterpret_cast<const float2 *>(wrr + 2);
                     ww[d] = make_float4(wa.x, wa.y, wb.x, wb.y);
                 }
+                const int id = r * pitch + x;
+                const AX *as = reinterpret_cast<const AX *>(s_it->as);
+                const F2 php = {*reinterpret_cast<const float2 *>(as + 4 * plane + id)};  // previous step's phi
                 const F2 phi = mk2(wph[1].y, wph[1].z);
                 const F2 mu = mk2(wmu[1].y, wmu[1].z);
                 F2 gpx, gpy, gmx, gmy, wgx, wgy;
@@ -382,115 +417,127 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 const unsigned char *own = srow(r);
                 const float2 p0v = *reinterpret_cast<const float2 *>(own + L::O0 + 4 * (2 * lane + 4));
                 const F2 phi0 = mk2(p0v.x, p0v.y);
-                // previous step's u, S (own cells) and phi
+                // previous step's u and S
                 const float *us = reinterpret_cast<const float *>(own + L::OA) + 2 * lane + 4;
                 const F2 upx = {*reinterpret_cast<const float2 *>(us)};
                 const F2 upy = {*reinterpret_cast<const float2 *>(us + L::WA)};
                 const F2 Spx = {*reinterpret_cast<const float2 *>(us + 2 * L::WA)};
                 const F2 Spy = {*reinterpret_cast<const float2 *>(us + 3 * L::WA)};
-                const F2 php = {*reinterpret_cast<const float2 *>(own + L::OL + 8 * lane)};
                 // pulled populations (Eq. 29): cell (x, r) reads f_i at (x - c_ix, r - c_iy)
                 const int c = 2 * lane + HS;  // staged column of the left cell
+                const int ro[3] = {srow_o(r - 1) + c * L::ES, srow_o(r) + c * L::ES, srow_o(r + 1) + c * L::ES};
                 F2 f1[9], f2[9];
                 long long racc[2] = {0, 0};
-                long long rest_own[2] = {0, 0};
                 if constexpr (P::MIX) {
                     const longlong2 rv = *reinterpret_cast<const longlong2 *>(own + L::OR + 8 * (2 * lane + 2));
-                    rest_own[0] = rv.x;
-                    rest_own[1] = rv.y;
                     int sold[2] = {0, 0};
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
-                        const ST qa = f1s(r - CY9[i], i - 1, c - CX9[i]);
-                        const ST qb = f1s(r - CY9[i], i - 1, c + 1 - CX9[i]);
+                        const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]] + L::O1) + (i - 1) * L::W1 -
+                                      CX9[i];
+                        const ST qa = q[0], qb = q[1];
                         sold[0] += fix24_stored<ST>(qa);
                         sold[1] += fix24_stored<ST>(qb);
-                        f1[i] = mk2(stored_to_float<ST>(qa), stored_to_float<ST>(qb)) * mk2(isc1);
+                        f1[i] = mk2(stored_to_float<ST>(qa), stored_to_float<ST>(qb)) * mk2(kp.inv_scale[0]);
                     }
-                    f1[0] = mk2(float_of_fixed(rest_own[0]), float_of_fixed(rest_own[1]));
-                    racc[0] = rest_own[0] + fix24_to_rest(sold[0], p.klog2[0]);
-                    racc[1] = rest_own[1] + fix24_to_rest(sold[1], p.klog2[0]);
+                    f1[0] = mk2(float_of_fixed(rv.x), float_of_fixed(rv.y));
+                    racc[0] = rv.x + fix24_to_rest(sold[0], s_it->klog1);
+                    racc[1] = rv.y + fix24_to_rest(sold[1], s_it->klog1);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        f1[i] = mk2(Conv<P>::ld(f1s(r - CY9[i], i, c - CX9[i]), 1.0f),
-                                    Conv<P>::ld(f1s(r - CY9[i], i, c + 1 - CX9[i]), 1.0f));
+                    for (int i = 0; i < 9; ++i) {
+                        const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]] + L::O1) + i * L::W1 - CX9[i];
+                        f1[i] = mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
+                    }
                 }
-                const float isc2 = kp.inv_scale[1];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    const ST qa = f2s(r - CY9[i], i, c - CX9[i]), qb = f2s(r - CY9[i], i, c + 1 - CX9[i]);
+                    const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]] + L::O2) + i * L::W1 - CX9[i];
                     if constexpr (P::MIX)
-                        f2[i] = mk2(stored_to_float<ST>(qa), stored_to_float<ST>(qb)) * mk2(isc2);
+                        f2[i] = mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1])) * mk2(kp.inv_scale[1]);
                     else
-                        f2[i] = mk2(Conv<P>::ld(qa, 1.0f), Conv<P>::ld(qb, 1.0f));
+                        f2[i] = mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
                 }
-                F2 ux, uy, Sx, Sy;
-                pair_physics<CAC, false>(p, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, mk2(0.0f), mk2(0.0f),
-                                         mk2(0.0f), upx, upy, Spx, Spy, php, f1, f2, ux, uy, Sx, Sy);
-
-                // ---- stores: the pair, and its ghost copies near the x ends
-                ST *fd = reinterpret_cast<ST *>(Dm.f[A.par ^ 1]);
-                AX *ad = reinterpret_cast<AX *>(Dm.aux[A.par ^ 1]);
-                long long *rd = reinterpret_cast<long long *>(Dm.rest[A.par ^ 1]);
-                const int id = r * pitch + x;
+                // ---- stores: the pair, and its ghost copies near the x ends (each
+                // lattice as soon as it has collided)
+                ST *fd = reinterpret_cast<ST *>(s_it->fd);
+                AX *ad = reinterpret_cast<AX *>(s_it->ad);
                 const bool gl = x < STRIP_GHOST;        // copies right of the row's end
                 const bool gr = x >= nx - STRIP_GHOST;  // copies left of its start
                 int bad = 0;
-                uint32_t q1w[9], q2w[9];
-                long long rnew[2] = {0, 0};
-                if constexpr (P::MIX) {
-                    const float sc1 = kp.scale[0], sc2 = kp.scale[1];
-                    int snew[2] = {0, 0};
-#pragma unroll
-                    for (int i = 1; i < 9; ++i) {
-                        ST qa = Conv<P>::st(f1[i].v.x, sc1), qb = Conv<P>::st(f1[i].v.y, sc1);
-                        if constexpr (P::id == 3) {
-                            qa = bf16_flush(qa);
-                            qb = bf16_flush(qb);
-                        }
-                        snew[0] += fix24_sat<ST>(qa, &bad);
-                        snew[1] += fix24_sat<ST>(qb, &bad);
-                        q1w[i] = pack2<ST>(qa, qb);
-                    }
-                    // exact: the sum of each cell's order-parameter populations is unchanged
-                    rnew[0] = racc[0] - fix24_to_rest(snew[0], p.klog2[0]);
-                    rnew[1] = racc[1] - fix24_to_rest(snew[1], p.klog2[0]);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        q2w[i] = pack2<ST>(Conv<P>::st(f2[i].v.x, sc2), Conv<P>::st(f2[i].v.y, sc2));
-                }
-                auto store_all = [&](int at, bool lagged_phi) {
+                auto store1 = [&](const F2 (&g)[9]) {
                     if constexpr (P::MIX) {
+                        const float sc1 = kp.scale[0];
+                        uint32_t w[9];
+                        int snew[2] = {0, 0};
 #pragma unroll
-                        for (int i = 1; i < 9; ++i) *reinterpret_cast<uint32_t *>(fd + i * plane + at) = q1w[i];
+                        for (int i = 1; i < 9; ++i) {
+                            ST qa = Conv<P>::st(g[i].v.x, sc1), qb = Conv<P>::st(g[i].v.y, sc1);
+                            if constexpr (P::id == 3) {
+                                qa = bf16_flush(qa);
+                                qb = bf16_flush(qb);
+                            }
+                            snew[0] += fix24_sat<ST>(qa, &bad);
+                            snew[1] += fix24_sat<ST>(qb, &bad);
+                            w[i] = pack2<ST>(qa, qb);
+                        }
+                        // exact: the sum of each cell's order-parameter populations is unchanged
+                        const longlong2 rn = make_longlong2(racc[0] - fix24_to_rest(snew[0], s_it->klog1),
+                                                           racc[1] - fix24_to_rest(snew[1], s_it->klog1));
+                        long long *rd = reinterpret_cast<long long *>(s_it->rd);
+                        auto put = [&](int at) {
+#pragma unroll
+                            for (int i = 1; i < 9; ++i) *reinterpret_cast<uint32_t *>(fd + i * plane + at) = w[i];
+                            *reinterpret_cast<longlong2 *>(rd + at) = rn;
+                        };
+                        put(id);
+                        if (gl) put(id + nx);
+                        if (gr) put(id - nx);
+                    } else {
+                        auto put = [&](int at) {
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) *reinterpret_cast<float2 *>(fd + i * plane + at) = g[i].v;
+                        };
+                        put(id);
+                        if (gl) put(id + nx);
+                        if (gr) put(id - nx);
+                    }
+                };
+                F2 ux, uy, Sx, Sy;
+                auto store2 = [&](const F2 (&g)[9], F2 vx, F2 vy, F2 sx, F2 sy) {
+                    uint32_t w[9];
+                    if constexpr (P::MIX) {
+                        const float sc2 = kp.scale[1];
 #pragma unroll
                         for (int i = 0; i < 9; ++i)
-                            *reinterpret_cast<uint32_t *>(fd + (9 + i) * plane + at) = q2w[i];
-                        *reinterpret_cast<longlong2 *>(rd + at) = make_longlong2(rnew[0], rnew[1]);
-                    } else {
+                            w[i] = pack2<ST>(Conv<P>::st(g[i].v.x, sc2), Conv<P>::st(g[i].v.y, sc2));
+                    }
+                    auto put = [&](int at, bool lagged_phi) {
 #pragma unroll
                         for (int i = 0; i < 9; ++i) {
-                            *reinterpret_cast<float2 *>(fd + i * plane + at) = f1[i].v;
-                            *reinterpret_cast<float2 *>(fd + (9 + i) * plane + at) = f2[i].v;
+                            if constexpr (P::MIX)
+                                *reinterpret_cast<uint32_t *>(fd + (9 + i) * plane + at) = w[i];
+                            else
+                                *reinterpret_cast<float2 *>(fd + (9 + i) * plane + at) = g[i].v;
                         }
-                    }
-                    *reinterpret_cast<float2 *>(ad + 0 * plane + at) = ux.v;
-                    *reinterpret_cast<float2 *>(ad + 1 * plane + at) = uy.v;
-                    *reinterpret_cast<float2 *>(ad + 2 * plane + at) = Sx.v;
-                    *reinterpret_cast<float2 *>(ad + 3 * plane + at) = Sy.v;
-                    if (lagged_phi) *reinterpret_cast<float2 *>(ad + 4 * plane + at) = phi.v;
+                        *reinterpret_cast<float2 *>(ad + 0 * plane + at) = vx.v;
+                        *reinterpret_cast<float2 *>(ad + 1 * plane + at) = vy.v;
+                        *reinterpret_cast<float2 *>(ad + 2 * plane + at) = sx.v;
+                        *reinterpret_cast<float2 *>(ad + 3 * plane + at) = sy.v;
+                        if (lagged_phi) *reinterpret_cast<float2 *>(ad + 4 * plane + at) = phi.v;
+                    };
+                    put(id, true);
+                    if (gl) put(id + nx, false);
+                    if (gr) put(id - nx, false);
                 };
-                store_all(id, true);
-                if (gl) store_all(id + nx, false);
-                if (gr) store_all(id - nx, false);
+                pair_physics<CAC, false>(s_it->phase_model, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, mk2(0.0f),
+                                         mk2(0.0f), mk2(0.0f), upx, upy, Spx, Spy, php, f1, f2, ux, uy, Sx, Sy,
+                                         store1, store2);
                 if (bad) atomicOr(A.flags, 2);
-                if (!isfinite(phi.v.x) || !isfinite(phi.v.y) || !isfinite(ux.v.x) || !isfinite(ux.v.y) ||
-                    !isfinite(uy.v.x) || !isfinite(uy.v.y))
-                    atomicOr(A.flags, 1);
+                // one test for the six values: a non-finite one makes the sum non-finite
+                const F2 chk = (phi + ux) + uy;
+                if (!isfinite(chk.v.x + chk.v.y)) atomicOr(A.flags, 1);
             }
-            fence_proxy_async_smem();  // this thread's reads of the ring precede the next copies
-            __syncthreads();
         }
     }
 }
