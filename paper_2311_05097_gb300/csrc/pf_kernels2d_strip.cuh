@@ -126,6 +126,51 @@ __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(__nv_bfloat16 a, __nv_b
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
+// two FP32 values rounded to the 16-bit storage type as one 32-bit word (one
+// conversion instruction for both), and back
+template <class S>
+__device__ __forceinline__ uint32_t cvt_pair(F2 v);
+template <>
+__device__ __forceinline__ uint32_t cvt_pair<__half>(F2 v)
+{
+    const __half2 h = __float22half2_rn(v.v);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+template <>
+__device__ __forceinline__ uint32_t cvt_pair<__nv_bfloat16>(F2 v)
+{
+    const __nv_bfloat162 h = __float22bfloat162_rn(v.v);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+template <class S>
+__device__ __forceinline__ F2 uncvt_pair(uint32_t w);
+template <>
+__device__ __forceinline__ F2 uncvt_pair<__half>(uint32_t w)
+{
+    return {__half22float2(*reinterpret_cast<const __half2 *>(&w))};
+}
+template <>
+__device__ __forceinline__ F2 uncvt_pair<__nv_bfloat16>(uint32_t w)
+{
+    return {__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w))};
+}
+// a 16-bit value from its bits
+template <class S>
+__device__ __forceinline__ S half_of(unsigned short b);
+template <>
+__device__ __forceinline__ __half half_of<__half>(unsigned short b) { return __ushort_as_half(b); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 half_of<__nv_bfloat16>(unsigned short b) { return __ushort_as_bfloat16(b); }
+
+// bit pattern of FIX24_LIMIT (8.0) in the 16-bit type: |v| < 8 exactly when
+// the magnitude bits of v are below it (NaN and infinity are not)
+template <class S>
+constexpr uint32_t fix24_limit_bits();
+template <>
+constexpr uint32_t fix24_limit_bits<__half>() { return 0x4800u; }
+template <>
+constexpr uint32_t fix24_limit_bits<__nv_bfloat16>() { return 0x4100u; }
+
 // ---- tensor copies ----------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(unsigned dst, const void *map, int x, int y, unsigned bar)
 {
@@ -249,12 +294,15 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             for (int rr = warp; rr < B + 6; rr += B)
                 strip_copy<P, B>(maps(), A.par, x0, ya, ny, ya - 3 + rr, lane, sbase, bar[0]);
 
-        // ring rows of segment row r (byte offsets into shared memory)
-        auto srow_o = [&](int r) -> int { return ((r - ya + 3) % R) * L::ROW; };
+        // ring rows of segment row r: the rings hold row Y (the band's first row)
+        // in slots bR, bP, bW, bM (advanced per band); r - Y stays within a ring
+        int Y = ya, bR = 3, bP = 2, bW = 1, bM = 1;
+        auto wrapn = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
+        auto srow_o = [&](int r) -> int { return wrapn(bR + (r - Y), R) * L::ROW; };
         auto srow = [&](int r) -> const unsigned char * { return smem + srow_o(r); };
-        auto phir = [&](int r) -> float * { return s_phi + ((r - ya + 2) % L::RP) * FP; };
-        auto wr = [&](int r) -> float * { return s_w + ((r - ya + 1) % L::RWW) * FM; };
-        auto mur = [&](int r) -> float * { return s_mu + ((r - ya + 1) % L::RM) * FM; };
+        auto phir = [&](int r) -> float * { return s_phi + wrapn(bP + (r - Y), L::RP) * FP; };
+        auto wr = [&](int r) -> float * { return s_w + wrapn(bW + (r - Y), L::RWW) * FM; };
+        auto mur = [&](int r) -> float * { return s_mu + wrapn(bM + (r - Y), L::RM) * FM; };
 
         // one bounded wait on band group j (its phase advances on success)
         auto wait_group = [&](int j) -> bool {
@@ -368,7 +416,13 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         }
 
         for (int k = 0; k < K; ++k) {
-            const int Y = ya + k * B;
+            if (k > 0) {
+                Y += B;
+                bR = wrapn(bR + B, R);
+                bP = wrapn(bP + B, L::RP);
+                bW = wrapn(bW + B, L::RWW);
+                bM = wrapn(bM + B, L::RM);
+            }
             const bool ok = k == 0 || wait_group(k);
             if (ok) phase_a(Y + 2, B, Y + 1, B);
             fence_proxy_async_smem();  // this thread's reads of the ring precede the next copies
@@ -428,35 +482,42 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 const int ro[3] = {srow_o(r - 1) + c * L::ES, srow_o(r) + c * L::ES, srow_o(r + 1) + c * L::ES};
                 F2 f1[9], f2[9];
                 long long racc[2] = {0, 0};
+                // the two cells' stored values of population i (32-bit load where c_x = 0)
+                auto pulled = [&](int box, int i, int q) -> F2 {
+                    const unsigned char *b = smem + ro[1 - CY9[i]] + box + q * L::W1 * L::ES;
+                    if constexpr (P::MIX) {
+                        if (CX9[i] == 0) return uncvt_pair<ST>(*reinterpret_cast<const uint32_t *>(b));
+                        const ST *e = reinterpret_cast<const ST *>(b) - CX9[i];
+                        return mk2(stored_to_float<ST>(e[0]), stored_to_float<ST>(e[1]));
+                    } else {
+                        if (CX9[i] == 0) return {*reinterpret_cast<const float2 *>(b)};
+                        const float *e = reinterpret_cast<const float *>(b) - CX9[i];
+                        return mk2(e[0], e[1]);
+                    }
+                };
                 if constexpr (P::MIX) {
                     const longlong2 rv = *reinterpret_cast<const longlong2 *>(own + L::OR + 8 * (2 * lane + 2));
                     int sold[2] = {0, 0};
+                    const F2 s24 = mk2(16777216.0f);
 #pragma unroll
                     for (int i = 1; i < 9; ++i) {
-                        const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]] + L::O1) + (i - 1) * L::W1 -
-                                      CX9[i];
-                        const ST qa = q[0], qb = q[1];
-                        sold[0] += fix24_stored<ST>(qa);
-                        sold[1] += fix24_stored<ST>(qb);
-                        f1[i] = mk2(stored_to_float<ST>(qa), stored_to_float<ST>(qb)) * mk2(kp.inv_scale[0]);
+                        const F2 v = pulled(L::O1, i, i - 1);
+                        const F2 im = v * s24;  // exact: the value in units of 2^-24
+                        sold[0] += __float2int_rn(im.v.x);
+                        sold[1] += __float2int_rn(im.v.y);
+                        f1[i] = v * mk2(kp.inv_scale[0]);
                     }
                     f1[0] = mk2(float_of_fixed(rv.x), float_of_fixed(rv.y));
                     racc[0] = rv.x + fix24_to_rest(sold[0], s_it->klog1);
                     racc[1] = rv.y + fix24_to_rest(sold[1], s_it->klog1);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]] + L::O1) + i * L::W1 - CX9[i];
-                        f1[i] = mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
-                    }
+                    for (int i = 0; i < 9; ++i) f1[i] = pulled(L::O1, i, i);
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]] + L::O2) + i * L::W1 - CX9[i];
-                    if constexpr (P::MIX)
-                        f2[i] = mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1])) * mk2(kp.inv_scale[1]);
-                    else
-                        f2[i] = mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
+                    const F2 v = pulled(L::O2, i, i);
+                    f2[i] = P::MIX ? v * mk2(kp.inv_scale[1]) : v;
                 }
                 // ---- stores: the pair, and its ghost copies near the x ends (each
                 // lattice as soon as it has collided)
@@ -467,19 +528,35 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 int bad = 0;
                 auto store1 = [&](const F2 (&g)[9]) {
                     if constexpr (P::MIX) {
-                        const float sc1 = kp.scale[0];
-                        uint32_t w[9];
-                        int snew[2] = {0, 0};
+                        const F2 sc1 = mk2(kp.scale[0]);
+                        uint32_t w[9], amax = 0u;
 #pragma unroll
                         for (int i = 1; i < 9; ++i) {
-                            ST qa = Conv<P>::st(g[i].v.x, sc1), qb = Conv<P>::st(g[i].v.y, sc1);
-                            if constexpr (P::id == 3) {
-                                qa = bf16_flush(qa);
-                                qb = bf16_flush(qb);
+                            w[i] = cvt_pair<ST>(g[i] * sc1);
+                            if constexpr (P::id == 3)
+                                w[i] = pack2<ST>(bf16_flush(half_of<ST>((unsigned short)(w[i] & 0xffffu))),
+                                                 bf16_flush(half_of<ST>((unsigned short)(w[i] >> 16))));
+                            amax = __vmaxu2(amax, w[i] & 0x7fff7fffu);
+                        }
+                        constexpr uint32_t lim = fix24_limit_bits<ST>();
+                        if ((amax & 0xffffu) >= lim || (amax >> 16) >= lim) {
+                            // a value out of the images' range: saturate it in place (rare)
+#pragma unroll
+                            for (int i = 1; i < 9; ++i) {
+                                ST qa = half_of<ST>((unsigned short)(w[i] & 0xffffu));
+                                ST qb = half_of<ST>((unsigned short)(w[i] >> 16));
+                                fix24_sat<ST>(qa, &bad);
+                                fix24_sat<ST>(qb, &bad);
+                                w[i] = pack2<ST>(qa, qb);
                             }
-                            snew[0] += fix24_sat<ST>(qa, &bad);
-                            snew[1] += fix24_sat<ST>(qb, &bad);
-                            w[i] = pack2<ST>(qa, qb);
+                        }
+                        int snew[2] = {0, 0};
+                        const F2 s24 = mk2(16777216.0f);
+#pragma unroll
+                        for (int i = 1; i < 9; ++i) {
+                            const F2 im = uncvt_pair<ST>(w[i]) * s24;  // exact: the stored value in 2^-24 units
+                            snew[0] += __float2int_rn(im.v.x);
+                            snew[1] += __float2int_rn(im.v.y);
                         }
                         // exact: the sum of each cell's order-parameter populations is unchanged
                         const longlong2 rn = make_longlong2(racc[0] - fix24_to_rest(snew[0], s_it->klog1),
@@ -507,10 +584,9 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 auto store2 = [&](const F2 (&g)[9], F2 vx, F2 vy, F2 sx, F2 sy) {
                     uint32_t w[9];
                     if constexpr (P::MIX) {
-                        const float sc2 = kp.scale[1];
+                        const F2 sc2 = mk2(kp.scale[1]);
 #pragma unroll
-                        for (int i = 0; i < 9; ++i)
-                            w[i] = pack2<ST>(Conv<P>::st(g[i].v.x, sc2), Conv<P>::st(g[i].v.y, sc2));
+                        for (int i = 0; i < 9; ++i) w[i] = cvt_pair<ST>(g[i] * sc2);
                     }
                     auto put = [&](int at, bool lagged_phi) {
 #pragma unroll
