@@ -78,11 +78,14 @@ struct StripLayout {
     static_assert(HS >= 3, "the order-parameter pulls of the phi frame reach 3 columns beyond the strip");
 };
 
-// rows of the band of the strip kernel (one warp per row)
+// rows of the band of the strip kernel (one warp per row): 6 for 16-bit
+// storage (two CTAs of 6 warps per SM by shared memory, up to 168 registers
+// per thread: measured faster than 8 rows at 128 registers, which spill), 4
+// for FP32 storage (its staged rows are larger)
 template <class P>
 constexpr int strip_band()
 {
-    return P::MIX ? 8 : 4;
+    return P::MIX ? 6 : 4;
 }
 
 // ---- horizontal pairs ---------------------------------------------------------------------------
