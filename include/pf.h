@@ -245,8 +245,13 @@ const char *pf_last_error(void);
  * nd domains of uneven size, each with its own grid g[i] and parameters p[i]
  * (all of one precision; stream taken from p[0]).  pf_batch_step advances all
  * domains with one persistent launch per step captured in a CUDA graph; the
- * tile shape and CTAs per SM are chosen by an autotuner on the first step and
- * cached per (dim, precision, size mix). */
+ * kernel, tile shape and CTAs per SM are chosen by an autotuner (which times
+ * the candidates on the live state) in the first step call of at least 256
+ * steps, and cached per (dim, precision, size mix, domain count and the
+ * features that decide which kernels can run it: walls, the Allen-Cahn
+ * lattice, own contact angles, strip eligibility); a later batch of the same
+ * kind takes the cached configuration in its first step call of any length.
+ * Before that, steps run kernel 0. */
 int pf_batch_create(int nd, const pf_grid *g, const pf_params *p, pf_batch **out);
 int pf_batch_init(pf_batch *b, int i, const double *phi0, const double *phi, const double *u,
                   const double *P, int where);
@@ -280,7 +285,14 @@ int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int
  *      others kernel 0, chosen on the device each step (one domain, P32 or
  *      PMIX, tile 32x16, no walls, the Cahn-Hilliard lattice, no particle
  *      with its own contact angle; giving one its own angle later falls back
- *      to kernel 0).
+ *      to kernel 0);
+ *   4  2D, two horizontally adjacent cells per thread in packed FP32
+ *      arithmetic on strips of 64 columns marched in y, every input staged
+ *      in shared memory by tensor copies one band of rows ahead, periodic
+ *      wrap in x through ghost columns (P32 and PMIX, fixed solids, no walls
+ *      at the ends of y, either lattice, every nx even and >= 8;
+ *      tile_x = 64, the strip width; tile_y = the rows of one work item,
+ *      any value >= 1).
  * Adding a particle later falls back to kernel 0.  PF_EINVAL for a
  * configuration that is not built or not allowed; a pending odd time step is
  * issued first.  Call after init (pf_set_config) or at any time between steps

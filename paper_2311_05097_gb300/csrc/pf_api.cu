@@ -891,7 +891,9 @@ static int tune_features(const Engine &E)
     return (any_walls(E) ? 1 : 0) | (any_cac(E) ? 2 : 0) | (E.wv ? 4 : 0) | (strip_ok(E) ? 8 : 0);
 }
 
-static int engine_configure(Engine &E)
+// Returns PF_OK with E.tuned set, or PF_OK with E.tuned unset when nothing is
+// cached for this launch and `tune` is false (the caller then takes defaults).
+static int engine_configure(Engine &E, bool tune)
 {
     long long cells = 0;
     for (auto &m : E.mem) cells += (long long)m.d.nx * m.d.ny * m.d.nz;
@@ -927,6 +929,7 @@ static int engine_configure(Engine &E)
             return PF_OK;
         }
     }
+    if (!tune) return PF_OK;
     // (tile x, tile y, variant): one cell per thread, then two (FP32
     // arithmetic policies without free particles)
     // (kernel 2, the bulk-copy staged variant, is selectable with
@@ -1031,14 +1034,17 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
     if (n == 0) return PF_OK;
     int64_t left = n;
     if (!E.tuned) {
-        int rc;
-        if (autotune && n >= TUNE_MIN_STEPS) {
-            // the timed candidate steps are real steps of the simulation and
-            // count towards n (every configuration computes the same update)
+        int rc = PF_OK;
+        if (autotune) {
+            // a configuration cached for this kind of launch is taken at once;
+            // otherwise a call of >= TUNE_MIN_STEPS steps runs the tuner: its
+            // timed candidate steps are real steps of the simulation and count
+            // towards n (every configuration computes the same update)
             const int64_t t0 = E.t;
-            rc = engine_configure(E);
+            rc = engine_configure(E, n >= TUNE_MIN_STEPS);
             left -= E.t - t0;
-        } else {
+        }
+        if (rc == PF_OK && !E.tuned) {
             int tx = 32, ty = 8;
             if (E.dim == 3) tile_shape3d(E.prec, &tx, &ty);
             E.variant = 0;
