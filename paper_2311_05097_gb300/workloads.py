@@ -451,6 +451,28 @@ def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2
                 wall=wall)
 
 
+def cap_on_flat_wall(nx, ny, theta_deg, R, wall=8, D=4.0, theta_wet=None, sigma=0.01, M=0.1):
+    """A drop of phase 1 on the bottom of two wall slabs (``wall`` cells each) of
+    an nx x ny box, cut from a circle of radius R whose centre lies
+    R cos(theta_deg) below the wall's phi0 = 1/2 level y_w = wall - 1/2, so
+    that the circle meets that level at theta_deg (Young's construction; the
+    equal-area equilibrium cap is not sought).  Distances in y are not
+    periodic (the walls separate the periodic copies).  Equal densities and
+    viscosities; theta_wet (default theta_deg) is the prescribed angle of the
+    walls."""
+    shape = (ny, nx)
+    phi0 = slab_walls(shape, wall, D, axis=1)
+    x, y = _coords(shape)
+    yc = wall - 0.5 - R * math.cos(math.radians(theta_deg))
+    dx = x - (nx - 1) / 2.0
+    dx -= nx * np.floor(dx / nx + 0.5)
+    r = np.sqrt(dx * dx + (y - yc) ** 2)
+    phi = (1.0 - phi0) * np.tanh(2.0 * (R - r) / D)
+    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
+               theta_deg=theta_deg if theta_wet is None else theta_wet)
+    return dict(shape=shape, phi0=phi0, phi=phi, params=p, wall=wall)
+
+
 def periodic_drop(L, rho_ratio, D=4.0, sigma=0.01, M=0.1, mu1=0.1, s0=1.6):
     """A drop of radius L/4 at the centre of an L x L periodic box without
     solids (mu2 as in ``flat_wall_drop``): a batch domain for either

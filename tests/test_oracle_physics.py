@@ -514,3 +514,73 @@ def test_walls_3d_poiseuille_and_mass():
     m0 = s.diagnostics()["mass"]
     s.step(200)
     assert abs(s.diagnostics()["mass"] - m0) <= 1e-13 * np.abs(c["phi"]).sum()
+
+
+# ---- prescribed contact angle (Young's law through the wetting terms) --------------------
+
+@pytest.mark.parametrize("theta,R,nx,ny", [(45.0, 30.0, 128, 48), (135.0, 16.0, 96, 64)])
+def test_cap_at_the_prescribed_angle_stays_there(theta, R, nx, ny):
+    """The wetting terms of the free energy (Eq. 8: 3 sigma cos(theta)/D
+    phi0 phi (phi^2/3 + phi0^2 - 1) ... and its gradient term) make the
+    prescribed theta the equilibrium angle of a drop on a wall (Young's law,
+    Sec. 2.1; theta is the angle of phase 1, reading R16).  A drop cut from a
+    circle that meets the flat indicator wall at theta keeps that angle: after
+    4000 steps the fitted angle is within 2.5 deg of theta (measured 45.1 and
+    137.3 deg; the D = 4 diffuse interface and the cap's distance from the
+    equal-area equilibrium leave about 2 deg).  A wrong sign of cos(theta)
+    would make the 45 deg wall repel the drop and the 135 deg wall attract it,
+    moving each cap by tens of degrees."""
+    c = W.cap_on_flat_wall(nx, ny, theta, R)
+    a0, _ = A.contact_angle_flat(c["phi"], c["phi0"], c["params"]["D"])
+    assert abs(a0 - theta) < 0.5, a0
+    s = make(c)
+    s.step(4000)
+    a, info = A.contact_angle_flat(s.macros()["phi"], c["phi0"], c["params"]["D"])
+    assert abs(a - theta) < 2.5, (a, info)
+
+
+@pytest.mark.parametrize("theta_wet", [45.0, 135.0])
+def test_semicircle_moves_toward_the_prescribed_angle(theta_wet):
+    """The same semicircular drop (90 deg) on walls wetting at 45 and at 135 deg
+    (Eq. 8): it spreads on the first and beads up on the second, monotonically,
+    by more than 10 deg in 4000 steps (measured 90 -> 82.1 -> 75.5 and 90 ->
+    100.1 -> 107.6 at 2000 and 4000 steps), never passing the prescribed angle.
+    The direction pins the sign of the wetting terms; the amount, their
+    size."""
+    c = W.cap_on_flat_wall(96, 48, 90.0, 16.0, theta_wet=theta_wet)
+    s = make(c)
+    angles = []
+    for _ in range(2):
+        s.step(2000)
+        angles.append(A.contact_angle_flat(s.macros()["phi"], c["phi0"], c["params"]["D"])[0])
+    sign = 1.0 if theta_wet > 90.0 else -1.0
+    steps = [sign * (angles[0] - 90.0), sign * (angles[1] - angles[0])]
+    assert all(v > 0.5 for v in steps), angles
+    assert sign * (angles[1] - 90.0) > 10.0, angles
+    assert sign * (theta_wet - angles[1]) > 0.0, angles
+
+
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_drop_on_cylinder_moves_toward_hmax(theta):
+    """A drop placed on a cylinder (Sec. 4.2 layout, reduced to a 96 x 96 box:
+    cylinder radius 16, drop radius 14 centred on its top) relaxes toward the
+    equal-area equilibrium height H_max of Eqs. (40)-(41) (closed form with
+    reading R13): downward on a wetting cylinder (60 deg, H_max = 29.58 below
+    the start 30.0) and upward on a non-wetting one (120 deg, H_max = 34.97),
+    monotonically and by at least a quarter of the initial gap within 4000
+    steps (measured 43 % and 57 %), without passing H_max."""
+    Rp, R0, n = 16.0, 14.0, 96
+    cyl = (n / 2.0, 32.0)
+    c = W.drop_on_cylinder(n=n, Rp=Rp, cyl=cyl, R0=R0, theta_deg=theta, rho2=1.0, mu2=0.1)
+    c["params"] = dict(c["params"], sigma=0.01, s0=1.0)
+    Hth, _, _ = CF.hmax_on_cylinder(theta, Rp, CF.initial_drop_area(R0, Rp))
+    H0 = A.drop_top_height(c["phi"], cyl[0], cyl[1])
+    s = make(c)
+    gaps = [abs(H0 - Hth)]
+    for _ in range(2):
+        s.step(2000)
+        H = A.drop_top_height(s.macros()["phi"], cyl[0], cyl[1])
+        assert (H - Hth) * (H0 - Hth) > 0.0, (H, Hth)  # still on the starting side
+        gaps.append(abs(H - Hth))
+    assert gaps[1] < gaps[0] and gaps[2] < gaps[1], gaps
+    assert gaps[2] < 0.75 * gaps[0], gaps
