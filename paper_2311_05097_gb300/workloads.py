@@ -451,15 +451,17 @@ def flat_wall_drop(L, theta_deg, rho_ratio, r0=None, wall=8, D=4.0, mu1=0.1, mu2
                 wall=wall)
 
 
-def cap_on_flat_wall(nx, ny, theta_deg, R, wall=8, D=4.0, theta_wet=None, sigma=0.01, M=0.1):
+def cap_on_flat_wall(nx, ny, theta_deg, R, wall=8, D=4.0, theta_wet=None, sigma=0.01, M=0.1,
+                     rho_ratio=1.0, s0=1.0):
     """A drop of phase 1 on the bottom of two wall slabs (``wall`` cells each) of
     an nx x ny box, cut from a circle of radius R whose centre lies
     R cos(theta_deg) below the wall's phi0 = 1/2 level y_w = wall - 1/2, so
     that the circle meets that level at theta_deg (Young's construction; the
     equal-area equilibrium cap is not sought).  Distances in y are not
-    periodic (the walls separate the periodic copies).  Equal densities and
-    viscosities; theta_wet (default theta_deg) is the prescribed angle of the
-    walls."""
+    periodic (the walls separate the periodic copies).  Density ratio
+    rho_ratio (1: equal densities), mu2 = 0.1 rho_ratio^(-2/3) as in
+    ``flat_wall_drop``; theta_wet (default theta_deg) is the prescribed angle
+    of the walls."""
     shape = (ny, nx)
     phi0 = slab_walls(shape, wall, D, axis=1)
     x, y = _coords(shape)
@@ -468,7 +470,8 @@ def cap_on_flat_wall(nx, ny, theta_deg, R, wall=8, D=4.0, theta_wet=None, sigma=
     dx -= nx * np.floor(dx / nx + 0.5)
     r = np.sqrt(dx * dx + (y - yc) ** 2)
     phi = (1.0 - phi0) * np.tanh(2.0 * (R - r) / D)
-    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0, mu1=0.1, mu2=0.1,
+    p = params(sigma=sigma, D=D, M=M, rho1=1.0, rho2=1.0 / rho_ratio, mu1=0.1,
+               mu2=0.1 * rho_ratio ** (-2.0 / 3.0), s0=s0,
                theta_deg=theta_deg if theta_wet is None else theta_wet)
     return dict(shape=shape, phi0=phi0, phi=phi, params=p, wall=wall)
 

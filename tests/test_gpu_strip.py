@@ -26,13 +26,16 @@ def pf():
     return _pf
 
 
-# per-field bounds (max |gpu - oracle| / max |oracle|) after 200 steps, as for
-# the other two-cells kernel: FP32 storage, and 16-bit storage of the
-# populations (FP16: 11 significant bits, BF16: 8) with FP32 arithmetic
+# per-field bounds (max |gpu - oracle| / max |oracle|) after 200 steps: FP32
+# storage, and 16-bit storage of the populations (FP16: 11 significant bits,
+# BF16: 8) with FP32 arithmetic.  Measured on the four grids below (worst):
+# P32 3.4e-6, 1.5e-6, 1.3e-5, 5.7e-6, 2.9e-5; FP16 4.4e-5, 2.0e-5, 6.5e-4,
+# 2.7e-3, 2.7e-4; BF16 3.4e-4, 1.5e-4, 4.4e-3, 1.3e-2, 1.9e-3 (phi, rho, u, P,
+# mu); the bounds are about 3x those.
 TOL = {
-    "p32": dict(phi=1e-5, rho=1e-5, u=1e-3, P=1e-3, mu=1e-3),
-    "fp16": dict(phi=2e-3, rho=2e-3, u=5e-2, P=5e-2, mu=5e-2),
-    "bf16": dict(phi=2e-2, rho=2e-2, u=5e-1, P=5e-1, mu=5e-1),
+    "p32": dict(phi=1e-5, rho=5e-6, u=5e-5, P=2e-5, mu=1e-4),
+    "fp16": dict(phi=1.5e-4, rho=6e-5, u=2e-3, P=8e-3, mu=8e-4),
+    "bf16": dict(phi=1e-3, rho=5e-4, u=1.5e-2, P=4e-2, mu=6e-3),
 }
 
 
