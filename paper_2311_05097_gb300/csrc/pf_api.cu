@@ -244,6 +244,10 @@ static DevParams derive(int dim, const pf_params *p)
     // Allen-Cahn: eta mu -> phi in the equilibrium, so eta = 1 sets s_1phi
     d.eta = p->phase_model == 1 ? 1.0 : (p->eta > 0 ? p->eta : 2.0 * p->M / d.cs2);
     d.s1phi = 1.0 / (p->M / (d.eta * d.cs2) + 0.5);  // M = (1/s_1phi - 1/2) eta cs^2
+    d.unit = (std::fabs(d.s1phi - 1.0) <= 1e-12 && p->s1 == 1.0 && p->s2 == 1.0 && p->s3 == 1.0 && p->s4 == 1.0 &&
+              p->phase_model == 0)
+                 ? 1
+                 : 0;
     d.cos_t = std::cos(p->theta_deg * 3.14159265358979323846 / 180.0);
     const double d0 = p->d0;
     d.w0f = dim == 2 ? 1.0 - 2.0 * d0 + d0 * d0 : 1.0 - 3.0 * d0 + 3.0 * d0 * d0;
@@ -605,10 +609,17 @@ static bool any_cac(const Engine &E)
 }
 
 // the instantiation flags of a 2D launch
+static bool all_unit(const Engine &E)
+{
+    for (auto &m : E.mem)
+        if (!m.d.p.unit) return false;
+    return true;
+}
+
 static int mode_flags(const Engine &E)
 {
     const bool w = any_walls(E), c = any_cac(E);
-    return (w || c ? MODE_EXT : 0) | (c ? MODE_CAC : 0) | (w ? MODE_WALL : 0);
+    return (w || c ? MODE_EXT : 0) | (c ? MODE_CAC : 0) | (w ? MODE_WALL : 0) | (all_unit(E) ? MODE_UNIT : 0);
 }
 
 static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
@@ -882,13 +893,14 @@ static int ensure_ghosts(Engine &E)
 static std::mutex g_tune_mu;
 // key: (dim, precision, free particles, cell-count bucket, domain count,
 // features: bit 0 walls, bit 1 Allen-Cahn, bit 2 own contact angles, bit 3
-// the strip step can run it)
+// the strip step can run it, bit 4 unit relaxation rates)
 static std::map<std::tuple<int, int, int, long long, int, int>, std::tuple<int, int, int, int>> g_tune_cache;
 
 // the features of a launch that decide which kernels can run it
 static int tune_features(const Engine &E)
 {
-    return (any_walls(E) ? 1 : 0) | (any_cac(E) ? 2 : 0) | (E.wv ? 4 : 0) | (strip_ok(E) ? 8 : 0);
+    return (any_walls(E) ? 1 : 0) | (any_cac(E) ? 2 : 0) | (E.wv ? 4 : 0) | (strip_ok(E) ? 8 : 0) |
+           (all_unit(E) ? 16 : 0);
 }
 
 // Returns PF_OK with E.tuned set, or PF_OK with E.tuned unset when nothing is

@@ -47,6 +47,10 @@ constexpr int MODE_MU0 = 64;
 // only the single-cell kernel handles them, so the dispatchers of the other
 // 2D kernels refuse a mode carrying this bit
 constexpr int MODE_WALL = 128;
+// or'ed into a 2D mode: every domain of the launch has unit relaxation rates
+// for its non-conserved moments (DevParams::unit); kernels with a
+// specialisation for that case take it
+constexpr int MODE_UNIT = 256;
 
 // Strip step (MODE_STEP_STRIP): strips of STRIP_SW columns; 2D rows carry
 // STRIP_GHOST ghost columns (periodic images) on each side.  Tensor maps of
@@ -117,6 +121,7 @@ struct DevParams {
     int klog2[2];      // PMIX scale exponents k of 2^k
     int dim;
     int phase_model;   // 0: Cahn-Hilliard (Eq. 2); 1: conservative Allen-Cahn
+    int unit;          // s_1phi, s1, s2, s3, s4 all 1 (s_1phi to 1e-12), Cahn-Hilliard lattice
 };
 
 struct ParticleDev {

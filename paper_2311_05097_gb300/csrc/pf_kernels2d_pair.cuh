@@ -87,6 +87,36 @@ __device__ __forceinline__ F2 lap9_pair(const float (*a)[W], int x, int y)
     return fma2(mk2(2.0f / 3.0f), side, fma2(mk2(1.0f / 6.0f), diag, mk2(-10.0f / 3.0f) * Cmid));
 }
 
+// Populations of two cells from their Hermite moments: raw moments m = N_H^-1 h,
+// then f = M_0^-1 m (Eq. 38).
+__device__ __forceinline__ void from_hermite9_pair(const F2 h[9], F2 f[9], F2 cs2, F2 cs4)
+{
+    F2 m[9];
+    m[0] = h[0];
+    m[1] = h[1];
+    m[2] = h[2];
+    m[3] = fma2(cs2, h[0], h[3]);
+    m[4] = fma2(cs2, h[0], h[4]);
+    m[5] = h[5];
+    m[6] = fma2(cs2, h[1], h[6]);
+    m[7] = fma2(cs2, h[2], h[7]);
+    m[8] = fma2(cs4, h[0], fma2(cs2, h[3] + h[4], h[8]));
+    const F2 q = mk2(0.25f), hh = mk2(0.5f);
+    const F2 p56 = m[8] + m[7], n56 = m[8] - m[7];
+    const F2 s56 = m[5] + m[6], d56 = m[5] - m[6];
+    f[5] = q * (p56 + s56);
+    f[6] = q * (p56 - s56);
+    f[7] = q * (n56 + d56);
+    f[8] = q * (n56 - d56);
+    const F2 a3 = m[3] - m[8], a4 = m[4] - m[8];
+    const F2 b1 = m[1] - m[6], b2 = m[2] - m[7];
+    f[1] = hh * (a3 + b1);
+    f[3] = hh * (a3 - b1);
+    f[2] = hh * (a4 + b2);
+    f[4] = hh * (a4 - b2);
+    f[0] = (m[0] - m[3]) + (m[8] - m[4]);
+}
+
 // Hermite-moment MRT collision (Eqs. 29, 37, 38 with c = 1) of two cells:
 // h = N_H M_0 f; h* = h - S (h - heq) + (1 - S/2) hF; f* = M_0^-1 N_H^-1 h*.
 // nS = -S and cF = 1 - S/2 per moment; ZEQ / ZF flag moments whose
@@ -126,31 +156,7 @@ __device__ __forceinline__ void collide9_pair(F2 f[9], const F2 heq[9], const F2
         if (!((ZF >> k) & 1u)) r = fma2(cF[k], hF[k], r);
         h[k] = r;
     }
-    // back to raw moments (N_H^-1)
-    m[0] = h[0];
-    m[1] = h[1];
-    m[2] = h[2];
-    m[3] = fma2(cs2, h[0], h[3]);
-    m[4] = fma2(cs2, h[0], h[4]);
-    m[5] = h[5];
-    m[6] = fma2(cs2, h[1], h[6]);
-    m[7] = fma2(cs2, h[2], h[7]);
-    m[8] = fma2(cs4, h[0], fma2(cs2, h[3] + h[4], h[8]));
-    // populations (M_0^-1)
-    const F2 q = mk2(0.25f), hh = mk2(0.5f);
-    const F2 p56 = m[8] + m[7], n56 = m[8] - m[7];
-    const F2 s56 = m[5] + m[6], d56 = m[5] - m[6];
-    f[5] = q * (p56 + s56);
-    f[6] = q * (p56 - s56);
-    f[7] = q * (n56 + d56);
-    f[8] = q * (n56 - d56);
-    const F2 a3 = m[3] - m[8], a4 = m[4] - m[8];
-    const F2 b1 = m[1] - m[6], b2 = m[2] - m[7];
-    f[1] = hh * (a3 + b1);
-    f[3] = hh * (a3 - b1);
-    f[2] = hh * (a4 + b2);
-    f[4] = hh * (a4 - b2);
-    f[0] = (m[0] - m[3]) + (m[8] - m[4]);
+    from_hermite9_pair(h, f, cs2, cs4);
 }
 
 // Stage B: mu_phi (Eq. 9) on the tile + 1 frame, two rows per work item.
@@ -197,7 +203,13 @@ struct NoEmit {
     __device__ __forceinline__ void operator()(T &&...) const {}
 };
 
-template <bool CAC, bool MU0, class E1 = NoEmit, class E2 = NoEmit>
+// UNIT: every relaxation rate that multiplies a non-conserved moment is 1
+// (s_1phi, s_1, s_2 = s_3 = s_4 of Eq. 38; the paper's defaults), so for those
+// moments h* = h - (h - heq) + hF/2 = heq + hF/2 (Eq. 37): the order-parameter
+// populations after collision follow from the macroscopic fields alone (f1 is
+// not read), and of the flow moments only 0 (rate s0) and the second-order
+// ones (rates s_2a, s_2b of Eq. 35) are taken from f2.
+template <bool CAC, bool MU0, class E1 = NoEmit, class E2 = NoEmit, bool UNIT = false>
 __device__ __forceinline__ void pair_physics(int phase_model, const KParams<float> &kp, F2 phi, F2 phi0,
                                              F2 mu, F2 gpx, F2 gpy, F2 gmx, F2 gmy, F2 wgx, F2 wgy, F2 lphi,
                                              F2 g0x, F2 g0y, F2 upx, F2 upy, F2 Spx, F2 Spy, F2 php,
@@ -282,14 +294,27 @@ __device__ __forceinline__ void pair_physics(int phase_model, const KParams<floa
             hF[1] = fma2(cs2, tnx, hF[1]);
             hF[2] = fma2(cs2, tny, hF[2]);
         }
-        const float s[9] = {kp.s0, kp.s1phi, kp.s1phi, kp.s2, kp.s2, kp.s2, kp.s3, kp.s3, kp.s4};
+        if constexpr (UNIT) {
+            // h* = heq + hF/2; moment 0 is phi itself (conserved)
+            F2 hs[9];
+            hs[0] = phi;
+            hs[1] = fma2(half, hF[1], heq[1]);
+            hs[2] = fma2(half, hF[2], heq[2]);
+            hs[3] = heq[3];
+            hs[4] = heq[3];
+            hs[5] = hs[6] = hs[7] = mk2(0.0f);
+            hs[8] = heq[8];
+            from_hermite9_pair(hs, f1, cs2, cs4);
+        } else {
+            const float s[9] = {kp.s0, kp.s1phi, kp.s1phi, kp.s2, kp.s2, kp.s2, kp.s3, kp.s3, kp.s4};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            nS[k] = mk2(-s[k]);
-            cF[k] = mk2(1.0f - 0.5f * s[k]);
+            for (int k = 0; k < 9; ++k) {
+                nS[k] = mk2(-s[k]);
+                cF[k] = mk2(1.0f - 0.5f * s[k]);
+            }
+            // zero equilibria: moments 5, 6, 7; zero sources: 0 and 3..8
+            collide9_pair<(1u << 5) | (1u << 6) | (1u << 7), 0x1F9u>(f1, heq, hF, nS, cF, cs2, cs4);
         }
-        // zero equilibria: moments 5, 6, 7; zero sources: 0 and 3..8
-        collide9_pair<(1u << 5) | (1u << 6) | (1u << 7), 0x1F9u>(f1, heq, hF, nS, cF, cs2, cs4);
         done1(f1);
     }
     // ---- flow lattice (Eqs. 32-34)
@@ -312,6 +337,30 @@ __device__ __forceinline__ void pair_physics(int phase_model, const KParams<floa
                 half * (fma2(Sx, uy, ux * Sy) - fma2(Spx, upy, upx * Spy)) + cs2 * fma2(ux, gry, grx * uy);
         const F2 s2a = rcp2(inv_s2a);
         const F2 s2b = rcp2(inv_s2b);
+        if constexpr (UNIT) {
+            // moments 0 (rate s0, zero equilibrium), 3, 4 (s_2a) and 5 (s_2b)
+            // from f2; 1, 2 at heq + hF/2; 6, 7 zero; 8 at its equilibrium
+            const F2 m8r = (f2[5] + f2[7]) + (f2[6] + f2[8]);
+            const F2 m0 = f2[0] + sum_f;
+            const F2 ncs2 = mk2(0.0f) - cs2;
+            const F2 h0 = m0;
+            const F2 h3 = fma2(ncs2, m0, (f2[1] + f2[3]) + m8r);
+            const F2 h4 = fma2(ncs2, m0, (f2[2] + f2[4]) + m8r);
+            const F2 h5 = (f2[5] + f2[7]) - (f2[6] + f2[8]);
+            const F2 ns2a = mk2(0.0f) - s2a, ns2b = mk2(0.0f) - s2b;
+            F2 hs[9];
+            hs[0] = fma2(mk2(1.0f - 0.5f * kp.s0), hF[0], fma2(mk2(-kp.s0), h0, h0));
+            hs[1] = fma2(half, hF[1], heq[1]);
+            hs[2] = fma2(half, hF[2], heq[2]);
+            hs[3] = fma2(fma2(mk2(-0.5f), s2a, one), hF[3], fma2(ns2a, h3 - heq[3], h3));
+            hs[4] = fma2(fma2(mk2(-0.5f), s2a, one), hF[4], fma2(ns2a, h4 - heq[4], h4));
+            hs[5] = fma2(fma2(mk2(-0.5f), s2b, one), hF[5], fma2(ns2b, h5 - heq[5], h5));
+            hs[6] = hs[7] = mk2(0.0f);
+            hs[8] = heq[8];
+            from_hermite9_pair(hs, f2, cs2, cs4);
+            done2(f2, ux, uy, Sx, Sy);
+            return;
+        }
         nS[0] = mk2(-kp.s0);
         nS[1] = nS[2] = mk2(-kp.s1);
         nS[3] = nS[4] = mk2(0.0f) - s2a;

@@ -69,7 +69,11 @@ struct StripLayout {
     static constexpr int RP = 2 * B + 4, RWW = 2 * B + 2, RM = B + 4;
     static constexpr int FP = SW + 4, FM = SW + 2;
     static constexpr int OPHI = R * ROW, OW = OPHI + RP * FP * 4, OMU = OW + RWW * FM * 4;
-    static constexpr int OKP = up128_c(OMU + RM * FM * 4);  // the domain's constants
+    // unit rates with 16-bit storage: each cell's exact fixed-point phi
+    // (rest + images of its pulled movers, from phase A) on the strip's columns
+    static constexpr int ORA = up128_c(OMU + RM * FM * 4);
+    static constexpr int BRA = P::MIX ? RP * SW * 8 : 0;
+    static constexpr int OKP = up128_c(ORA + BRA);  // the domain's constants
     static constexpr int OIT = up128_c(OKP + (int)sizeof(KParams<float>));  // the item's pointers and scalars
     static constexpr int OBAR = up128_c(OIT + 64);
     static constexpr int BYTES = OBAR + 16;
@@ -240,7 +244,7 @@ struct StripItem {
 //   C: the update of row Y + warp
 // Phase A of band k + 1 overlaps the last warps' phase C of band k (the phi
 // and w rings are long enough to keep the rows apart).
-template <class P, int B, bool CAC>
+template <class P, int B, bool CAC, bool UNIT>
 __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 {
     using ST = typename P::store;
@@ -248,6 +252,7 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
     using L = StripLayout<P, B>;
     static_assert(sizeof(typename P::real) == 4, "strip kernel: FP32 arithmetic policies only");
     static_assert(sizeof(AX) == 4, "strip kernel: FP32 auxiliary fields");
+    static_assert(!(UNIT && CAC), "the Allen-Cahn lattice has s_1phi != 1");
     constexpr int NT = 32 * B, R = L::R, HS = L::HS;
     constexpr int FP = L::FP, FM = L::FM;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -306,6 +311,9 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         auto phir = [&](int r) -> float * { return s_phi + wrapn(bP + (r - Y), L::RP) * FP; };
         auto wr = [&](int r) -> float * { return s_w + wrapn(bW + (r - Y), L::RWW) * FM; };
         auto mur = [&](int r) -> float * { return s_mu + wrapn(bM + (r - Y), L::RM) * FM; };
+        auto rar = [&](int r) -> long long * {  // (same slots as the phi ring)
+            return reinterpret_cast<long long *>(smem + L::ORA) + wrapn(bP + (r - Y), L::RP) * L::SW;
+        };
 
         // one bounded wait on band group j (its phase advances on success)
         auto wait_group = [&](int j) -> bool {
@@ -337,7 +345,26 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                     const int ro[3] = {srow_o(r - 1) + L::O1 + c * L::ES, srow_o(r) + L::O1 + c * L::ES,
                                        srow_o(r + 1) + L::O1 + c * L::ES};
                     F2 phv;
-                    if constexpr (P::MIX) {
+                    if constexpr (P::MIX && UNIT) {
+                        // the cells' exact fixed-point phi (rest + images of the pulled
+                        // movers), rounded once to FP32; kept for the update's bookkeeping
+                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(r) + L::OR + 16 * m);
+                        int sum[2] = {0, 0};
+                        const F2 s24 = mk2(16777216.0f);
+#pragma unroll
+                        for (int i = 1; i < 9; ++i) {
+                            const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + (i - 1) * L::W1 -
+                                          CX9[i];
+                            const F2 im = mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1])) * s24;
+                            sum[0] += __float2int_rn(im.v.x);
+                            sum[1] += __float2int_rn(im.v.y);
+                        }
+                        const long long ra = rv.x + fix24_to_rest(sum[0], s_it->klog1);
+                        const long long rb = rv.y + fix24_to_rest(sum[1], s_it->klog1);
+                        phv = mk2(float_of_fixed(ra), float_of_fixed(rb));
+                        if (m >= 1 && m <= L::SW / 2)  // the strip's own columns
+                            *reinterpret_cast<longlong2 *>(rar(r) + 2 * (m - 1)) = make_longlong2(ra, rb);
+                    } else if constexpr (P::MIX) {
                         const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(r) + L::OR + 16 * m);
                         F2 movers = mk2(0.0f);
 #pragma unroll
@@ -498,7 +525,14 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                         return mk2(e[0], e[1]);
                     }
                 };
-                if constexpr (P::MIX) {
+                if constexpr (UNIT) {
+                    // the order-parameter collision does not read f1 (unit rates)
+                    if constexpr (P::MIX) {
+                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(rar(r) + 2 * lane);
+                        racc[0] = rv.x;
+                        racc[1] = rv.y;
+                    }
+                } else if constexpr (P::MIX) {
                     const longlong2 rv = *reinterpret_cast<const longlong2 *>(own + L::OR + 8 * (2 * lane + 2));
                     int sold[2] = {0, 0};
                     const F2 s24 = mk2(16777216.0f);
@@ -609,9 +643,9 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                     if (gl) put(id + nx, false);
                     if (gr) put(id - nx, false);
                 };
-                pair_physics<CAC, false>(s_it->phase_model, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, mk2(0.0f),
-                                         mk2(0.0f), mk2(0.0f), upx, upy, Spx, Spy, php, f1, f2, ux, uy, Sx, Sy,
-                                         store1, store2);
+                pair_physics<CAC, false, decltype(store1), decltype(store2), UNIT>(
+                    s_it->phase_model, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, mk2(0.0f), mk2(0.0f),
+                    mk2(0.0f), upx, upy, Spx, Spy, php, f1, f2, ux, uy, Sx, Sy, store1, store2);
                 if (bad) atomicOr(A.flags, 2);
                 // one test for the six values: a non-finite one makes the sum non-finite
                 const F2 chk = (phi + ux) + uy;

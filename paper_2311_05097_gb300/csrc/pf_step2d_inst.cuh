@@ -95,10 +95,10 @@ static bool dispatch2d_stage(int tx, int ty, bool moving, int grid, cudaStream_t
     }
 }
 
-template <class P, int B, bool CAC>
+template <class P, int B, bool CAC, bool UNIT>
 static bool run2d_strip(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
-    auto kern = k_step2d_strip<P, B, CAC>;
+    auto kern = k_step2d_strip<P, B, CAC, UNIT>;
     const int dyn = StripLayout<P, B>::BYTES;
     static bool attr = false;  // set once per instantiation (process-wide, any device)
     if (!attr) {
@@ -119,8 +119,8 @@ static bool run2d_strip(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 // strips marched in y (tile_x = strip width, tile_y = segment rows: any), and
 // the ghost-column pass it needs (grid = number of domains)
 template <class P>
-static bool dispatch2d_strip(int tx, bool moving, bool cac, bool fill, int grid, cudaStream_t s, const StepArgs &a,
-                             int *occ)
+static bool dispatch2d_strip(int tx, bool moving, bool cac, bool unit, bool fill, int grid, cudaStream_t s,
+                             const StepArgs &a, int *occ)
 {
     if constexpr (P::id == 0) {
         return false;
@@ -136,7 +136,8 @@ static bool dispatch2d_strip(int tx, bool moving, bool cac, bool fill, int grid,
         }
         if (moving || tx != STRIP_SW) return false;
         constexpr int B = strip_band<P>();
-        return cac ? run2d_strip<P, B, true>(grid, s, a, occ) : run2d_strip<P, B, false>(grid, s, a, occ);
+        if (cac) return run2d_strip<P, B, true, false>(grid, s, a, occ);
+        return unit ? run2d_strip<P, B, false, true>(grid, s, a, occ) : run2d_strip<P, B, false, false>(grid, s, a, occ);
     }
 }
 
@@ -167,14 +168,14 @@ static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStre
                        const StepArgs &a, int *occ)
 {
     const bool ext = (mode & MODE_EXT) != 0, cac = (mode & MODE_CAC) != 0, mu0 = (mode & MODE_MU0) != 0;
-    const bool wall = (mode & MODE_WALL) != 0;
-    mode &= ~(MODE_EXT | MODE_CAC | MODE_MU0 | MODE_WALL);
+    const bool wall = (mode & MODE_WALL) != 0, unit = (mode & MODE_UNIT) != 0;
+    mode &= ~(MODE_EXT | MODE_CAC | MODE_MU0 | MODE_WALL | MODE_UNIT);
     // the two-cells-per-thread kernels have no wall handling: refuse walled launches
     if (mode == MODE_STEP_PAIR) return !wall && dispatch2d_pair<P>(tx, ty, moving, cac, mu0, grid, s, a, occ);
     if (mode == MODE_STEP_STAGE)
         return !wall && !ext && !cac && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
     if (mode == MODE_STEP_STRIP || mode == MODE_FILL_GHOSTS)
-        return !wall && dispatch2d_strip<P>(tx, moving, cac, mode == MODE_FILL_GHOSTS, grid, s, a, occ);
+        return !wall && dispatch2d_strip<P>(tx, moving, cac, unit, mode == MODE_FILL_GHOSTS, grid, s, a, occ);
     return ext ? dispatch2d_single<P, true>(tx, ty, moving, mode, grid, s, a, occ)
                : dispatch2d_single<P, false>(tx, ty, moving, mode, grid, s, a, occ);
 }
