@@ -65,8 +65,11 @@ struct StripLayout {
     // working rings: phi (x0 - 2 .. x0 + SW + 2) and w (x0 - 1 .. x0 + SW + 1)
     // are written for the next band while the last warps still read them for
     // the current one (2B + 4 and 2B + 2 rows keep the two apart); mu
-    // (x0 - 1 .. x0 + SW + 1) is written behind a barrier (B + 4 rows)
-    static constexpr int RP = 2 * B + 4, RWW = 2 * B + 2, RM = B + 4;
+    // (x0 - 1 .. x0 + SW + 1) is written behind a barrier (B + 4 rows).  When
+    // 2B + 4 is a power of two every ring gets that many rows and one slot,
+    // row & (R - 1), serves them all (and the copies)
+    static constexpr bool POW2 = (R & (R - 1)) == 0;
+    static constexpr int RP = R, RWW = POW2 ? R : 2 * B + 2, RM = POW2 ? R : B + 4;
     static constexpr int FP = SW + 4, FM = SW + 2;
     static constexpr int OPHI = R * ROW, OW = OPHI + RP * FP * 4, OMU = OW + RWW * FM * 4;
     // unit rates with 16-bit storage: each cell's exact fixed-point phi
@@ -210,7 +213,8 @@ __device__ __forceinline__ void strip_copy(const char *maps, int par, int x0, in
     const char *pm = maps + (size_t)par * STRIP_MAPS_PER_PAR * 128;
     int y = r % ny;
     if (y < 0) y += ny;
-    const unsigned row = sbase + (unsigned)(((r - ya + 3) % L::R) * L::ROW);
+    const int slot = L::POW2 ? (r & (L::R - 1)) : (r - ya + 3) % L::R;
+    const unsigned row = sbase + (unsigned)(slot * L::ROW);
     const int g = STRIP_GHOST;
     if (box == 0)
         tma_load_3d(row + L::O1, pm + SM_F * 128, x0 - L::HS + g, y, 0, bar);
@@ -306,13 +310,18 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         // in slots bR, bP, bW, bM (advanced per band); r - Y stays within a ring
         int Y = ya, bR = 3, bP = 2, bW = 1, bM = 1;
         auto wrapn = [](int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); };
-        auto srow_o = [&](int r) -> int { return wrapn(bR + (r - Y), R) * L::ROW; };
+        constexpr int MSK = L::R - 1;
+        auto slotR = [&](int r) { return L::POW2 ? (r & MSK) : wrapn(bR + (r - Y), R); };
+        auto slotP = [&](int r) { return L::POW2 ? (r & MSK) : wrapn(bP + (r - Y), L::RP); };
+        auto slotW = [&](int r) { return L::POW2 ? (r & MSK) : wrapn(bW + (r - Y), L::RWW); };
+        auto slotM = [&](int r) { return L::POW2 ? (r & MSK) : wrapn(bM + (r - Y), L::RM); };
+        auto srow_o = [&](int r) -> int { return slotR(r) * L::ROW; };
         auto srow = [&](int r) -> const unsigned char * { return smem + srow_o(r); };
-        auto phir = [&](int r) -> float * { return s_phi + wrapn(bP + (r - Y), L::RP) * FP; };
-        auto wr = [&](int r) -> float * { return s_w + wrapn(bW + (r - Y), L::RWW) * FM; };
-        auto mur = [&](int r) -> float * { return s_mu + wrapn(bM + (r - Y), L::RM) * FM; };
+        auto phir = [&](int r) -> float * { return s_phi + slotP(r) * FP; };
+        auto wr = [&](int r) -> float * { return s_w + slotW(r) * FM; };
+        auto mur = [&](int r) -> float * { return s_mu + slotM(r) * FM; };
         auto rar = [&](int r) -> long long * {  // (same slots as the phi ring)
-            return reinterpret_cast<long long *>(smem + L::ORA) + wrapn(bP + (r - Y), L::RP) * L::SW;
+            return reinterpret_cast<long long *>(smem + L::ORA) + slotP(r) * L::SW;
         };
 
         // one bounded wait on band group j (its phase advances on success)
@@ -448,10 +457,12 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         for (int k = 0; k < K; ++k) {
             if (k > 0) {
                 Y += B;
-                bR = wrapn(bR + B, R);
-                bP = wrapn(bP + B, L::RP);
-                bW = wrapn(bW + B, L::RWW);
-                bM = wrapn(bM + B, L::RM);
+                if constexpr (!L::POW2) {
+                    bR = wrapn(bR + B, R);
+                    bP = wrapn(bP + B, L::RP);
+                    bW = wrapn(bW + B, L::RWW);
+                    bM = wrapn(bM + B, L::RM);
+                }
             }
             const bool ok = k == 0 || wait_group(k);
             if (ok) phase_a(Y + 2, B, Y + 1, B);
