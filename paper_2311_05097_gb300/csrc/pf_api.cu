@@ -947,10 +947,10 @@ static int engine_configure(Engine &E, bool tune)
     // (kernel 2, the bulk-copy staged variant, is selectable with
     // pf_set_config but not a candidate: it measured slower than kernel 1)
     // (kernel 4: tile = strip width x segment rows)
-    int shapes[8][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 128, 4},
-                        {64, 256, 4}};
+    int shapes[9][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 96, 4},
+                        {64, 128, 4}, {64, 192, 4}};
     int nshapes = (E.prec != PF_P64 && E.np == 0 && !any_walls(E)) ? 6 : 3;
-    if (nshapes == 6 && strip_ok(E)) nshapes = 8;
+    if (nshapes == 6 && strip_ok(E)) nshapes = 9;
     if (split_ok(E)) {
         // particle domain: also the split of near (single-cell) and far
         // (two-cells-per-thread) tiles

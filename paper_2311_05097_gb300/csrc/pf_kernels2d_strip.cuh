@@ -568,7 +568,10 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                     f2[i] = P::MIX ? v * mk2(kp.inv_scale[1]) : v;
                 }
                 // ---- stores: the pair, and its ghost copies near the x ends (each
-                // lattice as soon as it has collided)
+                // lattice as soon as it has collided), marked as streaming (evict
+                // first: they are read again only in the next step, after the rest
+                // of the state has passed through the L2, while the halo rows the
+                // neighbouring strips and segments read soon should stay)
                 ST *fd = reinterpret_cast<ST *>(s_it->fd);
                 AX *ad = reinterpret_cast<AX *>(s_it->ad);
                 const bool gl = x < STRIP_GHOST;        // copies right of the row's end
@@ -612,8 +615,8 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                         long long *rd = reinterpret_cast<long long *>(s_it->rd);
                         auto put = [&](int at) {
 #pragma unroll
-                            for (int i = 1; i < 9; ++i) *reinterpret_cast<uint32_t *>(fd + i * plane + at) = w[i];
-                            *reinterpret_cast<longlong2 *>(rd + at) = rn;
+                            for (int i = 1; i < 9; ++i) __stcs(reinterpret_cast<unsigned int *>(fd + i * plane + at), w[i]);
+                            __stcs(reinterpret_cast<longlong2 *>(rd + at), rn);
                         };
                         put(id);
                         if (gl) put(id + nx);
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                     } else {
                         auto put = [&](int at) {
 #pragma unroll
-                            for (int i = 0; i < 9; ++i) *reinterpret_cast<float2 *>(fd + i * plane + at) = g[i].v;
+                            for (int i = 0; i < 9; ++i) __stcs(reinterpret_cast<float2 *>(fd + i * plane + at), g[i].v);
                         };
                         put(id);
                         if (gl) put(id + nx);
@@ -640,15 +643,15 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 #pragma unroll
                         for (int i = 0; i < 9; ++i) {
                             if constexpr (P::MIX)
-                                *reinterpret_cast<uint32_t *>(fd + (9 + i) * plane + at) = w[i];
+                                __stcs(reinterpret_cast<unsigned int *>(fd + (9 + i) * plane + at), w[i]);
                             else
-                                *reinterpret_cast<float2 *>(fd + (9 + i) * plane + at) = g[i].v;
+                                __stcs(reinterpret_cast<float2 *>(fd + (9 + i) * plane + at), g[i].v);
                         }
-                        *reinterpret_cast<float2 *>(ad + 0 * plane + at) = vx.v;
-                        *reinterpret_cast<float2 *>(ad + 1 * plane + at) = vy.v;
-                        *reinterpret_cast<float2 *>(ad + 2 * plane + at) = sx.v;
-                        *reinterpret_cast<float2 *>(ad + 3 * plane + at) = sy.v;
-                        if (lagged_phi) *reinterpret_cast<float2 *>(ad + 4 * plane + at) = phi.v;
+                        __stcs(reinterpret_cast<float2 *>(ad + 0 * plane + at), vx.v);
+                        __stcs(reinterpret_cast<float2 *>(ad + 1 * plane + at), vy.v);
+                        __stcs(reinterpret_cast<float2 *>(ad + 2 * plane + at), sx.v);
+                        __stcs(reinterpret_cast<float2 *>(ad + 3 * plane + at), sy.v);
+                        if (lagged_phi) __stcs(reinterpret_cast<float2 *>(ad + 4 * plane + at), phi.v);
                     };
                     put(id, true);
                     if (gl) put(id + nx, false);
