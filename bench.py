@@ -162,7 +162,7 @@ def _single_workload(name, n3d=256):
         c = W.porous_drainage_3d(n=n3d)
         c["precision"] = "fp16"
         c["desc"] = ("3D drainage, %d^3, random non-overlapping spheres R 8-16 (porosity %.3f), "
-                     "theta 120 deg, body force 1e-6, density ratio 1, solid viscosity cap 10x, D3Q19 + D3Q7"
+                     "theta 120 deg, body force 1e-6, density ratio 10, solid viscosity cap 10x, D3Q19 + D3Q7"
                      % (n3d, c["porosity"]))
         return c
     if name == "drop_on_cylinder":

@@ -625,7 +625,8 @@ static int mode_flags(const Engine &E)
 static bool launch_any(const Engine &E, int tx, int ty, int mode, int grid, const StepArgs &a)
 {
     if (E.dim == 3)
-        return launch_step3d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0), grid, E.stream, a);
+        return launch_step3d(E.prec, tx, ty, E.np > 0,
+                             mode | (any_walls(E) ? MODE_EXT : 0) | (all_unit(E) ? MODE_UNIT : 0), grid, E.stream, a);
     return launch_step2d(E.prec, tx, ty, E.np > 0, mode | mode_flags(E), grid, E.stream, a);
 }
 
@@ -668,7 +669,9 @@ static bool strip_ok(const Engine &E)
 
 static int occupancy_any(const Engine &E, int tx, int ty, int mode)
 {
-    if (E.dim == 3) return occupancy_step3d(E.prec, tx, ty, E.np > 0, mode | (any_walls(E) ? MODE_EXT : 0));
+    if (E.dim == 3)
+        return occupancy_step3d(E.prec, tx, ty, E.np > 0,
+                                mode | (any_walls(E) ? MODE_EXT : 0) | (all_unit(E) ? MODE_UNIT : 0));
     return occupancy_step2d(E.prec, tx, ty, E.np > 0, mode | mode_flags(E));
 }
 

@@ -23,6 +23,9 @@ __device__ constexpr int C19Z[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1
 // opposite direction (pairs 1-2, 3-4, ..., 17-18)
 __device__ __forceinline__ int opp19(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
+template <class R>
+__device__ __forceinline__ void from_hermite19(const R h[19], R f[19], R cs2);
+
 // Hermite-moment MRT collision of one D3Q19 cell.  Raw moments m = M0 f with
 // rows 1, c_a, c_a^2, c_x c_y, c_x c_z, c_y c_z, c_x c_y^2, c_x c_z^2,
 // c_y c_x^2, c_y c_z^2, c_z c_x^2, c_z c_y^2, c_x^2 c_y^2, c_x^2 c_z^2,
@@ -79,6 +82,16 @@ __device__ __forceinline__ void collide19(R f[19], const R heq[19], const R hF[1
 #pragma unroll
     for (int k = 0; k < 19; ++k)
         h[k] = h[k] - S[k] * (h[k] - heq[k]) + (R(1) - R(0.5) * S[k]) * hF[k];
+    from_hermite19<R>(h, f, cs2);
+}
+
+// D3Q19 populations from Hermite moments: raw moments m = N_H^-1 h, then
+// f = M0^-1 m.
+template <class R>
+__device__ __forceinline__ void from_hermite19(const R h[19], R f[19], R cs2)
+{
+    const R cs4 = cs2 * cs2;
+    R m[19];
     m[0] = h[0];
     m[1] = h[1];
     m[2] = h[2];
@@ -145,6 +158,81 @@ __device__ __forceinline__ void collide7(R f[7], const R heq[7], const R hF[7], 
     f[6] = c0 + hh * (-h[3] + h[6]);
 }
 
+// The unit-rate collisions (every rate of a non-conserved moment but the
+// flow's second-order ones is 1: h* = h - (h - heq) + hF/2 = heq + hF/2,
+// Eq. 37).  D3Q7: the result follows from heq and hF alone (moment 0 is phi
+// itself); f is only written.
+template <class R>
+__device__ __forceinline__ void collide7_unit(R f[7], const R heq[7], const R hF[7], R cs2)
+{
+    R h[7];
+    h[0] = heq[0];
+#pragma unroll
+    for (int k = 1; k < 7; ++k) h[k] = heq[k] + R(0.5) * hF[k];
+    const R hh = R(0.5), c0 = hh * cs2 * h[0];
+    f[0] = (R(1) - R(3) * cs2) * h[0] - h[4] - h[5] - h[6];
+    f[1] = c0 + hh * (h[1] + h[4]);
+    f[2] = c0 + hh * (-h[1] + h[4]);
+    f[3] = c0 + hh * (h[2] + h[5]);
+    f[4] = c0 + hh * (-h[2] + h[5]);
+    f[5] = c0 + hh * (h[3] + h[6]);
+    f[6] = c0 + hh * (-h[3] + h[6]);
+}
+
+// D3Q19 at unit rates s1, s3, s4: moment 0 relaxes at s0 and the second-order
+// moments 4-9 at s_2a (diagonal) and s_2b (off-diagonal) of Eq. 35, all from
+// f; moments 1-3 and 16-18 at heq + hF/2; 10-15 are zero.
+template <class R>
+__device__ __forceinline__ void collide19_unit(R f[19], const R heq[19], const R hF[19], R s0, R s2a, R s2b,
+                                               R cs2)
+{
+    R h[19];
+    const R m0 = f[0] + f[1] + f[2] + f[3] + f[4] + f[5] + f[6] + f[7] + f[8] + f[9] + f[10] + f[11] + f[12] +
+                 f[13] + f[14] + f[15] + f[16] + f[17] + f[18];
+    const R exy = f[7] + f[8] + f[9] + f[10], exz = f[11] + f[12] + f[13] + f[14],
+            eyz = f[15] + f[16] + f[17] + f[18];
+    h[0] = m0 - s0 * m0 + (R(1) - R(0.5) * s0) * hF[0];  // (heq[0] = 0)
+    const R d[3] = {f[1] + f[2] + exy + exz - cs2 * m0, f[3] + f[4] + exy + eyz - cs2 * m0,
+                    f[5] + f[6] + exz + eyz - cs2 * m0};
+    const R o[3] = {f[7] + f[8] - f[9] - f[10], f[11] + f[12] - f[13] - f[14], f[15] + f[16] - f[17] - f[18]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        h[1 + k] = heq[1 + k] + R(0.5) * hF[1 + k];
+        h[4 + k] = d[k] - s2a * (d[k] - heq[4 + k]) + (R(1) - R(0.5) * s2a) * hF[4 + k];
+        h[7 + k] = o[k] - s2b * (o[k] - heq[7 + k]) + (R(1) - R(0.5) * s2b) * hF[7 + k];
+        h[16 + k] = heq[16 + k] + R(0.5) * hF[16 + k];
+    }
+#pragma unroll
+    for (int k = 10; k < 16; ++k) h[k] = R(0);
+    from_hermite19<R>(h, f, cs2);
+}
+
+// 1/x: the hardware's approximate reciprocal in FP32 (within 1 ulp; the
+// arguments are a density, a bounded 1 - phi0 and rates >= 1/2), the exact
+// quotient in FP64 (whose path matches the oracle to 1e-12)
+template <class R>
+__device__ __forceinline__ R recip(R x)
+{
+    if constexpr (sizeof(R) == 4) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    } else {
+        return R(1) / x;
+    }
+}
+
+// a store marked streaming (evict first): the new state is read again only in
+// the next step, after the rest of the state has passed through the L2
+template <class T>
+__device__ __forceinline__ void st_stream(T *p, T v)
+{
+    if constexpr (sizeof(T) == 2)
+        __stcs(reinterpret_cast<unsigned short *>(p), *reinterpret_cast<const unsigned short *>(&v));
+    else
+        __stcs(p, v);
+}
+
 // D3Q19 isotropic stencils (weights 1/18 faces, 1/36 edges, cs^2 = 1/3) on
 // three shared-memory planes (below, centre, above) of width W.
 template <class R, int W>
@@ -198,7 +286,9 @@ __device__ __forceinline__ R particle_phi0_3d(const ParticleDev &pp, int gx, int
 }
 
 // EXT: the instantiation also handles domains with walls at the ends of y
-template <class P, int TX, int TY, int ZC, bool MOVING, int MODE, bool EXT>
+// UNIT: every domain of the launch has unit rates for its non-conserved
+// moments (FP32 arithmetic only): the collisions above
+template <class P, int TX, int TY, int ZC, bool MOVING, int MODE, bool EXT, bool UNIT = false>
 __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
 {
     using R = typename P::real;
@@ -522,7 +612,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                 jz += (R)C19Z[i] * f2[i];
                 sum_f += f2[i];
             }
-            const R irho = R(1) / rho;
+            const R irho = recip(rho);
             const R usx = (jx + R(0.5) * Fx) * irho, usy = (jy + R(0.5) * Fy) * irho,
                     usz = (jz + R(0.5) * Fz) * irho;
             R fpx = -phi0 * usx, fpy = -phi0 * usy, fpz = -phi0 * usz;
@@ -549,7 +639,11 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
             R solid = R(1) - phi0;
             const R seps = kp.solid_eps;
             solid = solid < seps ? seps : solid;
-            const R nu = muv / (rho * solid);
+            R nu;
+            if constexpr (sizeof(R) == 4)
+                nu = muv * irho * recip(solid);
+            else
+                nu = muv / (rho * solid);
             const R inv_s2a = R(0.5) + kp.two_over_1md0 * nu;
             const R inv_s2b = R(0.5) + kp.inv_cs2 * nu;
             const R Kf = kp.K;
@@ -604,10 +698,14 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                         hF[3] += cs2 * tnz;
                     }
                     hF[4] = hF[5] = hF[6] = R(0);
-                    S[0] = kp.s0;
-                    S[1] = S[2] = S[3] = kp.s1phi;
-                    S[4] = S[5] = S[6] = kp.s2;
-                    collide7<R>(f1, heq, hF, S, cs2);
+                    if constexpr (UNIT) {
+                        collide7_unit<R>(f1, heq, hF, cs2);
+                    } else {
+                        S[0] = kp.s0;
+                        S[1] = S[2] = S[3] = kp.s1phi;
+                        S[4] = S[5] = S[6] = kp.s2;
+                        collide7<R>(f1, heq, hF, S, cs2);
+                    }
                 }
                 // flow lattice (D3Q19)
                 {
@@ -654,15 +752,19 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                     hF[16] = -c4r * Mzz;
                     hF[17] = -c4r * Myy;
                     hF[18] = -c4r * Mxx;
-                    const R s2a = R(1) / inv_s2a, s2b = R(1) / inv_s2b;
-                    S[0] = kp.s0;
-                    S[1] = S[2] = S[3] = kp.s1;
-                    S[4] = S[5] = S[6] = s2a;
-                    S[7] = S[8] = S[9] = s2b;
+                    const R s2a = recip(inv_s2a), s2b = recip(inv_s2b);
+                    if constexpr (UNIT) {
+                        collide19_unit<R>(f2, heq, hF, kp.s0, s2a, s2b, cs2);
+                    } else {
+                        S[0] = kp.s0;
+                        S[1] = S[2] = S[3] = kp.s1;
+                        S[4] = S[5] = S[6] = s2a;
+                        S[7] = S[8] = S[9] = s2b;
 #pragma unroll
-                    for (int k = 10; k < 16; ++k) S[k] = kp.s3;
-                    S[16] = S[17] = S[18] = kp.s4;
-                    collide19<R>(f2, heq, hF, S, cs2);
+                        for (int k = 10; k < 16; ++k) S[k] = kp.s3;
+                        S[16] = S[17] = S[18] = kp.s4;
+                        collide19<R>(f2, heq, hF, S, cs2);
+                    }
                 }
                 if (valid) {
                     if constexpr (P::MIX) {
@@ -676,28 +778,25 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                             ST qv = Conv<P>::st(f1[i], sc1);
                             if constexpr (P::id == 3) qv = bf16_flush(qv);
                             snew += fix24_sat<ST>(qv, &bad);
-                            fd[i * plane + id] = qv;
+                            st_stream(fd + i * plane + id, qv);
                         }
                         // exact: sum of the cell's order-parameter populations is unchanged
-                        rd[id] = rs[id] + fix24_to_rest(sold - snew, k1);
+                        st_stream(rd + id, rs[id] + fix24_to_rest(sold - snew, k1));
                         if (bad) atomicOr(A.flags, 2);
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 7; ++i) fd[i * plane + id] = Conv<P>::st(f1[i], R(1));
+                        for (int i = 0; i < 7; ++i) st_stream(fd + i * plane + id, Conv<P>::st(f1[i], R(1)));
                     }
                     const R sc2 = P::MIX ? kp.scale[1] : R(1);
 #pragma unroll
-                    for (int i = 0; i < 19; ++i) {
-                        ST qv = Conv<P>::st(f2[i], sc2);
-                        fd[(7 + i) * plane + id] = qv;
-                    }
-                    ad[0 * plane + id] = (AX)ux;
-                    ad[1 * plane + id] = (AX)uy;
-                    ad[2 * plane + id] = (AX)uz;
-                    ad[3 * plane + id] = (AX)Sx;
-                    ad[4 * plane + id] = (AX)Sy;
-                    ad[5 * plane + id] = (AX)Sz;
-                    ad[6 * plane + id] = (AX)phi;
+                    for (int i = 0; i < 19; ++i) st_stream(fd + (7 + i) * plane + id, Conv<P>::st(f2[i], sc2));
+                    st_stream(ad + 0 * plane + id, (AX)ux);
+                    st_stream(ad + 1 * plane + id, (AX)uy);
+                    st_stream(ad + 2 * plane + id, (AX)uz);
+                    st_stream(ad + 3 * plane + id, (AX)Sx);
+                    st_stream(ad + 4 * plane + id, (AX)Sy);
+                    st_stream(ad + 5 * plane + id, (AX)Sz);
+                    st_stream(ad + 6 * plane + id, (AX)phi);
                     if (!isfinite(phi) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz)) atomicOr(A.flags, 1);
                 }
                 if constexpr (MOVING) {

@@ -6,10 +6,10 @@
 
 namespace pf {
 
-template <class P, int TX, int TY, bool MOVING, int MODE, bool EXT>
+template <class P, int TX, int TY, bool MOVING, int MODE, bool EXT, bool UNIT = false>
 static bool run3d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
-    auto kern = k_step3d<P, TX, TY, ZCHUNK3D, MOVING, MODE, EXT>;
+    auto kern = k_step3d<P, TX, TY, ZCHUNK3D, MOVING, MODE, EXT, UNIT>;
     if (occ) {
         int n = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0) != cudaSuccess) n = 0;
@@ -22,11 +22,15 @@ static bool run3d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 }
 
 template <class P, int TX, int TY, bool EXT>
-static bool dispatch3d_ext(bool moving, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ)
+static bool dispatch3d_ext(bool moving, bool unit, int mode, int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
     if (mode == MODE_MACROS)
         return moving ? run3d<P, TX, TY, true, MODE_MACROS, EXT>(grid, s, a, occ)
                       : run3d<P, TX, TY, false, MODE_MACROS, EXT>(grid, s, a, occ);
+    if constexpr (sizeof(typename P::real) == 4) {
+        // unit rates (FP32 arithmetic): the specialised collisions
+        if (unit && !moving) return run3d<P, TX, TY, false, MODE_STEP, EXT, true>(grid, s, a, occ);
+    }
     return moving ? run3d<P, TX, TY, true, MODE_STEP, EXT>(grid, s, a, occ)
                   : run3d<P, TX, TY, false, MODE_STEP, EXT>(grid, s, a, occ);
 }
@@ -37,10 +41,10 @@ static bool dispatch3d(int tx, int ty, bool moving, int mode, int grid, cudaStre
                        const StepArgs &a, int *occ)
 {
     if (tx != TX || ty != TY) return false;
-    const bool ext = (mode & MODE_EXT) != 0;
-    mode &= ~(MODE_EXT | MODE_CAC);
-    return ext ? dispatch3d_ext<P, TX, TY, true>(moving, mode, grid, s, a, occ)
-               : dispatch3d_ext<P, TX, TY, false>(moving, mode, grid, s, a, occ);
+    const bool ext = (mode & MODE_EXT) != 0, unit = (mode & MODE_UNIT) != 0;
+    mode &= ~(MODE_EXT | MODE_CAC | MODE_UNIT);
+    return ext ? dispatch3d_ext<P, TX, TY, true>(moving, unit, mode, grid, s, a, occ)
+               : dispatch3d_ext<P, TX, TY, false>(moving, unit, mode, grid, s, a, occ);
 }
 
 }  // namespace pf

@@ -1053,3 +1053,35 @@ def test_batch_fp16_two_cells_kernels_equal_single_runs(pf, config):
         for k in FIELDS:
             assert np.array_equal(mb[k], mg[k]), (i, k)
         assert b.diagnostics(i)["nan_flag"] == 0
+
+
+# 3D: the D3Q7/D3Q19 step (kernel 0, one cell per thread) in FP32 arithmetic
+# with FP32, FP16 and BF16 storage, every field against the FP64 oracle after
+# 100 steps, with the paper's unit relaxation rates (the instantiation whose
+# collisions follow from the equilibria and forcing terms) and with s2, s3,
+# s4 = 1.3, 1.2, 0.9 (the general collision; the 2D set's s4 = 1.4 makes the
+# FP64 oracle itself blow up within 90 steps on this 3D case).  Measured
+# (worst of both rate sets): P32 2.3e-6, 1.1e-6, 2.4e-5, 7.0e-7, 2.3e-5; FP16
+# 1.3e-5, 5.8e-6, 6.7e-4, 1.9e-4, 1.1e-4; BF16 1.1e-4, 4.9e-5, 5.6e-3,
+# 1.3e-3, 9.5e-4 (phi, rho, u, P, mu); the bounds are about 3x those.
+MIXED_TOL_3D = {
+    "p32": dict(phi=7e-6, rho=3.5e-6, u=7.5e-5, P=2.5e-6, mu=7e-5),
+    "fp16": dict(phi=4e-5, rho=1.8e-5, u=2e-3, P=6e-4, mu=3.5e-4),
+    "bf16": dict(phi=3.5e-4, rho=1.5e-4, u=1.7e-2, P=4e-3, mu=3e-3),
+}
+
+
+@pytest.mark.parametrize("unit_rates", [True, False])
+@pytest.mark.parametrize("precision", ["p32", "fp16", "bf16"])
+def test_3d_every_field_against_oracle(pf, precision, unit_rates):
+    c = W.small_case((20, 24, 28), seed=9, solid=True, theta_deg=60.0, u_amp=0.01)
+    if not unit_rates:
+        c["params"] = dict(c["params"], s2=1.3, s3=1.2, s4=0.9)
+    g, o = run_pair(pf, c, 100, precision=precision)
+    gm, om = g.macros(), o.macros()
+    e = {k: rel(gm[k], om[k]) for k in ("phi", "rho", "u", "P")}
+    e["mu"] = float(np.abs(gm["mu"] - om["mu"]).max() / max(np.abs(om["mu"]).max(), 3 * 0.01 / 4.0))
+    print("fields3d", precision, unit_rates, {k: "%.2e" % v for k, v in e.items()})
+    for k, v in e.items():
+        assert v < MIXED_TOL_3D[precision][k], (k, v)
+    assert g.diagnostics()["nan_flag"] == 0
