@@ -838,7 +838,7 @@ static int strip_setup(Engine &E, int seg)
                     rc = encode_map(q + SM_REST, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, d.rest[par], d.pitch, d.ny, 1,
                                     d.plane, STRIP_SW + 4);
                 if (!rc)
-                    rc = encode_map(q + SM_US, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, aux, d.pitch, d.ny, 4, d.plane,
+                    rc = encode_map(q + SM_US, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, aux, d.pitch, d.ny, 5, d.plane,
                                     STRIP_SW + 8);
 
             }

@@ -55,8 +55,8 @@ constexpr int MODE_UNIT = 256;
 // Strip step (MODE_STEP_STRIP): strips of STRIP_SW columns; 2D rows carry
 // STRIP_GHOST ghost columns (periodic images) on each side.  Tensor maps of
 // one domain: per read parity the populations (the order parameter's staged
-// planes, then the flow's), the rest population, the lagged u and S (4
-// planes); then phi0.
+// planes, then the flow's), the rest population, the lagged u, S and phi
+// (5 planes); then phi0.
 constexpr int STRIP_SW = 64;
 constexpr int STRIP_GHOST = 8;
 constexpr int STRIP_MAPS_PER_PAR = 3;

@@ -10,12 +10,11 @@
 //     of the CTA owns row Y + w of the band, lane l the horizontally adjacent
 //     cells x0 + 2l, x0 + 2l + 1.
 //   - Every staged array row (both lattices' populations, the PMIX rest
-//     population, the lagged u and S, phi0) is copied into a ring of
+//     population, the lagged u, S and phi, phi0) is copied into a ring of
 //     R = 2B + 4 shared-memory rows by one 3D / 2D tensor copy per array and row
 //     (cp.async.bulk.tensor, completing on an mbarrier).  The copies of band
 //     k + 1 are issued early in band k, so DRAM latency hides behind most of a
-//     band of work; the threads read only the lagged phi of their own cells
-//     from global memory.
+//     band of work; the update reads nothing from global memory.
 //   - phi (Eq. 31), mu_phi (Eq. 9) and w = S_x u_y - u_x S_y are computed once
 //     per row and kept in rings of rows: the halo in y costs nothing but the
 //     few rows that start a segment; the halo in x is 2 columns on each side.
@@ -52,8 +51,8 @@ struct StripLayout {
     static constexpr int I1 = P::MIX ? 1 : 0;      // first staged order-parameter plane
     static constexpr int W1 = SW + 2 * HS;         // population box: x0 - HS .. x0 + SW + HS
     static constexpr int WR = SW + 4;              // rest: x0 - 2 .. x0 + SW + 2
-    static constexpr int WA = SW + 8;              // u, S and phi0: x0 - 4 .. x0 + SW + 4
-    static constexpr int B1 = Q1 * W1 * ES, B2 = 9 * W1 * ES, BR = P::MIX ? WR * 8 : 0, BA = 4 * WA * 4,
+    static constexpr int WA = SW + 8;              // lagged u, S, phi and phi0: x0 - 4 .. x0 + SW + 4
+    static constexpr int B1 = Q1 * W1 * ES, B2 = 9 * W1 * ES, BR = P::MIX ? WR * 8 : 0, BA = 5 * WA * 4,
                          B0 = WA * 4;
     // both lattices' staged planes arrive in one box: order parameter, then flow
     static constexpr int O1 = 0, O2 = O1 + B1, OR = up128_c(O2 + B2), OA = up128_c(OR + BR),
@@ -232,7 +231,6 @@ struct StripItem {
     void *fd;            // populations written this step
     void *ad;            // lagged fields written this step
     void *rd;            // rest populations written this step
-    const void *as;      // lagged fields read this step
     int klog1;           // PMIX scale exponent of the order-parameter lattice
     int phase_model;
 };
@@ -295,7 +293,6 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             s_it->fd = Dm.f[A.par ^ 1];
             s_it->ad = Dm.aux[A.par ^ 1];
             s_it->rd = Dm.rest[A.par ^ 1];
-            s_it->as = Dm.aux[A.par];
             s_it->klog1 = Dm.p.klog2[0];
             s_it->phase_model = Dm.p.phase_model;
         }
@@ -501,8 +498,6 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                     ww[d] = make_float4(wa.x, wa.y, wb.x, wb.y);
                 }
                 const int id = r * pitch + x;
-                const AX *as = reinterpret_cast<const AX *>(s_it->as);
-                const F2 php = {*reinterpret_cast<const float2 *>(as + 4 * plane + id)};  // previous step's phi
                 const F2 phi = mk2(wph[1].y, wph[1].z);
                 const F2 mu = mk2(wmu[1].y, wmu[1].z);
                 F2 gpx, gpy, gmx, gmy, wgx, wgy;
@@ -518,6 +513,7 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 const F2 upy = {*reinterpret_cast<const float2 *>(us + L::WA)};
                 const F2 Spx = {*reinterpret_cast<const float2 *>(us + 2 * L::WA)};
                 const F2 Spy = {*reinterpret_cast<const float2 *>(us + 3 * L::WA)};
+                const F2 php = {*reinterpret_cast<const float2 *>(us + 4 * L::WA)};  // previous step's phi
                 // pulled populations (Eq. 29): cell (x, r) reads f_i at (x - c_ix, r - c_iy)
                 const int c = 2 * lane + HS;  // staged column of the left cell
                 const int ro[3] = {srow_o(r - 1) + c * L::ES, srow_o(r) + c * L::ES, srow_o(r + 1) + c * L::ES};
@@ -673,7 +669,7 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 // the 8 columns after each row's end copy its first 8 cells, the 8 before its
 // start (the end of the previous row's padding; before row 0, the front pad of
 // the array) copy its last 8 cells.  Populations, the PMIX rest population,
-// the lagged u and S and phi0; the lagged phi is read at the cell only.  Grid
+// the lagged u and S and phi0 (the lagged phi is used at the cell only).  Grid
 // (any, number of domains); needs nx >= 8.
 template <class P>
 __global__ void k_fill_ghosts(const DomainDev *doms, int par)
