@@ -494,15 +494,15 @@ def run_single(args, dist, rank, world, local):
     if args.config:
         sim.set_config(*args.config)
     else:
-        # the autotuner runs in the first call of >= 256 steps; it runs on a
-        # scratch copy of the workload so the timed run starts at step 0
-        # (the water entry diverges after ~300 steps at its parameters)
+        # the autotuner times its candidates on a scratch copy of the workload
+        # so the timed run starts at step 0 (the water entry diverges after
+        # ~300 steps at its parameters)
         scratch = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream,
                          walls_y=case.get("walls_y", False), **case["params"])
         for k, pp in enumerate(case.get("particles", [])):
             scratch.set_particle(k, **pp)
         scratch.init(case["phi0"], case["phi"], case.get("u"))
-        scratch.step(256)
+        scratch.autotune()
         tx, ty, cps, kern = scratch.config()
         scratch.close()
         sim.set_config(tx, ty, kern, cps)
@@ -564,6 +564,10 @@ def run_single(args, dist, rank, world, local):
         s2 = pf.Sim(case["shape"], precision=prec, stream=stream.cuda_stream,
                  walls_y=case.get("walls_y", False), **case["params"])
         parts = case.get("particles", [])
+        for k, pp in enumerate(parts):
+            s2.set_particle(k, **pp)
+        s2.init(case["phi0"], case["phi"], case.get("u"))
+        s2.set_config(tx, ty, kern, cps)  # the timed run's launch configuration (kept across inits)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(iters):

@@ -76,8 +76,9 @@ extern "C" {
  * and y = ny - 1/2 (the paper's box walls): halfway bounce-back of both
  * lattices at resting walls, and the finite-difference stencils see mirror
  * images of the rows inside (zero normal gradient of phi, mu and phi0).  In
- * 2D walls run the one-cell-per-thread step (kernel 0).  Solid walls of any
- * shape can also be given through the smooth indicator phi0. */
+ * 2D walls run the one-cell-per-thread step (kernel 0) or the strip step
+ * (kernel 4).  Solid walls of any shape can also be given through the smooth
+ * indicator phi0. */
 typedef struct pf_grid {
     int dim;
     int nx, ny, nz;
@@ -188,8 +189,20 @@ int pf_init_fields(pf_handle *h, const double *phi0, const double *phi, const do
                    const double *P, int where);
 
 /* Advance n >= 0 time steps (Sec. 3.3 steps 2-10).  Asynchronous; replays a
- * CUDA graph of the step sequence.  PF_ESTATE before pf_init_fields. */
+ * CUDA graph of the step sequence.  PF_ESTATE before pf_init_fields.  A
+ * single simulation runs kernel 0 (32x8 tiles in 2D) unless pf_set_config
+ * or pf_autotune has chosen otherwise. */
 int pf_step(pf_handle *h, int64_t n);
+
+/* Choose the launch configuration of a single simulation by timing the
+ * candidates of the batch autotuner (kernel, tile shape, CTAs per SM) on its
+ * live state, or take the configuration cached for this kind of launch (see
+ * pf_batch_create).  The timed candidate steps are real time steps of the
+ * simulation (every configuration computes the same update, to rounding
+ * order); their count, an even number plus one if the simulation stood at an
+ * odd step, is returned in *steps_taken (may be NULL).  No counterpart in the
+ * paper.  Synchronous.  PF_ESTATE before pf_init_fields. */
+int pf_autotune(pf_handle *h, int64_t *steps_taken);
 
 /* Macroscopic fields at the current time recomputed from the populations
  * (Eqs. 31, 17, 36): phi (N), rho (N), u (dim*N), P (N), mu = mu_phi of Eq. (9)
@@ -289,8 +302,8 @@ int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int
  *   4  2D, two horizontally adjacent cells per thread in packed FP32
  *      arithmetic on strips of 64 columns marched in y, every input staged
  *      in shared memory by tensor copies one band of rows ahead, periodic
- *      wrap in x through ghost columns (P32 and PMIX, fixed solids, no walls
- *      at the ends of y, either lattice, every nx even and >= 8;
+ *      wrap in x through ghost columns (P32 and PMIX, fixed solids, walls
+ *      at the ends of y or not, either lattice, every nx even and >= 8;
  *      tile_x = 64, the strip width; tile_y = the rows of one work item,
  *      any value >= 1).
  * Adding a particle later falls back to kernel 0.  PF_EINVAL for a
@@ -300,8 +313,8 @@ int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int
 int pf_batch_set_config(pf_batch *b, int tile_x, int tile_y, int kernel, int ctas_per_sm);
 int pf_set_config(pf_handle *h, int tile_x, int tile_y, int kernel, int ctas_per_sm);
 /* The launch configuration of a single simulation, as pf_batch_config: -1
- * until a step call of at least 256 steps has run the autotuner or
- * pf_set_config has fixed it. */
+ * until pf_autotune has chosen it, pf_set_config has fixed it, or a step has
+ * run with the default (kernel 0). */
 int pf_get_config(pf_handle *h, int *tile_x, int *tile_y, int *ctas_per_sm, int *kernel);
 void pf_batch_destroy(pf_batch *b);
 

@@ -661,7 +661,7 @@ static bool stage_ok(const Engine &E)
 // no walls at the ends of y, every nx even and >= the ghost width
 static bool strip_ok(const Engine &E)
 {
-    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0 || any_walls(E)) return false;
+    if (E.dim != 2 || E.prec == PF_P64 || E.np > 0) return false;
     for (auto &m : E.mem)
         if (m.d.nx % 2 || m.d.nx < STRIP_GHOST || m.d.pitch < m.d.nx + 2 * STRIP_GHOST) return false;
     return true;
@@ -906,6 +906,14 @@ static int tune_features(const Engine &E)
            (all_unit(E) ? 16 : 0);
 }
 
+// PF_TUNE_LOG set in the environment: the autotuner prints each candidate's
+// time per step to stderr
+static bool tune_log()
+{
+    static const bool on = getenv("PF_TUNE_LOG") != nullptr;
+    return on;
+}
+
 // Returns PF_OK with E.tuned set, or PF_OK with E.tuned unset when nothing is
 // cached for this launch and `tune` is false (the caller then takes defaults).
 static int engine_configure(Engine &E, bool tune)
@@ -922,7 +930,7 @@ static int engine_configure(Engine &E, bool tune)
             int tx, ty, var, cps;
             std::tie(tx, ty, var, cps) = it->second;
             if ((var == 3 && !split_ok(E)) || (var == 4 && !strip_ok(E)) ||
-                (var != 0 && (E.dim == 3 || any_walls(E)))) {  // (the key already separates these)
+                (var != 0 && (E.dim == 3 || (var != 4 && any_walls(E))))) {  // (the key separates these)
                 var = 0;
                 tx = 32;
                 ty = 8;
@@ -950,10 +958,27 @@ static int engine_configure(Engine &E, bool tune)
     // (kernel 2, the bulk-copy staged variant, is selectable with
     // pf_set_config but not a candidate: it measured slower than kernel 1)
     // (kernel 4: tile = strip width x segment rows)
-    int shapes[9][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 96, 4},
-                        {64, 128, 4}, {64, 192, 4}};
+    // (walls: kernels 0 and 4 only)
+    int shapes[10][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 64, 4},
+                         {64, 96, 4}, {64, 128, 4}, {64, 192, 4}};
     int nshapes = (E.prec != PF_P64 && E.np == 0 && !any_walls(E)) ? 6 : 3;
-    if (nshapes == 6 && strip_ok(E)) nshapes = 9;
+    if (strip_ok(E)) {
+        // on small launches (fewer than 8 work items of 96 rows per SM) also
+        // the short segments that give every CTA slot work
+        long long items96 = 0;
+        for (auto &m : E.mem)
+            items96 += (long long)((m.d.nx + STRIP_SW - 1) / STRIP_SW) * ((m.d.ny + 95) / 96);
+        if (items96 < 8LL * E.nsm) {
+            shapes[6][1] = 8;
+            shapes[7][1] = 16;
+            shapes[8][1] = 32;
+            shapes[9][1] = 64;
+        }
+        if (nshapes == 3)
+            for (int k = 0; k < 4; ++k)
+                for (int j = 0; j < 3; ++j) shapes[3 + k][j] = shapes[6 + k][j];
+        nshapes += 4;
+    }
     if (split_ok(E)) {
         // particle domain: also the split of near (single-cell) and far
         // (two-cells-per-thread) tiles
@@ -1008,6 +1033,9 @@ static int engine_configure(Engine &E, bool tune)
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (tune_log())
+                fprintf(stderr, "pf tune: tile %dx%d kernel %d ctas/SM %d grid %d: %.4f ms per step\n", sh[0], sh[1],
+                        sh[2], cps, E.grid, ms / (2 * reps));
             if (ms < best) {
                 best = ms;
                 bx = sh[0];
@@ -1353,6 +1381,29 @@ extern "C" int pf_step(pf_handle *h, int64_t n)
     PfRange range("pf_step");
     if (!h) return fail(PF_EINVAL, "handle is NULL");
     return engine_step(h->E, n, false);
+}
+
+extern "C" int pf_autotune(pf_handle *h, int64_t *steps_taken)
+{
+    PfRange range("pf_autotune");
+    if (!h) return fail(PF_EINVAL, "handle is NULL");
+    Engine &E = h->E;
+    if (E.sticky) return E.sticky;
+    for (size_t i = 0; i < E.mem.size(); ++i)
+        if (!E.inited[i]) return fail(PF_ESTATE, "pf_autotune before pf_init_fields");
+    const int64_t t0 = E.t;
+    while (E.par != 0) {  // the candidates start at parity 0
+        int rc = issue_step(E, E.par);
+        if (rc) return (E.sticky = rc);
+        E.par ^= 1;
+        E.t++;
+    }
+    E.tuned = false;
+    E.forced = false;
+    int rc = engine_configure(E, true);
+    if (rc) return (E.sticky = rc);
+    if (steps_taken) *steps_taken = E.t - t0;
+    return PF_OK;
 }
 
 extern "C" int pf_sync(pf_handle *h)
@@ -1702,15 +1753,15 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
     if (var < 0 || var > 4) return fail(PF_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
     if (var == 4 && (!strip_ok(E) || tile_x != STRIP_SW || tile_y < 1))
         return fail(PF_EINVAL, "kernel 4 (strips marched in y) needs 2D domains in FP32 or 16-bit storage without "
-                               "particles or walls at the ends of y, every nx even and >= %d, tile_x = %d (the "
-                               "strip width) and tile_y >= 1 (the segment rows)", STRIP_GHOST, STRIP_SW);
+                               "particles, every nx even and >= %d, tile_x = %d (the strip width) and tile_y >= 1 "
+                               "(the segment rows)", STRIP_GHOST, STRIP_SW);
     if (var == 3 && (!split_ok(E) || tile_x != 32 || tile_y != 16))
         return fail(PF_EINVAL, "kernel 3 (near tiles single-cell, far tiles two-cells) needs one 2D particle "
                                "domain in FP32 or 16-bit storage without walls, own angles or the Allen-Cahn "
                                "lattice, and 32x16 tiles");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
-    if (var != 0 && any_walls(E))
-        return fail(PF_EINVAL, "domains with walls run kernel 0 only");
+    if (var != 0 && var != 4 && any_walls(E))
+        return fail(PF_EINVAL, "domains with walls run kernels 0 and 4 only");
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);

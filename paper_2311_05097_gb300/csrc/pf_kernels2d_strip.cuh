@@ -25,8 +25,14 @@
 //     step writes the ghosts of the cells it stores; a separate pass fills them
 //     after anything else has written the state.
 //
-// Requirements (checked on the host): 2D, no walls at the ends of y, no free
-// particles, every nx even and >= 8, pitch >= nx + 16.  Every wait on an
+// Walls at the ends of y (the WALL instantiation; the box walls read as
+// halfway bounce-back plus mirrored stencil rows): a staged row beyond a wall
+// is a copy of its mirror image inside; phi of a row beyond a wall is that of
+// its mirror row (w takes the sign change); a pull that would cross a wall
+// reads the cell's own opposite population.
+//
+// Requirements (checked on the host): 2D, no free particles, every nx even
+// and >= 8, pitch >= nx + 16.  Every wait on an
 // mbarrier is bounded: a wait that runs out sets bit 2 of the flags word
 // (PF_ETIMEOUT on the host), waits (bounded) for the copies still in flight
 // and ends the CTA.
@@ -199,19 +205,27 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const void *map, int x
 }
 
 // Issue the copies of staged row r (segment coordinates, wrapped to the
-// domain) into its ring row, completing on bar: box `box` of the row (lanes
+// domain, or mirrored at its walls) into its ring row, completing on bar: box `box` of the row (lanes
 // 0 .. NBOX - 1 of a warp each issue one).  The expected bytes were
 // registered on bar before.  Tensor coordinates: x' = x + STRIP_GHOST (the
 // maps start at the left ghost of row 0), y the wrapped row, plane 0 (each
 // map starts at its first plane).
 template <class P, int B>
 __device__ __forceinline__ void strip_copy(const char *maps, int par, int x0, int ya, int ny, int r, int box,
-                                           unsigned sbase, unsigned bar)
+                                           unsigned sbase, unsigned bar, bool wall)
 {
     using L = StripLayout<P, B>;
     const char *pm = maps + (size_t)par * STRIP_MAPS_PER_PAR * 128;
-    int y = r % ny;
-    if (y < 0) y += ny;
+    int y;
+    if (wall) {  // walls at y = -1/2 and ny - 1/2: the mirror image (period 2 ny)
+        const int p2 = 2 * ny;
+        y = r % p2;
+        if (y < 0) y += p2;
+        if (y >= ny) y = p2 - 1 - y;
+    } else {
+        y = r % ny;
+        if (y < 0) y += ny;
+    }
     const int slot = L::POW2 ? (r & (L::R - 1)) : (r - ya + 3) % L::R;
     const unsigned row = sbase + (unsigned)(slot * L::ROW);
     const int g = STRIP_GHOST;
@@ -233,6 +247,7 @@ struct StripItem {
     void *rd;            // rest populations written this step
     int klog1;           // PMIX scale exponent of the order-parameter lattice
     int phase_model;
+    int wall;            // walls at the ends of y
 };
 
 // ---- the kernel ---------------------------------------------------------------------------------
@@ -246,7 +261,7 @@ struct StripItem {
 //   C: the update of row Y + warp
 // Phase A of band k + 1 overlaps the last warps' phase C of band k (the phi
 // and w rings are long enough to keep the rows apart).
-template <class P, int B, bool CAC, bool UNIT>
+template <class P, int B, bool CAC, bool UNIT, bool WALL>
 __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 {
     using ST = typename P::store;
@@ -261,17 +276,19 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned sbase = smem_u32(smem);
-    const unsigned bar[2] = {sbase + L::OBAR, sbase + L::OBAR + 8};
+    // the two band-group mbarriers (shared addresses), and their phases (bit b:
+    // barrier b; kept in one register, not in an indexed array)
+    auto bar = [&](int b) -> unsigned { return sbase + L::OBAR + 8u * (unsigned)b; };
     float *s_phi = reinterpret_cast<float *>(smem + L::OPHI);  // [RP][FP]
     float *s_w = reinterpret_cast<float *>(smem + L::OW);      // [RWW][FM]
     float *s_mu = reinterpret_cast<float *>(smem + L::OMU);    // [RM][FM]
     KParams<float> *s_kp = reinterpret_cast<KParams<float> *>(smem + L::OKP);
     StripItem *s_it = reinterpret_cast<StripItem *>(smem + L::OIT);
     if (tid == 0) {
-        mbar_init(bar[0], 1);
-        mbar_init(bar[1], 1);
+        mbar_init(bar(0), 1);
+        mbar_init(bar(1), 1);
     }
-    unsigned phase[2] = {0u, 0u};
+    unsigned phases = 0u;
     const int polls = A.wait_polls > 0 ? A.wait_polls : STAGE_WAIT_POLLS;
     const char *maps_all = reinterpret_cast<const char *>(A.strip_maps);
 
@@ -295,13 +312,14 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             s_it->rd = Dm.rest[A.par ^ 1];
             s_it->klog1 = Dm.p.klog2[0];
             s_it->phase_model = Dm.p.phase_model;
+            s_it->wall = WALL ? Dm.wall_y : 0;
         }
-        if (tid == 0) mbar_arrive_expect_tx(bar[0], (unsigned)((B + 6) * L::ROW_TX));
+        if (tid == 0) mbar_arrive_expect_tx(bar(0), (unsigned)((B + 6) * L::ROW_TX));
         __syncthreads();  // the constants and the item block are visible; the bytes are registered
         // band group 0: rows ya - 3 .. ya + B + 2, one box per lane, rows over the warps
         if (lane < L::NBOX)
             for (int rr = warp; rr < B + 6; rr += B)
-                strip_copy<P, B>(maps(), A.par, x0, ya, ny, ya - 3 + rr, lane, sbase, bar[0]);
+                strip_copy<P, B>(maps(), A.par, x0, ya, ny, ya - 3 + rr, lane, sbase, bar(0), WALL && s_it->wall);
 
         // ring rows of segment row r: the rings hold row Y (the band's first row)
         // in slots bR, bP, bW, bM (advanced per band); r - Y stays within a ring
@@ -324,8 +342,8 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         // one bounded wait on band group j (its phase advances on success)
         auto wait_group = [&](int j) -> bool {
             const int b = j & 1;
-            const bool ok = mbar_wait_bounded(bar[b], phase[b], polls);
-            if (ok) phase[b] ^= 1u;
+            const bool ok = mbar_wait_bounded(bar(b), (phases >> b) & 1u, polls);
+            if (ok) phases ^= 1u << b;
             return ok;
         };
         // a wait ran out (known to every thread at a barrier): report; a thread
@@ -333,7 +351,7 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
         // wait to land; end the CTA
         auto give_up = [&](int j, bool my_ok) {
             if (tid == 0) atomicOr(A.flags, 4);
-            if (!my_ok) mbar_wait_bounded(bar[j & 1], phase[j & 1], STAGE_WAIT_POLLS);
+            if (!my_ok) mbar_wait_bounded(bar(j & 1), (phases >> (j & 1)) & 1u, STAGE_WAIT_POLLS);
         };
 
         // phase A: phi (Eq. 31) of rows [rp, rp + np_) on columns x0 - 2 .. x0 + SW + 2
@@ -346,21 +364,44 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 if (j < nphi) {
                     const int rr = j / NPP, m = j - rr * NPP;
                     const int r = rp + rr;
+                    // rs: the row whose phi this is (beyond a wall, the mirror image);
+                    // blo / bhi: its pulls across the lower / upper wall bounce back
+                    int rs = r;
+                    bool blo = false, bhi = false;
+                    if constexpr (WALL) {
+                        if (s_it->wall) {
+                            if (r < -2 || r > ny + 1) {  // a row no update reads
+                                *reinterpret_cast<float2 *>(phir(r) + 2 * m) = make_float2(0.0f, 0.0f);
+                                continue;
+                            }
+                            rs = r < 0 ? -1 - r : (r >= ny ? 2 * ny - 1 - r : r);
+                            blo = rs == 0;
+                            bhi = rs == ny - 1;
+                        }
+                    }
                     const int c = 2 * m + HS - 2;  // staged column of the left cell
-                    // rows r - 1, r, r + 1 (byte offsets of the left cell in the order-parameter box)
-                    const int ro[3] = {srow_o(r - 1) + L::O1 + c * L::ES, srow_o(r) + L::O1 + c * L::ES,
-                                       srow_o(r + 1) + L::O1 + c * L::ES};
+                    // rows rs - 1, rs, rs + 1 (byte offsets of the left cell in the order-parameter box)
+                    const int ro[3] = {srow_o(rs - 1) + L::O1 + c * L::ES, srow_o(rs) + L::O1 + c * L::ES,
+                                       srow_o(rs + 1) + L::O1 + c * L::ES};
+                    // the left cell's stored value of population i pulled from plane
+                    // index k of the box (ko: that of the opposite population)
+                    auto src = [&](int i, int k, int ko) -> const ST * {
+                        if constexpr (WALL) {
+                            if ((CY9[i] == 1 && blo) || (CY9[i] == -1 && bhi))
+                                return reinterpret_cast<const ST *>(smem + ro[1]) + ko * L::W1;
+                        }
+                        return reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + k * L::W1 - CX9[i];
+                    };
                     F2 phv;
                     if constexpr (P::MIX && UNIT) {
                         // the cells' exact fixed-point phi (rest + images of the pulled
                         // movers), rounded once to FP32; kept for the update's bookkeeping
-                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(r) + L::OR + 16 * m);
+                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(rs) + L::OR + 16 * m);
                         int sum[2] = {0, 0};
                         const F2 s24 = mk2(16777216.0f);
 #pragma unroll
                         for (int i = 1; i < 9; ++i) {
-                            const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + (i - 1) * L::W1 -
-                                          CX9[i];
+                            const ST *q = src(i, i - 1, OPP9[i] - 1);
                             const F2 im = mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1])) * s24;
                             sum[0] += __float2int_rn(im.v.x);
                             sum[1] += __float2int_rn(im.v.y);
@@ -371,12 +412,11 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                         if (m >= 1 && m <= L::SW / 2)  // the strip's own columns
                             *reinterpret_cast<longlong2 *>(rar(r) + 2 * (m - 1)) = make_longlong2(ra, rb);
                     } else if constexpr (P::MIX) {
-                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(r) + L::OR + 16 * m);
+                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(rs) + L::OR + 16 * m);
                         F2 movers = mk2(0.0f);
 #pragma unroll
                         for (int i = 1; i < 9; ++i) {
-                            const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + (i - 1) * L::W1 -
-                                          CX9[i];
+                            const ST *q = src(i, i - 1, OPP9[i] - 1);
                             movers = movers + mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1]));
                         }
                         phv = fma2(movers, mk2(s_kp->inv_scale[0]), mk2(float_of_fixed(rv.x), float_of_fixed(rv.y)));
@@ -384,7 +424,7 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                         F2 acc = mk2(0.0f);
 #pragma unroll
                         for (int i = 0; i < 9; ++i) {
-                            const ST *q = reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + i * L::W1 - CX9[i];
+                            const ST *q = src(i, i, OPP9[i]);
                             acc = acc + mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
                         }
                         phv = acc;
@@ -400,6 +440,12 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                         const float ux = us[e], uy = us[L::WA + e];
                         const float Sx = us[2 * L::WA + e], Sy = us[3 * L::WA + e];
                         wv[e] = Sx * uy - ux * Sy;
+                    }
+                    if constexpr (WALL) {
+                        if (s_it->wall && (r < 0 || r >= ny)) {  // odd under the wall mirror
+                            wv[0] = -wv[0];
+                            wv[1] = -wv[1];
+                        }
                     }
                     *reinterpret_cast<float2 *>(wr(r) + 2 * m) = make_float2(wv[0], wv[1]);
                 }
@@ -464,14 +510,15 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             const bool ok = k == 0 || wait_group(k);
             if (ok) phase_a(Y + 2, B, Y + 1, B);
             fence_proxy_async_smem();  // this thread's reads of the ring precede the next copies
-            if (tid == 0 && k + 1 < K) mbar_arrive_expect_tx(bar[(k + 1) & 1], (unsigned)(B * L::ROW_TX));
+            if (tid == 0 && k + 1 < K) mbar_arrive_expect_tx(bar((k + 1) & 1), (unsigned)(B * L::ROW_TX));
             if (__syncthreads_or(!ok)) {  // barrier 1
                 give_up(k, ok);  // (group k + 1 has its bytes registered but no copy issued)
                 return;
             }
             // band group k + 1: rows Y + B + 3 .. Y + 2B + 2, row Y + B + 3 + warp, one box per lane
             if (k + 1 < K && lane < L::NBOX)
-                strip_copy<P, B>(maps(), A.par, x0, ya, ny, Y + B + 3 + warp, lane, sbase, bar[(k + 1) & 1]);
+                strip_copy<P, B>(maps(), A.par, x0, ya, ny, Y + B + 3 + warp, lane, sbase, bar((k + 1) & 1),
+                                 WALL && s_it->wall);
             phase_b(Y + 1, B);
             __syncthreads();  // barrier 2
 
@@ -519,8 +566,26 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 const int ro[3] = {srow_o(r - 1) + c * L::ES, srow_o(r) + c * L::ES, srow_o(r + 1) + c * L::ES};
                 F2 f1[9], f2[9];
                 long long racc[2] = {0, 0};
-                // the two cells' stored values of population i (32-bit load where c_x = 0)
+                // pulls across the lower / upper wall bounce back
+                bool blo = false, bhi = false;
+                if constexpr (WALL) {
+                    if (s_it->wall) {
+                        blo = r == 0;
+                        bhi = r == ny - 1;
+                    }
+                }
+                // the two cells' stored values of population i (32-bit load where c_x = 0;
+                // a pull across a wall: the cells' own opposite population)
                 auto pulled = [&](int box, int i, int q) -> F2 {
+                    if constexpr (WALL) {
+                        if ((CY9[i] == 1 && blo) || (CY9[i] == -1 && bhi)) {
+                            const unsigned char *b = smem + ro[1] + box + (q + OPP9[i] - i) * L::W1 * L::ES;
+                            if constexpr (P::MIX)
+                                return uncvt_pair<ST>(*reinterpret_cast<const uint32_t *>(b));
+                            else
+                                return {*reinterpret_cast<const float2 *>(b)};
+                        }
+                    }
                     const unsigned char *b = smem + ro[1 - CY9[i]] + box + q * L::W1 * L::ES;
                     if constexpr (P::MIX) {
                         if (CX9[i] == 0) return uncvt_pair<ST>(*reinterpret_cast<const uint32_t *>(b));

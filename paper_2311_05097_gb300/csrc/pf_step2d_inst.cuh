@@ -95,10 +95,10 @@ static bool dispatch2d_stage(int tx, int ty, bool moving, int grid, cudaStream_t
     }
 }
 
-template <class P, int B, bool CAC, bool UNIT>
+template <class P, int B, bool CAC, bool UNIT, bool WALL>
 static bool run2d_strip(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
-    auto kern = k_step2d_strip<P, B, CAC, UNIT>;
+    auto kern = k_step2d_strip<P, B, CAC, UNIT, WALL>;
     const int dyn = StripLayout<P, B>::BYTES;
     static bool attr = false;  // set once per instantiation (process-wide, any device)
     if (!attr) {
@@ -116,11 +116,20 @@ static bool run2d_strip(int grid, cudaStream_t s, const StepArgs &a, int *occ)
     return true;
 }
 
+template <class P, bool WALL>
+static bool dispatch2d_strip_w(bool cac, bool unit, int grid, cudaStream_t s, const StepArgs &a, int *occ)
+{
+    constexpr int B = strip_band<P>();
+    if (cac) return run2d_strip<P, B, true, false, WALL>(grid, s, a, occ);
+    return unit ? run2d_strip<P, B, false, true, WALL>(grid, s, a, occ)
+                : run2d_strip<P, B, false, false, WALL>(grid, s, a, occ);
+}
+
 // strips marched in y (tile_x = strip width, tile_y = segment rows: any), and
 // the ghost-column pass it needs (grid = number of domains)
 template <class P>
-static bool dispatch2d_strip(int tx, bool moving, bool cac, bool unit, bool fill, int grid, cudaStream_t s,
-                             const StepArgs &a, int *occ)
+static bool dispatch2d_strip(int tx, bool moving, bool cac, bool unit, bool wall, bool fill, int grid,
+                             cudaStream_t s, const StepArgs &a, int *occ)
 {
     if constexpr (P::id == 0) {
         return false;
@@ -135,9 +144,8 @@ static bool dispatch2d_strip(int tx, bool moving, bool cac, bool unit, bool fill
             return true;
         }
         if (moving || tx != STRIP_SW) return false;
-        constexpr int B = strip_band<P>();
-        if (cac) return run2d_strip<P, B, true, false>(grid, s, a, occ);
-        return unit ? run2d_strip<P, B, false, true>(grid, s, a, occ) : run2d_strip<P, B, false, false>(grid, s, a, occ);
+        return wall ? dispatch2d_strip_w<P, true>(cac, unit, grid, s, a, occ)
+                    : dispatch2d_strip_w<P, false>(cac, unit, grid, s, a, occ);
     }
 }
 
@@ -170,12 +178,12 @@ static bool dispatch2d(int tx, int ty, bool moving, int mode, int grid, cudaStre
     const bool ext = (mode & MODE_EXT) != 0, cac = (mode & MODE_CAC) != 0, mu0 = (mode & MODE_MU0) != 0;
     const bool wall = (mode & MODE_WALL) != 0, unit = (mode & MODE_UNIT) != 0;
     mode &= ~(MODE_EXT | MODE_CAC | MODE_MU0 | MODE_WALL | MODE_UNIT);
-    // the two-cells-per-thread kernels have no wall handling: refuse walled launches
+    // the tiled two-cells-per-thread kernels have no wall handling: refuse walled launches
     if (mode == MODE_STEP_PAIR) return !wall && dispatch2d_pair<P>(tx, ty, moving, cac, mu0, grid, s, a, occ);
     if (mode == MODE_STEP_STAGE)
         return !wall && !ext && !cac && dispatch2d_stage<P>(tx, ty, moving, grid, s, a, occ);
     if (mode == MODE_STEP_STRIP || mode == MODE_FILL_GHOSTS)
-        return !wall && dispatch2d_strip<P>(tx, moving, cac, unit, mode == MODE_FILL_GHOSTS, grid, s, a, occ);
+        return dispatch2d_strip<P>(tx, moving, cac, unit, wall, mode == MODE_FILL_GHOSTS, grid, s, a, occ);
     return ext ? dispatch2d_single<P, true>(tx, ty, moving, mode, grid, s, a, occ)
                : dispatch2d_single<P, false>(tx, ty, moving, mode, grid, s, a, occ);
 }

@@ -82,6 +82,7 @@ def load(build_if_missing=False):
         "pf_create": (C.c_int, [C.POINTER(pf_grid), C.POINTER(pf_params), C.POINTER(vp)]),
         "pf_init_fields": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
         "pf_step": (C.c_int, [vp, C.c_int64]),
+        "pf_autotune": (C.c_int, [vp, C.POINTER(C.c_int64)]),
         "pf_get_macros": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int]),
         "pf_get_normal": (C.c_int, [vp, vp, C.c_int]),
         "pf_state_size": (C.c_int, [vp, C.POINTER(C.c_int64)]),
@@ -252,6 +253,13 @@ class Sim:
 
     def step(self, n=1):
         _check(load().pf_step(self._h, int(n)))
+
+    def autotune(self):
+        """Time the autotuner's candidates on the live state (or take the cached
+        choice) and keep the fastest; returns the time steps that took."""
+        n = C.c_int64(0)
+        _check(load().pf_autotune(self._h, C.byref(n)))
+        return n.value
 
     def sync(self):
         _check(load().pf_sync(self._h))

@@ -523,12 +523,13 @@ def test_batch_mixes_wall_and_periodic_domains(pf):
 
 def test_tuned_periodic_config_is_not_reused_for_walls(pf):
     """The autotuner's cache must not hand a walled batch the configuration
-    tuned on a periodic batch of the same size: the two-cells-per-thread
+    tuned on a periodic batch of the same size: the tiled two-cells-per-thread
     kernels have no bounce-back, so a walled domain stepped by them would run
-    as periodic in y.  A periodic FP16 batch is tuned first (it usually picks
-    the two-cells kernel), then a walled batch of the same size and domain
-    count: it must report kernel 0 and match its single-handle run bit for
-    bit (that run is kernel 0, parity-tested against the oracle)."""
+    as periodic in y.  A periodic FP16 batch is tuned first (it picks a
+    two-cells kernel), then a walled batch of the same size and domain count:
+    it must report one of the kernels with walls (0 or 4), match the oracle
+    with walls within FP16 bounds, and conserve mass exactly (the same mass
+    as its single-handle run)."""
     L = 256
     per = W.flat_wall_drop(L, 60.0, 10.0)
     bp = pf.Batch([per["shape"]], [per["params"]], precision="fp16")
@@ -541,11 +542,16 @@ def test_tuned_periodic_config_is_not_reused_for_walls(pf):
     bw.init(0, c["phi0"], c["phi"], c.get("u"))
     bw.step(256)
     bw.sync()
-    assert bw.config()[3] == 0, bw.config()
-    g, _ = run_pair(pf, c, 256, precision="fp16", oracle=False, walls=True)
-    mb, mg = bw.macros(0), g.macros()
-    for k in FIELDS:
-        assert np.array_equal(mb[k], mg[k]), k
+    assert bw.config()[3] in (0, 4), bw.config()
+    g, o = run_pair(pf, c, 256, precision="fp16", walls=True)
+    mb, om = bw.macros(0), o.macros()
+    e = {k: rel(mb[k], om[k]) for k in ("phi", "rho", "u", "P")}
+    e["mu"] = float(np.abs(mb["mu"] - om["mu"]).max() / max(np.abs(om["mu"]).max(), 3 * 0.01 / 4.0))
+    # (the every-field bounds, 200 steps of a 56 x 37 case; mu here, 256 steps
+    # of this 256 x 256 wall case: measured 5.4e-4)
+    tol = dict(MIXED_TOL["fp16"], mu=1e-3)
+    for k, v in e.items():
+        assert v < tol[k], (k, v)
     assert abs(bw.diagnostics(0)["mass"] - g.diagnostics()["mass"]) == 0.0
 
 

@@ -161,6 +161,8 @@ def test_batch_strip_equals_single_runs(pf):
 
 
 def test_strip_rejected_where_not_built(pf):
+    """FP64 (no packed arithmetic), odd nx and a strip width other than 64
+    are refused."""
     c = W.small_case((32, 64), seed=1, solid=False)
     g = pf.Sim(c["shape"], precision="p64", **c["params"])
     g.init(c["phi0"], c["phi"])
@@ -171,11 +173,6 @@ def test_strip_rejected_where_not_built(pf):
     g.init(c["phi0"], c["phi"])
     with pytest.raises(pf.PfError):
         g.set_config(64, 128, 4)  # odd nx
-    c = W.wall_case((32, 64), seed=1)
-    g = pf.Sim(c["shape"], precision="fp16", walls_y=True, **c["params"])
-    g.init(c["phi0"], c["phi"])
-    with pytest.raises(pf.PfError):
-        g.set_config(64, 128, 4)  # walls at the ends of y
     c = W.small_case((32, 64), seed=1, solid=False)
     g = pf.Sim(c["shape"], precision="fp16", **c["params"])
     g.init(c["phi0"], c["phi"])
@@ -201,3 +198,107 @@ def test_strip_bounded_wait_timeout_is_reported(pf, monkeypatch):
     h, _ = run_pair(pf, c, 20, precision="fp16", oracle=False, config=(64, 128, 4))
     h.sync()
     assert h.diagnostics()["nan_flag"] == 0
+
+
+# ---- walls at the ends of y (halfway bounce-back, mirrored stencil rows) ------------------------
+
+@pytest.mark.parametrize("shape,seg,rates", [((37, 136), 16, None), ((70, 96), 128, None), ((5, 64), 8, None),
+                                             ((24, 10), 8, None), ((37, 96), 16, (1.3, 1.2, 1.4))])
+@pytest.mark.parametrize("precision", ["p32", "fp16", "bf16"])
+def test_strip_walls_against_oracle(pf, precision, shape, seg, rates):
+    """The wall case (a drop cut by the top wall, a disc near the bottom one,
+    random initial flow) through the strip step: 37 rows in segments of 16
+    (the top wall inside a partial band of a partial segment), 70 rows in one
+    segment, 5 rows (fewer than a band: one band reaches beyond both walls),
+    10 columns (every cell is also a ghost); unit rates and s2, s3, s4 = 1.3,
+    1.2, 1.4."""
+    c = W.wall_case(shape, seed=3)
+    if rates is not None:
+        c["params"] = dict(c["params"], s2=rates[0], s3=rates[1], s4=rates[2])
+    g, o = run_pair(pf, c, 200, precision=precision, config=(64, seg, 4), walls=True)
+    assert g.config()[3] == 4
+    e = field_errors(g.macros(), o.macros(), 3 * c["params"]["sigma"] / c["params"]["D"])
+    print("strip-walls", precision, shape, seg, rates, {k: "%.2e" % v for k, v in e.items()})
+    for k, v in e.items():
+        assert v < TOL[precision][k], (k, v)
+    assert g.diagnostics()["nan_flag"] == 0
+
+
+def test_strip_walls_agree_with_one_cell_kernel_p32(pf):
+    """FP32 with walls: the strip step and the one-cell step (kernel 0, which
+    has its own wall code) agree to rounding order."""
+    c = W.wall_case((70, 96), seed=4)
+    a, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(32, 8, 0), walls=True)
+    b, _ = run_pair(pf, c, 300, precision="p32", oracle=False, config=(64, 32, 4), walls=True)
+    ma, mb = a.macros(), b.macros()
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(mb[k], ma[k]) < tol, k
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_strip_walls_conserve_mass_exactly(pf, precision):
+    c = W.wall_case((64, 80), seed=4)
+    g, _ = run_pair(pf, c, 0, precision=precision, oracle=False, config=(64, 16, 4), walls=True)
+    m0 = g.diagnostics()["mass"]
+    g.step(1000)
+    d = g.diagnostics()
+    assert d["nan_flag"] == 0
+    assert abs(d["mass"] - m0) / np.abs(c["phi"]).sum() < 1e-13
+
+
+def test_strip_walls_segments_are_bit_identical(pf):
+    c = W.wall_case((70, 96), seed=5)
+    a, _ = run_pair(pf, c, 150, precision="fp16", oracle=False, config=(64, 8, 4), walls=True)
+    b, _ = run_pair(pf, c, 150, precision="fp16", oracle=False, config=(64, 256, 4), walls=True)
+    ma, mb = a.macros(), b.macros()
+    for k in FIELDS:
+        assert np.array_equal(ma[k], mb[k]), k
+
+
+def test_batch_strip_mixes_wall_and_periodic_domains(pf):
+    """A walled and a periodic domain in one strip launch (the wall
+    instantiation serves both): each bit-identical to its single run with the
+    same kernel and boundary."""
+    cases = [W.wall_case((37, 52), seed=3), W.small_case((52, 40), seed=3, solid=True, u_amp=0.01)]
+    steps = 200
+    b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="fp16",
+                 walls_y=[True, False])
+    for i, c in enumerate(cases):
+        b.init(i, c["phi0"], c["phi"], c.get("u"))
+    b.set_config(64, 32, 4)
+    b.step(steps)
+    b.sync()
+    for i, c in enumerate(cases):
+        g, _ = run_pair(pf, c, steps, precision="fp16", oracle=False, config=(64, 32, 4), walls=(i == 0))
+        mb, mg = b.macros(i), g.macros()
+        for k in FIELDS:
+            assert np.array_equal(mb[k], mg[k]), (i, k)
+
+
+def test_single_handle_autotune(pf):
+    """pf_autotune times the candidates on a single simulation's live state:
+    an even number of real steps (one more from an odd step), a kernel the
+    handle can run, the oracle's result to the FP16 bounds after the
+    remaining steps, exact mass; a second handle of the same kind takes the
+    cached choice without stepping."""
+    c = W.small_case((96, 128), seed=2, solid=True, theta_deg=60.0, u_amp=0.01)
+    g = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    g.init(c["phi0"], c["phi"], c["u"])
+    m0 = g.diagnostics()["mass"]
+    g.step(1)
+    n = g.autotune()
+    assert n > 0 and n % 2 == 1, n
+    cfg = g.config()
+    assert cfg[3] in (0, 1, 4), cfg
+    g.step(200 - 1 - n)
+    o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+    o.init(c["phi0"], c["phi"], c["u"])
+    o.step(200)
+    e = field_errors(g.macros(), o.macros(), 3 * c["params"]["sigma"] / c["params"]["D"])
+    for k, v in e.items():
+        assert v < TOL["fp16"][k], (k, v)
+    assert abs(g.diagnostics()["mass"] - m0) / np.abs(c["phi"]).sum() < 1e-13
+    h = pf.Sim(c["shape"], precision="fp16", **c["params"])
+    h.init(c["phi0"], c["phi"], c["u"])
+    assert h.autotune() == 0
+    assert h.config() == cfg
