@@ -643,7 +643,9 @@ static int step_mode(const Engine &E)
 // no particle with its own contact angle
 static bool split_ok(const Engine &E)
 {
-    return E.dim == 2 && E.np > 0 && !E.wv && E.prec != PF_P64 && E.mem.size() == 1 && !any_walls(E) && !any_cac(E);
+    // (particles with their own contact angles act only within their reach: on
+    // the near tiles, which run the single-cell step)
+    return E.dim == 2 && E.np > 0 && E.prec != PF_P64 && E.mem.size() == 1 && !any_walls(E) && !any_cac(E);
 }
 
 // the staged 2D step copies 16-byte chunks: every domain's nx must keep its
@@ -1598,7 +1600,7 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         for (int j = 0; j < E.np; ++j) wv |= E.hp[j].own;
         if (wv != E.wv) drop_graph(E);  // the step arguments change
         E.wv = wv;
-        if (E.variant == 3 && !split_ok(E)) {  // own angles: the far tiles need W and V
+        if (E.variant == 3 && !split_ok(E)) {  // (not reached: own angles keep the split)
             E.variant = 0;
             int rc0 = engine_tiles(E, E.tx, E.ty);
             if (rc0) return rc0;

@@ -165,7 +165,11 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
     __shared__ int s_gy[TY + 6];  // row offsets y * pitch (planes hold < 2^31 cells)
     __shared__ int s_gyi[TY + 6];
     __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
-    __shared__ double s_red[2][NT / 32][3];  // warps' sums, double-buffered over particles
+    // warps' force / torque sums of up to RED_J near particles, reduced behind
+    // one barrier (s_redk: their particle indices)
+    constexpr int RED_J = 8;
+    __shared__ double s_red[MOVING ? RED_J : 1][NT / 32][3];
+    __shared__ int s_redk[MOVING ? RED_J : 1];
     __shared__ unsigned long long s_near;  // particles whose indicator reaches this tile
     // particles whose image nearest to the tile is the minimum image of every
     // cell of its frames, and that image's centre in table coordinates (the
@@ -716,17 +720,36 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             if constexpr (MOVING) {
                 // hydrodynamic force and torque on each particle (Eq. 27):
                 // F_f = -sum rho phi0_k (u_s,k - u*), T_f = -sum r x (...)
-                int nred = 0;  // reductions so far in this tile: picks the s_red buffer
-                for (int k = 0; k < A.np; ++k) {
-                    if (!((near >> k) & 1ull)) {
-                        // no cell of this tile is reached by particle k
-                        if (tid < 6) A.partials[((long long)t * A.np + k) * 6 + tid] = 0.0;
-                        continue;
+                // 2D: F_x, F_y and T_z (components 0, 1, 5); the others stay 0.
+                // The cell terms and the warp's shuffle tree are in the
+                // arithmetic type (the terms are computed in it); the warps'
+                // sums, the tiles' partials and the update are FP64.  Fixed
+                // order: per particle, each warp's shuffle tree (skipped by warps
+                // whose terms are all 0: the indicator rounds to 0 well inside
+                // the reach used for the tile test), then the warps in order;
+                // the warps' sums of up to RED_J near particles wait in s_red for
+                // one barrier, after which one thread per particle and component
+                // adds them up.
+                // particles out of this tile's reach: zero partials
+                for (int q = tid; q < 6 * A.np; q += NT)
+                    if (!((near >> (q / 6)) & 1ull)) A.partials[(long long)t * A.np * 6 + q] = 0.0;
+                int nj = 0;
+                auto flush = [&]() {
+                    __syncthreads();  // the warps' sums of the nj particles are in s_red
+                    for (int q = tid; q < 6 * nj; q += NT) {
+                        const int j = q / 6, comp = q - 6 * j;
+                        double acc = 0.0;
+                        if (comp < 2 || comp == 5) {
+                            const int c = comp == 5 ? 2 : comp;
+                            for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[j][wq][c];
+                        }
+                        A.partials[((long long)t * A.np + s_redk[j]) * 6 + comp] = acc;
                     }
-                    // 2D: F_x, F_y and T_z (components 0, 1, 5); the others stay 0.
-                    // The cell terms and the warp's shuffle tree are in the
-                    // arithmetic type (the terms are computed in it); the warps'
-                    // sums, the tiles' partials and the update are FP64.
+                    __syncthreads();  // s_red and s_redk are free again
+                    nj = 0;
+                };
+                for (int k = 0; k < A.np; ++k) {
+                    if (!((near >> k) & 1ull)) continue;
                     R c6[3] = {R(0), R(0), R(0)};
                     bool hit = false;
                     if (valid) {
@@ -742,14 +765,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                             c6[2] = -(rx * fy - ry * fx);
                         }
                     }
-                    // fixed-order block reduction: warp shuffle tree (skipped by
-                    // warps whose terms are all 0: the indicator rounds to 0 well
-                    // inside the reach used for the tile test), then warps in
-                    // order; one barrier per particle (the buffer written here is
-                    // next written two particles later, after another barrier)
                     const bool wany = __any_sync(0xffffffffu, hit);
-                    double(*red)[3] = s_red[nred & 1];
-                    ++nred;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         R v = c6[c];
@@ -757,17 +773,12 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
 #pragma unroll
                             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                         }
-                        if ((tid & 31) == 0) red[tid >> 5][c] = (double)v;
+                        if ((tid & 31) == 0) s_red[nj][tid >> 5][c] = (double)v;
                     }
-                    __syncthreads();
-                    if (tid < 6) {
-                        double acc = 0.0;
-                        const int c = tid == 5 ? 2 : tid;
-                        if (tid < 2 || tid == 5)
-                            for (int wq = 0; wq < NT / 32; ++wq) acc += red[wq][c];
-                        A.partials[((long long)t * A.np + k) * 6 + tid] = acc;
-                    }
+                    if (tid == 0) s_redk[nj] = k;
+                    if (++nj == RED_J) flush();
                 }
+                if (nj > 0) flush();
             }
         }
     }

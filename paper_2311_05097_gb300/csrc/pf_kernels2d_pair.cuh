@@ -73,6 +73,32 @@ __device__ __forceinline__ void grad9_pair(const float (*a)[W], int x, int y, F2
     gy = fma2(third, Chi - Clo, twelfth * (Rhi - Rlo));
 }
 
+// the same gradient of the cubes a^3 (the phi0^3 stencil of the own-angle
+// wetting force, reading R18)
+template <int W>
+__device__ __forceinline__ void grad9_cubed_pair(const float (*a)[W], int x, int y, F2 &gx, F2 &gy)
+{
+    Col4<W> w = col4<W>(a, x - 1, y), c = col4<W>(a, x, y), e = col4<W>(a, x + 1, y);
+    auto cube = [](Col4<W> &q) {
+        q.r0 = q.r0 * q.r0 * q.r0;
+        q.r1 = q.r1 * q.r1 * q.r1;
+        q.r2 = q.r2 * q.r2 * q.r2;
+        q.r3 = q.r3 * q.r3 * q.r3;
+    };
+    cube(w);
+    cube(c);
+    cube(e);
+    const F2 Dlo = mk2(e.r0, e.r1) - mk2(w.r0, w.r1);
+    const F2 Dmid = mk2(e.r1, e.r2) - mk2(w.r1, w.r2);
+    const F2 Dhi = mk2(e.r2, e.r3) - mk2(w.r2, w.r3);
+    const F2 Rlo = mk2(e.r0, e.r1) + mk2(w.r0, w.r1);
+    const F2 Rhi = mk2(e.r2, e.r3) + mk2(w.r2, w.r3);
+    const F2 Clo = mk2(c.r0, c.r1), Chi = mk2(c.r2, c.r3);
+    const F2 third = mk2(1.0f / 3.0f), twelfth = mk2(1.0f / 12.0f);
+    gx = fma2(third, Dmid, twelfth * (Dlo + Dhi));
+    gy = fma2(third, Chi - Clo, twelfth * (Rhi - Rlo));
+}
+
 template <int W>
 __device__ __forceinline__ F2 lap9_pair(const float (*a)[W], int x, int y)
 {
@@ -195,7 +221,9 @@ __device__ __forceinline__ void pair_mu(const KParams<float> &kp, const float (*
 // instantiation also serves domains with the conservative Allen-Cahn order
 // parameter (checked per domain).  MU0: the force carries mu_phi0 grad phi0
 // (Eq. 19) of the fixed solids, from lphi (Laplacian of phi) and g0 (grad
-// phi0).  done1(f1) runs as soon as the order-parameter lattice has collided
+// phi0); with wv (some particle of the simulation has its own contact angle,
+// reading R18) the phi0^2 grad phi0 part of its wetting term is the stencil
+// gradient of phi0^3 over 3, g3 = grad(phi0^3).  done1(f1) runs as soon as the order-parameter lattice has collided
 // (a caller can store it and free its registers before the flow lattice
 // collides); done2(f2, u_x, u_y, S_x, S_y) at the end.
 struct NoEmit {
@@ -214,7 +242,8 @@ __device__ __forceinline__ void pair_physics(int phase_model, const KParams<floa
                                              F2 mu, F2 gpx, F2 gpy, F2 gmx, F2 gmy, F2 wgx, F2 wgy, F2 lphi,
                                              F2 g0x, F2 g0y, F2 upx, F2 upy, F2 Spx, F2 Spy, F2 php,
                                              F2 (&f1)[9], F2 (&f2)[9], F2 &ux, F2 &uy, F2 &Sx, F2 &Sy,
-                                             E1 done1 = E1(), E2 done2 = E2())
+                                             E1 done1 = E1(), E2 done2 = E2(), bool wv = false,
+                                             F2 g3x = mk2(0.0f), F2 g3y = mk2(0.0f))
 {
     const F2 drho = mk2(kp.drho), half = mk2(0.5f), one = mk2(1.0f), two = mk2(2.0f);
     const F2 rho = fma2(drho, phi, mk2(kp.rhom));
@@ -239,11 +268,19 @@ __device__ __forceinline__ void pair_physics(int phase_model, const KParams<floa
     F2 Fx = fma2(mu, gpx, fma2(mk2(-0.5f), wgy, mk2(kp.Fb[0])));
     F2 Fy = fma2(mu, gpy, fma2(half, wgx, mk2(kp.Fb[1])));
     if constexpr (MU0) {
-        const F2 mu0 = fma2(mk2(kp.c_pen) * phi0, phi * phi,
-                            fma2(mk2(kp.c_wet) * phi, fma2(mk2(3.0f) * phi0, phi0, phi * phi - one),
-                                 mk2(-kp.c_wlap) * lphi));
-        Fx = fma2(mu0, g0x, Fx);
-        Fy = fma2(mu0, g0y, Fy);
+        if (wv) {
+            const F2 m = fma2(mk2(kp.c_pen) * phi0, phi * phi,
+                              fma2(mk2(kp.c_wet) * phi, phi * phi - one, mk2(-kp.c_wlap) * lphi));
+            const F2 cv = mk2(kp.c_wet) * phi;
+            Fx = fma2(m, g0x, fma2(cv, g3x, Fx));
+            Fy = fma2(m, g0y, fma2(cv, g3y, Fy));
+        } else {
+            const F2 mu0 = fma2(mk2(kp.c_pen) * phi0, phi * phi,
+                                fma2(mk2(kp.c_wet) * phi, fma2(mk2(3.0f) * phi0, phi0, phi * phi - one),
+                                     mk2(-kp.c_wlap) * lphi));
+            Fx = fma2(mu0, g0x, Fx);
+            Fy = fma2(mu0, g0y, Fy);
+        }
     }
 
     // u* (Eq. 36a)
@@ -405,10 +442,11 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     grad9_pair<WX>(s_mu, wx, wy, gmx, gmy);
     grad9_pair<WX>(s_w, wx, wy, wgx, wgy);
     const F2 mu = mk2(s_mu[wy][wx], s_mu[wy + 1][wx]);
-    F2 lphi = mk2(0.0f), g0x = mk2(0.0f), g0y = mk2(0.0f);
+    F2 lphi = mk2(0.0f), g0x = mk2(0.0f), g0y = mk2(0.0f), g3x = mk2(0.0f), g3y = mk2(0.0f);
     if constexpr (MU0) {
         lphi = lap9_pair<FX>(s_phi, hx, hy);
         grad9_pair<FX>(s_p0, hx, hy, g0x, g0y);
+        if (A.wv) grad9_cubed_pair<FX>(s_p0, hx, hy, g3x, g3y);
     }
     F2 f2[9];
     const F2 isc2v = mk2(kp.inv_scale[1]);
@@ -423,7 +461,7 @@ __device__ __forceinline__ void pair_cells(const StepArgs &A, const DevParams &p
     const F2 php = mk2((float)lag[0][4], (float)lag[1][4]);
     F2 ux, uy, Sx, Sy;
     pair_physics<CAC, MU0>(p.phase_model, kp, phi, phi0, mu, gpx, gpy, gmx, gmy, wgx, wgy, lphi, g0x, g0y, upx, upy,
-                           Spx, Spy, php, f1, f2, ux, uy, Sx, Sy);
+                           Spx, Spy, php, f1, f2, ux, uy, Sx, Sy, NoEmit(), NoEmit(), MU0 && A.wv != 0, g3x, g3y);
 
     // ---------------- stores (per cell) ----------------
 #pragma unroll

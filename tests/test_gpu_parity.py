@@ -993,8 +993,44 @@ def test_split_particle_step_rejected_where_not_built(pf):
         g.set_config(32, 8, 3)  # 32 x 16 tiles only
     g.set_config(32, 16, 3)
     g.step(5)
-    g.set_particle(0, **dict(part, theta_deg=45.0))  # own angle: back to the single-cell step
+    g.set_particle(0, **dict(part, theta_deg=45.0))  # own angle: the split stays
     g.step(5)
+    assert g.config()[3] == 3
+    assert g.diagnostics()["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3)])
+def test_split_particle_step_own_angles_against_oracle(pf, precision, tol_phi):
+    """The split step when particles carry their own contact angles (reading
+    R18): the near tiles sum the wetting per solid, the far tiles see the
+    fixed solids only, with the phi0^2 grad phi0 part of their force from the
+    stencil of phi0^3 as the oracle has it.  A fixed wetting disc and three
+    particles (two with own angles); against the FP64 oracle after 200
+    steps and against the single-cell step at the same precision."""
+    c = W.small_case((128, 96), seed=12, solid=True, theta_deg=60.0, u_amp=0.005)
+    parts = [dict(x=(40.3, 30.6), u=(0.01, -0.004), w=(0.0, 0.0, 0.002), R=6.0, rho_p=2.0, theta_deg=120.0),
+             dict(x=(95.0, 70.0), u=(-0.006, 0.003), R=5.0, rho_p=1.5, theta_deg=40.0),
+             dict(x=(20.0, 100.0), u=(0.0, 0.004), R=5.0, rho_p=1.2)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], c["params"]["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 200, precision=precision, particles=parts, config=(32, 16, 3))
+    s, _ = run_pair(pf, c, 200, precision=precision, particles=parts, oracle=False, config=(32, 16, 0))
+    assert g.config()[3] == 3
+    gm, om, sm = g.macros(), o.macros(), s.macros()
+    print("split-own", precision, {k: "%.2e" % rel(gm[k], om[k]) for k in ("phi", "rho", "u", "P")})
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    assert rel(gm["rho"], om["rho"]) < tol_phi
+    for k in ("u", "P"):
+        assert rel(gm[k], om[k]) < 100 * tol_phi, k
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(gm[k], sm[k]) < (tol if precision == "p32" else 10 * tol_phi), k
+    us = max(np.abs(om["u"]).max(), 1e-3)
+    for k in range(len(parts)):
+        pg, po = g.particle(k), o.particle(k)
+        assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() < 1e-3
+        assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() < 100 * tol_phi * us
     assert g.diagnostics()["nan_flag"] == 0
 
 
