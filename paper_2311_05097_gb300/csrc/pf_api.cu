@@ -485,9 +485,14 @@ struct Engine {
     double *d_frep = nullptr;   // repulsion force per particle (3 doubles each)
     double *d_partials = nullptr;
     size_t partials_cap = 0;
-    // graph of CHUNK steps starting at parity 0
+    // graph of CHUNK steps starting at parity 0, and graphs of one step at
+    // parity 0 and 1 (the steps of a call that do not fill a chunk: one graph
+    // launch per step instead of one launch per kernel), with the kernel
+    // launches each replays
     static constexpr int CHUNK = 16;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec1[2] = {nullptr, nullptr};
+    long long glaunch = 0, glaunch1[2] = {0, 0};
     int sticky = PF_OK;
     // polls of one bounded device wait; 0: the kernels' default.  Read from the
     // environment variable PF_WAIT_POLLS at create (fault injection: a tiny
@@ -529,6 +534,8 @@ static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
 static void engine_free(Engine &E)
 {
     if (E.gexec) cudaGraphExecDestroy(E.gexec);
+    for (int p = 0; p < 2; ++p)
+        if (E.gexec1[p]) cudaGraphExecDestroy(E.gexec1[p]);
     for (auto &m : E.mem) domain_free(m);
     staging_release(E.staging);
     if (E.d_macro) cudaFree(E.d_macro);
@@ -557,6 +564,10 @@ static void drop_graph(Engine &E)
 {
     if (E.gexec) cudaGraphExecDestroy(E.gexec);
     E.gexec = nullptr;
+    for (int p = 0; p < 2; ++p) {
+        if (E.gexec1[p]) cudaGraphExecDestroy(E.gexec1[p]);
+        E.gexec1[p] = nullptr;
+    }
 }
 
 // upload the domain table and the tile table for shape (tx, ty)
@@ -1100,11 +1111,33 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
         }
         if (rc) return (E.sticky = rc);
     }
-    while (left > 0 && E.par != 0) {
-        int rc = issue_step(E, E.par);
-        if (rc) return (E.sticky = rc);
+    // one step from the graph of its parity (captured at first use)
+    auto one_step = [&]() -> int {
+        const int p = E.par;
+        int grc = ensure_ghosts(E);
+        if (grc) return grc;
+        if (!E.gexec1[p]) {
+            const long long before = g_launches.load();
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(E.stream, cudaStreamCaptureModeThreadLocal));
+            const int rc = issue_step(E, p);
+            cudaError_t ce = cudaStreamEndCapture(E.stream, &graph);
+            if (rc) return rc;
+            CK(ce);
+            CK(cudaGraphInstantiate(&E.gexec1[p], graph, 0));
+            cudaGraphDestroy(graph);
+            E.glaunch1[p] = g_launches.load() - before;
+            g_launches = before;  // captured launches run (and are counted) at replay
+        }
+        CK(cudaGraphLaunch(E.gexec1[p], E.stream));
+        count_launches(E.glaunch1[p]);
         E.par ^= 1;
         E.t++;
+        return PF_OK;
+    };
+    while (left > 0 && E.par != 0) {
+        int rc = one_step();
+        if (rc) return (E.sticky = rc);
         left--;
     }
     if (left >= Engine::CHUNK) {
@@ -1121,20 +1154,19 @@ static int engine_step(Engine &E, int64_t n, bool autotune)
             CK(ce);
             CK(cudaGraphInstantiate(&E.gexec, graph, 0));
             cudaGraphDestroy(graph);
+            E.glaunch = g_launches.load() - before;
             g_launches = before;  // captured launches run (and are counted) at replay
         }
         while (left >= Engine::CHUNK) {
             CK(cudaGraphLaunch(E.gexec, E.stream));
-            count_launches(Engine::CHUNK * (E.np > 0 ? 2 : 1));
+            count_launches(E.glaunch);
             left -= Engine::CHUNK;
             E.t += Engine::CHUNK;
         }
     }
     while (left > 0) {
-        int rc = issue_step(E, E.par);
+        int rc = one_step();
         if (rc) return (E.sticky = rc);
-        E.par ^= 1;
-        E.t++;
         left--;
     }
     return PF_OK;

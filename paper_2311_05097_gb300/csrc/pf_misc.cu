@@ -3,6 +3,7 @@
 //
 // These kernels run once per call (init, diagnostics) or once per step on a
 // handful of particles; they are written for clarity, in double precision.
+#include "pf.h"
 #include "pf_internal.h"
 
 namespace pf {
@@ -467,54 +468,61 @@ __global__ void k_diag_final(const double *partial, int nblocks, double *out)
 // eps/2, x_j the mirror image of particle k across that wall: a box wall at
 // y = -1/2 or ny - 1/2, or the circle p.wall_circle along its radius); from
 // the positions before this step's update.
+// One block per particle k: thread 0 takes the wall term, thread 1 + j the
+// pair with particle j, then a fixed-order sum (each warp's shuffle tree, the
+// warps in order).  FP64 throughout.
+constexpr int REP_THREADS = 128;
+static_assert(REP_THREADS >= PF_MAX_PARTICLES + 1, "one thread per partner and one for the wall");
 __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams p, int nx, int ny, int nz,
                                      int wall_y, double *frep)
 {
-    const int k = threadIdx.x;
+    const int k = blockIdx.x, tid = threadIdx.x;
     if (k >= np) return;
-    const int n[3] = {nx, ny, nz};
+    __shared__ double red[REP_THREADS / 32][3];
     double acc[3] = {0.0, 0.0, 0.0};
     if (p.rep_eps > 0.0) {
-        double best = INFINITY, dw0 = 0.0, dw1 = 0.0;  // x_k - x'_k
-        if (wall_y) {
-            const double y = parts[k].x[1];
-            const double lo = 2.0 * (y + 0.5), hi = 2.0 * (ny - 0.5 - y);
-            if (lo < best) {
-                best = lo;
-                dw0 = 0.0;
-                dw1 = lo;
-            }
-            if (hi < best) {
-                best = hi;
-                dw0 = 0.0;
-                dw1 = -hi;
-            }
-        }
-        if (p.dim == 2 && p.wall_circle[2] > 0.0) {
-            const double ex = parts[k].x[0] - p.wall_circle[0], ey = parts[k].x[1] - p.wall_circle[1];
-            const double r = sqrt(ex * ex + ey * ey);
-            if (r > 0.0) {
-                const double dd = 2.0 * fabs(p.wall_circle[2] - r);
-                if (dd < best) {
-                    const double s = (r - (2.0 * p.wall_circle[2] - r)) / r;
-                    best = dd;
-                    dw0 = s * ex;
-                    dw1 = s * ey;
+        if (tid == 0) {
+            double best = INFINITY, dw0 = 0.0, dw1 = 0.0;  // x_k - x'_k
+            if (wall_y) {
+                const double y = parts[k].x[1];
+                const double lo = 2.0 * (y + 0.5), hi = 2.0 * (ny - 0.5 - y);
+                if (lo < best) {
+                    best = lo;
+                    dw0 = 0.0;
+                    dw1 = lo;
+                }
+                if (hi < best) {
+                    best = hi;
+                    dw0 = 0.0;
+                    dw1 = -hi;
                 }
             }
-        }
-        if (best < INFINITY) {
-            const double rr = 2.0 * parts[k].R;
-            double f = 0.0;
-            if (best <= rr + p.rep_xi) {
-                if (best >= rr) f = (rr + p.rep_xi - best) * (rr + p.rep_xi - best) / (0.5 * p.rep_eps);
-                else f = (rr - best) / (0.5 * p.rep_eps);
+            if (p.dim == 2 && p.wall_circle[2] > 0.0) {
+                const double ex = parts[k].x[0] - p.wall_circle[0], ey = parts[k].x[1] - p.wall_circle[1];
+                const double r = sqrt(ex * ex + ey * ey);
+                if (r > 0.0) {
+                    const double dd = 2.0 * fabs(p.wall_circle[2] - r);
+                    if (dd < best) {
+                        const double s = (r - (2.0 * p.wall_circle[2] - r)) / r;
+                        best = dd;
+                        dw0 = s * ex;
+                        dw1 = s * ey;
+                    }
+                }
             }
-            acc[0] += f * dw0;
-            acc[1] += f * dw1;
-        }
-        for (int j = 0; j < np; ++j) {
-            if (j == k) continue;
+            if (best < INFINITY) {
+                const double rr = 2.0 * parts[k].R;
+                double f = 0.0;
+                if (best <= rr + p.rep_xi) {
+                    if (best >= rr) f = (rr + p.rep_xi - best) * (rr + p.rep_xi - best) / (0.5 * p.rep_eps);
+                    else f = (rr - best) / (0.5 * p.rep_eps);
+                }
+                acc[0] = f * dw0;
+                acc[1] = f * dw1;
+            }
+        } else if (tid - 1 < np && tid - 1 != k) {
+            const int j = tid - 1;
+            const int n[3] = {nx, ny, nz};
             double dx[3], d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double v = a < p.dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
@@ -528,15 +536,28 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
                 if (dist >= rr) f = (rr + p.rep_xi - dist) * (rr + p.rep_xi - dist) / p.rep_eps;
                 else f = (rr - dist) / p.rep_eps;
             }
-            for (int a = 0; a < 3; ++a) acc[a] += f * dx[a];
+            for (int a = 0; a < 3; ++a) acc[a] = f * dx[a];
         }
     }
-    for (int a = 0; a < 3; ++a) frep[3 * k + a] = acc[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double v = acc[a];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5][a] = v;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        double v = 0.0;
+        for (int w = 0; w < REP_THREADS / 32; ++w) v += red[w][tid];
+        frep[3 * k + tid] = v;
+    }
 }
 
 // One block per particle; each thread sums a fixed strided set of tiles, then
-// a fixed tree (the order depends only on the tile count).
-constexpr int UPDATE_THREADS = 512;
+// each warp's shuffle tree and the warps in order (the order depends only on
+// the tile count).
+constexpr int UPDATE_THREADS = 256;
 // sel: optional per-tile flags; tiles with sel[t] == 0 hold zero partials
 // and are skipped (adding them would not change the sums)
 __global__ void k_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
@@ -544,19 +565,27 @@ __global__ void k_particle_update(ParticleDev *parts, int np, const double *part
 {
     const int k = blockIdx.x;
     if (k >= np) return;
-    __shared__ double red[UPDATE_THREADS][6];
+    __shared__ double wred[UPDATE_THREADS / 32][6];
+    __shared__ double red[1][6];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         if (sel && !sel[t]) continue;
         for (int c = 0; c < 6; ++c) acc[c] += partials[((long long)t * np + k) * 6 + c];
     }
-    for (int c = 0; c < 6; ++c) red[threadIdx.x][c] = acc[c];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-            for (int c = 0; c < 6; ++c) red[threadIdx.x][c] += red[threadIdx.x + s][c];
-        __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        double v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5][c] = v;
     }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double v = 0.0;
+        for (int w = 0; w < UPDATE_THREADS / 32; ++w) v += wred[w][threadIdx.x];
+        red[0][threadIdx.x] = v;
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     ParticleDev &pp = parts[k];
     const double R = pp.R;
@@ -660,7 +689,7 @@ void launch_particle_update(ParticleDev *parts, int np, const double *partials, 
                             const DevParams &p, double *frep, int nx, int ny, int nz, int wall_y,
                             const unsigned char *sel, cudaStream_t s)
 {
-    k_particle_repulsion<<<1, 64, 0, s>>>(parts, np, p, nx, ny, nz, wall_y, frep);
+    k_particle_repulsion<<<np, REP_THREADS, 0, s>>>(parts, np, p, nx, ny, nz, wall_y, frep);
     k_particle_update<<<np, UPDATE_THREADS, 0, s>>>(parts, np, partials, ntiles, p, frep, sel);
     count_launches(2);
 }
