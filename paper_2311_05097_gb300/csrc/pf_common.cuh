@@ -222,7 +222,7 @@ struct StepArgs {
     int par;               // read buffer parity
     const ParticleDev *parts;
     int np;
-    double *partials;      // [tile][particle][6]: F_f and T_f partial sums (Eq. 27)
+    double *partials;      // [particle][6][tile]: F_f and T_f partial sums (Eq. 27)
     int *flags;            // [0]: non-finite value seen
     int wv;                // some particle has its own contact angle (W, V fields)
     int wait_polls;        // polls of one bounded device wait (staged kernel); 0: default

@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                 // adds them up.
                 // particles out of this tile's reach: zero partials
                 for (int q = tid; q < 6 * A.np; q += NT)
-                    if (!((near >> (q / 6)) & 1ull)) A.partials[(long long)t * A.np * 6 + q] = 0.0;
+                    if (!((near >> (q / 6)) & 1ull)) A.partials[(long long)q * A.ntiles + t] = 0.0;
                 int nj = 0;
                 auto flush = [&]() {
                     __syncthreads();  // the warps' sums of the nj particles are in s_red
@@ -743,7 +743,7 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                             const int c = comp == 5 ? 2 : comp;
                             for (int wq = 0; wq < NT / 32; ++wq) acc += s_red[j][wq][c];
                         }
-                        A.partials[((long long)t * A.np + s_redk[j]) * 6 + comp] = acc;
+                        A.partials[((long long)s_redk[j] * 6 + comp) * A.ntiles + t] = acc;
                     }
                     __syncthreads();  // s_red and s_redk are free again
                     nj = 0;

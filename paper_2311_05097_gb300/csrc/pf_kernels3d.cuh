@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
                             // per tile and plane: partial sums accumulate over the z loop in order
                             double acc = 0.0;
                             for (int wq = 0; wq < NT / 32; ++wq) acc += red[wq][tid];
-                            double *dst = A.partials + ((long long)t * A.np + k) * 6 + tid;
+                            double *dst = A.partials + ((long long)k * 6 + tid) * A.ntiles + t;
                             *dst = (z == z0 ? 0.0 : *dst) + acc;
                         }
                     }

@@ -435,7 +435,7 @@ __global__ void k_split_tiles(StepArgs A, int tx, int ty, unsigned char *sel)
     }
     sel[t] = near ? 1 : 0;
     if (!near)
-        for (int c = 0; c < 6 * A.np; ++c) A.partials[(long long)t * A.np * 6 + c] = 0.0;
+        for (int c = 0; c < 6 * A.np; ++c) A.partials[(long long)c * A.ntiles + t] = 0.0;
 }
 
 void launch_split_tiles(const StepArgs &a, int tx, int ty, unsigned char *sel, cudaStream_t s)
@@ -471,10 +471,11 @@ __global__ void k_diag_final(const double *partial, int nblocks, double *out)
 // One block per particle k: thread 0 takes the wall term, thread 1 + j the
 // pair with particle j, then a fixed-order sum (each warp's shuffle tree, the
 // warps in order).  FP64 throughout.
-constexpr int REP_THREADS = 128;
+constexpr int REP_THREADS = 96;
 static_assert(REP_THREADS >= PF_MAX_PARTICLES + 1, "one thread per partner and one for the wall");
-__global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams p, int nx, int ny, int nz,
-                                     int wall_y, double *frep)
+__global__ void __launch_bounds__(REP_THREADS) k_particle_repulsion(const ParticleDev *parts, int np, DevParams p,
+                                                                    int nx, int ny, int nz, int wall_y,
+                                                                    double *frep)
 {
     const int k = blockIdx.x, tid = threadIdx.x;
     if (k >= np) return;
@@ -526,17 +527,22 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
             double dx[3], d2 = 0.0;
             for (int a = 0; a < 3; ++a) {
                 double v = a < p.dim ? parts[k].x[a] - parts[j].x[a] : 0.0;
-                if (a < p.dim && !(a == 1 && wall_y)) v -= n[a] * floor(v / n[a] + 0.5);
+                // minimum image (the division only where it can shift: FP64 is slow here)
+                if (a < p.dim && !(a == 1 && wall_y) && (v >= 0.5 * n[a] || v <= -0.5 * n[a]))
+                    v -= n[a] * floor(v / n[a] + 0.5);
                 dx[a] = v;
                 d2 += v * v;
             }
-            const double dist = sqrt(d2), rr = parts[k].R + parts[j].R;
-            double f = 0.0;
-            if (dist <= rr + p.rep_xi) {
-                if (dist >= rr) f = (rr + p.rep_xi - dist) * (rr + p.rep_xi - dist) / p.rep_eps;
-                else f = (rr - dist) / p.rep_eps;
+            const double rr = parts[k].R + parts[j].R, reach = rr + p.rep_xi;
+            if (d2 <= reach * reach) {  // (the pairs farther apart get no force: no square root)
+                const double dist = sqrt(d2);
+                double f = 0.0;
+                if (dist <= reach) {
+                    if (dist >= rr) f = (reach - dist) * (reach - dist) / p.rep_eps;
+                    else f = (rr - dist) / p.rep_eps;
+                }
+                for (int a = 0; a < 3; ++a) acc[a] = f * dx[a];
             }
-            for (int a = 0; a < 3; ++a) acc[a] = f * dx[a];
         }
     }
 #pragma unroll
@@ -560,7 +566,8 @@ __global__ void k_particle_repulsion(const ParticleDev *parts, int np, DevParams
 constexpr int UPDATE_THREADS = 256;
 // sel: optional per-tile flags; tiles with sel[t] == 0 hold zero partials
 // and are skipped (adding them would not change the sums)
-__global__ void k_particle_update(ParticleDev *parts, int np, const double *partials, int ntiles,
+__global__ void __launch_bounds__(UPDATE_THREADS) k_particle_update(ParticleDev *parts, int np,
+                                                                    const double *partials, int ntiles,
                                   DevParams p, const double *frep, const unsigned char *sel)
 {
     const int k = blockIdx.x;
@@ -570,10 +577,25 @@ __global__ void k_particle_update(ParticleDev *parts, int np, const double *part
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
         if (sel && !sel[t]) continue;
-        for (int c = 0; c < 6; ++c) acc[c] += partials[((long long)t * np + k) * 6 + c];
+        // component c of tile t: partials[(6 k + c) ntiles + t] (consecutive
+        // threads read consecutive tiles); 2D: components 2, 3, 4 stay zero
+        const double *q = partials + (long long)k * 6 * ntiles + t;
+        acc[0] += q[0];
+        acc[1] += q[(long long)ntiles];
+        acc[5] += q[5LL * ntiles];
+        if (p.dim == 3) {
+            acc[2] += q[2LL * ntiles];
+            acc[3] += q[3LL * ntiles];
+            acc[4] += q[4LL * ntiles];
+        }
     }
+    // (FP64 adds are slow on this part: 2D sums only F_x, F_y, T_z)
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
+        if (p.dim == 2 && c >= 2 && c <= 4) {
+            if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5][c] = 0.0;
+            continue;
+        }
         double v = acc[c];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
