@@ -287,9 +287,13 @@ __device__ __forceinline__ R particle_phi0_3d(const ParticleDev &pp, int gx, int
 
 // EXT: the instantiation also handles domains with walls at the ends of y
 // UNIT: every domain of the launch has unit rates for its non-conserved
-// moments (FP32 arithmetic only): the collisions above
+// moments (FP32 arithmetic only): the collisions above.  FP32 arithmetic
+// without particles: three CTAs per SM (80 registers, a few spilled; the step
+// waits on global loads, and 24 warps per SM hide more of them than 16 at
+// 128 registers: measured 9.8k -> 11.8k MLUPS on the 256^3 drainage, while
+// four CTAs at 64 registers spill too much, 10.8k)
 template <class P, int TX, int TY, int ZC, bool MOVING, int MODE, bool EXT, bool UNIT = false>
-__global__ void __launch_bounds__(TX *TY) k_step3d(StepArgs A)
+__global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOVING) ? 3 : 1) k_step3d(StepArgs A)
 {
     using R = typename P::real;
     using ST = typename P::store;
