@@ -428,29 +428,30 @@ def run_batch(args, dist, rank, world, local):
         L = pf.load()
         e2e_b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases],
                          precision=prec, stream=stream.cuda_stream)
+        nd = len(hosts)
+        t_phi0 = (C.c_void_p * nd)(*[h[0].data_ptr() for h in hosts])
+        t_phi = (C.c_void_p * nd)(*[h[1].data_ptr() for h in hosts])
+        t_out = (C.c_void_p * nd)(*[h[2].data_ptr() for h in hosts])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i, (h0, h1, _) in enumerate(hosts):
-            rc = L.pf_batch_init(e2e_b._h, i, C.c_void_p(h0.data_ptr()), C.c_void_p(h1.data_ptr()),
-                                 None, None, pf.PF_HOST)
-            if rc:
-                raise pf.PfError(rc, pf.last_error())
+        rc = L.pf_batch_init_all(e2e_b._h, C.cast(t_phi0, C.c_void_p), C.cast(t_phi, C.c_void_p), None, None,
+                                 pf.PF_HOST)
+        if rc:
+            raise pf.PfError(rc, pf.last_error())
         e2e_b.step(S)
-        for i, (_, _, out) in enumerate(hosts):
-            rc = L.pf_batch_get_macros(e2e_b._h, i, C.c_void_p(out.data_ptr()), None, None, None,
-                                       None, pf.PF_HOST)
-            if rc:
-                raise pf.PfError(rc, pf.last_error())
+        rc = L.pf_batch_get_macros_all(e2e_b._h, C.cast(t_out, C.c_void_p), None, None, None, None, pf.PF_HOST)
+        if rc:
+            raise pf.PfError(rc, pf.last_error())
         dt = time.perf_counter() - t0
         e2e_b.close()
         e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
                "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
-               "desc": "one call sequence: pf_batch_init of every domain from pinned host phi0, "
-                       "phi; pf_batch_step(%d) (includes the autotuner's timed steps when the "
-                       "configuration is not cached); pf_batch_get_macros(phi) of every domain "
-                       "to pinned host; wall clock" % S}
+               "desc": "one call sequence: pf_batch_init_all (every domain from pinned host phi0, "
+                       "phi); pf_batch_step(%d) (includes the autotuner's timed steps when the "
+                       "configuration is not cached); pf_batch_get_macros_all (phi of every domain "
+                       "to pinned host); wall clock" % S}
     b.close()
     cfg = {"workload": args.workload, "domains": len(cases), "cells": cells, "precision": prec,
            "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"

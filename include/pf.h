@@ -271,6 +271,20 @@ int pf_batch_init(pf_batch *b, int i, const double *phi0, const double *phi, con
 int pf_batch_step(pf_batch *b, int64_t n);
 int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u, double *P,
                         double *mu, int where);
+/* Every domain of a batch in one call (no counterpart in the paper): the
+ * same work as pf_batch_init / pf_batch_get_macros for i = 0 .. nd - 1, in
+ * domain order on the batch's stream, with one wait at the end instead of
+ * one per domain.  Each argument is an array of nd pointers, one per domain,
+ * with the layout of the single-domain call; phi0 and phi (and their
+ * entries) are required; u, P (init) and any output array may be NULL (the
+ * field is not given / not read), and so may single entries.  where applies
+ * to every pointer.  Synchronous: the caller's arrays may be reused when
+ * the call returns.  Errors as for the single-domain calls; on an error the
+ * domains before the failing one may already be done. */
+int pf_batch_init_all(pf_batch *b, const double *const *phi0, const double *const *phi,
+                      const double *const *u, const double *const *P, int where);
+int pf_batch_get_macros_all(pf_batch *b, double *const *phi, double *const *rho, double *const *u,
+                            double *const *P, double *const *mu, int where);
 int pf_batch_diagnostics(pf_batch *b, int i, pf_diag *out);
 int pf_batch_sync(pf_batch *b);
 /* Total lattice cells of the batch and the chosen launch configuration

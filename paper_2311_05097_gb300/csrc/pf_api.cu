@@ -1255,15 +1255,12 @@ static int engine_macros(Engine &E, int i)
     return PF_OK;
 }
 
-static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double *u, double *P,
-                             double *mu, int where)
+// the macroscopic pass of domain i and the copies of the requested fields,
+// queued on the engine's stream (the caller waits)
+static int engine_queue_macros(Engine &E, int i, double *phi, double *rho, double *u, double *P, double *mu,
+                               int where)
 {
-    PfRange range("pf_get_macros");
-    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
-    if (!E.inited[i]) return fail(PF_ESTATE, "pf_get_macros before pf_init_fields");
-    int rc = engine_sync(E);
-    if (rc && rc != PF_ENUMERIC) return rc;
-    rc = engine_macros(E, i);
+    int rc = engine_macros(E, i);
     if (rc) return rc;
     const DomainMem &m = E.mem[i];
     const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
@@ -1276,6 +1273,19 @@ static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double 
     if (u) CK(cudaMemcpyAsync(u, mac + 2 * N, sizeof(double) * d * N, kind, E.stream));
     if (P) CK(cudaMemcpyAsync(P, mac + (2 + d) * N, sizeof(double) * N, kind, E.stream));
     if (mu) CK(cudaMemcpyAsync(mu, mac + (3 + d) * N, sizeof(double) * N, kind, E.stream));
+    return PF_OK;
+}
+
+static int engine_get_macros(Engine &E, int i, double *phi, double *rho, double *u, double *P,
+                             double *mu, int where)
+{
+    PfRange range("pf_get_macros");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    if (!E.inited[i]) return fail(PF_ESTATE, "pf_get_macros before pf_init_fields");
+    int rc = engine_sync(E);
+    if (rc && rc != PF_ENUMERIC) return rc;
+    rc = engine_queue_macros(E, i, phi, rho, u, P, mu, where);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(E.stream));
     return PF_OK;
 }
@@ -1721,6 +1731,38 @@ extern "C" int pf_batch_init(pf_batch *b, int i, const double *phi0, const doubl
     return PF_OK;
 }
 
+extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const double *const *phi,
+                                 const double *const *u, const double *const *P, int where)
+{
+    PfRange range("pf_batch_init_all");
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    if (!phi0 || !phi) return fail(PF_EINVAL, "phi0 and phi are required");
+    Engine &E = b->E;
+    if (E.sticky) return E.sticky;
+    if (E.t != 0) return fail(PF_ESTATE, "all domains are initialised before the first step");
+    E.ghosts_ok = false;
+    // the staging area sized for the largest domain once (the inits reuse it in stream order)
+    size_t big = 0;
+    auto cells = [&](size_t i) { return (long long)E.mem[i].d.nx * E.mem[i].d.ny * E.mem[i].d.nz; };
+    for (size_t i = 1; i < E.mem.size(); ++i)
+        if (cells(i) > cells(big)) big = i;
+    if (!E.mem.empty()) {
+        int rc = staging_reserve(E.staging, E.mem[big], E.dim);
+        if (rc) return rc;
+    }
+    for (size_t i = 0; i < E.mem.size(); ++i) {
+        int rc = domain_init(E.mem[i], E.staging, E.dim, E.prec, phi0[i], phi[i], u ? u[i] : nullptr,
+                             P ? P[i] : nullptr, where, E.d_parts, nullptr, 0, E.d_flags, E.stream);
+        if (rc) {
+            cudaStreamSynchronize(E.stream);
+            return rc;
+        }
+    }
+    CK(cudaStreamSynchronize(E.stream));
+    for (size_t i = 0; i < E.mem.size(); ++i) E.inited[i] = true;
+    return PF_OK;
+}
+
 extern "C" int pf_batch_step(pf_batch *b, int64_t n)
 {
     PfRange range("pf_batch_step");
@@ -1740,6 +1782,29 @@ extern "C" int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho,
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (i < 0 || i >= (int)b->E.mem.size()) return fail(PF_EINVAL, "domain index %d out of range", i);
     return engine_get_macros(b->E, i, phi, rho, u, P, mu, where);
+}
+
+extern "C" int pf_batch_get_macros_all(pf_batch *b, double *const *phi, double *const *rho, double *const *u,
+                                       double *const *P, double *const *mu, int where)
+{
+    PfRange range("pf_batch_get_macros_all");
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    Engine &E = b->E;
+    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
+    for (size_t i = 0; i < E.mem.size(); ++i)
+        if (!E.inited[i]) return fail(PF_ESTATE, "pf_batch_get_macros_all before every domain is initialised");
+    int rc = engine_sync(E);
+    if (rc && rc != PF_ENUMERIC) return rc;
+    for (size_t i = 0; i < E.mem.size(); ++i) {
+        rc = engine_queue_macros(E, (int)i, phi ? phi[i] : nullptr, rho ? rho[i] : nullptr, u ? u[i] : nullptr,
+                                 P ? P[i] : nullptr, mu ? mu[i] : nullptr, where);
+        if (rc) {
+            cudaStreamSynchronize(E.stream);
+            return rc;
+        }
+    }
+    CK(cudaStreamSynchronize(E.stream));
+    return PF_OK;
 }
 
 extern "C" int pf_batch_diagnostics(pf_batch *b, int i, pf_diag *out)

@@ -99,6 +99,8 @@ def load(build_if_missing=False):
         "pf_batch_init": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, C.c_int]),
         "pf_batch_step": (C.c_int, [vp, C.c_int64]),
         "pf_batch_get_macros": (C.c_int, [vp, C.c_int, vp, vp, vp, vp, vp, C.c_int]),
+        "pf_batch_init_all": (C.c_int, [vp, vp, vp, vp, vp, C.c_int]),
+        "pf_batch_get_macros_all": (C.c_int, [vp, vp, vp, vp, vp, vp, C.c_int]),
         "pf_batch_diagnostics": (C.c_int, [vp, C.c_int, C.POINTER(pf_diag)]),
         "pf_batch_sync": (C.c_int, [vp]),
         "pf_batch_cells": (C.c_int64, [vp]),
@@ -362,6 +364,41 @@ class Batch:
         where = PF_DEVICE if _is_device(phi) else PF_HOST
         keep = [_ptr(a, where) for a in (phi0, phi, u, P)]
         _check(load().pf_batch_init(self._h, int(i), *[k[0] for k in keep], where))
+
+    def init_all(self, phi0s, phis, us=None):
+        """pf_batch_init_all: every domain from lists of arrays (host or device)."""
+        where = PF_DEVICE if _is_device(phis[0]) else PF_HOST
+        n = len(self.shapes)
+        keep = []
+
+        def table(arrs):
+            if arrs is None:
+                return None
+            t = (C.c_void_p * n)()
+            for i, a in enumerate(arrs):
+                p, k = _ptr(a, where)
+                keep.append(k)
+                t[i] = p.value if p is not None else None
+            keep.append(t)
+            return C.cast(t, C.c_void_p)
+
+        _check(load().pf_batch_init_all(self._h, table(phi0s), table(phis), table(us), None, where))
+
+    def macros_all(self):
+        """pf_batch_get_macros_all: the fields of every domain (host arrays)."""
+        n = len(self.shapes)
+        outs = []
+        tabs = [(C.c_void_p * n)() for _ in range(5)]
+        for i, sh in enumerate(self.shapes):
+            N = int(np.prod(sh))
+            phi, rho, P, mu = (np.empty(N) for _ in range(4))
+            u = np.empty(self.dim * N)
+            for t, a in zip(tabs, (phi, rho, u, P, mu)):
+                t[i] = a.ctypes.data
+            outs.append(dict(phi=phi.reshape(sh), rho=rho.reshape(sh), u=u.reshape((self.dim,) + sh),
+                             P=P.reshape(sh), mu=mu.reshape(sh)))
+        _check(load().pf_batch_get_macros_all(self._h, *[C.cast(t, C.c_void_p) for t in tabs], PF_HOST))
+        return outs
 
     def step(self, n=1):
         _check(load().pf_batch_step(self._h, int(n)))

@@ -302,3 +302,27 @@ def test_single_handle_autotune(pf):
     h.init(c["phi0"], c["phi"], c["u"])
     assert h.autotune() == 0
     assert h.config() == cfg
+
+
+def test_batch_init_all_and_macros_all_equal_per_domain_calls(pf):
+    """pf_batch_init_all / pf_batch_get_macros_all (one wait for all domains)
+    give the same state and fields as the per-domain calls, bit for bit."""
+    cases = [W.flat_wall_drop(64, 40.0, 30.0), W.flat_wall_drop(128, 140.0, 3.0),
+             W.small_case((70, 96), seed=3, solid=True, theta_deg=120.0, u_amp=0.01)]
+    shapes = [c["shape"] for c in cases]
+    params = [c["params"] for c in cases]
+    a = pf.Batch(shapes, params, precision="fp16")
+    for i, c in enumerate(cases):
+        a.init(i, c["phi0"], c["phi"], c.get("u"))
+    b = pf.Batch(shapes, params, precision="fp16")
+    b.init_all([c["phi0"] for c in cases], [c["phi"] for c in cases],
+               [c.get("u") if c.get("u") is not None else None for c in cases])
+    for x in (a, b):
+        x.set_config(64, 32, 4)
+        x.step(40)
+        x.sync()
+    mb = b.macros_all()
+    for i in range(len(cases)):
+        ma = a.macros(i)
+        for k in FIELDS:
+            assert np.array_equal(ma[k], mb[i][k]), (i, k)
