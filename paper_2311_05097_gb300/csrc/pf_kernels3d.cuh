@@ -494,8 +494,27 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
         mu_plane(z0);
         __syncthreads();
 
+        // PRE: the own cell's loads of phase 3 (its pulled populations of both
+        // lattices, the rest population, the lagged fields) are issued at the
+        // top of the plane, so that their round trip overlaps the loads of
+        // phase 1 instead of following two barriers
+        constexpr bool PRE = MODE == MODE_STEP && !MOVING && sizeof(R) == 4;
         const int zend = min(z0 + ZC, nz);
         for (int z = z0; z < zend; ++z) {
+            [[maybe_unused]] ST q1p[7], q2p[19];
+            [[maybe_unused]] AX lagp[7];
+            [[maybe_unused]] long long restp = 0;
+            if constexpr (PRE) {
+                const int zo0 = zoff(z);
+                const int id0 = cidx(lx + 3, ly + 3, zo0);
+                if constexpr (P::MIX) restp = rs[id0];
+#pragma unroll
+                for (int i = P::MIX ? 1 : 0; i < 7; ++i) q1p[i] = ldg(fs + pull(0, i, lx + 3, ly + 3, z));
+#pragma unroll
+                for (int i = 0; i < 19; ++i) q2p[i] = ldg(fs + pull(7, i, lx + 3, ly + 3, z));
+#pragma unroll
+                for (int k = 0; k < 7; ++k) lagp[k] = ldg(as + k * plane + id0);
+            }
             // phase 1: phi plane z+2 and T plane z+1
             load_phi_plane(z + 2);
             if constexpr (MODE == MODE_STEP) load_T_plane(z + 1);
@@ -519,7 +538,33 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
 
             R f1[7];
             ST q1[7];
-            const R phi = phi_at(hx, hy, z, f1, q1);
+            R phi;
+            if constexpr (PRE) {
+                // phi_at's sum, in its order, from the values loaded at the top
+                if constexpr (P::MIX) {
+                    R acc = float_of_fixed(restp);
+                    f1[0] = acc;
+#pragma unroll
+                    for (int i = 1; i < 7; ++i) {
+                        const R v = Conv<P>::ld(q1p[i], isc1);
+                        f1[i] = v;
+                        q1[i] = q1p[i];
+                        acc += v;
+                    }
+                    phi = acc;
+                } else {
+                    R acc = R(0);
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) {
+                        const R v = Conv<P>::ld(q1p[i], isc1);
+                        f1[i] = v;
+                        acc += v;
+                    }
+                    phi = acc;
+                }
+            } else {
+                phi = phi_at(hx, hy, z, f1, q1);
+            }
             const R phi0 = s_p0[wrap_idx(z, 5)][hy * FX + hx];
             R gpx, gpy, gpz, gmx, gmy, gmz;
             grad19<R, FX>(plo, pmid, phi_hi, hx, hy, gpx, gpy, gpz);
@@ -607,7 +652,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
             R f2[19];
 #pragma unroll
             for (int i = 0; i < 19; ++i)
-                f2[i] = Conv<P>::ld(ldg(fs + pull(7, i, lx + 3, ly + 3, z)), isc2);
+                f2[i] = Conv<P>::ld(PRE ? q2p[i] : ldg(fs + pull(7, i, lx + 3, ly + 3, z)), isc2);
             R jx = R(0), jy = R(0), jz = R(0), sum_f = R(0);
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
@@ -634,11 +679,13 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
             }
             const R ux = usx + R(0.5) * fpx, uy = usy + R(0.5) * fpy, uz = usz + R(0.5) * fpz;
             const R Ftx = Fx + rho * fpx, Fty = Fy + rho * fpy, Ftz = Fz + rho * fpz;
-            const R upx = (R)ldg(as + 0 * plane + id), upy = (R)ldg(as + 1 * plane + id),
-                    upz = (R)ldg(as + 2 * plane + id);
-            const R Spx = (R)ldg(as + 3 * plane + id), Spy = (R)ldg(as + 4 * plane + id),
-                    Spz = (R)ldg(as + 5 * plane + id);
-            const R php = (R)ldg(as + 6 * plane + id);
+            const R upx = (R)(PRE ? lagp[0] : ldg(as + 0 * plane + id)),
+                    upy = (R)(PRE ? lagp[1] : ldg(as + 1 * plane + id)),
+                    upz = (R)(PRE ? lagp[2] : ldg(as + 2 * plane + id));
+            const R Spx = (R)(PRE ? lagp[3] : ldg(as + 3 * plane + id)),
+                    Spy = (R)(PRE ? lagp[4] : ldg(as + 4 * plane + id)),
+                    Spz = (R)(PRE ? lagp[5] : ldg(as + 5 * plane + id));
+            const R php = (R)(PRE ? lagp[6] : ldg(as + 6 * plane + id));
 
             R solid = R(1) - phi0;
             const R seps = kp.solid_eps;
@@ -785,7 +832,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
                             st_stream(fd + i * plane + id, qv);
                         }
                         // exact: sum of the cell's order-parameter populations is unchanged
-                        st_stream(rd + id, rs[id] + fix24_to_rest(sold - snew, k1));
+                        st_stream(rd + id, (PRE ? restp : rs[id]) + fix24_to_rest(sold - snew, k1));
                         if (bad) atomicOr(A.flags, 2);
                     } else {
 #pragma unroll
