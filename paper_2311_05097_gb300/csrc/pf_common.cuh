@@ -398,6 +398,14 @@ __device__ __forceinline__ int wrap_idx(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// d - n rint(d / n), the minimum image of a separation: without the FP64
+// division (slow on this part) where it cannot shift, |d| <= n/2 (rint of a
+// quotient in [-1/2, 1/2] is zero, so the result is the same)
+__device__ __forceinline__ double min_image(double d, int n)
+{
+    return fabs(d) > 0.5 * n ? d - n * rint(d / n) : d;
+}
+
 // periodic index for v in [-n, 2n): no division
 __device__ __forceinline__ int wrap_near(int v, int n)
 {

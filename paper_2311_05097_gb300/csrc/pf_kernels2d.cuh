@@ -108,8 +108,8 @@ __device__ __forceinline__ R particle_phi0(const ParticleDev &pp, int gx, int gy
                                            double D, double cut, R &rx, R &ry)
 {
     double dx = (double)gx - pp.x[0], dy = (double)gy - pp.x[1];
-    dx -= nx * rint(dx / nx);
-    if (!EXT || ny > 0) dy -= ny * rint(dy / ny);  // ny <= 0: walls in y, no minimum image
+    dx = min_image(dx, nx);
+    if (!EXT || ny > 0) dy = min_image(dy, ny);  // ny <= 0: walls in y, no minimum image
     rx = (R)dx;
     ry = (R)dy;
     double r2 = dx * dx + dy * dy;
@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
             for (int k = tid; k < A.np; k += NT) {
                 const ParticleDev &pp = A.parts[k];
                 double dx = (x0 + 0.5 * (TX - 1)) - pp.x[0], dy = (y0 + 0.5 * (TY - 1)) - pp.x[1];
-                dx -= nx * rint(dx / nx);
-                if (!EXT || !wall) dy -= ny * rint(dy / ny);
+                dx = min_image(dx, nx);
+                if (!EXT || !wall) dy = min_image(dy, ny);
                 const double ex = fmax(fabs(dx) - (0.5 * TX + 2.0), 0.0);
                 const double ey = fmax(fabs(dy) - (0.5 * TY + 2.0), 0.0);
                 const double lim = pp.R + p.cut + 1.0;

@@ -272,9 +272,9 @@ __device__ __forceinline__ R particle_phi0_3d(const ParticleDev &pp, int gx, int
                                               R &rz)
 {
     double dx = (double)gx - pp.x[0], dy = (double)gy - pp.x[1], dz = (double)gz - pp.x[2];
-    dx -= nx * rint(dx / nx);
-    if (ny > 0) dy -= ny * rint(dy / ny);  // ny <= 0: walls in y, no minimum image
-    dz -= nz * rint(dz / nz);
+    dx = min_image(dx, nx);
+    if (ny > 0) dy = min_image(dy, ny);  // ny <= 0: walls in y, no minimum image
+    dz = min_image(dz, nz);
     rx = (R)dx;
     ry = (R)dy;
     rz = (R)dz;

@@ -81,7 +81,7 @@ __device__ double particle_indicator_d(const ParticleDev &pp, int x, int y, int 
     const int n[3] = {Dm.nx, Dm.ny, Dm.nz};
     double r2 = 0.0;
     for (int a = 0; a < 3; ++a) {
-        if (a < dim && !(a == 1 && Dm.wall_y)) d[a] -= n[a] * rint(d[a] / n[a]);
+        if (a < dim && !(a == 1 && Dm.wall_y)) d[a] = min_image(d[a], n[a]);
         r[a] = d[a];
         r2 += d[a] * d[a];
     }
@@ -426,8 +426,8 @@ __global__ void k_split_tiles(StepArgs A, int tx, int ty, unsigned char *sel)
     for (int k = 0; k < A.np && !near; ++k) {
         const ParticleDev &pp = A.parts[k];
         double dx = (x0 + 0.5 * (tx - 1)) - pp.x[0], dy = (y0 + 0.5 * (ty - 1)) - pp.x[1];
-        dx -= nx * rint(dx / nx);
-        dy -= ny * rint(dy / ny);
+        dx = min_image(dx, nx);
+        dy = min_image(dy, ny);
         const double ex = fmax(fabs(dx) - (0.5 * tx + 2.0), 0.0);
         const double ey = fmax(fabs(dy) - (0.5 * ty + 2.0), 0.0);
         const double lim = pp.R + Dm.p.cut + 1.0;
