@@ -308,10 +308,11 @@ int pf_batch_config(pf_batch *b, int *tile_x, int *tile_y, int *ctas_per_sm, int
  *      multiple of 8 for 16-bit storage, of 4 for FP32; the Cahn-Hilliard
  *      lattice only);
  *   3  2D with free particles: the tiles out of every particle's reach run
- *      kernel 1 (with the fixed solids' mu_phi0 grad phi0 of Eq. 19), the
- *      others kernel 0, chosen on the device each step (one domain, P32 or
- *      PMIX, tile 32x16, no walls, the Cahn-Hilliard lattice; particles may
- *      have their own contact angles);
+ *      kernel 1 (with walls at the ends of y: kernel 0 without the particle
+ *      terms), with the fixed solids' mu_phi0 grad phi0 of Eq. 19, the
+ *      others kernel 0 with them, chosen on the device each step (one
+ *      domain, P32 or PMIX, tile 32x16, the Cahn-Hilliard lattice; particles
+ *      may have their own contact angles);
  *   4  2D, two horizontally adjacent cells per thread in packed FP32
  *      arithmetic on strips of 64 columns marched in y, every input staged
  *      in shared memory by tensor copies one band of rows ahead, periodic

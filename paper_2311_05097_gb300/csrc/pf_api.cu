@@ -656,7 +656,8 @@ static bool split_ok(const Engine &E)
 {
     // (particles with their own contact angles act only within their reach: on
     // the near tiles, which run the single-cell step)
-    return E.dim == 2 && E.np > 0 && E.prec != PF_P64 && E.mem.size() == 1 && !any_walls(E) && !any_cac(E);
+    // (walls: the far tiles run the single-cell step's wall instantiation)
+    return E.dim == 2 && E.np > 0 && E.prec != PF_P64 && E.mem.size() == 1 && !any_cac(E);
 }
 
 // the staged 2D step copies 16-byte chunks: every domain's nx must keep its
@@ -731,7 +732,15 @@ static int issue_step(Engine &E, int par)
         const bool ok_near = launch_any(E, E.tx, E.ty, MODE_STEP, E.grid, an);
         E.stream = main;
         CK(cudaEventRecord(E.ev_join, E.side));
-        const bool ok_far = launch_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0, E.grid_far, af);
+        bool ok_far;
+        if (any_walls(E)) {
+            // walls: the single-cell step's wall instantiation without the particle
+            // terms, with the fixed solids' mu_phi0 grad phi0
+            af.mu0 = 1;
+            ok_far = launch_step2d(E.prec, E.tx, E.ty, false, MODE_STEP | mode_flags(E), E.grid_far, E.stream, af);
+        } else {
+            ok_far = launch_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0, E.grid_far, af);
+        }
         CK(cudaStreamWaitEvent(E.stream, E.ev_join, 0));
         if (!ok_near || !ok_far) return fail(PF_EINVAL, "split step of tile shape %dx%d not built", E.tx, E.ty);
     } else if (E.variant == 4) {
@@ -775,7 +784,8 @@ static int split_setup(Engine &E)
     if (!E.side) CK(cudaStreamCreateWithFlags(&E.side, cudaStreamNonBlocking));
     if (!E.ev_fork) CK(cudaEventCreateWithFlags(&E.ev_fork, cudaEventDisableTiming));
     if (!E.ev_join) CK(cudaEventCreateWithFlags(&E.ev_join, cudaEventDisableTiming));
-    const int occ = std::max(1, occupancy_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0));
+    const int occ = std::max(1, any_walls(E) ? occupancy_step2d(E.prec, E.tx, E.ty, false, MODE_STEP | mode_flags(E))
+                                             : occupancy_any(E, E.tx, E.ty, MODE_STEP_PAIR | MODE_MU0));
     E.grid_far = (int)std::max(1LL, std::min((long long)occ * E.nsm, (long long)E.ntiles));
     return PF_OK;
 }
@@ -943,7 +953,7 @@ static int engine_configure(Engine &E, bool tune)
             int tx, ty, var, cps;
             std::tie(tx, ty, var, cps) = it->second;
             if ((var == 3 && !split_ok(E)) || (var == 4 && !strip_ok(E)) ||
-                (var != 0 && (E.dim == 3 || (var != 4 && any_walls(E))))) {  // (the key separates these)
+                (var != 0 && (E.dim == 3 || (var != 4 && var != 3 && any_walls(E))))) {  // (the key separates these)
                 var = 0;
                 tx = 32;
                 ty = 8;
@@ -1855,18 +1865,18 @@ static int engine_force(Engine &E, int tile_x, int tile_y, int kernel, int ctas_
                                "particles, every nx even and >= %d, tile_x = %d (the strip width) and tile_y >= 1 "
                                "(the segment rows)", STRIP_GHOST, STRIP_SW);
     if (var == 3 && (!split_ok(E) || tile_x != 32 || tile_y != 16))
-        return fail(PF_EINVAL, "kernel 3 (near tiles single-cell, far tiles two-cells) needs one 2D particle "
-                               "domain in FP32 or 16-bit storage without walls, own angles or the Allen-Cahn "
+        return fail(PF_EINVAL, "kernel 3 (near tiles single-cell with the particle terms, far tiles without) "
+                               "needs one 2D particle domain in FP32 or 16-bit storage without the Allen-Cahn "
                                "lattice, and 32x16 tiles");
     if (ctas_per_sm < 0) return fail(PF_EINVAL, "ctas_per_sm must be >= 0");
-    if (var != 0 && var != 4 && any_walls(E))
-        return fail(PF_EINVAL, "domains with walls run kernels 0 and 4 only");
+    if (var != 0 && var != 3 && var != 4 && any_walls(E))
+        return fail(PF_EINVAL, "domains with walls run kernels 0, 3 and 4 only");
     if (var == 2 && !stage_ok(E))
         return fail(PF_EINVAL, "kernel 2 needs 2D, FP32 or 16-bit storage, no particles and every nx a "
                                "multiple of %d", E.prec == PF_P32 ? 4 : 8);
     const int mode = var == 4 ? MODE_STEP_STRIP : var == 2 ? MODE_STEP_STAGE : (var == 1 ? MODE_STEP_PAIR : MODE_STEP);
     if (occupancy_any(E, tile_x, tile_y, mode) < 1 ||
-        (var == 3 && occupancy_any(E, tile_x, tile_y, MODE_STEP_PAIR | MODE_MU0) < 1)) {
+        (var == 3 && !any_walls(E) && occupancy_any(E, tile_x, tile_y, MODE_STEP_PAIR | MODE_MU0) < 1)) {
         return fail(PF_EINVAL, "launch configuration %dx%d of kernel %d is not built for this precision / "
                     "particle setting", tile_x, tile_y, var);
     }

@@ -92,6 +92,19 @@ __device__ __forceinline__ void grad9(const R (*a)[W], int x, int y, R &gx, R &g
     gy = third * (n - s) + twelfth * ((ne + nw) - (se + sw));
 }
 
+// the same gradient of the cubes a^3
+template <class R, int W>
+__device__ __forceinline__ void grad9_cubed(const R (*a)[W], int x, int y, R &gx, R &gy)
+{
+    auto c3 = [](R v) { return v * v * v; };
+    const R e = c3(a[y][x + 1]), w = c3(a[y][x - 1]), n = c3(a[y + 1][x]), s = c3(a[y - 1][x]);
+    const R ne = c3(a[y + 1][x + 1]), nw = c3(a[y + 1][x - 1]), sw = c3(a[y - 1][x - 1]),
+            se = c3(a[y - 1][x + 1]);
+    const R third = R(1) / R(3), twelfth = R(1) / R(12);
+    gx = third * (e - w) + twelfth * ((ne + se) - (nw + sw));
+    gy = third * (n - s) + twelfth * ((ne + nw) - (se + sw));
+}
+
 template <class R, int W>
 __device__ __forceinline__ R lap9(const R (*a)[W], int x, int y)
 {
@@ -134,11 +147,12 @@ __device__ __forceinline__ R particle_phi0_rel(R dx, R dy, R Rp, R lim, R D, R &
 
 // Resident CTAs per SM requested from the register allocator: FP64 keeps its
 // registers (no cap); the 32 x 8 FP32/16-bit kernels trade a few spills for a
-// fourth CTA, 64 x 4 keeps three; the autotuner picks among the shapes.
+// fourth CTA, 64 x 4 keeps three, 32 x 16 (the near tiles of the split step)
+// two; the autotuner picks among the shapes.
 template <class P, int TX, int TY>
 constexpr int step2d_min_blocks()
 {
-    return P::id == 0 ? 1 : (TX * TY > 256 ? 1 : ((TX == 32 && TY == 8) ? 4 : 3));
+    return P::id == 0 ? 1 : (TX * TY > 256 ? 2 : ((TX == 32 && TY == 8) ? 4 : 3));
 }
 
 // EXT: the instantiation also handles domains with walls at the ends of y;
@@ -525,6 +539,28 @@ __global__ void __launch_bounds__(TX *TY, (step2d_min_blocks<P, TX, TY>())) k_st
                               c_wlap * lphi;
                 Fx += mu0 * g0x;
                 Fy += mu0 * g0y;
+            }
+        } else if constexpr (EXT && MODE == MODE_STEP) {
+            if (A.mu0) {
+                // far tiles of a particle simulation with walls (split step): the
+                // fixed solids' mu_phi0 grad phi0 of Eq. 19; with own particle
+                // angles in the simulation, the oracle's W/V form, in which the
+                // phi0^2 grad phi0 part is the stencil of phi0^3 over 3
+                const R lp = lap9<R, FX>(s_phi, hx, hy);
+                R g0x, g0y;
+                grad9<R, FX>(s_p0, hx, hy, g0x, g0y);
+                if (A.wv) {
+                    R g3x, g3y;
+                    grad9_cubed<R, FX>(s_p0, hx, hy, g3x, g3y);
+                    const R m = c_pen * phi0 * phi * phi + c_wet * phi * (phi * phi - R(1)) - c_wlap * lp;
+                    Fx += m * g0x + c_wet * phi * g3x;
+                    Fy += m * g0y + c_wet * phi * g3y;
+                } else {
+                    const R mu0 = c_pen * phi0 * phi * phi +
+                                  c_wet * phi * (R(3) * phi0 * phi0 + phi * phi - R(1)) - c_wlap * lp;
+                    Fx += mu0 * g0x;
+                    Fy += mu0 * g0y;
+                }
             }
         }
         if constexpr (MODE == MODE_MACROS) {

@@ -1127,3 +1127,37 @@ def test_3d_every_field_against_oracle(pf, precision, unit_rates):
     for k, v in e.items():
         assert v < MIXED_TOL_3D[precision][k], (k, v)
     assert g.diagnostics()["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 2e-3)])
+def test_split_particle_step_walls_against_oracle(pf, precision, tol_phi):
+    """The split step with walls at the ends of y: the far tiles run the
+    single-cell step's wall instantiation without the particle terms but with
+    the fixed solids' mu_phi0 grad phi0 (Eq. 19); one particle with its own
+    angle.  Against the FP64 oracle with walls after 200 steps and against
+    the single-cell step at the same precision."""
+    c = W.wall_case((128, 96), seed=6)
+    parts = [dict(x=(30.3, 60.6), u=(0.008, -0.003), w=(0.0, 0.0, 0.002), R=6.0, rho_p=2.0, theta_deg=120.0),
+             dict(x=(70.0, 40.0), u=(-0.006, 0.004), R=5.0, rho_p=1.5)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], c["params"]["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 200, precision=precision, particles=parts, config=(32, 16, 3), walls=True)
+    s, _ = run_pair(pf, c, 200, precision=precision, particles=parts, oracle=False, config=(32, 16, 0),
+                    walls=True)
+    assert g.config()[3] == 3
+    gm, om, sm = g.macros(), o.macros(), s.macros()
+    print("split-walls", precision, {k: "%.2e" % rel(gm[k], om[k]) for k in ("phi", "rho", "u", "P")})
+    assert rel(gm["phi"], om["phi"]) < tol_phi
+    assert rel(gm["rho"], om["rho"]) < tol_phi
+    for k in ("u", "P"):
+        assert rel(gm[k], om[k]) < 100 * tol_phi, k
+    for k, tol in (("phi", 1e-5), ("rho", 1e-5), ("u", 1e-3), ("P", 1e-3)):
+        assert rel(gm[k], sm[k]) < (tol if precision == "p32" else 10 * tol_phi), k
+    us = max(np.abs(om["u"]).max(), 1e-3)
+    for k in range(len(parts)):
+        pg, po = g.particle(k), o.particle(k)
+        assert np.abs(np.array(pg["x"]) - np.array(po.x)).max() < 1e-3
+        assert np.abs(np.array(pg["u"]) - np.array(po.u)).max() < 100 * tol_phi * us
+    assert g.diagnostics()["nan_flag"] == 0
