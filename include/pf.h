@@ -76,9 +76,9 @@ extern "C" {
  * and y = ny - 1/2 (the paper's box walls): halfway bounce-back of both
  * lattices at resting walls, and the finite-difference stencils see mirror
  * images of the rows inside (zero normal gradient of phi, mu and phi0).  In
- * 2D walls run the one-cell-per-thread step (kernel 0) or the strip step
- * (kernel 4).  Solid walls of any shape can also be given through the smooth
- * indicator phi0. */
+ * 2D walls run the one-cell-per-thread step (kernel 0), the strip step
+ * (kernel 4) or, with particles, the split step (kernel 3).  Solid walls of
+ * any shape can also be given through the smooth indicator phi0. */
 typedef struct pf_grid {
     int dim;
     int nx, ny, nz;
@@ -262,9 +262,10 @@ const char *pf_last_error(void);
  * the candidates on the live state) in the first step call of at least 256
  * steps, and cached per (dim, precision, size mix, domain count and the
  * features that decide which kernels can run it: walls, the Allen-Cahn
- * lattice, own contact angles, strip eligibility); a later batch of the same
- * kind takes the cached configuration in its first step call of any length.
- * Before that, steps run kernel 0. */
+ * lattice, own contact angles, strip eligibility, unit relaxation rates); a
+ * later batch of the same kind takes the cached configuration in its first
+ * step call of any length.  Before that, steps run kernel 0.  Step calls
+ * shorter than a 16-step chunk replay one-step graphs. */
 int pf_batch_create(int nd, const pf_grid *g, const pf_params *p, pf_batch **out);
 int pf_batch_init(pf_batch *b, int i, const double *phi0, const double *phi, const double *u,
                   const double *P, int where);
