@@ -476,6 +476,7 @@ struct Engine {
     int2 *d_mtxy = nullptr;
     std::vector<int> mbase, mcount;
     int *d_flags = nullptr;
+    int *d_queue = nullptr;  // work-queue counter of the strip step
     double *d_diag = nullptr;  // partials + out
     // particles (single-domain handles)
     ParticleDev hp[PF_MAX_PARTICLES];
@@ -525,6 +526,7 @@ static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
     CK(cudaMalloc(&E.d_doms, sizeof(DomainDev) * nd));
     CK(cudaMalloc(&E.d_flags, sizeof(int) * 4));
     CK(cudaMemset(E.d_flags, 0, sizeof(int) * 4));
+    CK(cudaMalloc(&E.d_queue, sizeof(int) * 4));
     CK(cudaMalloc(&E.d_diag, sizeof(double) * (3 * diag_blocks() + 8)));
     CK(cudaMalloc(&E.d_parts, sizeof(ParticleDev) * PF_MAX_PARTICLES));
     CK(cudaMalloc(&E.d_frep, sizeof(double) * 3 * PF_MAX_PARTICLES));
@@ -546,6 +548,7 @@ static void engine_free(Engine &E)
     if (E.d_tdom) cudaFree(E.d_tdom);
     if (E.d_txy) cudaFree(E.d_txy);
     if (E.d_flags) cudaFree(E.d_flags);
+    if (E.d_queue) cudaFree(E.d_queue);
     if (E.d_diag) cudaFree(E.d_diag);
     if (E.d_parts) cudaFree(E.d_parts);
     if (E.d_frep) cudaFree(E.d_frep);
@@ -746,7 +749,11 @@ static int issue_step(Engine &E, int par)
     } else if (E.variant == 4) {
         if (!E.ghosts_ok && !launch_any(E, STRIP_SW, 0, MODE_FILL_GHOSTS, (int)E.mem.size(), a))
             return fail(PF_EINVAL, "ghost pass not built");
-        if (!launch_any(E, E.tx, E.ty, MODE_STEP_STRIP, E.grid, a))
+        // the items after each CTA's first come from a work queue
+        StepArgs aq = a;
+        aq.queue = E.d_queue;
+        CK(cudaMemsetAsync(E.d_queue, 0, sizeof(int), E.stream));
+        if (!launch_any(E, E.tx, E.ty, MODE_STEP_STRIP, E.grid, aq))
             return fail(PF_EINVAL, "strip step of width %d not built", E.tx);
     } else if (!launch_any(E, E.tx, E.ty, step_mode(E), E.grid, a)) {
         return fail(PF_EINVAL, "tile shape %dx%d (variant %d) not built", E.tx, E.ty, E.variant);
@@ -982,8 +989,8 @@ static int engine_configure(Engine &E, bool tune)
     // pf_set_config but not a candidate: it measured slower than kernel 1)
     // (kernel 4: tile = strip width x segment rows)
     // (walls: kernels 0 and 4 only)
-    int shapes[10][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 64, 4},
-                         {64, 96, 4}, {64, 128, 4}, {64, 192, 4}};
+    int shapes[10][3] = {{32, 8, 0}, {64, 4, 0}, {32, 16, 0}, {32, 16, 1}, {64, 8, 1}, {32, 32, 1}, {64, 96, 4},
+                         {64, 128, 4}, {64, 192, 4}, {64, 256, 4}};
     int nshapes = (E.prec != PF_P64 && E.np == 0 && !any_walls(E)) ? 6 : 3;
     if (strip_ok(E)) {
         // on small launches (fewer than 8 work items of 96 rows per SM) also

@@ -228,6 +228,8 @@ struct StepArgs {
     int wait_polls;        // polls of one bounded device wait (staged kernel); 0: default
     const unsigned char *tile_sel;  // optional, per tile in device memory: run only the tiles ...
     int sel;                        // ... whose byte equals sel (else every tile)
+    int *queue;            // strip step: work-queue counter (zeroed before the launch), or
+                           // null: static round-robin over the items
     int mu0;               // single-cell step, wall instantiation, no particle terms: the
                            // tiles out of every particle's reach (split step) carry the
                            // fixed solids' mu_phi0 grad phi0 (Eq. 19)

@@ -292,7 +292,16 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
     const int polls = A.wait_polls > 0 ? A.wait_polls : STAGE_WAIT_POLLS;
     const char *maps_all = reinterpret_cast<const char *>(A.strip_maps);
 
-    for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+    // items: the first one by block index, the next ones from the work queue
+    // (largest first: the short items fill the end of the step), or round-robin
+    __shared__ int s_next;
+    auto next_item = [&](int it) -> int {
+        if (!A.queue) return it + gridDim.x;
+        if (tid == 0) s_next = gridDim.x + atomicAdd(A.queue, 1);
+        __syncthreads();
+        return s_next;
+    };
+    for (int it = blockIdx.x; it < A.nitems; it = next_item(it)) {
         const int4 item = A.items[it];
         const DomainDev &Dm = A.doms[item.x];
         const int x0 = item.y, ya = item.z, yb = item.w;
