@@ -413,9 +413,10 @@ static int domain_init(DomainMem &m, Staging &st, int dim, int prec, const doubl
     return PF_OK;
 }
 
-// tile table of a set of domains (2D tiles of tx x ty)
+// tile table of a set of domains (2D tiles of tx x ty; 3D column tiles of tx x ty
+// cells and zc planes)
 static void build_tiles(const std::vector<DomainMem *> &doms, int tx, int ty, std::vector<int> &tdom,
-                        std::vector<int2> &txy)
+                        std::vector<int2> &txy, int zc = ZCHUNK3D)
 {
     tdom.clear();
     txy.clear();
@@ -423,7 +424,8 @@ static void build_tiles(const std::vector<DomainMem *> &doms, int tx, int ty, st
         DomainDev &d = doms[k]->d;
         d.tiles_x = (d.nx + tx - 1) / tx;
         d.tiles_y = (d.ny + ty - 1) / ty;
-        d.tiles_z = d.p.dim == 3 ? (d.nz + ZCHUNK3D - 1) / ZCHUNK3D : 1;
+        d.zc = zc;
+        d.tiles_z = d.p.dim == 3 ? (d.nz + zc - 1) / zc : 1;
         d.tile_base = (int)tdom.size();
         // 3D tiles encode (y tile, z chunk) as y + tiles_y * z
         for (int kz = 0; kz < d.tiles_z; ++kz)

@@ -201,6 +201,7 @@ struct DomainDev {
     double *macro;   // MODE_MACROS output: phi, rho, u(dim), P, mu, phi0 (double)
     int tile_base;   // index of this domain's first tile in the partial-sum table
     int tiles_x, tiles_y, tiles_z;
+    int zc;                // 3D: planes per z chunk of a tile (the last chunk may be shorter)
     DevParams p;
     KParams<float> kf;
     KParams<double> kd;

@@ -322,7 +322,8 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
         const int zstride = Dm.pitch * ny;
         const int x0 = txy.x * TX;
         const int y0 = (txy.y % Dm.tiles_y) * TY;
-        const int z0 = (txy.y / Dm.tiles_y) * ZC;
+        const int zc = Dm.zc;
+        const int z0 = (txy.y / Dm.tiles_y) * zc;
         const DevParams &p = Dm.p;
         const KParams<R> &kp = kparams<R>(Dm);
 
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
         const R c_dw = kp.c_dw, c_lap = kp.c_lap, c_pen = kp.c_pen, c_wet = kp.c_wet,
                 c_wlap = kp.c_wlap;
 
-        // the planes touched lie in [z0 - 3, min(z0 + ZC, nz) + 2], inside
+        // the planes touched lie in [z0 - 3, min(z0 + zc, nz) + 2], inside
         // [-nz, 2 nz) since nz >= 4
         auto zoff = [&](int z) { return wrap_near(z, nz) * zstride; };
         auto cidx = [&](int tx_, int ty_, int zo) {  // tile+3 table coordinates
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
         // top of the plane, so that their round trip overlaps the loads of
         // phase 1 instead of following two barriers
         constexpr bool PRE = MODE == MODE_STEP && !MOVING && sizeof(R) == 4;
-        const int zend = min(z0 + ZC, nz);
+        const int zend = min(z0 + zc, nz);
         for (int z = z0; z < zend; ++z) {
             [[maybe_unused]] ST q1p[7], q2p[19];
             [[maybe_unused]] AX lagp[7];
