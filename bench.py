@@ -47,8 +47,10 @@ BYTES_PER_CELL_3D = {
     "fp16": 2 * 2 * (6 + 19) + 2 * 8 + 4 * 15,
     "bf16": 2 * 2 * (6 + 19) + 2 * 8 + 4 * 15,
 }
-DTYPE = {"p64": "f64", "p32": "f32", "fp16": "f16 storage, f32 arithmetic",
-         "bf16": "bf16 storage, f32 arithmetic"}
+# arithmetic type of the path (the storage type of the populations goes in config.storage)
+DTYPE = {"p64": "f64", "p32": "f32", "fp16": "f32", "bf16": "f32"}
+STORAGE = {"p64": "f64", "p32": "f32", "fp16": "f16 populations (int64 rest, f32 lagged fields)",
+           "bf16": "bf16 populations (int64 rest, f32 lagged fields)"}
 
 
 KERNEL_DESC = ["one cell per thread (tiles)", "two cells per thread (tiles)",
@@ -739,7 +741,8 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": DTYPE[r["prec"]], "data": "synthetic",
-        "config": dict(r["cfg"], order_parameter="allen-cahn" if args.phase_model else "cahn-hilliard"),
+        "config": dict(r["cfg"], storage=STORAGE[r["prec"]],
+                       order_parameter="allen-cahn" if args.phase_model else "cahn-hilliard"),
         "roofline": roofline_entry(args, r, peak, peak_src),
         "clocks": r["clk"], "e2e": r["e2e"], "gpu_launches": r["launches"], "cpu_baseline": cpu,
         "wall_s": round(r["t_wall"], 3),
