@@ -186,6 +186,16 @@ constexpr uint32_t fix24_limit_bits<__half>() { return 0x4800u; }
 template <>
 constexpr uint32_t fix24_limit_bits<__nv_bfloat16>() { return 0x4100u; }
 
+// the lane index, read afresh where it is used (volatile: the values derived
+// from it are not hoisted out of the band loop, where they would hold
+// registers through the update)
+__device__ __forceinline__ int lane_now()
+{
+    int l;
+    asm volatile("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+
 // ---- tensor copies ----------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(unsigned dst, const void *map, int x, int y, unsigned bar)
 {
@@ -363,6 +373,138 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             if (!my_ok) mbar_wait_bounded(bar(j & 1), (phases >> (j & 1)) & 1u, STAGE_WAIT_POLLS);
         };
 
+        // phi of pair m of row r (ring columns 2m, 2m + 1: x0 - 2 + 2m, + 1)
+        auto phi_pair = [&](int r, int m) {
+            // rs: the row whose phi this is (beyond a wall, the mirror image);
+            // blo / bhi: its pulls across the lower / upper wall bounce back
+            int rs = r;
+            bool blo = false, bhi = false;
+            if constexpr (WALL) {
+                if (s_it->wall) {
+                    if (r < -2 || r > ny + 1) {  // a row no update reads
+                        *reinterpret_cast<float2 *>(phir(r) + 2 * m) = make_float2(0.0f, 0.0f);
+                        return;
+                    }
+                    rs = r < 0 ? -1 - r : (r >= ny ? 2 * ny - 1 - r : r);
+                    blo = rs == 0;
+                    bhi = rs == ny - 1;
+                }
+            }
+            const int c = 2 * m + HS - 2;  // staged column of the left cell
+            // rows rs - 1, rs, rs + 1 (byte offsets of the left cell in the order-parameter box)
+            const int ro[3] = {srow_o(rs - 1) + L::O1 + c * L::ES, srow_o(rs) + L::O1 + c * L::ES,
+                               srow_o(rs + 1) + L::O1 + c * L::ES};
+            // the left cell's stored value of population i pulled from plane
+            // index k of the box (ko: that of the opposite population)
+            auto src = [&](int i, int k, int ko) -> const ST * {
+                if constexpr (WALL) {
+                    if ((CY9[i] == 1 && blo) || (CY9[i] == -1 && bhi))
+                        return reinterpret_cast<const ST *>(smem + ro[1]) + ko * L::W1;
+                }
+                return reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + k * L::W1 - CX9[i];
+            };
+            F2 phv;
+            if constexpr (P::MIX && UNIT) {
+                // the cells' exact fixed-point phi (rest + images of the pulled
+                // movers), rounded once to FP32; kept for the update's bookkeeping
+                const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(rs) + L::OR + 16 * m);
+                int sum[2] = {0, 0};
+                const F2 s24 = mk2(16777216.0f);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const ST *q = src(i, i - 1, OPP9[i] - 1);
+                    const F2 im = mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1])) * s24;
+                    sum[0] += __float2int_rn(im.v.x);
+                    sum[1] += __float2int_rn(im.v.y);
+                }
+                const long long ra = rv.x + fix24_to_rest(sum[0], s_it->klog1);
+                const long long rb = rv.y + fix24_to_rest(sum[1], s_it->klog1);
+                phv = mk2(float_of_fixed(ra), float_of_fixed(rb));
+                if (m >= 1 && m <= L::SW / 2)  // the strip's own columns
+                    *reinterpret_cast<longlong2 *>(rar(r) + 2 * (m - 1)) = make_longlong2(ra, rb);
+            } else if constexpr (P::MIX) {
+                const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(rs) + L::OR + 16 * m);
+                F2 movers = mk2(0.0f);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const ST *q = src(i, i - 1, OPP9[i] - 1);
+                    movers = movers + mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1]));
+                }
+                phv = fma2(movers, mk2(s_kp->inv_scale[0]), mk2(float_of_fixed(rv.x), float_of_fixed(rv.y)));
+            } else {
+                F2 acc = mk2(0.0f);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const ST *q = src(i, i, OPP9[i]);
+                    acc = acc + mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
+                }
+                phv = acc;
+            }
+            *reinterpret_cast<float2 *>(phir(r) + 2 * m) = phv.v;
+        };
+        // w of pair m of row r (ring columns 2m, 2m + 1: x0 - 1 + 2m, + 1)
+        auto w_pair = [&](int r, int m) {
+            const float *us = reinterpret_cast<const float *>(srow(r) + L::OA) + 2 * m + 3;  // left cell
+            float wv[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float ux = us[e], uy = us[L::WA + e];
+                const float Sx = us[2 * L::WA + e], Sy = us[3 * L::WA + e];
+                wv[e] = Sx * uy - ux * Sy;
+            }
+            if constexpr (WALL) {
+                if (s_it->wall && (r < 0 || r >= ny)) {  // odd under the wall mirror
+                    wv[0] = -wv[0];
+                    wv[1] = -wv[1];
+                }
+            }
+            *reinterpret_cast<float2 *>(wr(r) + 2 * m) = make_float2(wv[0], wv[1]);
+        };
+        // phi of the four halo cells of row r (ring columns 0, 1, SW + 2, SW + 3:
+        // x0 - 2, x0 - 1, x0 + SW, x0 + SW + 1) with unit rates and 16-bit storage,
+        // one pulled population per lane: lane 8h + k takes population k + 1 of
+        // halo cell h.  The images are integers, so their sum over the 8 lanes
+        // of a cell (a shuffle tree) is the one phi_pair forms in sequence.
+        // Every lane of the warp takes part (the shuffles).
+        auto phi_halo = [&](int r) {
+            const int ln = lane_now(), k = ln & 7, h = ln >> 3;
+            const int idx = h < 2 ? h : h + L::SW;  // ring column; staged column HS - 2 + idx
+            int rs = r;
+            bool blo = false, bhi = false;
+            if constexpr (WALL) {
+                if (s_it->wall) {
+                    if (r < -2 || r > ny + 1) {  // a row no update reads
+                        if (k == 0) phir(r)[idx] = 0.0f;
+                        return;
+                    }
+                    rs = r < 0 ? -1 - r : (r >= ny ? 2 * ny - 1 - r : r);
+                    blo = rs == 0;
+                    bhi = rs == ny - 1;
+                }
+            }
+            // c_x + 1, c_y + 1 and the opposite population's plane of population
+            // k + 1, four bits each (D2Q9 in the order of CX9 / CY9 / OPP9)
+            const int cx = (int)((0x20021012u >> (4 * k)) & 15u) - 1;
+            const int cy = (int)((0x00220121u >> (4 * k)) & 15u) - 1;
+            const int ko = (int)((0x54761032u >> (4 * k)) & 15u);
+            int row = rs - cy, pl = k, col = HS - 2 + idx - cx;
+            if constexpr (WALL) {
+                if ((cy == 1 && blo) || (cy == -1 && bhi)) {  // bounces back: own opposite population
+                    row = rs;
+                    pl = ko;
+                    col = HS - 2 + idx;
+                }
+            }
+            const ST q = reinterpret_cast<const ST *>(smem + srow_o(row) + L::O1)[pl * L::W1 + col];
+            int im = __float2int_rn(__fmul_rn(stored_to_float<ST>(q), 16777216.0f));
+            im += __shfl_xor_sync(0xffffffffu, im, 1);
+            im += __shfl_xor_sync(0xffffffffu, im, 2);
+            im += __shfl_xor_sync(0xffffffffu, im, 4);
+            if (k == 0) {
+                const long long rv = *reinterpret_cast<const long long *>(smem + srow_o(rs) + L::OR + 8 * idx);
+                phir(r)[idx] = float_of_fixed(rv + fix24_to_rest(im, s_it->klog1));
+            }
+        };
         // phase A: phi (Eq. 31) of rows [rp, rp + np_) on columns x0 - 2 .. x0 + SW + 2
         // and w = S_x u_y - u_x S_y of the previous step on rows [rw, rw + nw),
         // columns x0 - 1 .. x0 + SW + 1; one list of pair items
@@ -371,127 +513,101 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             const int nphi = np_ * NPP, ntot = nphi + nw * NPW;
             for (int j = tid; j < ntot; j += NT) {
                 if (j < nphi) {
-                    const int rr = j / NPP, m = j - rr * NPP;
-                    const int r = rp + rr;
-                    // rs: the row whose phi this is (beyond a wall, the mirror image);
-                    // blo / bhi: its pulls across the lower / upper wall bounce back
-                    int rs = r;
-                    bool blo = false, bhi = false;
-                    if constexpr (WALL) {
-                        if (s_it->wall) {
-                            if (r < -2 || r > ny + 1) {  // a row no update reads
-                                *reinterpret_cast<float2 *>(phir(r) + 2 * m) = make_float2(0.0f, 0.0f);
-                                continue;
-                            }
-                            rs = r < 0 ? -1 - r : (r >= ny ? 2 * ny - 1 - r : r);
-                            blo = rs == 0;
-                            bhi = rs == ny - 1;
-                        }
-                    }
-                    const int c = 2 * m + HS - 2;  // staged column of the left cell
-                    // rows rs - 1, rs, rs + 1 (byte offsets of the left cell in the order-parameter box)
-                    const int ro[3] = {srow_o(rs - 1) + L::O1 + c * L::ES, srow_o(rs) + L::O1 + c * L::ES,
-                                       srow_o(rs + 1) + L::O1 + c * L::ES};
-                    // the left cell's stored value of population i pulled from plane
-                    // index k of the box (ko: that of the opposite population)
-                    auto src = [&](int i, int k, int ko) -> const ST * {
-                        if constexpr (WALL) {
-                            if ((CY9[i] == 1 && blo) || (CY9[i] == -1 && bhi))
-                                return reinterpret_cast<const ST *>(smem + ro[1]) + ko * L::W1;
-                        }
-                        return reinterpret_cast<const ST *>(smem + ro[1 - CY9[i]]) + k * L::W1 - CX9[i];
-                    };
-                    F2 phv;
-                    if constexpr (P::MIX && UNIT) {
-                        // the cells' exact fixed-point phi (rest + images of the pulled
-                        // movers), rounded once to FP32; kept for the update's bookkeeping
-                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(rs) + L::OR + 16 * m);
-                        int sum[2] = {0, 0};
-                        const F2 s24 = mk2(16777216.0f);
-#pragma unroll
-                        for (int i = 1; i < 9; ++i) {
-                            const ST *q = src(i, i - 1, OPP9[i] - 1);
-                            const F2 im = mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1])) * s24;
-                            sum[0] += __float2int_rn(im.v.x);
-                            sum[1] += __float2int_rn(im.v.y);
-                        }
-                        const long long ra = rv.x + fix24_to_rest(sum[0], s_it->klog1);
-                        const long long rb = rv.y + fix24_to_rest(sum[1], s_it->klog1);
-                        phv = mk2(float_of_fixed(ra), float_of_fixed(rb));
-                        if (m >= 1 && m <= L::SW / 2)  // the strip's own columns
-                            *reinterpret_cast<longlong2 *>(rar(r) + 2 * (m - 1)) = make_longlong2(ra, rb);
-                    } else if constexpr (P::MIX) {
-                        const longlong2 rv = *reinterpret_cast<const longlong2 *>(smem + srow_o(rs) + L::OR + 16 * m);
-                        F2 movers = mk2(0.0f);
-#pragma unroll
-                        for (int i = 1; i < 9; ++i) {
-                            const ST *q = src(i, i - 1, OPP9[i] - 1);
-                            movers = movers + mk2(stored_to_float<ST>(q[0]), stored_to_float<ST>(q[1]));
-                        }
-                        phv = fma2(movers, mk2(s_kp->inv_scale[0]), mk2(float_of_fixed(rv.x), float_of_fixed(rv.y)));
-                    } else {
-                        F2 acc = mk2(0.0f);
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) {
-                            const ST *q = src(i, i, OPP9[i]);
-                            acc = acc + mk2(Conv<P>::ld(q[0], 1.0f), Conv<P>::ld(q[1], 1.0f));
-                        }
-                        phv = acc;
-                    }
-                    *reinterpret_cast<float2 *>(phir(r) + 2 * m) = phv.v;
+                    const int rr = j / NPP;
+                    phi_pair(rp + rr, j - rr * NPP);
                 } else {
-                    const int jj = j - nphi, rr = jj / NPW, m = jj - rr * NPW;
-                    const int r = rw + rr;
-                    const float *us = reinterpret_cast<const float *>(srow(r) + L::OA) + 2 * m + 3;  // left cell
-                    float wv[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const float ux = us[e], uy = us[L::WA + e];
-                        const float Sx = us[2 * L::WA + e], Sy = us[3 * L::WA + e];
-                        wv[e] = Sx * uy - ux * Sy;
-                    }
-                    if constexpr (WALL) {
-                        if (s_it->wall && (r < 0 || r >= ny)) {  // odd under the wall mirror
-                            wv[0] = -wv[0];
-                            wv[1] = -wv[1];
-                        }
-                    }
-                    *reinterpret_cast<float2 *>(wr(r) + 2 * m) = make_float2(wv[0], wv[1]);
+                    const int jj = j - nphi, rr = jj / NPW;
+                    w_pair(rw + rr, jj - rr * NPW);
                 }
+            }
+        };
+        // phase A of a band with unit rates and 16-bit storage, one row per warp:
+        // phi of row rp + warp, w of row rw + warp.  Each warp computes its own
+        // row's halo (the x halo makes a phi row 34 pairs and a w row 33 pairs
+        // wide; handed out as one list over the CTA, the items beyond 32 per row
+        // all fell to warp 0, which then reached every barrier last)
+        auto phase_a_rows = [&](int rp, int rw) {
+            phi_pair(rp + warp, lane + 1);
+            phi_halo(rp + warp);
+            w_pair(rw + warp, lane);
+            if (lane == 0) w_pair(rw + warp, L::SW / 2);
+        };
+        // mu_phi (Eq. 9) of pair m of row r (ring columns 2m, 2m + 1: x0 - 1 + 2m, + 1)
+        auto mu_pair = [&](int r, int m) {
+            const KParams<float> &kp = *s_kp;
+            const F2 c_dw = mk2(kp.c_dw), c_lap = mk2(-kp.c_lap), c_pen = mk2(kp.c_pen), c_wet = mk2(kp.c_wet),
+                     c_wlap = mk2(-kp.c_wlap), one = mk2(1.0f), three = mk2(3.0f);
+            // 4-wide windows [left - 1, right + 1] of rows r - 1, r, r + 1
+            float4 wp[3], w0[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float *pr = phir(r - 1 + d) + 2 * m;  // phi column of the left cell - 1
+                const float2 a = *reinterpret_cast<const float2 *>(pr);
+                const float2 b = *reinterpret_cast<const float2 *>(pr + 2);
+                wp[d] = make_float4(a.x, a.y, b.x, b.y);
+                const float *qr = reinterpret_cast<const float *>(srow(r - 1 + d) + L::O0) + 2 * m + 2;
+                const float2 e = *reinterpret_cast<const float2 *>(qr);
+                const float2 f = *reinterpret_cast<const float2 *>(qr + 2);
+                w0[d] = make_float4(e.x, e.y, f.x, f.y);
+            }
+            const F2 ph = mk2(wp[1].y, wp[1].z), p0 = mk2(w0[1].y, w0[1].z);
+            const F2 lp = lap9_hpair(wp), lp0 = lap9_hpair(w0);
+            const F2 p02 = p0 * p0;
+            F2 mu = c_dw * ph * ((ph - one) * (ph + one));
+            mu = fma2(c_lap, lp, mu);
+            mu = fma2(c_pen * p02, ph, mu);
+            mu = fma2(c_wet * p0, fma2(three * ph, ph, p02) - one, mu);
+            mu = fma2(c_wlap, lp0, mu);
+            *reinterpret_cast<float2 *>(mur(r) + 2 * m) = mu.v;
+        };
+        // mu_phi of the last pair of row r (ring columns SW, SW + 1: x0 + SW - 1,
+        // x0 + SW), spread over the warp: lane 16h + p loads stencil point p of
+        // cell h (both fields), shuffles form the sums of lap9_hpair in its
+        // order and lanes 0 and 16 finish each cell with the operations of
+        // mu_pair in its order, one rounding each: the same bits as mu_pair.
+        // Every lane of the warp takes part (the shuffles).
+        auto mu_halo = [&](int r) {
+            const KParams<float> &kp = *s_kp;
+            const int ln = lane_now(), h = ln >> 4, p = min(ln & 15, 8), base = ln & 16;
+            // stencil point p: Rc, Lc, Md, Mu, Rd, Ld, Ru, Lu, Mc (d: row r - 1, u: row r + 1),
+            // dx + 1 and dy + 1 two bits each
+            const int dx = (int)((0x12252u >> (2 * p)) & 3u) - 1;
+            const int dy = (int)((0x1a085u >> (2 * p)) & 3u) - 1;
+            const int j = L::SW + h;  // mu ring column of cell h (x0 - 1 + j)
+            const float a = phir(r + dy)[j + 1 + dx];
+            const float b = reinterpret_cast<const float *>(srow(r + dy) + L::O0)[j + 3 + dx];
+            // (Rc + Lc), (Md + Mu), (Rd + Ld), (Ru + Lu), then side and diag
+            const float a1 = __fadd_rn(a, __shfl_xor_sync(0xffffffffu, a, 1));
+            const float b1 = __fadd_rn(b, __shfl_xor_sync(0xffffffffu, b, 1));
+            const float a2 = __fadd_rn(a1, __shfl_xor_sync(0xffffffffu, a1, 2));
+            const float b2 = __fadd_rn(b1, __shfl_xor_sync(0xffffffffu, b1, 2));
+            const float adiag = __shfl_sync(0xffffffffu, a2, base + 4), bdiag = __shfl_sync(0xffffffffu, b2, base + 4);
+            const float ph = __shfl_sync(0xffffffffu, a, base + 8), p0 = __shfl_sync(0xffffffffu, b, base + 8);
+            if ((ln & 15) == 0) {
+                const float lp = __fmaf_rn(2.0f / 3.0f, a2, __fmaf_rn(1.0f / 6.0f, adiag, __fmul_rn(-10.0f / 3.0f, ph)));
+                const float lp0 = __fmaf_rn(2.0f / 3.0f, b2, __fmaf_rn(1.0f / 6.0f, bdiag, __fmul_rn(-10.0f / 3.0f, p0)));
+                const float p02 = __fmul_rn(p0, p0);
+                float mu = __fmul_rn(__fmul_rn(kp.c_dw, ph), __fmul_rn(__fsub_rn(ph, 1.0f), __fadd_rn(ph, 1.0f)));
+                mu = __fmaf_rn(-kp.c_lap, lp, mu);
+                mu = __fmaf_rn(__fmul_rn(kp.c_pen, p02), ph, mu);
+                mu = __fmaf_rn(__fmul_rn(kp.c_wet, p0), __fsub_rn(__fmaf_rn(__fmul_rn(3.0f, ph), ph, p02), 1.0f), mu);
+                mu = __fmaf_rn(-kp.c_wlap, lp0, mu);
+                mur(r)[j] = mu;
             }
         };
         // phase B: mu_phi (Eq. 9), rows [rs, rs + nr), columns x0 - 1 .. x0 + SW + 1
         auto phase_b = [&](int rs, int nr) {
             constexpr int NP = FM / 2;
-            const KParams<float> &kp = *s_kp;
-            const F2 c_dw = mk2(kp.c_dw), c_lap = mk2(-kp.c_lap), c_pen = mk2(kp.c_pen), c_wet = mk2(kp.c_wet),
-                     c_wlap = mk2(-kp.c_wlap), one = mk2(1.0f), three = mk2(3.0f);
             for (int j = tid; j < nr * NP; j += NT) {
-                const int rr = j / NP, m = j - rr * NP;
-                const int r = rs + rr;
-                // 4-wide windows [left - 1, right + 1] of rows r - 1, r, r + 1
-                float4 wp[3], w0[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const float *pr = phir(r - 1 + d) + 2 * m;  // phi column of the left cell - 1
-                    const float2 a = *reinterpret_cast<const float2 *>(pr);
-                    const float2 b = *reinterpret_cast<const float2 *>(pr + 2);
-                    wp[d] = make_float4(a.x, a.y, b.x, b.y);
-                    const float *qr = reinterpret_cast<const float *>(srow(r - 1 + d) + L::O0) + 2 * m + 2;
-                    const float2 e = *reinterpret_cast<const float2 *>(qr);
-                    const float2 f = *reinterpret_cast<const float2 *>(qr + 2);
-                    w0[d] = make_float4(e.x, e.y, f.x, f.y);
-                }
-                const F2 ph = mk2(wp[1].y, wp[1].z), p0 = mk2(w0[1].y, w0[1].z);
-                const F2 lp = lap9_hpair(wp), lp0 = lap9_hpair(w0);
-                const F2 p02 = p0 * p0;
-                F2 mu = c_dw * ph * ((ph - one) * (ph + one));
-                mu = fma2(c_lap, lp, mu);
-                mu = fma2(c_pen * p02, ph, mu);
-                mu = fma2(c_wet * p0, fma2(three * ph, ph, p02) - one, mu);
-                mu = fma2(c_wlap, lp0, mu);
-                *reinterpret_cast<float2 *>(mur(r) + 2 * m) = mu.v;
+                const int rr = j / NP;
+                mu_pair(rs + rr, j - rr * NP);
             }
+        };
+        // phase B of a band with unit rates and 16-bit storage, one row per warp
+        // (row rs + warp, its halo pair spread over the warp; see phase_a_rows)
+        auto phase_b_rows = [&](int rs) {
+            mu_pair(rs + warp, lane);
+            mu_halo(rs + warp);
         };
 
         // ---- prologue: rows ya - 3 .. ya + B + 2 staged; phi of ya - 2 .. ya + 1,
@@ -517,7 +633,11 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
                 }
             }
             const bool ok = k == 0 || wait_group(k);
-            if (ok) phase_a(Y + 2, B, Y + 1, B);
+            if constexpr (P::MIX && UNIT) {
+                if (__all_sync(0xffffffffu, ok)) phase_a_rows(Y + 2, Y + 1);  // (warp-uniform: shuffles)
+            } else {
+                if (ok) phase_a(Y + 2, B, Y + 1, B);
+            }
             fence_proxy_async_smem();  // this thread's reads of the ring precede the next copies
             if (tid == 0 && k + 1 < K) mbar_arrive_expect_tx(bar((k + 1) & 1), (unsigned)(B * L::ROW_TX));
             if (__syncthreads_or(!ok)) {  // barrier 1
@@ -528,7 +648,10 @@ __global__ void __launch_bounds__(32 * B, 2) k_step2d_strip(StepArgs A)
             if (k + 1 < K && lane < L::NBOX)
                 strip_copy<P, B>(maps(), A.par, x0, ya, ny, Y + B + 3 + warp, lane, sbase, bar((k + 1) & 1),
                                  WALL && s_it->wall);
-            phase_b(Y + 1, B);
+            if constexpr (P::MIX && UNIT)
+                phase_b_rows(Y + 1);
+            else
+                phase_b(Y + 1, B);
             __syncthreads();  // barrier 2
 
             // ---- phase C: the thread's two cells, row Y + warp, columns x0 + 2 lane, + 1
