@@ -273,9 +273,20 @@ int pf_batch_step(pf_batch *b, int64_t n);
 int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u, double *P,
                         double *mu, int where);
 /* Every domain of a batch in one call (no counterpart in the paper): the
- * same work as pf_batch_init / pf_batch_get_macros for i = 0 .. nd - 1, in
- * domain order on the batch's stream, with one wait at the end instead of
- * one per domain.  Each argument is an array of nd pointers, one per domain,
+ * same work as pf_batch_init / pf_batch_get_macros for i = 0 .. nd - 1 (the
+ * same results, bit for bit), with one wait at the end instead of one per
+ * domain.  Host copies run on a stream of the library's own, so that the
+ * copies of one domain overlap the kernels of others.  pf_batch_init_all
+ * stages host inputs in a device ring of 2^25 doubles (256 MiB, or the
+ * environment variable PF_INIT_RING read at create; at least one domain's
+ * inputs), allocated for the call and freed before it returns, reads device
+ * inputs in place, and runs the init kernels of consecutive domains on the
+ * batch's stream and three more streams of its own in turn (the batch's
+ * stream waits for them before the call returns).
+ * pf_batch_get_macros_all runs the macroscopic passes in domain order on the
+ * batch's stream, rotating over up to four macro buffers (the extra ones,
+ * as many as fit in 256 MiB, are allocated at its first call and kept with
+ * the batch).  Each argument is an array of nd pointers, one per domain,
  * with the layout of the single-domain call; phi0 and phi (and their
  * entries) are required; u, P (init) and any output array may be NULL (the
  * field is not given / not read), and so may single entries.  where applies

@@ -365,10 +365,8 @@ struct Staging {
     size_t n = 0;
 };
 
-static int staging_reserve(Staging &st, const DomainMem &m, int dim)
+static int staging_reserve_n(Staging &st, size_t need)
 {
-    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
-    const size_t need = (size_t)(2 + dim + 1 + 4) * N;  // phi0, phi, u, P, phi0tot, mu, W, V
     if (st.n >= need) return PF_OK;
     if (st.p) cudaFree(st.p);
     st.p = nullptr;
@@ -376,6 +374,12 @@ static int staging_reserve(Staging &st, const DomainMem &m, int dim)
     CK(cudaMalloc(&st.p, sizeof(double) * need));
     st.n = need;
     return PF_OK;
+}
+
+static int staging_reserve(Staging &st, const DomainMem &m, int dim)
+{
+    const long long N = (long long)m.d.nx * m.d.ny * m.d.nz;
+    return staging_reserve_n(st, (size_t)(2 + dim + 1 + 4) * N);  // phi0, phi, u, P, phi0tot, mu, W, V
 }
 
 static void staging_release(Staging &st)
@@ -388,6 +392,19 @@ static void domain_free(DomainMem &m)
 {
     if (m.base) cudaFree(m.base);
     m = DomainMem{};
+}
+
+// the init kernels of one domain from device arrays (phi0, phi, and u, P or
+// NULL, in the caller's layout); tmp: scratch of 4 N doubles (phi0tot, mu, W, V)
+static int domain_init_kernels(DomainMem &m, int prec, const double *phi0, const double *phi, const double *u,
+                               const double *P, double *tmp, const ParticleDev *d_parts,
+                               const ParticleDev *hparts, int np, int *flags, cudaStream_t s)
+{
+    int wv = 0;
+    for (int k = 0; k < np; ++k) wv |= hparts ? hparts[k].own : 0;
+    launch_init(prec, m.d, flags, phi0, phi, u, P, tmp, d_parts, np, wv, s);
+    CK(cudaGetLastError());
+    return PF_OK;
 }
 
 // copy caller arrays into the staging area and run the init kernels
@@ -406,11 +423,8 @@ static int domain_init(DomainMem &m, Staging &st, int dim, int prec, const doubl
     CK(cudaMemcpyAsync(sphi, phi, sizeof(double) * N, kind, s));
     if (u) CK(cudaMemcpyAsync(su, u, sizeof(double) * dim * N, kind, s));
     if (P) CK(cudaMemcpyAsync(sP, P, sizeof(double) * N, kind, s));
-    int wv = 0;
-    for (int k = 0; k < np; ++k) wv |= hparts ? hparts[k].own : 0;
-    launch_init(prec, m.d, flags, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, np, wv, s);
-    CK(cudaGetLastError());
-    return PF_OK;
+    return domain_init_kernels(m, prec, sp0, sphi, u ? su : nullptr, P ? sP : nullptr, tmp, d_parts, hparts, np,
+                               flags, s);
 }
 
 // tile table of a set of domains (2D tiles of tx x ty; 3D column tiles of tx x ty
@@ -474,6 +488,20 @@ struct Engine {
     // tables of the macro kernel, built on first use
     double *d_macro = nullptr;
     DomainDev *d_mdoms = nullptr;
+    // pf_batch_init_all / pf_batch_get_macros_all: host copies run on a copy
+    // stream beside the engine's stream (the input copies of later domains
+    // overlap the init kernels of earlier ones; the readback of a domain
+    // overlaps the macroscopic passes of the next ones).  The init kernels of
+    // consecutive domains go round-robin to the engine's stream and PIPE - 1
+    // more (small domains' kernels are launch-latency bound: they overlap);
+    // the macroscopic passes rotate over up to PIPE macro buffers
+    static constexpr int PIPE = 4;
+    cudaStream_t cstream = nullptr;
+    cudaStream_t kstream[PIPE - 1] = {};
+    cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_k[PIPE] = {}, ev_c[PIPE] = {};
+    int nslots = 0;                          // macro buffers in rotation (d_macro and d_macro_x)
+    double *d_macro_x[PIPE - 1] = {};
+    DomainDev *d_mdoms_x[PIPE - 1] = {};
     int *d_mtdom = nullptr;
     int2 *d_mtxy = nullptr;
     std::vector<int> mbase, mcount;
@@ -501,6 +529,10 @@ struct Engine {
     // environment variable PF_WAIT_POLLS at create (fault injection: a tiny
     // value makes the staged kernel's first wait give up -> PF_ETIMEOUT)
     int wait_polls = 0;
+    // doubles of the input ring of pf_batch_init_all (at least one domain's
+    // inputs); 0: 2^25.  Read from PF_INIT_RING at create (a small value makes
+    // the ring wrap after every domain: the ordering test)
+    long long init_ring = 0;
 };
 
 static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
@@ -508,6 +540,7 @@ static int engine_setup(Engine &E, int nd, const pf_grid *g, const pf_params *p)
     E.dim = g[0].dim;
     E.prec = p[0].precision;
     if (const char *w = std::getenv("PF_WAIT_POLLS")) E.wait_polls = std::max(0, std::atoi(w));
+    if (const char *w = std::getenv("PF_INIT_RING")) E.init_ring = std::max(0LL, std::atoll(w));
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&E.nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -544,6 +577,18 @@ static void engine_free(Engine &E)
     staging_release(E.staging);
     if (E.d_macro) cudaFree(E.d_macro);
     if (E.d_mdoms) cudaFree(E.d_mdoms);
+    for (int k = 0; k < Engine::PIPE - 1; ++k) {
+        if (E.d_macro_x[k]) cudaFree(E.d_macro_x[k]);
+        if (E.d_mdoms_x[k]) cudaFree(E.d_mdoms_x[k]);
+        if (E.kstream[k]) cudaStreamDestroy(E.kstream[k]);
+    }
+    for (int k = 0; k < Engine::PIPE; ++k) {
+        if (E.ev_k[k]) cudaEventDestroy(E.ev_k[k]);
+        if (E.ev_c[k]) cudaEventDestroy(E.ev_c[k]);
+    }
+    if (E.ev_in) cudaEventDestroy(E.ev_in);
+    if (E.ev_start) cudaEventDestroy(E.ev_start);
+    if (E.cstream) cudaStreamDestroy(E.cstream);
     if (E.d_mtdom) cudaFree(E.d_mtdom);
     if (E.d_mtxy) cudaFree(E.d_mtxy);
     if (E.d_doms) cudaFree(E.d_doms);
@@ -1248,16 +1293,41 @@ static int engine_macro_tables(Engine &E)
     return PF_OK;
 }
 
-// macroscopic pass of domain i into the engine's macro buffer (E.d_macro,
-// valid until the next macroscopic pass)
-static int engine_macros(Engine &E, int i)
+// the macro buffers of pf_batch_get_macros_all beyond the first (as many as
+// fit in 256 MiB together, 1 .. PIPE - 1) and their domain tables (the first
+// table with each domain's macro pointer moved to the buffer)
+static int engine_macro_slots(Engine &E)
+{
+    int rc = engine_macro_tables(E);
+    if (rc) return rc;
+    if (E.nslots) return PF_OK;
+    const int nd = (int)E.mem.size();
+    long long nmax = 0;
+    for (auto &m : E.mem) nmax = std::max(nmax, (long long)m.d.nx * m.d.ny * m.d.nz);
+    const size_t bytes = sizeof(double) * (size_t)(7 + 2 * E.dim) * nmax;
+    const int extra = (int)std::min<size_t>(Engine::PIPE - 1, std::max<size_t>(1, ((size_t)256 << 20) / bytes));
+    std::vector<DomainDev> dd(nd);
+    CK(cudaMemcpy(dd.data(), E.d_mdoms, sizeof(DomainDev) * nd, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < extra; ++k) {
+        CK(cudaMalloc(&E.d_macro_x[k], bytes));
+        for (auto &d : dd) d.macro = E.d_macro_x[k];
+        CK(cudaMalloc(&E.d_mdoms_x[k], sizeof(DomainDev) * nd));
+        CK(cudaMemcpy(E.d_mdoms_x[k], dd.data(), sizeof(DomainDev) * nd, cudaMemcpyHostToDevice));
+    }
+    E.nslots = 1 + extra;
+    return PF_OK;
+}
+
+// macroscopic pass of domain i into the engine's macro buffer (E.d_macro, or
+// E.d_macro_x[slot - 1]; valid until the next macroscopic pass into it)
+static int engine_macros(Engine &E, int i, int slot = 0)
 {
     int rc = engine_macro_tables(E);
     if (rc) return rc;
     int mtx = 32, mty = 8;
     if (E.dim == 3) tile_shape3d(E.prec, &mtx, &mty);
     StepArgs a{};
-    a.doms = E.d_mdoms;
+    a.doms = slot ? E.d_mdoms_x[slot - 1] : E.d_mdoms;
     a.tile_dom = E.d_mtdom + E.mbase[i];
     a.tile_xy = E.d_mtxy + E.mbase[i];
     a.ntiles = E.mcount[i];
@@ -1756,29 +1826,95 @@ extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const d
     PfRange range("pf_batch_init_all");
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (!phi0 || !phi) return fail(PF_EINVAL, "phi0 and phi are required");
+    if (where != PF_HOST && where != PF_DEVICE) return fail(PF_EINVAL, "where must be PF_HOST or PF_DEVICE");
     Engine &E = b->E;
     if (E.sticky) return E.sticky;
     if (E.t != 0) return fail(PF_ESTATE, "all domains are initialised before the first step");
+    const int nd = (int)E.mem.size();
+    for (int i = 0; i < nd; ++i)
+        if (!phi0[i] || !phi[i]) return fail(PF_EINVAL, "phi0 and phi are required (domain %d)", i);
     E.ghosts_ok = false;
-    // the staging area sized for the largest domain once (the inits reuse it in stream order)
-    size_t big = 0;
-    auto cells = [&](size_t i) { return (long long)E.mem[i].d.nx * E.mem[i].d.ny * E.mem[i].d.nz; };
-    for (size_t i = 1; i < E.mem.size(); ++i)
-        if (cells(i) > cells(big)) big = i;
-    if (!E.mem.empty()) {
-        int rc = staging_reserve(E.staging, E.mem[big], E.dim);
-        if (rc) return rc;
+    constexpr int NS = Engine::PIPE;
+    auto cells = [&](int i) { return (size_t)E.mem[i].d.nx * E.mem[i].d.ny * E.mem[i].d.nz; };
+    size_t nbig = 0;
+    for (int i = 0; i < nd; ++i) nbig = std::max(nbig, cells(i));
+    // each kernel stream's scratch for the init kernels (phi0tot, mu, W, V of
+    // the largest domain)
+    int rc = staging_reserve_n(E.staging, (size_t)NS * 4 * nbig);
+    if (rc) return rc;
+    if (!E.cstream) CK(cudaStreamCreateWithFlags(&E.cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < NS - 1; ++k)
+        if (!E.kstream[k]) CK(cudaStreamCreateWithFlags(&E.kstream[k], cudaStreamNonBlocking));
+    for (cudaEvent_t *ev : {&E.ev_in, &E.ev_start, &E.ev_k[0], &E.ev_k[1], &E.ev_k[2], &E.ev_k[3]})
+        if (!*ev) CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    cudaStream_t ks[NS] = {E.stream, E.kstream[0], E.kstream[1], E.kstream[2]};
+    const int d = E.dim;
+    const bool host = where == PF_HOST;
+    // host arrays: copied on the copy stream into a ring of device memory
+    // (2^25 doubles, or PF_INIT_RING; at least one domain's inputs), each
+    // domain's kernels waiting for its own copies; when the ring wraps, the
+    // copy stream first waits for the kernels of every domain queued so far.
+    // Device arrays are read in place.
+    auto need = [&](int i) { return (size_t)(2 + (u && u[i] ? d : 0) + (P && P[i] ? 1 : 0)) * cells(i); };
+    size_t cap = 0;
+    double *ring = nullptr;
+    if (host) {
+        cap = E.init_ring > 0 ? (size_t)E.init_ring : (size_t)1 << 25;
+        for (int i = 0; i < nd; ++i) cap = std::max(cap, need(i));
+        CK(cudaMalloc(&ring, sizeof(double) * cap));
     }
-    for (size_t i = 0; i < E.mem.size(); ++i) {
-        int rc = domain_init(E.mem[i], E.staging, E.dim, E.prec, phi0[i], phi[i], u ? u[i] : nullptr,
-                             P ? P[i] : nullptr, where, E.d_parts, nullptr, 0, E.d_flags, E.stream);
-        if (rc) {
-            cudaStreamSynchronize(E.stream);
-            return rc;
+    bool ok = true;
+    auto cuok = [&](cudaError_t e) { ok = ok && e == cudaSuccess; };
+    // the other kernel streams start after the work already queued on the batch's stream
+    cuok(cudaEventRecord(E.ev_start, E.stream));
+    for (int k = 1; k < NS; ++k) cuok(cudaStreamWaitEvent(ks[k], E.ev_start, 0));
+    if (host) cuok(cudaStreamWaitEvent(E.cstream, E.ev_start, 0));
+    size_t off = 0;
+    for (int i = 0; i < nd && ok && rc == PF_OK; ++i) {
+        const size_t N = cells(i);
+        cudaStream_t s = ks[i % NS];
+        const double *a0 = phi0[i], *a1 = phi[i], *au = u ? u[i] : nullptr, *aP = P ? P[i] : nullptr;
+        if (host) {
+            if (off + need(i) > cap) {
+                for (int k = 0; k < NS; ++k) {
+                    cuok(cudaEventRecord(E.ev_k[k], ks[k]));
+                    cuok(cudaStreamWaitEvent(E.cstream, E.ev_k[k], 0));
+                }
+                off = 0;
+            }
+            double *s0 = ring + off, *s1 = s0 + N, *su = s1 + N, *sP = su + (au ? (size_t)d * N : 0);
+            cuok(cudaMemcpyAsync(s0, a0, sizeof(double) * N, cudaMemcpyHostToDevice, E.cstream));
+            cuok(cudaMemcpyAsync(s1, a1, sizeof(double) * N, cudaMemcpyHostToDevice, E.cstream));
+            if (au) cuok(cudaMemcpyAsync(su, au, sizeof(double) * d * N, cudaMemcpyHostToDevice, E.cstream));
+            if (aP) cuok(cudaMemcpyAsync(sP, aP, sizeof(double) * N, cudaMemcpyHostToDevice, E.cstream));
+            cuok(cudaEventRecord(E.ev_in, E.cstream));
+            cuok(cudaStreamWaitEvent(s, E.ev_in, 0));
+            off += need(i);
+            a0 = s0;
+            a1 = s1;
+            au = au ? su : nullptr;
+            aP = aP ? sP : nullptr;
         }
+        if (ok)
+            rc = domain_init_kernels(E.mem[i], E.prec, a0, a1, au, aP, E.staging.p + (size_t)(i % NS) * 4 * nbig,
+                                     E.d_parts, nullptr, 0, E.d_flags, s);
     }
-    CK(cudaStreamSynchronize(E.stream));
-    for (size_t i = 0; i < E.mem.size(); ++i) E.inited[i] = true;
+    const cudaError_t last = cudaGetLastError();
+    // the batch's stream continues after every kernel stream
+    for (int k = 1; k < NS; ++k) {
+        cudaEventRecord(E.ev_k[k], ks[k]);
+        cudaStreamWaitEvent(E.stream, E.ev_k[k], 0);
+    }
+    cudaError_t es = host ? cudaStreamSynchronize(E.cstream) : cudaSuccess;
+    for (int k = 0; k < NS; ++k) {
+        const cudaError_t e = cudaStreamSynchronize(ks[k]);
+        if (es == cudaSuccess) es = e;
+    }
+    if (ring) cudaFree(ring);
+    if (rc) return rc;
+    if (!ok) return fail(PF_ECUDA, "init_all: %s", cudaGetErrorString(last));
+    if (es != cudaSuccess) return fail(PF_ECUDA, "init_all: %s", cudaGetErrorString(es));
+    for (int i = 0; i < nd; ++i) E.inited[i] = true;
     return PF_OK;
 }
 
@@ -1814,15 +1950,45 @@ extern "C" int pf_batch_get_macros_all(pf_batch *b, double *const *phi, double *
         if (!E.inited[i]) return fail(PF_ESTATE, "pf_batch_get_macros_all before every domain is initialised");
     int rc = engine_sync(E);
     if (rc && rc != PF_ENUMERIC) return rc;
-    for (size_t i = 0; i < E.mem.size(); ++i) {
-        rc = engine_queue_macros(E, (int)i, phi ? phi[i] : nullptr, rho ? rho[i] : nullptr, u ? u[i] : nullptr,
-                                 P ? P[i] : nullptr, mu ? mu[i] : nullptr, where);
-        if (rc) {
-            cudaStreamSynchronize(E.stream);
-            return rc;
-        }
+    rc = engine_macro_slots(E);
+    if (rc) return rc;
+    if (!E.cstream) CK(cudaStreamCreateWithFlags(&E.cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < E.nslots; ++k) {
+        if (!E.ev_k[k]) CK(cudaEventCreateWithFlags(&E.ev_k[k], cudaEventDisableTiming));
+        if (!E.ev_c[k]) CK(cudaEventCreateWithFlags(&E.ev_c[k], cudaEventDisableTiming));
     }
-    CK(cudaStreamSynchronize(E.stream));
+    // domain i: its macroscopic pass into buffer i % nslots on the batch's
+    // stream (after the copies of domain i - nslots out of that buffer), its
+    // copies on the copy stream (after that pass)
+    const cudaMemcpyKind kind = where == PF_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    const int d = E.dim, ns = E.nslots;
+    bool ok = true;
+    for (size_t i = 0; i < E.mem.size() && ok && rc == PF_OK; ++i) {
+        const int slot = (int)(i % ns);
+        if (i >= (size_t)ns) ok = cudaStreamWaitEvent(E.stream, E.ev_c[slot], 0) == cudaSuccess;
+        if (ok) rc = engine_macros(E, (int)i, slot);
+        if (rc) break;
+        const long long N = (long long)E.mem[i].d.nx * E.mem[i].d.ny * E.mem[i].d.nz;
+        const double *mac = slot ? E.d_macro_x[slot - 1] : E.d_macro;
+        ok = ok && cudaEventRecord(E.ev_k[slot], E.stream) == cudaSuccess &&
+             cudaStreamWaitEvent(E.cstream, E.ev_k[slot], 0) == cudaSuccess;
+        auto cp = [&](double *const *dst, const double *src, long long n) {
+            if (ok && dst && dst[i])
+                ok = cudaMemcpyAsync(dst[i], src, sizeof(double) * n, kind, E.cstream) == cudaSuccess;
+        };
+        cp(phi, mac, N);
+        cp(rho, mac + N, N);
+        cp(u, mac + 2 * N, (long long)d * N);
+        cp(P, mac + (2 + d) * N, N);
+        cp(mu, mac + (3 + d) * N, N);
+        ok = ok && cudaEventRecord(E.ev_c[slot], E.cstream) == cudaSuccess;
+    }
+    const cudaError_t last = cudaGetLastError();
+    const cudaError_t e1 = cudaStreamSynchronize(E.cstream), e2 = cudaStreamSynchronize(E.stream);
+    if (rc) return rc;
+    if (!ok) return fail(PF_ECUDA, "get_macros_all: %s", cudaGetErrorString(last));
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(PF_ECUDA, "get_macros_all: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
     return PF_OK;
 }
 

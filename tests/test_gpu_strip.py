@@ -326,3 +326,45 @@ def test_batch_init_all_and_macros_all_equal_per_domain_calls(pf):
         ma = a.macros(i)
         for k in FIELDS:
             assert np.array_equal(ma[k], mb[i][k]), (i, k)
+
+
+@pytest.mark.parametrize("ring", [None, "20000"])
+def test_batch_init_all_copy_stream_and_device_inputs(pf, monkeypatch, ring):
+    """pf_batch_init_all stages host inputs on its copy stream (the default
+    ring, and one so small that it wraps at every domain, where the copy
+    stream first waits for the kernels of the domains before) and reads
+    device inputs in place; pf_batch_get_macros_all alternates two macro
+    buffers (five domains: each reused).  Every field equals the per-domain
+    calls' bit for bit."""
+    import torch
+    cases = [W.flat_wall_drop(64, 40.0, 30.0), W.flat_wall_drop(128, 140.0, 3.0),
+             W.small_case((70, 96), seed=3, solid=True, theta_deg=120.0, u_amp=0.01),
+             W.flat_wall_drop(64, 90.0, 10.0),
+             W.small_case((40, 72), seed=4, solid=False, u_amp=0.02)]
+    shapes = [c["shape"] for c in cases]
+    params = [c["params"] for c in cases]
+    us = [c.get("u") for c in cases]
+    a = pf.Batch(shapes, params, precision="fp16")
+    for i, c in enumerate(cases):
+        a.init(i, c["phi0"], c["phi"], us[i])
+    if ring:
+        monkeypatch.setenv("PF_INIT_RING", ring)
+    b = pf.Batch(shapes, params, precision="fp16")
+    if ring:
+        monkeypatch.delenv("PF_INIT_RING")
+    b.init_all([c["phi0"] for c in cases], [c["phi"] for c in cases], us)
+    d = pf.Batch(shapes, params, precision="fp16")
+    dev = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    t0, t1, tu = ([dev(c["phi0"]) for c in cases], [dev(c["phi"]) for c in cases], [dev(x) for x in us])
+    torch.cuda.synchronize()
+    d.init_all(t0, t1, tu)
+    for x in (a, b, d):
+        x.set_config(64, 32, 4)
+        x.step(30)
+        x.sync()
+    mb, md = b.macros_all(), d.macros_all()
+    for i in range(len(cases)):
+        ma = a.macros(i)
+        for k in FIELDS:
+            assert np.array_equal(ma[k], mb[i][k]), ("host", i, k)
+            assert np.array_equal(ma[k], md[i][k]), ("device", i, k)
