@@ -281,7 +281,7 @@ int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u,
  * environment variable PF_INIT_RING read at create; at least one domain's
  * inputs), allocated for the call and freed before it returns, reads device
  * inputs in place, and runs the init kernels of consecutive domains on the
- * batch's stream and three more streams of its own in turn (the batch's
+ * batch's stream and seven more streams of its own in turn (the batch's
  * stream waits for them before the call returns).
  * pf_batch_get_macros_all runs the macroscopic passes in domain order on the
  * batch's stream, rotating over up to four macro buffers (the extra ones,

@@ -492,13 +492,13 @@ struct Engine {
     // stream beside the engine's stream (the input copies of later domains
     // overlap the init kernels of earlier ones; the readback of a domain
     // overlaps the macroscopic passes of the next ones).  The init kernels of
-    // consecutive domains go round-robin to the engine's stream and PIPE - 1
+    // consecutive domains go round-robin to the engine's stream and KS - 1
     // more (small domains' kernels are launch-latency bound: they overlap);
     // the macroscopic passes rotate over up to PIPE macro buffers
-    static constexpr int PIPE = 4;
+    static constexpr int PIPE = 4, KS = 8;
     cudaStream_t cstream = nullptr;
-    cudaStream_t kstream[PIPE - 1] = {};
-    cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_k[PIPE] = {}, ev_c[PIPE] = {};
+    cudaStream_t kstream[KS - 1] = {};
+    cudaEvent_t ev_in = nullptr, ev_start = nullptr, ev_k[KS] = {}, ev_c[PIPE] = {};
     int nslots = 0;                          // macro buffers in rotation (d_macro and d_macro_x)
     double *d_macro_x[PIPE - 1] = {};
     DomainDev *d_mdoms_x[PIPE - 1] = {};
@@ -580,12 +580,13 @@ static void engine_free(Engine &E)
     for (int k = 0; k < Engine::PIPE - 1; ++k) {
         if (E.d_macro_x[k]) cudaFree(E.d_macro_x[k]);
         if (E.d_mdoms_x[k]) cudaFree(E.d_mdoms_x[k]);
+    }
+    for (int k = 0; k < Engine::KS - 1; ++k)
         if (E.kstream[k]) cudaStreamDestroy(E.kstream[k]);
-    }
-    for (int k = 0; k < Engine::PIPE; ++k) {
+    for (int k = 0; k < Engine::KS; ++k)
         if (E.ev_k[k]) cudaEventDestroy(E.ev_k[k]);
+    for (int k = 0; k < Engine::PIPE; ++k)
         if (E.ev_c[k]) cudaEventDestroy(E.ev_c[k]);
-    }
     if (E.ev_in) cudaEventDestroy(E.ev_in);
     if (E.ev_start) cudaEventDestroy(E.ev_start);
     if (E.cstream) cudaStreamDestroy(E.cstream);
@@ -1834,7 +1835,7 @@ extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const d
     for (int i = 0; i < nd; ++i)
         if (!phi0[i] || !phi[i]) return fail(PF_EINVAL, "phi0 and phi are required (domain %d)", i);
     E.ghosts_ok = false;
-    constexpr int NS = Engine::PIPE;
+    constexpr int NS = Engine::KS;
     auto cells = [&](int i) { return (size_t)E.mem[i].d.nx * E.mem[i].d.ny * E.mem[i].d.nz; };
     size_t nbig = 0;
     for (int i = 0; i < nd; ++i) nbig = std::max(nbig, cells(i));
@@ -1845,9 +1846,14 @@ extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const d
     if (!E.cstream) CK(cudaStreamCreateWithFlags(&E.cstream, cudaStreamNonBlocking));
     for (int k = 0; k < NS - 1; ++k)
         if (!E.kstream[k]) CK(cudaStreamCreateWithFlags(&E.kstream[k], cudaStreamNonBlocking));
-    for (cudaEvent_t *ev : {&E.ev_in, &E.ev_start, &E.ev_k[0], &E.ev_k[1], &E.ev_k[2], &E.ev_k[3]})
+    for (cudaEvent_t *ev : {&E.ev_in, &E.ev_start})
         if (!*ev) CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
-    cudaStream_t ks[NS] = {E.stream, E.kstream[0], E.kstream[1], E.kstream[2]};
+    cudaStream_t ks[NS];
+    ks[0] = E.stream;
+    for (int k = 0; k < NS; ++k) {
+        if (!E.ev_k[k]) CK(cudaEventCreateWithFlags(&E.ev_k[k], cudaEventDisableTiming));
+        if (k) ks[k] = E.kstream[k - 1];
+    }
     const int d = E.dim;
     const bool host = where == PF_HOST;
     // host arrays: copied on the copy stream into a ring of device memory
