@@ -61,6 +61,8 @@ KERNEL_DESC = ["one cell per thread (tiles)", "two cells per thread (tiles)",
 
 # timed regions of K steps each in the batched workloads; the median is reported
 REPEATS = 5
+# end-to-end call sequences of the batched workloads; the median is reported
+E2E_REPEATS = 3
 
 
 def parse():
@@ -428,32 +430,39 @@ def run_batch(args, dist, rank, world, local):
                   torch.from_numpy(np.ascontiguousarray(c["phi"])).pin_memory(),
                   torch.empty(c["phi"].shape, dtype=torch.float64).pin_memory()) for c in cases]
         L = pf.load()
-        e2e_b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases],
-                         precision=prec, stream=stream.cuda_stream)
         nd = len(hosts)
         t_phi0 = (C.c_void_p * nd)(*[h[0].data_ptr() for h in hosts])
         t_phi = (C.c_void_p * nd)(*[h[1].data_ptr() for h in hosts])
         t_out = (C.c_void_p * nd)(*[h[2].data_ptr() for h in hosts])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc = L.pf_batch_init_all(e2e_b._h, C.cast(t_phi0, C.c_void_p), C.cast(t_phi, C.c_void_p), None, None,
-                                 pf.PF_HOST)
-        if rc:
-            raise pf.PfError(rc, pf.last_error())
-        e2e_b.step(S)
-        rc = L.pf_batch_get_macros_all(e2e_b._h, C.cast(t_out, C.c_void_p), None, None, None, None, pf.PF_HOST)
-        if rc:
-            raise pf.PfError(rc, pf.last_error())
-        dt = time.perf_counter() - t0
-        e2e_b.close()
+        # E2E_REPEATS call sequences, each on a batch created for it (outside the
+        # timed region); the median is reported
+        dts = []
+        for _ in range(E2E_REPEATS):
+            e2e_b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases],
+                             precision=prec, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc = L.pf_batch_init_all(e2e_b._h, C.cast(t_phi0, C.c_void_p), C.cast(t_phi, C.c_void_p), None, None,
+                                     pf.PF_HOST)
+            if rc:
+                raise pf.PfError(rc, pf.last_error())
+            e2e_b.step(S)
+            rc = L.pf_batch_get_macros_all(e2e_b._h, C.cast(t_out, C.c_void_p), None, None, None, None,
+                                           pf.PF_HOST)
+            if rc:
+                raise pf.PfError(rc, pf.last_error())
+            dts.append(time.perf_counter() - t0)
+            e2e_b.close()
+        dt = statistics.median(dts)
         e2e = {"value": round(cells * S / dt / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": 16 * cells // S, "d2h_bytes_per_step": 8 * cells // S,
                "h2d_bytes_per_call": 16 * cells, "d2h_bytes_per_call": 8 * cells,
                "steps_per_call": S,
-               "desc": "one call sequence: pf_batch_init_all (every domain from pinned host phi0, "
+               "desc": "each call sequence: pf_batch_init_all (every domain from pinned host phi0, "
                        "phi); pf_batch_step(%d) (includes the autotuner's timed steps when the "
                        "configuration is not cached); pf_batch_get_macros_all (phi of every domain "
-                       "to pinned host); wall clock" % S}
+                       "to pinned host); wall clock, median of %d sequences (ms: %s)"
+                       % (S, E2E_REPEATS, ", ".join("%.1f" % (v * 1e3) for v in dts))}
     b.close()
     cfg = {"workload": args.workload, "domains": len(cases), "cells": cells, "precision": prec,
            "desc": bw["desc"], "l2": "state (%.2f GB) larger than L2 (129 MB); no flush"
