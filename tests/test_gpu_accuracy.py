@@ -85,9 +85,9 @@ def test_cylinder_fp32_against_fp64(pf):
     for k in dphi:
         for v, b in zip(dphi[k], bound[k]):
             assert v <= b, (k, dphi[k])
-    # the drop is still relaxing at 20000 steps (sigma = 0.001): it only
-    # moves toward the equilibrium height, from R0 + Rp = 110
-    assert abs(H - Hth) < abs(110.0 - Hth) + 4.0
+    # the drop is still relaxing at 20000 steps (sigma = 0.001): its top has
+    # moved from R0 + Rp = 110 toward the equal-area height, not past it
+    assert abs(H - Hth) < abs(110.0 - Hth), (H, Hth)
 
 
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
@@ -144,21 +144,22 @@ def test_batch_contact_angles(pf):
 
 def test_drainage_3d_saturation(pf):
     """3D drainage through random spheres (D3Q19 + D3Q7, theta = 120 deg,
-    body force 1e-6, density ratio 10): FP16-storage saturation within 1e-3 of
-    FP64 (128^3 box, 1000 steps)."""
+    body force 1e-6, density ratio 10): saturation of the FP16-storage path
+    within the configuration's 1e-3 of FP64 (128^3 box, 1000 steps), and of
+    the FP32 and BF16-storage paths.  Measured: FP16 1.5e-8, FP32 6.7e-8,
+    BF16 2.5e-6."""
     c = W.porous_drainage_3d(n=128)
     steps = 1000
     sat = {}
-    for prec in ("p64", "p32", "fp16"):
+    for prec in ("p64", "p32", "fp16", "bf16"):
         s = run(pf, c, steps, prec)
         sat[prec] = A.saturation(s.macros()["phi"], c["phi0"])
         assert s.diagnostics()["nan_flag"] == 0
     S0 = A.saturation(c["phi"], c["phi0"])
     record("drainage_3d", n=128, steps=steps, porosity=c["porosity"], S_init=S0,
-           S_fp64=sat["p64"], S_fp32=sat["p32"], S_fp16=sat["fp16"])
-    assert abs(sat["p32"] - sat["p64"]) <= 1e-3
-    # measured 3.5e-3 at 1000 steps (FP32: 2e-7): recorded, bounded loosely
-    assert abs(sat["fp16"] - sat["p64"]) <= 5e-3
+           S_fp64=sat["p64"], S_fp32=sat["p32"], S_fp16=sat["fp16"], S_bf16=sat["bf16"])
+    for prec in ("p32", "fp16", "bf16"):
+        assert abs(sat[prec] - sat["p64"]) <= 1e-3, (prec, sat)
 
 
 def test_water_entry_bf16_against_fp64(pf):
