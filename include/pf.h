@@ -281,8 +281,9 @@ int pf_batch_get_macros(pf_batch *b, int i, double *phi, double *rho, double *u,
  * environment variable PF_INIT_RING read at create; at least one domain's
  * inputs), allocated for the call and freed before it returns, reads device
  * inputs in place, and runs the init kernels of consecutive domains on the
- * batch's stream and seven more streams of its own in turn (the batch's
- * stream waits for them before the call returns).
+ * batch's stream and up to seven more streams of its own in turn (as many as
+ * keep their scratch, 32 bytes per cell of the largest domain each, within
+ * 512 MiB; the batch's stream waits for them before the call returns).
  * pf_batch_get_macros_all runs the macroscopic passes in domain order on the
  * batch's stream, rotating over up to four macro buffers (the extra ones,
  * as many as fit in 256 MiB, are allocated at its first call and kept with

@@ -1295,7 +1295,7 @@ static int engine_macro_tables(Engine &E)
 }
 
 // the macro buffers of pf_batch_get_macros_all beyond the first (as many as
-// fit in 256 MiB together, 1 .. PIPE - 1) and their domain tables (the first
+// fit in 256 MiB together, 0 .. PIPE - 1) and their domain tables (the first
 // table with each domain's macro pointer moved to the buffer)
 static int engine_macro_slots(Engine &E)
 {
@@ -1306,7 +1306,7 @@ static int engine_macro_slots(Engine &E)
     long long nmax = 0;
     for (auto &m : E.mem) nmax = std::max(nmax, (long long)m.d.nx * m.d.ny * m.d.nz);
     const size_t bytes = sizeof(double) * (size_t)(7 + 2 * E.dim) * nmax;
-    const int extra = (int)std::min<size_t>(Engine::PIPE - 1, std::max<size_t>(1, ((size_t)256 << 20) / bytes));
+    const int extra = (int)std::min<size_t>(Engine::PIPE - 1, ((size_t)256 << 20) / bytes);
     std::vector<DomainDev> dd(nd);
     CK(cudaMemcpy(dd.data(), E.d_mdoms, sizeof(DomainDev) * nd, cudaMemcpyDeviceToHost));
     for (int k = 0; k < extra; ++k) {
@@ -1840,17 +1840,20 @@ extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const d
     size_t nbig = 0;
     for (int i = 0; i < nd; ++i) nbig = std::max(nbig, cells(i));
     // each kernel stream's scratch for the init kernels (phi0tot, mu, W, V of
-    // the largest domain)
-    int rc = staging_reserve_n(E.staging, (size_t)NS * 4 * nbig);
+    // the largest domain); as many streams as keep the scratch within 512 MiB
+    // (the streams help batches of small domains: their kernels are short)
+    const size_t per = sizeof(double) * 4 * std::max<size_t>(nbig, 1);
+    const int ns = (int)std::min<size_t>(NS, std::max<size_t>(1, ((size_t)512 << 20) / per));
+    int rc = staging_reserve_n(E.staging, (size_t)ns * 4 * nbig);
     if (rc) return rc;
     if (!E.cstream) CK(cudaStreamCreateWithFlags(&E.cstream, cudaStreamNonBlocking));
-    for (int k = 0; k < NS - 1; ++k)
+    for (int k = 0; k < ns - 1; ++k)
         if (!E.kstream[k]) CK(cudaStreamCreateWithFlags(&E.kstream[k], cudaStreamNonBlocking));
     for (cudaEvent_t *ev : {&E.ev_in, &E.ev_start})
         if (!*ev) CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
     cudaStream_t ks[NS];
     ks[0] = E.stream;
-    for (int k = 0; k < NS; ++k) {
+    for (int k = 0; k < ns; ++k) {
         if (!E.ev_k[k]) CK(cudaEventCreateWithFlags(&E.ev_k[k], cudaEventDisableTiming));
         if (k) ks[k] = E.kstream[k - 1];
     }
@@ -1873,16 +1876,16 @@ extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const d
     auto cuok = [&](cudaError_t e) { ok = ok && e == cudaSuccess; };
     // the other kernel streams start after the work already queued on the batch's stream
     cuok(cudaEventRecord(E.ev_start, E.stream));
-    for (int k = 1; k < NS; ++k) cuok(cudaStreamWaitEvent(ks[k], E.ev_start, 0));
+    for (int k = 1; k < ns; ++k) cuok(cudaStreamWaitEvent(ks[k], E.ev_start, 0));
     if (host) cuok(cudaStreamWaitEvent(E.cstream, E.ev_start, 0));
     size_t off = 0;
     for (int i = 0; i < nd && ok && rc == PF_OK; ++i) {
         const size_t N = cells(i);
-        cudaStream_t s = ks[i % NS];
+        cudaStream_t s = ks[i % ns];
         const double *a0 = phi0[i], *a1 = phi[i], *au = u ? u[i] : nullptr, *aP = P ? P[i] : nullptr;
         if (host) {
             if (off + need(i) > cap) {
-                for (int k = 0; k < NS; ++k) {
+                for (int k = 0; k < ns; ++k) {
                     cuok(cudaEventRecord(E.ev_k[k], ks[k]));
                     cuok(cudaStreamWaitEvent(E.cstream, E.ev_k[k], 0));
                 }
@@ -1902,17 +1905,17 @@ extern "C" int pf_batch_init_all(pf_batch *b, const double *const *phi0, const d
             aP = aP ? sP : nullptr;
         }
         if (ok)
-            rc = domain_init_kernels(E.mem[i], E.prec, a0, a1, au, aP, E.staging.p + (size_t)(i % NS) * 4 * nbig,
+            rc = domain_init_kernels(E.mem[i], E.prec, a0, a1, au, aP, E.staging.p + (size_t)(i % ns) * 4 * nbig,
                                      E.d_parts, nullptr, 0, E.d_flags, s);
     }
     const cudaError_t last = cudaGetLastError();
     // the batch's stream continues after every kernel stream
-    for (int k = 1; k < NS; ++k) {
+    for (int k = 1; k < ns; ++k) {
         cudaEventRecord(E.ev_k[k], ks[k]);
         cudaStreamWaitEvent(E.stream, E.ev_k[k], 0);
     }
     cudaError_t es = host ? cudaStreamSynchronize(E.cstream) : cudaSuccess;
-    for (int k = 0; k < NS; ++k) {
+    for (int k = 0; k < ns; ++k) {
         const cudaError_t e = cudaStreamSynchronize(ks[k]);
         if (es == cudaSuccess) es = e;
     }
