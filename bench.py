@@ -62,7 +62,7 @@ KERNEL_DESC = ["one cell per thread (tiles)", "two cells per thread (tiles)",
 # timed regions of K steps each in the batched workloads; the median is reported
 REPEATS = 5
 # end-to-end call sequences of the batched workloads; the median is reported
-E2E_REPEATS = 3
+E2E_REPEATS = 5
 
 
 def parse():
