@@ -160,6 +160,35 @@ def test_batch_strip_equals_single_runs(pf):
         assert v < TOL["fp16"][k], (k, v)
 
 
+def test_headline_configuration_against_oracle(pf):
+    """The batched benchmark's own configuration: drops on a flat wall slab
+    (wetting angles 40, 140 and 75 deg, density ratios 30, 3 and 100, s0 = 1.6,
+    unit rates otherwise), FP16 storage, one strip launch with 192-row
+    segments (the 256 x 256 domain takes two segments per strip): every field
+    of every domain against the FP64 oracle after 200 steps, within the FP16
+    bounds of the strip step (measured worst: phi 3.4e-6, rho 1.3e-6,
+    u 3.8e-4, P 6.4e-4, mu 1.9e-5)."""
+    cases = [W.flat_wall_drop(64, 40.0, 30.0), W.flat_wall_drop(128, 140.0, 3.0),
+             W.flat_wall_drop(256, 75.0, 100.0)]
+    steps = 200
+    b = pf.Batch([c["shape"] for c in cases], [c["params"] for c in cases], precision="fp16")
+    b.init_all([c["phi0"] for c in cases], [c["phi"] for c in cases])
+    b.set_config(64, 192, 4)
+    b.step(steps)
+    b.sync()
+    assert b.config()[3] == 4
+    assert b.diagnostics(0)["nan_flag"] == 0
+    mb = b.macros_all()
+    for i, c in enumerate(cases):
+        o = O.OracleSim(c["shape"], O.make_params(**c["params"]))
+        o.init(c["phi0"], c["phi"])
+        o.step(steps)
+        e = field_errors(mb[i], o.macros(), 3 * c["params"]["sigma"] / c["params"]["D"])
+        print("headline case", i, {k: "%.2e" % v for k, v in e.items()})
+        for k, v in e.items():
+            assert v < TOL["fp16"][k], (i, k, v)
+
+
 def test_strip_rejected_where_not_built(pf):
     """FP64 (no packed arithmetic), odd nx and a strip width other than 64
     are refused."""
