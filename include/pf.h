@@ -142,7 +142,7 @@ typedef struct pf_params {
 typedef struct pf_particle {
     double x[3], u[3], w[3];
     double R, rho_p;
-    double theta_deg;  /* own contact angle (Sec. 4.5; 2D only), or NaN for the
+    double theta_deg;  /* own contact angle (Sec. 4.5; 2D and 3D), or NaN for the
                           handle's theta_deg.  The wetting terms of Eqs. 8, 9, 19
                           are then summed per solid, each with its own angle;
                           all solids without an own angle form one solid. */

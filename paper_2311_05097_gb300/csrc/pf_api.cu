@@ -1707,7 +1707,6 @@ extern "C" int pf_particle_state(pf_handle *h, int k, pf_particle *io, int set)
         const bool own = !std::isnan(io->theta_deg);
         if (own && !(io->theta_deg > 0 && io->theta_deg < 180))
             return fail(PF_EINVAL, "particle theta_deg must be NaN or lie in (0, 180)");
-        if (own && E.dim == 3) return fail(PF_EINVAL, "own particle contact angles are built for 2D");
         if (io->prescribed < 0 || io->prescribed > 31)
             return fail(PF_EINVAL, "particle prescribed flags must lie in 0..31");
         if (E.np > 0) CK(cudaMemcpy(E.hp, E.d_parts, sizeof(ParticleDev) * E.np, cudaMemcpyDeviceToHost));

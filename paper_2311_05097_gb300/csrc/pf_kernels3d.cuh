@@ -310,6 +310,12 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
     __shared__ int s_gyi[TY + 6];  // wrapped rows
     __shared__ int s_out[EXT ? TY + 6 : 1];  // walls: the row lies beyond a wall (mirror image)
     __shared__ double s_red[2][NT / 32][6];  // warps' sums, double-buffered over particles
+    // particles with their own contact angle (MOVING with A.wv): W and V of
+    // every staged phi0 plane (the same ring of 5), in dynamic shared memory
+    // (2 * 5 * FP values of R; the launch passes none otherwise)
+    extern __shared__ __align__(16) unsigned char s_dyn3d[];
+    R *const s_W = reinterpret_cast<R *>(s_dyn3d);
+    R *const s_V = s_W + 5 * FP;
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -416,14 +422,33 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
             }
             return acc;
         };
-        auto phi0_at = [&](int hx, int hy, int z) -> R {
+        // total indicator at (frame x, frame y) of plane z; with own particle
+        // angles (Wo set) also W = sum_s cos(theta_s) phi0_s and V = sum_s
+        // cos(theta_s) phi0_s^3, every solid without an own angle counted as one
+        auto phi0_at = [&](int hx, int hy, int z, R *Wo, R *Vo) -> R {
             const int cx = hx + 1, cy = hy + 1;
             R v = (R)ldg(ph0 + cidx(cx, cy, zoff(z)));
             if constexpr (MOVING) {
                 const int gx = s_gx[cx], gy = s_gyi[cy], gz = wrap_near(z, nz);
+                R dflt = v, w = R(0), vv = R(0);
                 for (int k = 0; k < A.np; ++k) {
                     R rx, ry, rz;
-                    v += particle_phi0_3d<R>(A.parts[k], gx, gy, gz, nx, nyw, nz, p.D, p.cut, rx, ry, rz);
+                    const R pk = particle_phi0_3d<R>(A.parts[k], gx, gy, gz, nx, nyw, nz, p.D, p.cut, rx, ry, rz);
+                    v += pk;
+                    if (Wo) {
+                        if (A.parts[k].own) {
+                            const R ck = (R)A.parts[k].ct;
+                            w += ck * pk;
+                            vv += ck * pk * pk * pk;
+                        } else {
+                            dflt += pk;
+                        }
+                    }
+                }
+                if (Wo) {
+                    const R ct = (R)p.cos_t;
+                    *Wo = ct * dflt + w;
+                    *Vo = ct * dflt * dflt * dflt + vv;
                 }
             }
             return v;
@@ -433,7 +458,10 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
             for (int r = tid; r < FP; r += NT) {
                 const int hx = r % FX, hy = r / FX;
                 s_phi[slot][r] = phi_at(hx, hy, z, nullptr, nullptr);
-                s_p0[slot][r] = phi0_at(hx, hy, z);
+                if (MOVING && A.wv)
+                    s_p0[slot][r] = phi0_at(hx, hy, z, s_W + slot * FP + r, s_V + slot * FP + r);
+                else
+                    s_p0[slot][r] = phi0_at(hx, hy, z, nullptr, nullptr);
             }
         };
         auto load_T_plane = [&](int z) {
@@ -459,7 +487,17 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
             for (int r = tid; r < WP; r += NT) {
                 const int hx = r % WX + 1, hy = r / WX + 1;
                 const R ph = mid[hy * FX + hx], p0 = mid0[hy * FX + hx];
-                const R lp = lap19<R, FX>(lo, mid, hi, hx, hy), lp0 = lap19<R, FX>(lo0, mid0, hi0, hx, hy);
+                const R lp = lap19<R, FX>(lo, mid, hi, hx, hy);
+                if (MOVING && A.wv) {
+                    // wetting summed per solid (own particle angles), through W and V
+                    const R *Wl = s_W + wrap_idx(z - 1, 5) * FP, *Wm = s_W + wrap_idx(z, 5) * FP,
+                            *Wh = s_W + wrap_idx(z + 1, 5) * FP;
+                    const R Wv = Wm[hy * FX + hx], Vv = s_V[wrap_idx(z, 5) * FP + hy * FX + hx];
+                    s_mu[slot][r] = c_dw * ph * (ph - R(1)) * (ph + R(1)) - c_lap * lp + c_pen * p0 * p0 * ph +
+                                    c_dw * (R(3) * ph * ph * Wv + Vv - Wv) - c_lap * lap19<R, FX>(Wl, Wm, Wh, hx, hy);
+                    continue;
+                }
+                const R lp0 = lap19<R, FX>(lo0, mid0, hi0, hx, hy);
                 s_mu[slot][r] = c_dw * ph * (ph - R(1)) * (ph + R(1)) - c_lap * lp + c_pen * p0 * p0 * ph +
                                 c_wet * p0 * (R(3) * ph * ph + p0 * p0 - R(1)) - c_wlap * lp0;
             }
@@ -643,11 +681,24 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
                 R g0x, g0y, g0z;
                 grad19<R, FX>(s_p0[wrap_idx(z - 1, 5)], s_p0[wrap_idx(z, 5)], s_p0[wrap_idx(z + 1, 5)], hx, hy,
                               g0x, g0y, g0z);
-                const R mu0 = c_pen * phi0 * phi * phi + c_wet * phi * (R(3) * phi0 * phi0 + phi * phi - R(1)) -
-                              c_wlap * lphi;
-                Fx += mu0 * g0x;
-                Fy += mu0 * g0y;
-                Fz += mu0 * g0z;
+                if (A.wv) {
+                    // sum over solids of mu_phi0,s grad phi0_s with their own angles
+                    const int s0w = wrap_idx(z - 1, 5) * FP, s1w = wrap_idx(z, 5) * FP, s2w = wrap_idx(z + 1, 5) * FP;
+                    R gWx, gWy, gWz, gVx, gVy, gVz;
+                    grad19<R, FX>(s_W + s0w, s_W + s1w, s_W + s2w, hx, hy, gWx, gWy, gWz);
+                    grad19<R, FX>(s_V + s0w, s_V + s1w, s_V + s2w, hx, hy, gVx, gVy, gVz);
+                    const R pen = c_pen * phi0 * phi * phi;
+                    const R aW = c_dw * phi * (phi * phi - R(1)) - c_lap * lphi, aV = c_dw * phi;
+                    Fx += pen * g0x + aW * gWx + aV * gVx;
+                    Fy += pen * g0y + aW * gWy + aV * gVy;
+                    Fz += pen * g0z + aW * gWz + aV * gVz;
+                } else {
+                    const R mu0 = c_pen * phi0 * phi * phi +
+                                  c_wet * phi * (R(3) * phi0 * phi0 + phi * phi - R(1)) - c_wlap * lphi;
+                    Fx += mu0 * g0x;
+                    Fy += mu0 * g0y;
+                    Fz += mu0 * g0z;
+                }
             }
 
             R f2[19];
@@ -727,6 +778,10 @@ __global__ void __launch_bounds__(TX *TY, (sizeof(typename P::real) == 4 && !MOV
                     Dm.macro[5 * N + o] = (double)Pr;
                     Dm.macro[6 * N + o] = (double)mu;
                     Dm.macro[7 * N + o] = (double)phi0;
+                    if (MOVING && A.wv) {
+                        Dm.macro[8 * N + o] = (double)s_W[wrap_idx(z, 5) * FP + hy * FX + hx];
+                        Dm.macro[9 * N + o] = (double)s_V[wrap_idx(z, 5) * FP + hy * FX + hx];
+                    }
                 }
                 continue;
             } else {

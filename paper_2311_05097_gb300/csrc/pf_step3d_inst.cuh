@@ -10,13 +10,18 @@ template <class P, int TX, int TY, bool MOVING, int MODE, bool EXT, bool UNIT = 
 static bool run3d(int grid, cudaStream_t s, const StepArgs &a, int *occ)
 {
     auto kern = k_step3d<P, TX, TY, ZCHUNK3D, MOVING, MODE, EXT, UNIT>;
+    // particles with their own contact angle: the W and V plane rings (5
+    // planes of the tile + 2 frame each) in dynamic shared memory
+    const int dyn = (MOVING && a.wv) ? (int)(2 * 5 * (TX + 4) * (TY + 4) * sizeof(typename P::real)) : 0;
+    if (dyn && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+        return false;
     if (occ) {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, 0) != cudaSuccess) n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, TX * TY, dyn) != cudaSuccess) n = 0;
         *occ = n;
         return true;
     }
-    kern<<<grid, TX * TY, 0, s>>>(a);
+    kern<<<grid, TX * TY, dyn, s>>>(a);
     count_launches(1);
     return true;
 }

@@ -369,6 +369,39 @@ def test_p64_moving_sphere_matches_oracle(pf):
         assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, a, b)
 
 
+def test_p64_own_angles_3d_match_oracle(pf):
+    """3D particles with their own contact angle (Sec. 4.5, reading R18: the
+    wetting terms of Eqs. 8, 9, 19 summed per solid through W and V): a fixed
+    sphere at the handle's 60 deg, two free spheres at 45 and 135 deg and one
+    at the handle's angle, FP64 against the oracle: fields, the FP64
+    diagnostics (E_F through W and V) and every particle's state."""
+    c = W.small_case((20, 22, 24), seed=6, solid=True, theta_deg=60.0)
+    parts = [dict(x=(14.2, 6.3, 8.1), u=(0.004, 0.0, -0.002), w=(0.0, 0.001, 0.0), R=4.0, rho_p=2.0,
+                  theta_deg=45.0),
+             dict(x=(5.4, 15.2, 12.7), u=(-0.003, 0.002, 0.0), R=3.5, rho_p=1.5, theta_deg=135.0),
+             dict(x=(15.0, 16.5, 17.0), u=(0.0, 0.0, 0.003), R=3.0, rho_p=1.2)]
+    phi = c["phi"]
+    for pp in parts:
+        phi = (1.0 - W.disc(c["shape"], pp["x"], pp["R"], c["params"]["D"])) * phi
+    c["phi"] = phi
+    g, o = run_pair(pf, c, 20, particles=parts)
+    assert_fields(g.macros(), o.macros(), 1e-12, mu_scale=3 * c["params"]["sigma"] / c["params"]["D"])
+    dg, do = g.diagnostics(), o.diagnostics()
+    for k in ("mass", "E_F", "E_K"):
+        assert abs(dg[k] - do[k]) <= 1e-12 * max(abs(do[k]), 1e-12), (k, dg[k], do[k])
+    for k in range(3):
+        pg, po = g.particle(k), o.particle(k)
+        for f in ("x", "u", "w", "F", "T"):
+            a, b = np.array(pg[f]), np.array(getattr(po, f))
+            assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-12), (k, f, a, b)
+    # the reduced-precision paths (32 x 8 tiles: the W and V rings of FP32
+    # values in dynamic shared memory)
+    for precision, tol in (("p32", 1e-5), ("fp16", 5e-3)):
+        h, _ = run_pair(pf, c, 20, precision=precision, particles=parts, oracle=False)
+        assert rel(h.macros()["phi"], o.macros()["phi"]) < tol, precision
+        assert h.diagnostics()["nan_flag"] == 0
+
+
 @pytest.mark.parametrize("precision,tol_phi", [("p32", 1e-5), ("fp16", 5e-3)])
 def test_3d_reduced_precision_against_oracle(pf, precision, tol_phi):
     c = W.small_case((20, 24, 28), seed=9, solid=True, theta_deg=120.0, u_amp=0.01)
