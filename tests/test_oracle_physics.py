@@ -305,15 +305,17 @@ def test_repulsion_invariants():
     assert np.abs(O.repulsion(2, O.make_params(rep_xi=3.0, rep_eps=0.0), n, [a, b])).max() == 0.0
 
 
-def test_own_contact_angle_superposes_eq9():
-    """A particle with its own contact angle (reading R18): the oracle's mu_phi
-    equals Eq. 9 with the total phi0 and no wetting, plus the wetting part of
-    Eq. 9 of each solid with its own angle (the fixed disc at the simulation's
-    60 deg, the particle at 130 deg) -- the superposition the reading defines,
-    evaluated with the pinned pointwise Eq. 9."""
-    c = W.small_case((40, 48), seed=2, solid=True, theta_deg=60.0)
+@pytest.mark.parametrize("shape,xp,rp", [((40, 48), (34.0, 12.0), 6.0), ((16, 18, 20), (14.5, 12.0, 11.0), 4.0)])
+def test_own_contact_angle_superposes_eq9(shape, xp, rp):
+    """A particle with its own contact angle (reading R18), in 2D and 3D: the
+    oracle's mu_phi equals Eq. 9 with the total phi0 and no wetting, plus the
+    wetting part of Eq. 9 of each solid with its own angle (the fixed disc or
+    sphere at the simulation's 60 deg, the particle at 130 deg) -- the
+    superposition the reading defines, evaluated with the pinned pointwise
+    Eq. 9."""
+    c = W.small_case(shape, seed=2, solid=True, theta_deg=60.0)
     prm = dict(c["params"])
-    part = O.Particle((34.0, 12.0), R=6.0, rho_p=2.0, theta_deg=130.0)
+    part = O.Particle(xp, R=rp, rho_p=2.0, theta_deg=130.0)
     phi = (1.0 - W.disc(c["shape"], part.x, part.R, prm["D"])) * c["phi"]
     o = O.OracleSim(c["shape"], O.make_params(**prm))
     o.set_particle(0, part)
@@ -339,7 +341,7 @@ def test_own_contact_angle_superposes_eq9():
     assert err < 1e-14, err
     # the same particle without its own angle reproduces the single-angle path
     o2 = O.OracleSim(c["shape"], O.make_params(**prm))
-    o2.set_particle(0, O.Particle((34.0, 12.0), R=6.0, rho_p=2.0))
+    o2.set_particle(0, O.Particle(xp, R=rp, rho_p=2.0))
     o2.init(c["phi0"], phi)
     mu2 = o2.macros()["mu"]
     ref = np.array([eq9(P[60.0], p0_tot, i) for i in range(ph.size)]).reshape(ph.shape)
